@@ -1,0 +1,244 @@
+"""FP64 CPU oracle of the batched Crazyflie 2.x dynamics step (test infrastructure).
+
+TEST INFRASTRUCTURE ONLY. Only the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import this package. The CUDA
+library and its Python binding never import, link or call it, and the two share
+no code: the oracle keeps its own constant table, its own formulas and its own
+build.
+
+The arithmetic lives in ``mdg_oracle.c`` (plain double-precision loops written
+from the paper's Section 3.1 equations, the exponential map of Section 3.2 and
+the PID of Section 4.2); this module compiles it with gcc and exposes it to
+numpy. ``mlp.py`` holds the FP64 reference of the learned surrogate.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mdg_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+
+GND, DRAG, DW = 1, 2, 4
+ACT_RPM, ACT_PID = 0, 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile mdg_oracle.c into oracle/_build/liboracle.so (gcc, -O2, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Params(ctypes.Structure):
+    """Mirror of the oracle's own ``orc_params`` struct (field order as in mdg_oracle.c)."""
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "mass", "arm", "thrust2weight", "Jxx", "Jyy", "Jzz", "kf", "km", "prop_radius", "g",
+        "c_gnd", "h_clip", "c_xy", "c_z", "dw_c1", "dw_c2", "dw_c3", "dw_max_xy", "dw_dz_min")] + [
+        ("pos_kp", ctypes.c_double * 3), ("pos_ki", ctypes.c_double * 3), ("pos_kd", ctypes.c_double * 3),
+        ("pos_iclamp", ctypes.c_double),
+        ("att_kp", ctypes.c_double * 3), ("att_ki", ctypes.c_double * 3), ("att_kd", ctypes.c_double * 3),
+        ("att_iclamp", ctypes.c_double),
+        ("dt_sim", ctypes.c_double), ("dt_ctrl", ctypes.c_double)]
+
+    def to_dict(self) -> dict:
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if isinstance(v, ctypes.Array) else float(v)
+        return out
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int32)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            P = ctypes.POINTER(Params)
+            sig = {
+                "orc_params_size": ([], ctypes.c_int),
+                "orc_params_cf2x": ([P], None),
+                "orc_hover_rpm": ([P], ctypes.c_double),
+                "orc_max_rpm": ([P], ctypes.c_double),
+                "orc_quat_mul": ([_D, _D, _D], None),
+                "orc_rotation": ([_D, _D], None),
+                "orc_rpy": ([_D, _D], None),
+                "orc_motor": ([P, _D, _D, _D], None),
+                "orc_env_forces": ([P, ctypes.c_int, _D, _D, ctypes.c_int, _D, _D], None),
+                "orc_substep": ([P, ctypes.c_int, _D, _D, ctypes.c_int, ctypes.c_double, _D], None),
+                "orc_allocation_matrix": ([P, _D], None),
+                "orc_pid": ([P, _D, _D, _D, _D, _D, _D], None),
+                "orc_kin": ([_D, _D, _D], None),
+                "orc_knn": ([ctypes.c_int, _D, ctypes.c_int, ctypes.c_int, _I, _D], None),
+                "orc_control_steps": ([P, ctypes.c_int, _I, _I, _I, _D, _D, _D, _D, ctypes.c_int, ctypes.c_int,
+                                       _D, _I, _D], ctypes.c_int),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            if L.orc_params_size() != ctypes.sizeof(Params):
+                raise RuntimeError("oracle Params struct does not match orc_params")
+            _lib = L
+    return _lib
+
+
+def _dptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_D)
+
+
+def _iptr(a: np.ndarray):
+    assert a.dtype == np.int32 and a.flags.c_contiguous
+    return a.ctypes.data_as(_I)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def cf2x() -> Params:
+    """Default CF2X parameters of the oracle (its own table)."""
+    p = Params()
+    lib().orc_params_cf2x(ctypes.byref(p))
+    return p
+
+
+def hover_rpm(p: Params) -> float:
+    return lib().orc_hover_rpm(ctypes.byref(p))
+
+
+def max_rpm(p: Params) -> float:
+    return lib().orc_max_rpm(ctypes.byref(p))
+
+
+def quat_mul(a, b) -> np.ndarray:
+    a, b = _f64(a), _f64(b)
+    out = np.zeros(4)
+    lib().orc_quat_mul(_dptr(a), _dptr(b), _dptr(out))
+    return out
+
+
+def rotation(q) -> np.ndarray:
+    q = _f64(q)
+    R = np.zeros(9)
+    lib().orc_rotation(_dptr(q), _dptr(R))
+    return R.reshape(3, 3)
+
+
+def rpy(q) -> np.ndarray:
+    q = _f64(q)
+    out = np.zeros(3)
+    lib().orc_rpy(_dptr(q), _dptr(out))
+    return out
+
+
+def motor(p: Params, rpm):
+    rpm = _f64(rpm)
+    T = ctypes.c_double()
+    tau = np.zeros(3)
+    lib().orc_motor(ctypes.byref(p), _dptr(rpm), ctypes.byref(T), _dptr(tau))
+    return T.value, tau
+
+
+def env_forces(p: Params, x, rpm, flags: int):
+    """World force (gravity included) [N,3] and body torque [N,3] for one env."""
+    x, rpm = _f64(x), _f64(rpm)
+    N = x.shape[0]
+    F = np.zeros((N, 3))
+    tau = np.zeros((N, 3))
+    lib().orc_env_forces(ctypes.byref(p), N, _dptr(x), _dptr(rpm), int(flags), _dptr(F), _dptr(tau))
+    return F, tau
+
+
+def substep(p: Params, x, rpm, flags: int, dt: float | None = None) -> np.ndarray:
+    """One substep of one environment: x [N,13], rpm [N,4] -> x' [N,13]."""
+    x, rpm = _f64(x), _f64(rpm)
+    out = np.zeros_like(x)
+    lib().orc_substep(ctypes.byref(p), x.shape[0], _dptr(x), _dptr(rpm), int(flags),
+                      p.dt_sim if dt is None else float(dt), _dptr(out))
+    return out
+
+
+def allocation_matrix(p: Params) -> np.ndarray:
+    M = np.zeros(16)
+    lib().orc_allocation_matrix(ctypes.byref(p), _dptr(M))
+    return M.reshape(4, 4)
+
+
+def pid(p: Params, x, integ, wp):
+    """One PID call: returns (rpm[4], pos_err[3], yaw_err, new integ[6])."""
+    x, wp = _f64(x), _f64(wp)
+    integ = _f64(integ).copy()
+    rpm = np.zeros(4)
+    pe = np.zeros(3)
+    ye = ctypes.c_double()
+    lib().orc_pid(ctypes.byref(p), _dptr(x), _dptr(integ), _dptr(wp), _dptr(rpm), _dptr(pe), ctypes.byref(ye))
+    return rpm, pe, ye.value, integ
+
+
+def kin(x, a_prev) -> np.ndarray:
+    x, a_prev = _f64(x), _f64(a_prev)
+    out = np.zeros(20)
+    lib().orc_kin(_dptr(x), _dptr(a_prev), _dptr(out))
+    return out
+
+
+def knn(x_env, j: int, idx_base: int = 0):
+    """4-NN of drone j inside one environment x_env [N,13]: (idx[4] int32, rel[24])."""
+    x_env = _f64(x_env)
+    idx = np.zeros(4, dtype=np.int32)
+    rel = np.zeros(24)
+    lib().orc_knn(x_env.shape[0], _dptr(x_env), int(j), int(idx_base), _iptr(idx), _dptr(rel))
+    return idx, rel
+
+
+def control_steps(p: Params, env_off, env_flags, env_act, x, integ, a_prev, actions, n_sub: int,
+                  obs: bool = False):
+    """K control steps over a CSR batch. x [n,13], integ [n,6], a_prev [n,4] and actions [K,n,4]
+    (float64). Returns (x, integ, a_prev) updated copies, plus (kin, nbr_idx, nbr_rel) when obs."""
+    env_off = np.ascontiguousarray(env_off, dtype=np.int32)
+    env_flags = np.ascontiguousarray(env_flags, dtype=np.int32)
+    env_act = np.ascontiguousarray(env_act, dtype=np.int32)
+    x = _f64(x).copy()
+    integ = _f64(integ).copy()
+    a_prev = _f64(a_prev).copy()
+    actions = _f64(actions)
+    n = x.shape[0]
+    K = actions.shape[0]
+    assert actions.shape == (K, n, 4) and integ.shape == (n, 6) and a_prev.shape == (n, 4)
+    n_envs = env_off.shape[0] - 1
+    kin_o = nbr_i = nbr_r = None
+    if obs:
+        kin_o = np.zeros((n, 20))
+        nbr_i = np.zeros((n, 4), dtype=np.int32)
+        nbr_r = np.zeros((n, 24))
+    rc = lib().orc_control_steps(ctypes.byref(p), n_envs, _iptr(env_off), _iptr(env_flags), _iptr(env_act),
+                                 _dptr(x), _dptr(integ), _dptr(a_prev), _dptr(actions), K, int(n_sub),
+                                 _dptr(kin_o) if obs else None, _iptr(nbr_i) if obs else None,
+                                 _dptr(nbr_r) if obs else None)
+    if rc != 0:
+        raise ValueError("orc_control_steps rejected its arguments")
+    if obs:
+        return x, integ, a_prev, kin_o, nbr_i, nbr_r
+    return x, integ, a_prev

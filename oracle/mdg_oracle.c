@@ -1,0 +1,542 @@
+/*
+ * FP64 CPU oracle of the batched Crazyflie 2.x dynamics step (MuJoCo-Drones-Gym,
+ * Section 3.1 "Quadrotor Dynamics", Section 3.2 "Physics Modes", Section 4.2
+ * "Control").
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the correctness reference that the
+ * test suite, the smoke check and the benchmark's CPU-baseline leg compare the
+ * CUDA library against. The product path never links, loads or calls it, and it
+ * shares no code, header, constant table or helper with the CUDA library.
+ *
+ * It is written to be read against the paper, not to be fast: every drone of an
+ * environment is handled by plain loops in double precision, each step in the
+ * order the paper states it. Where the paper is silent the reading taken is named
+ * in the comment beside the code.
+ *
+ * Parity pins: every function here is checked by tests that do not re-derive it
+ * (closed forms, invariants, special cases, brute force); see the tests named
+ * test_oracle_*.py.
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared -o liboracle.so mdg_oracle.c -lm
+ * (-ffp-contract=off: the kNN selection below must round like the kernel does.)
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PI 3.14159265358979323846
+
+/* Physics-mode bits (Table "Physics modes": ground effect, drag, downwash). */
+#define ORC_GND 1
+#define ORC_DRAG 2
+#define ORC_DW 4
+
+/* Action types (Table "Action types"): raw RPM or an absolute PID waypoint. */
+#define ORC_ACT_RPM 0
+#define ORC_ACT_PID 1
+
+/* Model parameters. Field order is the oracle's own; the Python side of the
+ * oracle mirrors it. */
+typedef struct {
+    /* Table "Drone model parameters", CF2X column. */
+    double mass, arm, thrust2weight, Jxx, Jyy, Jzz, kf, km, prop_radius;
+    double g;
+    /* Eq. ground, Eq. drag, Eq. downwash coefficients. */
+    double c_gnd, h_clip, c_xy, c_z;
+    double dw_c1, dw_c2, dw_c3, dw_max_xy, dw_dz_min;
+    /* Table "Default PIDControl gains". */
+    double pos_kp[3], pos_ki[3], pos_kd[3], pos_iclamp;
+    double att_kp[3], att_ki[3], att_kd[3], att_iclamp;
+    double dt_sim, dt_ctrl;
+} orc_params;
+
+int orc_params_size(void) { return (int)sizeof(orc_params); }
+
+/* Section 3.3: HOVER_RPM = sqrt(m g / (4 k_f)). */
+double orc_hover_rpm(const orc_params* P) { return sqrt(P->mass * P->g / (4.0 * P->kf)); }
+
+/* Section 3.3: MAX_RPM from (m, g, k_f, T/W): the four rotors at MAX_RPM give
+ * thrust2weight times the weight, 4 k_f MAX_RPM^2 = (T/W) m g. */
+double orc_max_rpm(const orc_params* P)
+{
+    return sqrt(P->thrust2weight * P->mass * P->g / (4.0 * P->kf));
+}
+
+/* Default constants. Table "Drone model parameters" (CF2X), the downwash
+ * coefficients of Eq. downwash and the gains of Table "Default PIDControl gains"
+ * are printed in the paper. g, C_gnd, c_xy, c_z are not printed: g is MuJoCo's
+ * default gravity, the three aerodynamic coefficients are documented defaults.
+ * h_clip is "derived from the propeller radius and the model's maximum thrust"
+ * (Section 3.1.3): it is the height at which the ground-effect increment at hover
+ * thrust equals the spare thrust MAX_THRUST - m g, i.e.
+ * C_gnd m g (r_p/(4 h))^2 = (T/W - 1) m g. */
+void orc_params_cf2x(orc_params* P)
+{
+    memset(P, 0, sizeof(*P));
+    P->mass = 0.027;
+    P->arm = 0.0397;
+    P->thrust2weight = 2.25;
+    P->Jxx = 1.4e-5;
+    P->Jyy = 1.4e-5;
+    P->Jzz = 2.17e-5;
+    P->kf = 3.16e-10;
+    P->km = 7.94e-12;
+    P->prop_radius = 0.02325;
+    P->g = 9.81;
+    P->c_gnd = 11.36859;
+    P->h_clip = 0.25 * P->prop_radius * sqrt(P->c_gnd / (P->thrust2weight - 1.0));
+    P->c_xy = 9.1785e-7;
+    P->c_z = 10.311e-7;
+    P->dw_c1 = 2267.18;
+    P->dw_c2 = 0.16;
+    P->dw_c3 = -0.11;
+    P->dw_max_xy = 10.0;
+    P->dw_dz_min = 0.0;
+    P->pos_kp[0] = 0.4; P->pos_kp[1] = 0.4; P->pos_kp[2] = 1.0;
+    P->pos_ki[0] = 0.01; P->pos_ki[1] = 0.01; P->pos_ki[2] = 0.01;
+    P->pos_kd[0] = 0.9; P->pos_kd[1] = 0.9; P->pos_kd[2] = 2.0;
+    P->pos_iclamp = 2.0;
+    P->att_kp[0] = 2e-3; P->att_kp[1] = 2e-3; P->att_kp[2] = 1e-3;
+    P->att_ki[0] = 0.0; P->att_ki[1] = 0.0; P->att_ki[2] = 1e-4;
+    P->att_kd[0] = 5e-4; P->att_kd[1] = 5e-4; P->att_kd[2] = 2e-4;
+    P->att_iclamp = 0.5;
+    P->dt_sim = 1.0 / 240.0;
+    P->dt_ctrl = 1.0 / 48.0;
+}
+
+/* ---- quaternion helpers; q = [w, x, y, z], body-to-world (Section 3.1.1) ---- */
+
+/* Hamilton product a (x) b. */
+void orc_quat_mul(const double a[4], const double b[4], double out[4])
+{
+    double w = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+    double x = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+    double y = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    double z = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+    out[0] = w; out[1] = x; out[2] = y; out[3] = z;
+}
+
+/* Rotation matrix R (row-major 3x3) of a unit quaternion: world = R * body. */
+void orc_rotation(const double q[4], double R[9])
+{
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1.0 - 2.0 * (y * y + z * z);
+    R[1] = 2.0 * (x * y - w * z);
+    R[2] = 2.0 * (x * z + w * y);
+    R[3] = 2.0 * (x * y + w * z);
+    R[4] = 1.0 - 2.0 * (x * x + z * z);
+    R[5] = 2.0 * (y * z - w * x);
+    R[6] = 2.0 * (x * z - w * y);
+    R[7] = 2.0 * (y * z + w * x);
+    R[8] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+/* Roll, pitch, yaw (ZYX convention, R = Rz(yaw) Ry(pitch) Rx(roll)), the eta of
+ * the KIN observation (Section 3.4.4). */
+void orc_rpy(const double q[4], double rpy[3])
+{
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    double sp = 2.0 * (w * y - z * x);
+    if (sp > 1.0) sp = 1.0;
+    if (sp < -1.0) sp = -1.0;
+    rpy[0] = atan2(2.0 * (w * x + y * z), 1.0 - 2.0 * (x * x + y * y));
+    rpy[1] = asin(sp);
+    rpy[2] = atan2(2.0 * (w * z + x * y), 1.0 - 2.0 * (y * y + z * z));
+}
+
+/* ---- forces: Eq. motor, Eq. ground, Eq. drag, Eq. downwash ---- */
+
+/* Eq. motor with the X-configuration mixing (Section 3.1.2): per-rotor thrust
+ * F_i = k_f n_i^2, collective thrust T = sum F_i, body torques
+ * tau_x = L/sqrt2 (F0 + F1 - F2 - F3), tau_y = L/sqrt2 (-F0 + F1 + F2 - F3) and
+ * the yaw torque from the alternating reaction torques (-1)^{m_i} k_m n_i^2,
+ * read as m = (1, 0, 1, 0): tau_z = k_m (-n0^2 + n1^2 - n2^2 + n3^2).
+ * n is in RPM and k_f, k_m are per RPM^2 (HOVER_RPM with the printed k_f is
+ * about 14476, an RPM figure). */
+void orc_motor(const orc_params* P, const double rpm[4], double* T, double tau[3])
+{
+    double F[4], n2[4];
+    for (int i = 0; i < 4; ++i) {
+        n2[i] = rpm[i] * rpm[i];
+        F[i] = P->kf * n2[i];
+    }
+    *T = F[0] + F[1] + F[2] + F[3];
+    const double l = P->arm / sqrt(2.0);
+    tau[0] = l * (F[0] + F[1] - F[2] - F[3]);
+    tau[1] = l * (-F[0] + F[1] + F[2] - F[3]);
+    tau[2] = P->km * (-n2[0] + n2[1] - n2[2] + n2[3]);
+}
+
+/* World-frame force (gravity included) and body-frame torque on every drone of
+ * one environment of N drones. x is [N][13] = p(3) q(4) v(3) omega(3), omega in
+ * the body frame; rpm is [N][4]. All drones read the same state snapshot x. */
+void orc_env_forces(const orc_params* P, int N, const double* x, const double* rpm, int flags,
+                    double* F, double* tau)
+{
+    for (int j = 0; j < N; ++j) {
+        const double* xj = x + 13 * j;
+        const double* q = xj + 3;
+        const double* v = xj + 7;
+        double T, R[9];
+        orc_motor(P, rpm + 4 * j, &T, tau + 3 * j);
+        orc_rotation(q, R);
+        /* thrust along the body z axis, rotated to the world frame, and gravity */
+        double fw[3] = {R[2] * T, R[5] * T, R[8] * T - P->mass * P->g};
+
+        if (flags & ORC_GND) {
+            /* Eq. ground: C_gnd * sum_i k_f n_i^2 * (r_p/(4h))^2, h = max(p_z, h_clip),
+             * applied along world +z, gated on |roll|, |pitch| < pi/2. */
+            double rpy[3];
+            orc_rpy(q, rpy);
+            if (fabs(rpy[0]) < ORC_PI / 2 && fabs(rpy[1]) < ORC_PI / 2) {
+                double h = fmax(xj[2], P->h_clip);
+                double r = P->prop_radius / (4.0 * h);
+                fw[2] += P->c_gnd * T * r * r;
+            }
+        }
+        if (flags & ORC_DRAG) {
+            /* Eq. drag: F_body = -diag(c_xy, c_xy, c_z) (sum_i 2 pi n_i / 60) v_body,
+             * v_body = R^T v, rotated back to the world frame by R. */
+            const double* n = rpm + 4 * j;
+            double omega_sum = 0.0;
+            for (int i = 0; i < 4; ++i) omega_sum += 2.0 * ORC_PI * n[i] / 60.0;
+            double vb[3], fb[3];
+            for (int r = 0; r < 3; ++r) vb[r] = R[0 + r] * v[0] + R[3 + r] * v[1] + R[6 + r] * v[2];
+            fb[0] = -P->c_xy * omega_sum * vb[0];
+            fb[1] = -P->c_xy * omega_sum * vb[1];
+            fb[2] = -P->c_z * omega_sum * vb[2];
+            for (int r = 0; r < 3; ++r) fw[r] += R[3 * r + 0] * fb[0] + R[3 * r + 1] * fb[1] + R[3 * r + 2] * fb[2];
+        }
+        if (flags & ORC_DW) {
+            /* Eq. downwash: every drone i strictly above j (dz > max(0, dz_min)) with
+             * lateral separation dxy < dw_max_xy pushes j down by
+             * alpha exp(-1/2 (dxy/beta)^2), alpha = C1 (r_p/(4 dz))^2, beta = C2 dz + C3.
+             * beta^2 is floored at 1e-12 so that beta = 0 (dz = -C3/C2) stays finite. */
+            const double dz_min = fmax(0.0, P->dw_dz_min);
+            for (int i = 0; i < N; ++i) {
+                if (i == j) continue;
+                const double* xi = x + 13 * i;
+                double dz = xi[2] - xj[2];
+                if (!(dz > dz_min)) continue;
+                double dxy = hypot(xi[0] - xj[0], xi[1] - xj[1]);
+                if (!(dxy < P->dw_max_xy)) continue;
+                double r = P->prop_radius / (4.0 * dz);
+                double alpha = P->dw_c1 * r * r;
+                double beta = P->dw_c2 * dz + P->dw_c3;
+                double b2 = fmax(beta * beta, 1e-12);
+                fw[2] -= alpha * exp(-0.5 * dxy * dxy / b2);
+            }
+        }
+        F[3 * j + 0] = fw[0];
+        F[3 * j + 1] = fw[1];
+        F[3 * j + 2] = fw[2];
+    }
+}
+
+/* One physics substep of length dt for one environment (Section 3.2, DYN mode,
+ * "explicit Euler", plus the closed-form exponential map of _integrateQ).
+ * Reading: forward Euler — p uses the old v, v the old acceleration, omega the
+ * old angular acceleration, and q is advanced with the old omega. Newton-Euler:
+ * a = F/m, omega_dot = J^-1 (tau - omega x (J omega)), omega in the body frame.
+ * The exponential map is q+ = q (x) [cos(|w| dt/2), sin(|w| dt/2) w/|w|] (the
+ * norm-preserving reading of the printed map with Lambda the half quaternion-product
+ * matrix; a body-frame rate multiplies on the right), then q+ is renormalised. */
+void orc_substep(const orc_params* P, int N, const double* x_in, const double* rpm, int flags,
+                 double dt, double* x_out)
+{
+    double* F = (double*)malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
+    double* tau = (double*)malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
+    orc_env_forces(P, N, x_in, rpm, flags, F, tau);
+    const double J[3] = {P->Jxx, P->Jyy, P->Jzz};
+    for (int j = 0; j < N; ++j) {
+        const double* s = x_in + 13 * j;
+        double* o = x_out + 13 * j;
+        const double* p = s;
+        const double* q = s + 3;
+        const double* v = s + 7;
+        const double* w = s + 10;
+        double Jw[3] = {J[0] * w[0], J[1] * w[1], J[2] * w[2]};
+        double gyro[3] = {w[1] * Jw[2] - w[2] * Jw[1], w[2] * Jw[0] - w[0] * Jw[2], w[0] * Jw[1] - w[1] * Jw[0]};
+        double wdot[3];
+        for (int r = 0; r < 3; ++r) wdot[r] = (tau[3 * j + r] - gyro[r]) / J[r];
+        double pn[3], vn[3], wn[3], qn[4];
+        for (int r = 0; r < 3; ++r) {
+            pn[r] = p[r] + dt * v[r];
+            vn[r] = v[r] + dt * F[3 * j + r] / P->mass;
+            wn[r] = w[r] + dt * wdot[r];
+        }
+        double wnorm = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+        if (wnorm > 0.0) {
+            double half = 0.5 * wnorm * dt;
+            double dq[4] = {cos(half), sin(half) * w[0] / wnorm, sin(half) * w[1] / wnorm,
+                            sin(half) * w[2] / wnorm};
+            orc_quat_mul(q, dq, qn);
+        } else {
+            for (int r = 0; r < 4; ++r) qn[r] = q[r];
+        }
+        double qnorm = sqrt(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
+        for (int r = 0; r < 3; ++r) o[r] = pn[r];
+        for (int r = 0; r < 4; ++r) o[3 + r] = qn[r] / qnorm;
+        for (int r = 0; r < 3; ++r) o[7 + r] = vn[r];
+        for (int r = 0; r < 3; ++r) o[10 + r] = wn[r];
+    }
+    free(F);
+    free(tau);
+}
+
+/* ---- PID waypoint controller (Section 4.2.1, Table "Default PIDControl gains") ---- */
+
+/* Solve A x = b for a 4x4 A by Gaussian elimination with partial pivoting (the
+ * plain definition of the linear solve the controller performs). */
+static void solve4(double A[4][4], double b[4], double x[4])
+{
+    for (int c = 0; c < 4; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 4; ++r)
+            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+        if (piv != c) {
+            for (int k = 0; k < 4; ++k) {
+                double t = A[c][k];
+                A[c][k] = A[piv][k];
+                A[piv][k] = t;
+            }
+            double t = b[c];
+            b[c] = b[piv];
+            b[piv] = t;
+        }
+        for (int r = c + 1; r < 4; ++r) {
+            double f = A[r][c] / A[c][c];
+            for (int k = c; k < 4; ++k) A[r][k] -= f * A[c][k];
+            b[r] -= f * b[c];
+        }
+    }
+    for (int r = 3; r >= 0; --r) {
+        double s = b[r];
+        for (int k = r + 1; k < 4; ++k) s -= A[r][k] * x[k];
+        x[r] = s / A[r][r];
+    }
+}
+
+/* The allocation matrix M of Section 4.2.1: [T, tau_x, tau_y, tau_z] = M f with
+ * f_i = k_f n_i^2, the rows being Eq. motor's mixing (tau_z = (k_m/k_f) sum
+ * (-1)^{m_i} f_i). */
+void orc_allocation_matrix(const orc_params* P, double M[16])
+{
+    const double l = P->arm / sqrt(2.0), r = P->km / P->kf;
+    const double rows[4][4] = {{1, 1, 1, 1}, {l, l, -l, -l}, {-l, l, l, -l}, {-r, r, -r, r}};
+    for (int i = 0; i < 4; ++i)
+        for (int k = 0; k < 4; ++k) M[4 * i + k] = rows[i][k];
+}
+
+/* Wrap an angle to [-pi, pi). */
+static double wrap_pi(double a)
+{
+    double w = fmod(a + ORC_PI, 2.0 * ORC_PI);
+    if (w < 0.0) w += 2.0 * ORC_PI;
+    return w - ORC_PI;
+}
+
+/* One call of the cascaded PID (computeControl) for one drone. x is the 13-d
+ * state, integ[6] = [position error integral (3), attitude error integral (3)]
+ * (updated in place), wp = [x*, y*, z*, psi*]. Readings, where the paper prints
+ * only the structure, the gains and T = m |a*|:
+ *  - position loop a* = Kp e_p + Ki I_p + Kd (0 - v) + g z_hat, with
+ *    I_p = clamp(I_p + e_p dt_ctrl, +-pos_iclamp), dt_ctrl the control period;
+ *  - small-angle attitude target phi* = (a*_x sin psi* - a*_y cos psi*)/g,
+ *    theta* = (a*_x cos psi* + a*_y sin psi*)/g;
+ *  - attitude PID tau* = Kp e_eta + Ki I_eta + Kd (0 - omega), e_eta the roll,
+ *    pitch and wrapped yaw errors, I_eta clamped to +-att_iclamp;
+ *  - solve M f = [T*, tau*], clip each f_i to [0, k_f MAX_RPM^2] (standing in
+ *    for the unprinted torque clamp), n_i = sqrt(f_i / k_f).
+ * Returns (rpm, pos_error, yaw_error) like computeControl. */
+void orc_pid(const orc_params* P, const double x[13], double integ[6], const double wp[4],
+             double rpm[4], double pos_err[3], double* yaw_err)
+{
+    const double* p = x;
+    const double* q = x + 3;
+    const double* v = x + 7;
+    const double* w = x + 10;
+    double ep[3], a[3];
+    for (int r = 0; r < 3; ++r) {
+        ep[r] = wp[r] - p[r];
+        double I = integ[r] + ep[r] * P->dt_ctrl;
+        if (I > P->pos_iclamp) I = P->pos_iclamp;
+        if (I < -P->pos_iclamp) I = -P->pos_iclamp;
+        integ[r] = I;
+        a[r] = P->pos_kp[r] * ep[r] + P->pos_ki[r] * I + P->pos_kd[r] * (0.0 - v[r]);
+    }
+    a[2] += P->g;
+    double T = P->mass * sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    double psi_t = wp[3];
+    double phi_t = (a[0] * sin(psi_t) - a[1] * cos(psi_t)) / P->g;
+    double theta_t = (a[0] * cos(psi_t) + a[1] * sin(psi_t)) / P->g;
+    double rpy[3];
+    orc_rpy(q, rpy);
+    double ee[3] = {phi_t - rpy[0], theta_t - rpy[1], wrap_pi(psi_t - rpy[2])};
+    double tau[3];
+    for (int r = 0; r < 3; ++r) {
+        double I = integ[3 + r] + ee[r] * P->dt_ctrl;
+        if (I > P->att_iclamp) I = P->att_iclamp;
+        if (I < -P->att_iclamp) I = -P->att_iclamp;
+        integ[3 + r] = I;
+        tau[r] = P->att_kp[r] * ee[r] + P->att_ki[r] * I + P->att_kd[r] * (0.0 - w[r]);
+    }
+    double M[16], A[4][4], b[4] = {T, tau[0], tau[1], tau[2]}, f[4];
+    orc_allocation_matrix(P, M);
+    for (int i = 0; i < 4; ++i)
+        for (int k = 0; k < 4; ++k) A[i][k] = M[4 * i + k];
+    solve4(A, b, f);
+    const double maxrpm = orc_max_rpm(P);
+    const double fmax_ = P->kf * maxrpm * maxrpm;
+    for (int i = 0; i < 4; ++i) {
+        double fi = f[i];
+        if (fi < 0.0) fi = 0.0;
+        if (fi > fmax_) fi = fmax_;
+        rpm[i] = sqrt(fi / P->kf);
+    }
+    if (pos_err) {
+        for (int r = 0; r < 3; ++r) pos_err[r] = ep[r];
+    }
+    if (yaw_err) *yaw_err = ee[2];
+}
+
+/* ---- observations (Section 3.4.4) ---- */
+
+/* KIN observation: [p(3), q(4), rpy(3), v(3), omega(3), a_{t-1}(4)] (20 values).
+ * a_{t-1} is read as the four RPMs applied over the last control step. */
+void orc_kin(const double x[13], const double a_prev[4], double out[20])
+{
+    double rpy[3];
+    orc_rpy(x + 3, rpy);
+    for (int r = 0; r < 3; ++r) out[r] = x[r];
+    for (int r = 0; r < 4; ++r) out[3 + r] = x[3 + r];
+    for (int r = 0; r < 3; ++r) out[7 + r] = rpy[r];
+    for (int r = 0; r < 3; ++r) out[10 + r] = x[7 + r];
+    for (int r = 0; r < 3; ++r) out[13 + r] = x[10 + r];
+    for (int r = 0; r < 4; ++r) out[16 + r] = a_prev[r];
+}
+
+/* Neighbourhood-adjacency observation (the abstract's "neighbourhood adjacency
+ * information"; the format is not printed). Reading: the 4 nearest other drones
+ * of the same environment by Euclidean distance, ties to the lower index, padded
+ * with index -1 and zero features when the environment has fewer than 5 drones;
+ * features per neighbour i of drone j: [p_i - p_j, v_i - v_j].
+ * The selection is an integer decision taken from floating-point distances; it is
+ * made in single precision with the kernel's operation order (squared distance
+ * ((dx*dx + dy*dy) + dz*dz), each difference and product rounded to float, no fused
+ * multiply-add) so that both sides choose the same indices. The features are
+ * computed in double precision. idx_base is added to the local indices written. */
+void orc_knn(int N, const double* x, int j, int idx_base, int32_t idx[4], double rel[24])
+{
+    float bestd[4];
+    int besti[4];
+    int nb = 0;
+    const float xj = (float)x[13 * j + 0], yj = (float)x[13 * j + 1], zj = (float)x[13 * j + 2];
+    for (int i = 0; i < N; ++i) {
+        if (i == j) continue;
+        const float dx = (float)x[13 * i + 0] - xj;
+        const float dy = (float)x[13 * i + 1] - yj;
+        const float dz = (float)x[13 * i + 2] - zj;
+        const float dxx = dx * dx;
+        const float dyy = dy * dy;
+        const float dzz = dz * dz;
+        const float s = dxx + dyy;
+        const float d2 = s + dzz;
+        /* insert (d2, i) into the sorted list; strict '<' keeps the lower index first */
+        int pos = nb;
+        while (pos > 0 && d2 < bestd[pos - 1]) --pos;
+        if (pos >= 4) continue;
+        int last = nb < 4 ? nb : 3;
+        for (int k = last; k > pos; --k) {
+            bestd[k] = bestd[k - 1];
+            besti[k] = besti[k - 1];
+        }
+        bestd[pos] = d2;
+        besti[pos] = i;
+        if (nb < 4) ++nb;
+    }
+    for (int k = 0; k < 4; ++k) {
+        if (k < nb) {
+            int i = besti[k];
+            idx[k] = idx_base + i;
+            for (int r = 0; r < 3; ++r) {
+                rel[6 * k + r] = x[13 * i + r] - x[13 * j + r];
+                rel[6 * k + 3 + r] = x[13 * i + 7 + r] - x[13 * j + 7 + r];
+            }
+        } else {
+            idx[k] = -1;
+            for (int r = 0; r < 6; ++r) rel[6 * k + r] = 0.0;
+        }
+    }
+}
+
+/* ---- batched driver: K control steps over a CSR batch of environments ---- */
+
+/* Runs K control steps (Section 3.4.2: sim_freq/ctrl_freq substeps per step) for
+ * n_envs environments laid out in CSR order (drones of env e are
+ * env_off[e] .. env_off[e+1]-1). Per control step and environment: the action of
+ * each drone becomes four RPMs (ORC_ACT_RPM: clipped to [0, MAX_RPM]; ORC_ACT_PID:
+ * orc_pid towards the waypoint), the RPMs are held over n_sub substeps of dt_sim,
+ * and a_prev records them. After the last step the observations are written when
+ * kin is not NULL.
+ *   x        [n][13]   state, updated in place
+ *   integ    [n][6]    PID integrals, updated in place
+ *   a_prev   [n][4]    last applied RPMs, written
+ *   actions  [K][n][4] RPMs or waypoints
+ *   kin      [n][20], nbr_idx [n][4], nbr_rel [n][24] (optional)
+ * Returns 0, or -1 on a bad argument. */
+int orc_control_steps(const orc_params* P, int n_envs, const int32_t* env_off, const int32_t* env_flags,
+                      const int32_t* env_act, double* x, double* integ, double* a_prev, const double* actions,
+                      int K, int n_sub, double* kin, int32_t* nbr_idx, double* nbr_rel)
+{
+    if (n_envs < 0 || K < 0 || n_sub < 1) return -1;
+    int maxN = 0;
+    for (int e = 0; e < n_envs; ++e) {
+        int N = env_off[e + 1] - env_off[e];
+        if (N < 0) return -1;
+        if (N > maxN) maxN = N;
+    }
+    const int64_t n = n_envs > 0 ? env_off[n_envs] : 0;
+    double* rpm = (double*)malloc(sizeof(double) * 4 * (size_t)(maxN > 0 ? maxN : 1));
+    double* tmp = (double*)malloc(sizeof(double) * 13 * (size_t)(maxN > 0 ? maxN : 1));
+    const double maxrpm = orc_max_rpm(P);
+    for (int k = 0; k < K; ++k) {
+        const double* act = actions + (size_t)k * (size_t)n * 4;
+        for (int e = 0; e < n_envs; ++e) {
+            const int b = env_off[e], N = env_off[e + 1] - env_off[e];
+            for (int j = 0; j < N; ++j) {
+                const double* a = act + 4 * (size_t)(b + j);
+                if (env_act[e] == ORC_ACT_PID) {
+                    orc_pid(P, x + 13 * (size_t)(b + j), integ + 6 * (size_t)(b + j), a, rpm + 4 * j, NULL, NULL);
+                } else {
+                    for (int i = 0; i < 4; ++i) {
+                        double r = a[i];
+                        if (r < 0.0) r = 0.0;
+                        if (r > maxrpm) r = maxrpm;
+                        rpm[4 * j + i] = r;
+                    }
+                }
+                for (int i = 0; i < 4; ++i) a_prev[4 * (size_t)(b + j) + i] = rpm[4 * j + i];
+            }
+            for (int s = 0; s < n_sub; ++s) {
+                orc_substep(P, N, x + 13 * (size_t)b, rpm, env_flags[e], P->dt_sim, tmp);
+                memcpy(x + 13 * (size_t)b, tmp, sizeof(double) * 13 * (size_t)N);
+            }
+        }
+    }
+    if (kin) {
+        for (int e = 0; e < n_envs; ++e) {
+            const int b = env_off[e], N = env_off[e + 1] - env_off[e];
+            for (int j = 0; j < N; ++j) {
+                orc_kin(x + 13 * (size_t)(b + j), a_prev + 4 * (size_t)(b + j), kin + 20 * (size_t)(b + j));
+                if (nbr_idx && nbr_rel)
+                    orc_knn(N, x + 13 * (size_t)b, j, b, nbr_idx + 4 * (size_t)(b + j),
+                            nbr_rel + 24 * (size_t)(b + j));
+            }
+        }
+    }
+    free(rpm);
+    free(tmp);
+    return 0;
+}

@@ -1,0 +1,68 @@
+"""The oracle pins have teeth: plant plausible mistakes in a copy of the oracle and
+check that the pin suite (test_oracle_dynamics.py) fails on each.
+
+Mistakes are planted only in a temporary copy of the oracle, on the CPU; the real
+oracle is not modified. CPU only.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# name: (text in mdg_oracle.c, planted mistake)
+MUTATIONS = {
+    "gyroscopic_sign": ("wdot[r] = (tau[3 * j + r] - gyro[r]) / J[r];",
+                        "wdot[r] = (tau[3 * j + r] + gyro[r]) / J[r];"),
+    "semi_implicit_position": ("pn[r] = p[r] + dt * v[r];",
+                               "pn[r] = p[r] + dt * (v[r] + dt * F[3 * j + r] / P->mass);"),
+    "world_frame_rate": ("orc_quat_mul(q, dq, qn);", "orc_quat_mul(dq, q, qn);"),
+    "full_angle_exp_map": ("double half = 0.5 * wnorm * dt;", "double half = wnorm * dt;"),
+    "transposed_thrust_axis": ("double fw[3] = {R[2] * T, R[5] * T, R[8] * T - P->mass * P->g};",
+                               "double fw[3] = {R[6] * T, R[7] * T, R[8] * T - P->mass * P->g};"),
+    "drag_axis_coefficient": ("fb[2] = -P->c_z * omega_sum * vb[2];", "fb[2] = -P->c_xy * omega_sum * vb[2];"),
+    "drag_not_rotated_back": (
+        "for (int r = 0; r < 3; ++r) fw[r] += R[3 * r + 0] * fb[0] + R[3 * r + 1] * fb[1] + R[3 * r + 2] * fb[2];",
+        "for (int r = 0; r < 3; ++r) fw[r] += R[r + 0] * fb[0] + R[r + 3] * fb[1] + R[r + 6] * fb[2];"),
+    "ground_effect_not_squared": ("fw[2] += P->c_gnd * T * r * r;", "fw[2] += P->c_gnd * T * r;"),
+    "ground_effect_ungated": ("if (fabs(rpy[0]) < ORC_PI / 2 && fabs(rpy[1]) < ORC_PI / 2) {", "if (1) {"),
+    "downwash_dz_sign": ("double dz = xi[2] - xj[2];", "double dz = xj[2] - xi[2];"),
+    "downwash_gaussian_half": ("fw[2] -= alpha * exp(-0.5 * dxy * dxy / b2);",
+                               "fw[2] -= alpha * exp(-dxy * dxy / b2);"),
+    "yaw_torque_sign": ("tau[2] = P->km * (-n2[0] + n2[1] - n2[2] + n2[3]);",
+                        "tau[2] = P->km * (n2[0] - n2[1] + n2[2] - n2[3]);"),
+    "roll_torque_pairing": ("tau[0] = l * (F[0] + F[1] - F[2] - F[3]);", "tau[0] = l * (F[0] - F[1] - F[2] + F[3]);"),
+    "inertia_index": ("double Jw[3] = {J[0] * w[0], J[1] * w[1], J[2] * w[2]};",
+                      "double Jw[3] = {J[0] * w[0], J[2] * w[1], J[1] * w[2]};"),
+    "pid_derivative_sign": (
+        "a[r] = P->pos_kp[r] * ep[r] + P->pos_ki[r] * I + P->pos_kd[r] * (0.0 - v[r]);",
+        "a[r] = P->pos_kp[r] * ep[r] + P->pos_ki[r] * I + P->pos_kd[r] * v[r];"),
+    "pid_roll_target_sign": ("double phi_t = (a[0] * sin(psi_t) - a[1] * cos(psi_t)) / P->g;",
+                             "double phi_t = (a[0] * sin(psi_t) + a[1] * cos(psi_t)) / P->g;"),
+    "pitch_extraction": ("double sp = 2.0 * (w * y - z * x);", "double sp = 2.0 * (w * y + z * x);"),
+    "knn_tie_order": ("while (pos > 0 && d2 < bestd[pos - 1]) --pos;", "while (pos > 0 && d2 <= bestd[pos - 1]) --pos;"),
+    "no_renormalisation": ("for (int r = 0; r < 4; ++r) o[3 + r] = qn[r] / qnorm;",
+                           "for (int r = 0; r < 4; ++r) o[3 + r] = qn[r];"),
+}
+
+
+@pytest.fixture(scope="module")
+def oracle_source():
+    with open(os.path.join(ROOT, "oracle", "mdg_oracle.c")) as f:
+        return f.read()
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, oracle_source, tmp_path):
+    before, after = MUTATIONS[name]
+    assert oracle_source.count(before) == 1, f"mutation site of {name} not found exactly once"
+    shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle", ignore=shutil.ignore_patterns("_build"))
+    shutil.copytree(os.path.join(ROOT, "tests"), tmp_path / "tests",
+                    ignore=shutil.ignore_patterns("__pycache__", "test_oracle_mutations.py"))
+    (tmp_path / "oracle" / "mdg_oracle.c").write_text(oracle_source.replace(before, after))
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_dynamics.py", "-q", "-x",
+                        "-p", "no:cacheprovider"], cwd=tmp_path, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 1, f"planted mistake {name} was not caught:\n{r.stdout[-2000:]}"
