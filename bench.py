@@ -1,0 +1,328 @@
+"""Benchmark of the batched multi-drone dynamics step on GB300.
+
+One benchmark step is one control step of the whole hot path over the full-aero swarm
+(16384 environments x 4 Crazyflies = 65536 drones): the PID waypoint controller, 5
+physics substeps at 240 Hz with motor model, ground effect, drag and pairwise downwash,
+and the KIN + 4-neighbour observations -- one launch of the fused step kernel through
+the C ABI (mdg_step_obs). The metric is drone-substeps per second.
+
+Timing: W untimed warm-up steps, then K timed steps, each bracketed by CUDA events on the
+launching stream with the L2 cache flushed (a 512 MiB write) between steps, outside the
+events. Every 1000 control steps (one episode of the workload) the swarm is reset to its
+initial state, outside the timed region. Under torchrun each rank runs its own replica on
+its own GPU (environments are independent: weak scaling, no data-path collective); the
+time is the max over ranks.
+
+Also reported: an end-to-end number through the public API with host buffers (waypoints
+copied in from pinned memory and the observations copied back every step), the roofline
+of the step kernel against the measured HBM bandwidth, SM clocks sampled during the timed
+region, and the FP64 oracle timed on the host cores on a bounded sample.
+
+--impl reference times the oracle alone (the reference arm of this project).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "drone-substeps/s on 1 GB300 (FP32 vs oracle)"
+UNIT = "drone-substeps/s"
+N_SUB = 5
+EPISODE = 1000
+STATE_BYTES_READ = 80    # planes 0-4 (PID integrals included)
+ACTION_BYTES = 16
+STATE_BYTES_WRITE = 96   # planes 0-5
+OBS_BYTES = 80 + 16 + 96  # KIN, neighbour indices, neighbour features
+BYTES_PER_DRONE_STEP = STATE_BYTES_READ + ACTION_BYTES + STATE_BYTES_WRITE + OBS_BYTES  # 384
+
+# DRAM traffic of one step-kernel launch on the full-aero workload, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel source whose
+# sha256 prefix is recorded with it; profiles/ holds the capture's summary.
+NCU_TRAFFIC = {"kernel_sha": None, "bytes": None}
+
+
+def kernel_sha() -> str:
+    with open(os.path.join(ROOT, "paper_2606_08039_gb300", "csrc", "mdg_step.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "src": "measured"}
+    return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(seconds_target: float = 10.0) -> dict:
+    """The FP64 oracle, as it stands, on a bounded sample of the full-aero workload: the
+    full 16384 x 4 swarm for as many control steps (PID + 5 substeps + observations each)
+    as fit in about `seconds_target` seconds, on one host core."""
+    import oracle
+    from paper_2606_08039_gb300 import workloads as wl
+    P = oracle.cf2x()
+    sw = wl.full_aero(1)
+    x, integ, a = sw.x13(), np.zeros((sw.n, 6)), np.zeros((sw.n, 4))
+    wp = wl.waypoints(1, sw.n).astype(np.float64)[None]
+    flags, acts = sw.flags.astype(np.int32), np.full(sw.n_envs, 1, np.int32)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        x, integ, a, *_ = oracle.control_steps(P, sw.env_off, flags, acts, x, integ, a, wp, N_SUB, obs=True)
+        steps += 1
+        dt = time.perf_counter() - t0
+        if dt >= seconds_target or steps >= 200:
+            break
+    return {"value": sw.n * N_SUB * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"full-aero swarm 16384 envs x 4 drones, {steps} control steps x {N_SUB} substeps "
+                      f"with PID and observations, FP64, single thread ({dt:.1f} s)"}
+
+
+def run_reference(args) -> None:
+    """Reference arm: the FP64 oracle timed as it stands on the host cores, on a bounded
+    sample of the same workload per step (2048 envs x 4 drones, one control step)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2606_08039_gb300 import workloads as wl
+    P = oracle.cf2x()
+    sw = wl.full_aero(1, n_envs=2048)
+    x, integ, a = sw.x13(), np.zeros((sw.n, 6)), np.zeros((sw.n, 4))
+    wp = wl.waypoints(1, sw.n).astype(np.float64)[None]
+    flags, acts = sw.flags.astype(np.int32), np.full(sw.n_envs, 1, np.int32)
+
+    def one():
+        nonlocal x, integ, a
+        x, integ, a, *_ = oracle.control_steps(P, sw.env_off, flags, acts, x, integ, a, wp, N_SUB, obs=True)
+
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    dt = time.perf_counter() - t0
+    value = sw.n * N_SUB * args.steps / dt
+    sample = (f"per step: 2048 envs x 4 drones of the full-aero swarm, one control step (PID + {N_SUB} substeps "
+              f"+ observations), FP64 oracle, single thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "full_aero 16384 envs x 4 drones (sampled 2048 envs per step)", "n_substeps": N_SUB,
+                   "l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="mdg", choices=["mdg", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import paper_2606_08039_gb300 as mdg
+    from paper_2606_08039_gb300 import workloads as wl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    # workload: the full-aero swarm, one independent replica per rank
+    sw = wl.full_aero(1 + rank)
+    h = mdg.Handle(sw.drones_per_env, sw.flags)
+    init_state = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=dev)
+    state = init_state.clone()
+    wp_host = torch.from_numpy(wl.waypoints(1 + rank, sw.n)).pin_memory()
+    wp = wp_host.to(dev)
+    kin, idx, rel = h.new_obs(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    steps_done = 0
+
+    def step():
+        nonlocal steps_done
+        if steps_done and steps_done % EPISODE == 0:
+            state.copy_(init_state)
+        h.step_obs(state, wp, mdg.ACT_PID, N_SUB, kin, idx, rel, stream=stream)
+        steps_done += 1
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    rc, _, _ = h.status()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)  # let the sampler start before the timed region
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        if steps_done % EPISODE == 0 and steps_done:
+            state.copy_(init_state)
+        starts[i].record(stream)
+        h.step_obs(state, wp, mdg.ACT_PID, N_SUB, kin, idx, rel, stream=stream)
+        ends[i].record(stream)
+        steps_done += 1
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = float(sum(ms))
+    rc, bits, first = h.status()
+    nonfinite = bool(bits & mdg.STATUS_NONFINITE)
+
+    # end to end through the public API with host buffers
+    kin_h = torch.empty(kin.shape, dtype=kin.dtype).pin_memory()
+    idx_h = torch.empty(idx.shape, dtype=idx.dtype).pin_memory()
+    rel_h = torch.empty(rel.shape, dtype=rel.dtype).pin_memory()
+    e_starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.e2e_steps)]
+    e_ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.e2e_steps)]
+    state.copy_(init_state)
+    for i in range(args.e2e_steps):
+        flush.zero_()
+        e_starts[i].record(stream)
+        wp.copy_(wp_host, non_blocking=True)
+        h.step_obs(state, wp, mdg.ACT_PID, N_SUB, kin, idx, rel, stream=stream)
+        kin_h.copy_(kin, non_blocking=True)
+        idx_h.copy_(idx, non_blocking=True)
+        rel_h.copy_(rel, non_blocking=True)
+        e_ends[i].record(stream)
+        e_ends[i].synchronize()
+    e2e_ms = float(sum(s.elapsed_time(e) for s, e in zip(e_starts, e_ends)))
+    h2d = wp_host.numel() * 4
+    d2h = kin_h.numel() * 4 + idx_h.numel() * 4 + rel_h.numel() * 4
+
+    t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms, e2e_ms = float(t[0]), float(t[1])
+    substeps_per_step = sw.n * N_SUB * world
+    value = substeps_per_step * args.steps / (total_ms * 1e-3)
+    e2e_value = substeps_per_step * args.e2e_steps / (e2e_ms * 1e-3)
+
+    if rank == 0:
+        peaks = measured_peaks()
+        avg_s = total_ms / args.steps * 1e-3
+        bytes_launch = BYTES_PER_DRONE_STEP * sw.n
+        achieved = bytes_launch / avg_s / 1e9
+        traffic = NCU_TRAFFIC["bytes"] if NCU_TRAFFIC["kernel_sha"] == kernel_sha() else None
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "full_aero: 16384 envs x 4 Crazyflie 2.x, ground effect + drag + downwash, "
+                                   "PID waypoints, 240 Hz physics / 48 Hz control (5 substeps), KIN + 4-NN obs; "
+                                   "one step = one control step (one fused kernel launch)",
+                       "n_drones_per_gpu": sw.n, "n_substeps": N_SUB, "block_size": h.block_size,
+                       "l2": "flushed (512 MiB write) between timed steps",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": args.e2e_steps},
+            "gpu_launches": args.steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                         "peak_src": peaks["src"], "algorithmic_bytes_per_launch": bytes_launch,
+                         "kernel": "step_kernel<obs>", "kernel_sha": kernel_sha()},
+            "clocks": clk,
+            "wall_s_timed_region": wall,
+            "nonfinite_during_timing": nonfinite,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

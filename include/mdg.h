@@ -1,0 +1,198 @@
+/*
+ * mdg.h — C ABI of the GB300-native batched multi-drone dynamics library.
+ *
+ * The library advances many independent environments of Crazyflie 2.x quadrotors
+ * with the explicit dynamics of MuJoCo-Drones-Gym (arxiv 2606.08039): the motor
+ * model (Eq. motor), ground effect (Eq. ground), blade drag (Eq. drag) and
+ * inter-drone downwash (Eq. downwash) of Section 3.1, explicit Euler integration
+ * with the closed-form quaternion exponential map (Section 3.2, DYN mode), the
+ * cascaded PID waypoint controller (Section 4.2.1, Table "Default PIDControl
+ * gains") and the KIN / neighbour observations (Section 3.4.4 and the abstract).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Return value: MDG_OK (0) or a negative MDG_ERR_* code. Argument errors are
+ *    found on the host before anything is launched; mdg_last_error() then holds a
+ *    message (thread-local, valid until the next call on that thread).
+ *  - Device pointers are plain CUDA device addresses owned by the caller (for
+ *    instance torch tensors); the library never frees them. Each must be 16-byte
+ *    aligned and hold the documented number of elements.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *    Every compute call is asynchronous on that stream.
+ *  - Drones are numbered in CSR order: the drones of environment e are
+ *    env_off[e] .. env_off[e+1]-1, env_off being the prefix sum of drones_per_env.
+ *  - A handle is bound to the CUDA device current when it was created; it is not
+ *    thread-safe (one host thread at a time).
+ *
+ * State layout (device, float32, caller-owned): MDG_STATE_PLANES planes of
+ * n_drones float4 each, plane k of drone i at float offset 4*(k*n_drones + i):
+ *   plane 0: p.x  p.y  p.z  q.w        (world position [m]; body-to-world quaternion)
+ *   plane 1: q.x  q.y  q.z  v.x        (world velocity [m/s])
+ *   plane 2: v.y  v.z  w.x  w.y        (body-frame angular velocity [rad/s])
+ *   plane 3: w.z  Ip.x Ip.y Ip.z       (PID position-error integral [m s])
+ *   plane 4: Ia.r Ia.p Ia.y  -         (PID attitude-error integral [rad s])
+ *   plane 5: a0   a1   a2   a3         (RPMs applied during the last control step)
+ * The quaternion is [w, x, y, z] (MuJoCo's order, Section 3.1.1); callers keep it
+ * unit-norm and the library renormalises it after every substep.
+ */
+#ifndef MDG_H
+#define MDG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MDG_OK 0
+#define MDG_ERR_ARG (-1)         /* invalid argument (message in mdg_last_error) */
+#define MDG_ERR_CUDA (-2)        /* a CUDA runtime call failed */
+#define MDG_ERR_NONFINITE (-3)   /* reported through mdg_status: a state became non-finite */
+#define MDG_ERR_UNSUPPORTED (-4) /* a valid request this build does not implement */
+
+/* Physics-mode bits per environment (Table "Physics modes"): any subset of the
+ * three aerodynamic effects on top of the explicit integrator. */
+#define MDG_GND 1u  /* ground effect, Eq. ground */
+#define MDG_DRAG 2u /* blade drag, Eq. drag */
+#define MDG_DW 4u   /* inter-drone downwash, Eq. downwash */
+
+/* Action types (Table "Action types"). */
+#define MDG_ACT_RPM 0   /* action = four motor speeds [RPM], clipped to [0, MAX_RPM] */
+#define MDG_ACT_PID 1   /* action = waypoint [x, y, z, yaw] for the PID controller */
+#define MDG_ACT_MIXED 2 /* per-environment type, set by mdg_set_action_types */
+
+/* Status bits written by the kernels (read with mdg_status). */
+#define MDG_STATUS_NONFINITE 1u /* a drone's state became NaN or infinite */
+
+#define MDG_STATE_PLANES 6
+#define MDG_KIN_DIM 20     /* [p(3), q(4), roll/pitch/yaw(3), v(3), w(3), a_prev(4)] */
+#define MDG_NBR_K 4        /* neighbours per drone */
+#define MDG_NBR_FEAT 6     /* [p_i - p_j (3), v_i - v_j (3)] per neighbour */
+#define MDG_MAX_ENV_DRONES 1024
+
+typedef struct mdg_ctx* mdg_handle;
+
+/* Model constants, SI units, double precision on the host (the kernels use float32
+ * copies). Table "Drone model parameters" gives mass..prop_radius for CF2X; n is in
+ * RPM, so kf [N/RPM^2] and km [N m/RPM^2] are per RPM squared. g, c_gnd, h_clip,
+ * c_xy and c_z are not printed in the paper (mdg_constants_cf2x documents the
+ * defaults). dw_c1..dw_c3 are Eq. downwash's (C1, C2, C3); dw_max_xy its 10 m lateral
+ * cut-off; dw_dz_min an optional minimum height difference (0 = as printed). The PID
+ * gains follow Table "Default PIDControl gains". dt_sim = 1/f_sim is the substep,
+ * dt_ctrl = 1/f_ctrl the control period (the PID's integration step). frame must be
+ * MDG_FRAME_X (X-configuration mixing of Eq. motor). */
+#define MDG_FRAME_X 0
+typedef struct mdg_constants {
+    double mass, arm, thrust2weight, Jxx, Jyy, Jzz, kf, km, prop_radius;
+    double g;
+    double c_gnd, h_clip, c_xy, c_z;
+    double dw_c1, dw_c2, dw_c3, dw_max_xy, dw_dz_min;
+    double pos_kp[3], pos_ki[3], pos_kd[3], pos_iclamp;
+    double att_kp[3], att_ki[3], att_kd[3], att_iclamp;
+    double dt_sim, dt_ctrl;
+    int32_t frame;
+    int32_t reserved;
+} mdg_constants;
+
+/* Fill *out with the CF2X constants (Table "Drone model parameters", Eq. downwash
+ * coefficients, Table "Default PIDControl gains", f_sim = 240 Hz, f_ctrl = 48 Hz) and
+ * the project defaults for what the paper does not print: g = 9.81 m/s^2 (MuJoCo's
+ * default gravity), c_gnd = 11.36859, c_xy = 9.1785e-7, c_z = 10.311e-7 and
+ * h_clip = (r_p/4) sqrt(c_gnd / (T/W - 1)) — the height at which the ground-effect
+ * increment at hover thrust equals the spare thrust (T/W - 1) m g, a clip "derived
+ * from the propeller radius and the model's maximum thrust" (Section 3.1.3).
+ * Host only. Returns MDG_ERR_ARG if out is NULL. */
+int mdg_constants_cf2x(mdg_constants* out);
+
+/* sizeof(mdg_constants), for bindings that mirror the struct. */
+int mdg_constants_size(void);
+
+/* HOVER_RPM = sqrt(m g / (4 kf)) and MAX_RPM = sqrt((T/W) m g / (4 kf)) (Section 3.3).
+ * Host only; return a negative value for a NULL or non-physical argument. */
+double mdg_hover_rpm(const mdg_constants* c);
+double mdg_max_rpm(const mdg_constants* c);
+
+/* Create a batch of n_envs environments on the current CUDA device.
+ *   drones_per_env  host [n_envs], each in [0, MDG_MAX_ENV_DRONES] (the
+ *                   constructor's num_drones per environment, Section 3.4.2)
+ *   model_flags     host [n_envs], each a subset of MDG_GND|MDG_DRAG|MDG_DW
+ *   c               constants (copied; NULL = mdg_constants_cf2x)
+ *   out             receives the handle
+ * n_envs = 0 is allowed (every compute call is then a no-op). The handle owns its
+ * device tables (CSR offsets, flags, launch tiles, status word); the caller owns
+ * every state, action and observation buffer. Errors: MDG_ERR_ARG, MDG_ERR_CUDA. */
+int mdg_create(int32_t n_envs, const int32_t* drones_per_env, const uint32_t* model_flags,
+               const mdg_constants* c, mdg_handle* out);
+
+/* Release the handle and its device tables (synchronises the device). NULL is allowed. */
+int mdg_destroy(mdg_handle h);
+
+/* Number of drones (sum of drones_per_env), or a negative code for a NULL handle. */
+int64_t mdg_num_drones(mdg_handle h);
+
+/* Per-environment action types for MDG_ACT_MIXED: host [n_envs] of MDG_ACT_RPM or
+ * MDG_ACT_PID (copied to the device on the default stream, synchronously). */
+int mdg_set_action_types(mdg_handle h, const uint8_t* per_env);
+
+/* Threads per block of the step kernels (a multiple of 32 in [32, 1024] and at least
+ * the largest environment, rounded up to 32). Environments are packed whole into
+ * blocks of at most this many drones. The default is chosen at creation;
+ * mdg_autotune overwrites it. */
+int mdg_set_block_size(mdg_handle h, int32_t threads_per_block);
+int32_t mdg_get_block_size(mdg_handle h);
+
+/* One control step (Section 3.4.2: sim_freq/ctrl_freq physics substeps per env.step).
+ *   state       device float32 [MDG_STATE_PLANES][n_drones][4], updated in place
+ *   action      device float32 [n_drones][4]: RPMs (MDG_ACT_RPM) or waypoints
+ *               [x, y, z, yaw] (MDG_ACT_PID); for MDG_ACT_MIXED each env reads it
+ *               according to its type. May be NULL only when n_drones is 0.
+ *   action_type MDG_ACT_RPM | MDG_ACT_PID | MDG_ACT_MIXED
+ *   n_substeps  >= 1 (5 for 240 Hz physics at 48 Hz control)
+ * The action is turned into four RPMs once (PID: Section 4.2.1, updating the
+ * integrals in planes 3-4), held for n_substeps substeps of dt_sim, and recorded in
+ * plane 5. Within a substep every drone of an environment sees the positions of the
+ * others at the start of that substep. A non-finite result sets MDG_STATUS_NONFINITE.
+ * Errors: MDG_ERR_ARG (bad pointer/alignment/type/count, MIXED without types),
+ * MDG_ERR_CUDA (launch failure). */
+int mdg_step(mdg_handle h, float* state, const float* action, int32_t action_type, int32_t n_substeps,
+             void* stream);
+
+/* mdg_step followed, in the same kernel, by the observations of the new state
+ * (the outputs of mdg_obs). kin and nbr_idx are required; nbr_rel may be NULL. */
+int mdg_step_obs(mdg_handle h, float* state, const float* action, int32_t action_type, int32_t n_substeps,
+                 float* kin, int32_t* nbr_idx, float* nbr_rel, void* stream);
+
+/* The PID controller alone (PIDControl.computeControl, Section 4.2.1): for every
+ * drone, from its state and waypoint [x, y, z, yaw], the four RPMs, the position
+ * error and the yaw error; the integrals in state planes 3-4 are updated in place.
+ *   state      device float32 [MDG_STATE_PLANES][n_drones][4] (planes 3-4 written)
+ *   waypoints  device float32 [n_drones][4]
+ *   rpm_out    device float32 [n_drones][4]
+ *   pos_err    device float32 [n_drones][3] or NULL
+ *   yaw_err    device float32 [n_drones] or NULL */
+int mdg_pid(mdg_handle h, float* state, const float* waypoints, float* rpm_out, float* pos_err, float* yaw_err,
+            void* stream);
+
+/* Observations of the current state (Section 3.4.4 KIN, and the neighbourhood
+ * adjacency of the abstract):
+ *   kin      device float32 [n_drones][20]: p, q, roll/pitch/yaw (ZYX), v, w, a_prev
+ *   nbr_idx  device int32 [n_drones][4]: global indices of the 4 nearest other drones
+ *            of the same environment (Euclidean distance, ties to the lower index),
+ *            -1 where the environment has fewer than 5 drones
+ *   nbr_rel  device float32 [n_drones][24] or NULL: per neighbour [p_i - p_j, v_i - v_j],
+ *            zeros for padded slots */
+int mdg_obs(mdg_handle h, const float* state, float* kin, int32_t* nbr_idx, float* nbr_rel, void* stream);
+
+/* Read and clear the status word: synchronises `stream`, writes the MDG_STATUS_* bits
+ * raised since the last call to *bits and the smallest offending drone index (or -1)
+ * to *first_drone (either may be NULL). Returns MDG_ERR_NONFINITE if the non-finite
+ * bit was set, else MDG_OK (or MDG_ERR_CUDA). */
+int mdg_status(mdg_handle h, void* stream, uint32_t* bits, int64_t* first_drone);
+
+/* Message of the last error on this host thread ("" if none). */
+const char* mdg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MDG_H */

@@ -1,0 +1,279 @@
+"""GB300-native batched multi-drone dynamics (MuJoCo-Drones-Gym hot path, arxiv 2606.08039).
+
+Thin Python binding of the C ABI in include/mdg.h. It only marshals arguments: torch
+tensors provide device memory and streams, every computation runs in the CUDA kernels
+of libmdg.so. There is no CPU fallback: if the library is not built the first call
+raises.
+
+    import paper_2606_08039_gb300 as mdg
+    h = mdg.Handle(drones_per_env, model_flags)          # one handle per batch layout
+    state = mdg.pack_state(p, q, v, w, device="cuda")    # [6, n, 4] float32 planes
+    h.step(state, action, mdg.ACT_PID, n_substeps=5)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import workloads  # noqa: F401  (seeded synthetic inputs)
+
+GND, DRAG, DW = 1, 2, 4
+ACT_RPM, ACT_PID, ACT_MIXED = 0, 1, 2
+STATUS_NONFINITE = 1
+STATE_PLANES = 6
+KIN_DIM = 20
+NBR_K = 4
+NBR_FEAT = 6
+MAX_ENV_DRONES = 1024
+
+OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_UNSUPPORTED = 0, -1, -2, -3, -4
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmdg.so")
+
+# Every symbol include/mdg.h declares, with its ctypes signature.
+_VP = ctypes.c_void_p
+_SIGNATURES = {
+    "mdg_constants_cf2x": ([_VP], ctypes.c_int),
+    "mdg_constants_size": ([], ctypes.c_int),
+    "mdg_hover_rpm": ([_VP], ctypes.c_double),
+    "mdg_max_rpm": ([_VP], ctypes.c_double),
+    "mdg_create": ([ctypes.c_int32, _VP, _VP, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
+    "mdg_destroy": ([_VP], ctypes.c_int),
+    "mdg_num_drones": ([_VP], ctypes.c_int64),
+    "mdg_set_action_types": ([_VP, _VP], ctypes.c_int),
+    "mdg_set_block_size": ([_VP, ctypes.c_int32], ctypes.c_int),
+    "mdg_get_block_size": ([_VP], ctypes.c_int32),
+    "mdg_step": ([_VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, _VP], ctypes.c_int),
+    "mdg_step_obs": ([_VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "mdg_pid": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "mdg_obs": ([_VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "mdg_status": ([_VP, _VP, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "mdg_last_error": ([], ctypes.c_char_p),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class MdgError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"mdg error {code}: {msg}")
+        self.code = code
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libmdg.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is not built; run paper_2606_08039_gb300.build.build_library() "
+                                   "(needs nvcc). There is no CPU fallback.")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in _SIGNATURES.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            if L.mdg_constants_size() != ctypes.sizeof(Constants):
+                raise RuntimeError("Constants mirror does not match mdg_constants")
+            _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise MdgError(rc, lib().mdg_last_error().decode())
+
+
+class Constants(ctypes.Structure):
+    """Mirror of mdg_constants (include/mdg.h)."""
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "mass", "arm", "thrust2weight", "Jxx", "Jyy", "Jzz", "kf", "km", "prop_radius", "g",
+        "c_gnd", "h_clip", "c_xy", "c_z", "dw_c1", "dw_c2", "dw_c3", "dw_max_xy", "dw_dz_min")] + [
+        ("pos_kp", ctypes.c_double * 3), ("pos_ki", ctypes.c_double * 3), ("pos_kd", ctypes.c_double * 3),
+        ("pos_iclamp", ctypes.c_double),
+        ("att_kp", ctypes.c_double * 3), ("att_ki", ctypes.c_double * 3), ("att_kd", ctypes.c_double * 3),
+        ("att_iclamp", ctypes.c_double),
+        ("dt_sim", ctypes.c_double), ("dt_ctrl", ctypes.c_double),
+        ("frame", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    @classmethod
+    def cf2x(cls) -> "Constants":
+        c = cls()
+        _check(lib().mdg_constants_cf2x(ctypes.byref(c)))
+        return c
+
+    def hover_rpm(self) -> float:
+        return lib().mdg_hover_rpm(ctypes.byref(self))
+
+    def max_rpm(self) -> float:
+        return lib().mdg_max_rpm(ctypes.byref(self))
+
+    def to_dict(self) -> dict:
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if isinstance(v, ctypes.Array) else v
+        return out
+
+
+# ---------------------------------------------------------------- tensor marshalling
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t, name, dtype, shape=None):
+    torch = _torch()
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.device.type != "cuda":
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def pack_state(p, q, v, w, ip=None, ia=None, a_prev=None, device="cuda"):
+    """Lay (p[n,3], q[n,4] (w,x,y,z), v[n,3], w[n,3], PID integrals ip[n,3], ia[n,3],
+    last RPMs a_prev[n,4]) out as the library's [6, n, 4] float32 state planes."""
+    torch = _torch()
+
+    def T(a, cols):
+        if a is None:
+            return torch.zeros((n, cols), dtype=torch.float32)
+        return torch.as_tensor(np.asarray(a, dtype=np.float32)).reshape(n, cols)
+
+    n = int(np.asarray(p).shape[0])
+    p, q, v, w = T(p, 3), T(q, 4), T(v, 3), T(w, 3)
+    ip, ia, a_prev = T(ip, 3), T(ia, 3), T(a_prev, 4)
+    z = torch.zeros((n, 1), dtype=torch.float32)
+    planes = torch.stack([
+        torch.cat([p, q[:, :1]], 1),
+        torch.cat([q[:, 1:], v[:, :1]], 1),
+        torch.cat([v[:, 1:], w[:, :2]], 1),
+        torch.cat([w[:, 2:], ip], 1),
+        torch.cat([ia, z], 1),
+        a_prev,
+    ])
+    return planes.contiguous().to(device)
+
+
+def unpack_state(state) -> dict:
+    """Inverse of pack_state: a dict of numpy float32 arrays p, q, v, w, ip, ia, a_prev."""
+    s = state.detach().cpu().numpy()
+    return {"p": s[0, :, 0:3].copy(), "q": np.concatenate([s[0, :, 3:4], s[1, :, 0:3]], 1),
+            "v": np.concatenate([s[1, :, 3:4], s[2, :, 0:2]], 1),
+            "w": np.concatenate([s[2, :, 2:4], s[3, :, 0:1]], 1),
+            "ip": s[3, :, 1:4].copy(), "ia": s[4, :, 0:3].copy(), "a_prev": s[5].copy()}
+
+
+class Handle:
+    """A batch of environments (mdg_create). Owns the device tables; all state, action and
+    observation tensors belong to the caller."""
+
+    def __init__(self, drones_per_env, model_flags, constants: Constants | None = None):
+        dpe = np.ascontiguousarray(drones_per_env, dtype=np.int32)
+        flg = np.ascontiguousarray(model_flags, dtype=np.uint32)
+        if dpe.shape != flg.shape or dpe.ndim != 1:
+            raise ValueError("drones_per_env and model_flags must be 1-d arrays of equal length")
+        self._h = ctypes.c_void_p()
+        self.constants = constants if constants is not None else Constants.cf2x()
+        _check(lib().mdg_create(int(dpe.shape[0]), dpe.ctypes.data_as(_VP), flg.ctypes.data_as(_VP),
+                                ctypes.byref(self.constants), ctypes.byref(self._h)))
+        self.n_envs = int(dpe.shape[0])
+        self.n = int(lib().mdg_num_drones(self._h))
+        self.drones_per_env = dpe
+
+    # -- lifetime
+    def close(self):
+        if self._h:
+            lib().mdg_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- configuration
+    def set_action_types(self, per_env):
+        a = np.ascontiguousarray(per_env, dtype=np.uint8)
+        if a.shape != (self.n_envs,):
+            raise ValueError("per_env must have one entry per environment")
+        _check(lib().mdg_set_action_types(self._h, a.ctypes.data_as(_VP)))
+
+    def set_block_size(self, threads_per_block: int):
+        _check(lib().mdg_set_block_size(self._h, int(threads_per_block)))
+
+    @property
+    def block_size(self) -> int:
+        return int(lib().mdg_get_block_size(self._h))
+
+    # -- compute
+    def step(self, state, action, action_type: int, n_substeps: int = 5, stream=None):
+        torch = _torch()
+        _check(lib().mdg_step(self._h, _ptr(state, "state", torch.float32, (STATE_PLANES, self.n, 4)),
+                              _ptr(action, "action", torch.float32, (self.n, 4)), int(action_type),
+                              int(n_substeps), _stream(stream)))
+
+    def step_obs(self, state, action, action_type: int, n_substeps, kin, nbr_idx, nbr_rel=None, stream=None):
+        torch = _torch()
+        _check(lib().mdg_step_obs(self._h, _ptr(state, "state", torch.float32, (STATE_PLANES, self.n, 4)),
+                                  _ptr(action, "action", torch.float32, (self.n, 4)), int(action_type),
+                                  int(n_substeps), _ptr(kin, "kin", torch.float32, (self.n, KIN_DIM)),
+                                  _ptr(nbr_idx, "nbr_idx", torch.int32, (self.n, NBR_K)),
+                                  _ptr(nbr_rel, "nbr_rel", torch.float32, (self.n, NBR_K * NBR_FEAT)),
+                                  _stream(stream)))
+
+    def pid(self, state, waypoints, rpm_out, pos_err=None, yaw_err=None, stream=None):
+        torch = _torch()
+        _check(lib().mdg_pid(self._h, _ptr(state, "state", torch.float32, (STATE_PLANES, self.n, 4)),
+                             _ptr(waypoints, "waypoints", torch.float32, (self.n, 4)),
+                             _ptr(rpm_out, "rpm_out", torch.float32, (self.n, 4)),
+                             _ptr(pos_err, "pos_err", torch.float32, (self.n, 3)),
+                             _ptr(yaw_err, "yaw_err", torch.float32, (self.n,)), _stream(stream)))
+
+    def obs(self, state, kin, nbr_idx, nbr_rel=None, stream=None):
+        torch = _torch()
+        _check(lib().mdg_obs(self._h, _ptr(state, "state", torch.float32, (STATE_PLANES, self.n, 4)),
+                             _ptr(kin, "kin", torch.float32, (self.n, KIN_DIM)),
+                             _ptr(nbr_idx, "nbr_idx", torch.int32, (self.n, NBR_K)),
+                             _ptr(nbr_rel, "nbr_rel", torch.float32, (self.n, NBR_K * NBR_FEAT)),
+                             _stream(stream)))
+
+    def status(self, stream=None):
+        """(return code, status bits, first non-finite drone or -1); clears the word."""
+        bits = ctypes.c_uint32()
+        first = ctypes.c_int64()
+        rc = lib().mdg_status(self._h, _stream(stream), ctypes.byref(bits), ctypes.byref(first))
+        if rc not in (OK, ERR_NONFINITE):
+            _check(rc)
+        return rc, bits.value, first.value
+
+    # -- output buffers
+    def new_obs(self, device="cuda"):
+        torch = _torch()
+        return (torch.empty((self.n, KIN_DIM), dtype=torch.float32, device=device),
+                torch.empty((self.n, NBR_K), dtype=torch.int32, device=device),
+                torch.empty((self.n, NBR_K * NBR_FEAT), dtype=torch.float32, device=device))

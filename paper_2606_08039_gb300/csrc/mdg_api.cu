@@ -1,0 +1,510 @@
+// Host side of the C ABI declared in include/mdg.h: constants, handle lifetime,
+// argument validation, launch tiles and the status word.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "mdg.h"
+#include "mdg_internal.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(MDG_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Makes the handle's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            ok = false;
+            return;
+        }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+struct mdg_ctx {
+    int device = 0;
+    int32_t n_envs = 0;
+    int64_t n_drones = 0;
+    int32_t max_env = 0;
+    mdg_constants c{};
+    mdg::DevConsts dc{};
+    std::vector<int32_t> h_off;
+    int32_t* d_off = nullptr;
+    uint8_t* d_flags = nullptr;
+    uint8_t* d_act = nullptr;
+    bool act_set = false;
+    mdg::Tile* d_tiles = nullptr;
+    int n_tiles = 0;
+    int block = 0;
+    uint32_t* d_status = nullptr;
+};
+
+namespace {
+
+bool constants_valid(const mdg_constants& c, std::string& why)
+{
+    const double pos[] = {c.mass, c.arm, c.thrust2weight, c.Jxx, c.Jyy, c.Jzz, c.kf, c.km, c.prop_radius,
+                          c.g, c.h_clip, c.dt_sim, c.dt_ctrl, c.dw_max_xy};
+    for (double v : pos)
+        if (!(v > 0.0) || !isfinite(v)) {
+            why = "model constants must be positive and finite";
+            return false;
+        }
+    if (c.thrust2weight <= 1.0) {
+        why = "thrust2weight must exceed 1";
+        return false;
+    }
+    if (c.frame != MDG_FRAME_X) {
+        why = "only the X-configuration frame (MDG_FRAME_X) is supported";
+        return false;
+    }
+    return true;
+}
+
+mdg::DevConsts make_dev_consts(const mdg_constants& c)
+{
+    mdg::DevConsts d{};
+    const double pi = 3.14159265358979323846;
+    d.mass = (float)c.mass;
+    d.inv_mass = (float)(1.0 / c.mass);
+    d.g = (float)c.g;
+    d.kf = (float)c.kf;
+    d.km = (float)c.km;
+    d.l_sqrt2 = (float)(c.arm / sqrt(2.0));
+    const double J[3] = {c.Jxx, c.Jyy, c.Jzz};
+    for (int i = 0; i < 3; ++i) {
+        d.J[i] = (float)J[i];
+        d.inv_J[i] = (float)(1.0 / J[i]);
+    }
+    d.gnd_k = (float)(c.c_gnd * (c.prop_radius / 4.0) * (c.prop_radius / 4.0));
+    d.h_clip = (float)c.h_clip;
+    d.drag_k = (float)(2.0 * pi / 60.0);
+    d.c_xy = (float)c.c_xy;
+    d.c_z = (float)c.c_z;
+    d.dw_k = (float)(c.dw_c1 * (c.prop_radius / 4.0) * (c.prop_radius / 4.0));
+    d.dw_c2 = (float)c.dw_c2;
+    d.dw_c3 = (float)c.dw_c3;
+    d.dw_max_xy2 = (float)(c.dw_max_xy * c.dw_max_xy);
+    d.dw_dz_min = (float)std::max(0.0, c.dw_dz_min);
+    for (int i = 0; i < 3; ++i) {
+        d.pos_kp[i] = (float)c.pos_kp[i];
+        d.pos_ki[i] = (float)c.pos_ki[i];
+        d.pos_kd[i] = (float)c.pos_kd[i];
+        d.att_kp[i] = (float)c.att_kp[i];
+        d.att_ki[i] = (float)c.att_ki[i];
+        d.att_kd[i] = (float)c.att_kd[i];
+    }
+    d.pos_iclamp = (float)c.pos_iclamp;
+    d.att_iclamp = (float)c.att_iclamp;
+    d.dt_sim = (float)c.dt_sim;
+    d.dt_ctrl = (float)c.dt_ctrl;
+    const double maxrpm = sqrt(c.thrust2weight * c.mass * c.g / (4.0 * c.kf));
+    d.max_rpm = (float)maxrpm;
+    d.f_max = (float)(c.kf * maxrpm * maxrpm);
+    d.inv_kf = (float)(1.0 / c.kf);
+    d.alloc_xy = (float)(sqrt(2.0) / c.arm);
+    d.alloc_z = (float)(c.kf / c.km);
+    return d;
+}
+
+// Greedy packing of whole environments, in CSR order, into tiles of at most `block`
+// drones and `block` environments.
+std::vector<mdg::Tile> build_tiles(const std::vector<int32_t>& off, int block)
+{
+    std::vector<mdg::Tile> tiles;
+    const int n_envs = (int)off.size() - 1;
+    int e = 0;
+    while (e < n_envs) {
+        const int e0 = e;
+        while (e < n_envs && (off[e + 1] - off[e0]) <= block && (e + 1 - e0) <= block) ++e;
+        if (e == e0) break;  // an environment larger than the block: rejected before this point
+        mdg::Tile t;
+        t.x = off[e0];
+        t.y = off[e] - off[e0];
+        t.z = e0;
+        t.w = e - e0;
+        if (t.y > 0) tiles.push_back(t);
+    }
+    return tiles;
+}
+
+int default_block(int32_t max_env)
+{
+    int b = 128;
+    while (b < max_env) b *= 2;
+    return std::min(b, 1024);
+}
+
+int set_block(mdg_ctx* h, int block)
+{
+    std::vector<mdg::Tile> tiles = build_tiles(h->h_off, block);
+    mdg::Tile* d_tiles = nullptr;
+    if (!tiles.empty()) {
+        cudaError_t e = cudaMalloc(&d_tiles, tiles.size() * sizeof(mdg::Tile));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(tiles)");
+        e = cudaMemcpy(d_tiles, tiles.data(), tiles.size() * sizeof(mdg::Tile), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(d_tiles);
+            return cuda_fail(e, "cudaMemcpy(tiles)");
+        }
+    }
+    if (h->d_tiles) {
+        cudaDeviceSynchronize();
+        cudaFree(h->d_tiles);
+    }
+    h->d_tiles = d_tiles;
+    h->n_tiles = (int)tiles.size();
+    h->block = block;
+    return MDG_OK;
+}
+
+void destroy_ctx(mdg_ctx* h)
+{
+    cudaFree(h->d_off);
+    cudaFree(h->d_flags);
+    cudaFree(h->d_act);
+    cudaFree(h->d_tiles);
+    cudaFree(h->d_status);
+    delete h;
+}
+
+int check_state_ptr(const mdg_ctx* h, const void* p, const char* name)
+{
+    if (h->n_drones == 0) return MDG_OK;
+    if (!p) return fail(MDG_ERR_ARG, "%s is NULL", name);
+    if (!aligned16(p)) return fail(MDG_ERR_ARG, "%s is not 16-byte aligned", name);
+    return MDG_OK;
+}
+
+mdg::StepArgs base_args(mdg_ctx* h, float* state)
+{
+    mdg::StepArgs a{};
+    a.state = reinterpret_cast<float4*>(state);
+    a.tiles = h->d_tiles;
+    a.env_off = h->d_off;
+    a.env_flags = h->d_flags;
+    a.env_act = h->d_act;
+    a.status = h->d_status;
+    a.n = h->n_drones;
+    a.c = h->dc;
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mdg_constants_cf2x(mdg_constants* out)
+{
+    if (!out) return fail(MDG_ERR_ARG, "mdg_constants_cf2x: out is NULL");
+    memset(out, 0, sizeof(*out));
+    out->mass = 0.027;
+    out->arm = 0.0397;
+    out->thrust2weight = 2.25;
+    out->Jxx = 1.4e-5;
+    out->Jyy = 1.4e-5;
+    out->Jzz = 2.17e-5;
+    out->kf = 3.16e-10;
+    out->km = 7.94e-12;
+    out->prop_radius = 0.02325;
+    out->g = 9.81;
+    out->c_gnd = 11.36859;
+    out->h_clip = 0.25 * out->prop_radius * sqrt(out->c_gnd / (out->thrust2weight - 1.0));
+    out->c_xy = 9.1785e-7;
+    out->c_z = 10.311e-7;
+    out->dw_c1 = 2267.18;
+    out->dw_c2 = 0.16;
+    out->dw_c3 = -0.11;
+    out->dw_max_xy = 10.0;
+    out->dw_dz_min = 0.0;
+    const double kp[3] = {0.4, 0.4, 1.0}, ki[3] = {0.01, 0.01, 0.01}, kd[3] = {0.9, 0.9, 2.0};
+    const double akp[3] = {2e-3, 2e-3, 1e-3}, aki[3] = {0.0, 0.0, 1e-4}, akd[3] = {5e-4, 5e-4, 2e-4};
+    for (int i = 0; i < 3; ++i) {
+        out->pos_kp[i] = kp[i];
+        out->pos_ki[i] = ki[i];
+        out->pos_kd[i] = kd[i];
+        out->att_kp[i] = akp[i];
+        out->att_ki[i] = aki[i];
+        out->att_kd[i] = akd[i];
+    }
+    out->pos_iclamp = 2.0;
+    out->att_iclamp = 0.5;
+    out->dt_sim = 1.0 / 240.0;
+    out->dt_ctrl = 1.0 / 48.0;
+    out->frame = MDG_FRAME_X;
+    return MDG_OK;
+}
+
+int mdg_constants_size(void) { return (int)sizeof(mdg_constants); }
+
+double mdg_hover_rpm(const mdg_constants* c)
+{
+    if (!c || !(c->kf > 0.0) || !(c->mass > 0.0) || !(c->g > 0.0)) return -1.0;
+    return sqrt(c->mass * c->g / (4.0 * c->kf));
+}
+
+double mdg_max_rpm(const mdg_constants* c)
+{
+    if (!c || !(c->kf > 0.0) || !(c->mass > 0.0) || !(c->g > 0.0) || !(c->thrust2weight > 0.0)) return -1.0;
+    return sqrt(c->thrust2weight * c->mass * c->g / (4.0 * c->kf));
+}
+
+int mdg_create(int32_t n_envs, const int32_t* drones_per_env, const uint32_t* model_flags, const mdg_constants* c,
+               mdg_handle* out)
+{
+    if (!out) return fail(MDG_ERR_ARG, "mdg_create: out is NULL");
+    *out = nullptr;
+    if (n_envs < 0) return fail(MDG_ERR_ARG, "mdg_create: n_envs < 0");
+    if (n_envs > 0 && (!drones_per_env || !model_flags))
+        return fail(MDG_ERR_ARG, "mdg_create: drones_per_env and model_flags are required");
+    mdg_constants cc;
+    if (c) cc = *c;
+    else mdg_constants_cf2x(&cc);
+    std::string why;
+    if (!constants_valid(cc, why)) return fail(MDG_ERR_ARG, "mdg_create: %s", why.c_str());
+    std::vector<int32_t> off(n_envs + 1, 0);
+    std::vector<uint8_t> flags(n_envs, 0);
+    int32_t max_env = 0;
+    int64_t total = 0;
+    for (int32_t e = 0; e < n_envs; ++e) {
+        const int32_t N = drones_per_env[e];
+        if (N < 0 || N > MDG_MAX_ENV_DRONES)
+            return fail(MDG_ERR_ARG, "mdg_create: drones_per_env[%d] = %d outside [0, %d]", e, N, MDG_MAX_ENV_DRONES);
+        if (model_flags[e] & ~(MDG_GND | MDG_DRAG | MDG_DW))
+            return fail(MDG_ERR_ARG, "mdg_create: model_flags[%d] has unknown bits", e);
+        total += N;
+        if (total > 0x7fffffffLL) return fail(MDG_ERR_ARG, "mdg_create: more than 2^31 - 1 drones");
+        off[e + 1] = (int32_t)total;
+        flags[e] = (uint8_t)model_flags[e];
+        max_env = std::max(max_env, N);
+    }
+    mdg_ctx* h = new mdg_ctx();
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    h->n_envs = n_envs;
+    h->n_drones = total;
+    h->max_env = max_env;
+    h->c = cc;
+    h->dc = make_dev_consts(cc);
+    h->h_off = off;
+    if ((e = cudaMalloc(&h->d_off, off.size() * sizeof(int32_t))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_flags, std::max<size_t>(1, flags.size()))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_act, std::max<size_t>(1, flags.size()))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_status, 2 * sizeof(uint32_t))) != cudaSuccess) {
+        destroy_ctx(h);
+        return cuda_fail(e, "mdg_create: cudaMalloc");
+    }
+    const uint32_t status0[2] = {0u, 0xffffffffu};
+    if ((e = cudaMemcpy(h->d_off, off.data(), off.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (n_envs > 0 && (e = cudaMemcpy(h->d_flags, flags.data(), flags.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (e = cudaMemcpy(h->d_status, status0, sizeof(status0), cudaMemcpyHostToDevice)) != cudaSuccess) {
+        destroy_ctx(h);
+        return cuda_fail(e, "mdg_create: cudaMemcpy");
+    }
+    int rc = set_block(h, default_block(max_env));
+    if (rc != MDG_OK) {
+        destroy_ctx(h);
+        return rc;
+    }
+    *out = h;
+    return MDG_OK;
+}
+
+int mdg_destroy(mdg_handle h)
+{
+    if (!h) return MDG_OK;
+    DeviceGuard dg(h->device);
+    cudaDeviceSynchronize();
+    destroy_ctx(h);
+    return MDG_OK;
+}
+
+int64_t mdg_num_drones(mdg_handle h)
+{
+    if (!h) return fail(MDG_ERR_ARG, "mdg_num_drones: NULL handle");
+    return h->n_drones;
+}
+
+int mdg_set_action_types(mdg_handle h, const uint8_t* per_env)
+{
+    if (!h) return fail(MDG_ERR_ARG, "mdg_set_action_types: NULL handle");
+    if (h->n_envs == 0) {
+        h->act_set = true;
+        return MDG_OK;
+    }
+    if (!per_env) return fail(MDG_ERR_ARG, "mdg_set_action_types: per_env is NULL");
+    for (int32_t e = 0; e < h->n_envs; ++e)
+        if (per_env[e] != MDG_ACT_RPM && per_env[e] != MDG_ACT_PID)
+            return fail(MDG_ERR_ARG, "mdg_set_action_types: per_env[%d] = %d is not RPM or PID", e, per_env[e]);
+    DeviceGuard dg(h->device);
+    cudaError_t e = cudaMemcpy(h->d_act, per_env, (size_t)h->n_envs, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "mdg_set_action_types: cudaMemcpy");
+    h->act_set = true;
+    return MDG_OK;
+}
+
+int mdg_set_block_size(mdg_handle h, int32_t threads_per_block)
+{
+    if (!h) return fail(MDG_ERR_ARG, "mdg_set_block_size: NULL handle");
+    if (threads_per_block < 32 || threads_per_block > 1024 || threads_per_block % 32 != 0)
+        return fail(MDG_ERR_ARG, "mdg_set_block_size: %d is not a multiple of 32 in [32, 1024]", threads_per_block);
+    if (threads_per_block < h->max_env)
+        return fail(MDG_ERR_ARG, "mdg_set_block_size: %d is smaller than the largest environment (%d drones)",
+                    threads_per_block, h->max_env);
+    DeviceGuard dg(h->device);
+    return set_block(h, threads_per_block);
+}
+
+int32_t mdg_get_block_size(mdg_handle h)
+{
+    if (!h) return fail(MDG_ERR_ARG, "mdg_get_block_size: NULL handle");
+    return h->block;
+}
+
+static int step_common(mdg_handle h, float* state, const float* action, int32_t action_type, int32_t n_substeps,
+                       float* kin, int32_t* nbr_idx, float* nbr_rel, bool with_obs, void* stream)
+{
+    if (!h) return fail(MDG_ERR_ARG, "mdg_step: NULL handle");
+    if (action_type != MDG_ACT_RPM && action_type != MDG_ACT_PID && action_type != MDG_ACT_MIXED)
+        return fail(MDG_ERR_ARG, "mdg_step: unknown action_type %d", action_type);
+    if (action_type == MDG_ACT_MIXED && !h->act_set)
+        return fail(MDG_ERR_ARG, "mdg_step: MDG_ACT_MIXED needs mdg_set_action_types first");
+    if (n_substeps < 1) return fail(MDG_ERR_ARG, "mdg_step: n_substeps = %d < 1", n_substeps);
+    int rc;
+    if ((rc = check_state_ptr(h, state, "state")) != MDG_OK) return rc;
+    if ((rc = check_state_ptr(h, action, "action")) != MDG_OK) return rc;
+    if (with_obs) {
+        if ((rc = check_state_ptr(h, kin, "kin")) != MDG_OK) return rc;
+        if ((rc = check_state_ptr(h, nbr_idx, "nbr_idx")) != MDG_OK) return rc;
+        if (nbr_rel && !aligned16(nbr_rel)) return fail(MDG_ERR_ARG, "nbr_rel is not 16-byte aligned");
+    }
+    if (h->n_drones == 0) return MDG_OK;
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(MDG_ERR_CUDA, "mdg_step: cannot select device %d", h->device);
+    mdg::StepArgs a = base_args(h, state);
+    a.action = reinterpret_cast<const float4*>(action);
+    a.kin = kin;
+    a.nbr_idx = reinterpret_cast<int4*>(nbr_idx);
+    a.nbr_rel = nbr_rel;
+    a.n_sub = n_substeps;
+    a.act_type = action_type;
+    cudaError_t e = mdg::launch_step(a, h->n_tiles, h->block, with_obs, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mdg_step: launch");
+    return MDG_OK;
+}
+
+int mdg_step(mdg_handle h, float* state, const float* action, int32_t action_type, int32_t n_substeps, void* stream)
+{
+    return step_common(h, state, action, action_type, n_substeps, nullptr, nullptr, nullptr, false, stream);
+}
+
+int mdg_step_obs(mdg_handle h, float* state, const float* action, int32_t action_type, int32_t n_substeps,
+                 float* kin, int32_t* nbr_idx, float* nbr_rel, void* stream)
+{
+    return step_common(h, state, action, action_type, n_substeps, kin, nbr_idx, nbr_rel, true, stream);
+}
+
+int mdg_pid(mdg_handle h, float* state, const float* waypoints, float* rpm_out, float* pos_err, float* yaw_err,
+            void* stream)
+{
+    if (!h) return fail(MDG_ERR_ARG, "mdg_pid: NULL handle");
+    int rc;
+    if ((rc = check_state_ptr(h, state, "state")) != MDG_OK) return rc;
+    if ((rc = check_state_ptr(h, waypoints, "waypoints")) != MDG_OK) return rc;
+    if ((rc = check_state_ptr(h, rpm_out, "rpm_out")) != MDG_OK) return rc;
+    if (pos_err && (reinterpret_cast<uintptr_t>(pos_err) & 3u)) return fail(MDG_ERR_ARG, "pos_err misaligned");
+    if (yaw_err && (reinterpret_cast<uintptr_t>(yaw_err) & 3u)) return fail(MDG_ERR_ARG, "yaw_err misaligned");
+    if (h->n_drones == 0) return MDG_OK;
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(MDG_ERR_CUDA, "mdg_pid: cannot select device %d", h->device);
+    mdg::PidArgs a{};
+    a.state = reinterpret_cast<float4*>(state);
+    a.waypoints = reinterpret_cast<const float4*>(waypoints);
+    a.rpm_out = reinterpret_cast<float4*>(rpm_out);
+    a.pos_err = pos_err;
+    a.yaw_err = yaw_err;
+    a.n = h->n_drones;
+    a.c = h->dc;
+    cudaError_t e = mdg::launch_pid(a, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mdg_pid: launch");
+    return MDG_OK;
+}
+
+int mdg_obs(mdg_handle h, const float* state, float* kin, int32_t* nbr_idx, float* nbr_rel, void* stream)
+{
+    if (!h) return fail(MDG_ERR_ARG, "mdg_obs: NULL handle");
+    int rc;
+    if ((rc = check_state_ptr(h, state, "state")) != MDG_OK) return rc;
+    if ((rc = check_state_ptr(h, kin, "kin")) != MDG_OK) return rc;
+    if ((rc = check_state_ptr(h, nbr_idx, "nbr_idx")) != MDG_OK) return rc;
+    if (nbr_rel && !aligned16(nbr_rel)) return fail(MDG_ERR_ARG, "nbr_rel is not 16-byte aligned");
+    if (h->n_drones == 0) return MDG_OK;
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(MDG_ERR_CUDA, "mdg_obs: cannot select device %d", h->device);
+    mdg::StepArgs a = base_args(h, const_cast<float*>(state));
+    a.kin = kin;
+    a.nbr_idx = reinterpret_cast<int4*>(nbr_idx);
+    a.nbr_rel = nbr_rel;
+    a.act_type = MDG_ACT_RPM;
+    cudaError_t e = mdg::launch_obs(a, h->n_tiles, h->block, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mdg_obs: launch");
+    return MDG_OK;
+}
+
+int mdg_status(mdg_handle h, void* stream, uint32_t* bits, int64_t* first_drone)
+{
+    if (!h) return fail(MDG_ERR_ARG, "mdg_status: NULL handle");
+    DeviceGuard dg(h->device);
+    uint32_t st[2];
+    cudaError_t e = cudaMemcpyAsync(st, h->d_status, sizeof(st), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mdg_status: read");
+    const uint32_t status0[2] = {0u, 0xffffffffu};
+    e = cudaMemcpyAsync(h->d_status, status0, sizeof(status0), cudaMemcpyHostToDevice, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mdg_status: clear");
+    if (bits) *bits = st[0];
+    if (first_drone) *first_drone = st[1] == 0xffffffffu ? -1 : (int64_t)st[1];
+    return (st[0] & MDG_STATUS_NONFINITE) ? MDG_ERR_NONFINITE : MDG_OK;
+}
+
+const char* mdg_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,63 @@
+// Internal declarations shared by the host API (mdg_api.cu) and the kernels (mdg_step.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mdg {
+
+// Float32 copies of the model constants with the products the kernels need folded in
+// once on the host (in double precision, then rounded).
+struct DevConsts {
+    float mass, inv_mass, g;
+    float kf, km, l_sqrt2;            // Eq. motor: k_f, k_m, L/sqrt(2)
+    float J[3], inv_J[3];
+    float gnd_k;                      // Eq. ground: C_gnd (r_p/4)^2
+    float h_clip;
+    float drag_k;                     // Eq. drag: 2 pi / 60 (RPM -> rad/s)
+    float c_xy, c_z;
+    float dw_k;                       // Eq. downwash: C1 (r_p/4)^2
+    float dw_c2, dw_c3, dw_max_xy2, dw_dz_min;
+    float pos_kp[3], pos_ki[3], pos_kd[3], pos_iclamp;
+    float att_kp[3], att_ki[3], att_kd[3], att_iclamp;
+    float dt_sim, dt_ctrl;
+    float max_rpm, f_max, inv_kf;     // PID output clip: f_i in [0, k_f MAX_RPM^2]
+    float alloc_xy, alloc_z;          // inverse mixing: sqrt(2)/L and k_f/k_m
+};
+
+// A launch tile: whole environments packed into one thread block.
+// x = first drone, y = drones, z = first environment, w = environments.
+typedef int4 Tile;
+
+struct StepArgs {
+    float4* state;            // [6][n] float4 planes
+    const float4* action;     // [n]
+    float* kin;               // [n][20] or null
+    int4* nbr_idx;            // [n] or null
+    float* nbr_rel;           // [n][24] or null
+    const Tile* tiles;
+    const int32_t* env_off;   // [n_envs + 1]
+    const uint8_t* env_flags; // [n_envs]
+    const uint8_t* env_act;   // [n_envs] (MIXED) or null
+    uint32_t* status;         // [2]: bits, first bad drone
+    long long n;
+    int n_sub;
+    int act_type;             // MDG_ACT_RPM / PID / MIXED
+    DevConsts c;
+};
+
+struct PidArgs {
+    float4* state;
+    const float4* waypoints;
+    float4* rpm_out;
+    float* pos_err;           // [n][3] or null
+    float* yaw_err;           // [n] or null
+    long long n;
+    DevConsts c;
+};
+
+cudaError_t launch_step(const StepArgs& a, int n_tiles, int block, bool with_obs, cudaStream_t s);
+cudaError_t launch_obs(const StepArgs& a, int n_tiles, int block, cudaStream_t s);
+cudaError_t launch_pid(const PidArgs& a, cudaStream_t s);
+
+}  // namespace mdg

@@ -1,0 +1,96 @@
+"""Shared helpers of the parity tests: layout conversion between the library's state
+planes and the oracle's [n, 13] arrays, and the tolerance checks.
+
+Tolerances (stated once, used everywhere):
+  per substep, restarted from the GPU's own float32 state:
+      position, velocity  |gpu - ref| <= 1e-5 * max(|ref|, 1)   (m, m/s)
+      body rate           |gpu - ref| <= 1e-4 * max(|ref|, 1)   (rad/s)
+      quaternion          |gpu - ref| <= 2e-6
+  The floor of 1 unit keeps the test relative for large values and absolute near zero,
+  where a sum of terms that cancel has no meaningful relative error.
+"""
+import numpy as np
+
+import oracle
+import paper_2606_08039_gb300 as mdg
+
+RTOL_PV = 1e-5
+RTOL_W = 1e-4
+ATOL_Q = 2e-6
+
+
+def oracle_arrays(state_tensor):
+    """Library state [6, n, 4] -> (x [n,13], integ [n,6], a_prev [n,4]) in float64."""
+    s = mdg.unpack_state(state_tensor)
+    x = np.concatenate([s["p"], s["q"], s["v"], s["w"]], axis=1).astype(np.float64)
+    integ = np.concatenate([s["ip"], s["ia"]], axis=1).astype(np.float64)
+    return x, integ, s["a_prev"].astype(np.float64)
+
+
+def swarm_state(swarm, device):
+    return mdg.pack_state(swarm.p, swarm.q, swarm.v, swarm.w, device=device)
+
+
+def excess(gpu, ref, rtol, floor=1.0):
+    """Largest |gpu - ref| / (rtol * max(|ref|, floor)); <= 1 passes."""
+    gpu = np.asarray(gpu, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return float(np.max(np.abs(gpu - ref) / (rtol * np.maximum(np.abs(ref), floor)), initial=0.0))
+
+
+def assert_state_close(xg, xo, scale=1.0, what=""):
+    """Compare [n,13] states with the per-substep tolerances times `scale`."""
+    e_p = excess(xg[:, 0:3], xo[:, 0:3], RTOL_PV * scale)
+    e_v = excess(xg[:, 7:10], xo[:, 7:10], RTOL_PV * scale)
+    e_w = excess(xg[:, 10:13], xo[:, 10:13], RTOL_W * scale)
+    e_q = float(np.max(np.abs(xg[:, 3:7] - xo[:, 3:7]), initial=0.0)) / (ATOL_Q * scale)
+    worst = max(e_p, e_v, e_w, e_q)
+    assert worst <= 1.0, f"{what}: tolerance exceeded (p {e_p:.3g}, v {e_v:.3g}, w {e_w:.3g}, q {e_q:.3g})"
+    return worst
+
+
+def oracle_step(P, swarm_or_layout, x, integ, a_prev, action, act_types, n_sub, obs=False):
+    """One control step of the oracle on the given batch layout."""
+    dpe, flags = swarm_or_layout
+    env_off = np.concatenate([[0], np.cumsum(dpe)]).astype(np.int32)
+    return oracle.control_steps(P, env_off, np.asarray(flags, np.int32), np.asarray(act_types, np.int32),
+                                x, integ, a_prev, np.asarray(action, np.float64)[None], n_sub, obs=obs)
+
+
+def subset_layout(dpe, envs):
+    """Drone indices and layout of a subset of environments."""
+    env_off = np.concatenate([[0], np.cumsum(dpe)])
+    idx = np.concatenate([np.arange(env_off[e], env_off[e + 1]) for e in envs]) if len(envs) else np.zeros(0, int)
+    return idx, np.asarray(dpe)[envs]
+
+
+def perturbed_spread(P, layout, x, integ, a_prev, action, act_types, n_sub, seed=0, ulps=1):
+    """Intrinsic conditioning of a short horizon: the oracle's change in the result when the
+    float32 input positions move by `ulps` float32 ulps (random signs). Returns |dx| [n,13]."""
+    rng = np.random.default_rng(seed)
+    x2 = x.copy()
+    p32 = x2[:, 0:3].astype(np.float32)
+    step = np.spacing(np.abs(p32)).astype(np.float64) * ulps
+    x2[:, 0:3] = x[:, 0:3] + rng.choice([-1.0, 1.0], size=p32.shape) * step
+    a = oracle_step(P, layout, x, integ, a_prev, action, act_types, n_sub)[0]
+    b = oracle_step(P, layout, x2, integ, a_prev, action, act_types, n_sub)[0]
+    return np.abs(a - b)
+
+
+def assert_horizon_close(xg, xo, spread, what=""):
+    """Short-horizon comparison: per component, |gpu - ref| <= tol * max(|ref|, 1) + 10 * spread,
+    the spread being the oracle's own response to a one-ulp perturbation of the input
+    positions (chaotic downwash amplifies float32 rounding by exactly that factor)."""
+    tol = np.zeros(13)
+    tol[0:3] = tol[7:10] = RTOL_PV
+    tol[10:13] = RTOL_W
+    bound = tol[None, :] * np.maximum(np.abs(xo), 1.0) + 10.0 * spread
+    bound[:, 3:7] = ATOL_Q + 10.0 * spread[:, 3:7]
+    err = np.abs(xg - xo)
+    ratio = err / bound
+    worst = float(np.max(ratio, initial=0.0))
+    if worst > 1.0:
+        i, k = np.unravel_index(np.argmax(ratio), ratio.shape)
+        raise AssertionError(f"{what}: drone {i} component {k}: gpu {xg[i, k]!r} oracle {xo[i, k]!r} "
+                             f"bound {bound[i, k]:.3g} (ratio {worst:.3g})")
+    return worst

@@ -1,0 +1,240 @@
+"""GPU parity: the CUDA kernels against the FP64 oracle on identical seeded inputs,
+through the C ABI (via the thin binding).
+
+Protocol: the oracle restarts from the GPU's own float32 state (exact in float64), so a
+single substep isolates one step's rounding; short horizons add a conditioning term
+measured on the oracle itself (helpers.assert_horizon_close). Sizes span several tiles
+with ragged tails; the full-size cases run the benchmark's launch configuration and
+compare a sample of environments.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2606_08039_gb300 as mdg
+from paper_2606_08039_gb300 import workloads as wl
+from helpers import (assert_horizon_close, assert_state_close, excess, oracle_arrays, oracle_step,
+                     perturbed_spread, subset_layout, swarm_state)
+
+pytestmark = pytest.mark.gpu
+
+P = oracle.cf2x()
+HOVER = oracle.hover_rpm(P)
+MAXRPM = oracle.max_rpm(P)
+F_MAX = P.kf * MAXRPM ** 2
+
+
+def _t(a, dev, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device=dev)
+
+
+def _mixed_layout(n_envs, sizes, seed):
+    e = np.arange(n_envs)
+    dpe = np.asarray(sizes)[e % len(sizes)].astype(np.int32)
+    flags = (e % 8).astype(np.uint32)
+    return dpe, flags
+
+
+def _random_swarm(dpe, seed, box=0.6):
+    n = int(np.sum(dpe))
+    p, q, v, w = wl.random_states(seed, n, pos_scale=box)
+    return p, q, v, w
+
+
+def _gpu_step(h, state, action, act_type, n_sub, obs=False):
+    if obs:
+        kin, idx, rel = h.new_obs(state.device)
+        h.step_obs(state, action, act_type, n_sub, kin, idx, rel)
+        torch.cuda.synchronize()
+        return kin, idx, rel
+    h.step(state, action, act_type, n_sub)
+    torch.cuda.synchronize()
+    return None
+
+
+def _check_obs(xg, ap, dpe, kin, idx, rel):
+    """Observations of the GPU's post-step state against the oracle's, restarted from it."""
+    env_off = np.concatenate([[0], np.cumsum(dpe)])
+    kin, idx, rel = (t.cpu().numpy() if torch.is_tensor(t) else np.asarray(t) for t in (kin, idx, rel))
+    kin, rel = kin.astype(np.float64), rel.astype(np.float64)
+    for e in range(len(dpe)):
+        b, N = int(env_off[e]), int(dpe[e])
+        for j in range(N):
+            k_ref = oracle.kin(xg[b + j], ap[b + j])
+            assert excess(kin[b + j], k_ref, 1e-6) <= 1.0, f"kin of drone {b + j}"
+            i_ref, r_ref = oracle.knn(xg[b:b + N], j, b)
+            np.testing.assert_array_equal(idx[b + j], i_ref, err_msg=f"neighbours of drone {b + j}")
+            assert excess(rel[b + j], r_ref, 1e-6, floor=1e-2) <= 1.0, f"nbr features of drone {b + j}"
+
+
+# ------------------------------------------------------------------ one substep
+@pytest.mark.parametrize("act_type", [mdg.ACT_RPM, mdg.ACT_PID])
+def test_single_substep_all_flag_subsets(cuda, act_type):
+    dpe, flags = _mixed_layout(300, [1, 2, 3, 4, 5, 6, 7], 0)
+    n = int(dpe.sum())
+    p, q, v, w = _random_swarm(dpe, 11)
+    if act_type == mdg.ACT_RPM:
+        action = wl.rpm_actions(12, n, 0, HOVER, lo=-0.2, hi=1.7)  # below 0 and above MAX_RPM too
+    else:
+        action = wl.waypoints(12, n)
+        action[:, 3] = wl.uniform_range(-3, 3, 12, 9, 0, np.arange(n, dtype=np.uint64), 0)
+    h = mdg.Handle(dpe, flags)
+    state = mdg.pack_state(p, q, v, w, device=cuda)
+    x0, i0, a0 = oracle_arrays(state)
+    _gpu_step(h, state, _t(action, cuda), act_type, 1)
+    xg, ig, ag = oracle_arrays(state)
+    xo, io, ao = oracle_step(P, (dpe, flags), x0, i0, a0, action, np.full(len(dpe), act_type), 1)
+    assert_state_close(xg, xo, what="one substep")
+    if act_type == mdg.ACT_RPM:
+        np.testing.assert_array_equal(ag, ao)  # clipping is exact
+    else:
+        assert excess(P.kf * ag ** 2, P.kf * ao ** 2, 1e-5, floor=F_MAX) <= 1.0
+        assert excess(ig, io, 1e-5) <= 1.0
+    assert h.status()[0] == mdg.OK
+
+
+def test_pid_entry_point(cuda):
+    n = 3000
+    p, q, v, w = wl.random_states(21, n)
+    integ = wl.uniform_range(-0.3, 0.3, 21, 10, 0, np.arange(n, dtype=np.uint64)[:, None],
+                             np.arange(6, dtype=np.uint64)[None, :])
+    wp = wl.waypoints(22, n)
+    wp[:, 3] = wl.uniform_range(-3, 3, 22, 9, 0, np.arange(n, dtype=np.uint64), 0)
+    h = mdg.Handle(np.ones(n, np.int32), np.zeros(n, np.uint32))
+    state = mdg.pack_state(p, q, v, w, ip=integ[:, :3], ia=integ[:, 3:], device=cuda)
+    x0, i0, _ = oracle_arrays(state)
+    rpm = torch.empty((n, 4), device=cuda)
+    pe = torch.empty((n, 3), device=cuda)
+    ye = torch.empty((n,), device=cuda)
+    h.pid(state, _t(wp, cuda), rpm, pe, ye)
+    torch.cuda.synchronize()
+    _, ig, _ = oracle_arrays(state)
+    rpm, pe, ye = (t.cpu().numpy().astype(np.float64) for t in (rpm, pe, ye))
+    for i in range(n):
+        r_o, pe_o, ye_o, in_o = oracle.pid(P, x0[i], i0[i], wp[i].astype(np.float64))
+        assert excess(P.kf * rpm[i] ** 2, P.kf * r_o ** 2, 1e-5, floor=F_MAX) <= 1.0, f"rpm {i}"
+        assert excess(pe[i], pe_o, 1e-6) <= 1.0
+        assert abs(ye[i] - ye_o) <= 1e-5
+        assert excess(ig[i], in_o, 1e-5) <= 1.0
+
+
+# ------------------------------------------------------------------ short horizons
+@pytest.mark.parametrize("recipe", ["single", "full_aero", "dense", "uneven"])
+def test_one_control_step_recipes(cuda, recipe):
+    if recipe == "single":
+        sw = wl.single(0)
+    elif recipe == "full_aero":
+        sw = wl.full_aero(1, n_envs=300)
+    elif recipe == "dense":
+        sw = wl.dense(5, n_envs=6)
+    else:
+        sw = wl.uneven(2, n_envs=150)
+    n = sw.n
+    h = mdg.Handle(sw.drones_per_env, sw.flags)
+    if recipe == "uneven":
+        h.set_action_types(sw.act_type)
+        action, act = wl.mixed_actions(sw, 3, 0, HOVER), mdg.ACT_MIXED
+        acts = sw.act_type
+    elif recipe == "full_aero":
+        action, act = wl.waypoints(1, n), mdg.ACT_PID
+        acts = np.full(sw.n_envs, act)
+    else:
+        action, act = wl.rpm_actions(sw.n_envs, n, 0, HOVER), mdg.ACT_RPM
+        acts = np.full(sw.n_envs, act)
+    state = swarm_state(sw, cuda)
+    x0, i0, a0 = oracle_arrays(state)
+    kin, idx, rel = _gpu_step(h, state, _t(action, cuda), act, 5, obs=True)
+    xg, ig, ag = oracle_arrays(state)
+    layout = (sw.drones_per_env, sw.flags)
+    xo, io, ao = oracle_step(P, layout, x0, i0, a0, action, acts, 5)
+    spread = perturbed_spread(P, layout, x0, i0, a0, action, acts, 5)
+    assert_horizon_close(xg, xo, spread, what=recipe)
+    _check_obs(xg, ag, sw.drones_per_env, kin, idx, rel)
+
+
+def test_single_recipe_ten_control_steps(cuda):
+    sw = wl.single(0)
+    h = mdg.Handle(sw.drones_per_env, sw.flags)
+    state = swarm_state(sw, cuda)
+    x0, i0, a0 = oracle_arrays(state)
+    acts = np.full(sw.n_envs, mdg.ACT_RPM)
+    actions = np.stack([wl.rpm_actions(0, sw.n, k, HOVER) for k in range(10)])
+    for k in range(10):
+        h.step(state, _t(actions[k], cuda), mdg.ACT_RPM, 5)
+    torch.cuda.synchronize()
+    xg, _, _ = oracle_arrays(state)
+    env_off = sw.env_off
+    xo = oracle.control_steps(P, env_off, sw.flags.astype(np.int32), acts, x0, i0, a0, actions, 5)[0]
+    # 50 substeps of a non-chaotic system: rounding errors add up at most linearly
+    assert_state_close(xg, xo, scale=50.0, what="10 control steps")
+
+
+# ------------------------------------------------------------------ benchmark launch configuration
+@pytest.mark.parametrize("recipe", ["full_aero", "dense"])
+def test_full_size_sampled(cuda, recipe):
+    sw = wl.full_aero(1) if recipe == "full_aero" else wl.dense(5)
+    n = sw.n
+    h = mdg.Handle(sw.drones_per_env, sw.flags)
+    if recipe == "full_aero":
+        action, act = wl.waypoints(1, n), mdg.ACT_PID
+    else:
+        action, act = wl.rpm_actions(5, n, 0, HOVER), mdg.ACT_RPM
+    state = swarm_state(sw, cuda)
+    x0, i0, a0 = oracle_arrays(state)
+    kin, idx, rel = _gpu_step(h, state, _t(action, cuda), act, 5, obs=True)
+    xg, ig, ag = oracle_arrays(state)
+    envs = np.linspace(0, sw.n_envs - 1, 96 if recipe == "full_aero" else 6).astype(int)
+    sel, dpe = subset_layout(sw.drones_per_env, envs)
+    layout = (dpe, sw.flags[envs])
+    acts = np.full(len(envs), act)
+    xo, _, _ = oracle_step(P, layout, x0[sel], i0[sel], a0[sel], action[sel], acts, 5)
+    spread = perturbed_spread(P, layout, x0[sel], i0[sel], a0[sel], action[sel], acts, 5)
+    assert_horizon_close(xg[sel], xo, spread, what=recipe)
+    # observations of the sampled environments (indices are global)
+    kin_s, idx_s, rel_s = kin.cpu().numpy()[sel], idx.cpu().numpy()[sel], rel.cpu().numpy()[sel]
+    base = np.concatenate([[0], np.cumsum(sw.drones_per_env)])[envs]
+    shift = np.repeat(base - np.concatenate([[0], np.cumsum(dpe)])[:-1], dpe)[:, None]
+    local = np.where(idx_s >= 0, idx_s - shift, -1)
+    _check_obs(xg[sel], ag[sel], dpe, kin_s, local, rel_s)
+    assert h.status()[0] == mdg.OK
+
+
+# ------------------------------------------------------------------ observations alone
+def test_obs_entry_point(cuda):
+    sizes = [1, 2, 3, 4, 5, 8, 31, 33, 64, 100]
+    dpe = np.asarray(sizes * 3, np.int32)
+    n = int(dpe.sum())
+    p, q, v, w = wl.random_states(31, n, pos_scale=0.5)
+    a_prev = wl.rpm_actions(31, n, 0, HOVER)
+    h = mdg.Handle(dpe, np.zeros(len(dpe), np.uint32))
+    state = mdg.pack_state(p, q, v, w, a_prev=a_prev, device=cuda)
+    kin, idx, rel = h.new_obs(cuda)
+    h.obs(state, kin, idx, rel)
+    torch.cuda.synchronize()
+    xg, _, ag = oracle_arrays(state)
+    _check_obs(xg, ag, dpe, kin, idx, rel)
+    # without the relative features
+    kin2, idx2, _ = h.new_obs(cuda)
+    h.obs(state, kin2, idx2, None)
+    torch.cuda.synchronize()
+    assert torch.equal(kin2, kin) and torch.equal(idx2, idx)
+
+
+# ------------------------------------------------------------------ tiling does not change results
+def test_block_size_does_not_change_results(cuda):
+    sw = wl.uneven(7, n_envs=120)
+    n = sw.n
+    action = wl.mixed_actions(sw, 7, 0, HOVER)
+    outs = []
+    for block in (32, 64, 256, 1024):
+        h = mdg.Handle(sw.drones_per_env, sw.flags)
+        h.set_action_types(sw.act_type)
+        h.set_block_size(block)
+        assert h.block_size == block
+        state = swarm_state(sw, cuda)
+        kin, idx, rel = _gpu_step(h, state, _t(action, cuda), mdg.ACT_MIXED, 5, obs=True)
+        outs.append((state.clone(), kin.clone(), idx.clone(), rel.clone()))
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert torch.equal(a, b)
