@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -63,6 +64,7 @@ struct mdg_ctx {
     mdg_constants c{};
     mdg::DevConsts dc{};
     std::vector<int32_t> h_off;
+    std::vector<uint8_t> h_flags;
     int32_t* d_off = nullptr;
     uint8_t* d_flags = nullptr;
     uint8_t* d_act = nullptr;
@@ -70,6 +72,10 @@ struct mdg_ctx {
     mdg::Tile* d_tiles = nullptr;
     int n_tiles = 0;
     int block = 0;
+    int uniform_N = 0;      // every environment has this many drones (0: mixed sizes)
+    int envs_per_tile = 0;
+    int uniform_bits = 0;
+    int uniform_flags = -1;  // physics subset shared by every environment, -1 if they differ
     uint32_t* d_status = nullptr;
 };
 
@@ -102,6 +108,7 @@ mdg::DevConsts make_dev_consts(const mdg_constants& c)
     d.mass = (float)c.mass;
     d.inv_mass = (float)(1.0 / c.mass);
     d.g = (float)c.g;
+    d.inv_g = (float)(1.0 / c.g);
     d.kf = (float)c.kf;
     d.km = (float)c.km;
     d.l_sqrt2 = (float)(c.arm / sqrt(2.0));
@@ -115,6 +122,7 @@ mdg::DevConsts make_dev_consts(const mdg_constants& c)
     d.drag_k = (float)(2.0 * pi / 60.0);
     d.c_xy = (float)c.c_xy;
     d.c_z = (float)c.c_z;
+    d.c_dz = (float)(c.c_z - c.c_xy);
     d.dw_k = (float)(c.dw_c1 * (c.prop_radius / 4.0) * (c.prop_radius / 4.0));
     d.dw_c2 = (float)c.dw_c2;
     d.dw_c3 = (float)c.dw_c3;
@@ -142,8 +150,8 @@ mdg::DevConsts make_dev_consts(const mdg_constants& c)
 }
 
 // Greedy packing of whole environments, in CSR order, into tiles of at most `block`
-// drones and `block` environments.
-std::vector<mdg::Tile> build_tiles(const std::vector<int32_t>& off, int block)
+// drones and `block` environments, with the tile bits the kernels branch on.
+std::vector<mdg::Tile> build_tiles(const std::vector<int32_t>& off, const std::vector<uint8_t>& flags, int block)
 {
     std::vector<mdg::Tile> tiles;
     const int n_envs = (int)off.size() - 1;
@@ -157,21 +165,44 @@ std::vector<mdg::Tile> build_tiles(const std::vector<int32_t>& off, int block)
         t.y = off[e] - off[e0];
         t.z = e0;
         t.w = e - e0;
+        bool any_dw = false, warp_local = true;
+        for (int k = e0; k < e; ++k) {
+            const int ls = off[k] - off[e0], N = off[k + 1] - off[k];
+            if (N > 0 && (flags[k] & MDG_DW)) any_dw = true;
+            if (N > 0 && (ls >> 5) != ((ls + N - 1) >> 5)) warp_local = false;
+        }
+        if (any_dw) t.w |= mdg::kTileAnyDW;
+        if (warp_local) t.w |= mdg::kTileWarpLocal;
         if (t.y > 0) tiles.push_back(t);
     }
     return tiles;
 }
 
-int default_block(int32_t max_env)
+// Default threads per block: enough for the largest environment, and otherwise the size
+// that spreads the tiles most evenly over the SMs (a block count close to a multiple of
+// the SM count), preferring larger blocks on ties.
+int default_block(int32_t max_env, int64_t n_drones, int n_sm)
 {
-    int b = 128;
-    while (b < max_env) b *= 2;
-    return std::min(b, 1024);
+    int lo = 32;
+    while (lo < max_env) lo *= 2;
+    if (lo >= 1024) return 1024;
+    int best = std::max(lo, 128);
+    double best_eff = -1.0;
+    for (int b = lo; b <= 256; b *= 2) {
+        const double blocks = std::ceil((double)n_drones / b);
+        const double waves = std::ceil(blocks / n_sm);
+        const double eff = blocks / (waves * n_sm);
+        if (eff > best_eff - 1e-9) {
+            best_eff = eff;
+            best = b;
+        }
+    }
+    return best;
 }
 
 int set_block(mdg_ctx* h, int block)
 {
-    std::vector<mdg::Tile> tiles = build_tiles(h->h_off, block);
+    std::vector<mdg::Tile> tiles = build_tiles(h->h_off, h->h_flags, block);
     mdg::Tile* d_tiles = nullptr;
     if (!tiles.empty()) {
         cudaError_t e = cudaMalloc(&d_tiles, tiles.size() * sizeof(mdg::Tile));
@@ -189,6 +220,23 @@ int set_block(mdg_ctx* h, int block)
     h->d_tiles = d_tiles;
     h->n_tiles = (int)tiles.size();
     h->block = block;
+    // Uniform batches (all environments of one size N > 0): the kernels compute the tiles
+    // arithmetically (block / N environments per block), which the greedy packing matches.
+    h->uniform_N = 0;
+    if (h->n_envs > 0 && h->max_env > 0) {
+        const int N = h->max_env;
+        bool uniform = true;
+        for (int32_t e = 0; e < h->n_envs && uniform; ++e) uniform = (h->h_off[e + 1] - h->h_off[e]) == N;
+        if (uniform) {
+            h->uniform_N = N;
+            h->envs_per_tile = block / N;
+            h->uniform_bits = 0;
+            for (const mdg::Tile& t : tiles) h->uniform_bits |= t.w & mdg::kTileAnyDW;
+            bool all_local = true;
+            for (const mdg::Tile& t : tiles) all_local = all_local && (t.w & mdg::kTileWarpLocal);
+            if (all_local) h->uniform_bits |= mdg::kTileWarpLocal;
+        }
+    }
     return MDG_OK;
 }
 
@@ -220,6 +268,10 @@ mdg::StepArgs base_args(mdg_ctx* h, float* state)
     a.env_act = h->d_act;
     a.status = h->d_status;
     a.n = h->n_drones;
+    a.n_envs = h->n_envs;
+    a.uniform_N = h->uniform_N;
+    a.envs_per_tile = h->envs_per_tile;
+    a.uniform_bits = h->uniform_bits;
     a.c = h->dc;
     return a;
 }
@@ -324,6 +376,10 @@ int mdg_create(int32_t n_envs, const int32_t* drones_per_env, const uint32_t* mo
     h->c = cc;
     h->dc = make_dev_consts(cc);
     h->h_off = off;
+    h->h_flags = flags;
+    h->uniform_flags = n_envs > 0 ? flags[0] : -1;
+    for (int32_t e2 = 1; e2 < n_envs; ++e2)
+        if (flags[e2] != flags[0]) h->uniform_flags = -1;
     if ((e = cudaMalloc(&h->d_off, off.size() * sizeof(int32_t))) != cudaSuccess ||
         (e = cudaMalloc(&h->d_flags, std::max<size_t>(1, flags.size()))) != cudaSuccess ||
         (e = cudaMalloc(&h->d_act, std::max<size_t>(1, flags.size()))) != cudaSuccess ||
@@ -338,7 +394,9 @@ int mdg_create(int32_t n_envs, const int32_t* drones_per_env, const uint32_t* mo
         destroy_ctx(h);
         return cuda_fail(e, "mdg_create: cudaMemcpy");
     }
-    int rc = set_block(h, default_block(max_env));
+    int n_sm = 152;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device);
+    int rc = set_block(h, default_block(max_env, total, n_sm > 0 ? n_sm : 152));
     if (rc != MDG_OK) {
         destroy_ctx(h);
         return rc;
@@ -425,7 +483,7 @@ static int step_common(mdg_handle h, float* state, const float* action, int32_t 
     a.nbr_rel = nbr_rel;
     a.n_sub = n_substeps;
     a.act_type = action_type;
-    cudaError_t e = mdg::launch_step(a, h->n_tiles, h->block, with_obs, (cudaStream_t)stream);
+    cudaError_t e = mdg::launch_step(a, h->n_tiles, h->block, with_obs, h->uniform_flags, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "mdg_step: launch");
     return MDG_OK;
 }

@@ -9,13 +9,13 @@ namespace mdg {
 // Float32 copies of the model constants with the products the kernels need folded in
 // once on the host (in double precision, then rounded).
 struct DevConsts {
-    float mass, inv_mass, g;
+    float mass, inv_mass, g, inv_g;
     float kf, km, l_sqrt2;            // Eq. motor: k_f, k_m, L/sqrt(2)
     float J[3], inv_J[3];
     float gnd_k;                      // Eq. ground: C_gnd (r_p/4)^2
     float h_clip;
     float drag_k;                     // Eq. drag: 2 pi / 60 (RPM -> rad/s)
-    float c_xy, c_z;
+    float c_xy, c_z, c_dz;            // c_dz = c_z - c_xy
     float dw_k;                       // Eq. downwash: C1 (r_p/4)^2
     float dw_c2, dw_c3, dw_max_xy2, dw_dz_min;
     float pos_kp[3], pos_ki[3], pos_kd[3], pos_iclamp;
@@ -26,8 +26,12 @@ struct DevConsts {
 };
 
 // A launch tile: whole environments packed into one thread block.
-// x = first drone, y = drones, z = first environment, w = environments.
+// x = first drone, y = drones, z = first environment,
+// w = environments (low 16 bits) | kTileAnyDW | kTileWarpLocal.
 typedef int4 Tile;
+constexpr int kTileEnvMask = 0xffff;
+constexpr int kTileAnyDW = 1 << 30;      // some environment of the tile has downwash on
+constexpr int kTileWarpLocal = 1 << 29;  // every environment lies inside one warp
 
 struct StepArgs {
     float4* state;            // [6][n] float4 planes
@@ -43,6 +47,10 @@ struct StepArgs {
     long long n;
     int n_sub;
     int act_type;             // MDG_ACT_RPM / PID / MIXED
+    int n_envs;
+    int uniform_N;            // > 0: every environment has this many drones (arithmetic tiles)
+    int envs_per_tile;        // uniform batches: environments per block
+    int uniform_bits;         // uniform batches: kTileAnyDW | kTileWarpLocal for every tile
     DevConsts c;
 };
 
@@ -56,7 +64,8 @@ struct PidArgs {
     DevConsts c;
 };
 
-cudaError_t launch_step(const StepArgs& a, int n_tiles, int block, bool with_obs, cudaStream_t s);
+// uniform_flags: the physics subset shared by every environment, or -1 if they differ.
+cudaError_t launch_step(const StepArgs& a, int n_tiles, int block, bool with_obs, int uniform_flags, cudaStream_t s);
 cudaError_t launch_obs(const StepArgs& a, int n_tiles, int block, cudaStream_t s);
 cudaError_t launch_pid(const PidArgs& a, cudaStream_t s);
 

@@ -59,6 +59,17 @@ __device__ __forceinline__ void load_state(const float4* __restrict__ S, long lo
     }
 }
 
+__device__ __forceinline__ void unpack_state(const float4& a, const float4& b, const float4& c, const float4& e,
+                                             const float4& f, Drone& d)
+{
+    d.p[0] = a.x; d.p[1] = a.y; d.p[2] = a.z;
+    d.q[0] = a.w; d.q[1] = b.x; d.q[2] = b.y; d.q[3] = b.z;
+    d.v[0] = b.w; d.v[1] = c.x; d.v[2] = c.y;
+    d.w[0] = c.z; d.w[1] = c.w; d.w[2] = e.x;
+    d.ip[0] = e.y; d.ip[1] = e.z; d.ip[2] = e.w;
+    d.ia[0] = f.x; d.ia[1] = f.y; d.ia[2] = f.z;
+}
+
 __device__ __forceinline__ void store_state(float4* __restrict__ S, long long n, long long g, const Drone& d,
                                             bool att_int)
 {
@@ -67,17 +78,6 @@ __device__ __forceinline__ void store_state(float4* __restrict__ S, long long n,
     S[2 * n + g] = make_float4(d.v[1], d.v[2], d.w[0], d.w[1]);
     S[3 * n + g] = make_float4(d.w[2], d.ip[0], d.ip[1], d.ip[2]);
     if (att_int) S[4 * n + g] = make_float4(d.ia[0], d.ia[1], d.ia[2], 0.f);
-}
-
-// Body-to-world rotation matrix of a unit quaternion [w, x, y, z] (row-major).
-__device__ __forceinline__ void rotation(const float q[4], float R[9])
-{
-    const float w = q[0], x = q[1], y = q[2], z = q[3];
-    const float xx = x * x, yy = y * y, zz = z * z;
-    const float xy = x * y, xz = x * z, yz = y * z, wx = w * x, wy = w * y, wz = w * z;
-    R[0] = 1.f - 2.f * (yy + zz); R[1] = 2.f * (xy - wz);        R[2] = 2.f * (xz + wy);
-    R[3] = 2.f * (xy + wz);        R[4] = 1.f - 2.f * (xx + zz); R[5] = 2.f * (yz - wx);
-    R[6] = 2.f * (xz - wy);        R[7] = 2.f * (yz + wx);        R[8] = 1.f - 2.f * (xx + yy);
 }
 
 // Roll, pitch, yaw in the ZYX convention.
@@ -125,8 +125,8 @@ __device__ __forceinline__ void pid(Drone& d, const float4 wp, const DevConsts& 
     const float T = c.mass * sqrtf(acc[0] * acc[0] + acc[1] * acc[1] + acc[2] * acc[2]);
     float sps, cps;
     sincosf(wp.w, &sps, &cps);
-    const float phi_t = (acc[0] * sps - acc[1] * cps) / c.g;
-    const float theta_t = (acc[0] * cps + acc[1] * sps) / c.g;
+    const float phi_t = (acc[0] * sps - acc[1] * cps) * c.inv_g;
+    const float theta_t = (acc[0] * cps + acc[1] * sps) * c.inv_g;
     float roll, pitch, yaw;
     rpy_of(d.q, roll, pitch, yaw);
     float e[3] = {phi_t - roll, theta_t - pitch, wp.w - yaw};
@@ -145,53 +145,83 @@ __device__ __forceinline__ void pid(Drone& d, const float4 wp, const DevConsts& 
     yaw_err = e[2];
 }
 
+// Downwash of Eq. downwash that drone j at p feels from one drone o of its environment:
+// C1 (r_p/(4 dz))^2 exp(-dxy^2 / (2 beta^2)), beta = C2 dz + C3, when o is strictly above
+// (dz > dz_min >= 0, which also excludes j itself) and dxy is within the lateral cut-off;
+// otherwise 0. One reciprocal r = 1/(dz^2 beta^2) yields 1/dz^2 = beta^2 r and
+// 1/beta^2 = dz^2 r; beta^2 is floored at 1e-12. Branch-free, so that unrolled pairs
+// interleave; the select discards the values computed for excluded pairs (including the
+// inf/NaN of dz = 0). Height differences whose dz^2 beta^2 underflows float32
+// (dz below about 1e-18 m) contribute nothing.
+__device__ __forceinline__ float downwash_pair(const float4 o, float px, float py, float pz, const DevConsts& c)
+{
+    const float dz = o.z - pz;
+    const float dx = o.x - px, dy = o.y - py;
+    const float d2 = dx * dx + dy * dy;
+    const float beta = fmaf(c.dw_c2, dz, c.dw_c3);
+    const float b2 = fmaxf(beta * beta, 1e-12f);
+    const float dz2 = dz * dz;
+    const float r = rcp_approx(dz2 * b2);
+    const float e = ex2_approx(-0.72134752044448170368f * d2 * dz2 * r);  // -0.5 log2(e)
+    const float f = c.dw_k * b2 * r * e;
+    return (dz > c.dw_dz_min && d2 < c.dw_max_xy2 && e > 0.f) ? f : 0.f;
+}
+
 // One substep: forces of Eq. motor/ground/drag/downwash, Newton-Euler, forward Euler
-// and the exponential map (all from the start-of-substep state). `env_pos` points at
-// the shared-memory positions of this drone's environment (N entries).
-__device__ __forceinline__ void substep(Drone& d, const Motor& m, int flags, const float4* env_pos, int N,
+// and the exponential map, all from the start-of-substep state. `env_pos` points at the
+// shared-memory positions of this drone's environment (N entries). kFlags (0..7) and kN
+// (> 0) fix the physics subset and environment size at compile time for uniform batches;
+// kFlags = 8 / kN = 0 take them from the runtime arguments.
+template <int kFlags, int kN>
+__device__ __forceinline__ void substep(Drone& d, const Motor& m, int flags_rt, const float4* env_pos, int N_rt,
                                         const DevConsts& c)
 {
-    float R[9];
-    rotation(d.q, R);
-    float F[3] = {R[2] * m.T, R[5] * m.T, R[8] * m.T - c.mass * c.g};
+    const int flags = kFlags < 8 ? kFlags : flags_rt;
+    const float dt = c.dt_sim;
+    // exponential map with the old body rate: q <- q (x) [cos(theta), sin(theta) w/|w|],
+    // theta = |w| dt/2. sin(theta)/|w| = (dt/2) sinc(theta); for theta^2 <= 0.6 both factors
+    // are the Taylor series of cos and sinc in theta^2 (truncation below 1.2e-10), with
+    // neither a square root nor a division. Larger rotations per substep take sqrtf/sincosf
+    // (the rarely taken branch below).
+    const float nw2 = d.w[0] * d.w[0] + d.w[1] * d.w[1] + d.w[2] * d.w[2];
+    const float hdt = 0.5f * dt;
+    const float t2 = nw2 * (hdt * hdt);
+    float co = fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, -2.7557319e-7f, 2.4801587e-5f), -1.3888889e-3f),
+                                      4.1666668e-2f), -0.5f), 1.0f);
+    float k = hdt * fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, -2.5052108e-8f, 2.7557319e-6f), -1.9841270e-4f),
+                                            8.3333333e-3f), -0.16666667f), 1.0f);
+
+    // Only the body z axis in the world frame, r = R e_z (the third column of R), and R20 are
+    // needed: thrust acts along r, the ground-effect gate reads R22 = r.z and R20, and the
+    // drag of Eq. drag, R diag(c_xy, c_xy, c_z) R^T v, equals c_xy v + (c_z - c_xy)(r . v) r.
+    const float qw = d.q[0], qx = d.q[1], qy = d.q[2], qz = d.q[3];
+    const float r0 = 2.f * (qx * qz + qw * qy);
+    const float r1 = 2.f * (qy * qz - qw * qx);
+    const float r2 = 1.f - 2.f * (qx * qx + qy * qy);
+    float F[3] = {r0 * m.T, r1 * m.T, r2 * m.T - c.mass * c.g};
     if (flags & MDG_GND) {
         // gate |roll| < pi/2 and |pitch| < pi/2: cos(roll) cos(pitch) = R22 > 0, |sin(pitch)| = |R20| < 1
-        if (R[8] > 0.f && fabsf(R[6]) < 1.f) {
-            const float h = fmaxf(d.p[2], c.h_clip);
-            F[2] += c.gnd_k * m.T / (h * h);
-        }
+        const float R20 = 2.f * (qx * qz - qw * qy);
+        const float h = fmaxf(d.p[2], c.h_clip);
+        const float g = c.gnd_k * m.T * rcp_approx(h * h);
+        F[2] += (r2 > 0.f && fabsf(R20) < 1.f) ? g : 0.f;
     }
     if (flags & MDG_DRAG) {
-        const float vb0 = R[0] * d.v[0] + R[3] * d.v[1] + R[6] * d.v[2];
-        const float vb1 = R[1] * d.v[0] + R[4] * d.v[1] + R[7] * d.v[2];
-        const float vb2 = R[2] * d.v[0] + R[5] * d.v[1] + R[8] * d.v[2];
-        const float fb0 = -m.wsum * c.c_xy * vb0, fb1 = -m.wsum * c.c_xy * vb1, fb2 = -m.wsum * c.c_z * vb2;
-        F[0] += R[0] * fb0 + R[1] * fb1 + R[2] * fb2;
-        F[1] += R[3] * fb0 + R[4] * fb1 + R[5] * fb2;
-        F[2] += R[6] * fb0 + R[7] * fb1 + R[8] * fb2;
+        const float rv = (r0 * d.v[0] + r1 * d.v[1]) + r2 * d.v[2];
+        const float kxy = -m.wsum * c.c_xy, kr = -m.wsum * c.c_dz * rv;
+        F[0] += kxy * d.v[0] + kr * r0;
+        F[1] += kxy * d.v[1] + kr * r1;
+        F[2] += kxy * d.v[2] + kr * r2;
     }
     if (flags & MDG_DW) {
-        // Sum over drones strictly above (dz > dz_min >= 0, which also skips this drone)
-        // within the lateral cut-off of C1 (r_p/(4 dz))^2 exp(-dxy^2 / (2 beta^2)),
-        // beta = C2 dz + C3. One reciprocal r = 1/(dz^2 beta^2) gives both 1/dz^2 = beta^2 r
-        // and 1/beta^2 = dz^2 r; beta^2 is floored at 1e-12.
         const float px = d.p[0], py = d.p[1], pz = d.p[2];
         float acc = 0.f;
-        for (int k = 0; k < N; ++k) {
-            const float4 o = env_pos[k];
-            const float dz = o.z - pz;
-            if (dz > c.dw_dz_min) {
-                const float dx = o.x - px, dy = o.y - py;
-                const float d2 = dx * dx + dy * dy;
-                if (d2 < c.dw_max_xy2) {
-                    const float beta = fmaf(c.dw_c2, dz, c.dw_c3);
-                    const float b2 = fmaxf(beta * beta, 1e-12f);
-                    const float dz2 = dz * dz;
-                    const float r = rcp_approx(dz2 * b2);
-                    const float e = ex2_approx(-0.72134752044448170368f * d2 * dz2 * r);  // -0.5 log2(e)
-                    acc += (e > 0.f) ? c.dw_k * b2 * r * e : 0.f;
-                }
-            }
+        if (kN > 0) {
+#pragma unroll (kN <= 8 ? kN : 8)
+            for (int j = 0; j < kN; ++j) acc += downwash_pair(env_pos[j], px, py, pz, c);
+        } else {
+#pragma unroll 4
+            for (int j = 0; j < N_rt; ++j) acc += downwash_pair(env_pos[j], px, py, pz, c);
         }
         F[2] -= acc;
     }
@@ -200,26 +230,20 @@ __device__ __forceinline__ void substep(Drone& d, const Motor& m, int flags, con
     const float wd0 = c.inv_J[0] * (m.tau[0] - (d.w[1] * Jw2 - d.w[2] * Jw1));
     const float wd1 = c.inv_J[1] * (m.tau[1] - (d.w[2] * Jw0 - d.w[0] * Jw2));
     const float wd2 = c.inv_J[2] * (m.tau[2] - (d.w[0] * Jw1 - d.w[1] * Jw0));
-    const float dt = c.dt_sim;
-    // exponential map with the old body rate: q <- q (x) [cos(|w| dt/2), sin(|w| dt/2) w/|w|]
-    const float nw2 = d.w[0] * d.w[0] + d.w[1] * d.w[1] + d.w[2] * d.w[2];
-    if (nw2 > 0.f) {
+    if (t2 > 0.6f) {
         const float nw = sqrtf(nw2);
-        float s, co;
-        sincosf(0.5f * dt * nw, &s, &co);
-        const float k = s / nw;
+        float sn;
+        sincosf(hdt * nw, &sn, &co);
+        k = sn / nw;
+    }
+    {
         const float bx = k * d.w[0], by = k * d.w[1], bz = k * d.w[2];
-        const float w = d.q[0], x = d.q[1], y = d.q[2], z = d.q[3];
-        float qw = w * co - x * bx - y * by - z * bz;
-        float qx = w * bx + x * co + y * bz - z * by;
-        float qy = w * by - x * bz + y * co + z * bx;
-        float qz = w * bz + x * by - y * bx + z * co;
-        const float inv = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-        d.q[0] = qw * inv; d.q[1] = qx * inv; d.q[2] = qy * inv; d.q[3] = qz * inv;
-    } else {
-        const float inv = rsqrtf(d.q[0] * d.q[0] + d.q[1] * d.q[1] + d.q[2] * d.q[2] + d.q[3] * d.q[3]);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) d.q[r] *= inv;
+        const float nqw = qw * co - qx * bx - qy * by - qz * bz;
+        const float nqx = qw * bx + qx * co + qy * bz - qz * by;
+        const float nqy = qw * by - qx * bz + qy * co + qz * bx;
+        const float nqz = qw * bz + qx * by - qy * bx + qz * co;
+        const float inv = rsqrtf(nqw * nqw + nqx * nqx + nqy * nqy + nqz * nqz);
+        d.q[0] = nqw * inv; d.q[1] = nqx * inv; d.q[2] = nqy * inv; d.q[3] = nqz * inv;
     }
     // forward Euler: p with the old v, v with the force of the old state
 #pragma unroll
@@ -256,57 +280,57 @@ __device__ __forceinline__ void write_kin(float* __restrict__ kin, long long g, 
 }
 
 // The 4 nearest other drones of the environment (squared distance rounded in the
-// order ((dx*dx + dy*dy) + dz*dz) without contraction, ties to the lower index),
-// from the shared-memory positions/velocities of the environment.
+// order ((dx*dx + dy*dy) + dz*dz) without contraction, ties to the lower index), from the
+// shared-memory positions/velocities of the environment. Candidates are taken in index
+// order; each enters the last slot if strictly closer and moves up past strictly farther
+// entries (branch-free selects), which keeps equal distances in index order.
+template <int kN>
 __device__ __forceinline__ void write_knn(int4* __restrict__ nbr_idx, float* __restrict__ nbr_rel, long long g,
                                           long long env_first, int j, const Drone& d, const float4* env_pos,
-                                          const float4* env_vel, int N)
+                                          const float4* env_vel, int N_rt)
 {
-    float bd[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
-    int bi[4] = {-1, -1, -1, -1};
-    for (int k = 0; k < N; ++k) {
-        if (k == j) continue;
+    float b0 = INFINITY, b1 = INFINITY, b2 = INFINITY, b3 = INFINITY;
+    int i0 = -1, i1 = -1, i2 = -1, i3 = -1;
+    auto consider = [&](int k) {
         const float4 o = env_pos[k];
         const float dx = __fsub_rn(o.x, d.p[0]), dy = __fsub_rn(o.y, d.p[1]), dz = __fsub_rn(o.z, d.p[2]);
-        const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-        if (d2 < bd[3]) {
-            if (d2 < bd[2]) {
-                bd[3] = bd[2]; bi[3] = bi[2];
-                if (d2 < bd[1]) {
-                    bd[2] = bd[1]; bi[2] = bi[1];
-                    if (d2 < bd[0]) {
-                        bd[1] = bd[0]; bi[1] = bi[0];
-                        bd[0] = d2; bi[0] = k;
-                    } else {
-                        bd[1] = d2; bi[1] = k;
-                    }
-                } else {
-                    bd[2] = d2; bi[2] = k;
-                }
-            } else {
-                bd[3] = d2; bi[3] = k;
-            }
-        }
+        float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+        d2 = (k == j) ? INFINITY : d2;
+        bool c = d2 < b3;
+        b3 = c ? d2 : b3; i3 = c ? k : i3;
+        c = b3 < b2;
+        { const float tf = b2; const int ti = i2; b2 = c ? b3 : b2; i2 = c ? i3 : i2; b3 = c ? tf : b3; i3 = c ? ti : i3; }
+        c = b2 < b1;
+        { const float tf = b1; const int ti = i1; b1 = c ? b2 : b1; i1 = c ? i2 : i1; b2 = c ? tf : b2; i2 = c ? ti : i2; }
+        c = b1 < b0;
+        { const float tf = b0; const int ti = i0; b0 = c ? b1 : b0; i0 = c ? i1 : i0; b1 = c ? tf : b1; i1 = c ? ti : i1; }
+    };
+    if (kN > 0) {
+#pragma unroll (kN <= 8 ? kN : 4)
+        for (int k = 0; k < kN; ++k) consider(k);
+    } else {
+        for (int k = 0; k < N_rt; ++k) consider(k);
     }
+    const int bi[4] = {i0, i1, i2, i3};
     int4 idx;
-    idx.x = bi[0] >= 0 ? (int)(env_first + bi[0]) : -1;
-    idx.y = bi[1] >= 0 ? (int)(env_first + bi[1]) : -1;
-    idx.z = bi[2] >= 0 ? (int)(env_first + bi[2]) : -1;
-    idx.w = bi[3] >= 0 ? (int)(env_first + bi[3]) : -1;
+    idx.x = i0 >= 0 ? (int)(env_first + i0) : -1;
+    idx.y = i1 >= 0 ? (int)(env_first + i1) : -1;
+    idx.z = i2 >= 0 ? (int)(env_first + i2) : -1;
+    idx.w = i3 >= 0 ? (int)(env_first + i3) : -1;
     nbr_idx[g] = idx;
     if (nbr_rel) {
         float4* o = reinterpret_cast<float4*>(nbr_rel + 24 * g);
         float f[24];
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
-            if (bi[s] >= 0) {
-                const float4 pp = env_pos[bi[s]], vv = env_vel[bi[s]];
-                f[6 * s + 0] = pp.x - d.p[0]; f[6 * s + 1] = pp.y - d.p[1]; f[6 * s + 2] = pp.z - d.p[2];
-                f[6 * s + 3] = vv.x - d.v[0]; f[6 * s + 4] = vv.y - d.v[1]; f[6 * s + 5] = vv.z - d.v[2];
-            } else {
-#pragma unroll
-                for (int r = 0; r < 6; ++r) f[6 * s + r] = 0.f;
-            }
+            const bool ok = bi[s] >= 0;
+            const float4 pp = env_pos[ok ? bi[s] : 0], vv = env_vel[ok ? bi[s] : 0];
+            f[6 * s + 0] = ok ? pp.x - d.p[0] : 0.f;
+            f[6 * s + 1] = ok ? pp.y - d.p[1] : 0.f;
+            f[6 * s + 2] = ok ? pp.z - d.p[2] : 0.f;
+            f[6 * s + 3] = ok ? vv.x - d.v[0] : 0.f;
+            f[6 * s + 4] = ok ? vv.y - d.v[1] : 0.f;
+            f[6 * s + 5] = ok ? vv.z - d.v[2] : 0.f;
         }
 #pragma unroll
         for (int k = 0; k < 6; ++k) o[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
@@ -318,25 +342,61 @@ __device__ __forceinline__ void write_knn(int4* __restrict__ nbr_idx, float* __r
 //   int off[B + 1] (tile-relative env offsets), int info[B] (flags | action type << 8)
 __host__ __device__ constexpr size_t tile_smem_bytes(int B) { return (size_t)B * 48 + (size_t)(2 * B + 1) * 4; }
 
-// Loads the tile's environment table into shared memory and finds this thread's
-// environment: local first drone, size, flags and action type.
+// The block's tile: whole environments, given by the host's tile table, or computed
+// arithmetically when every environment has the same size (uniform batches).
+struct TileInfo {
+    long long first_drone;
+    int n_drones, first_env, n_envs, bits;
+};
+
+__device__ __forceinline__ TileInfo get_tile(const StepArgs& a)
+{
+    TileInfo ti;
+    if (a.uniform_N > 0) {
+        ti.first_env = blockIdx.x * a.envs_per_tile;
+        ti.n_envs = min(a.envs_per_tile, a.n_envs - ti.first_env);
+        ti.first_drone = (long long)ti.first_env * a.uniform_N;
+        ti.n_drones = ti.n_envs * a.uniform_N;
+        ti.bits = a.uniform_bits;
+    } else {
+        const Tile t = a.tiles[blockIdx.x];
+        ti.first_drone = t.x;
+        ti.n_drones = t.y;
+        ti.first_env = t.z;
+        ti.n_envs = t.w & kTileEnvMask;
+        ti.bits = t.w & ~kTileEnvMask;
+    }
+    return ti;
+}
+
+// This thread's environment: first drone (tile-local), size, flags and action type.
 struct EnvSlot {
     int ls, N, flags, act;
 };
 
-__device__ __forceinline__ EnvSlot tile_env(const StepArgs& a, const Tile& tile, int* s_off, int* s_info)
+__device__ __forceinline__ EnvSlot tile_env(const StepArgs& a, const TileInfo& ti, int* s_off, int* s_info)
 {
+    const int t = threadIdx.x;
+    EnvSlot e = {0, 0, 0, 0};
+    if (a.uniform_N > 0) {
+        if (t < ti.n_drones) {
+            const int k = t / a.uniform_N;
+            e.ls = k * a.uniform_N;
+            e.N = a.uniform_N;
+            e.flags = a.env_flags[ti.first_env + k];
+            e.act = a.act_type == MDG_ACT_MIXED ? (int)a.env_act[ti.first_env + k] : a.act_type;
+        }
+        return e;
+    }
     const int B = blockDim.x;
-    for (int i = threadIdx.x; i <= tile.w; i += B) s_off[i] = a.env_off[tile.z + i] - tile.x;
-    for (int i = threadIdx.x; i < tile.w; i += B) {
-        const int act = a.act_type == MDG_ACT_MIXED ? (int)a.env_act[tile.z + i] : a.act_type;
-        s_info[i] = (int)a.env_flags[tile.z + i] | (act << 8);
+    for (int i = t; i <= ti.n_envs; i += B) s_off[i] = a.env_off[ti.first_env + i] - (int)ti.first_drone;
+    for (int i = t; i < ti.n_envs; i += B) {
+        const int act = a.act_type == MDG_ACT_MIXED ? (int)a.env_act[ti.first_env + i] : a.act_type;
+        s_info[i] = (int)a.env_flags[ti.first_env + i] | (act << 8);
     }
     __syncthreads();
-    EnvSlot e = {0, 0, 0, 0};
-    const int t = threadIdx.x;
-    if (t < tile.y) {
-        int lo = 0, hi = tile.w - 1;  // largest env with s_off[env] <= t
+    if (t < ti.n_drones) {
+        int lo = 0, hi = ti.n_envs - 1;  // largest env with s_off[env] <= t
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (s_off[mid] <= t) lo = mid;
@@ -350,8 +410,17 @@ __device__ __forceinline__ EnvSlot tile_env(const StepArgs& a, const Tile& tile,
     return e;
 }
 
-template <bool kObs>
-__global__ void __launch_bounds__(1024) step_kernel(const StepArgs a)
+// Variants with a compile-time environment size run blocks of at most kSmallBlock threads
+// and may use up to 128 registers; the generic variant takes any block size.
+constexpr int kSmallBlock = 256;
+template <int kN>
+struct StepBounds {
+    static constexpr int threads = kN > 0 ? kSmallBlock : 1024;
+    static constexpr int min_blocks = kN > 0 ? 2 : 1;
+};
+
+template <bool kObs, int kFlags, int kN>
+__global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_blocks) step_kernel(const StepArgs a)
 {
     extern __shared__ float4 smem[];
     const int B = blockDim.x;
@@ -360,18 +429,28 @@ __global__ void __launch_bounds__(1024) step_kernel(const StepArgs a)
     int* s_off = reinterpret_cast<int*>(smem + 3 * B);
     int* s_info = s_off + B + 1;
 
-    const Tile tile = a.tiles[blockIdx.x];
-    const EnvSlot env = tile_env(a, tile, s_off, s_info);
+    const TileInfo tile = get_tile(a);
     const int t = threadIdx.x;
-    const bool active = t < tile.y;
-    const long long g = (long long)tile.x + t;
+    const bool active = t < tile.n_drones;
+    const long long g = tile.first_drone + t;
+    // Issue the state and action loads before the environment lookup so that their
+    // latency overlaps it.
+    float4 s0 = {}, s1 = {}, s2 = {}, s3 = {}, s4 = {}, act = {};
+    if (active) {
+        s0 = a.state[g];
+        s1 = a.state[a.n + g];
+        s2 = a.state[2 * a.n + g];
+        s3 = a.state[3 * a.n + g];
+        if (a.act_type != MDG_ACT_RPM) s4 = a.state[4 * a.n + g];
+        act = a.action[g];
+    }
+    const EnvSlot env = tile_env(a, tile, s_off, s_info);
     const bool is_pid = env.act == MDG_ACT_PID;
 
-    Drone d = {};
+    Drone d;
+    unpack_state(s0, s1, s2, s3, s4, d);
     float rpm[4] = {0.f, 0.f, 0.f, 0.f};
     if (active) {
-        load_state(a.state, a.n, g, d, is_pid);
-        const float4 act = a.action[g];
         if (is_pid) {
             float ep[3], ye;
             pid(d, act, a.c, rpm, ep, ye);
@@ -383,14 +462,19 @@ __global__ void __launch_bounds__(1024) step_kernel(const StepArgs a)
         }
     }
     const Motor m = motor(rpm, a.c);
-    const bool tile_dw = __syncthreads_or(active && (env.flags & MDG_DW));
+    // Downwash needs the start-of-substep positions of the environment: published in a
+    // double-buffered shared array, one barrier per substep (a warp barrier when every
+    // environment of the tile lies inside one warp).
+    const bool tile_dw = (tile.bits & kTileAnyDW) != 0;
+    const bool warp_local = (tile.bits & kTileWarpLocal) != 0;
     for (int s = 0; s < a.n_sub; ++s) {
         float4* buf = s_pos + (s & 1) * B;
         if (tile_dw) {
             buf[t] = make_float4(d.p[0], d.p[1], d.p[2], 0.f);
-            __syncthreads();
+            if (warp_local) __syncwarp();
+            else __syncthreads();
         }
-        if (active) substep(d, m, env.flags, buf + env.ls, env.N, a.c);
+        if (active) substep<kFlags, kN>(d, m, env.flags, buf + env.ls, env.N, a.c);
     }
     bool bad = false;
     if (active) {
@@ -410,8 +494,8 @@ __global__ void __launch_bounds__(1024) step_kernel(const StepArgs a)
         __syncthreads();
         if (active) {
             write_kin(a.kin, g, d, rpm);
-            write_knn(a.nbr_idx, a.nbr_rel, g, (long long)tile.x + env.ls, t - env.ls, d, pb + env.ls,
-                      s_vel + env.ls, env.N);
+            write_knn<kN>(a.nbr_idx, a.nbr_rel, g, tile.first_drone + env.ls, t - env.ls, d, pb + env.ls,
+                          s_vel + env.ls, env.N);
         }
     }
 }
@@ -425,25 +509,25 @@ __global__ void __launch_bounds__(1024) obs_kernel(const StepArgs a)
     int* s_off = reinterpret_cast<int*>(smem + 3 * B);
     int* s_info = s_off + B + 1;
 
-    const Tile tile = a.tiles[blockIdx.x];
-    const EnvSlot env = tile_env(a, tile, s_off, s_info);
+    const TileInfo tile = get_tile(a);
     const int t = threadIdx.x;
-    const bool active = t < tile.y;
-    const long long g = (long long)tile.x + t;
+    const bool active = t < tile.n_drones;
+    const long long g = tile.first_drone + t;
     Drone d = {};
     float4 ap = make_float4(0.f, 0.f, 0.f, 0.f);
     if (active) {
         load_state(a.state, a.n, g, d, false);
         ap = a.state[5 * a.n + g];
     }
+    const EnvSlot env = tile_env(a, tile, s_off, s_info);
     s_pos[t] = make_float4(d.p[0], d.p[1], d.p[2], 0.f);
     s_vel[t] = make_float4(d.v[0], d.v[1], d.v[2], 0.f);
     __syncthreads();
     if (active) {
         const float apv[4] = {ap.x, ap.y, ap.z, ap.w};
         write_kin(a.kin, g, d, apv);
-        write_knn(a.nbr_idx, a.nbr_rel, g, (long long)tile.x + env.ls, t - env.ls, d, s_pos + env.ls,
-                  s_vel + env.ls, env.N);
+        write_knn<0>(a.nbr_idx, a.nbr_rel, g, tile.first_drone + env.ls, t - env.ls, d, s_pos + env.ls,
+                     s_vel + env.ls, env.N);
     }
 }
 
@@ -469,29 +553,63 @@ __global__ void __launch_bounds__(256) pid_kernel(const PidArgs a)
 
 }  // namespace
 
-cudaError_t launch_step(const StepArgs& a, int n_tiles, int block, bool with_obs, cudaStream_t s)
+// The step-kernel variants: compile-time physics subset and environment size for the
+// uniform batches of the benchmark workloads, and a runtime-generic one for the rest.
+#define MDG_STEP_VARIANTS(X) X(7, 4) X(7, 64) X(3, 1) X(8, 0)
+
+template <bool kObs>
+static void* step_kernel_ptr(int flags, int N, int block)
+{
+#define MDG_PICK(F, NN)                                                                       \
+    if ((F == 8 || flags == F) && (NN == 0 || (N == NN && block <= kSmallBlock)))            \
+        return (void*)step_kernel<kObs, F, NN>;
+    MDG_STEP_VARIANTS(MDG_PICK)
+#undef MDG_PICK
+    return nullptr;
+}
+
+// Opt the tile kernels in to the shared memory of the largest block, once per device.
+static cudaError_t tile_kernels_setup()
+{
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+    const int smem = (int)tile_smem_bytes(1024);
+#define MDG_ATTR(F, NN)                                                                                     \
+    if ((e = cudaFuncSetAttribute(step_kernel<true, F, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                  smem)) != cudaSuccess ||                                                  \
+        (e = cudaFuncSetAttribute(step_kernel<false, F, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                                  smem)) != cudaSuccess)                                                    \
+        return e;
+    MDG_STEP_VARIANTS(MDG_ATTR)
+#undef MDG_ATTR
+    if ((e = cudaFuncSetAttribute(obs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+        return e;
+    if (dev >= 0 && dev < 64) done[dev] = true;
+    return cudaSuccess;
+}
+
+cudaError_t launch_step(const StepArgs& a, int n_tiles, int block, bool with_obs, int uniform_flags, cudaStream_t s)
 {
     if (n_tiles == 0) return cudaSuccess;
-    const size_t smem = tile_smem_bytes(block);
-    if (with_obs) {
-        cudaError_t e = cudaFuncSetAttribute(step_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        step_kernel<true><<<n_tiles, block, smem, s>>>(a);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(step_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        step_kernel<false><<<n_tiles, block, smem, s>>>(a);
-    }
-    return cudaGetLastError();
+    cudaError_t e = tile_kernels_setup();
+    if (e != cudaSuccess) return e;
+    // a compile-time variant needs one physics subset and one environment size for the batch
+    const int flags = uniform_flags;
+    const int N = a.uniform_N;
+    void* fn = with_obs ? step_kernel_ptr<true>(flags, N, block) : step_kernel_ptr<false>(flags, N, block);
+    void* args[] = {const_cast<StepArgs*>(&a)};
+    return cudaLaunchKernel(fn, dim3(n_tiles), dim3(block), args, tile_smem_bytes(block), s);
 }
 
 cudaError_t launch_obs(const StepArgs& a, int n_tiles, int block, cudaStream_t s)
 {
     if (n_tiles == 0) return cudaSuccess;
-    const size_t smem = tile_smem_bytes(block);
-    cudaError_t e = cudaFuncSetAttribute(obs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = tile_kernels_setup();
     if (e != cudaSuccess) return e;
-    obs_kernel<<<n_tiles, block, smem, s>>>(a);
+    obs_kernel<<<n_tiles, block, tile_smem_bytes(block), s>>>(a);
     return cudaGetLastError();
 }
 

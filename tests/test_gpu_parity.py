@@ -15,7 +15,7 @@ import oracle
 import paper_2606_08039_gb300 as mdg
 from paper_2606_08039_gb300 import workloads as wl
 from helpers import (assert_horizon_close, assert_state_close, excess, oracle_arrays, oracle_step,
-                     perturbed_spread, subset_layout, swarm_state)
+                     tolerance_response, subset_layout, swarm_state)
 
 pytestmark = pytest.mark.gpu
 
@@ -87,7 +87,8 @@ def test_single_substep_all_flag_subsets(cuda, act_type):
     xo, io, ao = oracle_step(P, (dpe, flags), x0, i0, a0, action, np.full(len(dpe), act_type), 1)
     assert_state_close(xg, xo, what="one substep")
     if act_type == mdg.ACT_RPM:
-        np.testing.assert_array_equal(ag, ao)  # clipping is exact
+        # clipping is exact, at MAX_RPM rounded to float32 on the GPU side
+        np.testing.assert_allclose(ag, ao, rtol=2.0 ** -24, atol=0)
     else:
         assert excess(P.kf * ag ** 2, P.kf * ao ** 2, 1e-5, floor=F_MAX) <= 1.0
         assert excess(ig, io, 1e-5) <= 1.0
@@ -120,8 +121,11 @@ def test_pid_entry_point(cuda):
 
 
 # ------------------------------------------------------------------ short horizons
-@pytest.mark.parametrize("recipe", ["single", "full_aero", "dense", "uneven"])
-def test_one_control_step_recipes(cuda, recipe):
+@pytest.mark.parametrize("recipe,block", [("single", None), ("full_aero", None), ("dense", None), ("uneven", None),
+                                          ("single", 512), ("full_aero", 512), ("dense", 512)])
+def test_one_control_step_recipes(cuda, recipe, block):
+    """block=None: the default block size, which selects the compile-time variant of the step
+    kernel for uniform batches; block=512 forces the runtime-generic variant."""
     if recipe == "single":
         sw = wl.single(0)
     elif recipe == "full_aero":
@@ -132,6 +136,8 @@ def test_one_control_step_recipes(cuda, recipe):
         sw = wl.uneven(2, n_envs=150)
     n = sw.n
     h = mdg.Handle(sw.drones_per_env, sw.flags)
+    if block is not None:
+        h.set_block_size(block)
     if recipe == "uneven":
         h.set_action_types(sw.act_type)
         action, act = wl.mixed_actions(sw, 3, 0, HOVER), mdg.ACT_MIXED
@@ -148,8 +154,8 @@ def test_one_control_step_recipes(cuda, recipe):
     xg, ig, ag = oracle_arrays(state)
     layout = (sw.drones_per_env, sw.flags)
     xo, io, ao = oracle_step(P, layout, x0, i0, a0, action, acts, 5)
-    spread = perturbed_spread(P, layout, x0, i0, a0, action, acts, 5)
-    assert_horizon_close(xg, xo, spread, what=recipe)
+    spread = tolerance_response(P, layout, x0, i0, a0, action, acts, 5)
+    assert_horizon_close(xg, xo, spread, 5, what=recipe)
     _check_obs(xg, ag, sw.drones_per_env, kin, idx, rel)
 
 
@@ -189,8 +195,8 @@ def test_full_size_sampled(cuda, recipe):
     layout = (dpe, sw.flags[envs])
     acts = np.full(len(envs), act)
     xo, _, _ = oracle_step(P, layout, x0[sel], i0[sel], a0[sel], action[sel], acts, 5)
-    spread = perturbed_spread(P, layout, x0[sel], i0[sel], a0[sel], action[sel], acts, 5)
-    assert_horizon_close(xg[sel], xo, spread, what=recipe)
+    spread = tolerance_response(P, layout, x0[sel], i0[sel], a0[sel], action[sel], acts, 5)
+    assert_horizon_close(xg[sel], xo, spread, 5, what=recipe)
     # observations of the sampled environments (indices are global)
     kin_s, idx_s, rel_s = kin.cpu().numpy()[sel], idx.cpu().numpy()[sel], rel.cpu().numpy()[sel]
     base = np.concatenate([[0], np.cumsum(sw.drones_per_env)])[envs]
