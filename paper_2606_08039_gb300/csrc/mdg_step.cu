@@ -217,7 +217,7 @@ __device__ __forceinline__ void substep(Drone& d, const Motor& m, int flags_rt, 
         const float px = d.p[0], py = d.p[1], pz = d.p[2];
         float acc = 0.f;
         if (kN > 0) {
-#pragma unroll (kN <= 8 ? kN : 8)
+#pragma unroll((kN > 0 && kN <= 8) ? kN : 8)
             for (int j = 0; j < kN; ++j) acc += downwash_pair(env_pos[j], px, py, pz, c);
         } else {
 #pragma unroll 4
@@ -306,7 +306,7 @@ __device__ __forceinline__ void write_knn(int4* __restrict__ nbr_idx, float* __r
         { const float tf = b0; const int ti = i0; b0 = c ? b1 : b0; i0 = c ? i1 : i0; b1 = c ? tf : b1; i1 = c ? ti : i1; }
     };
     if (kN > 0) {
-#pragma unroll (kN <= 8 ? kN : 4)
+#pragma unroll((kN > 0 && kN <= 8) ? kN : 4)
         for (int k = 0; k < kN; ++k) consider(k);
     } else {
         for (int k = 0; k < N_rt; ++k) consider(k);
