@@ -52,7 +52,7 @@ BYTES_PER_DRONE_STEP = STATE_BYTES_READ + ACTION_BYTES + STATE_BYTES_WRITE + OBS
 # DRAM traffic of one step-kernel launch on the full-aero workload, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel source whose
 # sha256 prefix is recorded with it; profiles/ holds the capture's summary.
-NCU_TRAFFIC = {"kernel_sha": None, "bytes": None}
+NCU_TRAFFIC = {"kernel_sha": "ea163c4b5c9db96d", "bytes": 6322944 + 256}
 
 
 def kernel_sha() -> str:
@@ -119,6 +119,27 @@ class ClockSampler:
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def replica_seed(rank: int) -> int:
+    """Each rank simulates its own independent full-aero swarm (weak scaling)."""
+    return 1 + rank
+
+
+def combine_over_ranks(times_ms, world: int, device=None):
+    """Max over ranks of each timed quantity (a barrier-bracketed region is as slow as its
+    slowest rank). Uses the default process group when world > 1."""
+    import torch
+    t = torch.tensor(list(times_ms), dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def throughput(units_per_step_per_rank: int, world: int, steps: int, total_ms: float) -> float:
+    """Whole-job units per second: every rank's units over the max-over-ranks time."""
+    return units_per_step_per_rank * world * steps / (total_ms * 1e-3)
 
 
 def cpu_baseline(seconds_target: float = 10.0) -> dict:
@@ -212,11 +233,11 @@ def main() -> None:
         dist.init_process_group("nccl", device_id=dev)
 
     # workload: the full-aero swarm, one independent replica per rank
-    sw = wl.full_aero(1 + rank)
+    sw = wl.full_aero(replica_seed(rank))
     h = mdg.Handle(sw.drones_per_env, sw.flags)
     init_state = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=dev)
     state = init_state.clone()
-    wp_host = torch.from_numpy(wl.waypoints(1 + rank, sw.n)).pin_memory()
+    wp_host = torch.from_numpy(wl.waypoints(replica_seed(rank), sw.n)).pin_memory()
     wp = wp_host.to(dev)
     kin, idx, rel = h.new_obs(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -289,13 +310,9 @@ def main() -> None:
     h2d = wp_host.numel() * 4
     d2h = kin_h.numel() * 4 + idx_h.numel() * 4 + rel_h.numel() * 4
 
-    t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms, e2e_ms = float(t[0]), float(t[1])
-    substeps_per_step = sw.n * N_SUB * world
-    value = substeps_per_step * args.steps / (total_ms * 1e-3)
-    e2e_value = substeps_per_step * args.e2e_steps / (e2e_ms * 1e-3)
+    total_ms, e2e_ms = combine_over_ranks([total_ms, e2e_ms], world, device=dev)
+    value = throughput(sw.n * N_SUB, world, args.steps, total_ms)
+    e2e_value = throughput(sw.n * N_SUB, world, args.e2e_steps, e2e_ms)
 
     if rank == 0:
         peaks = measured_peaks()
