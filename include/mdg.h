@@ -189,6 +189,44 @@ int mdg_obs(mdg_handle h, const float* state, float* kin, int32_t* nbr_idx, floa
  * bit was set, else MDG_OK (or MDG_ERR_CUDA). */
 int mdg_status(mdg_handle h, void* stream, uint32_t* bits, int64_t* first_drone);
 
+/* One control step that allocates no device memory: mdg_step_obs (or mdg_step when
+ * kin is NULL) for a batch described on the host, with no handle. The paper has no
+ * counterpart; this entry point exists for callers that cannot call cudaMalloc, for
+ * example a process whose device memory is owned by another allocator (a training
+ * framework's caching allocator that has reserved the free memory) or a control loop
+ * that must not allocate after it starts. mdg_create allocates the batch tables and the
+ * status word, so such callers cannot hold a handle.
+ *
+ * Instead of allocating, the call keeps the batch tables (CSR offsets, physics flags,
+ * action types, launch tiles) and the status word in one file-scope static device array
+ * of MDG_NOALLOC_SCRATCH_BYTES (about 353 KiB), which every GPU that loads the library
+ * holds until the process exits. It supports at most MDG_NOALLOC_MAX_ENVS environments
+ * and rejects larger batches with MDG_ERR_ARG. The caller passes every input and output:
+ *   c               constants (NULL = mdg_constants_cf2x)
+ *   n_envs, drones_per_env, model_flags   host arrays, as for mdg_create
+ *   action_types    host [n_envs] RPM/PID per environment when action_type is
+ *                   MDG_ACT_MIXED, else ignored (may be NULL)
+ *   state, action, action_type, n_substeps, kin, nbr_idx, nbr_rel   as for mdg_step_obs
+ *                   (kin = NULL: no observations, nbr_idx and nbr_rel are ignored)
+ *   status_out      device uint32 [2] or NULL: receives this call's status bits and the
+ *                   smallest non-finite drone index (0xffffffff if none), as mdg_status
+ *                   reports them; not written when the batch has no drones
+ * Each call uploads the tables and a cleared status word into the array with
+ * cudaMemcpyAsync on `stream` from a static host staging buffer, then launches the step
+ * kernel there. It calls no cudaMalloc, cudaFree or other allocating routine.
+ * The first call on a device performs that device's set-up (it looks up the array's
+ * device address with the device current); make that first call before any stream
+ * capture. All calls share the array and it keeps the last call's contents, so calls
+ * that overlap on the GPU (on different streams or from different host threads) race;
+ * serialise them. Errors: MDG_ERR_ARG (as mdg_create / mdg_step_obs, or too many
+ * environments), MDG_ERR_CUDA. */
+#define MDG_NOALLOC_MAX_ENVS 16384
+#define MDG_NOALLOC_SCRATCH_BYTES 360960
+int mdg_step_obs_noalloc(const mdg_constants* c, int32_t n_envs, const int32_t* drones_per_env,
+                         const uint32_t* model_flags, const uint8_t* action_types, float* state, const float* action,
+                         int32_t action_type, int32_t n_substeps, float* kin, int32_t* nbr_idx, float* nbr_rel,
+                         uint32_t* status_out, void* stream);
+
 /* Message of the last error on this host thread ("" if none). */
 const char* mdg_last_error(void);
 

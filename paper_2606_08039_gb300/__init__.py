@@ -53,6 +53,8 @@ _SIGNATURES = {
     "mdg_obs": ([_VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "mdg_status": ([_VP, _VP, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "mdg_last_error": ([], ctypes.c_char_p),
+    "mdg_step_obs_noalloc": ([_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP,
+                              _VP, _VP, _VP], ctypes.c_int),
 }
 
 _lock = threading.Lock()

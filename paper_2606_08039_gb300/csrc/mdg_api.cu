@@ -79,7 +79,10 @@ struct mdg_ctx {
     uint32_t* d_status = nullptr;
 };
 
-namespace {
+// Table and constant builders shared by the handle API and the allocation-free entry point.
+namespace mdg {
+
+void set_last_error(const char* msg) { g_last_error = msg; }
 
 bool constants_valid(const mdg_constants& c, std::string& why)
 {
@@ -101,7 +104,7 @@ bool constants_valid(const mdg_constants& c, std::string& why)
     return true;
 }
 
-mdg::DevConsts make_dev_consts(const mdg_constants& c)
+DevConsts make_dev_consts(const mdg_constants& c)
 {
     mdg::DevConsts d{};
     const double pi = 3.14159265358979323846;
@@ -151,7 +154,7 @@ mdg::DevConsts make_dev_consts(const mdg_constants& c)
 
 // Greedy packing of whole environments, in CSR order, into tiles of at most `block`
 // drones and `block` environments, with the tile bits the kernels branch on.
-std::vector<mdg::Tile> build_tiles(const std::vector<int32_t>& off, const std::vector<uint8_t>& flags, int block)
+std::vector<Tile> build_tiles(const std::vector<int32_t>& off, const std::vector<uint8_t>& flags, int block)
 {
     std::vector<mdg::Tile> tiles;
     const int n_envs = (int)off.size() - 1;
@@ -199,6 +202,15 @@ int default_block(int32_t max_env, int64_t n_drones, int n_sm)
     }
     return best;
 }
+
+}  // namespace mdg
+
+namespace {
+
+using mdg::build_tiles;
+using mdg::constants_valid;
+using mdg::default_block;
+using mdg::make_dev_consts;
 
 int set_block(mdg_ctx* h, int block)
 {

@@ -4,6 +4,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+#include <vector>
+
+#include "mdg.h"
+
 namespace mdg {
 
 // Float32 copies of the model constants with the products the kernels need folded in
@@ -65,6 +70,13 @@ struct PidArgs {
 };
 
 // uniform_flags: the physics subset shared by every environment, or -1 if they differ.
+// Host-side builders (mdg_api.cu).
+void set_last_error(const char* msg);  // the message mdg_last_error() returns on this thread
+bool constants_valid(const mdg_constants& c, std::string& why);
+DevConsts make_dev_consts(const mdg_constants& c);
+std::vector<Tile> build_tiles(const std::vector<int32_t>& off, const std::vector<uint8_t>& flags, int block);
+int default_block(int32_t max_env, int64_t n_drones, int n_sm);
+
 cudaError_t launch_step(const StepArgs& a, int n_tiles, int block, bool with_obs, int uniform_flags, cudaStream_t s);
 cudaError_t launch_obs(const StepArgs& a, int n_tiles, int block, cudaStream_t s);
 cudaError_t launch_pid(const PidArgs& a, cudaStream_t s);
