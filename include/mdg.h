@@ -136,8 +136,8 @@ int mdg_set_action_types(mdg_handle h, const uint8_t* per_env);
 
 /* Threads per block of the step kernels (a multiple of 32 in [32, 1024] and at least
  * the largest environment, rounded up to 32). Environments are packed whole into
- * blocks of at most this many drones. The default is chosen at creation;
- * mdg_autotune overwrites it. */
+ * blocks of at most this many drones. The default (chosen at creation) spreads the
+ * blocks evenly over the SMs; mdg_autotune picks by measurement. */
 int mdg_set_block_size(mdg_handle h, int32_t threads_per_block);
 int32_t mdg_get_block_size(mdg_handle h);
 
@@ -182,6 +182,52 @@ int mdg_pid(mdg_handle h, float* state, const float* waypoints, float* rpm_out, 
  *   nbr_rel  device float32 [n_drones][24] or NULL: per neighbour [p_i - p_j, v_i - v_j],
  *            zeros for padded slots */
 int mdg_obs(mdg_handle h, const float* state, float* kin, int32_t* nbr_idx, float* nbr_rel, void* stream);
+
+/* Observation modes of mdg_rollout. */
+#define MDG_OBS_NONE 0       /* no observations */
+#define MDG_OBS_LAST 1       /* observations of the state after the last step ([n] outputs) */
+#define MDG_OBS_EVERY_STEP 2 /* observations after every step ([K][n] outputs) */
+
+/* K control steps in one launch (uneven batches in one persistent launch). Persistent
+ * thread blocks take work items — whole environments, for uneven batches grouped after
+ * sorting the environments by (size, physics subset) so that a warp's environments share
+ * both — from an atomic counter, longest items first, and advance each item through all
+ * K steps with the drones' state in registers: the state is read and written once per
+ * rollout. Every step is exactly mdg_step's (Section 3.4.2 per step), so K calls of
+ * mdg_step_obs give the same result.
+ *   state            as for mdg_step (updated in place)
+ *   actions          device float32 [K][n_drones][4] when action_per_step != 0, else one
+ *                    [n_drones][4] used for every step (e.g. fixed PID waypoints)
+ *   action_type, n_substeps   as for mdg_step
+ *   K                number of control steps (0: no-op)
+ *   obs_mode         MDG_OBS_NONE / MDG_OBS_LAST / MDG_OBS_EVERY_STEP; kin, nbr_idx and
+ *                    nbr_rel (may be NULL) are laid out as for mdg_obs, with a leading
+ *                    [K] dimension for MDG_OBS_EVERY_STEP
+ * The handle owns the work counter, so rollouts of one handle must not overlap on the GPU.
+ * Errors: as mdg_step. */
+int mdg_rollout(mdg_handle h, float* state, const float* actions, int32_t action_per_step, int32_t action_type,
+                int32_t n_substeps, int32_t K, int32_t obs_mode, float* kin, int32_t* nbr_idx, float* nbr_rel,
+                void* stream);
+
+/* A CUDA graph of one mdg_rollout with fixed arguments (the work-counter reset and the
+ * persistent launch), for replaying a K-step rollout with one host call. The buffers are
+ * bound at creation; the graph is tied to the handle's device and to its current block
+ * size (create it after mdg_autotune / mdg_set_block_size). Launch it on any stream. */
+typedef struct mdg_graph_s* mdg_graph;
+int mdg_rollout_graph_create(mdg_handle h, float* state, const float* actions, int32_t action_per_step,
+                             int32_t action_type, int32_t n_substeps, int32_t K, int32_t obs_mode, float* kin,
+                             int32_t* nbr_idx, float* nbr_rel, mdg_graph* out);
+int mdg_graph_launch(mdg_graph g, void* stream);
+int mdg_graph_destroy(mdg_graph g);
+
+/* Autotuner: times the step kernels (K = 0: mdg_step_obs; K > 0: a K-step mdg_rollout
+ * with observations after the last step) on the caller's state and actions for every
+ * block size 32, 64, 128, ..., 1024 that holds the largest environment (5 timed launches
+ * after 2 warm-ups each, the state restored before every launch), keeps the fastest with
+ * mdg_set_block_size and restores the state. Allocates temporary scratch; synchronises
+ * `stream`. Writes the chosen size and its mean time in ms (either pointer may be NULL). */
+int mdg_autotune(mdg_handle h, float* state, const float* actions, int32_t action_per_step, int32_t action_type,
+                 int32_t n_substeps, int32_t K, void* stream, int32_t* best_block, float* best_ms);
 
 /* Read and clear the status word: synchronises `stream`, writes the MDG_STATUS_* bits
  * raised since the last call to *bits and the smallest offending drone index (or -1)

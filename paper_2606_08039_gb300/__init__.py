@@ -30,6 +30,7 @@ NBR_FEAT = 6
 MAX_ENV_DRONES = 1024
 
 OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_UNSUPPORTED = 0, -1, -2, -3, -4
+OBS_NONE, OBS_LAST, OBS_EVERY_STEP = 0, 1, 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libmdg.so")
@@ -53,6 +54,14 @@ _SIGNATURES = {
     "mdg_obs": ([_VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "mdg_status": ([_VP, _VP, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "mdg_last_error": ([], ctypes.c_char_p),
+    "mdg_rollout": ([_VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                     _VP, _VP, _VP, _VP], ctypes.c_int),
+    "mdg_rollout_graph_create": ([_VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                  ctypes.c_int32, _VP, _VP, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
+    "mdg_graph_launch": ([_VP, _VP], ctypes.c_int),
+    "mdg_graph_destroy": ([_VP], ctypes.c_int),
+    "mdg_autotune": ([_VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP,
+                      ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     "mdg_step_obs_noalloc": ([_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP,
                               _VP, _VP, _VP], ctypes.c_int),
 }
@@ -189,6 +198,28 @@ def unpack_state(state) -> dict:
             "ip": s[3, :, 1:4].copy(), "ia": s[4, :, 0:3].copy(), "a_prev": s[5].copy()}
 
 
+class Graph:
+    """A replayable rollout (mdg_graph); keeps its buffers alive."""
+
+    def __init__(self, g, keep):
+        self._g = g
+        self._keep = keep
+
+    def launch(self, stream=None):
+        _check(lib().mdg_graph_launch(self._g, _stream(stream)))
+
+    def close(self):
+        if self._g:
+            lib().mdg_graph_destroy(self._g)
+            self._g = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Handle:
     """A batch of environments (mdg_create). Owns the device tables; all state, action and
     observation tensors belong to the caller."""
@@ -272,6 +303,49 @@ class Handle:
         if rc not in (OK, ERR_NONFINITE):
             _check(rc)
         return rc, bits.value, first.value
+
+    def rollout(self, state, actions, action_type: int, n_substeps: int, K: int, obs_mode: int = OBS_NONE,
+                kin=None, nbr_idx=None, nbr_rel=None, stream=None):
+        """K control steps in one persistent launch (mdg_rollout). `actions` is [K, n, 4]
+        (one action per step) or [n, 4] (reused every step)."""
+        torch = _torch()
+        per_step = actions.dim() == 3
+        shape = (K, self.n, 4) if per_step else (self.n, 4)
+        lead = (K,) if obs_mode == OBS_EVERY_STEP else ()
+        _check(lib().mdg_rollout(
+            self._h, _ptr(state, "state", torch.float32, (STATE_PLANES, self.n, 4)),
+            _ptr(actions, "actions", torch.float32, shape), int(per_step), int(action_type), int(n_substeps), int(K),
+            int(obs_mode), _ptr(kin, "kin", torch.float32, lead + (self.n, KIN_DIM)),
+            _ptr(nbr_idx, "nbr_idx", torch.int32, lead + (self.n, NBR_K)),
+            _ptr(nbr_rel, "nbr_rel", torch.float32, lead + (self.n, NBR_K * NBR_FEAT)), _stream(stream)))
+
+    def rollout_graph(self, state, actions, action_type: int, n_substeps: int, K: int, obs_mode: int = OBS_NONE,
+                      kin=None, nbr_idx=None, nbr_rel=None) -> "Graph":
+        """A CUDA graph replaying rollout() with these buffers (mdg_rollout_graph_create)."""
+        torch = _torch()
+        per_step = actions.dim() == 3
+        shape = (K, self.n, 4) if per_step else (self.n, 4)
+        lead = (K,) if obs_mode == OBS_EVERY_STEP else ()
+        g = ctypes.c_void_p()
+        _check(lib().mdg_rollout_graph_create(
+            self._h, _ptr(state, "state", torch.float32, (STATE_PLANES, self.n, 4)),
+            _ptr(actions, "actions", torch.float32, shape), int(per_step), int(action_type), int(n_substeps), int(K),
+            int(obs_mode), _ptr(kin, "kin", torch.float32, lead + (self.n, KIN_DIM)),
+            _ptr(nbr_idx, "nbr_idx", torch.int32, lead + (self.n, NBR_K)),
+            _ptr(nbr_rel, "nbr_rel", torch.float32, lead + (self.n, NBR_K * NBR_FEAT)), ctypes.byref(g)))
+        return Graph(g, keep=(state, actions, kin, nbr_idx, nbr_rel))
+
+    def autotune(self, state, actions, action_type: int, n_substeps: int = 5, K: int = 0, stream=None):
+        """Time every block size on these inputs and keep the fastest (mdg_autotune).
+        Returns (block size, mean ms)."""
+        torch = _torch()
+        per_step = actions.dim() == 3
+        best = ctypes.c_int32()
+        ms = ctypes.c_float()
+        _check(lib().mdg_autotune(self._h, _ptr(state, "state", torch.float32, (STATE_PLANES, self.n, 4)),
+                                  _ptr(actions, "actions", torch.float32), int(per_step), int(action_type),
+                                  int(n_substeps), int(K), _stream(stream), ctypes.byref(best), ctypes.byref(ms)))
+        return best.value, ms.value
 
     # -- output buffers
     def new_obs(self, device="cuda"):

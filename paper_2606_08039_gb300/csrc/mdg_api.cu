@@ -77,6 +77,15 @@ struct mdg_ctx {
     int uniform_bits = 0;
     int uniform_flags = -1;  // physics subset shared by every environment, -1 if they differ
     uint32_t* d_status = nullptr;
+    // rollout work items, built on first use for the current block size
+    int rollout_block = 0;
+    int n_items = 0;
+    int4* d_items = nullptr;
+    int* d_item_order = nullptr;
+    int* d_slot_env = nullptr;
+    int* d_slot_goff = nullptr;
+    int* d_slot_loff = nullptr;
+    int* d_counter = nullptr;
 };
 
 // Table and constant builders shared by the handle API and the allocation-free entry point.
@@ -252,8 +261,108 @@ int set_block(mdg_ctx* h, int block)
     return MDG_OK;
 }
 
+void free_rollout_tables(mdg_ctx* h)
+{
+    cudaFree(h->d_items);
+    cudaFree(h->d_item_order);
+    cudaFree(h->d_slot_env);
+    cudaFree(h->d_slot_goff);
+    cudaFree(h->d_slot_loff);
+    h->d_items = nullptr;
+    h->d_item_order = nullptr;
+    h->d_slot_env = h->d_slot_goff = h->d_slot_loff = nullptr;
+    h->n_items = 0;
+    h->rollout_block = 0;
+}
+
+template <typename T>
+cudaError_t upload(T** dst, const std::vector<T>& v)
+{
+    *dst = nullptr;
+    if (v.empty()) return cudaSuccess;
+    cudaError_t e = cudaMalloc(dst, v.size() * sizeof(T));
+    if (e == cudaSuccess) e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+// Work items of the rollout kernel for the current block size. Uniform batches use the
+// arithmetic tiles. Otherwise environments are sorted by (size descending, physics subset,
+// index), so that the environments sharing a warp share their size and branches, and
+// packed greedily into items of at most `block` drones and `block` environments; items are
+// handed out in decreasing cost (drones plus downwash pairs), longest first.
+int ensure_rollout_tables(mdg_ctx* h)
+{
+    if (h->rollout_block == h->block && h->d_counter) return MDG_OK;
+    if (h->d_item_order) cudaDeviceSynchronize();
+    free_rollout_tables(h);
+    cudaError_t e;
+    if (!h->d_counter && (e = cudaMalloc(&h->d_counter, sizeof(int))) != cudaSuccess)
+        return cuda_fail(e, "rollout: cudaMalloc(counter)");
+    std::vector<int> order;
+    if (h->uniform_N > 0) {
+        h->n_items = h->n_tiles;
+        order.resize(h->n_items);
+        for (int i = 0; i < h->n_items; ++i) order[i] = i;
+    } else {
+        std::vector<int> envs;
+        for (int32_t k = 0; k < h->n_envs; ++k)
+            if (h->h_off[k + 1] > h->h_off[k]) envs.push_back(k);
+        auto N = [&](int k) { return h->h_off[k + 1] - h->h_off[k]; };
+        std::sort(envs.begin(), envs.end(), [&](int a, int b) {
+            if (N(a) != N(b)) return N(a) > N(b);
+            if (h->h_flags[a] != h->h_flags[b]) return h->h_flags[a] < h->h_flags[b];
+            return a < b;
+        });
+        std::vector<int4> items;
+        std::vector<int> slot_goff(envs.size()), slot_loff(envs.size());
+        std::vector<double> cost;
+        size_t i = 0;
+        while (i < envs.size()) {
+            const size_t i0 = i;
+            int drones = 0;
+            bool any_dw = false, local = true;
+            double c = 0.0;
+            while (i < envs.size() && drones + N(envs[i]) <= h->block && (int)(i + 1 - i0) <= h->block) {
+                const int n = N(envs[i]);
+                slot_goff[i] = h->h_off[envs[i]];
+                slot_loff[i] = drones;
+                if (h->h_flags[envs[i]] & MDG_DW) {
+                    any_dw = true;
+                    c += (double)n * n;
+                }
+                if ((drones >> 5) != ((drones + n - 1) >> 5)) local = false;
+                c += n;
+                drones += n;
+                ++i;
+            }
+            if (i == i0) return fail(MDG_ERR_ARG, "rollout: an environment exceeds the block size");
+            int bits = (any_dw ? mdg::kTileAnyDW : 0) | (local ? mdg::kTileWarpLocal : 0);
+            items.push_back(make_int4((int)i0, (int)(i - i0), drones, bits));
+            cost.push_back(c);
+        }
+        h->n_items = (int)items.size();
+        order.resize(h->n_items);
+        for (int k = 0; k < h->n_items; ++k) order[k] = k;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+        if ((e = upload(&h->d_items, items)) != cudaSuccess || (e = upload(&h->d_slot_env, envs)) != cudaSuccess ||
+            (e = upload(&h->d_slot_goff, slot_goff)) != cudaSuccess ||
+            (e = upload(&h->d_slot_loff, slot_loff)) != cudaSuccess) {
+            free_rollout_tables(h);
+            return cuda_fail(e, "rollout: tables");
+        }
+    }
+    if ((e = upload(&h->d_item_order, order)) != cudaSuccess) {
+        free_rollout_tables(h);
+        return cuda_fail(e, "rollout: item order");
+    }
+    h->rollout_block = h->block;
+    return MDG_OK;
+}
+
 void destroy_ctx(mdg_ctx* h)
 {
+    free_rollout_tables(h);
+    cudaFree(h->d_counter);
     cudaFree(h->d_off);
     cudaFree(h->d_flags);
     cudaFree(h->d_act);
@@ -573,6 +682,218 @@ int mdg_status(mdg_handle h, void* stream, uint32_t* bits, int64_t* first_drone)
     if (bits) *bits = st[0];
     if (first_drone) *first_drone = st[1] == 0xffffffffu ? -1 : (int64_t)st[1];
     return (st[0] & MDG_STATUS_NONFINITE) ? MDG_ERR_NONFINITE : MDG_OK;
+}
+
+static int rollout_args(mdg_handle h, float* state, const float* actions, int32_t action_per_step, int32_t action_type,
+                        int32_t n_substeps, int32_t K, int32_t obs_mode, float* kin, int32_t* nbr_idx, float* nbr_rel,
+                        mdg::RolloutArgs* r)
+{
+    if (!h) return fail(MDG_ERR_ARG, "mdg_rollout: NULL handle");
+    if (action_type != MDG_ACT_RPM && action_type != MDG_ACT_PID && action_type != MDG_ACT_MIXED)
+        return fail(MDG_ERR_ARG, "mdg_rollout: unknown action_type %d", action_type);
+    if (action_type == MDG_ACT_MIXED && !h->act_set)
+        return fail(MDG_ERR_ARG, "mdg_rollout: MDG_ACT_MIXED needs mdg_set_action_types first");
+    if (n_substeps < 1) return fail(MDG_ERR_ARG, "mdg_rollout: n_substeps = %d < 1", n_substeps);
+    if (K < 0) return fail(MDG_ERR_ARG, "mdg_rollout: K = %d < 0", K);
+    if (obs_mode != MDG_OBS_NONE && obs_mode != MDG_OBS_LAST && obs_mode != MDG_OBS_EVERY_STEP)
+        return fail(MDG_ERR_ARG, "mdg_rollout: unknown obs_mode %d", obs_mode);
+    int rc;
+    if ((rc = check_state_ptr(h, state, "state")) != MDG_OK) return rc;
+    if ((rc = check_state_ptr(h, actions, "actions")) != MDG_OK) return rc;
+    if (obs_mode != MDG_OBS_NONE) {
+        if ((rc = check_state_ptr(h, kin, "kin")) != MDG_OK) return rc;
+        if ((rc = check_state_ptr(h, nbr_idx, "nbr_idx")) != MDG_OK) return rc;
+        if (nbr_rel && !aligned16(nbr_rel)) return fail(MDG_ERR_ARG, "nbr_rel is not 16-byte aligned");
+    }
+    if ((rc = ensure_rollout_tables(h)) != MDG_OK) return rc;
+    *r = mdg::RolloutArgs{};
+    r->s = base_args(h, state);
+    r->s.action = reinterpret_cast<const float4*>(actions);
+    r->s.kin = obs_mode != MDG_OBS_NONE ? kin : nullptr;
+    r->s.nbr_idx = obs_mode != MDG_OBS_NONE ? reinterpret_cast<int4*>(nbr_idx) : nullptr;
+    r->s.nbr_rel = obs_mode != MDG_OBS_NONE ? nbr_rel : nullptr;
+    r->s.n_sub = n_substeps;
+    r->s.act_type = action_type;
+    r->action_stride = action_per_step ? h->n_drones : 0;
+    r->K = K;
+    r->obs_mode = obs_mode;
+    r->n_items = h->n_items;
+    r->work_counter = h->d_counter;
+    r->item_order = h->d_item_order;
+    r->items = h->d_items;
+    r->slot_env = h->d_slot_env;
+    r->slot_goff = h->d_slot_goff;
+    r->slot_loff = h->d_slot_loff;
+    return MDG_OK;
+}
+
+static cudaError_t enqueue_rollout(mdg_handle h, const mdg::RolloutArgs& r, cudaStream_t s)
+{
+    if (r.n_items == 0 || r.K == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(h->d_counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    int n_sm = 152;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device);
+    const int grid = n_sm * mdg::rollout_blocks_per_sm(h->block, h->uniform_flags, h->uniform_N);
+    return mdg::launch_rollout(r, h->block, h->uniform_flags, grid, s);
+}
+
+int mdg_rollout(mdg_handle h, float* state, const float* actions, int32_t action_per_step, int32_t action_type,
+                int32_t n_substeps, int32_t K, int32_t obs_mode, float* kin, int32_t* nbr_idx, float* nbr_rel,
+                void* stream)
+{
+    if (!h) return fail(MDG_ERR_ARG, "mdg_rollout: NULL handle");
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(MDG_ERR_CUDA, "mdg_rollout: cannot select device %d", h->device);
+    if (h->n_drones == 0) return MDG_OK;
+    mdg::RolloutArgs r;
+    int rc = rollout_args(h, state, actions, action_per_step, action_type, n_substeps, K, obs_mode, kin, nbr_idx,
+                          nbr_rel, &r);
+    if (rc != MDG_OK) return rc;
+    cudaError_t e = enqueue_rollout(h, r, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mdg_rollout: launch");
+    return MDG_OK;
+}
+
+struct mdg_graph_s {
+    int device = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+int mdg_rollout_graph_create(mdg_handle h, float* state, const float* actions, int32_t action_per_step,
+                             int32_t action_type, int32_t n_substeps, int32_t K, int32_t obs_mode, float* kin,
+                             int32_t* nbr_idx, float* nbr_rel, mdg_graph* out)
+{
+    if (!out) return fail(MDG_ERR_ARG, "mdg_rollout_graph_create: out is NULL");
+    *out = nullptr;
+    if (!h) return fail(MDG_ERR_ARG, "mdg_rollout_graph_create: NULL handle");
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(MDG_ERR_CUDA, "mdg_rollout_graph_create: cannot select device %d", h->device);
+    mdg::RolloutArgs r{};
+    if (h->n_drones > 0) {
+        int rc = rollout_args(h, state, actions, action_per_step, action_type, n_substeps, K, obs_mode, kin, nbr_idx,
+                              nbr_rel, &r);
+        if (rc != MDG_OK) return rc;
+    }
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "mdg_rollout_graph_create: stream");
+    mdg_graph g = new mdg_graph_s();
+    g->device = h->device;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t le = h->n_drones > 0 ? enqueue_rollout(h, r, cs) : cudaSuccess;
+        e = cudaStreamEndCapture(cs, &g->graph);
+        if (e == cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return cuda_fail(e, "mdg_rollout_graph_create: capture");
+    }
+    *out = g;
+    return MDG_OK;
+}
+
+int mdg_graph_launch(mdg_graph g, void* stream)
+{
+    if (!g) return fail(MDG_ERR_ARG, "mdg_graph_launch: NULL graph");
+    DeviceGuard dg(g->device);
+    cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mdg_graph_launch");
+    return MDG_OK;
+}
+
+int mdg_graph_destroy(mdg_graph g)
+{
+    if (!g) return MDG_OK;
+    DeviceGuard dg(g->device);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return MDG_OK;
+}
+
+int mdg_autotune(mdg_handle h, float* state, const float* actions, int32_t action_per_step, int32_t action_type,
+                 int32_t n_substeps, int32_t K, void* stream, int32_t* best_block, float* best_ms)
+{
+    if (!h) return fail(MDG_ERR_ARG, "mdg_autotune: NULL handle");
+    if (K < 0) return fail(MDG_ERR_ARG, "mdg_autotune: K = %d < 0", K);
+    if (h->n_drones == 0) {
+        if (best_block) *best_block = h->block;
+        return MDG_OK;
+    }
+    int rc;
+    if ((rc = check_state_ptr(h, state, "state")) != MDG_OK) return rc;
+    if ((rc = check_state_ptr(h, actions, "actions")) != MDG_OK) return rc;
+    DeviceGuard dg(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t state_bytes = (size_t)MDG_STATE_PLANES * 16 * h->n_drones;
+    float* saved = nullptr;
+    float* kin = nullptr;
+    int32_t* idx = nullptr;
+    float* rel = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e;
+    const int original = h->block;
+    int best = original;
+    float best_t = 1e30f;
+    if ((e = cudaMalloc(&saved, state_bytes)) != cudaSuccess || (e = cudaMalloc(&kin, 80 * h->n_drones)) != cudaSuccess ||
+        (e = cudaMalloc(&idx, 16 * h->n_drones)) != cudaSuccess || (e = cudaMalloc(&rel, 96 * h->n_drones)) != cudaSuccess ||
+        (e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(saved, state, state_bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
+        rc = cuda_fail(e, "mdg_autotune: scratch");
+    } else {
+        int lo = 32;
+        while (lo < h->max_env) lo += 32;
+        for (int b = lo; b <= 1024 && rc == MDG_OK; b = b < 64 ? 64 : b * 2) {
+            if ((rc = set_block(h, b)) != MDG_OK) break;
+            float total = 0.f;
+            for (int rep = 0; rep < 7 && rc == MDG_OK; ++rep) {
+                e = cudaMemcpyAsync(state, saved, state_bytes, cudaMemcpyDeviceToDevice, s);
+                if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+                if (e != cudaSuccess) {
+                    rc = cuda_fail(e, "mdg_autotune");
+                    break;
+                }
+                if (K == 0)
+                    rc = step_common(h, state, actions, action_type, n_substeps, kin, idx, rel, true, stream);
+                else
+                    rc = mdg_rollout(h, state, actions, action_per_step, action_type, n_substeps, K, MDG_OBS_LAST, kin,
+                                     idx, rel, stream);
+                if (rc != MDG_OK) break;
+                if ((e = cudaEventRecord(e1, s)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) {
+                    rc = cuda_fail(e, "mdg_autotune: timing");
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep >= 2) total += ms;  // two warm-up launches per candidate
+            }
+            if (rc == MDG_OK && total / 5 < best_t) {
+                best_t = total / 5;
+                best = b;
+            }
+        }
+        if (rc == MDG_OK) rc = set_block(h, best);
+        else set_block(h, original);
+        cudaMemcpyAsync(state, saved, state_bytes, cudaMemcpyDeviceToDevice, s);
+        cudaStreamSynchronize(s);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(saved);
+    cudaFree(kin);
+    cudaFree(idx);
+    cudaFree(rel);
+    if (rc == MDG_OK) {
+        if (best_block) *best_block = best;
+        if (best_ms) *best_ms = best_t;
+    }
+    return rc;
 }
 
 const char* mdg_last_error(void) { return g_last_error.c_str(); }

@@ -59,6 +59,25 @@ struct StepArgs {
     DevConsts c;
 };
 
+// A multi-step rollout (persistent kernel): K control steps per launch, tiles pulled
+// from an atomic work counter. For batches of uneven environments the work items are
+// built from environments sorted by (size, physics subset): slot i of the sorted order
+// is environment slot_env[i], whose drones start at global index slot_goff[i] and at
+// item-local index slot_loff[i].
+struct RolloutArgs {
+    StepArgs s;                 // action = base of [K][n] (or [n] with action_stride 0)
+    long long action_stride;    // float4s between the actions of consecutive steps (n or 0)
+    int K;
+    int obs_mode;               // 0: none, 1: after the last step, 2: after every step ([K][n] outputs)
+    int n_items;
+    int* work_counter;          // zeroed before the launch
+    const int* item_order;      // work items in decreasing cost
+    const int4* items;          // uneven batches: {first slot, envs, drones, tile bits}
+    const int* slot_env;
+    const int* slot_goff;
+    const int* slot_loff;
+};
+
 struct PidArgs {
     float4* state;
     const float4* waypoints;
@@ -78,6 +97,9 @@ std::vector<Tile> build_tiles(const std::vector<int32_t>& off, const std::vector
 int default_block(int32_t max_env, int64_t n_drones, int n_sm);
 
 cudaError_t launch_step(const StepArgs& a, int n_tiles, int block, bool with_obs, int uniform_flags, cudaStream_t s);
+// grid: persistent CTAs (0: one per work item)
+cudaError_t launch_rollout(const RolloutArgs& a, int block, int uniform_flags, int grid, cudaStream_t s);
+int rollout_blocks_per_sm(int block, int uniform_flags, int uniform_N);
 cudaError_t launch_obs(const StepArgs& a, int n_tiles, int block, cudaStream_t s);
 cudaError_t launch_pid(const PidArgs& a, cudaStream_t s);
 

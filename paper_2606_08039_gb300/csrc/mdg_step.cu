@@ -171,7 +171,7 @@ __device__ __forceinline__ float downwash_pair(const float4 o, float px, float p
 // and the exponential map, all from the start-of-substep state. `env_pos` points at the
 // shared-memory positions of this drone's environment (N entries). kFlags (0..7) and kN
 // (> 0) fix the physics subset and environment size at compile time for uniform batches;
-// kFlags = 8 / kN = 0 take them from the runtime arguments.
+// kFlags = 8 / kN <= 0 take them from the runtime arguments.
 template <int kFlags, int kN>
 __device__ __forceinline__ void substep(Drone& d, const Motor& m, int flags_rt, const float4* env_pos, int N_rt,
                                         const DevConsts& c)
@@ -410,13 +410,14 @@ __device__ __forceinline__ EnvSlot tile_env(const StepArgs& a, const TileInfo& t
     return e;
 }
 
-// Variants with a compile-time environment size run blocks of at most kSmallBlock threads
-// and may use up to 128 registers; the generic variant takes any block size.
+// Variants with a compile-time environment size (kN > 0), and the runtime-size variant
+// kN = -1, run blocks of at most kSmallBlock threads and may use up to 128 registers;
+// the kN = 0 variant takes any block size (64 registers).
 constexpr int kSmallBlock = 256;
 template <int kN>
 struct StepBounds {
-    static constexpr int threads = kN > 0 ? kSmallBlock : 1024;
-    static constexpr int min_blocks = kN > 0 ? 2 : 1;
+    static constexpr int threads = kN != 0 ? kSmallBlock : 1024;
+    static constexpr int min_blocks = kN != 0 ? 2 : 1;
 };
 
 template <bool kObs, int kFlags, int kN>
@@ -500,6 +501,156 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
     }
 }
 
+// K control steps in one launch. Persistent CTAs take work items (whole environments)
+// from an atomic counter; an item keeps its drones in registers for all K steps, so the
+// state crosses HBM once per rollout instead of once per step. Per step: action (the
+// next one prefetched), RPMs or PID, n_sub substeps, optional observations.
+template <int kFlags, int kN>
+__global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_blocks)
+    rollout_kernel(const RolloutArgs r)
+{
+    extern __shared__ float4 smem[];
+    const StepArgs& a = r.s;
+    const int B = blockDim.x;
+    float4* s_pos = smem;          // [2][B]
+    float4* s_vel = smem + 2 * B;  // [B]
+    int* s_off = reinterpret_cast<int*>(smem + 3 * B);  // [B + 1]
+    int* s_info = s_off + B + 1;                         // [B]
+    int* s_goff = s_info + B;                            // [B]
+    int* s_item = s_goff + B;
+    const int t = threadIdx.x;
+    const bool uniform = a.uniform_N > 0;
+
+    for (;;) {
+        if (t == 0) *s_item = atomicAdd(r.work_counter, 1);
+        __syncthreads();
+        const int item_idx = *s_item;
+        if (item_idx >= r.n_items) break;
+        const int item = r.item_order[item_idx];
+
+        // ---- this thread's drone and environment
+        int n_drones, bits;
+        EnvSlot env = {0, 0, 0, 0};
+        long long g = 0, env_first = 0;
+        if (uniform) {
+            const int first_env = item * a.envs_per_tile;
+            const int n_envs = min(a.envs_per_tile, a.n_envs - first_env);
+            n_drones = n_envs * a.uniform_N;
+            bits = a.uniform_bits;
+            if (t < n_drones) {
+                const int k = t / a.uniform_N;
+                env.ls = k * a.uniform_N;
+                env.N = a.uniform_N;
+                env.flags = a.env_flags[first_env + k];
+                env.act = a.act_type == MDG_ACT_MIXED ? (int)a.env_act[first_env + k] : a.act_type;
+                env_first = (long long)(first_env + k) * a.uniform_N;
+                g = env_first + (t - env.ls);
+            }
+        } else {
+            const int4 it = r.items[item];
+            const int n_envs = it.y;
+            n_drones = it.z;
+            bits = it.w;
+            for (int i = t; i < n_envs; i += B) {
+                const int e = r.slot_env[it.x + i];
+                const int act = a.act_type == MDG_ACT_MIXED ? (int)a.env_act[e] : a.act_type;
+                s_off[i] = r.slot_loff[it.x + i];
+                s_goff[i] = r.slot_goff[it.x + i];
+                s_info[i] = (int)a.env_flags[e] | (act << 8);
+            }
+            if (t == 0) s_off[n_envs] = n_drones;
+            __syncthreads();
+            if (t < n_drones) {
+                int lo = 0, hi = n_envs - 1;  // largest slot with s_off[slot] <= t
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_off[mid] <= t) lo = mid;
+                    else hi = mid - 1;
+                }
+                env.ls = s_off[lo];
+                env.N = s_off[lo + 1] - env.ls;
+                env.flags = s_info[lo] & 0xff;
+                env.act = s_info[lo] >> 8;
+                env_first = s_goff[lo];
+                g = env_first + (t - env.ls);
+            }
+        }
+        const bool active = t < n_drones;
+        const bool is_pid = env.act == MDG_ACT_PID;
+        const bool tile_dw = (bits & kTileAnyDW) != 0;
+        const bool warp_local = (bits & kTileWarpLocal) != 0;
+
+        Drone d;
+        {
+            float4 s0 = {}, s1 = {}, s2 = {}, s3 = {}, s4 = {};
+            if (active) {
+                s0 = a.state[g];
+                s1 = a.state[a.n + g];
+                s2 = a.state[2 * a.n + g];
+                s3 = a.state[3 * a.n + g];
+                if (a.act_type != MDG_ACT_RPM) s4 = a.state[4 * a.n + g];
+            }
+            unpack_state(s0, s1, s2, s3, s4, d);
+        }
+        float4 act = {};
+        if (active) act = a.action[g];
+        float rpm[4] = {0.f, 0.f, 0.f, 0.f};
+        int sub = 0;  // substeps taken in this item: the snapshot buffers alternate across steps
+        for (int k = 0; k < r.K; ++k) {
+            float4 next = {};
+            if (active && k + 1 < r.K) next = a.action[(k + 1) * r.action_stride + g];
+            if (active) {
+                if (is_pid) {
+                    float ep[3], ye;
+                    pid(d, act, a.c, rpm, ep, ye);
+                } else {
+                    rpm[0] = fminf(a.c.max_rpm, fmaxf(0.f, act.x));
+                    rpm[1] = fminf(a.c.max_rpm, fmaxf(0.f, act.y));
+                    rpm[2] = fminf(a.c.max_rpm, fmaxf(0.f, act.z));
+                    rpm[3] = fminf(a.c.max_rpm, fmaxf(0.f, act.w));
+                }
+            }
+            const Motor m = motor(rpm, a.c);
+            for (int s = 0; s < a.n_sub; ++s, ++sub) {
+                float4* buf = s_pos + (sub & 1) * B;
+                if (tile_dw) {
+                    buf[t] = make_float4(d.p[0], d.p[1], d.p[2], 0.f);
+                    if (warp_local) __syncwarp();
+                    else __syncthreads();
+                }
+                if (active) substep<kFlags, kN>(d, m, env.flags, buf + env.ls, env.N, a.c);
+            }
+            if (r.obs_mode == 2 || (r.obs_mode == 1 && k == r.K - 1)) {
+                const long long o = r.obs_mode == 2 ? (long long)k * a.n : 0;
+                float4* pb = s_pos + (sub & 1) * B;  // not the buffer the last substep read
+                pb[t] = make_float4(d.p[0], d.p[1], d.p[2], 0.f);
+                s_vel[t] = make_float4(d.v[0], d.v[1], d.v[2], 0.f);
+                __syncthreads();
+                if (active) {
+                    write_kin(a.kin, o + g, d, rpm);
+                    write_knn<kN>(a.nbr_idx, a.nbr_rel, o + g, env_first, t - env.ls, d, pb + env.ls,
+                                  s_vel + env.ls, env.N);
+                }
+                __syncthreads();  // the next step publishes into pb again
+            }
+            act = next;
+        }
+        bool bad = false;
+        if (active) {
+            store_state(a.state, a.n, g, d, is_pid);
+            a.state[5 * a.n + g] = make_float4(rpm[0], rpm[1], rpm[2], rpm[3]);
+            bad = !finite_state(d);
+        }
+        const unsigned bad_mask = __ballot_sync(0xffffffffu, bad);
+        const long long g_bad = __shfl_sync(0xffffffffu, g, bad_mask ? __ffs(bad_mask) - 1 : 0);
+        if (bad_mask && (t & 31) == 0) {
+            atomicOr(a.status, MDG_STATUS_NONFINITE);
+            atomicMin(a.status + 1, (unsigned)g_bad);
+        }
+        __syncthreads();  // s_item and the tables are rewritten for the next item
+    }
+}
+
 __global__ void __launch_bounds__(1024) obs_kernel(const StepArgs a)
 {
     extern __shared__ float4 smem[];
@@ -555,13 +706,14 @@ __global__ void __launch_bounds__(256) pid_kernel(const PidArgs a)
 
 // The step-kernel variants: compile-time physics subset and environment size for the
 // uniform batches of the benchmark workloads, and a runtime-generic one for the rest.
-#define MDG_STEP_VARIANTS(X) X(7, 4) X(7, 64) X(3, 1) X(8, 0)
+#define MDG_STEP_VARIANTS(X) X(7, 4) X(7, 64) X(3, 1) X(8, -1) X(8, 0)
 
 template <bool kObs>
 static void* step_kernel_ptr(int flags, int N, int block)
 {
 #define MDG_PICK(F, NN)                                                                       \
-    if ((F == 8 || flags == F) && (NN == 0 || (N == NN && block <= kSmallBlock)))            \
+    if ((F == 8 || flags == F) &&                                                             \
+        (NN == 0 || (block <= kSmallBlock && (NN == -1 || N == NN))))                         \
         return (void*)step_kernel<kObs, F, NN>;
     MDG_STEP_VARIANTS(MDG_PICK)
 #undef MDG_PICK
@@ -602,6 +754,58 @@ cudaError_t launch_step(const StepArgs& a, int n_tiles, int block, bool with_obs
     void* fn = with_obs ? step_kernel_ptr<true>(flags, N, block) : step_kernel_ptr<false>(flags, N, block);
     void* args[] = {const_cast<StepArgs*>(&a)};
     return cudaLaunchKernel(fn, dim3(n_tiles), dim3(block), args, tile_smem_bytes(block), s);
+}
+
+static size_t rollout_smem_bytes(int B) { return (size_t)B * 48 + (size_t)(3 * B + 2) * 4; }
+
+static void* rollout_kernel_ptr(int flags, int N, int block)
+{
+#define MDG_PICK(F, NN)                                                                       \
+    if ((F == 8 || flags == F) &&                                                             \
+        (NN == 0 || (block <= kSmallBlock && (NN == -1 || N == NN))))                         \
+        return (void*)rollout_kernel<F, NN>;
+    MDG_STEP_VARIANTS(MDG_PICK)
+#undef MDG_PICK
+    return nullptr;
+}
+
+static cudaError_t rollout_setup()
+{
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+    const int smem = (int)rollout_smem_bytes(1024);
+#define MDG_ATTR(F, NN)                                                                                    \
+    if ((e = cudaFuncSetAttribute(rollout_kernel<F, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                                  smem)) != cudaSuccess)                                                   \
+        return e;
+    MDG_STEP_VARIANTS(MDG_ATTR)
+#undef MDG_ATTR
+    if (dev >= 0 && dev < 64) done[dev] = true;
+    return cudaSuccess;
+}
+
+int rollout_blocks_per_sm(int block, int uniform_flags, int uniform_N)
+{
+    if (rollout_setup() != cudaSuccess) return 1;
+    int n = 0;
+    void* fn = rollout_kernel_ptr(uniform_flags, uniform_N, block);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, rollout_smem_bytes(block)) != cudaSuccess || n < 1)
+        return 1;
+    return n;
+}
+
+cudaError_t launch_rollout(const RolloutArgs& r, int block, int uniform_flags, int grid, cudaStream_t s)
+{
+    if (r.n_items == 0 || r.K == 0) return cudaSuccess;
+    cudaError_t e = rollout_setup();
+    if (e != cudaSuccess) return e;
+    void* fn = rollout_kernel_ptr(uniform_flags, r.s.uniform_N, block);
+    if (grid <= 0 || grid > r.n_items) grid = r.n_items;
+    void* args[] = {const_cast<RolloutArgs*>(&r)};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, rollout_smem_bytes(block), s);
 }
 
 cudaError_t launch_obs(const StepArgs& a, int n_tiles, int block, cudaStream_t s)

@@ -101,3 +101,50 @@ def assert_horizon_close(xg, xo, response, n_sub, what=""):
         raise AssertionError(f"{what}: drone {i} component {k}: gpu {xg[i, k]!r} oracle {xo[i, k]!r} "
                              f"bound {bound[i, k]:.3g} (ratio {worst:.3g})")
     return worst
+
+
+def check_obs_against_own_state(dpe, kin, idx, rel, idx_base=None, what=""):
+    """Observations checked against the oracle restarted from the state they describe: KIN
+    carries p, q, v, omega of every drone, so the oracle recomputes roll/pitch/yaw and the
+    4 nearest neighbours from it (indices bit-exact, features within 1e-6, floor 1 cm).
+    idx_base[e] is the global index of env e's first drone (default: CSR offsets)."""
+    kin = np.asarray(kin, dtype=np.float64)
+    idx = np.asarray(idx)
+    rel = np.asarray(rel, dtype=np.float64)
+    env_off = np.concatenate([[0], np.cumsum(dpe)])
+    x = np.concatenate([kin[:, 0:7], kin[:, 10:16]], axis=1)
+    for e in range(len(dpe)):
+        b, N = int(env_off[e]), int(dpe[e])
+        base = b if idx_base is None else int(idx_base[e])
+        for j in range(N):
+            k_ref = oracle.kin(x[b + j], kin[b + j, 16:20])
+            assert excess(kin[b + j, 7:10], k_ref[7:10], 1e-6) <= 1.0, f"{what}: rpy of drone {b + j}"
+            i_ref, r_ref = oracle.knn(x[b:b + N], j, base)
+            np.testing.assert_array_equal(idx[b + j], i_ref, err_msg=f"{what}: neighbours of drone {b + j}")
+            assert excess(rel[b + j], r_ref, 1e-6, floor=1e-2) <= 1.0, f"{what}: features of drone {b + j}"
+
+
+def oracle_horizon(P, dpe, flags, act_types, x0, integ0, a0, actions, n_sub, seed=0):
+    """The oracle's K-step trajectory (actions [K, n, 4]) and, per step, its response to an
+    initial-state error of exactly the per-substep tolerance (see tolerance_response).
+    Returns (states [K, n, 13], responses [K, n, 13])."""
+    env_off = np.concatenate([[0], np.cumsum(dpe)]).astype(np.int32)
+    rng = np.random.default_rng(seed)
+    sgn = rng.choice([-1.0, 1.0], size=x0.shape)
+    x2 = x0.copy()
+    for sl, tol in ((slice(0, 3), RTOL_PV), (slice(7, 10), RTOL_PV), (slice(10, 13), RTOL_W)):
+        x2[:, sl] = x0[:, sl] + sgn[:, sl] * tol * np.maximum(np.abs(x0[:, sl]), 1.0)
+    q = x0[:, 3:7] + sgn[:, 3:7] * ATOL_Q
+    x2[:, 3:7] = q / np.linalg.norm(q, axis=1, keepdims=True)
+    fl = np.asarray(flags, np.int32)
+    at = np.asarray(act_types, np.int32)
+    xa, ia, aa = x0.copy(), integ0.copy(), a0.copy()
+    xb, ib, ab = x2, integ0.copy(), a0.copy()
+    states, resp = [], []
+    for k in range(actions.shape[0]):
+        a_k = np.asarray(actions[k], np.float64)[None]
+        xa, ia, aa = oracle.control_steps(P, env_off, fl, at, xa, ia, aa, a_k, n_sub)
+        xb, ib, ab = oracle.control_steps(P, env_off, fl, at, xb, ib, ab, a_k, n_sub)
+        states.append(xa.copy())
+        resp.append(np.abs(xa - xb))
+    return np.stack(states), np.stack(resp)
