@@ -204,6 +204,164 @@ def run_reference(args) -> None:
     }))
 
 
+# FP32 arithmetic per drone and substep, counted from the oracle's operation list (an FMA
+# counts as 2 flops, a special-function evaluation as 1): the explicit integrator with
+# thrust, gravity, Newton-Euler, exponential map and Euler update; each optional effect;
+# per other drone of the environment the downwash pair test, and per drone above it the
+# pair term. PID and observations are counted per control step.
+FLOPS_BASE, FLOPS_GND, FLOPS_DRAG = 130, 8, 16
+FLOPS_DW_PAIR_TEST, FLOPS_DW_PAIR_TERM = 8, 16
+FLOPS_PID, FLOPS_OBS, FLOPS_OBS_PER_NEIGHBOUR = 150, 60, 8
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock = 80.5
+
+
+def algorithmic_flops(sw, K: int, n_sub: int, obs_steps: int, pid_mask=None) -> float:
+    """Counted FP32 flops of K control steps of a swarm (pairs above: half the others)."""
+    N = sw.drones_per_env.astype(np.float64)
+    f = sw.flags
+    per_sub = FLOPS_BASE + ((f & 1) > 0) * FLOPS_GND + ((f & 2) > 0) * FLOPS_DRAG
+    per_sub = per_sub + ((f & 4) > 0) * ((N - 1) * FLOPS_DW_PAIR_TEST + 0.5 * (N - 1) * FLOPS_DW_PAIR_TERM)
+    pid = np.zeros_like(N) if pid_mask is None else pid_mask.astype(np.float64) * FLOPS_PID
+    per_step = n_sub * per_sub + pid
+    total = np.sum(N * (K * per_step + obs_steps * (FLOPS_OBS + FLOPS_OBS_PER_NEIGHBOUR * (N - 1))))
+    return float(total)
+
+
+def run_other(args) -> None:
+    """The other swarms, on one GPU:
+    uneven  4096 envs of 1..32 drones, mixed physics subsets and RPM/PID actions: one
+            step = one replay of the CUDA graph of a 32-control-step persistent rollout
+            (observations after the last step), block size autotuned; state reset to the
+            initial swarm before every replay (untimed).
+    dense   1024 envs x 64 drones, all effects, RPM actions: one step = one control step
+            (mdg_step_obs), 16 action sets cycled.
+    single  64 envs x 1 drone, ground effect + drag: one step = the 240-control-step
+            episode in one rollout launch (latency-bound; also reported per control step)."""
+    import torch
+    import paper_2606_08039_gb300 as mdg
+    from paper_2606_08039_gb300 import workloads as wl
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    sink = torch.empty(1, dtype=torch.float32, device=dev)
+    c = mdg.Constants.cf2x()
+    hover = c.hover_rpm()
+    extra = {}
+    if args.workload == "uneven":
+        sw, K, obs_steps = wl.uneven(2), 32, 1
+        h = mdg.Handle(sw.drones_per_env, sw.flags)
+        h.set_action_types(sw.act_type)
+        acts = torch.as_tensor(np.stack([wl.mixed_actions(sw, 2, k, hover) for k in range(K)]), device=dev)
+        init = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=dev)
+        state = init.clone()
+        kin, idx, rel = h.new_obs(dev)
+        block, _ = h.autotune(state, acts, mdg.ACT_MIXED, N_SUB, K)
+        graph = h.rollout_graph(state, acts, mdg.ACT_MIXED, N_SUB, K, mdg.OBS_LAST, kin, idx, rel)
+
+        def run():
+            graph.launch(stream)
+        reset = True
+        pid_mask = sw.act_type == mdg.ACT_PID
+        substeps = sw.n * N_SUB * K
+        desc = (f"uneven: 4096 envs, N in {{1,2,4,8,16,32}} ({sw.n} drones), 8 physics subsets, RPM/PID mixed; "
+                f"one step = CUDA-graph replay of a {K}-control-step persistent rollout, obs after the last")
+        launches = 1
+        # the same 32 control steps as 32 single-step launches, for comparison
+        extra_fn = lambda: [h.step_obs(state, acts[k], mdg.ACT_MIXED, N_SUB, kin, idx, rel, stream=stream)
+                            for k in range(K)]
+    elif args.workload == "dense":
+        sw, K, obs_steps = wl.dense(5), 1, 1
+        h = mdg.Handle(sw.drones_per_env, sw.flags)
+        acts = [torch.as_tensor(wl.rpm_actions(5, sw.n, k, hover), device=dev) for k in range(16)]
+        init = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=dev)
+        state = init.clone()
+        kin, idx, rel = h.new_obs(dev)
+        block = h.block_size
+        counter = [0]
+
+        def run():
+            if counter[0] and counter[0] % 500 == 0:  # 500-step episodes
+                state.copy_(init)
+            h.step_obs(state, acts[counter[0] % 16], mdg.ACT_RPM, N_SUB, kin, idx, rel, stream=stream)
+            counter[0] += 1
+        reset = False
+        pid_mask = None
+        substeps = sw.n * N_SUB
+        desc = "dense: 1024 envs x 64 drones, all effects, RPM actions; one step = one control step (mdg_step_obs)"
+        launches = 1
+        extra_fn = None
+    else:
+        sw, K, obs_steps = wl.single(0), 240, 1
+        h = mdg.Handle(sw.drones_per_env, sw.flags)
+        acts = torch.as_tensor(np.stack([wl.rpm_actions(0, sw.n, k, hover) for k in range(K)]), device=dev)
+        init = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=dev)
+        state = init.clone()
+        kin, idx, rel = h.new_obs(dev)
+        block = h.block_size
+
+        def run():
+            h.rollout(state, acts, mdg.ACT_RPM, N_SUB, K, mdg.OBS_LAST, kin, idx, rel, stream=stream)
+        reset = True
+        pid_mask = None
+        substeps = sw.n * N_SUB * K
+        desc = "single: 64 envs x 1 drone, ground effect + drag, RPM actions; one step = the 240-step episode in one rollout"
+        launches = 1
+        extra_fn = None
+
+    def flush_l2():
+        flush.fill_(1.0)
+        torch.sum(flush, dim=0, out=sink)
+
+    def timed(fn, n):
+        st = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+        en = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+        for i in range(n):
+            if reset:
+                state.copy_(init)
+            flush_l2()
+            st[i].record(stream)
+            fn()
+            en[i].record(stream)
+        torch.cuda.synchronize()
+        return float(sum(a.elapsed_time(b) for a, b in zip(st, en)))
+
+    steps = min(args.steps, 2000)
+    timed(run, args.warmup)
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    total_ms = timed(run, steps)
+    clk = clocks.stop()
+    rc, bits, _ = h.status()
+    if extra_fn is not None:
+        timed(extra_fn, 3)
+        per_step_ms = timed(extra_fn, min(steps, 200)) / min(steps, 200)
+        extra["same_work_as_single_step_launches"] = {"value": substeps / (per_step_ms * 1e-3), "ms": per_step_ms,
+                                                      "launches": K}
+    ms = total_ms / steps
+    flops = algorithmic_flops(sw, K, N_SUB, obs_steps, pid_mask)
+    achieved = flops / (ms * 1e-3) / 1e12
+    out = {
+        "metric": METRIC, "value": substeps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "n_drones": sw.n, "control_steps_per_step": K, "n_substeps": N_SUB,
+                   "block_size": block, "l2": "flushed between timed steps (512 MiB written, then read back)"},
+        "gpu_launches": launches * steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "peak_src": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz",
+                     "algorithmic_flops_per_step": flops},
+        "clocks": clk, "nonfinite_during_timing": bool(bits & mdg.STATUS_NONFINITE),
+    }
+    if args.workload == "single":
+        out["us_per_control_step"] = ms * 1e3 / K
+    out.update(extra)
+    print(json.dumps(out))
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -212,11 +370,16 @@ def main() -> None:
     ap.add_argument("--impl", default="mdg", choices=["mdg", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="full_aero", choices=["full_aero", "uneven", "dense", "single"],
+                    help="full_aero (default, the headline line); the others measure the other swarms")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload != "full_aero":
+        run_other(args)
         return
 
     import torch

@@ -150,9 +150,10 @@ __device__ __forceinline__ void pid(Drone& d, const float4 wp, const DevConsts& 
 // (dz > dz_min >= 0, which also excludes j itself) and dxy is within the lateral cut-off;
 // otherwise 0. One reciprocal r = 1/(dz^2 beta^2) yields 1/dz^2 = beta^2 r and
 // 1/beta^2 = dz^2 r; beta^2 is floored at 1e-12. Branch-free, so that unrolled pairs
-// interleave; the select discards the values computed for excluded pairs (including the
-// inf/NaN of dz = 0). Height differences whose dz^2 beta^2 underflows float32
-// (dz below about 1e-18 m) contribute nothing.
+// interleave; the select discards the values of excluded pairs. The reciprocal's argument
+// is floored at 1e-30 so that those values stay finite (no inf * 0). For an included pair
+// (beta^2 near 0.0121 at small dz) the floor binds only below dz ~ 1e-14 m, where the
+// force is already ~1e27 N; there it stays at that value instead of growing as 1/dz^2.
 __device__ __forceinline__ float downwash_pair(const float4 o, float px, float py, float pz, const DevConsts& c)
 {
     const float dz = o.z - pz;
@@ -161,10 +162,29 @@ __device__ __forceinline__ float downwash_pair(const float4 o, float px, float p
     const float beta = fmaf(c.dw_c2, dz, c.dw_c3);
     const float b2 = fmaxf(beta * beta, 1e-12f);
     const float dz2 = dz * dz;
-    const float r = rcp_approx(dz2 * b2);
+    const float r = rcp_approx(fmaxf(dz2 * b2, 1e-30f));
     const float e = ex2_approx(-0.72134752044448170368f * d2 * dz2 * r);  // -0.5 log2(e)
     const float f = c.dw_k * b2 * r * e;
-    return (dz > c.dw_dz_min && d2 < c.dw_max_xy2 && e > 0.f) ? f : 0.f;
+    return (dz > c.dw_dz_min && d2 < c.dw_max_xy2) ? f : 0.f;
+}
+
+// Downwash summed over the N drones of the environment in shared memory. The loop is
+// unrolled and branch-free so that independent pair terms interleave (a per-source warp
+// vote that skips sources below the whole warp measured slower: its branch serialises
+// the pairs).
+template <int kN>
+__device__ __forceinline__ float downwash_sum(const float4* env_pos, int N_rt, float px, float py, float pz,
+                                              const DevConsts& c)
+{
+    float acc = 0.f;
+    if (kN > 0) {
+#pragma unroll((kN > 0 && kN <= 8) ? kN : 8)
+        for (int j = 0; j < kN; ++j) acc += downwash_pair(env_pos[j], px, py, pz, c);
+    } else {
+#pragma unroll 4
+        for (int j = 0; j < N_rt; ++j) acc += downwash_pair(env_pos[j], px, py, pz, c);
+    }
+    return acc;
 }
 
 // One substep: forces of Eq. motor/ground/drag/downwash, Newton-Euler, forward Euler
@@ -213,18 +233,7 @@ __device__ __forceinline__ void substep(Drone& d, const Motor& m, int flags_rt, 
         F[1] += kxy * d.v[1] + kr * r1;
         F[2] += kxy * d.v[2] + kr * r2;
     }
-    if (flags & MDG_DW) {
-        const float px = d.p[0], py = d.p[1], pz = d.p[2];
-        float acc = 0.f;
-        if (kN > 0) {
-#pragma unroll((kN > 0 && kN <= 8) ? kN : 8)
-            for (int j = 0; j < kN; ++j) acc += downwash_pair(env_pos[j], px, py, pz, c);
-        } else {
-#pragma unroll 4
-            for (int j = 0; j < N_rt; ++j) acc += downwash_pair(env_pos[j], px, py, pz, c);
-        }
-        F[2] -= acc;
-    }
+    if (flags & MDG_DW) F[2] -= downwash_sum<kN>(env_pos, N_rt, d.p[0], d.p[1], d.p[2], c);
     // Newton-Euler: omega_dot = J^-1 (tau - omega x (J omega)), omega in the body frame
     const float Jw0 = c.J[0] * d.w[0], Jw1 = c.J[1] * d.w[1], Jw2 = c.J[2] * d.w[2];
     const float wd0 = c.inv_J[0] * (m.tau[0] - (d.w[1] * Jw2 - d.w[2] * Jw1));
