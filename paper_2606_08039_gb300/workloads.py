@@ -212,6 +212,20 @@ def mixed_actions(swarm: Swarm, seed: int, step: int, hover_rpm: float) -> np.nd
     return a
 
 
+S_MLP = 9
+
+
+def mlp_init(seed: int, dims=(64, 256, 256, 256, 16)):
+    """Initial surrogate weights: W_l ~ U[-b, b] with b = sqrt(6 / fan_in) (He uniform), b_l = 0;
+    float32 arrays [(W [out, in], b [out]), ...], drawn counter-based per (layer, row, col)."""
+    out = []
+    for l, (fi, fo) in enumerate(zip(dims[:-1], dims[1:])):
+        bound = math.sqrt(6.0 / fi)
+        u = uniform(seed, S_MLP, l, np.arange(fo, dtype=np.uint64)[:, None], np.arange(fi, dtype=np.uint64)[None, :])
+        out.append(((bound * (2.0 * u.astype(np.float64) - 1.0)).astype(np.float32), np.zeros(fo, np.float32)))
+    return out
+
+
 def random_states(seed: int, n: int, pos_scale=1.0, vel_scale=1.0, rate_scale=3.0, z0=1.0):
     """Generic tumbling states for parity tests: p around (0, 0, z0), any attitude, nonzero
     velocity and body rate. Returns (p, q, v, w) float32."""

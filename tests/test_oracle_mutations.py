@@ -49,6 +49,16 @@ MUTATIONS = {
 }
 
 
+# planted in oracle/mlp.py, caught by tests/test_oracle_mlp.py
+MLP_MUTATIONS = {
+    "silu_grad_sign": ("return s * (1.0 + z * (1.0 - s))", "return s * (1.0 - z * (1.0 - s))"),
+    "mse_grad_factor": ("dz = q(2.0 * (y - t) / y.size)", "dz = q((y - t) / y.size)"),
+    "adam_bias_correction": ("c1, c2 = 1.0 - b1 ** step, 1.0 - b2 ** step", "c1, c2 = 1.0, 1.0 - b2 ** step"),
+    "backprop_through_weights": ("dz = q((dz @ Wl) * silu_grad(zs[l - 1]))", "dz = q((dz @ Wl) * silu(zs[l - 1]))"),
+    "bf16_tie_rounding": ("rounded = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16", "rounded = ((u + 0x8000) >> 16) << 16"),
+}
+
+
 @pytest.fixture(scope="module")
 def oracle_source():
     with open(os.path.join(ROOT, "oracle", "mdg_oracle.c")) as f:
@@ -64,5 +74,19 @@ def test_planted_mistake_is_caught(name, oracle_source, tmp_path):
                     ignore=shutil.ignore_patterns("__pycache__", "test_oracle_mutations.py"))
     (tmp_path / "oracle" / "mdg_oracle.c").write_text(oracle_source.replace(before, after))
     r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_dynamics.py", "-q", "-x",
+                        "-p", "no:cacheprovider"], cwd=tmp_path, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 1, f"planted mistake {name} was not caught:\n{r.stdout[-2000:]}"
+
+
+@pytest.mark.parametrize("name", sorted(MLP_MUTATIONS))
+def test_planted_mlp_mistake_is_caught(name, tmp_path):
+    before, after = MLP_MUTATIONS[name]
+    src = open(os.path.join(ROOT, "oracle", "mlp.py")).read()
+    assert src.count(before) == 1, f"mutation site of {name} not found exactly once"
+    shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle", ignore=shutil.ignore_patterns("_build"))
+    shutil.copytree(os.path.join(ROOT, "tests"), tmp_path / "tests",
+                    ignore=shutil.ignore_patterns("__pycache__", "test_oracle_mutations.py"))
+    (tmp_path / "oracle" / "mlp.py").write_text(src.replace(before, after))
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_mlp.py", "-q", "-x",
                         "-p", "no:cacheprovider"], cwd=tmp_path, capture_output=True, text=True, timeout=300)
     assert r.returncode == 1, f"planted mistake {name} was not caught:\n{r.stdout[-2000:]}"
