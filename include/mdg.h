@@ -273,6 +273,65 @@ int mdg_step_obs_noalloc(const mdg_constants* c, int32_t n_envs, const int32_t* 
                          int32_t action_type, int32_t n_substeps, float* kin, int32_t* nbr_idx, float* nbr_rel,
                          uint32_t* status_out, void* stream);
 
+/* ---- learned surrogate (not in the paper) ----
+ * A multilayer perceptron stands in for the substep loop of one control step: from a
+ * drone's 13-d state (p, q, v, w), its four RPMs and its 4 nearest neighbours' relative
+ * positions and velocities (41 inputs) it predicts the 13-d state change over the control
+ * step. 41 -> 256 -> 256 -> 256 -> 13, SiLU hidden activations, bfloat16 weights and
+ * activations with FP32 accumulation on the tensor cores, trained with Adam on MSE of
+ * standardised targets. Stored padded: 64 inputs, 32 outputs (zeros beyond 41 / 13).
+ * Flat FP32 parameter layout (MDG_MLP_PARAMS floats): W1 [256][64], b1 [256],
+ * W2 [256][256], b2, W3 [256][256], b3, W4 [32][256], b4 [32]. */
+#define MDG_MLP_IN 41
+#define MDG_MLP_IN_PAD 64
+#define MDG_MLP_HIDDEN 256
+#define MDG_MLP_OUT 13
+#define MDG_MLP_OUT_PAD 32
+#define MDG_MLP_PARAMS 156448
+
+typedef struct mdg_mlp_s* mdg_mlp;
+
+/* Create a surrogate on the current device with scratch for batches of up to max_batch
+ * rows (a positive multiple of 128). init: host FP32 [MDG_MLP_PARAMS] or NULL (zeros). */
+int mdg_mlp_create(int32_t max_batch, const float* init, mdg_mlp* out);
+int mdg_mlp_destroy(mdg_mlp m);
+/* Copy the FP32 master parameters (or the last computed gradients) to/from the host
+ * (flat layout above; synchronous). */
+int mdg_mlp_get_params(mdg_mlp m, float* host_out);
+int mdg_mlp_set_params(mdg_mlp m, const float* host_in);
+int mdg_mlp_get_grads(mdg_mlp m, float* host_out);
+/* Input standardisation (41 means and standard deviations), output de-standardisation
+ * (13), and the out-of-distribution box of the raw inputs (41 lower and upper bounds);
+ * host arrays, copied. */
+int mdg_mlp_set_normalization(mdg_mlp m, const float* in_mean, const float* in_std, const float* out_mean,
+                              const float* out_std, const float* in_lo, const float* in_hi);
+/* x = bf16((raw - mean) / std), raw device [rows][41] FP32, x device [rows][64] bf16 (uint16). */
+int mdg_mlp_standardize(mdg_mlp m, const float* raw, uint16_t* x, int64_t rows, void* stream);
+/* Forward pass: x device [B][64] bf16, y device [B][32] FP32 (standardised outputs);
+ * B a multiple of 128, at most max_batch. */
+int mdg_mlp_forward(mdg_mlp m, const uint16_t* x, float* y, int32_t B, void* stream);
+/* Gradient of the MSE between the forward output and the standardised targets
+ * t device [B][32] (columns 13..31 ignored) into the surrogate's gradient buffer;
+ * loss_out: device float or NULL (receives the loss). */
+int mdg_mlp_grad(mdg_mlp m, const uint16_t* x, const float* t, int32_t B, float* loss_out, void* stream);
+/* One Adam step (b1 0.9, b2 0.999, eps 1e-8) with the gradient of the last mdg_mlp_grad. */
+int mdg_mlp_adam(mdg_mlp m, float lr, void* stream);
+
+/* Raw surrogate inputs of the current state: raw device [n_drones][41] =
+ * [p, q, v, w, rpm (4), 4 nearest neighbours' (p_i - p_j, v_i - v_j)]; rpm device
+ * [n_drones][4] are the RPMs to be applied. */
+int mdg_features(mdg_handle h, const float* state, const float* rpm, float* raw, void* stream);
+
+/* One control step with the surrogate in place of the substep loop (uniform batches of
+ * at most 32 drones per environment, n_drones <= the surrogate's max_batch): the action
+ * becomes RPMs as in mdg_step (PID integrals and plane 5 updated), the inputs are
+ * standardised, the network predicts the state change, q is renormalised. An environment
+ * any of whose drones has a standardised input beyond +-ood_z or a raw input outside the
+ * normalisation box takes the plain integrator instead (n_substeps substeps).
+ * n_fallback: device int32 or NULL, receives the number of such environments. */
+int mdg_surrogate_step(mdg_handle h, mdg_mlp m, float* state, const float* action, int32_t action_type,
+                       int32_t n_substeps, float ood_z, int32_t* n_fallback, void* stream);
+
 /* Message of the last error on this host thread ("" if none). */
 const char* mdg_last_error(void);
 

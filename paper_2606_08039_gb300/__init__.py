@@ -31,6 +31,9 @@ MAX_ENV_DRONES = 1024
 
 OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_UNSUPPORTED = 0, -1, -2, -3, -4
 OBS_NONE, OBS_LAST, OBS_EVERY_STEP = 0, 1, 2
+MLP_IN, MLP_IN_PAD, MLP_HIDDEN, MLP_OUT, MLP_OUT_PAD = 41, 64, 256, 13, 32
+MLP_DIMS = (MLP_IN_PAD, MLP_HIDDEN, MLP_HIDDEN, MLP_HIDDEN, MLP_OUT_PAD)
+MLP_PARAMS = 156448
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libmdg.so")
@@ -62,6 +65,19 @@ _SIGNATURES = {
     "mdg_graph_destroy": ([_VP], ctypes.c_int),
     "mdg_autotune": ([_VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP,
                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+    "mdg_mlp_create": ([ctypes.c_int32, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
+    "mdg_mlp_destroy": ([_VP], ctypes.c_int),
+    "mdg_mlp_get_params": ([_VP, _VP], ctypes.c_int),
+    "mdg_mlp_set_params": ([_VP, _VP], ctypes.c_int),
+    "mdg_mlp_get_grads": ([_VP, _VP], ctypes.c_int),
+    "mdg_mlp_set_normalization": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "mdg_mlp_standardize": ([_VP, _VP, _VP, ctypes.c_int64, _VP], ctypes.c_int),
+    "mdg_mlp_forward": ([_VP, _VP, _VP, ctypes.c_int32, _VP], ctypes.c_int),
+    "mdg_mlp_grad": ([_VP, _VP, _VP, ctypes.c_int32, _VP, _VP], ctypes.c_int),
+    "mdg_mlp_adam": ([_VP, ctypes.c_float, _VP], ctypes.c_int),
+    "mdg_features": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "mdg_surrogate_step": ([_VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, _VP, _VP],
+                           ctypes.c_int),
     "mdg_step_obs_noalloc": ([_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP,
                               _VP, _VP, _VP], ctypes.c_int),
 }
@@ -347,9 +363,116 @@ class Handle:
                                   int(n_substeps), int(K), _stream(stream), ctypes.byref(best), ctypes.byref(ms)))
         return best.value, ms.value
 
+    def features(self, state, rpm, raw, stream=None):
+        """Raw surrogate inputs [n, 41] of the current state with the given RPMs (mdg_features)."""
+        torch = _torch()
+        _check(lib().mdg_features(self._h, _ptr(state, "state", torch.float32, (STATE_PLANES, self.n, 4)),
+                                  _ptr(rpm, "rpm", torch.float32, (self.n, 4)),
+                                  _ptr(raw, "raw", torch.float32, (self.n, MLP_IN)), _stream(stream)))
+
     # -- output buffers
     def new_obs(self, device="cuda"):
         torch = _torch()
         return (torch.empty((self.n, KIN_DIM), dtype=torch.float32, device=device),
                 torch.empty((self.n, NBR_K), dtype=torch.int32, device=device),
                 torch.empty((self.n, NBR_K * NBR_FEAT), dtype=torch.float32, device=device))
+
+
+# ---------------------------------------------------------------- learned surrogate
+def mlp_flatten(layers) -> np.ndarray:
+    """[(W [out, in], b [out]), ...] (padded shapes of MLP_DIMS) -> flat float32 parameters."""
+    parts = []
+    for W, b in layers:
+        parts += [np.asarray(W, np.float32).reshape(-1), np.asarray(b, np.float32).reshape(-1)]
+    flat = np.concatenate(parts)
+    if flat.size != MLP_PARAMS:
+        raise ValueError(f"expected {MLP_PARAMS} parameters, got {flat.size}")
+    return flat
+
+
+def mlp_unflatten(flat):
+    """Flat parameters -> [(W [out, in], b [out]), ...]."""
+    flat = np.asarray(flat)
+    out, off = [], 0
+    for fi, fo in zip(MLP_DIMS[:-1], MLP_DIMS[1:]):
+        W = flat[off:off + fi * fo].reshape(fo, fi)
+        off += fi * fo
+        b = flat[off:off + fo]
+        off += fo
+        out.append((W, b))
+    return out
+
+
+class MLP:
+    """The surrogate network (mdg_mlp): FP32 master parameters, bf16 copies, Adam state and
+    scratch for batches of up to max_batch rows (a multiple of 128)."""
+
+    def __init__(self, max_batch: int, init=None):
+        flat = None if init is None else np.ascontiguousarray(
+            mlp_flatten(init) if isinstance(init, (list, tuple)) else init, np.float32)
+        self._m = ctypes.c_void_p()
+        _check(lib().mdg_mlp_create(int(max_batch), None if flat is None else flat.ctypes.data_as(_VP),
+                                    ctypes.byref(self._m)))
+        self.max_batch = int(max_batch)
+
+    def close(self):
+        if self._m:
+            lib().mdg_mlp_destroy(self._m)
+            self._m = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        out = np.empty(MLP_PARAMS, np.float32)
+        _check(lib().mdg_mlp_get_params(self._m, out.ctypes.data_as(_VP)))
+        return out
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, np.float32)
+        _check(lib().mdg_mlp_set_params(self._m, flat.ctypes.data_as(_VP)))
+
+    def grads(self) -> np.ndarray:
+        out = np.empty(MLP_PARAMS, np.float32)
+        _check(lib().mdg_mlp_get_grads(self._m, out.ctypes.data_as(_VP)))
+        return out
+
+    def set_normalization(self, in_mean, in_std, out_mean, out_std, in_lo, in_hi):
+        arrs = [np.ascontiguousarray(a, np.float32) for a in (in_mean, in_std, out_mean, out_std, in_lo, in_hi)]
+        _check(lib().mdg_mlp_set_normalization(self._m, *[a.ctypes.data_as(_VP) for a in arrs]))
+
+    def standardize(self, raw, x, stream=None):
+        torch = _torch()
+        rows = raw.shape[0]
+        _check(lib().mdg_mlp_standardize(self._m, _ptr(raw, "raw", torch.float32, (rows, MLP_IN)),
+                                         _ptr(x, "x", torch.bfloat16, (rows, MLP_IN_PAD)), int(rows),
+                                         _stream(stream)))
+
+    def forward(self, x, y, stream=None):
+        torch = _torch()
+        B = x.shape[0]
+        _check(lib().mdg_mlp_forward(self._m, _ptr(x, "x", torch.bfloat16, (B, MLP_IN_PAD)),
+                                     _ptr(y, "y", torch.float32, (B, MLP_OUT_PAD)), int(B), _stream(stream)))
+
+    def grad(self, x, t, loss=None, stream=None):
+        torch = _torch()
+        B = x.shape[0]
+        _check(lib().mdg_mlp_grad(self._m, _ptr(x, "x", torch.bfloat16, (B, MLP_IN_PAD)),
+                                  _ptr(t, "t", torch.float32, (B, MLP_OUT_PAD)), int(B),
+                                  _ptr(loss, "loss", torch.float32, (1,)), _stream(stream)))
+
+    def adam(self, lr: float, stream=None):
+        _check(lib().mdg_mlp_adam(self._m, ctypes.c_float(lr), _stream(stream)))
+
+    def step(self, handle: "Handle", state, action, action_type: int, n_substeps: int = 5, ood_z: float = 4.0,
+             n_fallback=None, stream=None):
+        """One control step with the surrogate (mdg_surrogate_step)."""
+        torch = _torch()
+        _check(lib().mdg_surrogate_step(handle._h, self._m,
+                                        _ptr(state, "state", torch.float32, (STATE_PLANES, handle.n, 4)),
+                                        _ptr(action, "action", torch.float32, (handle.n, 4)), int(action_type),
+                                        int(n_substeps), ctypes.c_float(ood_z),
+                                        _ptr(n_fallback, "n_fallback", torch.int32, (1,)), _stream(stream)))

@@ -56,37 +56,8 @@ struct DeviceGuard {
 
 }  // namespace
 
-struct mdg_ctx {
-    int device = 0;
-    int32_t n_envs = 0;
-    int64_t n_drones = 0;
-    int32_t max_env = 0;
-    mdg_constants c{};
-    mdg::DevConsts dc{};
-    std::vector<int32_t> h_off;
-    std::vector<uint8_t> h_flags;
-    int32_t* d_off = nullptr;
-    uint8_t* d_flags = nullptr;
-    uint8_t* d_act = nullptr;
-    bool act_set = false;
-    mdg::Tile* d_tiles = nullptr;
-    int n_tiles = 0;
-    int block = 0;
-    int uniform_N = 0;      // every environment has this many drones (0: mixed sizes)
-    int envs_per_tile = 0;
-    int uniform_bits = 0;
-    int uniform_flags = -1;  // physics subset shared by every environment, -1 if they differ
-    uint32_t* d_status = nullptr;
-    // rollout work items, built on first use for the current block size
-    int rollout_block = 0;
-    int n_items = 0;
-    int4* d_items = nullptr;
-    int* d_item_order = nullptr;
-    int* d_slot_env = nullptr;
-    int* d_slot_goff = nullptr;
-    int* d_slot_loff = nullptr;
-    int* d_counter = nullptr;
-};
+
+// (struct mdg_ctx is defined in mdg_internal.cuh)
 
 // Table and constant builders shared by the handle API and the allocation-free entry point.
 namespace mdg {

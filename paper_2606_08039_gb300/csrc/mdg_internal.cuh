@@ -78,6 +78,32 @@ struct RolloutArgs {
     const int* slot_loff;
 };
 
+// The surrogate's parameters as the kernels see them.
+struct MlpView {
+    float* master;   // FP32 flat parameters
+    void* w16;       // bf16 copies (same offsets; bias slots unused)
+    int w_off[4], b_off[4];
+};
+
+// Per-control-step surrogate kernels (uniform batches).
+struct SurrogateArgs {
+    StepArgs s;                  // state, action, tables, constants
+    void* x;                     // [n_pad][64] bf16 standardised inputs
+    const float* y;              // [n_pad][32] standardised outputs of the network
+    const float* in_mean;        // [41]
+    const float* in_inv_std;     // [41]
+    const float* in_lo;          // [41]
+    const float* in_hi;          // [41]
+    const float* out_mean;       // [13]
+    const float* out_std;        // [13]
+    float ood_z;
+    unsigned* env_flag;          // [n_envs], zeroed before prepare
+    int* fallback_list;          // [n_envs]
+    int* fallback_count;         // [1], zeroed before prepare
+    float* raw;                  // features only: [n][41]
+    const float4* rpm;           // features only: [n]
+};
+
 struct PidArgs {
     float4* state;
     const float4* waypoints;
@@ -100,7 +126,55 @@ cudaError_t launch_step(const StepArgs& a, int n_tiles, int block, bool with_obs
 // grid: persistent CTAs (0: one per work item)
 cudaError_t launch_rollout(const RolloutArgs& a, int block, int uniform_flags, int grid, cudaStream_t s);
 int rollout_blocks_per_sm(int block, int uniform_flags, int uniform_N);
+cudaError_t launch_features(const SurrogateArgs& a, int n_tiles, int block, cudaStream_t s);
+cudaError_t launch_surrogate_prepare(const SurrogateArgs& a, int n_tiles, int block, cudaStream_t s);
+cudaError_t launch_surrogate_apply(const SurrogateArgs& a, cudaStream_t s);
+cudaError_t launch_surrogate_fallback(const SurrogateArgs& a, cudaStream_t s);
+
+// mdg_mlp.cu
+cudaError_t mlp_forward(const MlpView& w, const void* x, int B, float* z_hidden[3], void* h_hidden[3], float* y,
+                        const float* target, void* dy, float* loss_acc, cudaStream_t s);
+cudaError_t mlp_backward(const MlpView& w, const void* x, int B, float* const z_hidden[3], void* const h_hidden[3],
+                         void* dy, void* dz_hidden[3], float* grad, cudaStream_t s);
+cudaError_t mlp_adam(const MlpView& w, const float* grad, float* m, float* v, float lr, int step, cudaStream_t s);
+cudaError_t mlp_refresh_bf16(const MlpView& w, cudaStream_t s);
+cudaError_t mlp_standardize(const float* raw, void* x, long long rows, const float* mean, const float* inv_std,
+                            cudaStream_t s);
+
 cudaError_t launch_obs(const StepArgs& a, int n_tiles, int block, cudaStream_t s);
 cudaError_t launch_pid(const PidArgs& a, cudaStream_t s);
 
 }  // namespace mdg
+
+// The handle behind mdg_handle (host side).
+struct mdg_ctx {
+    int device = 0;
+    int32_t n_envs = 0;
+    int64_t n_drones = 0;
+    int32_t max_env = 0;
+    mdg_constants c{};
+    mdg::DevConsts dc{};
+    std::vector<int32_t> h_off;
+    std::vector<uint8_t> h_flags;
+    int32_t* d_off = nullptr;
+    uint8_t* d_flags = nullptr;
+    uint8_t* d_act = nullptr;
+    bool act_set = false;
+    mdg::Tile* d_tiles = nullptr;
+    int n_tiles = 0;
+    int block = 0;
+    int uniform_N = 0;      // every environment has this many drones (0: mixed sizes)
+    int envs_per_tile = 0;
+    int uniform_bits = 0;
+    int uniform_flags = -1;  // physics subset shared by every environment, -1 if they differ
+    uint32_t* d_status = nullptr;
+    // rollout work items, built on first use for the current block size
+    int rollout_block = 0;
+    int n_items = 0;
+    int4* d_items = nullptr;
+    int* d_item_order = nullptr;
+    int* d_slot_env = nullptr;
+    int* d_slot_goff = nullptr;
+    int* d_slot_loff = nullptr;
+    int* d_counter = nullptr;
+};

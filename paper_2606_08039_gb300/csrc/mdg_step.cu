@@ -8,6 +8,7 @@
 // start-of-substep snapshot visible, and each drone sums the wake of the drones of its
 // own environment from shared memory. State moves between HBM and registers once per
 // control step, as coalesced float4 planes.
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include "mdg.h"
@@ -290,19 +291,18 @@ __device__ __forceinline__ void write_kin(float* __restrict__ kin, long long g, 
 
 // The 4 nearest other drones of the environment (squared distance rounded in the
 // order ((dx*dx + dy*dy) + dz*dz) without contraction, ties to the lower index), from the
-// shared-memory positions/velocities of the environment. Candidates are taken in index
-// order; each enters the last slot if strictly closer and moves up past strictly farther
-// entries (branch-free selects), which keeps equal distances in index order.
+// shared-memory positions of the environment; local indices, -1 where fewer exist.
+// Candidates are taken in index order; each enters the last slot if strictly closer and
+// moves up past strictly farther entries (branch-free selects), which keeps equal
+// distances in index order.
 template <int kN>
-__device__ __forceinline__ void write_knn(int4* __restrict__ nbr_idx, float* __restrict__ nbr_rel, long long g,
-                                          long long env_first, int j, const Drone& d, const float4* env_pos,
-                                          const float4* env_vel, int N_rt)
+__device__ __forceinline__ void knn_best4(int j, const float p[3], const float4* env_pos, int N_rt, int bi[4])
 {
     float b0 = INFINITY, b1 = INFINITY, b2 = INFINITY, b3 = INFINITY;
     int i0 = -1, i1 = -1, i2 = -1, i3 = -1;
     auto consider = [&](int k) {
         const float4 o = env_pos[k];
-        const float dx = __fsub_rn(o.x, d.p[0]), dy = __fsub_rn(o.y, d.p[1]), dz = __fsub_rn(o.z, d.p[2]);
+        const float dx = __fsub_rn(o.x, p[0]), dy = __fsub_rn(o.y, p[1]), dz = __fsub_rn(o.z, p[2]);
         float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
         d2 = (k == j) ? INFINITY : d2;
         bool c = d2 < b3;
@@ -320,27 +320,44 @@ __device__ __forceinline__ void write_knn(int4* __restrict__ nbr_idx, float* __r
     } else {
         for (int k = 0; k < N_rt; ++k) consider(k);
     }
-    const int bi[4] = {i0, i1, i2, i3};
+    bi[0] = i0; bi[1] = i1; bi[2] = i2; bi[3] = i3;
+}
+
+// Relative features [p_i - p_j, v_i - v_j] of the 4 slots (zeros for empty slots).
+__device__ __forceinline__ void knn_features(const int bi[4], const Drone& d, const float4* env_pos,
+                                             const float4* env_vel, float f[24])
+{
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const bool ok = bi[s] >= 0;
+        const float4 pp = env_pos[ok ? bi[s] : 0], vv = env_vel[ok ? bi[s] : 0];
+        f[6 * s + 0] = ok ? pp.x - d.p[0] : 0.f;
+        f[6 * s + 1] = ok ? pp.y - d.p[1] : 0.f;
+        f[6 * s + 2] = ok ? pp.z - d.p[2] : 0.f;
+        f[6 * s + 3] = ok ? vv.x - d.v[0] : 0.f;
+        f[6 * s + 4] = ok ? vv.y - d.v[1] : 0.f;
+        f[6 * s + 5] = ok ? vv.z - d.v[2] : 0.f;
+    }
+}
+
+// Writes the neighbour observation of drone g: global indices and (optionally) features.
+template <int kN>
+__device__ __forceinline__ void write_knn(int4* __restrict__ nbr_idx, float* __restrict__ nbr_rel, long long g,
+                                          long long env_first, int j, const Drone& d, const float4* env_pos,
+                                          const float4* env_vel, int N_rt)
+{
+    int bi[4];
+    knn_best4<kN>(j, d.p, env_pos, N_rt, bi);
     int4 idx;
-    idx.x = i0 >= 0 ? (int)(env_first + i0) : -1;
-    idx.y = i1 >= 0 ? (int)(env_first + i1) : -1;
-    idx.z = i2 >= 0 ? (int)(env_first + i2) : -1;
-    idx.w = i3 >= 0 ? (int)(env_first + i3) : -1;
+    idx.x = bi[0] >= 0 ? (int)(env_first + bi[0]) : -1;
+    idx.y = bi[1] >= 0 ? (int)(env_first + bi[1]) : -1;
+    idx.z = bi[2] >= 0 ? (int)(env_first + bi[2]) : -1;
+    idx.w = bi[3] >= 0 ? (int)(env_first + bi[3]) : -1;
     nbr_idx[g] = idx;
     if (nbr_rel) {
-        float4* o = reinterpret_cast<float4*>(nbr_rel + 24 * g);
         float f[24];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            const bool ok = bi[s] >= 0;
-            const float4 pp = env_pos[ok ? bi[s] : 0], vv = env_vel[ok ? bi[s] : 0];
-            f[6 * s + 0] = ok ? pp.x - d.p[0] : 0.f;
-            f[6 * s + 1] = ok ? pp.y - d.p[1] : 0.f;
-            f[6 * s + 2] = ok ? pp.z - d.p[2] : 0.f;
-            f[6 * s + 3] = ok ? vv.x - d.v[0] : 0.f;
-            f[6 * s + 4] = ok ? vv.y - d.v[1] : 0.f;
-            f[6 * s + 5] = ok ? vv.z - d.v[2] : 0.f;
-        }
+        knn_features(bi, d, env_pos, env_vel, f);
+        float4* o = reinterpret_cast<float4*>(nbr_rel + 24 * g);
 #pragma unroll
         for (int k = 0; k < 6; ++k) o[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
     }
@@ -691,6 +708,211 @@ __global__ void __launch_bounds__(1024) obs_kernel(const StepArgs a)
     }
 }
 
+// ---- learned surrogate: inputs, prepare / apply around the network, fallback ----
+
+// The 41 raw inputs of drone g: [p, q, v, w, rpm, 4 neighbours' (dp, dv)].
+__device__ __forceinline__ void surrogate_inputs(const Drone& d, const float rpm[4], const float f[24], float x[41])
+{
+    x[0] = d.p[0]; x[1] = d.p[1]; x[2] = d.p[2];
+    x[3] = d.q[0]; x[4] = d.q[1]; x[5] = d.q[2]; x[6] = d.q[3];
+    x[7] = d.v[0]; x[8] = d.v[1]; x[9] = d.v[2];
+    x[10] = d.w[0]; x[11] = d.w[1]; x[12] = d.w[2];
+    x[13] = rpm[0]; x[14] = rpm[1]; x[15] = rpm[2]; x[16] = rpm[3];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) x[17 + k] = f[k];
+}
+
+// Raw inputs of the current state with given RPMs (training data).
+__global__ void __launch_bounds__(1024) features_kernel(const SurrogateArgs sa)
+{
+    extern __shared__ float4 smem[];
+    const StepArgs& a = sa.s;
+    const int B = blockDim.x;
+    float4* s_pos = smem;
+    float4* s_vel = smem + 2 * B;
+    int* s_off = reinterpret_cast<int*>(smem + 3 * B);
+    int* s_info = s_off + B + 1;
+    const TileInfo tile = get_tile(a);
+    const int t = threadIdx.x;
+    const bool active = t < tile.n_drones;
+    const long long g = tile.first_drone + t;
+    Drone d = {};
+    float4 r4 = {};
+    if (active) {
+        load_state(a.state, a.n, g, d, false);
+        r4 = sa.rpm[g];
+    }
+    const EnvSlot env = tile_env(a, tile, s_off, s_info);
+    s_pos[t] = make_float4(d.p[0], d.p[1], d.p[2], 0.f);
+    s_vel[t] = make_float4(d.v[0], d.v[1], d.v[2], 0.f);
+    __syncthreads();
+    if (active) {
+        int bi[4];
+        float f[24], x[41];
+        knn_best4<0>(t - env.ls, d.p, s_pos + env.ls, env.N, bi);
+        knn_features(bi, d, s_pos + env.ls, s_vel + env.ls, f);
+        const float rpm[4] = {r4.x, r4.y, r4.z, r4.w};
+        surrogate_inputs(d, rpm, f, x);
+        float* o = sa.raw + 41 * g;
+#pragma unroll
+        for (int k = 0; k < 41; ++k) o[k] = x[k];
+    }
+}
+
+// Before the network: action -> RPMs (PID state and plane 5 updated), standardised
+// inputs (bf16, zero padded to 64), and the out-of-distribution test of each drone; an
+// environment with any such drone is flagged once and listed for the fallback.
+__global__ void __launch_bounds__(1024) surrogate_prepare_kernel(const SurrogateArgs sa)
+{
+    extern __shared__ float4 smem[];
+    const StepArgs& a = sa.s;
+    const int B = blockDim.x;
+    float4* s_pos = smem;
+    float4* s_vel = smem + 2 * B;
+    int* s_off = reinterpret_cast<int*>(smem + 3 * B);
+    int* s_info = s_off + B + 1;
+    const TileInfo tile = get_tile(a);
+    const int t = threadIdx.x;
+    const bool active = t < tile.n_drones;
+    const long long g = tile.first_drone + t;
+    float4 s0 = {}, s1 = {}, s2 = {}, s3 = {}, s4 = {}, act = {};
+    if (active) {
+        s0 = a.state[g];
+        s1 = a.state[a.n + g];
+        s2 = a.state[2 * a.n + g];
+        s3 = a.state[3 * a.n + g];
+        if (a.act_type != MDG_ACT_RPM) s4 = a.state[4 * a.n + g];
+        act = a.action[g];
+    }
+    const EnvSlot env = tile_env(a, tile, s_off, s_info);
+    const bool is_pid = env.act == MDG_ACT_PID;
+    Drone d;
+    unpack_state(s0, s1, s2, s3, s4, d);
+    float rpm[4] = {0.f, 0.f, 0.f, 0.f};
+    if (active) {
+        if (is_pid) {
+            float ep[3], ye;
+            pid(d, act, a.c, rpm, ep, ye);
+            a.state[3 * a.n + g] = make_float4(d.w[2], d.ip[0], d.ip[1], d.ip[2]);
+            a.state[4 * a.n + g] = make_float4(d.ia[0], d.ia[1], d.ia[2], 0.f);
+        } else {
+            rpm[0] = fminf(a.c.max_rpm, fmaxf(0.f, act.x));
+            rpm[1] = fminf(a.c.max_rpm, fmaxf(0.f, act.y));
+            rpm[2] = fminf(a.c.max_rpm, fmaxf(0.f, act.z));
+            rpm[3] = fminf(a.c.max_rpm, fmaxf(0.f, act.w));
+        }
+        a.state[5 * a.n + g] = make_float4(rpm[0], rpm[1], rpm[2], rpm[3]);
+    }
+    s_pos[t] = make_float4(d.p[0], d.p[1], d.p[2], 0.f);
+    s_vel[t] = make_float4(d.v[0], d.v[1], d.v[2], 0.f);
+    __syncthreads();
+    bool ood = false;
+    if (active) {
+        int bi[4];
+        float f[24], x[41];
+        knn_best4<0>(t - env.ls, d.p, s_pos + env.ls, env.N, bi);
+        knn_features(bi, d, s_pos + env.ls, s_vel + env.ls, f);
+        surrogate_inputs(d, rpm, f, x);
+        __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(sa.x) + 64 * g);
+#pragma unroll
+        for (int k = 0; k < 64; k += 2) {
+            float z0 = 0.f, z1 = 0.f;
+            if (k < 41) {
+                z0 = (x[k] - sa.in_mean[k]) * sa.in_inv_std[k];
+                ood = ood || !(fabsf(z0) <= sa.ood_z) || !(x[k] >= sa.in_lo[k] && x[k] <= sa.in_hi[k]);
+            }
+            if (k + 1 < 41) {
+                z1 = (x[k + 1] - sa.in_mean[k + 1]) * sa.in_inv_std[k + 1];
+                ood = ood || !(fabsf(z1) <= sa.ood_z) || !(x[k + 1] >= sa.in_lo[k + 1] && x[k + 1] <= sa.in_hi[k + 1]);
+            }
+            o[k / 2] = __floats2bfloat162_rn(z0, z1);
+        }
+        if (ood) {
+            const int e = (int)((tile.first_drone + env.ls) / env.N);  // uniform batches
+            if (atomicOr(&sa.env_flag[e], 1u) == 0u) sa.fallback_list[atomicAdd(sa.fallback_count, 1)] = e;
+        }
+    }
+}
+
+// After the network: state += de-standardised prediction (q renormalised) for every drone
+// whose environment is not flagged. Uniform batches: environment of drone g is g / N.
+__global__ void __launch_bounds__(256) surrogate_apply_kernel(const SurrogateArgs sa)
+{
+    const StepArgs& a = sa.s;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < a.n;
+         g += (long long)gridDim.x * blockDim.x) {
+        if (sa.env_flag[g / a.uniform_N]) continue;
+        Drone d;
+        load_state(a.state, a.n, g, d, false);
+        const float4* y4 = reinterpret_cast<const float4*>(sa.y + 32 * g);
+        float y[16];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float4 v = y4[k];
+            y[4 * k] = v.x; y[4 * k + 1] = v.y; y[4 * k + 2] = v.z; y[4 * k + 3] = v.w;
+        }
+        float dl[13];
+#pragma unroll
+        for (int k = 0; k < 13; ++k) dl[k] = sa.out_mean[k] + sa.out_std[k] * y[k];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            d.p[r] += dl[r];
+            d.v[r] += dl[7 + r];
+            d.w[r] += dl[10 + r];
+        }
+        float qn = 0.f;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            d.q[r] += dl[3 + r];
+            qn += d.q[r] * d.q[r];
+        }
+        const float inv = rsqrtf(qn);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) d.q[r] *= inv;
+        store_state(a.state, a.n, g, d, false);
+    }
+}
+
+// The plain integrator for the flagged environments: one warp per environment (N <= 32),
+// the RPMs the prepare step stored in plane 5, n_sub substeps with the warp's own
+// position snapshot.
+__global__ void __launch_bounds__(128) surrogate_fallback_kernel(const SurrogateArgs sa)
+{
+    __shared__ float4 s_pos[4][2][32];
+    const StepArgs& a = sa.s;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int count = *sa.fallback_count;
+    for (int item = blockIdx.x * 4 + wib; item < count; item += gridDim.x * 4) {
+        const int e = sa.fallback_list[item];
+        const int N = a.uniform_N;
+        const bool active = lane < N;
+        const long long g = (long long)e * N + lane;
+        Drone d = {};
+        float rpm[4] = {0.f, 0.f, 0.f, 0.f};
+        if (active) {
+            load_state(a.state, a.n, g, d, false);
+            const float4 r = a.state[5 * a.n + g];
+            rpm[0] = r.x; rpm[1] = r.y; rpm[2] = r.z; rpm[3] = r.w;
+        }
+        const int flags = a.env_flags[e];
+        const Motor m = motor(rpm, a.c);
+        for (int s = 0; s < a.n_sub; ++s) {
+            float4* buf = s_pos[wib][s & 1];
+            buf[lane] = make_float4(d.p[0], d.p[1], d.p[2], 0.f);
+            __syncwarp();
+            if (active) substep<8, -1>(d, m, flags, buf, N, a.c);
+        }
+        if (active) {
+            store_state(a.state, a.n, g, d, false);
+            if (!finite_state(d)) {
+                atomicOr(a.status, MDG_STATUS_NONFINITE);
+                atomicMin(a.status + 1, (unsigned)g);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 __global__ void __launch_bounds__(256) pid_kernel(const PidArgs a)
 {
     for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < a.n;
@@ -815,6 +1037,45 @@ cudaError_t launch_rollout(const RolloutArgs& r, int block, int uniform_flags, i
     if (grid <= 0 || grid > r.n_items) grid = r.n_items;
     void* args[] = {const_cast<RolloutArgs*>(&r)};
     return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, rollout_smem_bytes(block), s);
+}
+
+cudaError_t launch_features(const SurrogateArgs& a, int n_tiles, int block, cudaStream_t s)
+{
+    if (n_tiles == 0) return cudaSuccess;
+    const size_t smem = tile_smem_bytes(block);
+    cudaError_t e = cudaFuncSetAttribute(features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    features_kernel<<<n_tiles, block, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_surrogate_prepare(const SurrogateArgs& a, int n_tiles, int block, cudaStream_t s)
+{
+    if (n_tiles == 0) return cudaSuccess;
+    const size_t smem = tile_smem_bytes(block);
+    cudaError_t e =
+        cudaFuncSetAttribute(surrogate_prepare_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    surrogate_prepare_kernel<<<n_tiles, block, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_surrogate_apply(const SurrogateArgs& a, cudaStream_t s)
+{
+    if (a.s.n == 0) return cudaSuccess;
+    long long blocks = (a.s.n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    surrogate_apply_kernel<<<(int)blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_surrogate_fallback(const SurrogateArgs& a, cudaStream_t s)
+{
+    if (a.s.n == 0) return cudaSuccess;
+    int blocks = (a.s.n_envs + 3) / 4;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    surrogate_fallback_kernel<<<blocks, 128, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_obs(const StepArgs& a, int n_tiles, int block, cudaStream_t s)

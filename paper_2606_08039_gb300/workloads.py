@@ -215,7 +215,7 @@ def mixed_actions(swarm: Swarm, seed: int, step: int, hover_rpm: float) -> np.nd
 S_MLP = 9
 
 
-def mlp_init(seed: int, dims=(64, 256, 256, 256, 16)):
+def mlp_init(seed: int, dims=(64, 256, 256, 256, 32)):
     """Initial surrogate weights: W_l ~ U[-b, b] with b = sqrt(6 / fan_in) (He uniform), b_l = 0;
     float32 arrays [(W [out, in], b [out]), ...], drawn counter-based per (layer, row, col)."""
     out = []
