@@ -63,6 +63,7 @@ extern "C" {
 
 /* Status bits written by the kernels (read with mdg_status). */
 #define MDG_STATUS_NONFINITE 1u /* a drone's state became NaN or infinite */
+#define MDG_STATUS_TIMEOUT 2u   /* a tensor-core kernel gave up waiting for its MMAs (bounded wait) */
 
 #define MDG_STATE_PLANES 6
 #define MDG_KIN_DIM 20     /* [p(3), q(4), roll/pitch/yaw(3), v(3), w(3), a_prev(4)] */
@@ -316,6 +317,17 @@ int mdg_mlp_forward(mdg_mlp m, const uint16_t* x, float* y, int32_t B, void* str
 int mdg_mlp_grad(mdg_mlp m, const uint16_t* x, const float* t, int32_t B, float* loss_out, void* stream);
 /* One Adam step (b1 0.9, b2 0.999, eps 1e-8) with the gradient of the last mdg_mlp_grad. */
 int mdg_mlp_adam(mdg_mlp m, float lr, void* stream);
+
+/* Inference path of mdg_mlp_forward and mdg_surrogate_step: MDG_MLP_PATH_TCGEN05 (default:
+ * one fused kernel on tcgen05.mma with the accumulator in tensor memory and the
+ * activations in shared memory) or MDG_MLP_PATH_MMA_SYNC (one mma.sync GEMM per layer, the
+ * training kernels). Training always uses the mma.sync kernels. */
+#define MDG_MLP_PATH_MMA_SYNC 0
+#define MDG_MLP_PATH_TCGEN05 1
+int mdg_mlp_set_path(mdg_mlp m, int32_t path);
+/* Read and clear the surrogate's status word (synchronises `stream`): MDG_STATUS_TIMEOUT
+ * if a tensor-core kernel abandoned its work. */
+int mdg_mlp_status(mdg_mlp m, void* stream, uint32_t* bits);
 
 /* Raw surrogate inputs of the current state: raw device [n_drones][41] =
  * [p, q, v, w, rpm (4), 4 nearest neighbours' (p_i - p_j, v_i - v_j)]; rpm device

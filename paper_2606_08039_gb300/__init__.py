@@ -23,6 +23,8 @@ from . import workloads  # noqa: F401  (seeded synthetic inputs)
 GND, DRAG, DW = 1, 2, 4
 ACT_RPM, ACT_PID, ACT_MIXED = 0, 1, 2
 STATUS_NONFINITE = 1
+STATUS_TIMEOUT = 2
+MLP_PATH_MMA_SYNC, MLP_PATH_TCGEN05 = 0, 1
 STATE_PLANES = 6
 KIN_DIM = 20
 NBR_K = 4
@@ -75,6 +77,8 @@ _SIGNATURES = {
     "mdg_mlp_forward": ([_VP, _VP, _VP, ctypes.c_int32, _VP], ctypes.c_int),
     "mdg_mlp_grad": ([_VP, _VP, _VP, ctypes.c_int32, _VP, _VP], ctypes.c_int),
     "mdg_mlp_adam": ([_VP, ctypes.c_float, _VP], ctypes.c_int),
+    "mdg_mlp_set_path": ([_VP, ctypes.c_int32], ctypes.c_int),
+    "mdg_mlp_status": ([_VP, _VP, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
     "mdg_features": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "mdg_surrogate_step": ([_VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, _VP, _VP],
                            ctypes.c_int),
@@ -463,6 +467,15 @@ class MLP:
         _check(lib().mdg_mlp_grad(self._m, _ptr(x, "x", torch.bfloat16, (B, MLP_IN_PAD)),
                                   _ptr(t, "t", torch.float32, (B, MLP_OUT_PAD)), int(B),
                                   _ptr(loss, "loss", torch.float32, (1,)), _stream(stream)))
+
+    def set_path(self, path: int):
+        """Inference path: MLP_PATH_TCGEN05 (fused tensor-memory kernel) or MLP_PATH_MMA_SYNC."""
+        _check(lib().mdg_mlp_set_path(self._m, int(path)))
+
+    def status(self, stream=None) -> int:
+        bits = ctypes.c_uint32()
+        _check(lib().mdg_mlp_status(self._m, _stream(stream), ctypes.byref(bits)))
+        return bits.value
 
     def adam(self, lr: float, stream=None):
         _check(lib().mdg_mlp_adam(self._m, ctypes.c_float(lr), _stream(stream)))

@@ -68,6 +68,8 @@ struct mdg_mlp_s {
     unsigned* env_flag = nullptr;
     int* fb_list = nullptr;
     int* fb_count = nullptr;
+    uint32_t* status = nullptr;
+    int path = MDG_MLP_PATH_TCGEN05;
     mdg::MlpView view() const { return layout(master, w16); }
 };
 
@@ -93,6 +95,7 @@ void destroy_mlp(mdg_mlp m)
     cudaFree(m->env_flag);
     cudaFree(m->fb_list);
     cudaFree(m->fb_count);
+    cudaFree(m->status);
     delete m;
 }
 
@@ -147,6 +150,7 @@ int mdg_mlp_create(int32_t max_batch, const float* init, mdg_mlp* out)
     alloc((void**)&m->env_flag, B * 4);
     alloc((void**)&m->fb_list, B * 4);
     alloc((void**)&m->fb_count, 4);
+    alloc((void**)&m->status, 8);
     if (e == cudaSuccess && init) e = cudaMemcpy(m->master, init, P * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = mdg::mlp_refresh_bf16(m->view(), 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -232,10 +236,17 @@ int mdg_mlp_forward(mdg_mlp m, const uint16_t* x, float* y, int32_t B, void* str
 {
     if (!m || !x || !y) return fail(MDG_ERR_ARG, "mdg_mlp_forward: NULL argument");
     if (!batch_ok(m, B)) return fail(MDG_ERR_ARG, "mdg_mlp_forward: B = %d must be a multiple of 128 <= %d", B, m->max_batch);
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15u)
+        return fail(MDG_ERR_ARG, "mdg_mlp_forward: x and y must be 16-byte aligned");
     Guard g(m->device);
-    float* zs[3] = {nullptr, nullptr, nullptr};
-    void* hs[3] = {m->h[0], m->h[1], m->h[2]};
-    cudaError_t e = mdg::mlp_forward(m->view(), x, B, zs, hs, y, nullptr, nullptr, nullptr, (cudaStream_t)stream);
+    cudaError_t e;
+    if (m->path == MDG_MLP_PATH_TCGEN05) {
+        e = mdg::mlp_forward_umma(m->view(), x, B, y, m->status, (cudaStream_t)stream);
+    } else {
+        float* zs[3] = {nullptr, nullptr, nullptr};
+        void* hs[3] = {m->h[0], m->h[1], m->h[2]};
+        e = mdg::mlp_forward(m->view(), x, B, zs, hs, y, nullptr, nullptr, nullptr, (cudaStream_t)stream);
+    }
     return e == cudaSuccess ? MDG_OK : cuda_fail(e, "mdg_mlp_forward");
 }
 
@@ -263,6 +274,28 @@ int mdg_mlp_adam(mdg_mlp m, float lr, void* stream)
     m->step += 1;
     cudaError_t e = mdg::mlp_adam(m->view(), m->grad, m->m, m->v, lr, m->step, (cudaStream_t)stream);
     return e == cudaSuccess ? MDG_OK : cuda_fail(e, "mdg_mlp_adam");
+}
+
+int mdg_mlp_set_path(mdg_mlp m, int32_t path)
+{
+    if (!m) return fail(MDG_ERR_ARG, "mdg_mlp_set_path: NULL handle");
+    if (path != MDG_MLP_PATH_MMA_SYNC && path != MDG_MLP_PATH_TCGEN05)
+        return fail(MDG_ERR_ARG, "mdg_mlp_set_path: unknown path %d", path);
+    m->path = path;
+    return MDG_OK;
+}
+
+int mdg_mlp_status(mdg_mlp m, void* stream, uint32_t* bits)
+{
+    if (!m) return fail(MDG_ERR_ARG, "mdg_mlp_status: NULL handle");
+    Guard g(m->device);
+    uint32_t st[2] = {0u, 0u};
+    cudaError_t e = cudaMemcpyAsync(st, m->status, 8, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->status, 0, 8, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mdg_mlp_status");
+    if (bits) *bits = st[0];
+    return MDG_OK;
 }
 
 int mdg_features(mdg_handle h, const float* state, const float* rpm, float* raw, void* stream)
@@ -351,9 +384,13 @@ int mdg_surrogate_step(mdg_handle h, mdg_mlp m, float* state, const float* actio
                             (size_t)(n_pad - h->n_drones) * MDG_MLP_IN_PAD * 2, s);
     if (e == cudaSuccess) e = mdg::launch_surrogate_prepare(a, h->n_tiles, h->block, s);
     if (e == cudaSuccess) {
-        float* zs[3] = {nullptr, nullptr, nullptr};
-        void* hs[3] = {m->h[0], m->h[1], m->h[2]};
-        e = mdg::mlp_forward(m->view(), m->x, n_pad, zs, hs, m->y, nullptr, nullptr, nullptr, s);
+        if (m->path == MDG_MLP_PATH_TCGEN05) {
+            e = mdg::mlp_forward_umma(m->view(), m->x, n_pad, m->y, h->d_status, s);
+        } else {
+            float* zs[3] = {nullptr, nullptr, nullptr};
+            void* hs[3] = {m->h[0], m->h[1], m->h[2]};
+            e = mdg::mlp_forward(m->view(), m->x, n_pad, zs, hs, m->y, nullptr, nullptr, nullptr, s);
+        }
     }
     if (e == cudaSuccess) e = mdg::launch_surrogate_apply(a, s);
     if (e == cudaSuccess) e = mdg::launch_surrogate_fallback(a, s);

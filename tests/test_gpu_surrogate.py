@@ -40,14 +40,20 @@ def _f64(layers):
     return [(np.asarray(W, np.float64), np.asarray(b, np.float64)) for W, b in layers]
 
 
-def test_forward_matches_oracle(cuda):
-    B = 384
+@pytest.mark.parametrize("path,B", [(mdg.MLP_PATH_TCGEN05, 128), (mdg.MLP_PATH_TCGEN05, 384 * 8),
+                                    (mdg.MLP_PATH_MMA_SYNC, 384)])
+def test_forward_matches_oracle(cuda, path, B):
+    """Both inference paths (fused tcgen05 kernel, per-layer mma.sync GEMMs) against the
+    oracle on identical bf16 inputs and weights; several tiles per block for the persistent
+    tcgen05 kernel."""
     layers = _layers(1)
     m = mdg.MLP(B, layers)
+    m.set_path(path)
     x = torch.as_tensor(_inputs(2, B), device=cuda).to(torch.bfloat16)
-    y = torch.empty((B, mdg.MLP_OUT_PAD), device=cuda)
+    y = torch.full((B, mdg.MLP_OUT_PAD), float("nan"), device=cuda)
     m.forward(x, y)
     torch.cuda.synchronize()
+    assert m.status() == 0
     yo, _ = omlp.forward(_f64(layers), x.float().cpu().numpy().astype(np.float64), bf16_storage=True)
     # identical bf16 inputs and weights; FP32 vs FP64 accumulation can flip the bf16 rounding
     # of a hidden activation by one bf16 unit (2^-8 relative), hence 1e-2
@@ -217,4 +223,25 @@ def test_out_of_distribution_environments_take_the_integrator(cuda, trained):
     resp = tolerance_response(P, layout, x0, i0, a0, wp, acts, 5)
     assert_horizon_close(xg, xo, resp, 5, what="fallback")
     assert excess(ig, io, 1e-5) <= 1.0
+    assert h.status()[0] == mdg.OK
+
+
+def test_surrogate_step_paths_agree(cuda, trained):
+    m, data, _ = trained
+    sw = wl.full_aero(79, n_envs=512)
+    h = mdg.Handle(sw.drones_per_env, sw.flags)
+    wp = torch.as_tensor(wl.waypoints(79, sw.n), device=cuda)
+    out = []
+    for path in (mdg.MLP_PATH_MMA_SYNC, mdg.MLP_PATH_TCGEN05):
+        m.set_path(path)
+        st = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=cuda)
+        m.step(h, st, wp, mdg.ACT_PID, 5, 4.0)
+        torch.cuda.synchronize()
+        out.append(sg.state13(st).cpu().numpy().astype(np.float64))
+    m.set_path(mdg.MLP_PATH_TCGEN05)
+    # same network, same inputs and the same out-of-distribution decisions: the states differ
+    # only by out_std times the difference of the standardised outputs, which the forward
+    # test bounds by 1e-2 max(|y|, 1); |y| stays below ~4 in distribution, hence 0.05 out_std
+    tol = 0.05 * data.out_std.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(out[1] - out[0]) <= tol[None, :])
     assert h.status()[0] == mdg.OK
