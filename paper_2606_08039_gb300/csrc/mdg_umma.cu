@@ -1,14 +1,14 @@
 // Fused inference of the surrogate network on the 5th-generation tensor cores (sm_103a):
 // tcgen05.mma with the accumulator in tensor memory, operands in shared memory.
 //
-// One persistent thread block (8 warps) per SM takes 128-row tiles of drones. For every
-// tile it stages the bf16 inputs in shared memory, then for each of the four layers:
-// stages the layer's weights, lets one thread issue the K/16 tcgen05.mma instructions
-// (M = 128, N = 256 or 32, bf16 x bf16 -> FP32 in TMEM) and commit them to an mbarrier,
-// and after their completion reads the accumulator back with tcgen05.ld, adds the bias,
-// applies SiLU and writes the bf16 activations into the shared-memory operand of the next
-// layer (the output layer's FP32 values go to global memory). Activations never leave
-// the SM.
+// One persistent thread block (16 warps) per SM takes 128-row tiles of drones. For each of
+// the four layers one thread issues the K/16 tcgen05.mma instructions (M = 128, N = 256 or
+// 32, bf16 x bf16 -> FP32 in TMEM) on the shared-memory activations and weights and commits
+// them to an mbarrier; once they complete, the copy of the next operands (the next layer's
+// weights, or the next tile's inputs and first-layer weights) is issued, and meanwhile the
+// warps read the accumulator back with tcgen05.ld, add the bias, apply SiLU and write the
+// bf16 activations into the shared-memory operand of the next layer (the output layer's
+// FP32 values go to global memory). Activations never leave the SM.
 //
 // Shared-memory operands use the canonical K-major layout with 128-byte swizzling: a
 // [rows x K] bf16 matrix is stored as K/64 chunks of rows x 128 bytes; within a chunk row r
@@ -26,7 +26,7 @@ namespace mdg {
 namespace {
 
 constexpr int kRows = 128;         // tile rows (UMMA M)
-constexpr int kThreads = 256;      // 8 warps: two per TMEM lane quadrant
+constexpr int kThreads = 512;      // 16 warps: four per TMEM lane quadrant, 64 columns each
 constexpr int kActBytes = 128 * 256 * 2;   // activations [128 x 256] bf16
 constexpr int kWBytes = 256 * 256 * 2;     // largest weight matrix [256 x 256] bf16
 constexpr uint32_t kTmemCols = 256;
@@ -110,15 +110,28 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32])
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Stage a row-major [rows x K] bf16 matrix (K contiguous) into the SW128 K-major layout.
-__device__ __forceinline__ void stage(uint32_t s_base, const __nv_bfloat16* g, int rows, int K)
+// Issue the copy of a row-major [rows x K] bf16 matrix (K contiguous) into the SW128
+// K-major layout (cp.async, one commit group); cp_wait() completes it.
+__device__ __forceinline__ void stage_async(uint32_t s_base, const __nv_bfloat16* g, int rows, int K)
 {
     const int pieces = rows * (K >> 3);
     for (int i = threadIdx.x; i < pieces; i += kThreads) {
         const int r = i / (K >> 3), k8 = i % (K >> 3);
         cp_async16(s_base + sw128_offset(r, k8, rows), g + (size_t)r * K + k8 * 8);
     }
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// SiLU(z) = z / (1 + exp(-z)) = z/2 (1 + tanh(z/2)): one special-function instruction
+// (tanh.approx.f32, relative error about 2^-11) instead of an exponential and a division.
+__device__ __forceinline__ float silu_tanh(float z)
+{
+    const float h = 0.5f * z;
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(h));
+    return fmaf(h, t, h);
 }
 
 __device__ __forceinline__ void make_operands_visible()
@@ -141,6 +154,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t* s_w = base + kActBytes;
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t s_tmem;
+    __shared__ float s_bias[3 * MDG_MLP_HIDDEN + MDG_MLP_OUT_PAD];  // b1, b2, b3, b4
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t mbar_a = smem_u32(&mbar);
@@ -153,23 +167,31 @@ __global__ void __launch_bounds__(kThreads, 1)
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
+    for (int i = threadIdx.x; i < 3 * MDG_MLP_HIDDEN + MDG_MLP_OUT_PAD; i += kThreads) {
+        const int l = i < 3 * MDG_MLP_HIDDEN ? i / MDG_MLP_HIDDEN : 3;
+        s_bias[i] = master[w.b_off[l] + (i - l * MDG_MLP_HIDDEN)];
+    }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = s_tmem;
     const uint32_t act_a = smem_u32(s_act), w_a = smem_u32(s_w);
-    const int quad = warp & 3, half = warp >> 2;
+    const int quad = warp & 3, part = warp >> 2;  // TMEM lane quadrant, column quarter
     const int row = quad * 32 + lane;  // this thread's accumulator row (TMEM lane)
     const uint32_t t_row = tmem + ((uint32_t)(quad * 32) << 16);
     const int dims[5] = {MDG_MLP_IN_PAD, MDG_MLP_HIDDEN, MDG_MLP_HIDDEN, MDG_MLP_HIDDEN, MDG_MLP_OUT_PAD};
     uint32_t phase = 0;
     bool abort = false;  // identical in every thread (set from __syncthreads_and)
 
+    // the first tile's inputs and first-layer weights
+    if (blockIdx.x < n_tiles) {
+        stage_async(act_a, x + (size_t)blockIdx.x * kRows * MDG_MLP_IN_PAD, kRows, MDG_MLP_IN_PAD);
+        stage_async(w_a, w16 + w.w_off[0], dims[1], dims[0]);
+    }
     for (int tile = blockIdx.x; tile < n_tiles && !abort; tile += gridDim.x) {
-        stage(act_a, x + (size_t)tile * kRows * MDG_MLP_IN_PAD, kRows, MDG_MLP_IN_PAD);
         for (int l = 0; l < 4; ++l) {
             const int K = dims[l], N = dims[l + 1];
-            stage(w_a, w16 + w.w_off[l], N, K);
+            cp_wait();  // this layer's weights (and, for l = 0, the tile's inputs) have landed
             make_operands_visible();
             if (threadIdx.x == 0) {
                 const uint32_t idesc = idesc_bf16(kRows, N);
@@ -189,20 +211,27 @@ __global__ void __launch_bounds__(kThreads, 1)
                 abort = true;
                 break;
             }
-            const float* bias = master + w.b_off[l];
+            // The MMAs have consumed their operands: start the next copies now so that they
+            // overlap this layer's epilogue (the next layer's weights, or after the last layer
+            // the next tile's inputs and first-layer weights).
             if (l < 3) {
-                // bias + SiLU -> bf16 activations, this warp's half of the 256 columns
+                stage_async(w_a, w16 + w.w_off[l + 1], dims[l + 2], dims[l + 1]);
+            } else if (tile + (int)gridDim.x < n_tiles) {
+                stage_async(act_a, x + (size_t)(tile + gridDim.x) * kRows * MDG_MLP_IN_PAD, kRows, MDG_MLP_IN_PAD);
+                stage_async(w_a, w16 + w.w_off[0], dims[1], dims[0]);
+            }
+            const float* bias = s_bias + l * MDG_MLP_HIDDEN;
+            if (l < 3) {
+                // bias + SiLU -> bf16 activations, this warp's quarter of the 256 columns
 #pragma unroll 1
-                for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 32) {
+                for (int c0 = part * 64; c0 < part * 64 + 64; c0 += 32) {
                     float v[32];
                     tmem_ld32(t_row + c0, v);
                     __nv_bfloat162 o[16];
 #pragma unroll
-                    for (int i = 0; i < 32; i += 2) {
-                        const float z0 = v[i] + __ldg(bias + c0 + i), z1 = v[i + 1] + __ldg(bias + c0 + i + 1);
-                        o[i / 2] = __floats2bfloat162_rn(__fdividef(z0, 1.f + __expf(-z0)),
-                                                         __fdividef(z1, 1.f + __expf(-z1)));
-                    }
+                    for (int i = 0; i < 32; i += 2)
+                        o[i / 2] = __floats2bfloat162_rn(silu_tanh(v[i] + bias[c0 + i]),
+                                                         silu_tanh(v[i + 1] + bias[c0 + i + 1]));
                     const uint4* o4 = reinterpret_cast<const uint4*>(o);
 #pragma unroll
                     for (int p = 0; p < 4; ++p) {
@@ -210,20 +239,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                         *reinterpret_cast<uint4*>(s_act + off) = o4[p];
                     }
                 }
-            } else if (half == 0) {
+            } else if (part == 0) {
                 float v[32];
                 tmem_ld32(t_row, v);
                 float4* out = reinterpret_cast<float4*>(y + ((size_t)tile * kRows + row) * MDG_MLP_OUT_PAD);
 #pragma unroll
                 for (int i = 0; i < 32; i += 4)
-                    out[i / 4] = make_float4(v[i] + __ldg(bias + i), v[i + 1] + __ldg(bias + i + 1),
-                                             v[i + 2] + __ldg(bias + i + 2), v[i + 3] + __ldg(bias + i + 3));
+                    out[i / 4] = make_float4(v[i] + bias[i], v[i + 1] + bias[i + 1], v[i + 2] + bias[i + 2],
+                                             v[i + 3] + bias[i + 3]);
             }
             // all tensor-memory reads and activation writes done before the next MMA
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             __syncthreads();
         }
     }
+    cp_wait();  // no copy left in flight
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (warp == 0)
