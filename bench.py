@@ -245,7 +245,7 @@ def run_other(args) -> None:
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    sink = torch.empty(1, dtype=torch.float32, device=dev)
+    sink = torch.empty((), dtype=torch.float32, device=dev)
     c = mdg.Constants.cf2x()
     hover = c.hover_rpm()
     extra = {}
@@ -362,6 +362,123 @@ def run_other(args) -> None:
     print(json.dumps(out))
 
 
+def run_surrogate(args) -> None:
+    """The learned surrogate on one GPU: trained on ~10M transitions generated by the
+    full-aero kernels (16384 envs x 4 drones, 153 control steps of PID with +-10% RPM
+    perturbations), then one control step of 65536 envs x 4 drones (PID waypoints) with the
+    surrogate (fused tcgen05 network, out-of-distribution environments on the plain
+    integrator) against the plain fused step on the same swarm. Metric: drone-control-steps/s.
+    Also: the one-step error of the surrogate against the plain integrator on the regular
+    regime, the out-of-distribution fraction, and the tensor roofline of the network kernel."""
+    import torch
+    import paper_2606_08039_gb300 as mdg
+    from paper_2606_08039_gb300 import surrogate as sg
+    from paper_2606_08039_gb300 import workloads as wl
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    raw, delta = sg.generate_transitions(16384, 153, seed=3, device=dev)
+    data = sg.Dataset(raw, delta)
+    del raw, delta
+    sw = wl.surrogate_eval(4, 65536)
+    m = mdg.MLP(sw.n, wl.mlp_init(3))
+    data.attach(m)
+    hist = sg.fit(m, data, epochs=4, batch=8192, lr=2e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    n_train = len(data)
+    kept = data.kept_fraction
+    out_std = data.out_std
+    out_mean = data.out_mean
+    del data
+
+    h = mdg.Handle(sw.drones_per_env, sw.flags)
+    init = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=dev)
+    wp = torch.as_tensor(wl.waypoints(4, sw.n), device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    sink = torch.empty((), dtype=torch.float32, device=dev)
+
+    def timed(fn, n, state):
+        st = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+        en = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+        for i in range(n):
+            state.copy_(init)
+            flush.fill_(1.0)
+            torch.sum(flush, dim=0, out=sink)
+            st[i].record(stream)
+            fn()
+            en[i].record(stream)
+        torch.cuda.synchronize()
+        return float(sum(a.elapsed_time(b) for a, b in zip(st, en))) / n
+
+    steps = min(args.steps, 500)
+    s_sur, s_pln = init.clone(), init.clone()
+    nfb = torch.zeros(1, dtype=torch.int32, device=dev)
+    sur = lambda: m.step(h, s_sur, wp, mdg.ACT_PID, N_SUB, 4.0, nfb, stream=stream)
+    pln = lambda: h.step(s_pln, wp, mdg.ACT_PID, N_SUB, stream=stream)
+    timed(sur, args.warmup, s_sur)
+    timed(pln, args.warmup, s_pln)
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    ms_sur = timed(sur, steps, s_sur)
+    ms_pln = timed(pln, steps, s_pln)
+    clk = clocks.stop()
+    # the network kernel alone (tensor roofline)
+    x = torch.empty((sw.n, mdg.MLP_IN_PAD), dtype=torch.bfloat16, device=dev)
+    x.copy_(torch.randn_like(x, dtype=torch.float32).to(torch.bfloat16))
+    y = torch.empty((sw.n, mdg.MLP_OUT_PAD), device=dev)
+    ms_net = timed(lambda: m.forward(x, y, stream=stream), steps, s_sur)
+    flops = 2.0 * sw.n * (64 * 256 + 2 * 256 * 256 + 256 * 32)
+    # one-step accuracy from the initial swarm
+    s_sur.copy_(init)
+    s_pln.copy_(init)
+    before = sg.state13(init).clone()
+    sur()
+    pln()
+    torch.cuda.synchronize()
+    xs, xp = sg.state13(s_sur), sg.state13(s_pln)
+    true_d = xp - before
+    zt = (true_d - out_mean) / out_std
+    fb_env = ((xs - xp).abs().max(1).values.view(-1, 4) == 0).all(1).repeat_interleave(4)
+    regular = (zt.abs() <= 8).all(1) & ~fb_env
+    err = {}
+    for name, sl in (("position", slice(0, 3)), ("quaternion", slice(3, 7)), ("velocity", slice(7, 10)),
+                     ("body_rate", slice(10, 13))):
+        e = float((xs[regular, sl] - xp[regular, sl]).pow(2).mean().sqrt())
+        b = float(true_d[regular, sl].pow(2).mean().sqrt())
+        err[name] = {"rms_error": e, "rms_change": b, "ratio_vs_no_network": e / b if b > 0 else None}
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0}
+    ach = flops / (ms_net * 1e-3) / 1e12
+    value = sw.n / (ms_sur * 1e-3)
+    out = {
+        "metric": "surrogate speedup at stated error: drone-control-steps/s of the surrogate step",
+        "value": value, "unit": "drone-control-steps/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": ms_sur, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic",
+        "config": {"workload": "surrogate: 65536 envs x 4 drones, PID waypoints, one control step; network "
+                               "41-256-256-256-13 SiLU, bf16 weights/activations, FP32 accumulation, fused tcgen05 "
+                               "kernel; out-of-distribution environments on the plain integrator",
+                   "l2": "flushed between timed steps (512 MiB written, then read back)",
+                   "training": {"transitions_generated": 16384 * 4 * 153, "transitions_kept": n_train,
+                                "kept_fraction": kept, "epochs": 4, "batch": 8192, "seconds": train_s,
+                                "loss_per_epoch": hist}},
+        "plain_integrator": {"value": sw.n / (ms_pln * 1e-3), "ms_per_step": ms_pln},
+        "speedup_vs_plain": ms_pln / ms_sur,
+        "one_step_error_vs_plain": err, "regular_fraction": float(regular.float().mean()),
+        "ood_env_fraction": int(nfb) / sw.n_envs,
+        "gpu_launches": 5 * steps,
+        "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                     "frac": ach / peaks["bf16_tflops"], "traffic": None, "peak_src": "measured (bf16 burst)",
+                     "kernel": "mlp_umma_kernel", "ms": ms_net, "algorithmic_flops_per_launch": flops},
+        "clocks": clk,
+    }
+    print(json.dumps(out))
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -370,13 +487,16 @@ def main() -> None:
     ap.add_argument("--impl", default="mdg", choices=["mdg", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="full_aero", choices=["full_aero", "uneven", "dense", "single"],
+    ap.add_argument("--workload", default="full_aero", choices=["full_aero", "uneven", "dense", "single", "surrogate"],
                     help="full_aero (default, the headline line); the others measure the other swarms")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "surrogate":
+        run_surrogate(args)
         return
     if args.workload != "full_aero":
         run_other(args)
@@ -404,7 +524,7 @@ def main() -> None:
     wp = wp_host.to(dev)
     kin, idx, rel = h.new_obs(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    flush_sink = torch.empty(1, dtype=torch.float32, device=dev)
+    flush_sink = torch.empty((), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def flush_l2():
