@@ -52,7 +52,7 @@ BYTES_PER_DRONE_STEP = STATE_BYTES_READ + ACTION_BYTES + STATE_BYTES_WRITE + OBS
 # DRAM traffic of one step-kernel launch on the full-aero workload, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel source whose
 # sha256 prefix is recorded with it; profiles/ holds the capture's summary.
-NCU_TRAFFIC = {"kernel_sha": "ea163c4b5c9db96d", "bytes": 6322944 + 256}
+NCU_TRAFFIC = {"kernel_sha": "511331ce3f40a1ac", "bytes": 6322944 + 256}
 
 
 def kernel_sha() -> str:
@@ -362,6 +362,54 @@ def run_other(args) -> None:
     print(json.dumps(out))
 
 
+def run_mlp(args) -> None:
+    """The surrogate network's inference kernels alone: 262144 rows (the 65536 x 4 swarm),
+    initial weights, bf16 inputs; the fused tcgen05 kernel (the step's path) and, for
+    comparison, the per-layer mma.sync GEMMs. Tensor roofline against the measured bf16 peak."""
+    import torch
+    import paper_2606_08039_gb300 as mdg
+    from paper_2606_08039_gb300 import workloads as wl
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    rows = 262144
+    m = mdg.MLP(rows, wl.mlp_init(3))
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    x = torch.randn((rows, mdg.MLP_IN_PAD), generator=g, device=dev).to(torch.bfloat16)
+    y = torch.empty((rows, mdg.MLP_OUT_PAD), device=dev)
+    flops = 2.0 * rows * (64 * 256 + 2 * 256 * 256 + 256 * 32)
+    res = {}
+    steps = min(args.steps, 500)
+    for name, path in (("mma_sync", mdg.MLP_PATH_MMA_SYNC), ("tcgen05", mdg.MLP_PATH_TCGEN05)):
+        m.set_path(path)
+        for _ in range(args.warmup):
+            m.forward(x, y, stream=stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(steps):
+            m.forward(x, y, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        res[name] = a.elapsed_time(b) / steps
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0}
+    ach = flops / (res["tcgen05"] * 1e-3) / 1e12
+    print(json.dumps({
+        "metric": "surrogate network rows/s", "value": rows / (res["tcgen05"] * 1e-3), "unit": "rows/s",
+        "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": res["tcgen05"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "surrogate network forward, 262144 rows, 64-256-256-256-32, bf16/FP32 accumulation",
+                   "l2": "inputs (33.5 MB) and weights stay in L2 between launches"},
+        "mma_sync_ms": res["mma_sync"], "gpu_launches": steps,
+        "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                     "frac": ach / peaks["bf16_tflops"], "traffic": None, "peak_src": "measured (bf16 burst)",
+                     "kernel": "mlp_umma_kernel", "algorithmic_flops_per_launch": flops},
+        "status": m.status()}))
+
+
 def run_surrogate(args) -> None:
     """The learned surrogate on one GPU: trained on ~10M transitions generated by the
     full-aero kernels (16384 envs x 4 drones, 153 control steps of PID with +-10% RPM
@@ -487,7 +535,7 @@ def main() -> None:
     ap.add_argument("--impl", default="mdg", choices=["mdg", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="full_aero", choices=["full_aero", "uneven", "dense", "single", "surrogate"],
+    ap.add_argument("--workload", default="full_aero", choices=["full_aero", "uneven", "dense", "single", "surrogate", "mlp"],
                     help="full_aero (default, the headline line); the others measure the other swarms")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -497,6 +545,9 @@ def main() -> None:
         return
     if args.workload == "surrogate":
         run_surrogate(args)
+        return
+    if args.workload == "mlp":
+        run_mlp(args)
         return
     if args.workload != "full_aero":
         run_other(args)
