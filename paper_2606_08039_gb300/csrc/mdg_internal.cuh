@@ -140,8 +140,13 @@ cudaError_t mlp_adam(const MlpView& w, const float* grad, float* m, float* v, fl
 cudaError_t mlp_refresh_bf16(const MlpView& w, cudaStream_t s);
 cudaError_t mlp_standardize(const float* raw, void* x, long long rows, const float* mean, const float* inv_std,
                             cudaStream_t s);
-// mdg_umma.cu: fused tcgen05 forward, B a multiple of 128, y [B][32]
-cudaError_t mlp_forward_umma(const MlpView& w, const void* x, int B, float* y, uint32_t* status, cudaStream_t s);
+// mdg_umma.cu: fused tcgen05 forward, B a multiple of 128, y [B][32]. `img` is the weight
+// image of mlp_build_image (mlp_image_bytes() bytes, 16-byte aligned), rebuilt whenever the
+// bf16 weights change.
+size_t mlp_image_bytes();
+cudaError_t mlp_build_image(const MlpView& w, void* img, cudaStream_t s);
+cudaError_t mlp_forward_umma(const MlpView& w, const void* img, const void* x, int B, float* y, uint32_t* status,
+                             cudaStream_t s);
 
 cudaError_t launch_obs(const StepArgs& a, int n_tiles, int block, cudaStream_t s);
 cudaError_t launch_pid(const PidArgs& a, cudaStream_t s);

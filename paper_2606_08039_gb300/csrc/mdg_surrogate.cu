@@ -70,6 +70,8 @@ struct mdg_mlp_s {
     int* fb_count = nullptr;
     uint32_t* status = nullptr;
     int path = MDG_MLP_PATH_TCGEN05;
+    uint8_t* img = nullptr;      // weight image of the tcgen05 kernel
+    bool img_stale = true;       // the bf16 weights changed since the image was built
     mdg::MlpView view() const { return layout(master, w16); }
 };
 
@@ -96,7 +98,19 @@ void destroy_mlp(mdg_mlp m)
     cudaFree(m->fb_list);
     cudaFree(m->fb_count);
     cudaFree(m->status);
+    cudaFree(m->img);
     delete m;
+}
+
+// The tcgen05 kernel reads the weights from their image; rebuild it after they change.
+cudaError_t forward_umma(mdg_mlp m, const void* x, int B, float* y, uint32_t* status, cudaStream_t s)
+{
+    if (m->img_stale) {
+        cudaError_t e = mdg::mlp_build_image(m->view(), m->img, s);
+        if (e != cudaSuccess) return e;
+        m->img_stale = false;
+    }
+    return mdg::mlp_forward_umma(m->view(), m->img, x, B, y, status, s);
 }
 
 bool batch_ok(mdg_mlp m, int B) { return B > 0 && B % 128 == 0 && B <= m->max_batch; }
@@ -151,6 +165,7 @@ int mdg_mlp_create(int32_t max_batch, const float* init, mdg_mlp* out)
     alloc((void**)&m->fb_list, B * 4);
     alloc((void**)&m->fb_count, 4);
     alloc((void**)&m->status, 8);
+    alloc((void**)&m->img, mdg::mlp_image_bytes());
     if (e == cudaSuccess && init) e = cudaMemcpy(m->master, init, P * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = mdg::mlp_refresh_bf16(m->view(), 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -185,6 +200,7 @@ int mdg_mlp_set_params(mdg_mlp m, const float* host_in)
     Guard g(m->device);
     cudaError_t e = cudaMemcpy(m->master, host_in, (size_t)MDG_MLP_PARAMS * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = mdg::mlp_refresh_bf16(m->view(), 0);
+    m->img_stale = true;
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     return e == cudaSuccess ? MDG_OK : cuda_fail(e, "mdg_mlp_set_params");
 }
@@ -241,7 +257,7 @@ int mdg_mlp_forward(mdg_mlp m, const uint16_t* x, float* y, int32_t B, void* str
     Guard g(m->device);
     cudaError_t e;
     if (m->path == MDG_MLP_PATH_TCGEN05) {
-        e = mdg::mlp_forward_umma(m->view(), x, B, y, m->status, (cudaStream_t)stream);
+        e = forward_umma(m, x, B, y, m->status, (cudaStream_t)stream);
     } else {
         float* zs[3] = {nullptr, nullptr, nullptr};
         void* hs[3] = {m->h[0], m->h[1], m->h[2]};
@@ -272,6 +288,7 @@ int mdg_mlp_adam(mdg_mlp m, float lr, void* stream)
     if (!(lr > 0.f)) return fail(MDG_ERR_ARG, "mdg_mlp_adam: lr must be > 0");
     Guard g(m->device);
     m->step += 1;
+    m->img_stale = true;
     cudaError_t e = mdg::mlp_adam(m->view(), m->grad, m->m, m->v, lr, m->step, (cudaStream_t)stream);
     return e == cudaSuccess ? MDG_OK : cuda_fail(e, "mdg_mlp_adam");
 }
@@ -385,7 +402,7 @@ int mdg_surrogate_step(mdg_handle h, mdg_mlp m, float* state, const float* actio
     if (e == cudaSuccess) e = mdg::launch_surrogate_prepare(a, h->n_tiles, h->block, s);
     if (e == cudaSuccess) {
         if (m->path == MDG_MLP_PATH_TCGEN05) {
-            e = mdg::mlp_forward_umma(m->view(), m->x, n_pad, m->y, h->d_status, s);
+            e = forward_umma(m, m->x, n_pad, m->y, h->d_status, s);
         } else {
             float* zs[3] = {nullptr, nullptr, nullptr};
             void* hs[3] = {m->h[0], m->h[1], m->h[2]};

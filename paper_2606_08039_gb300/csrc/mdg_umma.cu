@@ -1,21 +1,34 @@
 // Fused inference of the surrogate network on the 5th-generation tensor cores (sm_103a):
-// tcgen05.mma with the accumulator in tensor memory, operands in shared memory.
+// tcgen05.mma with the accumulators in tensor memory, operands in shared memory.
 //
-// One persistent thread block (16 warps) per SM takes 128-row tiles of drones. For each of
-// the four layers one thread issues the K/16 tcgen05.mma instructions (M = 128, N = 256 or
-// 32, bf16 x bf16 -> FP32 in TMEM) on the shared-memory activations and weights and commits
-// them to an mbarrier; once they complete, the copy of the next operands (the next layer's
-// weights, or the next tile's inputs and first-layer weights) is issued, and meanwhile the
-// warps read the accumulator back with tcgen05.ld, add the bias, apply SiLU and write the
-// bf16 activations into the shared-memory operand of the next layer (the output layer's
-// FP32 values go to global memory). Activations never leave the SM.
+// One persistent thread block per SM takes 128-row tiles of drones; its warps have fixed
+// roles and hand work to each other through mbarriers:
+//
+//   producer warp   streams the weights, chunk by chunk, into a ring of four 32 KB shared-
+//                   memory slots with bulk asynchronous copies (cp.async.bulk, completion
+//                   counted in bytes on the slot's mbarrier), and copies each tile's inputs
+//                   into their operand buffer one tile ahead;
+//   MMA warp        one thread issues the tcgen05.mma instructions (M = 128, N = 256 or 32,
+//                   K = 16 each; bf16 x bf16 -> FP32) of every layer, one 64-column K chunk
+//                   at a time, and commits them to the mbarriers that free a weight slot,
+//                   free the input buffer, or announce a finished accumulator;
+//   16 epilogue     read an accumulator back (tcgen05.ld), add the bias, apply SiLU and
+//   warps           write the bf16 activations, chunk by chunk, as the next layer's A
+//                   operand; the output layer's FP32 values go to global memory.
+//
+// The two 256-column accumulators in tensor memory alternate between layers, so layer
+// l+1's MMAs on chunk c start as soon as the epilogue of layer l has written chunk c of
+// the activations, while that epilogue still reads the rest of layer l's accumulator.
+// Activations never leave the SM; the weights are re-read from L2 for every tile.
 //
 // Shared-memory operands use the canonical K-major layout with 128-byte swizzling: a
-// [rows x K] bf16 matrix is stored as K/64 chunks of rows x 128 bytes; within a chunk row r
-// starts at r * 128 and its 16-byte pieces are permuted by XOR with (r mod 8). Each chunk
-// starts on a 1024-byte boundary. Every wait on the mbarrier is bounded: on expiry the
-// block records MDG_STATUS_TIMEOUT in the status word, releases its tensor memory and
-// returns.
+// [rows x 64] bf16 chunk stores row r at r * 128 bytes with its 16-byte pieces permuted by
+// XOR with (r mod 8); every chunk starts on a 1024-byte boundary. The weights are kept in
+// global memory as an image of exactly these chunks (mlp_build_image), so each slot is
+// filled by one bulk copy. Every mbarrier wait is bounded: on expiry the block records
+// MDG_STATUS_TIMEOUT in the status word, every role leaves its loop, the copies and MMAs
+// already issued are waited for (again with a bound), the tensor memory is freed and the
+// block returns.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -25,26 +38,50 @@
 namespace mdg {
 namespace {
 
-constexpr int kRows = 128;         // tile rows (UMMA M)
-constexpr int kThreads = 512;      // 16 warps: four per TMEM lane quadrant, 64 columns each
-constexpr int kActBytes = 128 * 256 * 2;   // activations [128 x 256] bf16
-constexpr int kWBytes = 256 * 256 * 2;     // largest weight matrix [256 x 256] bf16
-constexpr uint32_t kTmemCols = 256;
-constexpr int kWaitLimit = 1 << 22;        // mbarrier polls (with 64 ns back-off: ~0.3 s) before giving up
+constexpr int kRows = 128;                 // tile rows (UMMA M)
+constexpr int kEpiWarps = 16;              // four per TMEM lane quadrant
+constexpr int kProdWarp = kEpiWarps;       // producer warp
+constexpr int kMmaWarp = kEpiWarps + 1;    // MMA warp (also allocates the tensor memory)
+constexpr int kThreads = (kEpiWarps + 2) * 32;
+constexpr int kSlots = 4;
+constexpr uint32_t kSlotBytes = 32768;     // one [256 x 64] bf16 weight chunk
+constexpr uint32_t kChunkBytes = 16384;    // one [128 x 64] bf16 activation chunk
+constexpr uint32_t kOffAct = 0;            // activations [128 x 256]: four chunks
+constexpr uint32_t kOffX = 4 * kChunkBytes;  // inputs [128 x 64]: one chunk
+constexpr uint32_t kOffSlot = kOffX + kChunkBytes;
+constexpr uint32_t kDynBytes = kOffSlot + kSlots * kSlotBytes;
+constexpr uint32_t kTmemCols = 512;        // two accumulators of 256 columns
+constexpr int kLoadsPerTile = 10;          // W1, W2 chunks 0-3, W3 chunks 0-3, W4
+constexpr uint32_t kSuspendNs = 1000;      // longest suspension of one mbarrier try_wait
+constexpr int kWaitLimit = 1 << 18;        // try_waits (at most ~0.26 s) before giving up
+
+// Weight image: the chunks in the order the MMAs consume them, load i at i * 32 KB.
+//   load 0      W1 [256 x 64]
+//   loads 1-4   W2 chunk c [256 x 64]
+//   loads 5-8   W3 chunk c [256 x 64]
+//   load 9      W4 [32 x 256] as four [32 x 64] chunks of 4 KB (16 KB)
+constexpr uint32_t kImgBytes = 9 * kSlotBytes + 16384;
+static_assert(kImgBytes == 2 * (256 * 64 + 2 * 256 * 256 + 32 * 256), "the image holds every weight once");
+static_assert(kDynBytes + 1024 + 4096 <= 232448, "shared memory of one block");
+
+__device__ __forceinline__ uint32_t image_layer_base(int l)
+{
+    return l == 0 ? 0u : l == 1 ? kSlotBytes : l == 2 ? 5 * kSlotBytes : 9 * kSlotBytes;
+}
+
+// mbarriers
+enum {
+    kBarWFull = 0,                    // [kSlots] producer expect_tx; the bulk copy completes it
+    kBarWEmpty = kBarWFull + kSlots,  // [kSlots] MMA commit: the slot's MMAs are done
+    kBarXFull = kBarWEmpty + kSlots,  // producer: the tile's inputs have landed
+    kBarXEmpty,                       // MMA commit: layer 0 is done with the inputs
+    kBarAccFull,                      // [2] MMA commit: accumulator b holds a finished layer
+    kBarActFull = kBarAccFull + 2,    // [4] the 16 epilogue warps: activation chunk c written
+    kBarMmaDone = kBarActFull + 4,    // MMA commit at the end: nothing left in flight
+    kNumBars
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void cp_async16(uint32_t s, const void* g)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(g));
-}
-
-// byte offset of the 16-byte piece (row r, piece k8) of a [rows x K] K-major SW128 matrix
-__device__ __forceinline__ uint32_t sw128_offset(int r, int k8, int rows)
-{
-    const int chunk = k8 >> 3, piece = k8 & 7;
-    return (uint32_t)(chunk * rows * 128 + r * 128 + ((piece ^ (r & 7)) << 4));
-}
 
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
@@ -72,199 +109,346 @@ __device__ __forceinline__ void mma_bf16_ss(uint32_t tmem_d, uint64_t adesc, uin
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
+// The mbarrier completes once every tcgen05 operation issued so far by this thread is done.
 __device__ __forceinline__ void mma_commit(uint32_t mbar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase)
+// Wait for the phase of `parity` to complete: mbarrier.try_wait suspends the thread in
+// hardware until the phase completes or about kSuspendNs pass. Gives up when another role
+// has aborted (abort != null) or after kWaitLimit tries, which records the timeout and
+// aborts the block.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int* abort, uint32_t* status)
 {
     for (int i = 0; i < kWaitLimit; ++i) {
         uint32_t done;
         asm volatile(
-            "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
-            : "r"(mbar), "r"(phase)
+            : "r"(mbar), "r"(parity), "r"(kSuspendNs)
             : "memory");
         if (done) return true;
-        __nanosleep(64);
+        if (abort && *abort) return false;
     }
+    if (abort) *abort = 1;
+    atomicOr(status, MDG_STATUS_TIMEOUT);
     return false;
 }
 
-// 32 consecutive FP32 accumulator columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32])
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar)
 {
-    uint32_t r[32];
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// Bulk copy global -> shared; completes `bytes` of the mbarrier's transaction count.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t s, const void* g)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(g));
+}
+
+// 16 (x16) or 8 (x8) consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
+{
+    uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Issue the copy of a row-major [rows x K] bf16 matrix (K contiguous) into the SW128
-// K-major layout (cp.async, one commit group); cp_wait() completes it.
-__device__ __forceinline__ void stage_async(uint32_t s_base, const __nv_bfloat16* g, int rows, int K)
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8])
 {
-    const int pieces = rows * (K >> 3);
-    for (int i = threadIdx.x; i < pieces; i += kThreads) {
-        const int r = i / (K >> 3), k8 = i % (K >> 3);
-        cp_async16(s_base + sw128_offset(r, k8, rows), g + (size_t)r * K + k8 * 8);
-    }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-// SiLU(z) = z / (1 + exp(-z)) = z/2 (1 + tanh(z/2)): one special-function instruction
-// (tanh.approx.f32, relative error about 2^-11) instead of an exponential and a division.
-__device__ __forceinline__ float silu_tanh(float z)
+// SiLU of two pre-activations given as h = z/2: silu(z) = z / (1 + exp(-z)) = h (1 + tanh h),
+// one special-function instruction each (tanh.approx.f32, relative error about 2^-11).
+__device__ __forceinline__ __nv_bfloat162 silu_pair(float h0, float h1)
 {
-    const float h = 0.5f * z;
-    float t;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(h));
-    return fmaf(h, t, h);
-}
-
-__device__ __forceinline__ void make_operands_visible()
-{
-    // generic-proxy shared-memory writes (cp.async, st.shared) -> async proxy (tcgen05.mma)
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    float t0, t1;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t0) : "f"(h0));
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t1) : "f"(h1));
+    return __floats2bfloat162_rn(fmaf(h0, t0, h0), fmaf(h1, t1, h1));
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-    mlp_umma_kernel(const __nv_bfloat16* __restrict__ x, float* __restrict__ y, int n_tiles, const float* __restrict__ master,
-                    const __nv_bfloat16* __restrict__ w16, MlpView w, uint32_t* status)
+    mlp_umma_kernel(const __nv_bfloat16* __restrict__ x, float* __restrict__ y, int n_tiles,
+                    const uint8_t* __restrict__ w_img, const float* __restrict__ master, MlpView w, uint32_t* status)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    // 1024-byte aligned operand buffers
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* s_act = base;
-    uint8_t* s_w = base + kActBytes;
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t bars[kNumBars];
     __shared__ uint32_t s_tmem;
-    __shared__ float s_bias[3 * MDG_MLP_HIDDEN + MDG_MLP_OUT_PAD];  // b1, b2, b3, b4
+    __shared__ int s_abort;
+    // b/2 of the hidden layers (SiLU takes z/2), then the output bias
+    __shared__ __align__(16) float s_hb[3 * MDG_MLP_HIDDEN + MDG_MLP_OUT_PAD];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t mbar_a = smem_u32(&mbar);
+    const uint32_t act_a = smem_u32(base + kOffAct), x_a = smem_u32(base + kOffX), slot_a = smem_u32(base + kOffSlot);
+    const uint32_t bar0 = smem_u32(&bars[0]);
+    auto bar = [bar0](int i) { return bar0 + 8u * (uint32_t)i; };
+    volatile int* abort = &s_abort;
+
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar_a));
+        for (int i = 0; i < kNumBars; ++i) {
+            const uint32_t count = (i >= kBarActFull && i < kBarActFull + 4) ? kEpiWarps : 1;
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar(i)), "r"(count));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        s_abort = 0;
     }
-    if (warp == 0) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
-    for (int i = threadIdx.x; i < 3 * MDG_MLP_HIDDEN + MDG_MLP_OUT_PAD; i += kThreads) {
-        const int l = i < 3 * MDG_MLP_HIDDEN ? i / MDG_MLP_HIDDEN : 3;
-        s_bias[i] = master[w.b_off[l] + (i - l * MDG_MLP_HIDDEN)];
-    }
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+        for (int i = threadIdx.x; i < (l < 3 ? MDG_MLP_HIDDEN : MDG_MLP_OUT_PAD); i += kThreads)
+            s_hb[l * MDG_MLP_HIDDEN + i] = (l < 3 ? 0.5f : 1.f) * master[w.b_off[l] + i];
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = s_tmem;
-    const uint32_t act_a = smem_u32(s_act), w_a = smem_u32(s_w);
-    const int quad = warp & 3, part = warp >> 2;  // TMEM lane quadrant, column quarter
-    const int row = quad * 32 + lane;  // this thread's accumulator row (TMEM lane)
-    const uint32_t t_row = tmem + ((uint32_t)(quad * 32) << 16);
-    const int dims[5] = {MDG_MLP_IN_PAD, MDG_MLP_HIDDEN, MDG_MLP_HIDDEN, MDG_MLP_HIDDEN, MDG_MLP_OUT_PAD};
-    uint32_t phase = 0;
-    bool abort = false;  // identical in every thread (set from __syncthreads_and)
 
-    // the first tile's inputs and first-layer weights
-    if (blockIdx.x < n_tiles) {
-        stage_async(act_a, x + (size_t)blockIdx.x * kRows * MDG_MLP_IN_PAD, kRows, MDG_MLP_IN_PAD);
-        stage_async(w_a, w16 + w.w_off[0], dims[1], dims[0]);
-    }
-    for (int tile = blockIdx.x; tile < n_tiles && !abort; tile += gridDim.x) {
-        for (int l = 0; l < 4; ++l) {
-            const int K = dims[l], N = dims[l + 1];
-            cp_wait();  // this layer's weights (and, for l = 0, the tile's inputs) have landed
-            make_operands_visible();
-            if (threadIdx.x == 0) {
-                const uint32_t idesc = idesc_bf16(kRows, N);
-                for (int k16 = 0; k16 < K / 16; ++k16) {
-                    const int chunk = k16 >> 2, within = (k16 & 3) * 32;
-                    const uint64_t ad = sw128_desc(act_a + chunk * kRows * 128 + within);
-                    const uint64_t bd = sw128_desc(w_a + chunk * N * 128 + within);
-                    mma_bf16_ss(tmem, ad, bd, idesc, k16 > 0);
+    if (warp == kProdWarp) {
+        // ---------------- producer (whole warp; lane 0 issues the bulk copies) ----------------
+        int j = 0;  // weight loads issued
+        int s = 0;  // tiles of this block
+        bool ok = true;
+        auto load_x = [&](int tile) {
+            const __nv_bfloat16* src = x + (size_t)tile * kRows * MDG_MLP_IN_PAD;
+#pragma unroll 4
+            for (int i = lane; i < kRows * 8; i += 32) {
+                const int r = i >> 3, k8 = i & 7;
+                cp_async16(x_a + r * 128 + ((k8 ^ (r & 7)) << 4), src + r * MDG_MLP_IN_PAD + k8 * 8);
+            }
+        };
+        load_x(blockIdx.x);  // the grid never exceeds the tile count
+        for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++s) {
+            for (int i = 0; i < kLoadsPerTile; ++i, ++j) {
+                const int slot = j % kSlots, use = j / kSlots;
+                if (use > 0) ok = __all_sync(0xffffffffu, mbar_wait(bar(kBarWEmpty + slot), (use - 1) & 1, abort, status));
+                if (!ok) break;
+                const uint32_t bytes = i == kLoadsPerTile - 1 ? 16384u : kSlotBytes;
+                if (lane == 0) {
+                    mbar_expect_tx(bar(kBarWFull + slot), bytes);
+                    bulk_g2s(slot_a + slot * kSlotBytes, w_img + (size_t)i * kSlotBytes, bytes, bar(kBarWFull + slot));
                 }
-                mma_commit(mbar_a);
-            }
-            const bool ok = mbar_wait(mbar_a, phase);
-            phase ^= 1;
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            if (!__syncthreads_and(ok)) {
-                if (threadIdx.x == 0) atomicOr(status, MDG_STATUS_TIMEOUT);
-                abort = true;
-                break;
-            }
-            // The MMAs have consumed their operands: start the next copies now so that they
-            // overlap this layer's epilogue (the next layer's weights, or after the last layer
-            // the next tile's inputs and first-layer weights).
-            if (l < 3) {
-                stage_async(w_a, w16 + w.w_off[l + 1], dims[l + 2], dims[l + 1]);
-            } else if (tile + (int)gridDim.x < n_tiles) {
-                stage_async(act_a, x + (size_t)(tile + gridDim.x) * kRows * MDG_MLP_IN_PAD, kRows, MDG_MLP_IN_PAD);
-                stage_async(w_a, w16 + w.w_off[0], dims[1], dims[0]);
-            }
-            const float* bias = s_bias + l * MDG_MLP_HIDDEN;
-            if (l < 3) {
-                // bias + SiLU -> bf16 activations, this warp's quarter of the 256 columns
-#pragma unroll 1
-                for (int c0 = part * 64; c0 < part * 64 + 64; c0 += 32) {
-                    float v[32];
-                    tmem_ld32(t_row + c0, v);
-                    __nv_bfloat162 o[16];
-#pragma unroll
-                    for (int i = 0; i < 32; i += 2)
-                        o[i / 2] = __floats2bfloat162_rn(silu_tanh(v[i] + bias[c0 + i]),
-                                                         silu_tanh(v[i + 1] + bias[c0 + i + 1]));
-                    const uint4* o4 = reinterpret_cast<const uint4*>(o);
-#pragma unroll
-                    for (int p = 0; p < 4; ++p) {
-                        const uint32_t off = sw128_offset(row, (c0 >> 3) + p, kRows);
-                        *reinterpret_cast<uint4*>(s_act + off) = o4[p];
+                __syncwarp();
+                if (i == 0) {
+                    // this tile's inputs (issued one tile ahead) complete before layer 0 reads them
+                    asm volatile("cp.async.wait_all;\n" ::: "memory");
+                    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar(kBarXFull));
+                } else if (i == 4 && tile + (int)gridDim.x < n_tiles) {
+                    // layer 0 of this tile is done with the input buffer: fetch the next tile's
+                    ok = __all_sync(0xffffffffu, mbar_wait(bar(kBarXEmpty), s & 1, abort, status));
+                    if (!ok) {
+                        ++j;
+                        break;
                     }
+                    load_x(tile + gridDim.x);
                 }
-            } else if (part == 0) {
-                float v[32];
-                tmem_ld32(t_row, v);
-                float4* out = reinterpret_cast<float4*>(y + ((size_t)tile * kRows + row) * MDG_MLP_OUT_PAD);
-#pragma unroll
-                for (int i = 0; i < 32; i += 4)
-                    out[i / 4] = make_float4(v[i] + bias[i], v[i + 1] + bias[i + 1], v[i + 2] + bias[i + 2],
-                                             v[i + 3] + bias[i + 3]);
             }
-            // all tensor-memory reads and activation writes done before the next MMA
+        }
+        // drain: every copy issued has landed before the block may exit
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        if (lane == 0)
+            for (int slot = 0; slot < kSlots && slot < j; ++slot) {
+                const int uses = (j - 1 - slot) / kSlots + 1;  // loads issued into this slot
+                mbar_wait(bar(kBarWFull + slot), (uses - 1) & 1, nullptr, status);
+            }
+        __syncwarp();
+    } else if (warp == kMmaWarp) {
+        // ---------------- MMA issue (one thread) ----------------
+        if (lane == 0) {
+            const uint32_t id_h = idesc_bf16(kRows, MDG_MLP_HIDDEN), id_o = idesc_bf16(kRows, MDG_MLP_OUT_PAD);
+            int j = 0, s = 0;
+            uint32_t n_act = 0;  // completed activation phases (one per hidden-layer epilogue)
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++s) {
+                // layer 0: x [128 x 64] . W1^T -> accumulator 0
+                ok = mbar_wait(bar(kBarXFull), s & 1, abort, status) &&
+                     mbar_wait(bar(kBarWFull + j % kSlots), (j / kSlots) & 1, abort, status);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                {
+                    const uint32_t wsl = slot_a + (j % kSlots) * kSlotBytes;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        mma_bf16_ss(tmem, sw128_desc(x_a + k * 32), sw128_desc(wsl + k * 32), id_h, k != 0);
+                    mma_commit(bar(kBarWEmpty + j % kSlots));
+                    mma_commit(bar(kBarXEmpty));
+                    mma_commit(bar(kBarAccFull + 0));
+                    ++j;
+                }
+                // layers 1, 2: chunk c of the activations as soon as the epilogue has written it
+                for (int l = 1; l < 3 && ok; ++l) {
+                    const uint32_t d = tmem + (uint32_t)(l & 1) * 256;
+                    for (int c = 0; c < 4; ++c, ++j) {
+                        ok = mbar_wait(bar(kBarActFull + c), n_act & 1, abort, status) &&
+                             mbar_wait(bar(kBarWFull + j % kSlots), (j / kSlots) & 1, abort, status);
+                        if (!ok) break;
+                        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                        const uint32_t asl = act_a + c * kChunkBytes, wsl = slot_a + (j % kSlots) * kSlotBytes;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            mma_bf16_ss(d, sw128_desc(asl + k * 32), sw128_desc(wsl + k * 32), id_h, (c | k) != 0);
+                        mma_commit(bar(kBarWEmpty + j % kSlots));
+                    }
+                    if (!ok) break;
+                    ++n_act;
+                    mma_commit(bar(kBarAccFull + (l & 1)));
+                }
+                if (!ok) break;
+                // layer 3: W4 [32 x 256] in one slot as four [32 x 64] chunks -> accumulator 1
+                ok = mbar_wait(bar(kBarWFull + j % kSlots), (j / kSlots) & 1, abort, status);
+                const uint32_t wsl = slot_a + (j % kSlots) * kSlotBytes;
+                for (int c = 0; c < 4 && ok; ++c) {
+                    ok = mbar_wait(bar(kBarActFull + c), n_act & 1, abort, status);
+                    if (!ok) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    const uint32_t asl = act_a + c * kChunkBytes, bsl = wsl + c * 4096;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        mma_bf16_ss(tmem + 256, sw128_desc(asl + k * 32), sw128_desc(bsl + k * 32), id_o, (c | k) != 0);
+                }
+                if (!ok) break;
+                ++n_act;
+                mma_commit(bar(kBarWEmpty + j % kSlots));
+                mma_commit(bar(kBarAccFull + 1));
+                ++j;
+            }
+            // nothing in flight before the tensor memory is freed
+            mma_commit(bar(kBarMmaDone));
+            mbar_wait(bar(kBarMmaDone), 0, nullptr, status);
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue (warps 0-15) ----------------
+        const int q = warp & 3, p = warp >> 2;  // TMEM lane quadrant, column part
+        const int row = q * 32 + lane;
+        const uint32_t t_row = tmem + ((uint32_t)(q * 32) << 16);
+        const int sw = row & 7;
+        uint32_t n_acc0 = 0, n_acc1 = 0;  // completed phases of the two accumulators
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+            for (int l = 0; l < 3 && ok; ++l) {
+                const int b = l & 1;
+                ok = __all_sync(0xffffffffu, mbar_wait(bar(kBarAccFull + b), (b ? n_acc1 : n_acc0) & 1, abort, status));
+                if (!ok) break;
+                n_acc0 += 1 - b;
+                n_acc1 += b;
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const float4* hb4 = reinterpret_cast<const float4*>(s_hb + l * MDG_MLP_HIDDEN);
+#pragma unroll 1
+                for (int c = 0; c < 4; ++c) {
+                    const int col = c * 64 + p * 16;
+                    float v[16];
+                    tmem_ld16(t_row + (uint32_t)b * 256 + col, v);
+                    float hb[16];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float4 t = hb4[col / 4 + i];
+                        hb[4 * i] = t.x, hb[4 * i + 1] = t.y, hb[4 * i + 2] = t.z, hb[4 * i + 3] = t.w;
+                    }
+                    __nv_bfloat162 o[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        o[i] = silu_pair(fmaf(v[2 * i], 0.5f, hb[2 * i]), fmaf(v[2 * i + 1], 0.5f, hb[2 * i + 1]));
+                    uint8_t* dst = base + kOffAct + c * kChunkBytes + row * 128;
+                    *reinterpret_cast<uint4*>(dst + (((2 * p) ^ sw) << 4)) = *reinterpret_cast<const uint4*>(&o[0]);
+                    *reinterpret_cast<uint4*>(dst + (((2 * p + 1) ^ sw) << 4)) = *reinterpret_cast<const uint4*>(&o[4]);
+                    // generic-proxy stores -> the MMAs' async proxy; TMEM reads done before the arrive
+                    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar(kBarActFull + c));
+                }
+            }
+            if (!ok) break;
+            // output layer: accumulator 1, 32 columns, eight per column part
+            ok = __all_sync(0xffffffffu, mbar_wait(bar(kBarAccFull + 1), n_acc1 & 1, abort, status));
+            if (!ok) break;
+            ++n_acc1;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            float v[8];
+            tmem_ld8(t_row + 256 + p * 8, v);
+            const float* b4 = s_hb + 3 * MDG_MLP_HIDDEN + p * 8;
+            float4* out = reinterpret_cast<float4*>(y + ((size_t)tile * kRows + row) * MDG_MLP_OUT_PAD + p * 8);
+            out[0] = make_float4(v[0] + b4[0], v[1] + b4[1], v[2] + b4[2], v[3] + b4[3]);
+            out[1] = make_float4(v[4] + b4[4], v[5] + b4[5], v[6] + b4[6], v[7] + b4[7]);
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-            __syncthreads();
         }
     }
-    cp_wait();  // no copy left in flight
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
-    if (warp == 0)
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (warp == kMmaWarp)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
+}
+
+// One thread per 16-byte piece (8 consecutive k of one row n) of every weight matrix.
+__global__ void build_image_kernel(const __nv_bfloat16* __restrict__ w16, MlpView w, uint8_t* __restrict__ img)
+{
+    const int dims[5] = {MDG_MLP_IN_PAD, MDG_MLP_HIDDEN, MDG_MLP_HIDDEN, MDG_MLP_HIDDEN, MDG_MLP_OUT_PAD};
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int l = 0; l < 4; ++l) {
+        const int K = dims[l], N = dims[l + 1], pieces = N * K / 8;
+        if (i < pieces) {
+            const int n = i / (K / 8), k8 = i % (K / 8);
+            const int c = k8 >> 3, kk8 = k8 & 7;
+            const uint32_t off = image_layer_base(l) + (uint32_t)c * N * 128 + n * 128 + ((kk8 ^ (n & 7)) << 4);
+            *reinterpret_cast<uint4*>(img + off) =
+                *reinterpret_cast<const uint4*>(w16 + w.w_off[l] + (size_t)n * K + k8 * 8);
+            return;
+        }
+        i -= pieces;
+    }
 }
 
 }  // namespace
 
-constexpr size_t kUmmaSmem = 1024 + kActBytes + kWBytes;
+constexpr size_t kUmmaSmem = 1024 + kDynBytes;
 
-cudaError_t mlp_forward_umma(const MlpView& w, const void* x, int B, float* y, uint32_t* status, cudaStream_t s)
+size_t mlp_image_bytes() { return kImgBytes; }
+
+cudaError_t mlp_build_image(const MlpView& w, void* img, cudaStream_t s)
+{
+    const int pieces = (int)(kImgBytes / 16);
+    build_image_kernel<<<(pieces + 255) / 256, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(w.w16), w,
+                                                             static_cast<uint8_t*>(img));
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_forward_umma(const MlpView& w, const void* img, const void* x, int B, float* y, uint32_t* status,
+                             cudaStream_t s)
 {
     if (B % kRows) return cudaErrorInvalidValue;
     const int n_tiles = B / kRows;
@@ -282,8 +466,8 @@ cudaError_t mlp_forward_umma(const MlpView& w, const void* x, int B, float* y, u
     int n_sm = 152;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     const int grid = n_tiles < n_sm ? n_tiles : n_sm;
-    mlp_umma_kernel<<<grid, kThreads, kUmmaSmem, s>>>(static_cast<const __nv_bfloat16*>(x), y, n_tiles, w.master,
-                                                      static_cast<const __nv_bfloat16*>(w.w16), w, status);
+    mlp_umma_kernel<<<grid, kThreads, kUmmaSmem, s>>>(static_cast<const __nv_bfloat16*>(x), y, n_tiles,
+                                                      static_cast<const uint8_t*>(img), w.master, w, status);
     return cudaGetLastError();
 }
 
