@@ -54,6 +54,7 @@ constexpr uint32_t kTmemCols = 512;        // two accumulators of 256 columns
 constexpr int kLoadsPerTile = 10;          // W1, W2 chunks 0-3, W3 chunks 0-3, W4
 constexpr uint32_t kSuspendNs = 1000;      // longest suspension of one mbarrier try_wait
 constexpr int kWaitLimit = 1 << 18;        // try_waits (at most ~0.26 s) before giving up
+constexpr int kSpinLimit = 1 << 22;        // polls of a spinning wait (a few tenths of a second)
 
 // Weight image: the chunks in the order the MMAs consume them, load i at i * 32 KB.
 //   load 0      W1 [256 x 64]
@@ -116,12 +117,24 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar)
                  : "memory");
 }
 
-// Wait for the phase of `parity` to complete: mbarrier.try_wait suspends the thread in
-// hardware until the phase completes or about kSuspendNs pass. Gives up when another role
-// has aborted (abort != null) or after kWaitLimit tries, which records the timeout and
-// aborts the block.
+__device__ __forceinline__ bool mbar_test(uint32_t mbar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Wait for the phase of `parity` to complete: one non-blocking test, then mbarrier.try_wait,
+// which suspends the thread in hardware until the phase completes or about kSuspendNs pass.
+// Gives up when another role has aborted (abort != null) or after kWaitLimit tries, which
+// records the timeout and aborts the block.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int* abort, uint32_t* status)
 {
+    if (mbar_test(mbar, parity)) return true;
     for (int i = 0; i < kWaitLimit; ++i) {
         uint32_t done;
         asm volatile(
@@ -133,6 +146,22 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volati
         if (abort && *abort) return false;
     }
     if (abort) *abort = 1;
+    atomicOr(status, MDG_STATUS_TIMEOUT);
+    return false;
+}
+
+// The same for waits on the critical path between MMAs and epilogue: poll with test_wait
+// (a suspended thread wakes up later than a polling one), backing off by `sleep_ns` between
+// polls (0: none), at most kSpinLimit polls.
+__device__ __forceinline__ bool mbar_spin(uint32_t mbar, uint32_t parity, volatile int* abort, uint32_t* status,
+                                          int sleep_ns)
+{
+    for (int i = 0; i < kSpinLimit; ++i) {
+        if (mbar_test(mbar, parity)) return true;
+        if ((i & 63) == 63 && *abort) return false;
+        if (sleep_ns) __nanosleep(sleep_ns);
+    }
+    *abort = 1;
     atomicOr(status, MDG_STATUS_TIMEOUT);
     return false;
 }
@@ -308,21 +337,30 @@ __global__ void __launch_bounds__(kThreads, 1)
                     mma_commit(bar(kBarAccFull + 0));
                     ++j;
                 }
-                // layers 1, 2: chunk c of the activations as soon as the epilogue has written it
+                // layers 1, 2: chunk c of the activations as soon as the epilogue has written it.
+                // The tensor cores take ~128 cycles per MMA and this thread can run only about
+                // one MMA ahead of them, so the bookkeeping of the next group (the previous
+                // group's commit, non-blocking tests of the next group's barriers) is spread
+                // between the four MMAs of the current one.
                 for (int l = 1; l < 3 && ok; ++l) {
                     const uint32_t d = tmem + (uint32_t)(l & 1) * 256;
+                    bool act_ok = false, w_ok = false;  // the group's barriers, tested ahead
                     for (int c = 0; c < 4; ++c, ++j) {
-                        ok = mbar_wait(bar(kBarActFull + c), n_act & 1, abort, status) &&
-                             mbar_wait(bar(kBarWFull + j % kSlots), (j / kSlots) & 1, abort, status);
+                        ok = (act_ok || mbar_spin(bar(kBarActFull + c), n_act & 1, abort, status, 0)) &&
+                             (w_ok || mbar_wait(bar(kBarWFull + j % kSlots), (j / kSlots) & 1, abort, status));
                         if (!ok) break;
                         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                         const uint32_t asl = act_a + c * kChunkBytes, wsl = slot_a + (j % kSlots) * kSlotBytes;
-#pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            mma_bf16_ss(d, sw128_desc(asl + k * 32), sw128_desc(wsl + k * 32), id_h, (c | k) != 0);
-                        mma_commit(bar(kBarWEmpty + j % kSlots));
+                        mma_bf16_ss(d, sw128_desc(asl), sw128_desc(wsl), id_h, c != 0);
+                        if (c > 0) mma_commit(bar(kBarWEmpty + (j - 1) % kSlots));
+                        mma_bf16_ss(d, sw128_desc(asl + 32), sw128_desc(wsl + 32), id_h, 1);
+                        act_ok = c < 3 && mbar_test(bar(kBarActFull + c + 1), n_act & 1);
+                        mma_bf16_ss(d, sw128_desc(asl + 64), sw128_desc(wsl + 64), id_h, 1);
+                        w_ok = c < 3 && mbar_test(bar(kBarWFull + (j + 1) % kSlots), ((j + 1) / kSlots) & 1);
+                        mma_bf16_ss(d, sw128_desc(asl + 96), sw128_desc(wsl + 96), id_h, 1);
                     }
                     if (!ok) break;
+                    mma_commit(bar(kBarWEmpty + (j - 1) % kSlots));
                     ++n_act;
                     mma_commit(bar(kBarAccFull + (l & 1)));
                 }
@@ -330,14 +368,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // layer 3: W4 [32 x 256] in one slot as four [32 x 64] chunks -> accumulator 1
                 ok = mbar_wait(bar(kBarWFull + j % kSlots), (j / kSlots) & 1, abort, status);
                 const uint32_t wsl = slot_a + (j % kSlots) * kSlotBytes;
+                bool act_ok = false;
                 for (int c = 0; c < 4 && ok; ++c) {
-                    ok = mbar_wait(bar(kBarActFull + c), n_act & 1, abort, status);
+                    ok = act_ok || mbar_spin(bar(kBarActFull + c), n_act & 1, abort, status, 0);
                     if (!ok) break;
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                     const uint32_t asl = act_a + c * kChunkBytes, bsl = wsl + c * 4096;
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        mma_bf16_ss(tmem + 256, sw128_desc(asl + k * 32), sw128_desc(bsl + k * 32), id_o, (c | k) != 0);
+                    mma_bf16_ss(tmem + 256, sw128_desc(asl), sw128_desc(bsl), id_o, c != 0);
+                    mma_bf16_ss(tmem + 256, sw128_desc(asl + 32), sw128_desc(bsl + 32), id_o, 1);
+                    act_ok = c < 3 && mbar_test(bar(kBarActFull + c + 1), n_act & 1);
+                    mma_bf16_ss(tmem + 256, sw128_desc(asl + 64), sw128_desc(bsl + 64), id_o, 1);
+                    mma_bf16_ss(tmem + 256, sw128_desc(asl + 96), sw128_desc(bsl + 96), id_o, 1);
                 }
                 if (!ok) break;
                 ++n_act;
@@ -361,7 +402,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
             for (int l = 0; l < 3 && ok; ++l) {
                 const int b = l & 1;
-                ok = __all_sync(0xffffffffu, mbar_wait(bar(kBarAccFull + b), (b ? n_acc1 : n_acc0) & 1, abort, status));
+                ok = __all_sync(0xffffffffu, mbar_spin(bar(kBarAccFull + b), (b ? n_acc1 : n_acc0) & 1, abort, status, 32));
                 if (!ok) break;
                 n_acc0 += 1 - b;
                 n_acc1 += b;
@@ -394,7 +435,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (!ok) break;
             // output layer: accumulator 1, 32 columns, eight per column part
-            ok = __all_sync(0xffffffffu, mbar_wait(bar(kBarAccFull + 1), n_acc1 & 1, abort, status));
+            ok = __all_sync(0xffffffffu, mbar_spin(bar(kBarAccFull + 1), n_acc1 & 1, abort, status, 32));
             if (!ok) break;
             ++n_acc1;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
