@@ -805,6 +805,13 @@ __global__ void __launch_bounds__(1024) surrogate_prepare_kernel(const Surrogate
     }
     s_pos[t] = make_float4(d.p[0], d.p[1], d.p[2], 0.f);
     s_vel[t] = make_float4(d.v[0], d.v[1], d.v[2], 0.f);
+    // the normalisation (mean, 1/std, lo, hi of every input), read by every drone
+    __shared__ float s_nrm[4][MDG_MLP_IN];
+    for (int i = t; i < 4 * MDG_MLP_IN; i += B) {
+        const int r = i / MDG_MLP_IN, k = i % MDG_MLP_IN;
+        const float* src = r == 0 ? sa.in_mean : r == 1 ? sa.in_inv_std : r == 2 ? sa.in_lo : sa.in_hi;
+        s_nrm[r][k] = src[k];
+    }
     __syncthreads();
     bool ood = false;
     if (active) {
@@ -813,19 +820,27 @@ __global__ void __launch_bounds__(1024) surrogate_prepare_kernel(const Surrogate
         knn_best4<0>(t - env.ls, d.p, s_pos + env.ls, env.N, bi);
         knn_features(bi, d, s_pos + env.ls, s_vel + env.ls, f);
         surrogate_inputs(d, rpm, f, x);
-        __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(sa.x) + 64 * g);
+        // the 128-byte input row in eight 16-byte stores of eight standardised inputs each
+        uint4* row = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(sa.x) + 64 * g);
 #pragma unroll
-        for (int k = 0; k < 64; k += 2) {
-            float z0 = 0.f, z1 = 0.f;
-            if (k < 41) {
-                z0 = (x[k] - sa.in_mean[k]) * sa.in_inv_std[k];
-                ood = ood || !(fabsf(z0) <= sa.ood_z) || !(x[k] >= sa.in_lo[k] && x[k] <= sa.in_hi[k]);
+        for (int q = 0; q < 8; ++q) {
+            uint32_t o[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int k = 8 * q + 2 * i;
+                float z0 = 0.f, z1 = 0.f;
+                if (k < 41) {
+                    z0 = (x[k] - s_nrm[0][k]) * s_nrm[1][k];
+                    ood = ood || !(fabsf(z0) <= sa.ood_z) || !(x[k] >= s_nrm[2][k] && x[k] <= s_nrm[3][k]);
+                }
+                if (k + 1 < 41) {
+                    z1 = (x[k + 1] - s_nrm[0][k + 1]) * s_nrm[1][k + 1];
+                    ood = ood || !(fabsf(z1) <= sa.ood_z) || !(x[k + 1] >= s_nrm[2][k + 1] && x[k + 1] <= s_nrm[3][k + 1]);
+                }
+                const __nv_bfloat162 zz = __floats2bfloat162_rn(z0, z1);
+                o[i] = *reinterpret_cast<const uint32_t*>(&zz);
             }
-            if (k + 1 < 41) {
-                z1 = (x[k + 1] - sa.in_mean[k + 1]) * sa.in_inv_std[k + 1];
-                ood = ood || !(fabsf(z1) <= sa.ood_z) || !(x[k + 1] >= sa.in_lo[k + 1] && x[k + 1] <= sa.in_hi[k + 1]);
-            }
-            o[k / 2] = __floats2bfloat162_rn(z0, z1);
+            row[q] = make_uint4(o[0], o[1], o[2], o[3]);
         }
         if (ood) {
             const int e = (int)((tile.first_drone + env.ls) / env.N);  // uniform batches
