@@ -163,6 +163,23 @@ int mdg_step(mdg_handle h, float* state, const float* action, int32_t action_typ
 int mdg_step_obs(mdg_handle h, float* state, const float* action, int32_t action_type, int32_t n_substeps,
                  float* kin, int32_t* nbr_idx, float* nbr_rel, void* stream);
 
+/* mdg_step_obs with the actions read from, and the observations written to, page-locked
+ * host memory that the device can address (cudaHostAlloc, or cudaHostRegister with
+ * cudaHostRegisterMapped): the step kernel itself loads the actions and stores the
+ * observations across the host link, so the transfers overlap its arithmetic and no
+ * separate copies are issued. The state stays in device memory. This is the call for a
+ * host-side consumer of every step (a learner, a logger); the paper's environment returns
+ * observations to the host after every step in the same way (Section 3.4.2).
+ *   state                  as for mdg_step (device memory)
+ *   action_host            page-locked float32 [n_drones][4], 16-byte aligned
+ *   kin_host, nbr_idx_host, nbr_rel_host (may be NULL)   page-locked, layouts of mdg_obs
+ * The outputs are complete once `stream` has passed the step (synchronise on it or on an
+ * event recorded after the call before reading them).
+ * Errors: MDG_ERR_ARG when a buffer is not mapped page-locked host memory or as
+ * mdg_step_obs; MDG_ERR_CUDA. */
+int mdg_step_obs_host(mdg_handle h, float* state, const float* action_host, int32_t action_type, int32_t n_substeps,
+                      float* kin_host, int32_t* nbr_idx_host, float* nbr_rel_host, void* stream);
+
 /* The PID controller alone (PIDControl.computeControl, Section 4.2.1): for every
  * drone, from its state and waypoint [x, y, z, yaw], the four RPMs, the position
  * error and the yaw error; the integrals in state planes 3-4 are updated in place.

@@ -82,6 +82,7 @@ _SIGNATURES = {
     "mdg_features": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "mdg_surrogate_step": ([_VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, _VP, _VP],
                            ctypes.c_int),
+    "mdg_step_obs_host": ([_VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP, _VP], ctypes.c_int),
     "mdg_step_obs_noalloc": ([_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP,
                               _VP, _VP, _VP], ctypes.c_int),
 }
@@ -166,6 +167,24 @@ def _ptr(t, name, dtype, shape=None):
         raise TypeError(f"{name} must be a torch tensor")
     if t.device.type != "cuda":
         raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_ptr(t, name, dtype, shape=None):
+    """Pointer of a page-locked (pinned) CPU tensor; the library checks that it is mapped."""
+    torch = _torch()
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.device.type != "cpu" or not t.is_pinned():
+        raise ValueError(f"{name} must be a pinned CPU tensor")
     if t.dtype != dtype:
         raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
     if not t.is_contiguous():
@@ -298,6 +317,20 @@ class Handle:
                                   _ptr(nbr_idx, "nbr_idx", torch.int32, (self.n, NBR_K)),
                                   _ptr(nbr_rel, "nbr_rel", torch.float32, (self.n, NBR_K * NBR_FEAT)),
                                   _stream(stream)))
+
+    def step_obs_host(self, state, action_host, action_type: int, n_substeps, kin_host, nbr_idx_host,
+                      nbr_rel_host=None, stream=None):
+        """step_obs with the actions and observations in pinned host tensors, read and written
+        by the step kernel itself (mdg_step_obs_host); the state stays on the device."""
+        torch = _torch()
+        _check(lib().mdg_step_obs_host(self._h, _ptr(state, "state", torch.float32, (STATE_PLANES, self.n, 4)),
+                                       _host_ptr(action_host, "action_host", torch.float32, (self.n, 4)),
+                                       int(action_type), int(n_substeps),
+                                       _host_ptr(kin_host, "kin_host", torch.float32, (self.n, KIN_DIM)),
+                                       _host_ptr(nbr_idx_host, "nbr_idx_host", torch.int32, (self.n, NBR_K)),
+                                       _host_ptr(nbr_rel_host, "nbr_rel_host", torch.float32,
+                                                 (self.n, NBR_K * NBR_FEAT)),
+                                       _stream(stream)))
 
     def pid(self, state, waypoints, rpm_out, pos_err=None, yaw_err=None, stream=None):
         torch = _torch()

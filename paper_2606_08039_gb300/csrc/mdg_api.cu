@@ -549,7 +549,8 @@ int32_t mdg_get_block_size(mdg_handle h)
 }
 
 static int step_common(mdg_handle h, float* state, const float* action, int32_t action_type, int32_t n_substeps,
-                       float* kin, int32_t* nbr_idx, float* nbr_rel, bool with_obs, void* stream)
+                       float* kin, int32_t* nbr_idx, float* nbr_rel, bool with_obs, void* stream,
+                       bool obs_host = false)
 {
     if (!h) return fail(MDG_ERR_ARG, "mdg_step: NULL handle");
     if (action_type != MDG_ACT_RPM && action_type != MDG_ACT_PID && action_type != MDG_ACT_MIXED)
@@ -575,6 +576,7 @@ static int step_common(mdg_handle h, float* state, const float* action, int32_t 
     a.nbr_rel = nbr_rel;
     a.n_sub = n_substeps;
     a.act_type = action_type;
+    a.obs_host = obs_host ? 1 : 0;
     cudaError_t e = mdg::launch_step(a, h->n_tiles, h->block, with_obs, h->uniform_flags, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "mdg_step: launch");
     return MDG_OK;
@@ -589,6 +591,41 @@ int mdg_step_obs(mdg_handle h, float* state, const float* action, int32_t action
                  float* kin, int32_t* nbr_idx, float* nbr_rel, void* stream)
 {
     return step_common(h, state, action, action_type, n_substeps, kin, nbr_idx, nbr_rel, true, stream);
+}
+
+// The device address of page-locked, mapped host memory (NULL stays NULL).
+static int mapped_ptr(const void* host, void** dev, const char* name)
+{
+    *dev = nullptr;
+    if (!host) return MDG_OK;
+    cudaPointerAttributes at{};
+    cudaError_t e = cudaPointerGetAttributes(&at, host);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MDG_ERR_ARG, "mdg_step_obs_host: %s: %s", name, cudaGetErrorString(e));
+    }
+    if (at.type != cudaMemoryTypeHost || !at.devicePointer)
+        return fail(MDG_ERR_ARG, "mdg_step_obs_host: %s is not mapped page-locked host memory", name);
+    *dev = at.devicePointer;
+    return MDG_OK;
+}
+
+int mdg_step_obs_host(mdg_handle h, float* state, const float* action_host, int32_t action_type, int32_t n_substeps,
+                      float* kin_host, int32_t* nbr_idx_host, float* nbr_rel_host, void* stream)
+{
+    if (!h) return fail(MDG_ERR_ARG, "mdg_step_obs_host: NULL handle");
+    if (h->n_drones == 0) return MDG_OK;
+    if (!action_host || !kin_host || !nbr_idx_host) return fail(MDG_ERR_ARG, "mdg_step_obs_host: NULL buffer");
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(MDG_ERR_CUDA, "mdg_step_obs_host: cannot select device %d", h->device);
+    void *act = nullptr, *kin = nullptr, *idx = nullptr, *rel = nullptr;
+    int rc;
+    if ((rc = mapped_ptr(action_host, &act, "action_host")) != MDG_OK) return rc;
+    if ((rc = mapped_ptr(kin_host, &kin, "kin_host")) != MDG_OK) return rc;
+    if ((rc = mapped_ptr(nbr_idx_host, &idx, "nbr_idx_host")) != MDG_OK) return rc;
+    if ((rc = mapped_ptr(nbr_rel_host, &rel, "nbr_rel_host")) != MDG_OK) return rc;
+    return step_common(h, state, static_cast<const float*>(act), action_type, n_substeps, static_cast<float*>(kin),
+                       static_cast<int32_t*>(idx), static_cast<float*>(rel), true, stream, true);
 }
 
 int mdg_pid(mdg_handle h, float* state, const float* waypoints, float* rpm_out, float* pos_err, float* yaw_err,

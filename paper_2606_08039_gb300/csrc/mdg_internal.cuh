@@ -56,6 +56,7 @@ struct StepArgs {
     int uniform_N;            // > 0: every environment has this many drones (arithmetic tiles)
     int envs_per_tile;        // uniform batches: environments per block
     int uniform_bits;         // uniform batches: kTileAnyDW | kTileWarpLocal for every tile
+    int obs_host;             // 1: observations go to host memory, written through per-warp staging
     DevConsts c;
 };
 

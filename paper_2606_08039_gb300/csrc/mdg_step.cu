@@ -276,17 +276,25 @@ __device__ __forceinline__ bool finite_state(const Drone& d)
     return ok;
 }
 
-// KIN observation [p, q, roll/pitch/yaw, v, w, a_prev] as five float4 stores.
-__device__ __forceinline__ void write_kin(float* __restrict__ kin, long long g, const Drone& d, const float a[4])
+// KIN observation [p, q, roll/pitch/yaw, v, w, a_prev] as five float4.
+__device__ __forceinline__ void kin_values(const Drone& d, const float a[4], float4 o[5])
 {
     float roll, pitch, yaw;
     rpy_of(d.q, roll, pitch, yaw);
-    float4* o = reinterpret_cast<float4*>(kin + 20 * g);
     o[0] = make_float4(d.p[0], d.p[1], d.p[2], d.q[0]);
     o[1] = make_float4(d.q[1], d.q[2], d.q[3], roll);
     o[2] = make_float4(pitch, yaw, d.v[0], d.v[1]);
     o[3] = make_float4(d.v[2], d.w[0], d.w[1], d.w[2]);
     o[4] = make_float4(a[0], a[1], a[2], a[3]);
+}
+
+__device__ __forceinline__ void write_kin(float* __restrict__ kin, long long g, const Drone& d, const float a[4])
+{
+    float4 v[5];
+    kin_values(d, a, v);
+    float4* o = reinterpret_cast<float4*>(kin + 20 * g);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) o[k] = v[k];
 }
 
 // The 4 nearest other drones of the environment (squared distance rounded in the
@@ -363,10 +371,58 @@ __device__ __forceinline__ void write_knn(int4* __restrict__ nbr_idx, float* __r
     }
 }
 
+// Observations for host memory: a lane's KIN (80 B) and feature (96 B) rows are strided
+// 16-byte pieces, which the host link carries at a quarter of its rate. Each warp stages
+// its 32 consecutive rows in shared memory (`stage`: 192 float4 of its own) and writes the
+// contiguous span in 16-byte pieces, lane by lane. Active lanes form a prefix of the warp;
+// every lane of the warp calls this.
+template <int kN>
+__device__ __forceinline__ void write_obs_staged(const StepArgs& a, float4* stage, bool active, long long g, int lane,
+                                                 long long env_first, int j, const Drone& d, const float rpm[4],
+                                                 const float4* env_pos, const float4* env_vel, int N_rt)
+{
+    const int n_act = __popc(__ballot_sync(0xffffffffu, active));
+    const long long g0 = g - lane;
+    if (active) {
+        float4 v[5];
+        kin_values(d, rpm, v);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) stage[lane * 5 + k] = v[k];
+    }
+    __syncwarp();
+    float4* kin = reinterpret_cast<float4*>(a.kin) + g0 * 5;
+    for (int i = lane; i < n_act * 5; i += 32) kin[i] = stage[i];
+    __syncwarp();
+    if (active) {
+        int bi[4];
+        knn_best4<kN>(j, d.p, env_pos, N_rt, bi);
+        int4 idx;
+        idx.x = bi[0] >= 0 ? (int)(env_first + bi[0]) : -1;
+        idx.y = bi[1] >= 0 ? (int)(env_first + bi[1]) : -1;
+        idx.z = bi[2] >= 0 ? (int)(env_first + bi[2]) : -1;
+        idx.w = bi[3] >= 0 ? (int)(env_first + bi[3]) : -1;
+        a.nbr_idx[g] = idx;  // 16 bytes per lane, contiguous across the warp
+        if (a.nbr_rel) {
+            float f[24];
+            knn_features(bi, d, env_pos, env_vel, f);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) stage[lane * 6 + k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+        }
+    }
+    __syncwarp();
+    if (a.nbr_rel) {
+        float4* rel = reinterpret_cast<float4*>(a.nbr_rel) + g0 * 6;
+        for (int i = lane; i < n_act * 6; i += 32) rel[i] = stage[i];
+    }
+}
+
 // Shared-memory layout of the tile kernels (B = blockDim.x):
 //   float4 pos[2][B] (double-buffered substep snapshot), float4 vel[B],
 //   int off[B + 1] (tile-relative env offsets), int info[B] (flags | action type << 8)
 __host__ __device__ constexpr size_t tile_smem_bytes(int B) { return (size_t)B * 48 + (size_t)(2 * B + 1) * 4; }
+// ... followed, for observations to host memory, by 192 float4 of staging per warp
+__host__ __device__ constexpr size_t obs_stage_offset(int B) { return (tile_smem_bytes(B) + 15) / 16 * 16; }
+__host__ __device__ constexpr size_t obs_stage_bytes(int B) { return (size_t)(B / 32) * 192 * 16; }
 
 // The block's tile: whole environments, given by the host's tile table, or computed
 // arithmetically when every environment has the same size (uniform batches).
@@ -519,7 +575,12 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
         pb[t] = make_float4(d.p[0], d.p[1], d.p[2], 0.f);
         s_vel[t] = make_float4(d.v[0], d.v[1], d.v[2], 0.f);
         __syncthreads();
-        if (active) {
+        if (a.obs_host) {
+            float4* stage = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem) + obs_stage_offset(B)) +
+                            (t >> 5) * 192;
+            write_obs_staged<kN>(a, stage, active, g, t & 31, tile.first_drone + env.ls, t - env.ls, d, rpm,
+                                 pb + env.ls, s_vel + env.ls, env.N);
+        } else if (active) {
             write_kin(a.kin, g, d, rpm);
             write_knn<kN>(a.nbr_idx, a.nbr_rel, g, tile.first_drone + env.ls, t - env.ls, d, pb + env.ls,
                           s_vel + env.ls, env.N);
@@ -974,7 +1035,7 @@ static cudaError_t tile_kernels_setup()
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
-    const int smem = (int)tile_smem_bytes(1024);
+    const int smem = (int)(obs_stage_offset(1024) + obs_stage_bytes(1024));
 #define MDG_ATTR(F, NN)                                                                                     \
     if ((e = cudaFuncSetAttribute(step_kernel<true, F, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                   smem)) != cudaSuccess ||                                                  \
@@ -999,7 +1060,8 @@ cudaError_t launch_step(const StepArgs& a, int n_tiles, int block, bool with_obs
     const int N = a.uniform_N;
     void* fn = with_obs ? step_kernel_ptr<true>(flags, N, block) : step_kernel_ptr<false>(flags, N, block);
     void* args[] = {const_cast<StepArgs*>(&a)};
-    return cudaLaunchKernel(fn, dim3(n_tiles), dim3(block), args, tile_smem_bytes(block), s);
+    const size_t smem = with_obs && a.obs_host ? obs_stage_offset(block) + obs_stage_bytes(block) : tile_smem_bytes(block);
+    return cudaLaunchKernel(fn, dim3(n_tiles), dim3(block), args, smem, s);
 }
 
 static size_t rollout_smem_bytes(int B) { return (size_t)B * 48 + (size_t)(3 * B + 2) * 4; }
