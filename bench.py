@@ -52,7 +52,7 @@ BYTES_PER_DRONE_STEP = STATE_BYTES_READ + ACTION_BYTES + STATE_BYTES_WRITE + OBS
 # DRAM traffic of one step-kernel launch on the full-aero workload, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel source whose
 # sha256 prefix is recorded with it; profiles/ holds the capture's summary.
-NCU_TRAFFIC = {"kernel_sha": "511331ce3f40a1ac", "bytes": 6322944 + 256}
+NCU_TRAFFIC = {"kernel_sha": "a9ee7e61a6ed2fdb", "bytes": 6331648 + 512}
 
 
 def kernel_sha() -> str:
