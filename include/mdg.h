@@ -49,6 +49,7 @@ extern "C" {
 #define MDG_ERR_CUDA (-2)        /* a CUDA runtime call failed */
 #define MDG_ERR_NONFINITE (-3)   /* reported through mdg_status: a state became non-finite */
 #define MDG_ERR_UNSUPPORTED (-4) /* a valid request this build does not implement */
+#define MDG_ERR_TIMEOUT (-5)     /* mdg_sync: the stream was still busy when its limit ran out */
 
 /* Physics-mode bits per environment (Table "Physics modes"): any subset of the
  * three aerodynamic effects on top of the explicit integrator. */
@@ -252,6 +253,15 @@ int mdg_autotune(mdg_handle h, float* state, const float* actions, int32_t actio
  * to *first_drone (either may be NULL). Returns MDG_ERR_NONFINITE if the non-finite
  * bit was set, else MDG_OK (or MDG_ERR_CUDA). */
 int mdg_status(mdg_handle h, void* stream, uint32_t* bits, int64_t* first_drone);
+
+/* Wait on the host for `stream` to finish its work, for at most timeout_ms milliseconds
+ * (polling, so the calling thread never blocks inside the driver). Returns MDG_OK when the
+ * stream is idle, MDG_ERR_TIMEOUT when the limit ran out first (the work keeps running; the
+ * caller decides whether to wait again, report a stuck worker or tear down), MDG_ERR_CUDA
+ * when the stream reports an error, MDG_ERR_ARG for a negative limit. The paper's
+ * environments step synchronously (Section 3.4.2); this is the bounded form of that wait
+ * for a host loop that must notice a stuck device. */
+int mdg_sync(void* stream, int32_t timeout_ms);
 
 /* One control step that allocates no device memory: mdg_step_obs (or mdg_step when
  * kin is NULL) for a batch described on the host, with no handle. The paper has no

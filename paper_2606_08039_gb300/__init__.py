@@ -31,7 +31,7 @@ NBR_K = 4
 NBR_FEAT = 6
 MAX_ENV_DRONES = 1024
 
-OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_UNSUPPORTED = 0, -1, -2, -3, -4
+OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_UNSUPPORTED, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
 OBS_NONE, OBS_LAST, OBS_EVERY_STEP = 0, 1, 2
 MLP_IN, MLP_IN_PAD, MLP_HIDDEN, MLP_OUT, MLP_OUT_PAD = 41, 64, 256, 13, 32
 MLP_DIMS = (MLP_IN_PAD, MLP_HIDDEN, MLP_HIDDEN, MLP_HIDDEN, MLP_OUT_PAD)
@@ -82,6 +82,7 @@ _SIGNATURES = {
     "mdg_features": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "mdg_surrogate_step": ([_VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, _VP, _VP],
                            ctypes.c_int),
+    "mdg_sync": ([_VP, ctypes.c_int32], ctypes.c_int),
     "mdg_step_obs_host": ([_VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP, _VP], ctypes.c_int),
     "mdg_step_obs_noalloc": ([_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP,
                               _VP, _VP, _VP], ctypes.c_int),
@@ -192,6 +193,14 @@ def _host_ptr(t, name, dtype, shape=None):
     if shape is not None and tuple(t.shape) != tuple(shape):
         raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def sync(stream=None, timeout_ms: int = 1000) -> int:
+    """Bounded host-side wait on a stream (mdg_sync): OK, or ERR_TIMEOUT if it is still busy."""
+    rc = lib().mdg_sync(_stream(stream), int(timeout_ms))
+    if rc not in (OK, ERR_TIMEOUT):
+        _check(rc)
+    return rc
 
 
 def _stream(stream):

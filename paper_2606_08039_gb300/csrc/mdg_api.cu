@@ -6,8 +6,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "mdg.h"
@@ -608,6 +610,21 @@ static int mapped_ptr(const void* host, void** dev, const char* name)
         return fail(MDG_ERR_ARG, "mdg_step_obs_host: %s is not mapped page-locked host memory", name);
     *dev = at.devicePointer;
     return MDG_OK;
+}
+
+int mdg_sync(void* stream, int32_t timeout_ms)
+{
+    if (timeout_ms < 0) return fail(MDG_ERR_ARG, "mdg_sync: timeout_ms = %d < 0", timeout_ms);
+    const auto t0 = std::chrono::steady_clock::now();
+    const auto limit = std::chrono::milliseconds(timeout_ms);
+    for (;;) {
+        const cudaError_t e = cudaStreamQuery((cudaStream_t)stream);
+        if (e == cudaSuccess) return MDG_OK;
+        if (e != cudaErrorNotReady) return cuda_fail(e, "mdg_sync");
+        if (std::chrono::steady_clock::now() - t0 >= limit)
+            return fail(MDG_ERR_TIMEOUT, "mdg_sync: stream still busy after %d ms", timeout_ms);
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
 }
 
 int mdg_step_obs_host(mdg_handle h, float* state, const float* action_host, int32_t action_type, int32_t n_substeps,

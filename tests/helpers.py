@@ -148,3 +148,49 @@ def oracle_horizon(P, dpe, flags, act_types, x0, integ0, a0, actions, n_sub, see
         states.append(xa.copy())
         resp.append(np.abs(xa - xb))
     return np.stack(states), np.stack(resp)
+
+
+def ensemble_check(snaps_a, snaps_b, alpha=1e-3):
+    """Compare two trajectories of the same swarm as ensembles, snapshot by snapshot ([n, 13]
+    states at the same times): per snapshot, the fraction of non-finite drones within 3
+    binomial standard errors, and for height z, speed |v| and body-rate magnitude |w| of the
+    finite drones a two-sample Kolmogorov-Smirnov test at level alpha / (number of tests)
+    and the means within 3 standard errors. Returns (ok, first failure or '')."""
+    from scipy import stats
+    n_tests = 3 * len(snaps_a)
+    for t, (a, b) in enumerate(zip(snaps_a, snaps_b)):
+        fa, fb = np.isfinite(a).all(axis=1), np.isfinite(b).all(axis=1)
+        k1, k2, n1, n2 = int((~fa).sum()), int((~fb).sum()), a.shape[0], b.shape[0]
+        p = (k1 + k2) / (n1 + n2)
+        se = np.sqrt(max(p * (1 - p), 1.0 / (n1 + n2)) * (1.0 / n1 + 1.0 / n2))
+        if abs(k1 / n1 - k2 / n2) > 3 * se:
+            return False, f"snapshot {t}: non-finite fractions {k1 / n1:.4f} vs {k2 / n2:.4f}"
+        if fa.sum() < 0.5 * n1 or fb.sum() < 0.5 * n2:
+            return False, f"snapshot {t}: fewer than half the drones finite"
+        for name, f in (("z", lambda x: x[:, 2]), ("|v|", lambda x: np.linalg.norm(x[:, 7:10], axis=1)),
+                        ("|w|", lambda x: np.linalg.norm(x[:, 10:13], axis=1))):
+            g, o = f(a)[fa], f(b)[fb]
+            pv = stats.ks_2samp(g, o).pvalue
+            if pv <= alpha / n_tests:
+                return False, f"snapshot {t} {name}: KS p = {pv:.2e}"
+            se = np.sqrt(g.var(ddof=1) / g.size + o.var(ddof=1) / o.size)
+            if abs(g.mean() - o.mean()) > 3 * se + 1e-12:
+                return False, f"snapshot {t} {name}: means {g.mean():.6g} vs {o.mean():.6g}, 3 SE {3 * se:.3g}"
+    return True, ""
+
+
+def oracle_snapshots(P, swarm, act_type, actions, every, x0=None, n_sub=5):
+    """The oracle's trajectory of a swarm from rest (or from x0 [n, 13]) with actions [K, n, 4],
+    the state recorded every `every` control steps. Returns a list of [n, 13] states."""
+    x = (np.concatenate([swarm.p, swarm.q, swarm.v, swarm.w], axis=1).astype(np.float64) if x0 is None
+         else np.asarray(x0, np.float64).copy())
+    integ = np.zeros((swarm.n, 6))
+    a = np.zeros((swarm.n, 4))
+    env_off = np.concatenate([[0], np.cumsum(swarm.drones_per_env)]).astype(np.int32)
+    acts = np.full(swarm.n_envs, act_type, np.int32)
+    snaps = []
+    for k0 in range(0, actions.shape[0], every):
+        x, integ, a = oracle.control_steps(P, env_off, np.asarray(swarm.flags, np.int32), acts, x, integ, a,
+                                           np.asarray(actions[k0:k0 + every], np.float64), n_sub)
+        snaps.append(x.copy())
+    return snaps

@@ -189,3 +189,16 @@ def test_exp_map_across_rotation_rates(cuda):
     xo = oracle_step(P, (np.ones(n, np.int32), np.zeros(n)), x0, i0, a0, action, np.zeros(n), 1)[0]
     assert_state_close(xg, xo, what="exp map")
     np.testing.assert_allclose(np.linalg.norm(xg[:, 3:7], axis=1), 1.0, atol=3e-7)
+
+
+def test_sync_reports_a_busy_stream_then_recovers(cuda):
+    """Failure detection on the host: mdg_sync returns MDG_ERR_TIMEOUT while a stream is
+    still busy (here a bounded device sleep of ~0.3 s stands in for a stuck worker), and OK
+    once the work is done; the context stays usable throughout."""
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        torch.cuda._sleep(int(0.3 * 2.07e9))
+    assert mdg.sync(s, timeout_ms=20) == mdg.ERR_TIMEOUT
+    assert b"still busy" in mdg.lib().mdg_last_error()
+    assert mdg.sync(s, timeout_ms=10000) == mdg.OK
+    assert mdg.sync(s, timeout_ms=0) == mdg.OK

@@ -96,3 +96,8 @@ def test_null_handle_calls_fail_cleanly(mdg_lib):
     assert L.mdg_destroy(None) == mdg.OK
     assert L.mdg_num_drones(None) < 0
     assert L.mdg_create(0, None, None, None, None) == mdg.ERR_ARG
+
+
+def test_sync_rejects_a_negative_limit_before_any_cuda_call(mdg_lib):
+    assert mdg_lib.mdg_sync(None, -1) == mdg.ERR_ARG
+    assert b"timeout_ms" in mdg_lib.mdg_last_error()
