@@ -65,6 +65,8 @@ extern "C" {
 /* Status bits written by the kernels (read with mdg_status). */
 #define MDG_STATUS_NONFINITE 1u /* a drone's state became NaN or infinite */
 #define MDG_STATUS_TIMEOUT 2u   /* a tensor-core kernel gave up waiting for its MMAs (bounded wait) */
+#define MDG_STATUS_BOUNDS 4u    /* library built with MDG_DEBUG: a kernel found a tile, environment or
+                                   list index outside its table and skipped the access */
 
 #define MDG_STATE_PLANES 6
 #define MDG_KIN_DIM 20     /* [p(3), q(4), roll/pitch/yaw(3), v(3), w(3), a_prev(4)] */

@@ -24,6 +24,7 @@ GND, DRAG, DW = 1, 2, 4
 ACT_RPM, ACT_PID, ACT_MIXED = 0, 1, 2
 STATUS_NONFINITE = 1
 STATUS_TIMEOUT = 2
+STATUS_BOUNDS = 4
 MLP_PATH_MMA_SYNC, MLP_PATH_TCGEN05 = 0, 1
 STATE_PLANES = 6
 KIN_DIM = 20
@@ -38,7 +39,8 @@ MLP_DIMS = (MLP_IN_PAD, MLP_HIDDEN, MLP_HIDDEN, MLP_HIDDEN, MLP_OUT_PAD)
 MLP_PARAMS = 156448
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libmdg.so")
+# MDG_DEBUG_LIBRARY=1 loads the index-checking debug build (build_library(debug=True))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmdg_debug.so" if os.environ.get("MDG_DEBUG_LIBRARY") == "1" else "libmdg.so")
 
 # Every symbol include/mdg.h declares, with its ctypes signature.
 _VP = ctypes.c_void_p

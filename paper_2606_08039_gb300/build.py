@@ -38,31 +38,38 @@ def _deps():
     return _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(INCLUDE, "mdg.h"), __file__]
 
 
-def lib_path() -> str:
-    return os.path.join(OUT_DIR, LIB_NAME)
+DEBUG_LIB_NAME = "libmdg_debug.so"
 
 
-def up_to_date() -> bool:
-    p = lib_path()
+def lib_path(debug: bool = False) -> str:
+    return os.path.join(OUT_DIR, DEBUG_LIB_NAME if debug else LIB_NAME)
+
+
+def up_to_date(debug: bool = False) -> bool:
+    p = lib_path(debug)
     if not os.path.exists(p):
         return False
     t = os.path.getmtime(p)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build_library(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile csrc/*.cu for sm_103a and link libmdg.so. Returns the library path."""
-    if not force and up_to_date():
-        return lib_path()
+def build_library(force: bool = False, verbose: bool = False, ptxas_info: bool = False, debug: bool = False) -> str:
+    """Compile csrc/*.cu for sm_103a and link libmdg.so (debug=True: libmdg_debug.so with
+    -DMDG_DEBUG, whose kernels check their table indices and report MDG_STATUS_BOUNDS).
+    Returns the library path."""
+    if not force and up_to_date(debug):
+        return lib_path(debug)
     nvcc = _nvcc()
     os.makedirs(OUT_DIR, exist_ok=True)
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
                      "--expt-relaxed-constexpr"]
     if ptxas_info:
         common += ["-Xptxas", "-v"]
+    if debug:
+        common += ["-DMDG_DEBUG"]
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src) + f".{os.getpid()}.o")
+        obj = os.path.join(OUT_DIR, os.path.basename(src) + f".{'d' if debug else 'r'}{os.getpid()}.o")
         cmd = [nvcc, *common, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -76,15 +83,15 @@ def build_library(force: bool = False, verbose: bool = False, ptxas_info: bool =
             if log.strip():
                 print(log, file=sys.stderr)
     objs = [o for o, _ in results]
-    tmp = lib_path() + f".tmp{os.getpid()}"
+    tmp = lib_path(debug) + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     for o in objs:
         os.remove(o)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, lib_path())
-    return lib_path()
+    os.replace(tmp, lib_path(debug))
+    return lib_path(debug)
 
 
 if __name__ == "__main__":

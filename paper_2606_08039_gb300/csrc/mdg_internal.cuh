@@ -11,6 +11,15 @@
 
 namespace mdg {
 
+// Index checks of the debug build (compiled with -DMDG_DEBUG): a false condition records
+// MDG_STATUS_BOUNDS in the status word and lets the caller skip the access. Release builds
+// compile every check to `true`.
+#ifdef MDG_DEBUG
+#define MDG_CHECK(cond, status) ((cond) ? true : (atomicOr((status), MDG_STATUS_BOUNDS), false))
+#else
+#define MDG_CHECK(cond, status) true
+#endif
+
 // Float32 copies of the model constants with the products the kernels need folded in
 // once on the host (in double precision, then rounded).
 struct DevConsts {

@@ -431,6 +431,11 @@ struct TileInfo {
     int n_drones, first_env, n_envs, bits;
 };
 
+// This thread's environment: first drone (tile-local), size, flags and action type.
+struct EnvSlot {
+    int ls, N, flags, act;
+};
+
 __device__ __forceinline__ TileInfo get_tile(const StepArgs& a)
 {
     TileInfo ti;
@@ -448,13 +453,28 @@ __device__ __forceinline__ TileInfo get_tile(const StepArgs& a)
         ti.n_envs = t.w & kTileEnvMask;
         ti.bits = t.w & ~kTileEnvMask;
     }
+    // debug builds: the tile lies inside the batch, fits the block and covers whole environments
+    if (!MDG_CHECK(ti.first_drone >= 0 && ti.n_drones >= 0 && ti.n_drones <= (int)blockDim.x &&
+                       ti.first_drone + ti.n_drones <= a.n && ti.first_env >= 0 && ti.n_envs >= 0 &&
+                       ti.first_env + ti.n_envs <= a.n_envs &&
+                       (a.uniform_N > 0 || (a.env_off[ti.first_env] == ti.first_drone &&
+                                            a.env_off[ti.first_env + ti.n_envs] == ti.first_drone + ti.n_drones)),
+                   a.status)) {
+        ti.n_drones = 0;
+        ti.n_envs = 0;
+    }
     return ti;
 }
 
-// This thread's environment: first drone (tile-local), size, flags and action type.
-struct EnvSlot {
-    int ls, N, flags, act;
-};
+// debug builds: a thread's environment contains the thread and lies inside the tile
+__device__ __forceinline__ void check_env(EnvSlot& e, int t, int n_drones, uint32_t* status)
+{
+    if (t < n_drones && !MDG_CHECK(e.ls >= 0 && e.N >= 1 && e.ls <= t && t < e.ls + e.N && e.ls + e.N <= n_drones, status)) {
+        e.ls = 0;
+        e.N = 0;
+    }
+}
+
 
 __device__ __forceinline__ EnvSlot tile_env(const StepArgs& a, const TileInfo& ti, int* s_off, int* s_info)
 {
@@ -468,6 +488,7 @@ __device__ __forceinline__ EnvSlot tile_env(const StepArgs& a, const TileInfo& t
             e.flags = a.env_flags[ti.first_env + k];
             e.act = a.act_type == MDG_ACT_MIXED ? (int)a.env_act[ti.first_env + k] : a.act_type;
         }
+        check_env(e, t, ti.n_drones, a.status);
         return e;
     }
     const int B = blockDim.x;
@@ -489,6 +510,7 @@ __device__ __forceinline__ EnvSlot tile_env(const StepArgs& a, const TileInfo& t
         e.flags = s_info[lo] & 0xff;
         e.act = s_info[lo] >> 8;
     }
+    check_env(e, t, ti.n_drones, a.status);
     return e;
 }
 
@@ -621,7 +643,11 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
         long long g = 0, env_first = 0;
         if (uniform) {
             const int first_env = item * a.envs_per_tile;
-            const int n_envs = min(a.envs_per_tile, a.n_envs - first_env);
+            int n_envs = min(a.envs_per_tile, a.n_envs - first_env);
+            if (!MDG_CHECK(item >= 0 && first_env >= 0 && n_envs >= 0 && n_envs * a.uniform_N <= B &&
+                               (long long)(first_env + n_envs) * a.uniform_N <= a.n,
+                           a.status))
+                n_envs = 0;
             n_drones = n_envs * a.uniform_N;
             bits = a.uniform_bits;
             if (t < n_drones) {
@@ -635,9 +661,15 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
             }
         } else {
             const int4 it = r.items[item];
-            const int n_envs = it.y;
+            int n_envs = it.y;
             n_drones = it.z;
             bits = it.w;
+            if (!MDG_CHECK(item >= 0 && it.x >= 0 && n_envs >= 0 && n_envs <= B && n_drones >= 0 && n_drones <= B &&
+                               it.x + n_envs <= a.n_envs,
+                           a.status)) {
+                n_envs = 0;
+                n_drones = 0;
+            }
             for (int i = t; i < n_envs; i += B) {
                 const int e = r.slot_env[it.x + i];
                 const int act = a.act_type == MDG_ACT_MIXED ? (int)a.env_act[e] : a.act_type;
@@ -660,9 +692,16 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
                 env.act = s_info[lo] >> 8;
                 env_first = s_goff[lo];
                 g = env_first + (t - env.ls);
+                // debug builds: the environment's drones lie inside the batch
+                if (!MDG_CHECK(env_first >= 0 && env_first + env.N <= a.n, a.status)) {
+                    env_first = 0;
+                    g = 0;
+                    env.N = 0;
+                }
             }
+            check_env(env, t, n_drones, a.status);
         }
-        const bool active = t < n_drones;
+        const bool active = t < n_drones && env.N > 0;  // env.N == 0 only after a failed debug check
         const bool is_pid = env.act == MDG_ACT_PID;
         const bool tile_dw = (bits & kTileAnyDW) != 0;
         const bool warp_local = (bits & kTileWarpLocal) != 0;
@@ -960,6 +999,7 @@ __global__ void __launch_bounds__(128) surrogate_fallback_kernel(const Surrogate
     const int count = *sa.fallback_count;
     for (int item = blockIdx.x * 4 + wib; item < count; item += gridDim.x * 4) {
         const int e = sa.fallback_list[item];
+        if (!MDG_CHECK(e >= 0 && e < a.n_envs, a.status)) continue;
         const int N = a.uniform_N;
         const bool active = lane < N;
         const long long g = (long long)e * N + lane;
