@@ -27,6 +27,8 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
 GND, DRAG, DW = 1, 2, 4
 ACT_RPM, ACT_PID = 0, 1
+FRAME_X, FRAME_P = 0, 1
+EULER, RK4 = 0, 1
 
 _lock = threading.Lock()
 _lib = None
@@ -55,7 +57,8 @@ class Params(ctypes.Structure):
         ("pos_iclamp", ctypes.c_double),
         ("att_kp", ctypes.c_double * 3), ("att_ki", ctypes.c_double * 3), ("att_kd", ctypes.c_double * 3),
         ("att_iclamp", ctypes.c_double),
-        ("dt_sim", ctypes.c_double), ("dt_ctrl", ctypes.c_double)]
+        ("dt_sim", ctypes.c_double), ("dt_ctrl", ctypes.c_double),
+        ("frame", ctypes.c_int32), ("integrator", ctypes.c_int32)]
 
     def to_dict(self) -> dict:
         out = {}
@@ -78,6 +81,10 @@ def lib():
             sig = {
                 "orc_params_size": ([], ctypes.c_int),
                 "orc_params_cf2x": ([P], None),
+                "orc_params_cf2p": ([P], None),
+                "orc_params_race": ([P], None),
+                "orc_env_deriv": ([P, ctypes.c_int, _D, _D, ctypes.c_int, _D], None),
+                "orc_substep_rk4": ([P, ctypes.c_int, _D, _D, ctypes.c_int, ctypes.c_double, _D], None),
                 "orc_hover_rpm": ([P], ctypes.c_double),
                 "orc_max_rpm": ([P], ctypes.c_double),
                 "orc_quat_mul": ([_D, _D, _D], None),
@@ -121,6 +128,20 @@ def cf2x() -> Params:
     """Default CF2X parameters of the oracle (its own table)."""
     p = Params()
     lib().orc_params_cf2x(ctypes.byref(p))
+    return p
+
+
+def cf2p() -> Params:
+    """CF2P: the CF2X parameters with the + rotor layout."""
+    p = Params()
+    lib().orc_params_cf2p(ctypes.byref(p))
+    return p
+
+
+def race() -> Params:
+    """RACE parameters of the oracle (its own table; readings in mdg_oracle.c)."""
+    p = Params()
+    lib().orc_params_race(ctypes.byref(p))
     return p
 
 
@@ -177,6 +198,23 @@ def substep(p: Params, x, rpm, flags: int, dt: float | None = None) -> np.ndarra
     out = np.zeros_like(x)
     lib().orc_substep(ctypes.byref(p), x.shape[0], _dptr(x), _dptr(rpm), int(flags),
                       p.dt_sim if dt is None else float(dt), _dptr(out))
+    return out
+
+
+def env_deriv(p: Params, x, rpm, flags: int) -> np.ndarray:
+    """Time derivative of one environment's state: x [N,13], rpm [N,4] -> dx/dt [N,13]."""
+    x, rpm = _f64(x), _f64(rpm)
+    out = np.zeros_like(x)
+    lib().orc_env_deriv(ctypes.byref(p), x.shape[0], _dptr(x), _dptr(rpm), int(flags), _dptr(out))
+    return out
+
+
+def substep_rk4(p: Params, x, rpm, flags: int, dt: float | None = None) -> np.ndarray:
+    """One classical RK4 substep of one environment: x [N,13], rpm [N,4] -> x' [N,13]."""
+    x, rpm = _f64(x), _f64(rpm)
+    out = np.zeros_like(x)
+    lib().orc_substep_rk4(ctypes.byref(p), x.shape[0], _dptr(x), _dptr(rpm), int(flags),
+                          p.dt_sim if dt is None else float(dt), _dptr(out))
     return out
 
 

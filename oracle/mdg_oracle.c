@@ -36,6 +36,15 @@
 #define ORC_ACT_RPM 0
 #define ORC_ACT_PID 1
 
+/* Rotor layouts (Section 3.1.2): X configuration (CF2X, RACE) or + configuration (CF2P). */
+#define ORC_FRAME_X 0
+#define ORC_FRAME_P 1
+
+/* Integrators (Table "Physics modes"): the explicit Euler of the DYN mode, or classical
+ * fourth-order Runge-Kutta (the MuJoCo modes integrate with RK4). */
+#define ORC_EULER 0
+#define ORC_RK4 1
+
 /* Model parameters. Field order is the oracle's own; the Python side of the
  * oracle mirrors it. */
 typedef struct {
@@ -49,6 +58,8 @@ typedef struct {
     double pos_kp[3], pos_ki[3], pos_kd[3], pos_iclamp;
     double att_kp[3], att_ki[3], att_kd[3], att_iclamp;
     double dt_sim, dt_ctrl;
+    int32_t frame;      /* ORC_FRAME_X / ORC_FRAME_P */
+    int32_t integrator; /* ORC_EULER / ORC_RK4 */
 } orc_params;
 
 int orc_params_size(void) { return (int)sizeof(orc_params); }
@@ -103,6 +114,45 @@ void orc_params_cf2x(orc_params* P)
     P->att_iclamp = 0.5;
     P->dt_sim = 1.0 / 240.0;
     P->dt_ctrl = 1.0 / 48.0;
+    P->frame = ORC_FRAME_X;
+    P->integrator = ORC_EULER;
+}
+
+/* CF2P: the CF2X parameters (Table "Drone model parameters" lists one column for both)
+ * with the + rotor layout. */
+void orc_params_cf2p(orc_params* P)
+{
+    orc_params_cf2x(P);
+    P->frame = ORC_FRAME_P;
+}
+
+/* RACE: the RACE column of Table "Drone model parameters". Not printed for RACE, and
+ * read here: the aerodynamic coefficients (C_gnd, c_xy, c_z, C1..C3) keep their CF2.x
+ * values, h_clip follows the same derivation from r_p and T/W, the position-loop gains
+ * (which command accelerations; the thrust T = m |a*| scales with the mass) are kept, and
+ * the attitude-loop gains (which command torques) are scaled per axis by the inertia ratio
+ * J_RACE / J_CF2 so that the angular-acceleration response matches the Crazyflie's. */
+void orc_params_race(orc_params* P)
+{
+    orc_params cf;
+    orc_params_cf2x(&cf);
+    *P = cf;
+    P->mass = 0.25;
+    P->arm = 0.125;
+    P->thrust2weight = 4.0;
+    P->Jxx = 4.86e-4;
+    P->Jyy = 4.86e-4;
+    P->Jzz = 8.80e-4;
+    P->kf = 1.28e-8;
+    P->km = 5.96e-10;
+    P->prop_radius = 0.0635;
+    P->h_clip = 0.25 * P->prop_radius * sqrt(P->c_gnd / (P->thrust2weight - 1.0));
+    const double ratio[3] = {P->Jxx / cf.Jxx, P->Jyy / cf.Jyy, P->Jzz / cf.Jzz};
+    for (int r = 0; r < 3; ++r) {
+        P->att_kp[r] = cf.att_kp[r] * ratio[r];
+        P->att_ki[r] = cf.att_ki[r] * ratio[r];
+        P->att_kd[r] = cf.att_kd[r] * ratio[r];
+    }
 }
 
 /* ---- quaternion helpers; q = [w, x, y, z], body-to-world (Section 3.1.1) ---- */
@@ -162,9 +212,19 @@ void orc_motor(const orc_params* P, const double rpm[4], double* T, double tau[3
         F[i] = P->kf * n2[i];
     }
     *T = F[0] + F[1] + F[2] + F[3];
-    const double l = P->arm / sqrt(2.0);
-    tau[0] = l * (F[0] + F[1] - F[2] - F[3]);
-    tau[1] = l * (-F[0] + F[1] + F[2] - F[3]);
+    if (P->frame == ORC_FRAME_P) {
+        /* + configuration: "the L/sqrt2 factor replaced by L on a different pair of
+         * motors". Read as the X layout turned by 45 degrees: the X torques place rotor i
+         * at (x, y) = L/sqrt2 ((+,+), (-,+), (-,-), (+,-)) (tau_x = sum y_i F_i,
+         * tau_y = -sum x_i F_i); turned by 45 degrees the rotors sit at L (+x, +y, -x, -y),
+         * so tau_x = L (F1 - F3), tau_y = L (F2 - F0); the yaw signs are unchanged. */
+        tau[0] = P->arm * (F[1] - F[3]);
+        tau[1] = P->arm * (F[2] - F[0]);
+    } else {
+        const double l = P->arm / sqrt(2.0);
+        tau[0] = l * (F[0] + F[1] - F[2] - F[3]);
+        tau[1] = l * (-F[0] + F[1] + F[2] - F[3]);
+    }
     tau[2] = P->km * (-n2[0] + n2[1] - n2[2] + n2[3]);
 }
 
@@ -234,6 +294,14 @@ void orc_env_forces(const orc_params* P, int N, const double* x, const double* r
     }
 }
 
+/* Rotational Newton-Euler in the body frame: omega_dot = J^-1 (tau - omega x (J omega)). */
+static void orc_angular_accel(const double J[3], const double tau[3], const double w[3], double wdot[3])
+{
+    double Jw[3] = {J[0] * w[0], J[1] * w[1], J[2] * w[2]};
+    double gyro[3] = {w[1] * Jw[2] - w[2] * Jw[1], w[2] * Jw[0] - w[0] * Jw[2], w[0] * Jw[1] - w[1] * Jw[0]};
+    for (int r = 0; r < 3; ++r) wdot[r] = (tau[r] - gyro[r]) / J[r];
+}
+
 /* One physics substep of length dt for one environment (Section 3.2, DYN mode,
  * "explicit Euler", plus the closed-form exponential map of _integrateQ).
  * Reading: forward Euler — p uses the old v, v the old acceleration, omega the
@@ -256,10 +324,8 @@ void orc_substep(const orc_params* P, int N, const double* x_in, const double* r
         const double* q = s + 3;
         const double* v = s + 7;
         const double* w = s + 10;
-        double Jw[3] = {J[0] * w[0], J[1] * w[1], J[2] * w[2]};
-        double gyro[3] = {w[1] * Jw[2] - w[2] * Jw[1], w[2] * Jw[0] - w[0] * Jw[2], w[0] * Jw[1] - w[1] * Jw[0]};
         double wdot[3];
-        for (int r = 0; r < 3; ++r) wdot[r] = (tau[3 * j + r] - gyro[r]) / J[r];
+        orc_angular_accel(J, tau + 3 * j, w, wdot);
         double pn[3], vn[3], wn[3], qn[4];
         for (int r = 0; r < 3; ++r) {
             pn[r] = p[r] + dt * v[r];
@@ -283,6 +349,78 @@ void orc_substep(const orc_params* P, int N, const double* x_in, const double* r
     }
     free(F);
     free(tau);
+}
+
+/* Time derivative of one environment's state: p' = v, q' = 1/2 q (x) [0, omega] (the
+ * body-frame rate multiplies on the right, as in the exponential map), v' = F/m,
+ * omega' = J^-1 (tau - omega x (J omega)), the forces of orc_env_forces evaluated at x
+ * with the quaternions taken at unit length (the stage states of a Runge-Kutta step
+ * leave the unit sphere by O(dt^2)). dx is [N][13]. */
+void orc_env_deriv(const orc_params* P, int N, const double* x, const double* rpm, int flags, double* dx)
+{
+    double* xu = (double*)malloc(sizeof(double) * 13 * (size_t)(N > 0 ? N : 1));
+    double* F = (double*)malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
+    double* tau = (double*)malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
+    memcpy(xu, x, sizeof(double) * 13 * (size_t)N);
+    for (int j = 0; j < N; ++j) {
+        double* q = xu + 13 * j + 3;
+        const double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        for (int r = 0; r < 4; ++r) q[r] /= qn;
+    }
+    orc_env_forces(P, N, xu, rpm, flags, F, tau);
+    const double J[3] = {P->Jxx, P->Jyy, P->Jzz};
+    for (int j = 0; j < N; ++j) {
+        const double* s = x + 13 * j;
+        double* d = dx + 13 * j;
+        const double* q = s + 3;
+        const double* w = s + 10;
+        const double wq[4] = {0.0, w[0], w[1], w[2]};
+        double qd[4];
+        orc_quat_mul(q, wq, qd);
+        for (int r = 0; r < 3; ++r) d[r] = s[7 + r];
+        for (int r = 0; r < 4; ++r) d[3 + r] = 0.5 * qd[r];
+        for (int r = 0; r < 3; ++r) d[7 + r] = F[3 * j + r] / P->mass;
+        orc_angular_accel(J, tau + 3 * j, w, d + 10);
+    }
+    free(xu);
+    free(F);
+    free(tau);
+}
+
+/* One substep of classical fourth-order Runge-Kutta for one environment (the MuJoCo
+ * modes of Table "Physics modes" integrate with RK4). Reading: the 13-d states of all
+ * drones of the environment advance jointly (the downwash couples them, so every stage
+ * evaluates every force at that stage's states), k1 = f(x), k2 = f(x + dt/2 k1),
+ * k3 = f(x + dt/2 k2), k4 = f(x + dt k3), x+ = x + dt/6 (k1 + 2 k2 + 2 k3 + k4), the
+ * quaternion advanced like the other components and renormalised at the end. */
+void orc_substep_rk4(const orc_params* P, int N, const double* x_in, const double* rpm, int flags, double dt,
+                     double* x_out)
+{
+    const size_t n13 = 13 * (size_t)(N > 0 ? N : 1);
+    double* k1 = (double*)malloc(sizeof(double) * n13);
+    double* k2 = (double*)malloc(sizeof(double) * n13);
+    double* k3 = (double*)malloc(sizeof(double) * n13);
+    double* k4 = (double*)malloc(sizeof(double) * n13);
+    double* xs = (double*)malloc(sizeof(double) * n13);
+    const size_t m = 13 * (size_t)N;
+    orc_env_deriv(P, N, x_in, rpm, flags, k1);
+    for (size_t i = 0; i < m; ++i) xs[i] = x_in[i] + 0.5 * dt * k1[i];
+    orc_env_deriv(P, N, xs, rpm, flags, k2);
+    for (size_t i = 0; i < m; ++i) xs[i] = x_in[i] + 0.5 * dt * k2[i];
+    orc_env_deriv(P, N, xs, rpm, flags, k3);
+    for (size_t i = 0; i < m; ++i) xs[i] = x_in[i] + dt * k3[i];
+    orc_env_deriv(P, N, xs, rpm, flags, k4);
+    for (size_t i = 0; i < m; ++i) x_out[i] = x_in[i] + dt / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+    for (int j = 0; j < N; ++j) {
+        double* q = x_out + 13 * j + 3;
+        const double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        for (int r = 0; r < 4; ++r) q[r] /= qn;
+    }
+    free(k1);
+    free(k2);
+    free(k3);
+    free(k4);
+    free(xs);
 }
 
 /* ---- PID waypoint controller (Section 4.2.1, Table "Default PIDControl gains") ---- */
@@ -323,7 +461,15 @@ static void solve4(double A[4][4], double b[4], double x[4])
  * (-1)^{m_i} f_i). */
 void orc_allocation_matrix(const orc_params* P, double M[16])
 {
-    const double l = P->arm / sqrt(2.0), r = P->km / P->kf;
+    const double r = P->km / P->kf;
+    if (P->frame == ORC_FRAME_P) {
+        const double L = P->arm;
+        const double rows[4][4] = {{1, 1, 1, 1}, {0, L, 0, -L}, {-L, 0, L, 0}, {-r, r, -r, r}};
+        for (int i = 0; i < 4; ++i)
+            for (int k = 0; k < 4; ++k) M[4 * i + k] = rows[i][k];
+        return;
+    }
+    const double l = P->arm / sqrt(2.0);
     const double rows[4][4] = {{1, 1, 1, 1}, {l, l, -l, -l}, {-l, l, l, -l}, {-r, r, -r, r}};
     for (int i = 0; i < 4; ++i)
         for (int k = 0; k < 4; ++k) M[4 * i + k] = rows[i][k];
@@ -520,7 +666,10 @@ int orc_control_steps(const orc_params* P, int n_envs, const int32_t* env_off, c
                 for (int i = 0; i < 4; ++i) a_prev[4 * (size_t)(b + j) + i] = rpm[4 * j + i];
             }
             for (int s = 0; s < n_sub; ++s) {
-                orc_substep(P, N, x + 13 * (size_t)b, rpm, env_flags[e], P->dt_sim, tmp);
+                if (P->integrator == ORC_RK4)
+                    orc_substep_rk4(P, N, x + 13 * (size_t)b, rpm, env_flags[e], P->dt_sim, tmp);
+                else
+                    orc_substep(P, N, x + 13 * (size_t)b, rpm, env_flags[e], P->dt_sim, tmp);
                 memcpy(x + 13 * (size_t)b, tmp, sizeof(double) * 13 * (size_t)N);
             }
         }

@@ -1,5 +1,5 @@
 """The oracle pins have teeth: plant plausible mistakes in a copy of the oracle and
-check that the pin suite (test_oracle_dynamics.py) fails on each.
+check that the pin suite (test_oracle_dynamics.py, test_oracle_models.py) fails on each.
 
 Mistakes are planted only in a temporary copy of the oracle, on the CPU; the real
 oracle is not modified. CPU only.
@@ -15,8 +15,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 # name: (text in mdg_oracle.c, planted mistake)
 MUTATIONS = {
-    "gyroscopic_sign": ("wdot[r] = (tau[3 * j + r] - gyro[r]) / J[r];",
-                        "wdot[r] = (tau[3 * j + r] + gyro[r]) / J[r];"),
+    "gyroscopic_sign": ("wdot[r] = (tau[r] - gyro[r]) / J[r];", "wdot[r] = (tau[r] + gyro[r]) / J[r];"),
     "semi_implicit_position": ("pn[r] = p[r] + dt * v[r];",
                                "pn[r] = p[r] + dt * (v[r] + dt * F[3 * j + r] / P->mass);"),
     "world_frame_rate": ("orc_quat_mul(q, dq, qn);", "orc_quat_mul(dq, q, qn);"),
@@ -46,6 +45,16 @@ MUTATIONS = {
     "knn_tie_order": ("while (pos > 0 && d2 < bestd[pos - 1]) --pos;", "while (pos > 0 && d2 <= bestd[pos - 1]) --pos;"),
     "no_renormalisation": ("for (int r = 0; r < 4; ++r) o[3 + r] = qn[r] / qnorm;",
                            "for (int r = 0; r < 4; ++r) o[3 + r] = qn[r];"),
+    "rk4_third_stage_from_k1": ("for (size_t i = 0; i < m; ++i) xs[i] = x_in[i] + 0.5 * dt * k2[i];",
+                                "for (size_t i = 0; i < m; ++i) xs[i] = x_in[i] + 0.5 * dt * k1[i];"),
+    "rk4_weights": ("dt / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i])",
+                    "dt / 6.0 * (2.0 * k1[i] + k2[i] + 2.0 * k3[i] + k4[i])"),
+    "rk4_quaternion_rate_sign": ("for (int r = 0; r < 4; ++r) d[3 + r] = 0.5 * qd[r];",
+                                 "for (int r = 0; r < 4; ++r) d[3 + r] = -0.5 * qd[r];"),
+    "plus_roll_pair": ("tau[0] = P->arm * (F[1] - F[3]);", "tau[0] = P->arm * (F[0] - F[2]);"),
+    "plus_allocation_row": ("{{1, 1, 1, 1}, {0, L, 0, -L}, {-L, 0, L, 0}, {-r, r, -r, r}}",
+                            "{{1, 1, 1, 1}, {L, 0, -L, 0}, {-L, 0, L, 0}, {-r, r, -r, r}}"),
+    "race_gain_ratio": ("P->att_kp[r] = cf.att_kp[r] * ratio[r];", "P->att_kp[r] = cf.att_kp[r];"),
 }
 
 
@@ -73,8 +82,9 @@ def test_planted_mistake_is_caught(name, oracle_source, tmp_path):
     shutil.copytree(os.path.join(ROOT, "tests"), tmp_path / "tests",
                     ignore=shutil.ignore_patterns("__pycache__", "test_oracle_mutations.py"))
     (tmp_path / "oracle" / "mdg_oracle.c").write_text(oracle_source.replace(before, after))
-    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_dynamics.py", "-q", "-x",
-                        "-p", "no:cacheprovider"], cwd=tmp_path, capture_output=True, text=True, timeout=300)
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_dynamics.py", "tests/test_oracle_models.py",
+                        "-q", "-x", "-p", "no:cacheprovider"], cwd=tmp_path, capture_output=True, text=True,
+                       timeout=300)
     assert r.returncode == 1, f"planted mistake {name} was not caught:\n{r.stdout[-2000:]}"
 
 
