@@ -83,9 +83,17 @@ typedef struct mdg_ctx* mdg_handle;
  * defaults). dw_c1..dw_c3 are Eq. downwash's (C1, C2, C3); dw_max_xy its 10 m lateral
  * cut-off; dw_dz_min an optional minimum height difference (0 = as printed). The PID
  * gains follow Table "Default PIDControl gains". dt_sim = 1/f_sim is the substep,
- * dt_ctrl = 1/f_ctrl the control period (the PID's integration step). frame must be
- * MDG_FRAME_X (X-configuration mixing of Eq. motor). */
+ * dt_ctrl = 1/f_ctrl the control period (the PID's integration step). frame selects the
+ * rotor layout of Eq. motor: MDG_FRAME_X (CF2X, RACE) or MDG_FRAME_P (CF2P, the X layout
+ * turned by 45 degrees: tau_x = L (F1 - F3), tau_y = L (F2 - F0)). integrator selects the
+ * substep: MDG_INTEGRATOR_EULER (the DYN mode's explicit Euler with the exponential map)
+ * or MDG_INTEGRATOR_RK4 (classical fourth-order Runge-Kutta on each environment's drones
+ * jointly, every stage evaluating every force at that stage's states, the quaternion
+ * renormalised after the substep; Table "Physics modes" lists RK4 for the MuJoCo modes). */
 #define MDG_FRAME_X 0
+#define MDG_FRAME_P 1
+#define MDG_INTEGRATOR_EULER 0
+#define MDG_INTEGRATOR_RK4 1
 typedef struct mdg_constants {
     double mass, arm, thrust2weight, Jxx, Jyy, Jzz, kf, km, prop_radius;
     double g;
@@ -95,7 +103,7 @@ typedef struct mdg_constants {
     double att_kp[3], att_ki[3], att_kd[3], att_iclamp;
     double dt_sim, dt_ctrl;
     int32_t frame;
-    int32_t reserved;
+    int32_t integrator;
 } mdg_constants;
 
 /* Fill *out with the CF2X constants (Table "Drone model parameters", Eq. downwash
@@ -107,6 +115,14 @@ typedef struct mdg_constants {
  * from the propeller radius and the model's maximum thrust" (Section 3.1.3).
  * Host only. Returns MDG_ERR_ARG if out is NULL. */
 int mdg_constants_cf2x(mdg_constants* out);
+/* CF2P: the CF2X constants with frame = MDG_FRAME_P (Table "Drone model parameters" has
+ * one column for both). */
+int mdg_constants_cf2p(mdg_constants* out);
+/* RACE: the RACE column of Table "Drone model parameters". Not printed for RACE and set
+ * here: C_gnd, c_xy, c_z and the downwash coefficients keep their CF2.x values, h_clip
+ * follows the CF2X derivation from r_p and T/W, the position gains are kept and the
+ * attitude gains are scaled per axis by the inertia ratio J_RACE / J_CF2X. */
+int mdg_constants_race(mdg_constants* out);
 
 /* sizeof(mdg_constants), for bindings that mirror the struct. */
 int mdg_constants_size(void);

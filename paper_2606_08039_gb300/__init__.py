@@ -33,6 +33,8 @@ NBR_FEAT = 6
 MAX_ENV_DRONES = 1024
 
 OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_UNSUPPORTED, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
+FRAME_X, FRAME_P = 0, 1
+INTEGRATOR_EULER, INTEGRATOR_RK4 = 0, 1
 OBS_NONE, OBS_LAST, OBS_EVERY_STEP = 0, 1, 2
 MLP_IN, MLP_IN_PAD, MLP_HIDDEN, MLP_OUT, MLP_OUT_PAD = 41, 64, 256, 13, 32
 MLP_DIMS = (MLP_IN_PAD, MLP_HIDDEN, MLP_HIDDEN, MLP_HIDDEN, MLP_OUT_PAD)
@@ -46,6 +48,8 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libmdg_debug.so" if os.environ.get("MDG_
 _VP = ctypes.c_void_p
 _SIGNATURES = {
     "mdg_constants_cf2x": ([_VP], ctypes.c_int),
+    "mdg_constants_cf2p": ([_VP], ctypes.c_int),
+    "mdg_constants_race": ([_VP], ctypes.c_int),
     "mdg_constants_size": ([], ctypes.c_int),
     "mdg_hover_rpm": ([_VP], ctypes.c_double),
     "mdg_max_rpm": ([_VP], ctypes.c_double),
@@ -134,12 +138,24 @@ class Constants(ctypes.Structure):
         ("att_kp", ctypes.c_double * 3), ("att_ki", ctypes.c_double * 3), ("att_kd", ctypes.c_double * 3),
         ("att_iclamp", ctypes.c_double),
         ("dt_sim", ctypes.c_double), ("dt_ctrl", ctypes.c_double),
-        ("frame", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+        ("frame", ctypes.c_int32), ("integrator", ctypes.c_int32)]
 
     @classmethod
     def cf2x(cls) -> "Constants":
         c = cls()
         _check(lib().mdg_constants_cf2x(ctypes.byref(c)))
+        return c
+
+    @classmethod
+    def cf2p(cls) -> "Constants":
+        c = cls()
+        _check(lib().mdg_constants_cf2p(ctypes.byref(c)))
+        return c
+
+    @classmethod
+    def race(cls) -> "Constants":
+        c = cls()
+        _check(lib().mdg_constants_race(ctypes.byref(c)))
         return c
 
     def hover_rpm(self) -> float:

@@ -79,8 +79,12 @@ bool constants_valid(const mdg_constants& c, std::string& why)
         why = "thrust2weight must exceed 1";
         return false;
     }
-    if (c.frame != MDG_FRAME_X) {
-        why = "only the X-configuration frame (MDG_FRAME_X) is supported";
+    if (c.frame != MDG_FRAME_X && c.frame != MDG_FRAME_P) {
+        why = "frame must be MDG_FRAME_X or MDG_FRAME_P";
+        return false;
+    }
+    if (c.integrator != MDG_INTEGRATOR_EULER && c.integrator != MDG_INTEGRATOR_RK4) {
+        why = "integrator must be MDG_INTEGRATOR_EULER or MDG_INTEGRATOR_RK4";
         return false;
     }
     return true;
@@ -129,8 +133,22 @@ DevConsts make_dev_consts(const mdg_constants& c)
     d.max_rpm = (float)maxrpm;
     d.f_max = (float)(c.kf * maxrpm * maxrpm);
     d.inv_kf = (float)(1.0 / c.kf);
-    d.alloc_xy = (float)(sqrt(2.0) / c.arm);
     d.alloc_z = (float)(c.kf / c.km);
+    d.frame_p = c.frame == MDG_FRAME_P ? 1 : 0;
+    d.rk4 = c.integrator == MDG_INTEGRATOR_RK4 ? 1 : 0;
+    if (d.frame_p) {
+        // + layout: tau_x = L (F1 - F3), tau_y = L (F2 - F0); the mixing rows [1,1,1,1],
+        // [0,1,0,-1] L, [-1,0,1,0] L, [-1,1,-1,1] k_m/k_f are orthogonal with squared norms
+        // 4, 2 L^2, 2 L^2, 4 (k_m/k_f)^2
+        d.l_sqrt2 = (float)c.arm;
+        d.alloc_xy = (float)(2.0 / c.arm);
+        const float sx[4] = {0.f, 1.f, 0.f, -1.f}, sy[4] = {-1.f, 0.f, 1.f, 0.f};
+        for (int i = 0; i < 4; ++i) d.mix_x[i] = sx[i], d.mix_y[i] = sy[i];
+    } else {
+        d.alloc_xy = (float)(sqrt(2.0) / c.arm);
+        const float sx[4] = {1.f, 1.f, -1.f, -1.f}, sy[4] = {-1.f, 1.f, 1.f, -1.f};
+        for (int i = 0; i < 4; ++i) d.mix_x[i] = sx[i], d.mix_y[i] = sy[i];
+    }
     return d;
 }
 
@@ -412,6 +430,40 @@ int mdg_constants_cf2x(mdg_constants* out)
     out->dt_sim = 1.0 / 240.0;
     out->dt_ctrl = 1.0 / 48.0;
     out->frame = MDG_FRAME_X;
+    out->integrator = MDG_INTEGRATOR_EULER;
+    return MDG_OK;
+}
+
+int mdg_constants_cf2p(mdg_constants* out)
+{
+    if (!out) return fail(MDG_ERR_ARG, "mdg_constants_cf2p: out is NULL");
+    mdg_constants_cf2x(out);
+    out->frame = MDG_FRAME_P;
+    return MDG_OK;
+}
+
+int mdg_constants_race(mdg_constants* out)
+{
+    if (!out) return fail(MDG_ERR_ARG, "mdg_constants_race: out is NULL");
+    mdg_constants cf;
+    mdg_constants_cf2x(&cf);
+    *out = cf;
+    out->mass = 0.25;
+    out->arm = 0.125;
+    out->thrust2weight = 4.0;
+    out->Jxx = 4.86e-4;
+    out->Jyy = 4.86e-4;
+    out->Jzz = 8.80e-4;
+    out->kf = 1.28e-8;
+    out->km = 5.96e-10;
+    out->prop_radius = 0.0635;
+    out->h_clip = 0.25 * out->prop_radius * sqrt(out->c_gnd / (out->thrust2weight - 1.0));
+    const double ratio[3] = {out->Jxx / cf.Jxx, out->Jyy / cf.Jyy, out->Jzz / cf.Jzz};
+    for (int i = 0; i < 3; ++i) {
+        out->att_kp[i] = cf.att_kp[i] * ratio[i];
+        out->att_ki[i] = cf.att_ki[i] * ratio[i];
+        out->att_kd[i] = cf.att_kd[i] * ratio[i];
+    }
     return MDG_OK;
 }
 
@@ -759,7 +811,7 @@ static cudaError_t enqueue_rollout(mdg_handle h, const mdg::RolloutArgs& r, cuda
     if (e != cudaSuccess) return e;
     int n_sm = 152;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device);
-    const int grid = n_sm * mdg::rollout_blocks_per_sm(h->block, h->uniform_flags, h->uniform_N);
+    const int grid = n_sm * mdg::rollout_blocks_per_sm(h->block, h->uniform_flags, h->uniform_N, h->dc.rk4 != 0);
     return mdg::launch_rollout(r, h->block, h->uniform_flags, grid, s);
 }
 

@@ -36,7 +36,10 @@ struct DevConsts {
     float att_kp[3], att_ki[3], att_kd[3], att_iclamp;
     float dt_sim, dt_ctrl;
     float max_rpm, f_max, inv_kf;     // PID output clip: f_i in [0, k_f MAX_RPM^2]
-    float alloc_xy, alloc_z;          // inverse mixing: sqrt(2)/L and k_f/k_m
+    float alloc_xy, alloc_z;          // inverse mixing: sqrt(2)/L (X) or 2/L (+), and k_f/k_m
+    float mix_x[4], mix_y[4];         // inverse mixing signs of tau_x, tau_y per rotor
+    int frame_p;                      // 1: + rotor layout (l_sqrt2 then holds L)
+    int rk4;                          // 1: fourth-order Runge-Kutta substeps
 };
 
 // A launch tile: whole environments packed into one thread block.
@@ -135,7 +138,7 @@ int default_block(int32_t max_env, int64_t n_drones, int n_sm);
 cudaError_t launch_step(const StepArgs& a, int n_tiles, int block, bool with_obs, int uniform_flags, cudaStream_t s);
 // grid: persistent CTAs (0: one per work item)
 cudaError_t launch_rollout(const RolloutArgs& a, int block, int uniform_flags, int grid, cudaStream_t s);
-int rollout_blocks_per_sm(int block, int uniform_flags, int uniform_N);
+int rollout_blocks_per_sm(int block, int uniform_flags, int uniform_N, bool rk4);
 cudaError_t launch_features(const SurrogateArgs& a, int n_tiles, int block, cudaStream_t s);
 cudaError_t launch_surrogate_prepare(const SurrogateArgs& a, int n_tiles, int block, cudaStream_t s);
 cudaError_t launch_surrogate_apply(const SurrogateArgs& a, cudaStream_t s);

@@ -100,17 +100,24 @@ __device__ __forceinline__ Motor motor(const float n[4], const DevConsts& c)
     const float f0 = c.kf * n0, f1 = c.kf * n1, f2 = c.kf * n2, f3 = c.kf * n3;
     Motor m;
     m.T = (f0 + f1) + (f2 + f3);
-    m.tau[0] = c.l_sqrt2 * ((f0 + f1) - (f2 + f3));
-    m.tau[1] = c.l_sqrt2 * ((f1 + f2) - (f0 + f3));
+    if (c.frame_p) {  // + layout: rotors at L (+x, +y, -x, -y)
+        m.tau[0] = c.l_sqrt2 * (f1 - f3);
+        m.tau[1] = c.l_sqrt2 * (f2 - f0);
+    } else {
+        m.tau[0] = c.l_sqrt2 * ((f0 + f1) - (f2 + f3));
+        m.tau[1] = c.l_sqrt2 * ((f1 + f2) - (f0 + f3));
+    }
     m.tau[2] = c.km * ((n1 + n3) - (n0 + n2));
     m.wsum = c.drag_k * ((n[0] + n[1]) + (n[2] + n[3]));
     return m;
 }
 
 // Cascaded PID of Section 4.2.1 (position PID -> T = m |a*| and small-angle attitude
-// target -> attitude PID -> inverse mixing). The mixing rows [1,1,1,1], [1,1,-1,-1],
+// target -> attitude PID -> inverse mixing). The X mixing rows [1,1,1,1], [1,1,-1,-1],
 // [-1,1,1,-1], [-1,1,-1,1] are mutually orthogonal with squared norm 4, so the solve of
-// M f = [T, tau] is f = 1/4 (T + sqrt2/L tau_x r1 + sqrt2/L tau_y r2 + k_f/k_m tau_z r3).
+// M f = [T, tau] is f = 1/4 (T + sqrt2/L tau_x r1 + sqrt2/L tau_y r2 + k_f/k_m tau_z r3);
+// for the + layout the rows [0,1,0,-1] and [-1,0,1,0] (norm^2 2, times L^2) give
+// f = 1/4 (T + 2/L tau_x r1 + 2/L tau_y r2 + k_f/k_m tau_z r3). r1, r2 are mix_x, mix_y.
 __device__ __forceinline__ void pid(Drone& d, const float4 wp, const DevConsts& c, float rpm[4], float ep[3],
                                     float& yaw_err)
 {
@@ -139,8 +146,11 @@ __device__ __forceinline__ void pid(Drone& d, const float4 wp, const DevConsts& 
         tau[r] = c.att_kp[r] * e[r] + c.att_ki[r] * d.ia[r] - c.att_kd[r] * d.w[r];
     }
     const float tx = tau[0] * c.alloc_xy, ty = tau[1] * c.alloc_xy, tz = tau[2] * c.alloc_z;
-    const float f[4] = {0.25f * (T + tx - ty - tz), 0.25f * (T + tx + ty + tz), 0.25f * (T - tx + ty - tz),
-                        0.25f * (T - tx - ty + tz)};
+    // multiplying by the signs +-1, 0 is exact, so the X layout rounds as T + tx - ty - tz
+    const float f[4] = {0.25f * (((T + c.mix_x[0] * tx) + c.mix_y[0] * ty) - tz),
+                        0.25f * (((T + c.mix_x[1] * tx) + c.mix_y[1] * ty) + tz),
+                        0.25f * (((T + c.mix_x[2] * tx) + c.mix_y[2] * ty) - tz),
+                        0.25f * (((T + c.mix_x[3] * tx) + c.mix_y[3] * ty) + tz)};
 #pragma unroll
     for (int i = 0; i < 4; ++i) rpm[i] = sqrtf(fminf(c.f_max, fmaxf(0.f, f[i])) * c.inv_kf);
     yaw_err = e[2];
@@ -514,10 +524,124 @@ __device__ __forceinline__ EnvSlot tile_env(const StepArgs& a, const TileInfo& t
     return e;
 }
 
+// ---- fourth-order Runge-Kutta substeps (MDG_INTEGRATOR_RK4) ----
+
+// Time derivative of one drone's state at a Runge-Kutta stage: the forces of Eq. motor,
+// ground, drag and downwash at the stage state s (its quaternion taken at unit length for
+// the forces; env_pos holds the environment's stage positions) and Newton-Euler:
+// p' = v, q' = 1/2 q (x) [0, w] (body rate on the right), v' = F/m,
+// w' = J^-1 (tau - w x (J w)). The force expressions are those of substep().
+struct StateRate {
+    float p[3], q[4], v[3], w[3];
+};
+
+template <int kFlags, int kN>
+__device__ __forceinline__ void stage_rate(const Drone& s, const Motor& m, int flags_rt, const float4* env_pos,
+                                           int N_rt, const DevConsts& c, StateRate& k)
+{
+    const int flags = kFlags < 8 ? kFlags : flags_rt;
+    const float qi = rsqrtf(s.q[0] * s.q[0] + s.q[1] * s.q[1] + s.q[2] * s.q[2] + s.q[3] * s.q[3]);
+    const float qw = s.q[0] * qi, qx = s.q[1] * qi, qy = s.q[2] * qi, qz = s.q[3] * qi;
+    const float r0 = 2.f * (qx * qz + qw * qy);
+    const float r1 = 2.f * (qy * qz - qw * qx);
+    const float r2 = 1.f - 2.f * (qx * qx + qy * qy);
+    float F[3] = {r0 * m.T, r1 * m.T, r2 * m.T - c.mass * c.g};
+    if (flags & MDG_GND) {
+        const float R20 = 2.f * (qx * qz - qw * qy);
+        const float h = fmaxf(s.p[2], c.h_clip);
+        const float g = c.gnd_k * m.T * rcp_approx(h * h);
+        F[2] += (r2 > 0.f && fabsf(R20) < 1.f) ? g : 0.f;
+    }
+    if (flags & MDG_DRAG) {
+        const float rv = (r0 * s.v[0] + r1 * s.v[1]) + r2 * s.v[2];
+        const float kxy = -m.wsum * c.c_xy, kr = -m.wsum * c.c_dz * rv;
+        F[0] += kxy * s.v[0] + kr * r0;
+        F[1] += kxy * s.v[1] + kr * r1;
+        F[2] += kxy * s.v[2] + kr * r2;
+    }
+    if (flags & MDG_DW) F[2] -= downwash_sum<kN>(env_pos, N_rt, s.p[0], s.p[1], s.p[2], c);
+    const float Jw0 = c.J[0] * s.w[0], Jw1 = c.J[1] * s.w[1], Jw2 = c.J[2] * s.w[2];
+    k.w[0] = c.inv_J[0] * (m.tau[0] - (s.w[1] * Jw2 - s.w[2] * Jw1));
+    k.w[1] = c.inv_J[1] * (m.tau[1] - (s.w[2] * Jw0 - s.w[0] * Jw2));
+    k.w[2] = c.inv_J[2] * (m.tau[2] - (s.w[0] * Jw1 - s.w[1] * Jw0));
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        k.p[r] = s.v[r];
+        k.v[r] = F[r] * c.inv_mass;
+    }
+    // 1/2 q (x) [0, w] with the stage quaternion as it is
+    k.q[0] = 0.5f * (-s.q[1] * s.w[0] - s.q[2] * s.w[1] - s.q[3] * s.w[2]);
+    k.q[1] = 0.5f * (s.q[0] * s.w[0] + s.q[2] * s.w[2] - s.q[3] * s.w[1]);
+    k.q[2] = 0.5f * (s.q[0] * s.w[1] - s.q[1] * s.w[2] + s.q[3] * s.w[0]);
+    k.q[3] = 0.5f * (s.q[0] * s.w[2] + s.q[1] * s.w[1] - s.q[2] * s.w[0]);
+}
+
+// n_sub Runge-Kutta substeps of every drone of the block: k1 = f(x), k2 = f(x + dt/2 k1),
+// k3 = f(x + dt/2 k2), k4 = f(x + dt k3), x+ = x + dt/6 (k1 + 2 k2 + 2 k3 + k4), q
+// renormalised. Each stage publishes its positions into the double-buffered shared array
+// (`ph` counts the publications, so that consecutive stages alternate buffers) and every
+// drone of the environment evaluates the downwash at that stage's positions. Called by
+// every thread of the block (barriers inside).
+template <int kFlags, int kN>
+__device__ __forceinline__ void rk4_substeps(Drone& d, const Motor& m, const EnvSlot& env, float4* s_pos, int B,
+                                             int t, bool active, bool tile_dw, bool warp_local, int n_sub, int& ph,
+                                             const DevConsts& c)
+{
+    const float dt = c.dt_sim;
+    for (int s = 0; s < n_sub; ++s) {
+        Drone st = d;
+        StateRate sum = {};
+#pragma unroll 1
+        for (int stage = 0; stage < 4; ++stage, ++ph) {
+            float4* buf = s_pos + (ph & 1) * B;
+            if (tile_dw) {
+                buf[t] = make_float4(st.p[0], st.p[1], st.p[2], 0.f);
+                if (warp_local) __syncwarp();
+                else __syncthreads();
+            }
+            if (active) {
+                StateRate k;
+                stage_rate<kFlags, kN>(st, m, env.flags, buf + env.ls, env.N, c, k);
+                const float wgt = (stage == 0 || stage == 3) ? 1.f : 2.f;
+                const float h = stage < 2 ? 0.5f * dt : dt;  // offset of the next stage
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    sum.p[r] += wgt * k.p[r];
+                    sum.v[r] += wgt * k.v[r];
+                    sum.w[r] += wgt * k.w[r];
+                    st.p[r] = d.p[r] + h * k.p[r];
+                    st.v[r] = d.v[r] + h * k.v[r];
+                    st.w[r] = d.w[r] + h * k.w[r];
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    sum.q[r] += wgt * k.q[r];
+                    st.q[r] = d.q[r] + h * k.q[r];
+                }
+            }
+        }
+        if (active) {
+            const float h6 = dt * (1.f / 6.f);
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                d.p[r] += h6 * sum.p[r];
+                d.v[r] += h6 * sum.v[r];
+                d.w[r] += h6 * sum.w[r];
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) d.q[r] += h6 * sum.q[r];
+            const float inv = rsqrtf(d.q[0] * d.q[0] + d.q[1] * d.q[1] + d.q[2] * d.q[2] + d.q[3] * d.q[3]);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) d.q[r] *= inv;
+        }
+    }
+}
+
 // Variants with a compile-time environment size (kN > 0), and the runtime-size variant
 // kN = -1, run blocks of at most kSmallBlock threads and may use up to 128 registers;
 // the kN = 0 variant takes any block size (64 registers).
 constexpr int kSmallBlock = 256;
+constexpr int kFlagsRK4 = 9;  // kernel variants with Runge-Kutta substeps (runtime physics flags)
 template <int kN>
 struct StepBounds {
     static constexpr int threads = kN != 0 ? kSmallBlock : 1024;
@@ -572,14 +696,19 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
     // environment of the tile lies inside one warp).
     const bool tile_dw = (tile.bits & kTileAnyDW) != 0;
     const bool warp_local = (tile.bits & kTileWarpLocal) != 0;
-    for (int s = 0; s < a.n_sub; ++s) {
-        float4* buf = s_pos + (s & 1) * B;
-        if (tile_dw) {
-            buf[t] = make_float4(d.p[0], d.p[1], d.p[2], 0.f);
-            if (warp_local) __syncwarp();
-            else __syncthreads();
+    int ph = 0;  // position publications (the double buffer's parity)
+    if (kFlags == kFlagsRK4) {
+        rk4_substeps<kFlags, kN>(d, m, env, s_pos, B, t, active, tile_dw, warp_local, a.n_sub, ph, a.c);
+    } else {
+        for (int s = 0; s < a.n_sub; ++s, ++ph) {
+            float4* buf = s_pos + (s & 1) * B;
+            if (tile_dw) {
+                buf[t] = make_float4(d.p[0], d.p[1], d.p[2], 0.f);
+                if (warp_local) __syncwarp();
+                else __syncthreads();
+            }
+            if (active) substep<kFlags, kN>(d, m, env.flags, buf + env.ls, env.N, a.c);
         }
-        if (active) substep<kFlags, kN>(d, m, env.flags, buf + env.ls, env.N, a.c);
     }
     bool bad = false;
     if (active) {
@@ -593,7 +722,7 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
         atomicMin(a.status + 1, (unsigned)(g + __ffs(bad_mask) - 1));
     }
     if (kObs) {
-        float4* pb = s_pos + (a.n_sub & 1) * B;  // not the buffer the last substep read
+        float4* pb = s_pos + (ph & 1) * B;  // not the buffer the last substep read
         pb[t] = make_float4(d.p[0], d.p[1], d.p[2], 0.f);
         s_vel[t] = make_float4(d.v[0], d.v[1], d.v[2], 0.f);
         __syncthreads();
@@ -737,14 +866,18 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
                 }
             }
             const Motor m = motor(rpm, a.c);
-            for (int s = 0; s < a.n_sub; ++s, ++sub) {
-                float4* buf = s_pos + (sub & 1) * B;
-                if (tile_dw) {
-                    buf[t] = make_float4(d.p[0], d.p[1], d.p[2], 0.f);
-                    if (warp_local) __syncwarp();
-                    else __syncthreads();
+            if (kFlags == kFlagsRK4) {
+                rk4_substeps<kFlags, kN>(d, m, env, s_pos, B, t, active, tile_dw, warp_local, a.n_sub, sub, a.c);
+            } else {
+                for (int s = 0; s < a.n_sub; ++s, ++sub) {
+                    float4* buf = s_pos + (sub & 1) * B;
+                    if (tile_dw) {
+                        buf[t] = make_float4(d.p[0], d.p[1], d.p[2], 0.f);
+                        if (warp_local) __syncwarp();
+                        else __syncthreads();
+                    }
+                    if (active) substep<kFlags, kN>(d, m, env.flags, buf + env.ls, env.N, a.c);
                 }
-                if (active) substep<kFlags, kN>(d, m, env.flags, buf + env.ls, env.N, a.c);
             }
             if (r.obs_mode == 2 || (r.obs_mode == 1 && k == r.K - 1)) {
                 const long long o = r.obs_mode == 2 ? (long long)k * a.n : 0;
@@ -1053,13 +1186,17 @@ __global__ void __launch_bounds__(256) pid_kernel(const PidArgs a)
 
 // The step-kernel variants: compile-time physics subset and environment size for the
 // uniform batches of the benchmark workloads, and a runtime-generic one for the rest.
-#define MDG_STEP_VARIANTS(X) X(7, 4) X(7, 64) X(3, 1) X(8, -1) X(8, 0)
+// (physics flags, environment size): kFlags 0-7 a compile-time physics subset, 8 the
+// runtime flags, kFlagsRK4 the runtime flags with Runge-Kutta substeps; kN > 0 a
+// compile-time environment size, -1 a runtime size in blocks of at most kSmallBlock
+// threads, 0 any block size.
+#define MDG_STEP_VARIANTS(X) X(7, 4) X(7, 64) X(3, 1) X(8, -1) X(8, 0) X(9, -1) X(9, 0)
 
 template <bool kObs>
 static void* step_kernel_ptr(int flags, int N, int block)
 {
 #define MDG_PICK(F, NN)                                                                       \
-    if ((F == 8 || flags == F) &&                                                             \
+    if ((flags == F || (F == 8 && flags != kFlagsRK4)) &&                                                             \
         (NN == 0 || (block <= kSmallBlock && (NN == -1 || N == NN))))                         \
         return (void*)step_kernel<kObs, F, NN>;
     MDG_STEP_VARIANTS(MDG_PICK)
@@ -1095,9 +1232,10 @@ cudaError_t launch_step(const StepArgs& a, int n_tiles, int block, bool with_obs
     if (n_tiles == 0) return cudaSuccess;
     cudaError_t e = tile_kernels_setup();
     if (e != cudaSuccess) return e;
-    // a compile-time variant needs one physics subset and one environment size for the batch
-    const int flags = uniform_flags;
-    const int N = a.uniform_N;
+    // a compile-time variant needs one physics subset and one environment size for the
+    // batch; Runge-Kutta substeps have runtime-generic variants of their own
+    const int flags = a.c.rk4 ? kFlagsRK4 : uniform_flags;
+    const int N = a.c.rk4 ? -1 : a.uniform_N;
     void* fn = with_obs ? step_kernel_ptr<true>(flags, N, block) : step_kernel_ptr<false>(flags, N, block);
     void* args[] = {const_cast<StepArgs*>(&a)};
     const size_t smem = with_obs && a.obs_host ? obs_stage_offset(block) + obs_stage_bytes(block) : tile_smem_bytes(block);
@@ -1109,7 +1247,7 @@ static size_t rollout_smem_bytes(int B) { return (size_t)B * 48 + (size_t)(3 * B
 static void* rollout_kernel_ptr(int flags, int N, int block)
 {
 #define MDG_PICK(F, NN)                                                                       \
-    if ((F == 8 || flags == F) &&                                                             \
+    if ((flags == F || (F == 8 && flags != kFlagsRK4)) &&                                                             \
         (NN == 0 || (block <= kSmallBlock && (NN == -1 || N == NN))))                         \
         return (void*)rollout_kernel<F, NN>;
     MDG_STEP_VARIANTS(MDG_PICK)
@@ -1135,8 +1273,9 @@ static cudaError_t rollout_setup()
     return cudaSuccess;
 }
 
-int rollout_blocks_per_sm(int block, int uniform_flags, int uniform_N)
+int rollout_blocks_per_sm(int block, int uniform_flags, int uniform_N, bool rk4)
 {
+    if (rk4) uniform_flags = kFlagsRK4, uniform_N = -1;  // Runge-Kutta variants
     if (rollout_setup() != cudaSuccess) return 1;
     int n = 0;
     void* fn = rollout_kernel_ptr(uniform_flags, uniform_N, block);
@@ -1148,9 +1287,11 @@ int rollout_blocks_per_sm(int block, int uniform_flags, int uniform_N)
 cudaError_t launch_rollout(const RolloutArgs& r, int block, int uniform_flags, int grid, cudaStream_t s)
 {
     if (r.n_items == 0 || r.K == 0) return cudaSuccess;
+    const int uniform_N = r.s.c.rk4 ? -1 : r.s.uniform_N;
+    if (r.s.c.rk4) uniform_flags = kFlagsRK4;  // Runge-Kutta variants
     cudaError_t e = rollout_setup();
     if (e != cudaSuccess) return e;
-    void* fn = rollout_kernel_ptr(uniform_flags, r.s.uniform_N, block);
+    void* fn = rollout_kernel_ptr(uniform_flags, uniform_N, block);
     if (grid <= 0 || grid > r.n_items) grid = r.n_items;
     void* args[] = {const_cast<RolloutArgs*>(&r)};
     return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, rollout_smem_bytes(block), s);

@@ -81,9 +81,22 @@ def test_create_rejects_bad_constants(mdg_lib):
     rc, _ = _create(1, [1], [0], c)
     assert rc == mdg.ERR_ARG
     c = mdg.Constants.cf2x()
-    c.frame = 1
+    c.frame = 2
     rc, _ = _create(1, [1], [0], c)
     assert rc == mdg.ERR_ARG and "frame" in mdg_lib.mdg_last_error().decode()
+    c = mdg.Constants.cf2x()
+    c.integrator = 7
+    rc, _ = _create(1, [1], [0], c)
+    assert rc == mdg.ERR_ARG and "integrator" in mdg_lib.mdg_last_error().decode()
+
+
+@pytest.mark.parametrize("model", ["cf2p", "race"])
+def test_model_constants_match_the_oracle(mdg_lib, model):
+    """CF2P and RACE: the library's constants equal the oracle's own table field by field."""
+    c = getattr(mdg.Constants, model)().to_dict()
+    o = getattr(oracle, model)().to_dict()
+    for k, v in o.items():
+        np.testing.assert_allclose(c[k], v, rtol=1e-15, err_msg=k)
 
 
 def test_null_handle_calls_fail_cleanly(mdg_lib):
