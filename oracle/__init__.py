@@ -29,6 +29,7 @@ GND, DRAG, DW = 1, 2, 4
 ACT_RPM, ACT_PID = 0, 1
 FRAME_X, FRAME_P = 0, 1
 EULER, RK4 = 0, 1
+GND_COM, GND_ROTOR = 0, 1
 
 _lock = threading.Lock()
 _lib = None
@@ -58,7 +59,7 @@ class Params(ctypes.Structure):
         ("att_kp", ctypes.c_double * 3), ("att_ki", ctypes.c_double * 3), ("att_kd", ctypes.c_double * 3),
         ("att_iclamp", ctypes.c_double),
         ("dt_sim", ctypes.c_double), ("dt_ctrl", ctypes.c_double),
-        ("frame", ctypes.c_int32), ("integrator", ctypes.c_int32)]
+        ("frame", ctypes.c_int32), ("integrator", ctypes.c_int32), ("gnd_heights", ctypes.c_int32)]
 
     def to_dict(self) -> dict:
         out = {}
@@ -91,6 +92,7 @@ def lib():
                 "orc_rotation": ([_D, _D], None),
                 "orc_rpy": ([_D, _D], None),
                 "orc_motor": ([P, _D, _D, _D], None),
+                "orc_rotor_position": ([P, ctypes.c_int, _D], None),
                 "orc_env_forces": ([P, ctypes.c_int, _D, _D, ctypes.c_int, _D, _D], None),
                 "orc_substep": ([P, ctypes.c_int, _D, _D, ctypes.c_int, ctypes.c_double, _D], None),
                 "orc_allocation_matrix": ([P, _D], None),
@@ -180,6 +182,13 @@ def motor(p: Params, rpm):
     tau = np.zeros(3)
     lib().orc_motor(ctypes.byref(p), _dptr(rpm), ctypes.byref(T), _dptr(tau))
     return T.value, tau
+
+
+def rotor_position(p: Params, i: int) -> np.ndarray:
+    """Body-frame position of rotor i (read from the torque equations of Section 3.1.2)."""
+    r = np.zeros(3)
+    lib().orc_rotor_position(ctypes.byref(p), int(i), _dptr(r))
+    return r
 
 
 def env_forces(p: Params, x, rpm, flags: int):

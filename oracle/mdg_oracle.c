@@ -45,6 +45,13 @@
 #define ORC_EULER 0
 #define ORC_RK4 1
 
+/* Heights at which Eq. ground is evaluated: the centre of mass for all four rotors (h from
+ * p_z, as printed), or each rotor's own height (a variant: rotor i adds
+ * C_gnd k_f n_i^2 (r_p/(4 h_i))^2, h_i = max(p_z + (R r_i)_z, h_clip), r_i its body
+ * position). */
+#define ORC_GND_COM 0
+#define ORC_GND_ROTOR 1
+
 /* Model parameters. Field order is the oracle's own; the Python side of the
  * oracle mirrors it. */
 typedef struct {
@@ -60,6 +67,7 @@ typedef struct {
     double dt_sim, dt_ctrl;
     int32_t frame;      /* ORC_FRAME_X / ORC_FRAME_P */
     int32_t integrator; /* ORC_EULER / ORC_RK4 */
+    int32_t gnd_heights; /* ORC_GND_COM / ORC_GND_ROTOR */
 } orc_params;
 
 int orc_params_size(void) { return (int)sizeof(orc_params); }
@@ -116,6 +124,7 @@ void orc_params_cf2x(orc_params* P)
     P->dt_ctrl = 1.0 / 48.0;
     P->frame = ORC_FRAME_X;
     P->integrator = ORC_EULER;
+    P->gnd_heights = ORC_GND_COM;
 }
 
 /* CF2P: the CF2X parameters (Table "Drone model parameters" lists one column for both)
@@ -228,6 +237,25 @@ void orc_motor(const orc_params* P, const double rpm[4], double* T, double tau[3
     tau[2] = P->km * (-n2[0] + n2[1] - n2[2] + n2[3]);
 }
 
+/* Body-frame position of rotor i (z = 0). With tau = sum_i r_i x (0, 0, F_i), i.e.
+ * tau_x = sum_i y_i F_i and tau_y = -sum_i x_i F_i, the torque equations of Section 3.1.2
+ * place the X layout's rotors at L/sqrt2 (+,+), (-,+), (-,-), (+,-) and the + layout's at
+ * L (+x, +y, -x, -y) (orc_motor). */
+void orc_rotor_position(const orc_params* P, int i, double r[3])
+{
+    static const double xs[4] = {1.0, -1.0, -1.0, 1.0}, ys[4] = {1.0, 1.0, -1.0, -1.0};
+    static const double xp[4] = {1.0, 0.0, -1.0, 0.0}, yp[4] = {0.0, 1.0, 0.0, -1.0};
+    if (P->frame == ORC_FRAME_P) {
+        r[0] = P->arm * xp[i];
+        r[1] = P->arm * yp[i];
+    } else {
+        const double l = P->arm / sqrt(2.0);
+        r[0] = l * xs[i];
+        r[1] = l * ys[i];
+    }
+    r[2] = 0.0;
+}
+
 /* World-frame force (gravity included) and body-frame torque on every drone of
  * one environment of N drones. x is [N][13] = p(3) q(4) v(3) omega(3), omega in
  * the body frame; rpm is [N][4]. All drones read the same state snapshot x. */
@@ -246,13 +274,25 @@ void orc_env_forces(const orc_params* P, int N, const double* x, const double* r
 
         if (flags & ORC_GND) {
             /* Eq. ground: C_gnd * sum_i k_f n_i^2 * (r_p/(4h))^2, h = max(p_z, h_clip),
-             * applied along world +z, gated on |roll|, |pitch| < pi/2. */
+             * applied along world +z, gated on |roll|, |pitch| < pi/2. With per-rotor
+             * heights, h_i = max(p_z + (R r_i)_z, h_clip) for rotor i. */
             double rpy[3];
             orc_rpy(q, rpy);
             if (fabs(rpy[0]) < ORC_PI / 2 && fabs(rpy[1]) < ORC_PI / 2) {
-                double h = fmax(xj[2], P->h_clip);
-                double r = P->prop_radius / (4.0 * h);
-                fw[2] += P->c_gnd * T * r * r;
+                if (P->gnd_heights == ORC_GND_ROTOR) {
+                    const double* n = rpm + 4 * j;
+                    for (int i = 0; i < 4; ++i) {
+                        double ri[3];
+                        orc_rotor_position(P, i, ri);
+                        double zi = xj[2] + R[6] * ri[0] + R[7] * ri[1] + R[8] * ri[2];
+                        double r = P->prop_radius / (4.0 * fmax(zi, P->h_clip));
+                        fw[2] += P->c_gnd * P->kf * n[i] * n[i] * r * r;
+                    }
+                } else {
+                    double h = fmax(xj[2], P->h_clip);
+                    double r = P->prop_radius / (4.0 * h);
+                    fw[2] += P->c_gnd * T * r * r;
+                }
             }
         }
         if (flags & ORC_DRAG) {

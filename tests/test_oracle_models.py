@@ -218,3 +218,107 @@ def test_race_constants_match_the_printed_table():
     P = oracle.race()
     assert oracle.hover_rpm(P) == pytest.approx(np.sqrt(P.mass * P.g / (4 * P.kf)), rel=1e-15)
     assert 4 * P.kf * oracle.max_rpm(P) ** 2 == pytest.approx(P.thrust2weight * P.mass * P.g, rel=1e-14)
+
+
+# ------------------------------------------------------------------ per-rotor ground-effect heights
+def _gnd_rotor(P):
+    P.gnd_heights = oracle.GND_ROTOR
+    return P
+
+
+@pytest.mark.parametrize("model", ["cf2x", "cf2p", "race"])
+def test_rotor_positions_reproduce_the_torque_equations(model):
+    """tau = sum_i r_i x (0, 0, F_i) with the rotor positions equals orc_motor's roll and
+    pitch torques (Section 3.1.2) for random rotor speeds."""
+    P = getattr(oracle, model)()
+    r = np.array([oracle.rotor_position(P, i) for i in range(4)])
+    assert np.all(r[:, 2] == 0)
+    np.testing.assert_allclose(np.hypot(r[:, 0], r[:, 1]), P.arm, rtol=1e-15)
+    rng = np.random.default_rng(21)
+    for _ in range(5):
+        rpm = rng.uniform(5000, 20000, 4)
+        F = P.kf * rpm ** 2
+        _, tau = oracle.motor(P, rpm)
+        tau_geo = np.cross(r, np.stack([np.zeros(4), np.zeros(4), F], axis=1)).sum(axis=0)
+        np.testing.assert_allclose(tau[:2], tau_geo[:2], rtol=1e-13, atol=1e-22)
+
+
+@pytest.mark.parametrize("model", ["cf2x", "cf2p"])
+def test_per_rotor_ground_effect_of_a_level_drone_is_the_printed_one(model):
+    """Level: every rotor sits at p_z, so the variant equals Eq. ground at the CoM height,
+    also below h_clip."""
+    Pc = getattr(oracle, model)()
+    Pr = _gnd_rotor(getattr(oracle, model)())
+    rng = np.random.default_rng(22)
+    for z in (0.005, Pc.h_clip, 0.03, 0.2, 1.5):
+        x = _level(p=(0.1, -0.2, z), v=(0.3, 0.1, -0.2))
+        rpm = rng.uniform(10000, 20000, (1, 4))
+        Fc, _ = oracle.env_forces(Pc, x, rpm, oracle.GND)
+        Fr, _ = oracle.env_forces(Pr, x, rpm, oracle.GND)
+        np.testing.assert_allclose(Fr, Fc, rtol=1e-14, atol=0)
+
+
+def _axis_quat(axis, angle):
+    q = np.zeros(4)
+    q[0] = np.cos(angle / 2)
+    q[1 + axis] = np.sin(angle / 2)
+    return q
+
+
+@pytest.mark.parametrize("model, axis, rotor, offset", [
+    # X layout, rotor 0 at (l, l): rolled by phi about body x its height is z + l sin(phi),
+    # pitched by theta about body y it is z - l sin(theta) (l = L/sqrt2)
+    ("cf2x", 0, 0, lambda P, a: P.arm / np.sqrt(2) * np.sin(a)),
+    ("cf2x", 1, 0, lambda P, a: -P.arm / np.sqrt(2) * np.sin(a)),
+    ("cf2x", 0, 2, lambda P, a: -P.arm / np.sqrt(2) * np.sin(a)),
+    # + layout: rotor 1 on +y rises with roll, rotor 0 on +x sinks with pitch, rotor 0 does
+    # not move under roll
+    ("cf2p", 0, 1, lambda P, a: P.arm * np.sin(a)),
+    ("cf2p", 1, 0, lambda P, a: -P.arm * np.sin(a)),
+    ("cf2p", 0, 0, lambda P, a: 0.0),
+])
+def test_per_rotor_ground_effect_of_one_rotor_on_a_tilted_drone(model, axis, rotor, offset):
+    """One rotor spinning on a drone tilted about a body axis: the increment is Eq. ground
+    for that rotor at the height its lever arm gives it (hand geometry), thrust along the
+    tilted body z axis."""
+    P = _gnd_rotor(getattr(oracle, model)())
+    z, ang, n = 0.08, 0.4, 16000.0
+    x = _level(p=(0.0, 0.0, z), q=_axis_quat(axis, ang))
+    rpm = np.zeros((1, 4))
+    rpm[0, rotor] = n
+    F, _ = oracle.env_forces(P, x, rpm, oracle.GND)
+    f = P.kf * n * n
+    h = z + offset(P, ang)
+    expected = f * np.cos(ang) - P.mass * P.g + P.c_gnd * f * (P.prop_radius / (4 * h)) ** 2
+    assert F[0, 2] == pytest.approx(expected, rel=1e-13)
+
+
+def test_per_rotor_ground_effect_clips_each_rotor():
+    """A rotor lowered below h_clip is clipped on its own: at p_z = h_clip and roll phi, rotor 2
+    (lowered) sees h_clip, rotor 0 (raised) h_clip + l sin(phi)."""
+    P = _gnd_rotor(oracle.cf2x())
+    ang, n = 0.3, 15000.0
+    x = _level(p=(0.0, 0.0, P.h_clip), q=_axis_quat(0, ang))
+    f = P.kf * n * n
+    for rotor, h in ((2, P.h_clip), (0, P.h_clip + P.arm / np.sqrt(2) * np.sin(ang))):
+        rpm = np.zeros((1, 4))
+        rpm[0, rotor] = n
+        F, _ = oracle.env_forces(P, x, rpm, oracle.GND)
+        gnd = F[0, 2] - (f * np.cos(ang) - P.mass * P.g)
+        assert gnd == pytest.approx(P.c_gnd * f * (P.prop_radius / (4 * h)) ** 2, rel=1e-12)
+
+
+def test_per_rotor_ground_effect_symmetry_and_convexity():
+    """Equal rotor speeds: rolling by +phi or -phi gives the same force (the rotor pairs swap
+    heights), and since 1/h^2 is convex the per-rotor increment exceeds the CoM one for a
+    tilted drone whose rotors all stay above h_clip (Jensen)."""
+    Pc, Pr = oracle.cf2x(), _gnd_rotor(oracle.cf2x())
+    rpm = np.full((1, 4), 15000.0)
+    for axis in (0, 1):
+        xp = _level(p=(0.2, 0.1, 0.06), q=_axis_quat(axis, 0.35))
+        xm = _level(p=(0.2, 0.1, 0.06), q=_axis_quat(axis, -0.35))
+        Fp, _ = oracle.env_forces(Pr, xp, rpm, oracle.GND)
+        Fm, _ = oracle.env_forces(Pr, xm, rpm, oracle.GND)
+        np.testing.assert_allclose(Fp[0, 2], Fm[0, 2], rtol=1e-14)
+        Fc, _ = oracle.env_forces(Pc, xp, rpm, oracle.GND)
+        assert Fp[0, 2] > Fc[0, 2] + 1e-6

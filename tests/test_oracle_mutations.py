@@ -55,6 +55,13 @@ MUTATIONS = {
     "plus_allocation_row": ("{{1, 1, 1, 1}, {0, L, 0, -L}, {-L, 0, L, 0}, {-r, r, -r, r}}",
                             "{{1, 1, 1, 1}, {L, 0, -L, 0}, {-L, 0, L, 0}, {-r, r, -r, r}}"),
     "race_gain_ratio": ("P->att_kp[r] = cf.att_kp[r] * ratio[r];", "P->att_kp[r] = cf.att_kp[r];"),
+    "rotor_height_sign": ("double zi = xj[2] + R[6] * ri[0] + R[7] * ri[1] + R[8] * ri[2];",
+                          "double zi = xj[2] - R[6] * ri[0] - R[7] * ri[1] - R[8] * ri[2];"),
+    "rotor_height_transposed": ("double zi = xj[2] + R[6] * ri[0] + R[7] * ri[1] + R[8] * ri[2];",
+                                "double zi = xj[2] + R[2] * ri[0] + R[5] * ri[1] + R[8] * ri[2];"),
+    "rotor_height_at_com": ("double r = P->prop_radius / (4.0 * fmax(zi, P->h_clip));",
+                            "double r = P->prop_radius / (4.0 * fmax(xj[2], P->h_clip));"),
+    "rotor_positions_swapped": ("r[0] = l * xs[i];", "r[0] = l * ys[i];"),
 }
 
 
