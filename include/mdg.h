@@ -89,11 +89,18 @@ typedef struct mdg_ctx* mdg_handle;
  * substep: MDG_INTEGRATOR_EULER (the DYN mode's explicit Euler with the exponential map)
  * or MDG_INTEGRATOR_RK4 (classical fourth-order Runge-Kutta on each environment's drones
  * jointly, every stage evaluating every force at that stage's states, the quaternion
- * renormalised after the substep; Table "Physics modes" lists RK4 for the MuJoCo modes). */
+ * renormalised after the substep; Table "Physics modes" lists RK4 for the MuJoCo modes).
+ * gnd_heights selects where Eq. ground takes h: MDG_GND_COM (the centre of mass for all
+ * four rotors, as printed) or MDG_GND_ROTOR (rotor i adds C_gnd k_f n_i^2 (r_p/(4 h_i))^2
+ * with h_i = max(p_z + (R r_i)_z, h_clip), r_i its body position: L/sqrt2 (+,+), (-,+),
+ * (-,-), (+,-) for X, L (+x, +y, -x, -y) for +, as the torque equations of Section 3.1.2
+ * place them). */
 #define MDG_FRAME_X 0
 #define MDG_FRAME_P 1
 #define MDG_INTEGRATOR_EULER 0
 #define MDG_INTEGRATOR_RK4 1
+#define MDG_GND_COM 0
+#define MDG_GND_ROTOR 1
 typedef struct mdg_constants {
     double mass, arm, thrust2weight, Jxx, Jyy, Jzz, kf, km, prop_radius;
     double g;
@@ -104,6 +111,7 @@ typedef struct mdg_constants {
     double dt_sim, dt_ctrl;
     int32_t frame;
     int32_t integrator;
+    int32_t gnd_heights;
 } mdg_constants;
 
 /* Fill *out with the CF2X constants (Table "Drone model parameters", Eq. downwash

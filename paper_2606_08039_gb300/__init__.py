@@ -35,6 +35,7 @@ MAX_ENV_DRONES = 1024
 OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_UNSUPPORTED, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
 FRAME_X, FRAME_P = 0, 1
 INTEGRATOR_EULER, INTEGRATOR_RK4 = 0, 1
+GND_COM, GND_ROTOR = 0, 1
 OBS_NONE, OBS_LAST, OBS_EVERY_STEP = 0, 1, 2
 MLP_IN, MLP_IN_PAD, MLP_HIDDEN, MLP_OUT, MLP_OUT_PAD = 41, 64, 256, 13, 32
 MLP_DIMS = (MLP_IN_PAD, MLP_HIDDEN, MLP_HIDDEN, MLP_HIDDEN, MLP_OUT_PAD)
@@ -138,7 +139,7 @@ class Constants(ctypes.Structure):
         ("att_kp", ctypes.c_double * 3), ("att_ki", ctypes.c_double * 3), ("att_kd", ctypes.c_double * 3),
         ("att_iclamp", ctypes.c_double),
         ("dt_sim", ctypes.c_double), ("dt_ctrl", ctypes.c_double),
-        ("frame", ctypes.c_int32), ("integrator", ctypes.c_int32)]
+        ("frame", ctypes.c_int32), ("integrator", ctypes.c_int32), ("gnd_heights", ctypes.c_int32)]
 
     @classmethod
     def cf2x(cls) -> "Constants":

@@ -87,6 +87,10 @@ bool constants_valid(const mdg_constants& c, std::string& why)
         why = "integrator must be MDG_INTEGRATOR_EULER or MDG_INTEGRATOR_RK4";
         return false;
     }
+    if (c.gnd_heights != MDG_GND_COM && c.gnd_heights != MDG_GND_ROTOR) {
+        why = "gnd_heights must be MDG_GND_COM or MDG_GND_ROTOR";
+        return false;
+    }
     return true;
 }
 
@@ -136,6 +140,7 @@ DevConsts make_dev_consts(const mdg_constants& c)
     d.alloc_z = (float)(c.kf / c.km);
     d.frame_p = c.frame == MDG_FRAME_P ? 1 : 0;
     d.rk4 = c.integrator == MDG_INTEGRATOR_RK4 ? 1 : 0;
+    d.gnd_rotor = c.gnd_heights == MDG_GND_ROTOR ? 1 : 0;
     if (d.frame_p) {
         // + layout: tau_x = L (F1 - F3), tau_y = L (F2 - F0); the mixing rows [1,1,1,1],
         // [0,1,0,-1] L, [-1,0,1,0] L, [-1,1,-1,1] k_m/k_f are orthogonal with squared norms
@@ -148,6 +153,12 @@ DevConsts make_dev_consts(const mdg_constants& c)
         d.alloc_xy = (float)(sqrt(2.0) / c.arm);
         const float sx[4] = {1.f, 1.f, -1.f, -1.f}, sy[4] = {-1.f, 1.f, 1.f, -1.f};
         for (int i = 0; i < 4; ++i) d.mix_x[i] = sx[i], d.mix_y[i] = sy[i];
+    }
+    // rotor body positions: tau_x = sum_i y_i F_i and tau_y = -sum_i x_i F_i, so rotor i
+    // sits at y_i = a mix_x[i], x_i = -a mix_y[i] with a = L/sqrt2 (X) or L (+)
+    for (int i = 0; i < 4; ++i) {
+        d.rotor_x[i] = -d.l_sqrt2 * d.mix_y[i];
+        d.rotor_y[i] = d.l_sqrt2 * d.mix_x[i];
     }
     return d;
 }
@@ -811,7 +822,8 @@ static cudaError_t enqueue_rollout(mdg_handle h, const mdg::RolloutArgs& r, cuda
     if (e != cudaSuccess) return e;
     int n_sm = 152;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device);
-    const int grid = n_sm * mdg::rollout_blocks_per_sm(h->block, h->uniform_flags, h->uniform_N, h->dc.rk4 != 0);
+    const int grid = n_sm * mdg::rollout_blocks_per_sm(h->block, h->uniform_flags, h->uniform_N, h->dc.rk4 != 0,
+                                                           h->dc.gnd_rotor != 0);
     return mdg::launch_rollout(r, h->block, h->uniform_flags, grid, s);
 }
 

@@ -40,6 +40,8 @@ struct DevConsts {
     float mix_x[4], mix_y[4];         // inverse mixing signs of tau_x, tau_y per rotor
     int frame_p;                      // 1: + rotor layout (l_sqrt2 then holds L)
     int rk4;                          // 1: fourth-order Runge-Kutta substeps
+    int gnd_rotor;                    // 1: Eq. ground at each rotor's height (runtime-flag kernels)
+    float rotor_x[4], rotor_y[4];     // rotor body positions (z = 0)
 };
 
 // A launch tile: whole environments packed into one thread block.
@@ -138,7 +140,7 @@ int default_block(int32_t max_env, int64_t n_drones, int n_sm);
 cudaError_t launch_step(const StepArgs& a, int n_tiles, int block, bool with_obs, int uniform_flags, cudaStream_t s);
 // grid: persistent CTAs (0: one per work item)
 cudaError_t launch_rollout(const RolloutArgs& a, int block, int uniform_flags, int grid, cudaStream_t s);
-int rollout_blocks_per_sm(int block, int uniform_flags, int uniform_N, bool rk4);
+int rollout_blocks_per_sm(int block, int uniform_flags, int uniform_N, bool rk4, bool gnd_rotor);
 cudaError_t launch_features(const SurrogateArgs& a, int n_tiles, int block, cudaStream_t s);
 cudaError_t launch_surrogate_prepare(const SurrogateArgs& a, int n_tiles, int block, cudaStream_t s);
 cudaError_t launch_surrogate_apply(const SurrogateArgs& a, cudaStream_t s);

@@ -198,6 +198,37 @@ __device__ __forceinline__ float downwash_sum(const float4* env_pos, int N_rt, f
     return acc;
 }
 
+// Kernel variants beyond the compile-time physics subsets 0-7 (all take the physics flags
+// at run time): 8 Euler substeps, kFlagsRK4 Runge-Kutta substeps, kFlagsGndRotor Euler
+// substeps with Eq. ground at each rotor's height. The Runge-Kutta variants handle
+// per-rotor heights too; variant 8 leaves that code out, so that its register allocation
+// is the one the mixed-physics batches need.
+constexpr int kFlagsRK4 = 9;
+constexpr int kFlagsGndRotor = 10;
+
+// Eq. ground's increment along world +z, before its gate. With per-rotor heights rotor i
+// is at height p_z + R20 x_i + R21 y_i, and its thrust f_i is recovered from T and the
+// torques by the inverse mixing the PID uses (orthogonal rows).
+template <int kFlags>
+__device__ __forceinline__ float ground_increment(const Motor& m, float pz, float qw, float qx, float qy, float qz,
+                                                  float R20, const DevConsts& c)
+{
+    if ((kFlags == kFlagsRK4 || kFlags == kFlagsGndRotor) && c.gnd_rotor) {
+        const float R21 = 2.f * (qy * qz + qw * qx);
+        const float tx = c.alloc_xy * m.tau[0], ty = c.alloc_xy * m.tau[1], tz = c.alloc_z * m.tau[2];
+        float acc = 0.f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float f = 0.25f * (((m.T + c.mix_x[i] * tx) + c.mix_y[i] * ty) + ((i & 1) ? tz : -tz));
+            const float h = fmaxf(fmaf(R20, c.rotor_x[i], fmaf(R21, c.rotor_y[i], pz)), c.h_clip);
+            acc = fmaf(f, rcp_approx(h * h), acc);
+        }
+        return c.gnd_k * acc;
+    }
+    const float h = fmaxf(pz, c.h_clip);
+    return c.gnd_k * m.T * rcp_approx(h * h);
+}
+
 // One substep: forces of Eq. motor/ground/drag/downwash, Newton-Euler, forward Euler
 // and the exponential map, all from the start-of-substep state. `env_pos` points at the
 // shared-memory positions of this drone's environment (N entries). kFlags (0..7) and kN
@@ -233,8 +264,7 @@ __device__ __forceinline__ void substep(Drone& d, const Motor& m, int flags_rt, 
     if (flags & MDG_GND) {
         // gate |roll| < pi/2 and |pitch| < pi/2: cos(roll) cos(pitch) = R22 > 0, |sin(pitch)| = |R20| < 1
         const float R20 = 2.f * (qx * qz - qw * qy);
-        const float h = fmaxf(d.p[2], c.h_clip);
-        const float g = c.gnd_k * m.T * rcp_approx(h * h);
+        const float g = ground_increment<kFlags>(m, d.p[2], qw, qx, qy, qz, R20, c);
         F[2] += (r2 > 0.f && fabsf(R20) < 1.f) ? g : 0.f;
     }
     if (flags & MDG_DRAG) {
@@ -548,8 +578,7 @@ __device__ __forceinline__ void stage_rate(const Drone& s, const Motor& m, int f
     float F[3] = {r0 * m.T, r1 * m.T, r2 * m.T - c.mass * c.g};
     if (flags & MDG_GND) {
         const float R20 = 2.f * (qx * qz - qw * qy);
-        const float h = fmaxf(s.p[2], c.h_clip);
-        const float g = c.gnd_k * m.T * rcp_approx(h * h);
+        const float g = ground_increment<kFlags>(m, s.p[2], qw, qx, qy, qz, R20, c);
         F[2] += (r2 > 0.f && fabsf(R20) < 1.f) ? g : 0.f;
     }
     if (flags & MDG_DRAG) {
@@ -641,7 +670,6 @@ __device__ __forceinline__ void rk4_substeps(Drone& d, const Motor& m, const Env
 // kN = -1, run blocks of at most kSmallBlock threads and may use up to 128 registers;
 // the kN = 0 variant takes any block size (64 registers).
 constexpr int kSmallBlock = 256;
-constexpr int kFlagsRK4 = 9;  // kernel variants with Runge-Kutta substeps (runtime physics flags)
 template <int kN>
 struct StepBounds {
     static constexpr int threads = kN != 0 ? kSmallBlock : 1024;
@@ -1149,7 +1177,7 @@ __global__ void __launch_bounds__(128) surrogate_fallback_kernel(const Surrogate
             float4* buf = s_pos[wib][s & 1];
             buf[lane] = make_float4(d.p[0], d.p[1], d.p[2], 0.f);
             __syncwarp();
-            if (active) substep<8, -1>(d, m, flags, buf, N, a.c);
+            if (active) substep<kFlagsGndRotor, -1>(d, m, flags, buf, N, a.c);
         }
         if (active) {
             store_state(a.state, a.n, g, d, false);
@@ -1187,16 +1215,17 @@ __global__ void __launch_bounds__(256) pid_kernel(const PidArgs a)
 // The step-kernel variants: compile-time physics subset and environment size for the
 // uniform batches of the benchmark workloads, and a runtime-generic one for the rest.
 // (physics flags, environment size): kFlags 0-7 a compile-time physics subset, 8 the
-// runtime flags, kFlagsRK4 the runtime flags with Runge-Kutta substeps; kN > 0 a
+// runtime flags, kFlagsRK4 the runtime flags with Runge-Kutta substeps, kFlagsGndRotor
+// the runtime flags with per-rotor ground heights; kN > 0 a
 // compile-time environment size, -1 a runtime size in blocks of at most kSmallBlock
 // threads, 0 any block size.
-#define MDG_STEP_VARIANTS(X) X(7, 4) X(7, 64) X(3, 1) X(8, -1) X(8, 0) X(9, -1) X(9, 0)
+#define MDG_STEP_VARIANTS(X) X(7, 4) X(7, 64) X(3, 1) X(8, -1) X(8, 0) X(9, -1) X(9, 0) X(10, -1) X(10, 0)
 
 template <bool kObs>
 static void* step_kernel_ptr(int flags, int N, int block)
 {
 #define MDG_PICK(F, NN)                                                                       \
-    if ((flags == F || (F == 8 && flags != kFlagsRK4)) &&                                                             \
+    if ((flags == F || (F == 8 && flags != kFlagsRK4 && flags != kFlagsGndRotor)) &&                                \
         (NN == 0 || (block <= kSmallBlock && (NN == -1 || N == NN))))                         \
         return (void*)step_kernel<kObs, F, NN>;
     MDG_STEP_VARIANTS(MDG_PICK)
@@ -1234,7 +1263,8 @@ cudaError_t launch_step(const StepArgs& a, int n_tiles, int block, bool with_obs
     if (e != cudaSuccess) return e;
     // a compile-time variant needs one physics subset and one environment size for the
     // batch; Runge-Kutta substeps have runtime-generic variants of their own
-    const int flags = a.c.rk4 ? kFlagsRK4 : uniform_flags;
+    // Runge-Kutta substeps and per-rotor ground heights run in the runtime-flag variants
+    const int flags = a.c.rk4 ? kFlagsRK4 : (a.c.gnd_rotor ? kFlagsGndRotor : uniform_flags);
     const int N = a.c.rk4 ? -1 : a.uniform_N;
     void* fn = with_obs ? step_kernel_ptr<true>(flags, N, block) : step_kernel_ptr<false>(flags, N, block);
     void* args[] = {const_cast<StepArgs*>(&a)};
@@ -1247,7 +1277,7 @@ static size_t rollout_smem_bytes(int B) { return (size_t)B * 48 + (size_t)(3 * B
 static void* rollout_kernel_ptr(int flags, int N, int block)
 {
 #define MDG_PICK(F, NN)                                                                       \
-    if ((flags == F || (F == 8 && flags != kFlagsRK4)) &&                                                             \
+    if ((flags == F || (F == 8 && flags != kFlagsRK4 && flags != kFlagsGndRotor)) &&                                \
         (NN == 0 || (block <= kSmallBlock && (NN == -1 || N == NN))))                         \
         return (void*)rollout_kernel<F, NN>;
     MDG_STEP_VARIANTS(MDG_PICK)
@@ -1273,9 +1303,10 @@ static cudaError_t rollout_setup()
     return cudaSuccess;
 }
 
-int rollout_blocks_per_sm(int block, int uniform_flags, int uniform_N, bool rk4)
+int rollout_blocks_per_sm(int block, int uniform_flags, int uniform_N, bool rk4, bool gnd_rotor)
 {
     if (rk4) uniform_flags = kFlagsRK4, uniform_N = -1;  // Runge-Kutta variants
+    else if (gnd_rotor) uniform_flags = kFlagsGndRotor;    // per-rotor ground heights
     if (rollout_setup() != cudaSuccess) return 1;
     int n = 0;
     void* fn = rollout_kernel_ptr(uniform_flags, uniform_N, block);
@@ -1289,6 +1320,7 @@ cudaError_t launch_rollout(const RolloutArgs& r, int block, int uniform_flags, i
     if (r.n_items == 0 || r.K == 0) return cudaSuccess;
     const int uniform_N = r.s.c.rk4 ? -1 : r.s.uniform_N;
     if (r.s.c.rk4) uniform_flags = kFlagsRK4;  // Runge-Kutta variants
+    else if (r.s.c.gnd_rotor) uniform_flags = kFlagsGndRotor;  // per-rotor ground heights
     cudaError_t e = rollout_setup();
     if (e != cudaSuccess) return e;
     void* fn = rollout_kernel_ptr(uniform_flags, uniform_N, block);

@@ -8,7 +8,8 @@ record MDG_STATUS_BOUNDS instead of touching memory outside it. This test builds
 in a separate process that loads it, runs every kernel family on the workloads of the
 parity suite (uniform and table tiles, compile-time and runtime environment sizes, the
 persistent rollout, observations, PID, surrogate features, preparation, application and
-the fallback pass, the allocation-free entry point, the RK4 variants); no check may fail.
+the fallback pass, the allocation-free entry point, the RK4 and per-rotor ground-height
+variants); no check may fail.
 """
 import ctypes
 import os
@@ -86,12 +87,15 @@ def _run():
             torch.cuda.synchronize()
             assert int(nfb) == sw.n_envs
             check(h, f"{name} surrogate")
-    # the RK4 variants (runtime flags and sizes; the small-block and any-size kernels)
+    # the RK4 and per-rotor ground-height variants (runtime flags and sizes; the small-block
+    # and any-size kernels)
     rk4 = mdg.Constants.cf2x()
     rk4.integrator = mdg.INTEGRATOR_RK4
-    for name in ("uneven", "dense"):
+    gnd_rotor = mdg.Constants.cf2p()
+    gnd_rotor.gnd_heights = mdg.GND_ROTOR
+    for name, c, tag in (("uneven", rk4, "rk4"), ("dense", rk4, "rk4"), ("uneven", gnd_rotor, "per-rotor")):
         sw = swarms[name]
-        h = mdg.Handle(sw.drones_per_env, sw.flags, rk4)
+        h = mdg.Handle(sw.drones_per_env, sw.flags, c)
         h.set_action_types(sw.act_type)
         st = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=dev)
         act = torch.as_tensor(wl.mixed_actions(sw, 90, 0, hover), device=dev)
@@ -102,7 +106,7 @@ def _run():
             h.set_block_size(block)
             h.step_obs(st, act, mdg.ACT_MIXED, 5, kin, idx, rel)
             h.rollout(st, act[None], mdg.ACT_MIXED, 5, 1)
-            check(h, f"{name} rk4 block {block}")
+            check(h, f"{name} {tag} block {block}")
     # the allocation-free entry point builds its tables in static scratch
     sw = swarms["uneven"]
     st = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=dev)

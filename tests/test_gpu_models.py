@@ -186,3 +186,73 @@ def test_surrogate_step_refuses_rk4(cuda):
     with pytest.raises(mdg.MdgError) as e:
         m.step(h, state, torch.as_tensor(wl.waypoints(1, sw.n), device=cuda), mdg.ACT_PID)
     assert e.value.code == mdg.ERR_UNSUPPORTED
+
+
+def _with_gnd_rotor(model, rk4):
+    c, P = _pair(model, rk4)
+    c.gnd_heights = mdg.GND_ROTOR
+    P.gnd_heights = oracle.GND_ROTOR
+    return c, P
+
+
+@pytest.mark.parametrize("model, recipe, rk4", [
+    ("cf2x", "single", False), ("cf2p", "single", False), ("race", "single", False), ("cf2x", "single", True),
+    ("cf2x", "full_aero", False), ("cf2x", "uneven", False), ("cf2p", "uneven_spread", True)])
+def test_per_rotor_ground_heights_match_oracle(cuda, model, recipe, rk4):
+    """Eq. ground at each rotor's height (MDG_GND_ROTOR) through one substep and one control
+    step. The single-drone recipe flies tilted drones 5 cm to 1 m above the ground, where
+    the rotors' heights differ from the centre's by a sizeable fraction; there the result
+    must also differ from the printed (centre-of-mass) model, so that the switch is seen to
+    act."""
+    sw = _swarm(recipe)
+    c, P = _with_gnd_rotor(model, rk4)
+    h = mdg.Handle(sw.drones_per_env, sw.flags, c)
+    if recipe.startswith("uneven"):
+        h.set_action_types(sw.act_type)
+    action, act, acts = _actions(sw, P, recipe, mdg.ACT_PID if recipe == "full_aero" else mdg.ACT_RPM)
+    layout = (sw.drones_per_env, sw.flags)
+    state = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=cuda)
+    a_dev = torch.as_tensor(action, device=cuda)
+    x0, i0, a0 = oracle_arrays(state)
+    h.step(state, a_dev, act, 1)
+    torch.cuda.synchronize()
+    xg, _, _ = oracle_arrays(state)
+    xo, _, _ = oracle_step(P, layout, x0, i0, a0, action, acts, 1)
+    if recipe == "single":
+        assert_state_close(xg, xo, what=f"{model} per-rotor substep")
+        Pc = getattr(oracle, model)()
+        Pc.integrator = P.integrator
+        xc, _, _ = oracle_step(Pc, layout, x0, i0, a0, action, acts, 1)
+        # one substep separates the two models by ~8e-5 m/s (CF2.x) to ~6e-3 m/s (RACE)
+        assert np.max(np.abs(xg[:, 9] - xc[:, 9])) > 5 * 1e-5, "per-rotor heights had no effect"
+    else:
+        resp = tolerance_response(P, layout, x0, i0, a0, action, acts, 1)
+        assert_horizon_close(xg, xo, resp, 1, what=f"{model} {recipe} per-rotor substep")
+    x0, i0, a0 = oracle_arrays(state)
+    kin, idx, rel = h.new_obs(cuda)
+    h.step_obs(state, a_dev, act, 5, kin, idx, rel)
+    torch.cuda.synchronize()
+    xg, _, ag = oracle_arrays(state)
+    xo, _, _ = oracle_step(P, layout, x0, i0, a0, action, acts, 5)
+    resp = tolerance_response(P, layout, x0, i0, a0, action, acts, 5)
+    assert_horizon_close(xg, xo, resp, 5, what=f"{model} {recipe} per-rotor control step")
+    _check_obs(xg, ag, sw.drones_per_env, kin, idx, rel)
+
+
+def test_per_rotor_ground_heights_rollout(cuda):
+    """The persistent rollout's per-rotor variant: 10 control steps of the single-drone
+    recipe (no downwash: linear accumulation of the per-substep tolerance)."""
+    sw = wl.single(13, n_envs=100)
+    c, P = _with_gnd_rotor("cf2x", False)
+    h = mdg.Handle(sw.drones_per_env, sw.flags, c)
+    hover = oracle.hover_rpm(P)
+    acts = np.stack([wl.rpm_actions(14, sw.n, k, hover) for k in range(10)])
+    state = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=cuda)
+    x0, i0, a0 = oracle_arrays(state)
+    h.rollout(state, torch.as_tensor(acts, device=cuda), mdg.ACT_RPM, 5, 10)
+    torch.cuda.synchronize()
+    xg, _, _ = oracle_arrays(state)
+    env_off = np.arange(sw.n + 1, dtype=np.int32)
+    xo, _, _ = oracle.control_steps(P, env_off, np.asarray(sw.flags, np.int32), np.full(sw.n, oracle.ACT_RPM, np.int32),
+                                    x0, i0, a0, acts.astype(np.float64), 5)
+    assert_state_close(xg, xo, scale=50.0, what="per-rotor rollout")

@@ -88,9 +88,13 @@ def test_create_rejects_bad_constants(mdg_lib):
     c.integrator = 7
     rc, _ = _create(1, [1], [0], c)
     assert rc == mdg.ERR_ARG and "integrator" in mdg_lib.mdg_last_error().decode()
+    c = mdg.Constants.cf2x()
+    c.gnd_heights = -1
+    rc, _ = _create(1, [1], [0], c)
+    assert rc == mdg.ERR_ARG and "gnd_heights" in mdg_lib.mdg_last_error().decode()
 
 
-@pytest.mark.parametrize("model", ["cf2p", "race"])
+@pytest.mark.parametrize("model", ["cf2x", "cf2p", "race"])
 def test_model_constants_match_the_oracle(mdg_lib, model):
     """CF2P and RACE: the library's constants equal the oracle's own table field by field."""
     c = getattr(mdg.Constants, model)().to_dict()
