@@ -20,6 +20,10 @@ copied in from pinned memory and the observations copied back every step), the r
 of the step kernel against the measured HBM bandwidth, SM clocks sampled during the timed
 region, and the FP64 oracle timed on the host cores on a bounded sample.
 
+--model / --integrator / --gnd-heights select the drone model (CF2X, CF2P, RACE), Euler or
+RK4 substeps and the ground-effect heights (centre of mass, or per rotor) for the dynamics
+workloads; the defaults are the headline configuration (CF2X, Euler, centre of mass).
+
 --impl reference times the oracle alone (the reference arm of this project).
 """
 from __future__ import annotations
@@ -52,12 +56,38 @@ BYTES_PER_DRONE_STEP = STATE_BYTES_READ + ACTION_BYTES + STATE_BYTES_WRITE + OBS
 # DRAM traffic of one step-kernel launch on the full-aero workload, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel source whose
 # sha256 prefix is recorded with it; profiles/ holds the capture's summary.
-NCU_TRAFFIC = {"kernel_sha": "a9ee7e61a6ed2fdb", "bytes": 6331648 + 512}
+NCU_TRAFFIC = {"kernel_sha": "de4f8370f7563eac", "bytes": 6331648 + 512}
 
 
 def kernel_sha() -> str:
     with open(os.path.join(ROOT, "paper_2606_08039_gb300", "csrc", "mdg_step.cu"), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def model_config(args) -> dict:
+    return {"model": args.model, "integrator": args.integrator, "gnd_heights": args.gnd_heights}
+
+
+def is_default_model(args) -> bool:
+    return (args.model, args.integrator, args.gnd_heights) == ("cf2x", "euler", "com")
+
+
+def library_constants(args):
+    """The library's constants for the chosen model, integrator and ground-effect heights."""
+    import paper_2606_08039_gb300 as mdg
+    c = getattr(mdg.Constants, args.model)()
+    c.integrator = mdg.INTEGRATOR_RK4 if args.integrator == "rk4" else mdg.INTEGRATOR_EULER
+    c.gnd_heights = mdg.GND_ROTOR if args.gnd_heights == "rotor" else mdg.GND_COM
+    return c
+
+
+def oracle_params(args):
+    """The oracle's own parameters for the same choice (CPU-baseline and reference legs)."""
+    import oracle
+    P = getattr(oracle, args.model)()
+    P.integrator = oracle.RK4 if args.integrator == "rk4" else oracle.EULER
+    P.gnd_heights = oracle.GND_ROTOR if args.gnd_heights == "rotor" else oracle.GND_COM
+    return P
 
 
 def measured_peaks() -> dict:
@@ -142,13 +172,13 @@ def throughput(units_per_step_per_rank: int, world: int, steps: int, total_ms: f
     return units_per_step_per_rank * world * steps / (total_ms * 1e-3)
 
 
-def cpu_baseline(seconds_target: float = 10.0) -> dict:
+def cpu_baseline(args, seconds_target: float = 10.0) -> dict:
     """The FP64 oracle, as it stands, on a bounded sample of the full-aero workload: the
     full 16384 x 4 swarm for as many control steps (PID + 5 substeps + observations each)
-    as fit in about `seconds_target` seconds, on one host core."""
+    as fit in about `seconds_target` seconds, on one host core, with the chosen model."""
     import oracle
     from paper_2606_08039_gb300 import workloads as wl
-    P = oracle.cf2x()
+    P = oracle_params(args)
     sw = wl.full_aero(1)
     x, integ, a = sw.x13(), np.zeros((sw.n, 6)), np.zeros((sw.n, 4))
     wp = wl.waypoints(1, sw.n).astype(np.float64)[None]
@@ -163,7 +193,7 @@ def cpu_baseline(seconds_target: float = 10.0) -> dict:
             break
     return {"value": sw.n * N_SUB * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"full-aero swarm 16384 envs x 4 drones, {steps} control steps x {N_SUB} substeps "
-                      f"with PID and observations, FP64, single thread ({dt:.1f} s)"}
+                      f"with PID and observations, FP64, single thread ({dt:.1f} s)", **model_config(args)}
 
 
 def run_reference(args) -> None:
@@ -174,7 +204,7 @@ def run_reference(args) -> None:
         return
     import oracle
     from paper_2606_08039_gb300 import workloads as wl
-    P = oracle.cf2x()
+    P = oracle_params(args)
     sw = wl.full_aero(1, n_envs=2048)
     x, integ, a = sw.x13(), np.zeros((sw.n, 6)), np.zeros((sw.n, 4))
     wp = wl.waypoints(1, sw.n).astype(np.float64)[None]
@@ -198,7 +228,7 @@ def run_reference(args) -> None:
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "full_aero 16384 envs x 4 drones (sampled 2048 envs per step)", "n_substeps": N_SUB,
-                   "l2": "n/a (host)"},
+                   "l2": "n/a (host)", **model_config(args)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -212,19 +242,43 @@ def run_reference(args) -> None:
 FLOPS_BASE, FLOPS_GND, FLOPS_DRAG = 130, 8, 16
 FLOPS_DW_PAIR_TEST, FLOPS_DW_PAIR_TERM = 8, 16
 FLOPS_PID, FLOPS_OBS, FLOPS_OBS_PER_NEIGHBOUR = 150, 60, 8
+# RK4 (same counting): per stage the quaternion normalisation (12), the body z axis (9),
+# thrust and gravity (4), Newton-Euler (18), q' = 1/2 q (x) [0, w] (24), v' (3) and the stage
+# update of the 13 components (sum and next stage state, 52); per substep the final update
+# and renormalisation (38). Each effect is evaluated once per stage.
+FLOPS_RK4_STAGE, FLOPS_RK4_FINAL = 122, 38
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock = 80.5
+ALU_PEAK_SRC = "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz"
 
 
-def algorithmic_flops(sw, K: int, n_sub: int, obs_steps: int, pid_mask=None) -> float:
+def algorithmic_flops(sw, K: int, n_sub: int, obs_steps: int, pid_mask=None, rk4: bool = False) -> float:
     """Counted FP32 flops of K control steps of a swarm (pairs above: half the others)."""
     N = sw.drones_per_env.astype(np.float64)
     f = sw.flags
-    per_sub = FLOPS_BASE + ((f & 1) > 0) * FLOPS_GND + ((f & 2) > 0) * FLOPS_DRAG
-    per_sub = per_sub + ((f & 4) > 0) * ((N - 1) * FLOPS_DW_PAIR_TEST + 0.5 * (N - 1) * FLOPS_DW_PAIR_TERM)
+    effects = ((f & 1) > 0) * FLOPS_GND + ((f & 2) > 0) * FLOPS_DRAG
+    effects = effects + ((f & 4) > 0) * ((N - 1) * FLOPS_DW_PAIR_TEST + 0.5 * (N - 1) * FLOPS_DW_PAIR_TERM)
+    per_sub = (4 * (FLOPS_RK4_STAGE + effects) + FLOPS_RK4_FINAL) if rk4 else FLOPS_BASE + effects
     pid = np.zeros_like(N) if pid_mask is None else pid_mask.astype(np.float64) * FLOPS_PID
     per_step = n_sub * per_sub + pid
     total = np.sum(N * (K * per_step + obs_steps * (FLOPS_OBS + FLOPS_OBS_PER_NEIGHBOUR * (N - 1))))
     return float(total)
+
+
+def binding_roofline(bytes_launch: float, flops_launch: float, sec: float, peaks) -> dict:
+    """The roofline of a launch against the bound whose ideal time is the longer: HBM
+    (algorithmic bytes over the measured copy bandwidth) or FP32 ALU (counted flops over
+    the derived peak); the other bound is reported beside it."""
+    t_hbm = bytes_launch / (peaks["hbm_gbs"] * 1e9)
+    t_alu = flops_launch / (FP32_PEAK_TFLOPS * 1e12)
+    hbm = {"bound": "hbm", "achieved": bytes_launch / sec / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+           "peak_src": peaks["src"], "algorithmic_bytes_per_launch": bytes_launch}
+    alu = {"bound": "alu", "achieved": flops_launch / sec / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+           "peak_src": ALU_PEAK_SRC, "algorithmic_flops_per_launch": flops_launch}
+    for r in (hbm, alu):
+        r["frac"] = r["achieved"] / r["peak"]
+    main, other = (hbm, alu) if t_hbm >= t_alu else (alu, hbm)
+    main["other_bound"] = {k: other[k] for k in ("bound", "achieved", "peak", "unit", "frac")}
+    return main
 
 
 EPISODE_REPS = 3
@@ -233,18 +287,18 @@ EPISODE_REPS = 3
 BYTES_OBS_PER_DRONE_STEP = 80 + 16 + 96
 
 
-def episode_line(n: int, world: int, ep_ms: float, peaks) -> dict:
+def episode_line(n: int, world: int, ep_ms: float, peaks, flops_step: float) -> dict:
     value = throughput(n * N_SUB * EPISODE, world, EPISODE_REPS, ep_ms)
     sec = ep_ms / EPISODE_REPS * 1e-3
     nbytes = n * (80 + 96 + 16 + EPISODE * BYTES_OBS_PER_DRONE_STEP)
+    roof = binding_roofline(nbytes, flops_step * EPISODE, sec, peaks)
+    roof["kernel"] = "rollout_kernel<obs every step>"
     return {"what": f"the {EPISODE}-control-step episode as one persistent rollout per launch (mdg_rollout, "
                     "observations of every step written), L2 flushed between episodes; the headline value "
                     "above is one control step per launch",
             "value": value, "unit": UNIT, "ms_per_episode": ep_ms / EPISODE_REPS, "episodes": EPISODE_REPS,
             "us_per_control_step": ep_ms / EPISODE_REPS / EPISODE * 1e3,
-            "roofline": {"bound": "hbm", "achieved": nbytes / sec / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": nbytes / sec / 1e9 / peaks["hbm_gbs"], "algorithmic_bytes_per_launch": nbytes,
-                         "kernel": "rollout_kernel<obs every step>"}}
+            "roofline": roof}
 
 
 def run_other(args) -> None:
@@ -266,12 +320,12 @@ def run_other(args) -> None:
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     sink = torch.empty((), dtype=torch.float32, device=dev)
-    c = mdg.Constants.cf2x()
+    c = library_constants(args)
     hover = c.hover_rpm()
     extra = {}
     if args.workload == "uneven":
         sw, K, obs_steps = wl.uneven(2), 32, 1
-        h = mdg.Handle(sw.drones_per_env, sw.flags)
+        h = mdg.Handle(sw.drones_per_env, sw.flags, c)
         h.set_action_types(sw.act_type)
         acts = torch.as_tensor(np.stack([wl.mixed_actions(sw, 2, k, hover) for k in range(K)]), device=dev)
         init = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=dev)
@@ -293,7 +347,7 @@ def run_other(args) -> None:
                             for k in range(K)]
     elif args.workload == "dense":
         sw, K, obs_steps = wl.dense(5), 1, 1
-        h = mdg.Handle(sw.drones_per_env, sw.flags)
+        h = mdg.Handle(sw.drones_per_env, sw.flags, c)
         acts = [torch.as_tensor(wl.rpm_actions(5, sw.n, k, hover), device=dev) for k in range(16)]
         init = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=dev)
         state = init.clone()
@@ -314,7 +368,7 @@ def run_other(args) -> None:
         extra_fn = None
     else:
         sw, K, obs_steps = wl.single(0), 240, 1
-        h = mdg.Handle(sw.drones_per_env, sw.flags)
+        h = mdg.Handle(sw.drones_per_env, sw.flags, c)
         acts = torch.as_tensor(np.stack([wl.rpm_actions(0, sw.n, k, hover) for k in range(K)]), device=dev)
         init = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=dev)
         state = init.clone()
@@ -361,19 +415,19 @@ def run_other(args) -> None:
         extra["same_work_as_single_step_launches"] = {"value": substeps / (per_step_ms * 1e-3), "ms": per_step_ms,
                                                       "launches": K}
     ms = total_ms / steps
-    flops = algorithmic_flops(sw, K, N_SUB, obs_steps, pid_mask)
+    flops = algorithmic_flops(sw, K, N_SUB, obs_steps, pid_mask, rk4=args.integrator == "rk4")
     achieved = flops / (ms * 1e-3) / 1e12
     out = {
         "metric": METRIC, "value": substeps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "n_drones": sw.n, "control_steps_per_step": K, "n_substeps": N_SUB,
-                   "block_size": block, "l2": "flushed between timed steps (512 MiB written, then read back)"},
+                   "block_size": block, "l2": "flushed between timed steps (512 MiB written, then read back)",
+                   **model_config(args)},
         "gpu_launches": launches * steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                     "peak_src": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz",
-                     "algorithmic_flops_per_step": flops},
+                     "peak_src": ALU_PEAK_SRC, "algorithmic_flops_per_step": flops},
         "clocks": clk, "nonfinite_during_timing": bool(bits & mdg.STATUS_NONFINITE),
     }
     if args.workload == "single":
@@ -557,12 +611,17 @@ def main() -> None:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="full_aero", choices=["full_aero", "uneven", "dense", "single", "surrogate", "mlp"],
                     help="full_aero (default, the headline line); the others measure the other swarms")
+    ap.add_argument("--model", default="cf2x", choices=["cf2x", "cf2p", "race"])
+    ap.add_argument("--integrator", default="euler", choices=["euler", "rk4"])
+    ap.add_argument("--gnd-heights", default="com", choices=["com", "rotor"])
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         run_reference(args)
         return
+    if args.workload in ("surrogate", "mlp") and not is_default_model(args):
+        ap.error("--model/--integrator/--gnd-heights apply to the dynamics workloads only")
     if args.workload == "surrogate":
         run_surrogate(args)
         return
@@ -588,7 +647,7 @@ def main() -> None:
 
     # workload: the full-aero swarm, one independent replica per rank
     sw = wl.full_aero(replica_seed(rank))
-    h = mdg.Handle(sw.drones_per_env, sw.flags)
+    h = mdg.Handle(sw.drones_per_env, sw.flags, library_constants(args))
     init_state = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=dev)
     state = init_state.clone()
     wp_host = torch.from_numpy(wl.waypoints(replica_seed(rank), sw.n)).pin_memory()
@@ -691,8 +750,14 @@ def main() -> None:
         peaks = measured_peaks()
         avg_s = total_ms / args.steps * 1e-3
         bytes_launch = BYTES_PER_DRONE_STEP * sw.n
-        achieved = bytes_launch / avg_s / 1e9
-        traffic = NCU_TRAFFIC["bytes"] if NCU_TRAFFIC["kernel_sha"] == kernel_sha() else None
+        pid_all = np.ones(sw.n_envs, bool)
+        flops_launch = algorithmic_flops(sw, 1, N_SUB, 1, pid_all, rk4=args.integrator == "rk4")
+        roofline = binding_roofline(bytes_launch, flops_launch, avg_s, peaks)
+        # the ncu capture is of the default configuration's kernel at this source
+        roofline["traffic"] = (NCU_TRAFFIC["bytes"] if NCU_TRAFFIC["kernel_sha"] == kernel_sha()
+                               and is_default_model(args) else None)
+        roofline["kernel"] = "step_kernel<obs>"
+        roofline["kernel_sha"] = kernel_sha()
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -708,17 +773,15 @@ def main() -> None:
                     "path": "mdg_step_obs_host: waypoints read and observations written in pinned host memory "
                             "by the step kernel, synchronised on every step"},
             "gpu_launches": args.steps,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                         "peak_src": peaks["src"], "algorithmic_bytes_per_launch": bytes_launch,
-                         "kernel": "step_kernel<obs>", "kernel_sha": kernel_sha()},
+            "roofline": roofline,
             "clocks": clk,
             "wall_s_timed_region": wall,
             "nonfinite_during_timing": nonfinite,
-            "episode": episode_line(sw.n, world, ep_ms, peaks),
+            "episode": episode_line(sw.n, world, ep_ms, peaks, flops_launch),
         }
+        out["config"].update(model_config(args))
         if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline()
+            out["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
