@@ -27,6 +27,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
 GND, DRAG, DW = 1, 2, 4
 ACT_RPM, ACT_PID = 0, 1
+ACT_RPM_NORM, ACT_ONE_D_RPM, ACT_VEL, ACT_ATTITUDE = 3, 4, 5, 6
 FRAME_X, FRAME_P = 0, 1
 EULER, RK4 = 0, 1
 GND_COM, GND_ROTOR = 0, 1
@@ -97,6 +98,8 @@ def lib():
                 "orc_substep": ([P, ctypes.c_int, _D, _D, ctypes.c_int, ctypes.c_double, _D], None),
                 "orc_allocation_matrix": ([P, _D], None),
                 "orc_pid": ([P, _D, _D, _D, _D, _D, _D], None),
+                "orc_normalized_rpm": ([P, ctypes.c_double], ctypes.c_double),
+                "orc_action_to_rpm": ([P, ctypes.c_int, _D, _D, _D, _D], None),
                 "orc_kin": ([_D, _D, _D], None),
                 "orc_knn": ([ctypes.c_int, _D, ctypes.c_int, ctypes.c_int, _I, _D], None),
                 "orc_control_steps": ([P, ctypes.c_int, _I, _I, _I, _D, _D, _D, _D, ctypes.c_int, ctypes.c_int,
@@ -242,6 +245,19 @@ def pid(p: Params, x, integ, wp):
     ye = ctypes.c_double()
     lib().orc_pid(ctypes.byref(p), _dptr(x), _dptr(integ), _dptr(wp), _dptr(rpm), _dptr(pe), ctypes.byref(ye))
     return rpm, pe, ye.value, integ
+
+
+def normalized_rpm(p: Params, a: float) -> float:
+    return lib().orc_normalized_rpm(ctypes.byref(p), float(a))
+
+
+def action_to_rpm(p: Params, act_type: int, x, integ, act):
+    """One drone's action -> (rpm [4], updated integ [6]) for any action type."""
+    x, act = _f64(x), _f64(act)
+    integ = _f64(integ).copy()
+    rpm = np.zeros(4)
+    lib().orc_action_to_rpm(ctypes.byref(p), int(act_type), _dptr(x), _dptr(integ), _dptr(act), _dptr(rpm))
+    return rpm, integ
 
 
 def kin(x, a_prev) -> np.ndarray:

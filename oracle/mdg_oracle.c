@@ -35,6 +35,10 @@
 /* Action types (Table "Action types"): raw RPM or an absolute PID waypoint. */
 #define ORC_ACT_RPM 0
 #define ORC_ACT_PID 1
+#define ORC_ACT_RPM_NORM 3
+#define ORC_ACT_ONE_D_RPM 4
+#define ORC_ACT_VEL 5
+#define ORC_ACT_ATTITUDE 6
 
 /* Rotor layouts (Section 3.1.2): X configuration (CF2X, RACE) or + configuration (CF2P). */
 #define ORC_FRAME_X 0
@@ -523,51 +527,60 @@ static double wrap_pi(double a)
     return w - ORC_PI;
 }
 
-/* One call of the cascaded PID (computeControl) for one drone. x is the 13-d
- * state, integ[6] = [position error integral (3), attitude error integral (3)]
- * (updated in place), wp = [x*, y*, z*, psi*]. Readings, where the paper prints
+/* The cascaded PID of Section 4.2.1 in its three stages. Readings, where the paper prints
  * only the structure, the gains and T = m |a*|:
- *  - position loop a* = Kp e_p + Ki I_p + Kd (0 - v) + g z_hat, with
- *    I_p = clamp(I_p + e_p dt_ctrl, +-pos_iclamp), dt_ctrl the control period;
+ *  - position loop a* = Kp e_p + Ki I_p + Kd (v_t - v) + g z_hat, e_p = p_t - p, with
+ *    I_p = clamp(I_p + e_p dt_ctrl, +-pos_iclamp), dt_ctrl the control period, and the
+ *    target velocity v_t zero for waypoints;
  *  - small-angle attitude target phi* = (a*_x sin psi* - a*_y cos psi*)/g,
  *    theta* = (a*_x cos psi* + a*_y sin psi*)/g;
- *  - attitude PID tau* = Kp e_eta + Ki I_eta + Kd (0 - omega), e_eta the roll,
- *    pitch and wrapped yaw errors, I_eta clamped to +-att_iclamp;
- *  - solve M f = [T*, tau*], clip each f_i to [0, k_f MAX_RPM^2] (standing in
- *    for the unprinted torque clamp), n_i = sqrt(f_i / k_f).
- * Returns (rpm, pos_error, yaw_error) like computeControl. */
-void orc_pid(const orc_params* P, const double x[13], double integ[6], const double wp[4],
-             double rpm[4], double pos_err[3], double* yaw_err)
+ *  - attitude PID tau* = Kp e_eta + Ki I_eta + Kd (w_t - omega), e_eta the roll, pitch
+ *    and wrapped yaw errors, I_eta clamped to +-att_iclamp, the target body rate w_t zero
+ *    for waypoints;
+ *  - mixer: solve M f = [T*, tau*], clip each f_i to [0, k_f MAX_RPM^2] (standing in for
+ *    the unprinted torque clamp), n_i = sqrt(f_i / k_f). */
+static void orc_position_loop(const orc_params* P, const double x[13], double integ[6], const double p_t[3],
+                              const double v_t[3], double psi_t, double* T, double att_t[2], double ep[3])
 {
     const double* p = x;
-    const double* q = x + 3;
     const double* v = x + 7;
-    const double* w = x + 10;
-    double ep[3], a[3];
+    double a[3];
     for (int r = 0; r < 3; ++r) {
-        ep[r] = wp[r] - p[r];
+        ep[r] = p_t[r] - p[r];
         double I = integ[r] + ep[r] * P->dt_ctrl;
         if (I > P->pos_iclamp) I = P->pos_iclamp;
         if (I < -P->pos_iclamp) I = -P->pos_iclamp;
         integ[r] = I;
-        a[r] = P->pos_kp[r] * ep[r] + P->pos_ki[r] * I + P->pos_kd[r] * (0.0 - v[r]);
+        a[r] = P->pos_kp[r] * ep[r] + P->pos_ki[r] * I + P->pos_kd[r] * (v_t[r] - v[r]);
     }
     a[2] += P->g;
-    double T = P->mass * sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
-    double psi_t = wp[3];
+    *T = P->mass * sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
     double phi_t = (a[0] * sin(psi_t) - a[1] * cos(psi_t)) / P->g;
     double theta_t = (a[0] * cos(psi_t) + a[1] * sin(psi_t)) / P->g;
+    att_t[0] = phi_t;
+    att_t[1] = theta_t;
+}
+
+static void orc_attitude_loop(const orc_params* P, const double x[13], double integ[6], double phi_t,
+                              double theta_t, double psi_t, const double w_t[3], double tau[3], double* yaw_err)
+{
+    const double* q = x + 3;
+    const double* w = x + 10;
     double rpy[3];
     orc_rpy(q, rpy);
     double ee[3] = {phi_t - rpy[0], theta_t - rpy[1], wrap_pi(psi_t - rpy[2])};
-    double tau[3];
     for (int r = 0; r < 3; ++r) {
         double I = integ[3 + r] + ee[r] * P->dt_ctrl;
         if (I > P->att_iclamp) I = P->att_iclamp;
         if (I < -P->att_iclamp) I = -P->att_iclamp;
         integ[3 + r] = I;
-        tau[r] = P->att_kp[r] * ee[r] + P->att_ki[r] * I + P->att_kd[r] * (0.0 - w[r]);
+        tau[r] = P->att_kp[r] * ee[r] + P->att_ki[r] * I + P->att_kd[r] * (w_t[r] - w[r]);
     }
+    if (yaw_err) *yaw_err = ee[2];
+}
+
+static void orc_mix(const orc_params* P, double T, const double tau[3], double rpm[4])
+{
     double M[16], A[4][4], b[4] = {T, tau[0], tau[1], tau[2]}, f[4];
     orc_allocation_matrix(P, M);
     for (int i = 0; i < 4; ++i)
@@ -581,10 +594,85 @@ void orc_pid(const orc_params* P, const double x[13], double integ[6], const dou
         if (fi > fmax_) fi = fmax_;
         rpm[i] = sqrt(fi / P->kf);
     }
+}
+
+/* One call of the cascaded PID (computeControl) for one drone towards a waypoint. x is
+ * the 13-d state, integ[6] = [position error integral (3), attitude error integral (3)]
+ * (updated in place), wp = [x*, y*, z*, psi*]; zero target velocity and body rate.
+ * Returns (rpm, pos_error, yaw_error) like computeControl. */
+void orc_pid(const orc_params* P, const double x[13], double integ[6], const double wp[4],
+             double rpm[4], double pos_err[3], double* yaw_err)
+{
+    static const double zero[3] = {0.0, 0.0, 0.0};
+    double T, att[2], ep[3], tau[3];
+    orc_position_loop(P, x, integ, wp, zero, wp[3], &T, att, ep);
+    orc_attitude_loop(P, x, integ, att[0], att[1], wp[3], zero, tau, yaw_err);
+    orc_mix(P, T, tau, rpm);
     if (pos_err) {
         for (int r = 0; r < 3; ++r) pos_err[r] = ep[r];
     }
-    if (yaw_err) *yaw_err = ee[2];
+}
+
+/* Normalized RPM action (Table "Action types"; the tasks map actions in [-1, 1] to RPMs,
+ * the map itself is not printed). Reading: a clipped to [-1, 1], -1 -> 0, 0 -> HOVER_RPM,
+ * 1 -> MAX_RPM, linear on each side of hover. */
+double orc_normalized_rpm(const orc_params* P, double a)
+{
+    if (a < -1.0) a = -1.0;
+    if (a > 1.0) a = 1.0;
+    const double hover = orc_hover_rpm(P), maxrpm = orc_max_rpm(P);
+    return a <= 0.0 ? hover * (1.0 + a) : hover + (maxrpm - hover) * a;
+}
+
+/* Action -> four RPMs for one drone (Table "Action types", converted in
+ * _preprocessAction):
+ *  RPM        the four speeds clipped to [0, MAX_RPM];
+ *  RPM_NORM   four normalized values (orc_normalized_rpm);
+ *  ONE_D_RPM  act[0] normalized, the same speed on all four motors;
+ *  PID        waypoint [x, y, z, psi] (orc_pid);
+ *  VEL        body-frame [v_x, v_y, v_z, omega_z] through the PID: reading, the position
+ *             loop holds the current position (e_p = 0) with target velocity R v_body,
+ *             and the attitude loop holds the current yaw with target body rate
+ *             [0, 0, omega_z];
+ *  ATTITUDE   [T, phi*, theta*, yaw rate]: reading, T the collective thrust in N, the
+ *             attitude loop towards phi*, theta* and the current yaw with target body rate
+ *             [0, 0, yaw rate], then the mixer.
+ * integ is updated as the loops run. */
+void orc_action_to_rpm(const orc_params* P, int type, const double x[13], double integ[6], const double act[4],
+                       double rpm[4])
+{
+    if (type == ORC_ACT_PID) {
+        orc_pid(P, x, integ, act, rpm, NULL, NULL);
+    } else if (type == ORC_ACT_RPM_NORM) {
+        for (int i = 0; i < 4; ++i) rpm[i] = orc_normalized_rpm(P, act[i]);
+    } else if (type == ORC_ACT_ONE_D_RPM) {
+        const double r = orc_normalized_rpm(P, act[0]);
+        for (int i = 0; i < 4; ++i) rpm[i] = r;
+    } else if (type == ORC_ACT_VEL || type == ORC_ACT_ATTITUDE) {
+        double rpy[3], tau[3], T, att[2], ep[3];
+        orc_rpy(x + 3, rpy);
+        const double w_t[3] = {0.0, 0.0, act[3]};
+        if (type == ORC_ACT_VEL) {
+            double R[9], v_t[3];
+            orc_rotation(x + 3, R);
+            for (int r = 0; r < 3; ++r) v_t[r] = R[3 * r] * act[0] + R[3 * r + 1] * act[1] + R[3 * r + 2] * act[2];
+            orc_position_loop(P, x, integ, x, v_t, rpy[2], &T, att, ep);
+        } else {
+            T = act[0];
+            att[0] = act[1];
+            att[1] = act[2];
+        }
+        orc_attitude_loop(P, x, integ, att[0], att[1], rpy[2], w_t, tau, NULL);
+        orc_mix(P, T, tau, rpm);
+    } else {
+        const double maxrpm = orc_max_rpm(P);
+        for (int i = 0; i < 4; ++i) {
+            double r = act[i];
+            if (r < 0.0) r = 0.0;
+            if (r > maxrpm) r = maxrpm;
+            rpm[i] = r;
+        }
+    }
 }
 
 /* ---- observations (Section 3.4.4) ---- */
@@ -662,14 +750,13 @@ void orc_knn(int N, const double* x, int j, int idx_base, int32_t idx[4], double
 /* Runs K control steps (Section 3.4.2: sim_freq/ctrl_freq substeps per step) for
  * n_envs environments laid out in CSR order (drones of env e are
  * env_off[e] .. env_off[e+1]-1). Per control step and environment: the action of
- * each drone becomes four RPMs (ORC_ACT_RPM: clipped to [0, MAX_RPM]; ORC_ACT_PID:
- * orc_pid towards the waypoint), the RPMs are held over n_sub substeps of dt_sim,
- * and a_prev records them. After the last step the observations are written when
- * kin is not NULL.
+ * each drone becomes four RPMs by the environment's action type (orc_action_to_rpm),
+ * the RPMs are held over n_sub substeps of dt_sim, and a_prev records them. After the
+ * last step the observations are written when kin is not NULL.
  *   x        [n][13]   state, updated in place
  *   integ    [n][6]    PID integrals, updated in place
  *   a_prev   [n][4]    last applied RPMs, written
- *   actions  [K][n][4] RPMs or waypoints
+ *   actions  [K][n][4] one action per drone (RPMs, waypoints, velocities, ...)
  *   kin      [n][20], nbr_idx [n][4], nbr_rel [n][24] (optional)
  * Returns 0, or -1 on a bad argument. */
 int orc_control_steps(const orc_params* P, int n_envs, const int32_t* env_off, const int32_t* env_flags,
@@ -686,23 +773,14 @@ int orc_control_steps(const orc_params* P, int n_envs, const int32_t* env_off, c
     const int64_t n = n_envs > 0 ? env_off[n_envs] : 0;
     double* rpm = (double*)malloc(sizeof(double) * 4 * (size_t)(maxN > 0 ? maxN : 1));
     double* tmp = (double*)malloc(sizeof(double) * 13 * (size_t)(maxN > 0 ? maxN : 1));
-    const double maxrpm = orc_max_rpm(P);
     for (int k = 0; k < K; ++k) {
         const double* act = actions + (size_t)k * (size_t)n * 4;
         for (int e = 0; e < n_envs; ++e) {
             const int b = env_off[e], N = env_off[e + 1] - env_off[e];
             for (int j = 0; j < N; ++j) {
                 const double* a = act + 4 * (size_t)(b + j);
-                if (env_act[e] == ORC_ACT_PID) {
-                    orc_pid(P, x + 13 * (size_t)(b + j), integ + 6 * (size_t)(b + j), a, rpm + 4 * j, NULL, NULL);
-                } else {
-                    for (int i = 0; i < 4; ++i) {
-                        double r = a[i];
-                        if (r < 0.0) r = 0.0;
-                        if (r > maxrpm) r = maxrpm;
-                        rpm[4 * j + i] = r;
-                    }
-                }
+                orc_action_to_rpm(P, env_act[e], x + 13 * (size_t)(b + j), integ + 6 * (size_t)(b + j), a,
+                                  rpm + 4 * j);
                 for (int i = 0; i < 4; ++i) a_prev[4 * (size_t)(b + j) + i] = rpm[4 * j + i];
             }
             for (int s = 0; s < n_sub; ++s) {

@@ -1,5 +1,6 @@
 """The oracle pins have teeth: plant plausible mistakes in a copy of the oracle and
-check that the pin suite (test_oracle_dynamics.py, test_oracle_models.py) fails on each.
+check that the pin suite (test_oracle_dynamics.py, test_oracle_models.py,
+test_oracle_actions.py) fails on each.
 
 Mistakes are planted only in a temporary copy of the oracle, on the CPU; the real
 oracle is not modified. CPU only.
@@ -37,8 +38,8 @@ MUTATIONS = {
     "inertia_index": ("double Jw[3] = {J[0] * w[0], J[1] * w[1], J[2] * w[2]};",
                       "double Jw[3] = {J[0] * w[0], J[2] * w[1], J[1] * w[2]};"),
     "pid_derivative_sign": (
-        "a[r] = P->pos_kp[r] * ep[r] + P->pos_ki[r] * I + P->pos_kd[r] * (0.0 - v[r]);",
-        "a[r] = P->pos_kp[r] * ep[r] + P->pos_ki[r] * I + P->pos_kd[r] * v[r];"),
+        "a[r] = P->pos_kp[r] * ep[r] + P->pos_ki[r] * I + P->pos_kd[r] * (v_t[r] - v[r]);",
+        "a[r] = P->pos_kp[r] * ep[r] + P->pos_ki[r] * I + P->pos_kd[r] * (v[r] - v_t[r]);"),
     "pid_roll_target_sign": ("double phi_t = (a[0] * sin(psi_t) - a[1] * cos(psi_t)) / P->g;",
                              "double phi_t = (a[0] * sin(psi_t) + a[1] * cos(psi_t)) / P->g;"),
     "pitch_extraction": ("double sp = 2.0 * (w * y - z * x);", "double sp = 2.0 * (w * y + z * x);"),
@@ -62,6 +63,13 @@ MUTATIONS = {
     "rotor_height_at_com": ("double r = P->prop_radius / (4.0 * fmax(zi, P->h_clip));",
                             "double r = P->prop_radius / (4.0 * fmax(xj[2], P->h_clip));"),
     "rotor_positions_swapped": ("r[0] = l * xs[i];", "r[0] = l * ys[i];"),
+    "vel_world_frame": (
+        "for (int r = 0; r < 3; ++r) v_t[r] = R[3 * r] * act[0] + R[3 * r + 1] * act[1] + R[3 * r + 2] * act[2];",
+        "for (int r = 0; r < 3; ++r) v_t[r] = act[r];"),
+    "attitude_roll_pitch_swap": ("att[0] = act[1];", "att[0] = act[2];"),
+    "normalized_upper_slope": ("return a <= 0.0 ? hover * (1.0 + a) : hover + (maxrpm - hover) * a;",
+                               "return a <= 0.0 ? hover * (1.0 + a) : hover * (1.0 + a);"),
+    "yaw_rate_sign": ("const double w_t[3] = {0.0, 0.0, act[3]};", "const double w_t[3] = {0.0, 0.0, -act[3]};"),
 }
 
 
@@ -90,8 +98,8 @@ def test_planted_mistake_is_caught(name, oracle_source, tmp_path):
                     ignore=shutil.ignore_patterns("__pycache__", "test_oracle_mutations.py"))
     (tmp_path / "oracle" / "mdg_oracle.c").write_text(oracle_source.replace(before, after))
     r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_dynamics.py", "tests/test_oracle_models.py",
-                        "-q", "-x", "-p", "no:cacheprovider"], cwd=tmp_path, capture_output=True, text=True,
-                       timeout=300)
+                        "tests/test_oracle_actions.py", "-q", "-x", "-p", "no:cacheprovider"], cwd=tmp_path,
+                       capture_output=True, text=True, timeout=300)
     assert r.returncode == 1, f"planted mistake {name} was not caught:\n{r.stdout[-2000:]}"
 
 
