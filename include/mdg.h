@@ -57,10 +57,23 @@ extern "C" {
 #define MDG_DRAG 2u /* blade drag, Eq. drag */
 #define MDG_DW 4u   /* inter-drone downwash, Eq. downwash */
 
-/* Action types (Table "Action types"). */
+/* Action types (Table "Action types"); every action is four floats per drone. */
 #define MDG_ACT_RPM 0   /* action = four motor speeds [RPM], clipped to [0, MAX_RPM] */
 #define MDG_ACT_PID 1   /* action = waypoint [x, y, z, yaw] for the PID controller */
 #define MDG_ACT_MIXED 2 /* per-environment type, set by mdg_set_action_types */
+/* Normalized speeds: four values in [-1, 1] (clipped), mapped piecewise linearly with
+ * -1 -> 0, 0 -> HOVER_RPM, 1 -> MAX_RPM (the tasks' normalized actions; the map is not
+ * printed, this is the library's reading). */
+#define MDG_ACT_RPM_NORM 3
+/* ONE_D_RPM: the first value, normalized as above, on all four motors (others ignored). */
+#define MDG_ACT_ONE_D_RPM 4
+/* VEL: body-frame [v_x, v_y, v_z, omega_z] through the PID: the position loop holds the
+ * current position with target velocity R v_body, the attitude loop the current yaw with
+ * target body rate [0, 0, omega_z]. Updates the integrals like PID. */
+#define MDG_ACT_VEL 5
+/* ATTITUDE: [T (N), roll*, pitch* (rad), yaw rate (rad/s)] through the attitude loop (current
+ * yaw, target body rate [0, 0, yaw rate]) and the mixer. Updates the attitude integrals. */
+#define MDG_ACT_ATTITUDE 6
 
 /* Status bits written by the kernels (read with mdg_status). */
 #define MDG_STATUS_NONFINITE 1u /* a drone's state became NaN or infinite */
@@ -158,8 +171,8 @@ int mdg_destroy(mdg_handle h);
 /* Number of drones (sum of drones_per_env), or a negative code for a NULL handle. */
 int64_t mdg_num_drones(mdg_handle h);
 
-/* Per-environment action types for MDG_ACT_MIXED: host [n_envs] of MDG_ACT_RPM or
- * MDG_ACT_PID (copied to the device on the default stream, synchronously). */
+/* Per-environment action types for MDG_ACT_MIXED: host [n_envs], each an action type
+ * other than MDG_ACT_MIXED (copied to the device on the default stream, synchronously). */
 int mdg_set_action_types(mdg_handle h, const uint8_t* per_env);
 
 /* Threads per block of the step kernels (a multiple of 32 in [32, 1024] and at least
@@ -171,13 +184,14 @@ int32_t mdg_get_block_size(mdg_handle h);
 
 /* One control step (Section 3.4.2: sim_freq/ctrl_freq physics substeps per env.step).
  *   state       device float32 [MDG_STATE_PLANES][n_drones][4], updated in place
- *   action      device float32 [n_drones][4]: RPMs (MDG_ACT_RPM) or waypoints
- *               [x, y, z, yaw] (MDG_ACT_PID); for MDG_ACT_MIXED each env reads it
- *               according to its type. May be NULL only when n_drones is 0.
- *   action_type MDG_ACT_RPM | MDG_ACT_PID | MDG_ACT_MIXED
+ *   action      device float32 [n_drones][4]: RPMs (MDG_ACT_RPM), waypoints
+ *               [x, y, z, yaw] (MDG_ACT_PID) or the values of another action type; for
+ *               MDG_ACT_MIXED each env reads it according to its type. May be NULL only
+ *               when n_drones is 0.
+ *   action_type one of the MDG_ACT_* types
  *   n_substeps  >= 1 (5 for 240 Hz physics at 48 Hz control)
- * The action is turned into four RPMs once (PID: Section 4.2.1, updating the
- * integrals in planes 3-4), held for n_substeps substeps of dt_sim, and recorded in
+ * The action is turned into four RPMs once (PID, VEL, ATTITUDE: Section 4.2.1, updating
+ * the integrals in planes 3-4), held for n_substeps substeps of dt_sim, and recorded in
  * plane 5. Within a substep every drone of an environment sees the positions of the
  * others at the start of that substep. A non-finite result sets MDG_STATUS_NONFINITE.
  * Errors: MDG_ERR_ARG (bad pointer/alignment/type/count, MIXED without types),

@@ -22,6 +22,7 @@ from . import workloads  # noqa: F401  (seeded synthetic inputs)
 
 GND, DRAG, DW = 1, 2, 4
 ACT_RPM, ACT_PID, ACT_MIXED = 0, 1, 2
+ACT_RPM_NORM, ACT_ONE_D_RPM, ACT_VEL, ACT_ATTITUDE = 3, 4, 5, 6
 STATUS_NONFINITE = 1
 STATUS_TIMEOUT = 2
 STATUS_BOUNDS = 4

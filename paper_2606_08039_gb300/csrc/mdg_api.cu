@@ -137,6 +137,7 @@ DevConsts make_dev_consts(const mdg_constants& c)
     d.max_rpm = (float)maxrpm;
     d.f_max = (float)(c.kf * maxrpm * maxrpm);
     d.inv_kf = (float)(1.0 / c.kf);
+    d.hover_rpm = (float)sqrt(c.mass * c.g / (4.0 * c.kf));
     d.alloc_z = (float)(c.kf / c.km);
     d.frame_p = c.frame == MDG_FRAME_P ? 1 : 0;
     d.rk4 = c.integrator == MDG_INTEGRATOR_RK4 ? 1 : 0;
@@ -585,13 +586,17 @@ int mdg_set_action_types(mdg_handle h, const uint8_t* per_env)
         return MDG_OK;
     }
     if (!per_env) return fail(MDG_ERR_ARG, "mdg_set_action_types: per_env is NULL");
-    for (int32_t e = 0; e < h->n_envs; ++e)
-        if (per_env[e] != MDG_ACT_RPM && per_env[e] != MDG_ACT_PID)
-            return fail(MDG_ERR_ARG, "mdg_set_action_types: per_env[%d] = %d is not RPM or PID", e, per_env[e]);
+    bool ext = false;
+    for (int32_t e = 0; e < h->n_envs; ++e) {
+        if (!mdg::valid_env_action(per_env[e]))
+            return fail(MDG_ERR_ARG, "mdg_set_action_types: per_env[%d] = %d is not an action type", e, per_env[e]);
+        ext = ext || mdg::extended_action(per_env[e]);
+    }
     DeviceGuard dg(h->device);
     cudaError_t e = cudaMemcpy(h->d_act, per_env, (size_t)h->n_envs, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "mdg_set_action_types: cudaMemcpy");
     h->act_set = true;
+    h->act_ext = ext;
     return MDG_OK;
 }
 
@@ -613,13 +618,20 @@ int32_t mdg_get_block_size(mdg_handle h)
     return h->block;
 }
 
+// The physics-flag selector handed to the launchers: the batch's uniform flags, or 8 (the
+// runtime-flag kernels) when an action type beyond RPM/PID is in use.
+static int launch_flags(mdg_handle h, int32_t action_type)
+{
+    const bool ext = mdg::extended_action(action_type) || (action_type == MDG_ACT_MIXED && h->act_ext);
+    return ext ? 8 : h->uniform_flags;
+}
+
 static int step_common(mdg_handle h, float* state, const float* action, int32_t action_type, int32_t n_substeps,
                        float* kin, int32_t* nbr_idx, float* nbr_rel, bool with_obs, void* stream,
                        bool obs_host = false)
 {
     if (!h) return fail(MDG_ERR_ARG, "mdg_step: NULL handle");
-    if (action_type != MDG_ACT_RPM && action_type != MDG_ACT_PID && action_type != MDG_ACT_MIXED)
-        return fail(MDG_ERR_ARG, "mdg_step: unknown action_type %d", action_type);
+    if (!mdg::valid_action(action_type)) return fail(MDG_ERR_ARG, "mdg_step: unknown action_type %d", action_type);
     if (action_type == MDG_ACT_MIXED && !h->act_set)
         return fail(MDG_ERR_ARG, "mdg_step: MDG_ACT_MIXED needs mdg_set_action_types first");
     if (n_substeps < 1) return fail(MDG_ERR_ARG, "mdg_step: n_substeps = %d < 1", n_substeps);
@@ -642,7 +654,8 @@ static int step_common(mdg_handle h, float* state, const float* action, int32_t 
     a.n_sub = n_substeps;
     a.act_type = action_type;
     a.obs_host = obs_host ? 1 : 0;
-    cudaError_t e = mdg::launch_step(a, h->n_tiles, h->block, with_obs, h->uniform_flags, (cudaStream_t)stream);
+    cudaError_t e =
+        mdg::launch_step(a, h->n_tiles, h->block, with_obs, launch_flags(h, action_type), (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "mdg_step: launch");
     return MDG_OK;
 }
@@ -777,8 +790,7 @@ static int rollout_args(mdg_handle h, float* state, const float* actions, int32_
                         mdg::RolloutArgs* r)
 {
     if (!h) return fail(MDG_ERR_ARG, "mdg_rollout: NULL handle");
-    if (action_type != MDG_ACT_RPM && action_type != MDG_ACT_PID && action_type != MDG_ACT_MIXED)
-        return fail(MDG_ERR_ARG, "mdg_rollout: unknown action_type %d", action_type);
+    if (!mdg::valid_action(action_type)) return fail(MDG_ERR_ARG, "mdg_rollout: unknown action_type %d", action_type);
     if (action_type == MDG_ACT_MIXED && !h->act_set)
         return fail(MDG_ERR_ARG, "mdg_rollout: MDG_ACT_MIXED needs mdg_set_action_types first");
     if (n_substeps < 1) return fail(MDG_ERR_ARG, "mdg_rollout: n_substeps = %d < 1", n_substeps);
@@ -822,9 +834,10 @@ static cudaError_t enqueue_rollout(mdg_handle h, const mdg::RolloutArgs& r, cuda
     if (e != cudaSuccess) return e;
     int n_sm = 152;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device);
-    const int grid = n_sm * mdg::rollout_blocks_per_sm(h->block, h->uniform_flags, h->uniform_N, h->dc.rk4 != 0,
-                                                           h->dc.gnd_rotor != 0);
-    return mdg::launch_rollout(r, h->block, h->uniform_flags, grid, s);
+    const int flags = launch_flags(h, r.s.act_type);
+    const int grid =
+        n_sm * mdg::rollout_blocks_per_sm(h->block, flags, h->uniform_N, h->dc.rk4 != 0, h->dc.gnd_rotor != 0);
+    return mdg::launch_rollout(r, h->block, flags, grid, s);
 }
 
 int mdg_rollout(mdg_handle h, float* state, const float* actions, int32_t action_per_step, int32_t action_type,

@@ -36,6 +36,7 @@ struct DevConsts {
     float att_kp[3], att_ki[3], att_kd[3], att_iclamp;
     float dt_sim, dt_ctrl;
     float max_rpm, f_max, inv_kf;     // PID output clip: f_i in [0, k_f MAX_RPM^2]
+    float hover_rpm;                  // normalized actions: 0 -> HOVER_RPM
     float alloc_xy, alloc_z;          // inverse mixing: sqrt(2)/L (X) or 2/L (+), and k_f/k_m
     float mix_x[4], mix_y[4];         // inverse mixing signs of tau_x, tau_y per rotor
     int frame_p;                      // 1: + rotor layout (l_sqrt2 then holds L)
@@ -138,6 +139,11 @@ std::vector<Tile> build_tiles(const std::vector<int32_t>& off, const std::vector
 int default_block(int32_t max_env, int64_t n_drones, int n_sm);
 
 cudaError_t launch_step(const StepArgs& a, int n_tiles, int block, bool with_obs, int uniform_flags, cudaStream_t s);
+
+// Action types the kernels accept, and those only the runtime-flag kernels convert.
+inline bool valid_env_action(int t) { return t == MDG_ACT_RPM || t == MDG_ACT_PID || (t >= MDG_ACT_RPM_NORM && t <= MDG_ACT_ATTITUDE); }
+inline bool valid_action(int t) { return valid_env_action(t) || t == MDG_ACT_MIXED; }
+inline bool extended_action(int t) { return t >= MDG_ACT_RPM_NORM && t <= MDG_ACT_ATTITUDE; }
 // grid: persistent CTAs (0: one per work item)
 cudaError_t launch_rollout(const RolloutArgs& a, int block, int uniform_flags, int grid, cudaStream_t s);
 int rollout_blocks_per_sm(int block, int uniform_flags, int uniform_N, bool rk4, bool gnd_rotor);
@@ -182,6 +188,7 @@ struct mdg_ctx {
     uint8_t* d_flags = nullptr;
     uint8_t* d_act = nullptr;
     bool act_set = false;
+    bool act_ext = false;  // some environment's type is beyond RPM/PID (runtime-flag kernels)
     mdg::Tile* d_tiles = nullptr;
     int n_tiles = 0;
     int block = 0;

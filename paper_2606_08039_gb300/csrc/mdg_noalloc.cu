@@ -86,7 +86,7 @@ extern "C" int mdg_step_obs_noalloc(const mdg_constants* c, int32_t n_envs, cons
                     n_envs, MDG_NOALLOC_MAX_ENVS);
     if (n_envs > 0 && (!drones_per_env || !model_flags))
         return fail(MDG_ERR_ARG, "mdg_step_obs_noalloc: drones_per_env and model_flags are required");
-    if (action_type != MDG_ACT_RPM && action_type != MDG_ACT_PID && action_type != MDG_ACT_MIXED)
+    if (!mdg::valid_action(action_type))
         return fail(MDG_ERR_ARG, "mdg_step_obs_noalloc: unknown action_type %d", action_type);
     if (action_type == MDG_ACT_MIXED && n_envs > 0 && !action_types)
         return fail(MDG_ERR_ARG, "mdg_step_obs_noalloc: MDG_ACT_MIXED needs action_types");
@@ -104,6 +104,7 @@ extern "C" int mdg_step_obs_noalloc(const mdg_constants* c, int32_t n_envs, cons
     off[0] = 0;
     int64_t total = 0;
     int32_t max_env = 0;
+    bool ext = mdg::extended_action(action_type);
     for (int32_t e = 0; e < n_envs; ++e) {
         const int32_t N = drones_per_env[e];
         if (N < 0 || N > MDG_MAX_ENV_DRONES)
@@ -111,8 +112,11 @@ extern "C" int mdg_step_obs_noalloc(const mdg_constants* c, int32_t n_envs, cons
                         MDG_MAX_ENV_DRONES);
         if (model_flags[e] & ~(MDG_GND | MDG_DRAG | MDG_DW))
             return fail(MDG_ERR_ARG, "mdg_step_obs_noalloc: model_flags[%d] has unknown bits", e);
-        if (action_type == MDG_ACT_MIXED && action_types[e] != MDG_ACT_RPM && action_types[e] != MDG_ACT_PID)
-            return fail(MDG_ERR_ARG, "mdg_step_obs_noalloc: action_types[%d] is not RPM or PID", e);
+        if (action_type == MDG_ACT_MIXED) {
+            if (!mdg::valid_env_action(action_types[e]))
+                return fail(MDG_ERR_ARG, "mdg_step_obs_noalloc: action_types[%d] is not an action type", e);
+            ext = ext || mdg::extended_action(action_types[e]);
+        }
         total += N;
         if (total > 0x7fffffffLL) return fail(MDG_ERR_ARG, "mdg_step_obs_noalloc: more than 2^31 - 1 drones");
         off[e + 1] = (int32_t)total;
@@ -177,6 +181,7 @@ extern "C" int mdg_step_obs_noalloc(const mdg_constants* c, int32_t n_envs, cons
         if (off[e + 1] - off[e] != max_env) uniform = false;
         if (flg[e] != flg[0]) uniform_flags = -1;
     }
+    if (ext) uniform_flags = 8;  // action types beyond RPM/PID: the runtime-flag kernels
     uint32_t* st = reinterpret_cast<uint32_t*>(g_stage + kOffStatus);
     st[0] = 0u;            // status bits start clear
     st[1] = 0xffffffffu;   // no offending drone yet

@@ -118,6 +118,32 @@ __device__ __forceinline__ Motor motor(const float n[4], const DevConsts& c)
 // M f = [T, tau] is f = 1/4 (T + sqrt2/L tau_x r1 + sqrt2/L tau_y r2 + k_f/k_m tau_z r3);
 // for the + layout the rows [0,1,0,-1] and [-1,0,1,0] (norm^2 2, times L^2) give
 // f = 1/4 (T + 2/L tau_x r1 + 2/L tau_y r2 + k_f/k_m tau_z r3). r1, r2 are mix_x, mix_y.
+template <bool kRate>
+__device__ __forceinline__ void attitude_and_mix(Drone& d, float T, float phi_t, float theta_t, float psi_t, float wz_t,
+                                                 float roll, float pitch, float yaw, const DevConsts& c, float rpm[4],
+                                                 float& yaw_err)
+{
+    float e[3] = {phi_t - roll, theta_t - pitch, psi_t - yaw};
+    e[2] -= 2.f * kPi * floorf((e[2] + kPi) * (0.5f / kPi));  // wrap to [-pi, pi)
+    float tau[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        d.ia[r] = fminf(c.att_iclamp, fmaxf(-c.att_iclamp, d.ia[r] + e[r] * c.dt_ctrl));
+        tau[r] = c.att_kp[r] * e[r] + c.att_ki[r] * d.ia[r] - c.att_kd[r] * d.w[r];
+    }
+    if (kRate)  // target body rate [0, 0, wz_t]
+        tau[2] = c.att_kp[2] * e[2] + c.att_ki[2] * d.ia[2] + c.att_kd[2] * (wz_t - d.w[2]);
+    const float tx = tau[0] * c.alloc_xy, ty = tau[1] * c.alloc_xy, tz = tau[2] * c.alloc_z;
+    // multiplying by the signs +-1, 0 is exact, so the X layout rounds as T + tx - ty - tz
+    const float f[4] = {0.25f * (((T + c.mix_x[0] * tx) + c.mix_y[0] * ty) - tz),
+                        0.25f * (((T + c.mix_x[1] * tx) + c.mix_y[1] * ty) + tz),
+                        0.25f * (((T + c.mix_x[2] * tx) + c.mix_y[2] * ty) - tz),
+                        0.25f * (((T + c.mix_x[3] * tx) + c.mix_y[3] * ty) + tz)};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) rpm[i] = sqrtf(fminf(c.f_max, fmaxf(0.f, f[i])) * c.inv_kf);
+    yaw_err = e[2];
+}
+
 __device__ __forceinline__ void pid(Drone& d, const float4 wp, const DevConsts& c, float rpm[4], float ep[3],
                                     float& yaw_err)
 {
@@ -137,23 +163,70 @@ __device__ __forceinline__ void pid(Drone& d, const float4 wp, const DevConsts& 
     const float theta_t = (acc[0] * cps + acc[1] * sps) * c.inv_g;
     float roll, pitch, yaw;
     rpy_of(d.q, roll, pitch, yaw);
-    float e[3] = {phi_t - roll, theta_t - pitch, wp.w - yaw};
-    e[2] -= 2.f * kPi * floorf((e[2] + kPi) * (0.5f / kPi));  // wrap to [-pi, pi)
-    float tau[3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        d.ia[r] = fminf(c.att_iclamp, fmaxf(-c.att_iclamp, d.ia[r] + e[r] * c.dt_ctrl));
-        tau[r] = c.att_kp[r] * e[r] + c.att_ki[r] * d.ia[r] - c.att_kd[r] * d.w[r];
+    attitude_and_mix<false>(d, T, phi_t, theta_t, wp.w, 0.f, roll, pitch, yaw, c, rpm, yaw_err);
+}
+
+// Normalized RPM action (the tasks' [-1, 1] actions; the map is not printed). Reading: a
+// clipped to [-1, 1], -1 -> 0, 0 -> HOVER_RPM, 1 -> MAX_RPM, linear on each side of hover.
+__device__ __forceinline__ float normalized_rpm(float a, const DevConsts& c)
+{
+    a = fminf(1.f, fmaxf(-1.f, a));
+    return a <= 0.f ? c.hover_rpm * (1.f + a) : c.hover_rpm + (c.max_rpm - c.hover_rpm) * a;
+}
+
+// The action types of Table "Action types" beyond RPM and PID, compiled into the
+// runtime-flag kernels only:
+//  RPM_NORM   four normalized values; ONE_D_RPM  act.x normalized, on all four motors;
+//  VEL        body-frame [v_x, v_y, v_z, omega_z] through the PID: the position loop holds
+//             the current position (zero error) with target velocity R v_body, the attitude
+//             loop the current yaw with target body rate [0, 0, omega_z];
+//  ATTITUDE   [T (N), roll*, pitch*, yaw rate] through the attitude loop (current yaw,
+//             target body rate [0, 0, yaw rate]) and the mixer.
+__device__ __forceinline__ void ext_action_rpm(Drone& d, const float4 act, int type, const DevConsts& c,
+                                               float rpm[4])
+{
+    if (type == MDG_ACT_RPM_NORM) {
+        rpm[0] = normalized_rpm(act.x, c);
+        rpm[1] = normalized_rpm(act.y, c);
+        rpm[2] = normalized_rpm(act.z, c);
+        rpm[3] = normalized_rpm(act.w, c);
+        return;
     }
-    const float tx = tau[0] * c.alloc_xy, ty = tau[1] * c.alloc_xy, tz = tau[2] * c.alloc_z;
-    // multiplying by the signs +-1, 0 is exact, so the X layout rounds as T + tx - ty - tz
-    const float f[4] = {0.25f * (((T + c.mix_x[0] * tx) + c.mix_y[0] * ty) - tz),
-                        0.25f * (((T + c.mix_x[1] * tx) + c.mix_y[1] * ty) + tz),
-                        0.25f * (((T + c.mix_x[2] * tx) + c.mix_y[2] * ty) - tz),
-                        0.25f * (((T + c.mix_x[3] * tx) + c.mix_y[3] * ty) + tz)};
+    if (type == MDG_ACT_ONE_D_RPM) {
+        const float r = normalized_rpm(act.x, c);
+        rpm[0] = rpm[1] = rpm[2] = rpm[3] = r;
+        return;
+    }
+    float roll, pitch, yaw;
+    rpy_of(d.q, roll, pitch, yaw);
+    float T = act.x, phi_t = act.y, theta_t = act.z;
+    if (type == MDG_ACT_VEL) {
+        const float qw = d.q[0], qx = d.q[1], qy = d.q[2], qz = d.q[3];
+        const float vt[3] = {
+            (1.f - 2.f * (qy * qy + qz * qz)) * act.x + 2.f * (qx * qy - qw * qz) * act.y + 2.f * (qx * qz + qw * qy) * act.z,
+            2.f * (qx * qy + qw * qz) * act.x + (1.f - 2.f * (qx * qx + qz * qz)) * act.y + 2.f * (qy * qz - qw * qx) * act.z,
+            2.f * (qx * qz - qw * qy) * act.x + 2.f * (qy * qz + qw * qx) * act.y + (1.f - 2.f * (qx * qx + qy * qy)) * act.z};
+        float acc[3];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) rpm[i] = sqrtf(fminf(c.f_max, fmaxf(0.f, f[i])) * c.inv_kf);
-    yaw_err = e[2];
+        for (int r = 0; r < 3; ++r) {
+            d.ip[r] = fminf(c.pos_iclamp, fmaxf(-c.pos_iclamp, d.ip[r]));  // zero position error
+            acc[r] = c.pos_ki[r] * d.ip[r] + c.pos_kd[r] * (vt[r] - d.v[r]);
+        }
+        acc[2] += c.g;
+        T = c.mass * sqrtf(acc[0] * acc[0] + acc[1] * acc[1] + acc[2] * acc[2]);
+        float sps, cps;
+        sincosf(yaw, &sps, &cps);
+        phi_t = (acc[0] * sps - acc[1] * cps) * c.inv_g;
+        theta_t = (acc[0] * cps + acc[1] * sps) * c.inv_g;
+    }
+    float ye;
+    attitude_and_mix<true>(d, T, phi_t, theta_t, yaw, act.w, roll, pitch, yaw, c, rpm, ye);
+}
+
+// Whether an action type runs the PID loops (and so reads and writes their integrals).
+__device__ __forceinline__ bool uses_loops(int act)
+{
+    return act == MDG_ACT_PID || act == MDG_ACT_VEL || act == MDG_ACT_ATTITUDE;
 }
 
 // Downwash of Eq. downwash that drone j at p feels from one drone o of its environment:
@@ -703,12 +776,15 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
     }
     const EnvSlot env = tile_env(a, tile, s_off, s_info);
     const bool is_pid = env.act == MDG_ACT_PID;
+    const bool loops = is_pid || (kFlags >= 8 && uses_loops(env.act));
 
     Drone d;
     unpack_state(s0, s1, s2, s3, s4, d);
     float rpm[4] = {0.f, 0.f, 0.f, 0.f};
     if (active) {
-        if (is_pid) {
+        if (kFlags >= 8 && env.act >= MDG_ACT_RPM_NORM) {
+            ext_action_rpm(d, act, env.act, a.c, rpm);
+        } else if (is_pid) {
             float ep[3], ye;
             pid(d, act, a.c, rpm, ep, ye);
         } else {
@@ -740,7 +816,7 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
     }
     bool bad = false;
     if (active) {
-        store_state(a.state, a.n, g, d, is_pid);
+        store_state(a.state, a.n, g, d, loops);
         a.state[5 * a.n + g] = make_float4(rpm[0], rpm[1], rpm[2], rpm[3]);
         bad = !finite_state(d);
     }
@@ -860,6 +936,7 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
         }
         const bool active = t < n_drones && env.N > 0;  // env.N == 0 only after a failed debug check
         const bool is_pid = env.act == MDG_ACT_PID;
+        const bool loops = is_pid || (kFlags >= 8 && uses_loops(env.act));
         const bool tile_dw = (bits & kTileAnyDW) != 0;
         const bool warp_local = (bits & kTileWarpLocal) != 0;
 
@@ -883,7 +960,9 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
             float4 next = {};
             if (active && k + 1 < r.K) next = a.action[(k + 1) * r.action_stride + g];
             if (active) {
-                if (is_pid) {
+                if (kFlags >= 8 && env.act >= MDG_ACT_RPM_NORM) {
+                    ext_action_rpm(d, act, env.act, a.c, rpm);
+                } else if (is_pid) {
                     float ep[3], ye;
                     pid(d, act, a.c, rpm, ep, ye);
                 } else {
@@ -924,7 +1003,7 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
         }
         bool bad = false;
         if (active) {
-            store_state(a.state, a.n, g, d, is_pid);
+            store_state(a.state, a.n, g, d, loops);
             a.state[5 * a.n + g] = make_float4(rpm[0], rpm[1], rpm[2], rpm[3]);
             bad = !finite_state(d);
         }
@@ -1046,16 +1125,21 @@ __global__ void __launch_bounds__(1024) surrogate_prepare_kernel(const Surrogate
         act = a.action[g];
     }
     const EnvSlot env = tile_env(a, tile, s_off, s_info);
-    const bool is_pid = env.act == MDG_ACT_PID;
     Drone d;
     unpack_state(s0, s1, s2, s3, s4, d);
     float rpm[4] = {0.f, 0.f, 0.f, 0.f};
     if (active) {
-        if (is_pid) {
-            float ep[3], ye;
-            pid(d, act, a.c, rpm, ep, ye);
-            a.state[3 * a.n + g] = make_float4(d.w[2], d.ip[0], d.ip[1], d.ip[2]);
-            a.state[4 * a.n + g] = make_float4(d.ia[0], d.ia[1], d.ia[2], 0.f);
+        if (uses_loops(env.act) || env.act >= MDG_ACT_RPM_NORM) {
+            if (env.act == MDG_ACT_PID) {
+                float ep[3], ye;
+                pid(d, act, a.c, rpm, ep, ye);
+            } else {
+                ext_action_rpm(d, act, env.act, a.c, rpm);
+            }
+            if (uses_loops(env.act)) {
+                a.state[3 * a.n + g] = make_float4(d.w[2], d.ip[0], d.ip[1], d.ip[2]);
+                a.state[4 * a.n + g] = make_float4(d.ia[0], d.ia[1], d.ia[2], 0.f);
+            }
         } else {
             rpm[0] = fminf(a.c.max_rpm, fmaxf(0.f, act.x));
             rpm[1] = fminf(a.c.max_rpm, fmaxf(0.f, act.y));

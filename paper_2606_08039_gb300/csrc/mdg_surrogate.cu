@@ -353,7 +353,7 @@ int mdg_surrogate_step(mdg_handle h, mdg_mlp m, float* state, const float* actio
         return fail(MDG_ERR_UNSUPPORTED, "mdg_surrogate_step: needs environments of one size, at most 32 drones");
     if (h->dc.rk4)
         return fail(MDG_ERR_UNSUPPORTED, "mdg_surrogate_step: the fallback integrates with Euler substeps only");
-    if (action_type != MDG_ACT_RPM && action_type != MDG_ACT_PID && action_type != MDG_ACT_MIXED)
+    if (!mdg::valid_action(action_type))
         return fail(MDG_ERR_ARG, "mdg_surrogate_step: unknown action_type %d", action_type);
     if (action_type == MDG_ACT_MIXED && !h->act_set)
         return fail(MDG_ERR_ARG, "mdg_surrogate_step: MDG_ACT_MIXED needs mdg_set_action_types first");

@@ -38,6 +38,8 @@ import numpy as np
 
 GND, DRAG, DW = 1, 2, 4
 ACT_RPM, ACT_PID = 0, 1
+ACT_RPM_NORM, ACT_ONE_D_RPM, ACT_VEL, ACT_ATTITUDE = 3, 4, 5, 6
+ALL_ACTION_TYPES = (ACT_RPM, ACT_PID, ACT_RPM_NORM, ACT_ONE_D_RPM, ACT_VEL, ACT_ATTITUDE)
 
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
@@ -210,6 +212,47 @@ def mixed_actions(swarm: Swarm, seed: int, step: int, hover_rpm: float) -> np.nd
     pid = np.repeat(swarm.act_type == ACT_PID, swarm.drones_per_env)
     a[pid] = waypoints(seed, swarm.n)[pid]
     return a
+
+
+S_ACT_TYPE, S_ACT_EXT = 10, 11
+
+
+def all_action_types(seed: int, n_envs: int) -> np.ndarray:
+    """uint8 [n_envs]: each environment's action type drawn uniformly from the six types."""
+    u = uniform(seed, S_ACT_TYPE, 0, np.arange(n_envs, dtype=np.uint64), 0).astype(np.float64)
+    pick = np.minimum((u * len(ALL_ACTION_TYPES)).astype(np.int64), len(ALL_ACTION_TYPES) - 1)
+    return np.asarray(ALL_ACTION_TYPES, np.uint8)[pick]
+
+
+def typed_actions(drones_per_env: np.ndarray, act_types: np.ndarray, seed: int, step: int, hover_rpm: float,
+                  hover_thrust: float) -> np.ndarray:
+    """[n, 4] float32 actions for per-environment action types (hover_rpm and hover_thrust
+    are the caller's scales):
+    RPM        U[0.9, 1.1] x hover_rpm per motor
+    PID        waypoints (see waypoints)
+    RPM_NORM   U[-1.2, 1.2] per motor (beyond [-1, 1] to exercise the clip)
+    ONE_D_RPM  U[-1.2, 1.2] in the first value, the others U[-1.2, 1.2] too (ignored)
+    VEL        U[-1, 1]^3 m/s body velocity, U[-1, 1] rad/s yaw rate
+    ATTITUDE   U[0.8, 1.2] x hover_thrust, roll and pitch U[-0.3, 0.3] rad, yaw rate U[-1, 1]."""
+    n = int(np.sum(drones_per_env))
+    per = np.repeat(np.asarray(act_types), drones_per_env)
+    idx = np.arange(n, dtype=np.uint64)[:, None]
+    comp = np.arange(4, dtype=np.uint64)[None, :]
+    u = uniform(seed, S_ACT_EXT, step, idx, comp).astype(np.float64)
+    out = np.zeros((n, 4), np.float64)
+    rpm = rpm_actions(seed, n, step, hover_rpm).astype(np.float64)
+    wp = waypoints(seed, n).astype(np.float64)
+    out[per == ACT_RPM] = rpm[per == ACT_RPM]
+    out[per == ACT_PID] = wp[per == ACT_PID]
+    norm = -1.2 + 2.4 * u
+    for t in (ACT_RPM_NORM, ACT_ONE_D_RPM):
+        out[per == t] = norm[per == t]
+    vel = np.concatenate([-1.0 + 2.0 * u[:, 0:3], -1.0 + 2.0 * u[:, 3:4]], axis=1)
+    out[per == ACT_VEL] = vel[per == ACT_VEL]
+    att = np.stack([hover_thrust * (0.8 + 0.4 * u[:, 0]), -0.3 + 0.6 * u[:, 1], -0.3 + 0.6 * u[:, 2],
+                    -1.0 + 2.0 * u[:, 3]], axis=1)
+    out[per == ACT_ATTITUDE] = att[per == ACT_ATTITUDE]
+    return out.astype(np.float32)
 
 
 S_MLP = 9

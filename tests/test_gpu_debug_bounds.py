@@ -9,7 +9,7 @@ in a separate process that loads it, runs every kernel family on the workloads o
 parity suite (uniform and table tiles, compile-time and runtime environment sizes, the
 persistent rollout, observations, PID, surrogate features, preparation, application and
 the fallback pass, the allocation-free entry point, the RK4 and per-rotor ground-height
-variants); no check may fail.
+variants, every action type); no check may fail.
 """
 import ctypes
 import os
@@ -93,12 +93,19 @@ def _run():
     rk4.integrator = mdg.INTEGRATOR_RK4
     gnd_rotor = mdg.Constants.cf2p()
     gnd_rotor.gnd_heights = mdg.GND_ROTOR
-    for name, c, tag in (("uneven", rk4, "rk4"), ("dense", rk4, "rk4"), ("uneven", gnd_rotor, "per-rotor")):
+    cf2x = mdg.Constants.cf2x()
+    for name, c, tag in (("uneven", rk4, "rk4"), ("dense", rk4, "rk4"), ("uneven", gnd_rotor, "per-rotor"),
+                         ("uneven", cf2x, "all action types")):
         sw = swarms[name]
         h = mdg.Handle(sw.drones_per_env, sw.flags, c)
-        h.set_action_types(sw.act_type)
+        if tag == "all action types":
+            types = wl.all_action_types(91, sw.n_envs)
+            h.set_action_types(types)
+            act = torch.as_tensor(wl.typed_actions(sw.drones_per_env, types, 92, 0, hover, 0.265), device=dev)
+        else:
+            h.set_action_types(sw.act_type)
+            act = torch.as_tensor(wl.mixed_actions(sw, 90, 0, hover), device=dev)
         st = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=dev)
-        act = torch.as_tensor(wl.mixed_actions(sw, 90, 0, hover), device=dev)
         kin, idx, rel = h.new_obs(dev)
         for block in sorted({h.block_size, 256, 1024}):
             if block < max(sw.drones_per_env):
