@@ -31,6 +31,7 @@ ACT_RPM_NORM, ACT_ONE_D_RPM, ACT_VEL, ACT_ATTITUDE = 3, 4, 5, 6
 FRAME_X, FRAME_P = 0, 1
 EULER, RK4 = 0, 1
 GND_COM, GND_ROTOR = 0, 1
+CTRL_PID, CTRL_DSL = 0, 1
 
 _lock = threading.Lock()
 _lib = None
@@ -60,7 +61,9 @@ class Params(ctypes.Structure):
         ("att_kp", ctypes.c_double * 3), ("att_ki", ctypes.c_double * 3), ("att_kd", ctypes.c_double * 3),
         ("att_iclamp", ctypes.c_double),
         ("dt_sim", ctypes.c_double), ("dt_ctrl", ctypes.c_double),
-        ("frame", ctypes.c_int32), ("integrator", ctypes.c_int32), ("gnd_heights", ctypes.c_int32)]
+        ("sp_rate_pos", ctypes.c_double), ("sp_rate_yaw", ctypes.c_double),
+        ("frame", ctypes.c_int32), ("integrator", ctypes.c_int32), ("gnd_heights", ctypes.c_int32),
+        ("controller", ctypes.c_int32)]
 
     def to_dict(self) -> dict:
         out = {}
@@ -98,12 +101,15 @@ def lib():
                 "orc_substep": ([P, ctypes.c_int, _D, _D, ctypes.c_int, ctypes.c_double, _D], None),
                 "orc_allocation_matrix": ([P, _D], None),
                 "orc_pid": ([P, _D, _D, _D, _D, _D, _D], None),
+                "orc_pid_ff": ([P, _D, _D, _D, _D, _D, _D, _D, _D], None),
+                "orc_dsl_setpoint": ([P, _D, _D, _D], None),
+                "orc_controller_dsl": ([P], None),
                 "orc_normalized_rpm": ([P, ctypes.c_double], ctypes.c_double),
-                "orc_action_to_rpm": ([P, ctypes.c_int, _D, _D, _D, _D], None),
+                "orc_action_to_rpm": ([P, ctypes.c_int, _D, _D, _D, _D, _D], None),
                 "orc_kin": ([_D, _D, _D], None),
                 "orc_knn": ([ctypes.c_int, _D, ctypes.c_int, ctypes.c_int, _I, _D], None),
                 "orc_control_steps": ([P, ctypes.c_int, _I, _I, _I, _D, _D, _D, _D, ctypes.c_int, ctypes.c_int,
-                                       _D, _I, _D], ctypes.c_int),
+                                       _D, _I, _D, _D], ctypes.c_int),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -247,16 +253,50 @@ def pid(p: Params, x, integ, wp):
     return rpm, pe, ye.value, integ
 
 
+def controller_dsl(p: Params) -> Params:
+    """The DSL controller's gains, clamps and rate limits applied to a copy of p."""
+    q = Params()
+    ctypes.memmove(ctypes.byref(q), ctypes.byref(p), ctypes.sizeof(Params))
+    lib().orc_controller_dsl(ctypes.byref(q))
+    return q
+
+
+def new_setpoints(n: int) -> np.ndarray:
+    """[n, 4] DSL setpoints not yet set (NaN): each starts at its drone's position and yaw."""
+    return np.full((n, 4), np.nan)
+
+
+def dsl_setpoint(p: Params, x, wp, sp):
+    """One step of the setpoint limiter; returns the new setpoint [4]."""
+    x, wp = _f64(x), _f64(wp)
+    sp = _f64(sp).copy()
+    lib().orc_dsl_setpoint(ctypes.byref(p), _dptr(x), _dptr(wp), _dptr(sp))
+    return sp
+
+
+def pid_ff(p: Params, x, integ, wp, a_ff=None, sp=None):
+    """One controller call with an optional feed-forward acceleration and DSL setpoint:
+    returns (rpm[4], pos_err[3], yaw_err, new integ[6], new setpoint[4] or None)."""
+    x, wp = _f64(x), _f64(wp)
+    integ = _f64(integ).copy()
+    sp = None if sp is None else _f64(sp).copy()
+    ff = None if a_ff is None else _f64(a_ff)
+    rpm, pe, ye = np.zeros(4), np.zeros(3), ctypes.c_double()
+    lib().orc_pid_ff(ctypes.byref(p), _dptr(x), _dptr(integ), _dptr(sp) if sp is not None else None, _dptr(wp),
+                     _dptr(ff) if ff is not None else None, _dptr(rpm), _dptr(pe), ctypes.byref(ye))
+    return rpm, pe, ye.value, integ, sp
+
+
 def normalized_rpm(p: Params, a: float) -> float:
     return lib().orc_normalized_rpm(ctypes.byref(p), float(a))
 
 
 def action_to_rpm(p: Params, act_type: int, x, integ, act):
-    """One drone's action -> (rpm [4], updated integ [6]) for any action type."""
+    """One drone's action -> (rpm [4], updated integ [6]) for any action type (no DSL setpoint)."""
     x, act = _f64(x), _f64(act)
     integ = _f64(integ).copy()
     rpm = np.zeros(4)
-    lib().orc_action_to_rpm(ctypes.byref(p), int(act_type), _dptr(x), _dptr(integ), _dptr(act), _dptr(rpm))
+    lib().orc_action_to_rpm(ctypes.byref(p), int(act_type), _dptr(x), _dptr(integ), None, _dptr(act), _dptr(rpm))
     return rpm, integ
 
 
@@ -277,9 +317,13 @@ def knn(x_env, j: int, idx_base: int = 0):
 
 
 def control_steps(p: Params, env_off, env_flags, env_act, x, integ, a_prev, actions, n_sub: int,
-                  obs: bool = False):
+                  obs: bool = False, setpoint=None):
     """K control steps over a CSR batch. x [n,13], integ [n,6], a_prev [n,4] and actions [K,n,4]
-    (float64). Returns (x, integ, a_prev) updated copies, plus (kin, nbr_idx, nbr_rel) when obs."""
+    (float64). Returns (x, integ, a_prev) updated copies, plus (kin, nbr_idx, nbr_rel) when obs.
+    setpoint: float64 C-contiguous [n,4] DSL setpoints, updated in place (required with the
+    DSL controller)."""
+    if setpoint is not None:
+        assert isinstance(setpoint, np.ndarray) and setpoint.dtype == np.float64 and setpoint.flags.c_contiguous
     env_off = np.ascontiguousarray(env_off, dtype=np.int32)
     env_flags = np.ascontiguousarray(env_flags, dtype=np.int32)
     env_act = np.ascontiguousarray(env_act, dtype=np.int32)
@@ -299,7 +343,7 @@ def control_steps(p: Params, env_off, env_flags, env_act, x, integ, a_prev, acti
     rc = lib().orc_control_steps(ctypes.byref(p), n_envs, _iptr(env_off), _iptr(env_flags), _iptr(env_act),
                                  _dptr(x), _dptr(integ), _dptr(a_prev), _dptr(actions), K, int(n_sub),
                                  _dptr(kin_o) if obs else None, _iptr(nbr_i) if obs else None,
-                                 _dptr(nbr_r) if obs else None)
+                                 _dptr(nbr_r) if obs else None, _dptr(setpoint) if setpoint is not None else None)
     if rc != 0:
         raise ValueError("orc_control_steps rejected its arguments")
     if obs:

@@ -56,6 +56,11 @@
 #define ORC_GND_COM 0
 #define ORC_GND_ROTOR 1
 
+/* Controllers (Section 4.2.1): PIDControl, or DSLPIDControl (retuned gains, halved
+ * integral clamps, rate-limited position and yaw setpoints, feed-forward acceleration). */
+#define ORC_CTRL_PID 0
+#define ORC_CTRL_DSL 1
+
 /* Model parameters. Field order is the oracle's own; the Python side of the
  * oracle mirrors it. */
 typedef struct {
@@ -69,9 +74,12 @@ typedef struct {
     double pos_kp[3], pos_ki[3], pos_kd[3], pos_iclamp;
     double att_kp[3], att_ki[3], att_kd[3], att_iclamp;
     double dt_sim, dt_ctrl;
+    /* DSLPIDControl's setpoint rate limits (m/s, rad/s) */
+    double sp_rate_pos, sp_rate_yaw;
     int32_t frame;      /* ORC_FRAME_X / ORC_FRAME_P */
     int32_t integrator; /* ORC_EULER / ORC_RK4 */
     int32_t gnd_heights; /* ORC_GND_COM / ORC_GND_ROTOR */
+    int32_t controller;  /* ORC_CTRL_PID / ORC_CTRL_DSL */
 } orc_params;
 
 int orc_params_size(void) { return (int)sizeof(orc_params); }
@@ -129,6 +137,9 @@ void orc_params_cf2x(orc_params* P)
     P->frame = ORC_FRAME_X;
     P->integrator = ORC_EULER;
     P->gnd_heights = ORC_GND_COM;
+    P->sp_rate_pos = 2.0;
+    P->sp_rate_yaw = ORC_PI;
+    P->controller = ORC_CTRL_PID;
 }
 
 /* CF2P: the CF2X parameters (Table "Drone model parameters" lists one column for both)
@@ -206,6 +217,32 @@ void orc_rpy(const double q[4], double rpy[3])
     rpy[0] = atan2(2.0 * (w * x + y * z), 1.0 - 2.0 * (x * x + y * y));
     rpy[1] = asin(sp);
     rpy[2] = atan2(2.0 * (w * z + x * y), 1.0 - 2.0 * (y * y + z * z));
+}
+
+/* DSLPIDControl (Section 4.2.1): "retunes the position and attitude gains" (not printed),
+ * "halves the integral clamps" and rate-limits the position (2.0 m/s) and yaw (pi rad/s)
+ * setpoints. Reading for the gains: each loop is tuned as a second-order system,
+ * x'' + Kd x' + Kp x = 0 for the position loop (the PID commands an acceleration) and
+ * J x'' + Kd x' + Kp x = 0 for the attitude loop (it commands a torque), with natural
+ * frequency w_n and damping z: Kp = w_n^2, Kd = 2 z w_n (position; w_n = 1.5, 1.5, 2.0 rad/s,
+ * z = 0.8, 0.8, 1.0, Ki = 0.05) and Kp = J w_n^2, Kd = 2 z w_n J (attitude; w_n = 20, 20,
+ * 10 rad/s, z = 0.9, Ki = J (0, 0, 5)), the model's own J. The clamps are half of P's. */
+void orc_controller_dsl(orc_params* P)
+{
+    const double wp[3] = {1.5, 1.5, 2.0}, zp[3] = {0.8, 0.8, 1.0};
+    const double wa[3] = {20.0, 20.0, 10.0}, za = 0.9, kia[3] = {0.0, 0.0, 5.0};
+    const double J[3] = {P->Jxx, P->Jyy, P->Jzz};
+    for (int r = 0; r < 3; ++r) {
+        P->pos_kp[r] = wp[r] * wp[r];
+        P->pos_kd[r] = 2.0 * zp[r] * wp[r];
+        P->pos_ki[r] = 0.05;
+        P->att_kp[r] = J[r] * wa[r] * wa[r];
+        P->att_kd[r] = 2.0 * za * wa[r] * J[r];
+        P->att_ki[r] = J[r] * kia[r];
+    }
+    P->pos_iclamp *= 0.5;
+    P->att_iclamp *= 0.5;
+    P->controller = ORC_CTRL_DSL;
 }
 
 /* ---- forces: Eq. motor, Eq. ground, Eq. drag, Eq. downwash ---- */
@@ -529,9 +566,10 @@ static double wrap_pi(double a)
 
 /* The cascaded PID of Section 4.2.1 in its three stages. Readings, where the paper prints
  * only the structure, the gains and T = m |a*|:
- *  - position loop a* = Kp e_p + Ki I_p + Kd (v_t - v) + g z_hat, e_p = p_t - p, with
- *    I_p = clamp(I_p + e_p dt_ctrl, +-pos_iclamp), dt_ctrl the control period, and the
- *    target velocity v_t zero for waypoints;
+ *  - position loop a* = Kp e_p + Ki I_p + Kd (v_t - v) + a_ff + g z_hat, e_p = p_t - p,
+ *    with I_p = clamp(I_p + e_p dt_ctrl, +-pos_iclamp), dt_ctrl the control period, the
+ *    target velocity v_t zero for waypoints and the feed-forward acceleration a_ff
+ *    (DSLPIDControl's target_acc) zero unless given;
  *  - small-angle attitude target phi* = (a*_x sin psi* - a*_y cos psi*)/g,
  *    theta* = (a*_x cos psi* + a*_y sin psi*)/g;
  *  - attitude PID tau* = Kp e_eta + Ki I_eta + Kd (w_t - omega), e_eta the roll, pitch
@@ -540,7 +578,8 @@ static double wrap_pi(double a)
  *  - mixer: solve M f = [T*, tau*], clip each f_i to [0, k_f MAX_RPM^2] (standing in for
  *    the unprinted torque clamp), n_i = sqrt(f_i / k_f). */
 static void orc_position_loop(const orc_params* P, const double x[13], double integ[6], const double p_t[3],
-                              const double v_t[3], double psi_t, double* T, double att_t[2], double ep[3])
+                              const double v_t[3], const double a_ff[3], double psi_t, double* T, double att_t[2],
+                              double ep[3])
 {
     const double* p = x;
     const double* v = x + 7;
@@ -552,6 +591,7 @@ static void orc_position_loop(const orc_params* P, const double x[13], double in
         if (I < -P->pos_iclamp) I = -P->pos_iclamp;
         integ[r] = I;
         a[r] = P->pos_kp[r] * ep[r] + P->pos_ki[r] * I + P->pos_kd[r] * (v_t[r] - v[r]);
+        a[r] += a_ff[r];
     }
     a[2] += P->g;
     *T = P->mass * sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
@@ -596,21 +636,62 @@ static void orc_mix(const orc_params* P, double T, const double tau[3], double r
     }
 }
 
+/* DSLPIDControl's setpoint limiter: the setpoint sp = [x, y, z, psi] moves towards the
+ * waypoint by at most sp_rate_pos dt_ctrl (Euclidean distance) and sp_rate_yaw dt_ctrl
+ * (wrapped yaw difference) per control step. Reading: a setpoint whose x is NaN has not
+ * been set and starts at the drone's position and yaw. */
+void orc_dsl_setpoint(const orc_params* P, const double x[13], const double wp[4], double sp[4])
+{
+    if (isnan(sp[0])) {
+        double rpy[3];
+        orc_rpy(x + 3, rpy);
+        for (int r = 0; r < 3; ++r) sp[r] = x[r];
+        sp[3] = rpy[2];
+    }
+    double d[3], n2 = 0.0;
+    for (int r = 0; r < 3; ++r) {
+        d[r] = wp[r] - sp[r];
+        n2 += d[r] * d[r];
+    }
+    const double lim = P->sp_rate_pos * P->dt_ctrl;
+    const double n = sqrt(n2);
+    const double s = n > lim ? lim / n : 1.0;
+    for (int r = 0; r < 3; ++r) sp[r] += s * d[r];
+    double dy = wrap_pi(wp[3] - sp[3]);
+    const double ly = P->sp_rate_yaw * P->dt_ctrl;
+    if (dy > ly) dy = ly;
+    if (dy < -ly) dy = -ly;
+    sp[3] = wrap_pi(sp[3] + dy);
+}
+
 /* One call of the cascaded PID (computeControl) for one drone towards a waypoint. x is
  * the 13-d state, integ[6] = [position error integral (3), attitude error integral (3)]
- * (updated in place), wp = [x*, y*, z*, psi*]; zero target velocity and body rate.
+ * (updated in place), wp = [x*, y*, z*, psi*], a_ff the feed-forward acceleration (NULL:
+ * zero); zero target velocity and body rate. With the DSL controller and a setpoint sp
+ * (updated in place), the loops track the rate-limited setpoint instead of wp.
  * Returns (rpm, pos_error, yaw_error) like computeControl. */
-void orc_pid(const orc_params* P, const double x[13], double integ[6], const double wp[4],
-             double rpm[4], double pos_err[3], double* yaw_err)
+void orc_pid_ff(const orc_params* P, const double x[13], double integ[6], double* sp, const double wp[4],
+                const double* a_ff, double rpm[4], double pos_err[3], double* yaw_err)
 {
     static const double zero[3] = {0.0, 0.0, 0.0};
+    const double* tgt = wp;
+    if (P->controller == ORC_CTRL_DSL && sp) {
+        orc_dsl_setpoint(P, x, wp, sp);
+        tgt = sp;
+    }
     double T, att[2], ep[3], tau[3];
-    orc_position_loop(P, x, integ, wp, zero, wp[3], &T, att, ep);
-    orc_attitude_loop(P, x, integ, att[0], att[1], wp[3], zero, tau, yaw_err);
+    orc_position_loop(P, x, integ, tgt, zero, a_ff ? a_ff : zero, tgt[3], &T, att, ep);
+    orc_attitude_loop(P, x, integ, att[0], att[1], tgt[3], zero, tau, yaw_err);
     orc_mix(P, T, tau, rpm);
     if (pos_err) {
         for (int r = 0; r < 3; ++r) pos_err[r] = ep[r];
     }
+}
+
+void orc_pid(const orc_params* P, const double x[13], double integ[6], const double wp[4],
+             double rpm[4], double pos_err[3], double* yaw_err)
+{
+    orc_pid_ff(P, x, integ, NULL, wp, NULL, rpm, pos_err, yaw_err);
 }
 
 /* Normalized RPM action (Table "Action types"; the tasks map actions in [-1, 1] to RPMs,
@@ -629,7 +710,7 @@ double orc_normalized_rpm(const orc_params* P, double a)
  *  RPM        the four speeds clipped to [0, MAX_RPM];
  *  RPM_NORM   four normalized values (orc_normalized_rpm);
  *  ONE_D_RPM  act[0] normalized, the same speed on all four motors;
- *  PID        waypoint [x, y, z, psi] (orc_pid);
+ *  PID        waypoint [x, y, z, psi] (orc_pid_ff; sp the DSL setpoint or NULL);
  *  VEL        body-frame [v_x, v_y, v_z, omega_z] through the PID: reading, the position
  *             loop holds the current position (e_p = 0) with target velocity R v_body,
  *             and the attitude loop holds the current yaw with target body rate
@@ -638,11 +719,11 @@ double orc_normalized_rpm(const orc_params* P, double a)
  *             attitude loop towards phi*, theta* and the current yaw with target body rate
  *             [0, 0, yaw rate], then the mixer.
  * integ is updated as the loops run. */
-void orc_action_to_rpm(const orc_params* P, int type, const double x[13], double integ[6], const double act[4],
-                       double rpm[4])
+void orc_action_to_rpm(const orc_params* P, int type, const double x[13], double integ[6], double* sp,
+                       const double act[4], double rpm[4])
 {
     if (type == ORC_ACT_PID) {
-        orc_pid(P, x, integ, act, rpm, NULL, NULL);
+        orc_pid_ff(P, x, integ, sp, act, NULL, rpm, NULL, NULL);
     } else if (type == ORC_ACT_RPM_NORM) {
         for (int i = 0; i < 4; ++i) rpm[i] = orc_normalized_rpm(P, act[i]);
     } else if (type == ORC_ACT_ONE_D_RPM) {
@@ -656,7 +737,8 @@ void orc_action_to_rpm(const orc_params* P, int type, const double x[13], double
             double R[9], v_t[3];
             orc_rotation(x + 3, R);
             for (int r = 0; r < 3; ++r) v_t[r] = R[3 * r] * act[0] + R[3 * r + 1] * act[1] + R[3 * r + 2] * act[2];
-            orc_position_loop(P, x, integ, x, v_t, rpy[2], &T, att, ep);
+            static const double no_ff[3] = {0.0, 0.0, 0.0};
+            orc_position_loop(P, x, integ, x, v_t, no_ff, rpy[2], &T, att, ep);
         } else {
             T = act[0];
             att[0] = act[1];
@@ -758,12 +840,15 @@ void orc_knn(int N, const double* x, int j, int idx_base, int32_t idx[4], double
  *   a_prev   [n][4]    last applied RPMs, written
  *   actions  [K][n][4] one action per drone (RPMs, waypoints, velocities, ...)
  *   kin      [n][20], nbr_idx [n][4], nbr_rel [n][24] (optional)
+ *   setpoint [n][4]    DSL setpoints, updated in place (required with the DSL
+ *                      controller, else ignored; may be NULL)
  * Returns 0, or -1 on a bad argument. */
 int orc_control_steps(const orc_params* P, int n_envs, const int32_t* env_off, const int32_t* env_flags,
                       const int32_t* env_act, double* x, double* integ, double* a_prev, const double* actions,
-                      int K, int n_sub, double* kin, int32_t* nbr_idx, double* nbr_rel)
+                      int K, int n_sub, double* kin, int32_t* nbr_idx, double* nbr_rel, double* setpoint)
 {
     if (n_envs < 0 || K < 0 || n_sub < 1) return -1;
+    if (P->controller == ORC_CTRL_DSL && !setpoint) return -1;
     int maxN = 0;
     for (int e = 0; e < n_envs; ++e) {
         int N = env_off[e + 1] - env_off[e];
@@ -779,8 +864,8 @@ int orc_control_steps(const orc_params* P, int n_envs, const int32_t* env_off, c
             const int b = env_off[e], N = env_off[e + 1] - env_off[e];
             for (int j = 0; j < N; ++j) {
                 const double* a = act + 4 * (size_t)(b + j);
-                orc_action_to_rpm(P, env_act[e], x + 13 * (size_t)(b + j), integ + 6 * (size_t)(b + j), a,
-                                  rpm + 4 * j);
+                orc_action_to_rpm(P, env_act[e], x + 13 * (size_t)(b + j), integ + 6 * (size_t)(b + j),
+                                  setpoint ? setpoint + 4 * (size_t)(b + j) : NULL, a, rpm + 4 * j);
                 for (int i = 0; i < 4; ++i) a_prev[4 * (size_t)(b + j) + i] = rpm[4 * j + i];
             }
             for (int s = 0; s < n_sub; ++s) {

@@ -70,6 +70,10 @@ MUTATIONS = {
     "normalized_upper_slope": ("return a <= 0.0 ? hover * (1.0 + a) : hover + (maxrpm - hover) * a;",
                                "return a <= 0.0 ? hover * (1.0 + a) : hover * (1.0 + a);"),
     "yaw_rate_sign": ("const double w_t[3] = {0.0, 0.0, act[3]};", "const double w_t[3] = {0.0, 0.0, -act[3]};"),
+    "dsl_rate_limit_dropped": ("const double s = n > lim ? lim / n : 1.0;", "const double s = 1.0;"),
+    "dsl_yaw_limit_sign": ("if (dy < -ly) dy = -ly;", "if (dy < -ly) dy = ly;"),
+    "feed_forward_dropped": ("a[r] += a_ff[r];", "a[r] += 0.0 * a_ff[r];"),
+    "dsl_setpoint_unused": ("        tgt = sp;\n", "        tgt = wp;\n"),
 }
 
 
