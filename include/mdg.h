@@ -114,6 +114,13 @@ typedef struct mdg_ctx* mdg_handle;
 #define MDG_INTEGRATOR_RK4 1
 #define MDG_GND_COM 0
 #define MDG_GND_ROTOR 1
+/* controller selects the cascaded PID of Section 4.2.1: MDG_CTRL_PID (PIDControl) or
+ * MDG_CTRL_DSL (DSLPIDControl: its gains and halved clamps are set by
+ * mdg_controller_dsl; the waypoint is tracked through a setpoint that moves towards it by
+ * at most sp_rate_pos [m/s] and sp_rate_yaw [rad/s] per control period; the setpoints live
+ * in a caller-owned buffer attached with mdg_set_setpoints). */
+#define MDG_CTRL_PID 0
+#define MDG_CTRL_DSL 1
 typedef struct mdg_constants {
     double mass, arm, thrust2weight, Jxx, Jyy, Jzz, kf, km, prop_radius;
     double g;
@@ -122,9 +129,11 @@ typedef struct mdg_constants {
     double pos_kp[3], pos_ki[3], pos_kd[3], pos_iclamp;
     double att_kp[3], att_ki[3], att_kd[3], att_iclamp;
     double dt_sim, dt_ctrl;
+    double sp_rate_pos, sp_rate_yaw;
     int32_t frame;
     int32_t integrator;
     int32_t gnd_heights;
+    int32_t controller;
 } mdg_constants;
 
 /* Fill *out with the CF2X constants (Table "Drone model parameters", Eq. downwash
@@ -144,6 +153,15 @@ int mdg_constants_cf2p(mdg_constants* out);
  * follows the CF2X derivation from r_p and T/W, the position gains are kept and the
  * attitude gains are scaled per axis by the inertia ratio J_RACE / J_CF2X. */
 int mdg_constants_race(mdg_constants* out);
+
+/* DSLPIDControl (Section 4.2.1: retuned gains, integral clamps halved, setpoint rate
+ * limits 2.0 m/s and pi rad/s, feed-forward acceleration) applied to *c in place: the
+ * gains are not printed, and are set here by tuning each loop as a second-order system
+ * from c's own inertia: position Kp = w^2, Kd = 2 z w, Ki = 0.05 (w = 1.5, 1.5, 2.0 rad/s,
+ * z = 0.8, 0.8, 1.0); attitude Kp = J w^2, Kd = 2 z w J, Ki = J (0, 0, 5) (w = 20, 20,
+ * 10 rad/s, z = 0.9). pos_iclamp and att_iclamp are halved, controller = MDG_CTRL_DSL.
+ * Host only. Returns MDG_ERR_ARG if c is NULL. */
+int mdg_controller_dsl(mdg_constants* c);
 
 /* sizeof(mdg_constants), for bindings that mirror the struct. */
 int mdg_constants_size(void);
@@ -174,6 +192,15 @@ int64_t mdg_num_drones(mdg_handle h);
 /* Per-environment action types for MDG_ACT_MIXED: host [n_envs], each an action type
  * other than MDG_ACT_MIXED (copied to the device on the default stream, synchronously). */
 int mdg_set_action_types(mdg_handle h, const uint8_t* per_env);
+
+/* Attach the DSL controller's setpoints: device float32 [n_drones][4] = (x, y, z, yaw),
+ * 16-byte aligned, caller-owned, read and written by every step, rollout, surrogate step
+ * and mdg_pid call with the DSL controller (waypoint actions move each drone's setpoint
+ * towards its waypoint, rate-limited, and the PID tracks the setpoint). A setpoint whose
+ * x is NaN is not set yet and starts at the drone's position and yaw (fill the buffer
+ * with NaN to start, or a drone's row to reset it). NULL detaches. Required before any
+ * compute call of a handle created with the DSL controller. Errors: MDG_ERR_ARG. */
+int mdg_set_setpoints(mdg_handle h, float* setpoints);
 
 /* Threads per block of the step kernels (a multiple of 32 in [32, 1024] and at least
  * the largest environment, rounded up to 32). Environments are packed whole into
@@ -231,6 +258,13 @@ int mdg_step_obs_host(mdg_handle h, float* state, const float* action_host, int3
  *   yaw_err    device float32 [n_drones] or NULL */
 int mdg_pid(mdg_handle h, float* state, const float* waypoints, float* rpm_out, float* pos_err, float* yaw_err,
             void* stream);
+
+/* mdg_pid with a feed-forward acceleration (DSLPIDControl's target_acc, added to the
+ * position loop's output before the thrust direction is formed; any controller):
+ *   target_acc device float32 [n_drones][4] = (a_x, a_y, a_z, unused) [m/s^2], or NULL
+ *              (zero). The step functions' waypoint actions carry no feed-forward. */
+int mdg_pid_ff(mdg_handle h, float* state, const float* waypoints, const float* target_acc, float* rpm_out,
+               float* pos_err, float* yaw_err, void* stream);
 
 /* Observations of the current state (Section 3.4.4 KIN, and the neighbourhood
  * adjacency of the abstract):

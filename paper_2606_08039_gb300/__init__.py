@@ -37,6 +37,7 @@ OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_UNSUPPORTED, ERR_TIMEOUT = 0, -1, -2, 
 FRAME_X, FRAME_P = 0, 1
 INTEGRATOR_EULER, INTEGRATOR_RK4 = 0, 1
 GND_COM, GND_ROTOR = 0, 1
+CTRL_PID, CTRL_DSL = 0, 1
 OBS_NONE, OBS_LAST, OBS_EVERY_STEP = 0, 1, 2
 MLP_IN, MLP_IN_PAD, MLP_HIDDEN, MLP_OUT, MLP_OUT_PAD = 41, 64, 256, 13, 32
 MLP_DIMS = (MLP_IN_PAD, MLP_HIDDEN, MLP_HIDDEN, MLP_HIDDEN, MLP_OUT_PAD)
@@ -52,6 +53,9 @@ _SIGNATURES = {
     "mdg_constants_cf2x": ([_VP], ctypes.c_int),
     "mdg_constants_cf2p": ([_VP], ctypes.c_int),
     "mdg_constants_race": ([_VP], ctypes.c_int),
+    "mdg_controller_dsl": ([_VP], ctypes.c_int),
+    "mdg_set_setpoints": ([_VP, _VP], ctypes.c_int),
+    "mdg_pid_ff": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "mdg_constants_size": ([], ctypes.c_int),
     "mdg_hover_rpm": ([_VP], ctypes.c_double),
     "mdg_max_rpm": ([_VP], ctypes.c_double),
@@ -140,7 +144,16 @@ class Constants(ctypes.Structure):
         ("att_kp", ctypes.c_double * 3), ("att_ki", ctypes.c_double * 3), ("att_kd", ctypes.c_double * 3),
         ("att_iclamp", ctypes.c_double),
         ("dt_sim", ctypes.c_double), ("dt_ctrl", ctypes.c_double),
-        ("frame", ctypes.c_int32), ("integrator", ctypes.c_int32), ("gnd_heights", ctypes.c_int32)]
+        ("sp_rate_pos", ctypes.c_double), ("sp_rate_yaw", ctypes.c_double),
+        ("frame", ctypes.c_int32), ("integrator", ctypes.c_int32), ("gnd_heights", ctypes.c_int32),
+        ("controller", ctypes.c_int32)]
+
+    def with_dsl(self) -> "Constants":
+        """A copy with the DSL controller's gains, clamps and setpoint limits (mdg_controller_dsl)."""
+        c = Constants()
+        ctypes.memmove(ctypes.byref(c), ctypes.byref(self), ctypes.sizeof(Constants))
+        _check(lib().mdg_controller_dsl(ctypes.byref(c)))
+        return c
 
     @classmethod
     def cf2x(cls) -> "Constants":
@@ -324,6 +337,19 @@ class Handle:
             raise ValueError("per_env must have one entry per environment")
         _check(lib().mdg_set_action_types(self._h, a.ctypes.data_as(_VP)))
 
+    def set_setpoints(self, setpoints):
+        """Attach the DSL controller's setpoints: a caller-owned float32 [n, 4] (x, y, z, yaw)
+        device tensor, NaN where not set yet (new_setpoints); None detaches. The tensor must
+        stay alive while attached."""
+        torch = _torch()
+        self._setpoints = setpoints
+        _check(lib().mdg_set_setpoints(self._h, _ptr(setpoints, "setpoints", torch.float32, (self.n, 4))))
+
+    def new_setpoints(self, device="cuda"):
+        """float32 [n, 4] setpoints, all NaN (each starts at its drone's position and yaw)."""
+        torch = _torch()
+        return torch.full((self.n, 4), float("nan"), dtype=torch.float32, device=device)
+
     def set_block_size(self, threads_per_block: int):
         _check(lib().mdg_set_block_size(self._h, int(threads_per_block)))
 
@@ -361,10 +387,11 @@ class Handle:
                                                  (self.n, NBR_K * NBR_FEAT)),
                                        _stream(stream)))
 
-    def pid(self, state, waypoints, rpm_out, pos_err=None, yaw_err=None, stream=None):
+    def pid(self, state, waypoints, rpm_out, pos_err=None, yaw_err=None, stream=None, target_acc=None):
         torch = _torch()
-        _check(lib().mdg_pid(self._h, _ptr(state, "state", torch.float32, (STATE_PLANES, self.n, 4)),
+        _check(lib().mdg_pid_ff(self._h, _ptr(state, "state", torch.float32, (STATE_PLANES, self.n, 4)),
                              _ptr(waypoints, "waypoints", torch.float32, (self.n, 4)),
+                             _ptr(target_acc, "target_acc", torch.float32, (self.n, 4)),
                              _ptr(rpm_out, "rpm_out", torch.float32, (self.n, 4)),
                              _ptr(pos_err, "pos_err", torch.float32, (self.n, 3)),
                              _ptr(yaw_err, "yaw_err", torch.float32, (self.n,)), _stream(stream)))

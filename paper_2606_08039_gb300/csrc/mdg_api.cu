@@ -91,6 +91,15 @@ bool constants_valid(const mdg_constants& c, std::string& why)
         why = "gnd_heights must be MDG_GND_COM or MDG_GND_ROTOR";
         return false;
     }
+    if (c.controller != MDG_CTRL_PID && c.controller != MDG_CTRL_DSL) {
+        why = "controller must be MDG_CTRL_PID or MDG_CTRL_DSL";
+        return false;
+    }
+    if (c.controller == MDG_CTRL_DSL &&
+        (!(c.sp_rate_pos > 0.0) || !isfinite(c.sp_rate_pos) || !(c.sp_rate_yaw > 0.0) || !isfinite(c.sp_rate_yaw))) {
+        why = "the DSL controller needs positive, finite setpoint rates";
+        return false;
+    }
     return true;
 }
 
@@ -142,6 +151,9 @@ DevConsts make_dev_consts(const mdg_constants& c)
     d.frame_p = c.frame == MDG_FRAME_P ? 1 : 0;
     d.rk4 = c.integrator == MDG_INTEGRATOR_RK4 ? 1 : 0;
     d.gnd_rotor = c.gnd_heights == MDG_GND_ROTOR ? 1 : 0;
+    d.dsl = c.controller == MDG_CTRL_DSL ? 1 : 0;
+    d.sp_step_pos = (float)(c.sp_rate_pos * c.dt_ctrl);
+    d.sp_step_yaw = (float)(c.sp_rate_yaw * c.dt_ctrl);
     if (d.frame_p) {
         // + layout: tau_x = L (F1 - F3), tau_y = L (F2 - F0); the mixing rows [1,1,1,1],
         // [0,1,0,-1] L, [-1,0,1,0] L, [-1,1,-1,1] k_m/k_f are orthogonal with squared norms
@@ -396,6 +408,7 @@ mdg::StepArgs base_args(mdg_ctx* h, float* state)
     a.uniform_N = h->uniform_N;
     a.envs_per_tile = h->envs_per_tile;
     a.uniform_bits = h->uniform_bits;
+    a.setpoints = h->d_sp;
     a.c = h->dc;
     return a;
 }
@@ -441,8 +454,11 @@ int mdg_constants_cf2x(mdg_constants* out)
     out->att_iclamp = 0.5;
     out->dt_sim = 1.0 / 240.0;
     out->dt_ctrl = 1.0 / 48.0;
+    out->sp_rate_pos = 2.0;
+    out->sp_rate_yaw = 3.14159265358979323846;
     out->frame = MDG_FRAME_X;
     out->integrator = MDG_INTEGRATOR_EULER;
+    out->controller = MDG_CTRL_PID;
     return MDG_OK;
 }
 
@@ -476,6 +492,26 @@ int mdg_constants_race(mdg_constants* out)
         out->att_ki[i] = cf.att_ki[i] * ratio[i];
         out->att_kd[i] = cf.att_kd[i] * ratio[i];
     }
+    return MDG_OK;
+}
+
+int mdg_controller_dsl(mdg_constants* c)
+{
+    if (!c) return fail(MDG_ERR_ARG, "mdg_controller_dsl: c is NULL");
+    const double wp[3] = {1.5, 1.5, 2.0}, zp[3] = {0.8, 0.8, 1.0};
+    const double wa[3] = {20.0, 20.0, 10.0}, za = 0.9, kia[3] = {0.0, 0.0, 5.0};
+    const double J[3] = {c->Jxx, c->Jyy, c->Jzz};
+    for (int r = 0; r < 3; ++r) {
+        c->pos_kp[r] = wp[r] * wp[r];
+        c->pos_kd[r] = 2.0 * zp[r] * wp[r];
+        c->pos_ki[r] = 0.05;
+        c->att_kp[r] = J[r] * wa[r] * wa[r];
+        c->att_kd[r] = 2.0 * za * wa[r] * J[r];
+        c->att_ki[r] = J[r] * kia[r];
+    }
+    c->pos_iclamp *= 0.5;
+    c->att_iclamp *= 0.5;
+    c->controller = MDG_CTRL_DSL;
     return MDG_OK;
 }
 
@@ -600,6 +636,14 @@ int mdg_set_action_types(mdg_handle h, const uint8_t* per_env)
     return MDG_OK;
 }
 
+int mdg_set_setpoints(mdg_handle h, float* setpoints)
+{
+    if (!h) return fail(MDG_ERR_ARG, "mdg_set_setpoints: NULL handle");
+    if (setpoints && !aligned16(setpoints)) return fail(MDG_ERR_ARG, "mdg_set_setpoints: not 16-byte aligned");
+    h->d_sp = reinterpret_cast<float4*>(setpoints);
+    return MDG_OK;
+}
+
 int mdg_set_block_size(mdg_handle h, int32_t threads_per_block)
 {
     if (!h) return fail(MDG_ERR_ARG, "mdg_set_block_size: NULL handle");
@@ -623,7 +667,15 @@ int32_t mdg_get_block_size(mdg_handle h)
 static int launch_flags(mdg_handle h, int32_t action_type)
 {
     const bool ext = mdg::extended_action(action_type) || (action_type == MDG_ACT_MIXED && h->act_ext);
-    return ext ? 8 : h->uniform_flags;
+    return (ext || h->dc.dsl) ? 8 : h->uniform_flags;
+}
+
+// The DSL controller reads and writes the caller's setpoints: they must be attached.
+static int check_setpoints(mdg_handle h, const char* fn)
+{
+    if (h->dc.dsl && !h->d_sp && h->n_drones > 0)
+        return fail(MDG_ERR_ARG, "%s: the DSL controller needs mdg_set_setpoints first", fn);
+    return MDG_OK;
 }
 
 static int step_common(mdg_handle h, float* state, const float* action, int32_t action_type, int32_t n_substeps,
@@ -636,6 +688,7 @@ static int step_common(mdg_handle h, float* state, const float* action, int32_t 
         return fail(MDG_ERR_ARG, "mdg_step: MDG_ACT_MIXED needs mdg_set_action_types first");
     if (n_substeps < 1) return fail(MDG_ERR_ARG, "mdg_step: n_substeps = %d < 1", n_substeps);
     int rc;
+    if ((rc = check_setpoints(h, "mdg_step")) != MDG_OK) return rc;
     if ((rc = check_state_ptr(h, state, "state")) != MDG_OK) return rc;
     if ((rc = check_state_ptr(h, action, "action")) != MDG_OK) return rc;
     if (with_obs) {
@@ -721,22 +774,26 @@ int mdg_step_obs_host(mdg_handle h, float* state, const float* action_host, int3
                        static_cast<int32_t*>(idx), static_cast<float*>(rel), true, stream, true);
 }
 
-int mdg_pid(mdg_handle h, float* state, const float* waypoints, float* rpm_out, float* pos_err, float* yaw_err,
-            void* stream)
+int mdg_pid_ff(mdg_handle h, float* state, const float* waypoints, const float* target_acc, float* rpm_out,
+               float* pos_err, float* yaw_err, void* stream)
 {
     if (!h) return fail(MDG_ERR_ARG, "mdg_pid: NULL handle");
     int rc;
     if ((rc = check_state_ptr(h, state, "state")) != MDG_OK) return rc;
     if ((rc = check_state_ptr(h, waypoints, "waypoints")) != MDG_OK) return rc;
     if ((rc = check_state_ptr(h, rpm_out, "rpm_out")) != MDG_OK) return rc;
+    if (target_acc && !aligned16(target_acc)) return fail(MDG_ERR_ARG, "target_acc is not 16-byte aligned");
     if (pos_err && (reinterpret_cast<uintptr_t>(pos_err) & 3u)) return fail(MDG_ERR_ARG, "pos_err misaligned");
     if (yaw_err && (reinterpret_cast<uintptr_t>(yaw_err) & 3u)) return fail(MDG_ERR_ARG, "yaw_err misaligned");
+    if ((rc = check_setpoints(h, "mdg_pid")) != MDG_OK) return rc;
     if (h->n_drones == 0) return MDG_OK;
     DeviceGuard dg(h->device);
     if (!dg.ok) return fail(MDG_ERR_CUDA, "mdg_pid: cannot select device %d", h->device);
     mdg::PidArgs a{};
     a.state = reinterpret_cast<float4*>(state);
     a.waypoints = reinterpret_cast<const float4*>(waypoints);
+    a.target_acc = reinterpret_cast<const float4*>(target_acc);
+    a.setpoints = h->d_sp;
     a.rpm_out = reinterpret_cast<float4*>(rpm_out);
     a.pos_err = pos_err;
     a.yaw_err = yaw_err;
@@ -745,6 +802,12 @@ int mdg_pid(mdg_handle h, float* state, const float* waypoints, float* rpm_out, 
     cudaError_t e = mdg::launch_pid(a, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "mdg_pid: launch");
     return MDG_OK;
+}
+
+int mdg_pid(mdg_handle h, float* state, const float* waypoints, float* rpm_out, float* pos_err, float* yaw_err,
+            void* stream)
+{
+    return mdg_pid_ff(h, state, waypoints, nullptr, rpm_out, pos_err, yaw_err, stream);
 }
 
 int mdg_obs(mdg_handle h, const float* state, float* kin, int32_t* nbr_idx, float* nbr_rel, void* stream)
@@ -795,6 +858,7 @@ static int rollout_args(mdg_handle h, float* state, const float* actions, int32_
         return fail(MDG_ERR_ARG, "mdg_rollout: MDG_ACT_MIXED needs mdg_set_action_types first");
     if (n_substeps < 1) return fail(MDG_ERR_ARG, "mdg_rollout: n_substeps = %d < 1", n_substeps);
     if (K < 0) return fail(MDG_ERR_ARG, "mdg_rollout: K = %d < 0", K);
+    if (check_setpoints(h, "mdg_rollout") != MDG_OK) return MDG_ERR_ARG;
     if (obs_mode != MDG_OBS_NONE && obs_mode != MDG_OBS_LAST && obs_mode != MDG_OBS_EVERY_STEP)
         return fail(MDG_ERR_ARG, "mdg_rollout: unknown obs_mode %d", obs_mode);
     int rc;

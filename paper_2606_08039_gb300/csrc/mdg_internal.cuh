@@ -42,6 +42,8 @@ struct DevConsts {
     int frame_p;                      // 1: + rotor layout (l_sqrt2 then holds L)
     int rk4;                          // 1: fourth-order Runge-Kutta substeps
     int gnd_rotor;                    // 1: Eq. ground at each rotor's height (runtime-flag kernels)
+    int dsl;                          // 1: DSL controller (rate-limited setpoints; runtime-flag kernels)
+    float sp_step_pos, sp_step_yaw;   // DSL setpoint limits per control period (rate x dt_ctrl)
     float rotor_x[4], rotor_y[4];     // rotor body positions (z = 0)
 };
 
@@ -72,6 +74,7 @@ struct StepArgs {
     int envs_per_tile;        // uniform batches: environments per block
     int uniform_bits;         // uniform batches: kTileAnyDW | kTileWarpLocal for every tile
     int obs_host;             // 1: observations go to host memory, written through per-warp staging
+    float4* setpoints;        // [n] DSL setpoints (x, y, z, yaw) or null
     DevConsts c;
 };
 
@@ -123,6 +126,8 @@ struct SurrogateArgs {
 struct PidArgs {
     float4* state;
     const float4* waypoints;
+    const float4* target_acc;  // [n] feed-forward (x, y, z, -) or null
+    float4* setpoints;         // [n] DSL setpoints or null
     float4* rpm_out;
     float* pos_err;           // [n][3] or null
     float* yaw_err;           // [n] or null
@@ -189,6 +194,7 @@ struct mdg_ctx {
     uint8_t* d_act = nullptr;
     bool act_set = false;
     bool act_ext = false;  // some environment's type is beyond RPM/PID (runtime-flag kernels)
+    float4* d_sp = nullptr;  // caller-owned DSL setpoints (mdg_set_setpoints)
     mdg::Tile* d_tiles = nullptr;
     int n_tiles = 0;
     int block = 0;

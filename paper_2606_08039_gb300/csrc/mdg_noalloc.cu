@@ -96,6 +96,8 @@ extern "C" int mdg_step_obs_noalloc(const mdg_constants* c, int32_t n_envs, cons
     else mdg_constants_cf2x(&cc);
     std::string why;
     if (!mdg::constants_valid(cc, why)) return fail(MDG_ERR_ARG, "mdg_step_obs_noalloc: %s", why.c_str());
+    if (cc.controller == MDG_CTRL_DSL)
+        return fail(MDG_ERR_UNSUPPORTED, "mdg_step_obs_noalloc: the DSL controller needs a handle's setpoints");
 
     std::lock_guard<std::mutex> lock(g_lock);
     int32_t* off = reinterpret_cast<int32_t*>(g_stage + kOffEnvOff);

@@ -144,16 +144,21 @@ __device__ __forceinline__ void attitude_and_mix(Drone& d, float T, float phi_t,
     yaw_err = e[2];
 }
 
+// kFF: add the feed-forward acceleration ff (DSLPIDControl's target_acc) to the position
+// loop's output (the standalone controller only; waypoint actions carry none).
+template <bool kFF = false>
 __device__ __forceinline__ void pid(Drone& d, const float4 wp, const DevConsts& c, float rpm[4], float ep[3],
-                                    float& yaw_err)
+                                    float& yaw_err, float4 ff = float4{})
 {
     const float tgt[3] = {wp.x, wp.y, wp.z};
+    const float aff[3] = {ff.x, ff.y, ff.z};
     float acc[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
         ep[r] = tgt[r] - d.p[r];
         d.ip[r] = fminf(c.pos_iclamp, fmaxf(-c.pos_iclamp, d.ip[r] + ep[r] * c.dt_ctrl));
         acc[r] = c.pos_kp[r] * ep[r] + c.pos_ki[r] * d.ip[r] - c.pos_kd[r] * d.v[r];
+        if (kFF) acc[r] += aff[r];
     }
     acc[2] += c.g;
     const float T = c.mass * sqrtf(acc[0] * acc[0] + acc[1] * acc[1] + acc[2] * acc[2]);
@@ -164,6 +169,34 @@ __device__ __forceinline__ void pid(Drone& d, const float4 wp, const DevConsts& 
     float roll, pitch, yaw;
     rpy_of(d.q, roll, pitch, yaw);
     attitude_and_mix<false>(d, T, phi_t, theta_t, wp.w, 0.f, roll, pitch, yaw, c, rpm, yaw_err);
+}
+
+// DSLPIDControl's setpoint limiter (Section 4.2.1): the drone's setpoint moves towards the
+// waypoint by at most sp_rate_pos dt_ctrl (straight line) and sp_rate_yaw dt_ctrl (wrapped
+// yaw difference) per control step, and the PID tracks the setpoint. A setpoint whose x is
+// NaN is not set yet and starts at the drone's position and yaw. Reads and writes *spp.
+__device__ __forceinline__ float4 dsl_setpoint(const Drone& d, const float4 wp, float4* spp, const DevConsts& c)
+{
+    float4 sp = *spp;
+    if (isnan(sp.x)) {
+        float roll, pitch, yaw;
+        rpy_of(d.q, roll, pitch, yaw);
+        sp = make_float4(d.p[0], d.p[1], d.p[2], yaw);
+    }
+    const float dx = wp.x - sp.x, dy = wp.y - sp.y, dz = wp.z - sp.z;
+    const float n = sqrtf(dx * dx + dy * dy + dz * dz);
+    const float s = n > c.sp_step_pos ? c.sp_step_pos / n : 1.f;
+    sp.x += s * dx;
+    sp.y += s * dy;
+    sp.z += s * dz;
+    float e = wp.w - sp.w;
+    e -= 2.f * kPi * floorf((e + kPi) * (0.5f / kPi));
+    e = fminf(c.sp_step_yaw, fmaxf(-c.sp_step_yaw, e));
+    float y = sp.w + e;
+    y -= 2.f * kPi * floorf((y + kPi) * (0.5f / kPi));
+    sp.w = y;
+    *spp = sp;
+    return sp;
 }
 
 // Normalized RPM action (the tasks' [-1, 1] actions; the map is not printed). Reading: a
@@ -786,7 +819,8 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
             ext_action_rpm(d, act, env.act, a.c, rpm);
         } else if (is_pid) {
             float ep[3], ye;
-            pid(d, act, a.c, rpm, ep, ye);
+            const float4 wp = (kFlags >= 8 && a.c.dsl) ? dsl_setpoint(d, act, a.setpoints + g, a.c) : act;
+            pid(d, wp, a.c, rpm, ep, ye);
         } else {
             rpm[0] = fminf(a.c.max_rpm, fmaxf(0.f, act.x));
             rpm[1] = fminf(a.c.max_rpm, fmaxf(0.f, act.y));
@@ -964,7 +998,8 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
                     ext_action_rpm(d, act, env.act, a.c, rpm);
                 } else if (is_pid) {
                     float ep[3], ye;
-                    pid(d, act, a.c, rpm, ep, ye);
+                    const float4 wp = (kFlags >= 8 && a.c.dsl) ? dsl_setpoint(d, act, a.setpoints + g, a.c) : act;
+                    pid(d, wp, a.c, rpm, ep, ye);
                 } else {
                     rpm[0] = fminf(a.c.max_rpm, fmaxf(0.f, act.x));
                     rpm[1] = fminf(a.c.max_rpm, fmaxf(0.f, act.y));
@@ -1132,7 +1167,8 @@ __global__ void __launch_bounds__(1024) surrogate_prepare_kernel(const Surrogate
         if (uses_loops(env.act) || env.act >= MDG_ACT_RPM_NORM) {
             if (env.act == MDG_ACT_PID) {
                 float ep[3], ye;
-                pid(d, act, a.c, rpm, ep, ye);
+                const float4 wp = a.c.dsl ? dsl_setpoint(d, act, a.setpoints + g, a.c) : act;
+                pid(d, wp, a.c, rpm, ep, ye);
             } else {
                 ext_action_rpm(d, act, env.act, a.c, rpm);
             }
@@ -1281,7 +1317,10 @@ __global__ void __launch_bounds__(256) pid_kernel(const PidArgs a)
         Drone d;
         load_state(a.state, a.n, g, d, true);
         float rpm[4], ep[3], ye;
-        pid(d, a.waypoints[g], a.c, rpm, ep, ye);
+        float4 wp = a.waypoints[g];
+        if (a.c.dsl) wp = dsl_setpoint(d, wp, a.setpoints + g, a.c);
+        if (a.target_acc) pid<true>(d, wp, a.c, rpm, ep, ye, a.target_acc[g]);
+        else pid(d, wp, a.c, rpm, ep, ye);
         a.rpm_out[g] = make_float4(rpm[0], rpm[1], rpm[2], rpm[3]);
         a.state[3 * a.n + g] = make_float4(d.w[2], d.ip[0], d.ip[1], d.ip[2]);
         a.state[4 * a.n + g] = make_float4(d.ia[0], d.ia[1], d.ia[2], 0.f);

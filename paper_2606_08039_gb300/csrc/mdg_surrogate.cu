@@ -358,6 +358,8 @@ int mdg_surrogate_step(mdg_handle h, mdg_mlp m, float* state, const float* actio
     if (action_type == MDG_ACT_MIXED && !h->act_set)
         return fail(MDG_ERR_ARG, "mdg_surrogate_step: MDG_ACT_MIXED needs mdg_set_action_types first");
     if (n_substeps < 1) return fail(MDG_ERR_ARG, "mdg_surrogate_step: n_substeps < 1");
+    if (h->dc.dsl && !h->d_sp)
+        return fail(MDG_ERR_ARG, "mdg_surrogate_step: the DSL controller needs mdg_set_setpoints first");
     if (!m->norm_set) return fail(MDG_ERR_ARG, "mdg_surrogate_step: the surrogate has no normalisation");
     const int n_pad = (int)((h->n_drones + 127) / 128 * 128);
     if (n_pad > m->max_batch)
@@ -383,6 +385,7 @@ int mdg_surrogate_step(mdg_handle h, mdg_mlp m, float* state, const float* actio
     a.s.uniform_N = h->uniform_N;
     a.s.envs_per_tile = h->envs_per_tile;
     a.s.uniform_bits = h->uniform_bits;
+    a.s.setpoints = h->d_sp;
     a.s.c = h->dc;
     a.x = m->x;
     a.y = m->y;

@@ -57,6 +57,17 @@ def oracle_step(P, swarm_or_layout, x, integ, a_prev, action, act_types, n_sub, 
                                 x, integ, a_prev, np.asarray(action, np.float64)[None], n_sub, obs=obs)
 
 
+def spread_heights(sw, dz=0.3, z0=0.5):
+    """The swarm with the drones of every environment at heights z0, z0 + dz, ... (in drone
+    order; x, y and everything else unchanged)."""
+    off = np.concatenate([[0], np.cumsum(sw.drones_per_env)])
+    p = sw.p.copy()
+    for e in range(sw.n_envs):
+        p[off[e]:off[e + 1], 2] = z0 + dz * np.arange(off[e + 1] - off[e])
+    sw.p = p.astype(np.float32)
+    return sw
+
+
 def subset_layout(dpe, envs):
     """Drone indices and layout of a subset of environments."""
     env_off = np.concatenate([[0], np.cumsum(dpe)])

@@ -17,7 +17,7 @@ import torch
 import oracle
 import paper_2606_08039_gb300 as mdg
 from paper_2606_08039_gb300 import workloads as wl
-from helpers import (assert_horizon_close, excess, oracle_arrays, oracle_horizon, oracle_step,
+from helpers import (assert_horizon_close, excess, oracle_arrays, oracle_horizon, oracle_step, spread_heights,
                      tolerance_response)
 
 pytestmark = pytest.mark.gpu
@@ -165,3 +165,151 @@ def test_action_type_arguments_are_checked(cuda):
     a = torch.zeros((sw.n, 4), device=cuda)
     with pytest.raises(mdg.MdgError):
         h.step(state, a, 7, 5)
+
+
+# ------------------------------------------------------------------ DSL controller
+PD = oracle.controller_dsl(oracle.cf2x())
+
+
+def _dsl_oracle(layout, x, integ, a_prev, actions, types, sp, n_sub=5):
+    """The oracle's DSL control steps (actions [K, n, 4]) from a state and setpoints; returns
+    (x, integ, a_prev, sp) and the response to a tolerance-size error in x (see
+    tolerance_response), with the same setpoints."""
+    dpe, flags = layout
+    env_off = np.concatenate([[0], np.cumsum(dpe)]).astype(np.int32)
+    args = (env_off, np.asarray(flags, np.int32), np.asarray(types, np.int32))
+    sa = np.ascontiguousarray(sp, np.float64).copy()
+    xa, ia, aa = oracle.control_steps(PD, *args, x, integ, a_prev, np.asarray(actions, np.float64), n_sub, setpoint=sa)
+    rng = np.random.default_rng(0)
+    sgn = rng.choice([-1.0, 1.0], size=x.shape)
+    x2 = x.copy()
+    for sl, tol in ((slice(0, 3), 1e-5), (slice(7, 10), 1e-5), (slice(10, 13), 1e-4)):
+        x2[:, sl] = x[:, sl] + sgn[:, sl] * tol * np.maximum(np.abs(x[:, sl]), 1.0)
+    q = x[:, 3:7] + sgn[:, 3:7] * 2e-6
+    x2[:, 3:7] = q / np.linalg.norm(q, axis=1, keepdims=True)
+    sb = np.ascontiguousarray(sp, np.float64).copy()
+    xb, _, _ = oracle.control_steps(PD, *args, x2, integ, a_prev, np.asarray(actions, np.float64), n_sub, setpoint=sb)
+    return (xa, ia, aa, sa), np.abs(xa - xb)
+
+
+def _dsl_handle(sw, cuda, types=None):
+    h = mdg.Handle(sw.drones_per_env, sw.flags, mdg.Constants.cf2x().with_dsl())
+    if types is not None:
+        h.set_action_types(types)
+    sp = h.new_setpoints(cuda)
+    h.set_setpoints(sp)
+    return h, sp
+
+
+@pytest.mark.parametrize("recipe", ["full_aero", "mixed"])
+def test_dsl_control_steps(cuda, recipe):
+    """Three control steps one launch each, the oracle restarted from the GPU's state and
+    setpoints every step (the first step initialises the NaN setpoints). Heights spread per
+    environment (helpers.spread_heights): the controller is under test here, not the
+    downwash's conditioning at near-equal heights."""
+    if recipe == "full_aero":
+        sw = spread_heights(wl.full_aero(41, n_envs=200))
+        types = np.full(sw.n_envs, mdg.ACT_PID, np.uint8)
+        act_type = mdg.ACT_PID
+    else:
+        sw = spread_heights(wl.uneven(42, n_envs=150))
+        types = wl.all_action_types(43, sw.n_envs)
+        act_type = mdg.ACT_MIXED
+    h, sp = _dsl_handle(sw, cuda, types if act_type == mdg.ACT_MIXED else None)
+    state = _state(sw, cuda, 44)
+    layout = (sw.drones_per_env, sw.flags)
+    pid_rows = np.repeat(types == mdg.ACT_PID, sw.drones_per_env)
+    for k in range(3):
+        action = wl.typed_actions(sw.drones_per_env, types, 45, k, HOVER, PD.mass * PD.g)
+        x0, i0, a0 = oracle_arrays(state)
+        sp0 = sp.cpu().numpy().astype(np.float64)
+        h.step(state, torch.as_tensor(action, device=cuda), act_type, 5)
+        torch.cuda.synchronize()
+        xg, ig, ag = oracle_arrays(state)
+        (xo, io, ao, so), resp = _dsl_oracle(layout, x0, i0, a0, action[None], types, sp0)
+        assert_horizon_close(xg, xo, resp, 5, what=f"dsl {recipe} step {k}")
+        np.testing.assert_allclose(PD.kf * ag ** 2, PD.kf * ao ** 2, rtol=0,
+                                   atol=1e-5 * PD.kf * oracle.max_rpm(PD) ** 2, err_msg=f"rpm step {k}")
+        assert excess(ig, io, 1e-5) <= 1.0
+        sg = sp.cpu().numpy().astype(np.float64)
+        assert np.all(np.isfinite(sg[pid_rows])) and np.all(np.isnan(sg[~pid_rows, 0]))
+        assert excess(sg[pid_rows], so[pid_rows], 1e-6) <= 1.0, f"setpoints step {k}"
+
+
+def test_dsl_rollout_carries_setpoints(cuda):
+    sw = spread_heights(wl.full_aero(46, n_envs=160))
+    K = 4
+    h, sp = _dsl_handle(sw, cuda)
+    state = _state(sw, cuda, 47)
+    wp = wl.waypoints(48, sw.n)
+    x0, i0, a0 = oracle_arrays(state)
+    h.rollout(state, torch.as_tensor(wp, device=cuda), mdg.ACT_PID, 5, K)
+    torch.cuda.synchronize()
+    xg, _, _ = oracle_arrays(state)
+    types = np.full(sw.n_envs, mdg.ACT_PID)
+    (xo, _, _, so), resp = _dsl_oracle((sw.drones_per_env, sw.flags), x0, i0, a0,
+                                       np.repeat(wp[None], K, axis=0), types, oracle.new_setpoints(sw.n))
+    assert_horizon_close(xg, xo, resp, 5 * K, what="dsl rollout")
+    assert excess(sp.cpu().numpy(), so, 1e-5) <= 1.0
+
+
+@pytest.mark.parametrize("dsl", [False, True])
+def test_standalone_controller_with_feed_forward(cuda, dsl):
+    sw = wl.full_aero(49, n_envs=64)
+    c = mdg.Constants.cf2x().with_dsl() if dsl else mdg.Constants.cf2x()
+    P = PD if dsl else oracle.cf2x()
+    h = mdg.Handle(sw.drones_per_env, sw.flags, c)
+    sp = h.new_setpoints(cuda)
+    if dsl:
+        h.set_setpoints(sp)
+    state = _state(sw, cuda, 50)
+    wp = wl.waypoints(51, sw.n)
+    ff = np.zeros((sw.n, 4), np.float32)
+    ff[:, 0:3] = wl.uniform_range(-2.0, 2.0, 52, 14, 0, np.arange(sw.n, dtype=np.uint64)[:, None],
+                                  np.arange(3, dtype=np.uint64)[None, :])
+    x0, i0, _ = oracle_arrays(state)
+    rpm = torch.empty((sw.n, 4), device=cuda)
+    pe = torch.empty((sw.n, 3), device=cuda)
+    ye = torch.empty((sw.n,), device=cuda)
+    h.pid(state, torch.as_tensor(wp, device=cuda), rpm, pe, ye, target_acc=torch.as_tensor(ff, device=cuda))
+    torch.cuda.synchronize()
+    _, ig, _ = oracle_arrays(state)
+    rpm, pe, ye = rpm.cpu().numpy(), pe.cpu().numpy(), ye.cpu().numpy()
+    sg = sp.cpu().numpy()
+    for j in range(sw.n):
+        r, e, y, integ, s = oracle.pid_ff(P, x0[j], i0[j], wp[j], a_ff=ff[j, 0:3],
+                                          sp=oracle.new_setpoints(1)[0] if dsl else None)
+        np.testing.assert_allclose(P.kf * rpm[j].astype(np.float64) ** 2, P.kf * r ** 2, rtol=0,
+                                   atol=1e-5 * P.kf * oracle.max_rpm(P) ** 2)
+        np.testing.assert_allclose(pe[j], e, rtol=1e-5, atol=1e-6)
+        assert abs(ye[j] - y) < 1e-5
+        assert excess(ig[j], integ, 1e-5) <= 1.0
+        if dsl:
+            assert excess(sg[j], s, 1e-6) <= 1.0
+
+
+def test_dsl_surrogate_fallback(cuda):
+    sw = spread_heights(wl.full_aero(53, n_envs=120))
+    h, sp = _dsl_handle(sw, cuda)
+    m = mdg.MLP((sw.n + 127) // 128 * 128, wl.mlp_init(54))
+    z = np.zeros(mdg.MLP_IN, np.float32)
+    m.set_normalization(z, z + 1, np.zeros(mdg.MLP_OUT, np.float32), np.ones(mdg.MLP_OUT, np.float32), z - 1e30,
+                        z + 1e30)
+    state = _state(sw, cuda, 55)
+    wp = wl.waypoints(56, sw.n)
+    x0, i0, a0 = oracle_arrays(state)
+    m.step(h, state, torch.as_tensor(wp, device=cuda), mdg.ACT_PID, 5, 0.0)
+    torch.cuda.synchronize()
+    xg, _, _ = oracle_arrays(state)
+    (xo, _, _, so), resp = _dsl_oracle((sw.drones_per_env, sw.flags), x0, i0, a0, wp[None],
+                                       np.full(sw.n_envs, mdg.ACT_PID), oracle.new_setpoints(sw.n))
+    assert_horizon_close(xg, xo, resp, 5, what="dsl surrogate fallback")
+    assert excess(sp.cpu().numpy(), so, 1e-6) <= 1.0
+
+
+def test_dsl_needs_setpoints(cuda):
+    sw = wl.full_aero(57, n_envs=8)
+    h = mdg.Handle(sw.drones_per_env, sw.flags, mdg.Constants.cf2x().with_dsl())
+    state = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=cuda)
+    with pytest.raises(mdg.MdgError):
+        h.step(state, torch.as_tensor(wl.waypoints(58, sw.n), device=cuda), mdg.ACT_PID, 5)

@@ -161,7 +161,7 @@ def test_argument_errors(cuda):
     with pytest.raises(mdg.MdgError):
         h.set_block_size(48)
     with pytest.raises(mdg.MdgError):
-        h.set_action_types(np.full(sw.n_envs, 5, np.uint8))
+        h.set_action_types(np.full(sw.n_envs, 7, np.uint8))
     big = mdg.Handle(np.array([64], np.int32), np.zeros(1, np.uint32))
     with pytest.raises(mdg.MdgError):
         big.set_block_size(32)

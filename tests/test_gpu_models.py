@@ -22,7 +22,7 @@ import torch
 import oracle
 import paper_2606_08039_gb300 as mdg
 from paper_2606_08039_gb300 import workloads as wl
-from helpers import assert_horizon_close, assert_state_close, oracle_arrays, oracle_step, tolerance_response
+from helpers import assert_horizon_close, assert_state_close, oracle_arrays, oracle_step, spread_heights, tolerance_response
 
 pytestmark = pytest.mark.gpu
 
@@ -35,17 +35,6 @@ def _pair(model, rk4):
         c.integrator = mdg.INTEGRATOR_RK4
         P.integrator = oracle.RK4
     return c, P
-
-
-def spread_heights(sw, dz=0.3, z0=0.5):
-    """The swarm with the drones of every environment at heights z0, z0 + dz, ... (in drone
-    order; x, y and everything else unchanged)."""
-    off = np.concatenate([[0], np.cumsum(sw.drones_per_env)])
-    p = sw.p.copy()
-    for e in range(sw.n_envs):
-        p[off[e]:off[e + 1], 2] = z0 + dz * np.arange(off[e + 1] - off[e])
-    sw.p = p.astype(np.float32)
-    return sw
 
 
 def _swarm(recipe):

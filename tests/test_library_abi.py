@@ -92,6 +92,14 @@ def test_create_rejects_bad_constants(mdg_lib):
     c.gnd_heights = -1
     rc, _ = _create(1, [1], [0], c)
     assert rc == mdg.ERR_ARG and "gnd_heights" in mdg_lib.mdg_last_error().decode()
+    c = mdg.Constants.cf2x()
+    c.controller = 5
+    rc, _ = _create(1, [1], [0], c)
+    assert rc == mdg.ERR_ARG and "controller" in mdg_lib.mdg_last_error().decode()
+    c = mdg.Constants.cf2x().with_dsl()
+    c.sp_rate_pos = 0.0
+    rc, _ = _create(1, [1], [0], c)
+    assert rc == mdg.ERR_ARG and "setpoint rates" in mdg_lib.mdg_last_error().decode()
 
 
 @pytest.mark.parametrize("model", ["cf2x", "cf2p", "race"])
@@ -101,6 +109,16 @@ def test_model_constants_match_the_oracle(mdg_lib, model):
     o = getattr(oracle, model)().to_dict()
     for k, v in o.items():
         np.testing.assert_allclose(c[k], v, rtol=1e-15, err_msg=k)
+
+
+@pytest.mark.parametrize("model", ["cf2x", "cf2p", "race"])
+def test_dsl_constants_match_the_oracle(mdg_lib, model):
+    """mdg_controller_dsl and the oracle's own DSL tuning give the same gains, clamps and limits."""
+    c = getattr(mdg.Constants, model)().with_dsl().to_dict()
+    o = oracle.controller_dsl(getattr(oracle, model)()).to_dict()
+    for k, v in o.items():
+        np.testing.assert_allclose(c[k], v, rtol=1e-15, err_msg=k)
+    assert c["controller"] == mdg.CTRL_DSL
 
 
 def test_null_handle_calls_fail_cleanly(mdg_lib):
