@@ -64,12 +64,25 @@ def kernel_sha() -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
+ACTION_CHOICES = {"pid": 1, "rpm": 0, "rpm_norm": 3, "one_d_rpm": 4, "vel": 5, "attitude": 6, "mixed": 2}
+
+
 def model_config(args) -> dict:
-    return {"model": args.model, "integrator": args.integrator, "gnd_heights": args.gnd_heights}
+    return {"model": args.model, "integrator": args.integrator, "gnd_heights": args.gnd_heights,
+            "actions": getattr(args, "actions", "pid"), "controller": getattr(args, "controller", "pid")}
 
 
 def is_default_model(args) -> bool:
-    return (args.model, args.integrator, args.gnd_heights) == ("cf2x", "euler", "com")
+    return ((args.model, args.integrator, args.gnd_heights) == ("cf2x", "euler", "com")
+            and getattr(args, "actions", "pid") == "pid" and getattr(args, "controller", "pid") == "pid")
+
+
+def action_types(args, n_envs: int, seed: int) -> np.ndarray:
+    """uint8 [n_envs] per-environment action types of the full-aero workload."""
+    from paper_2606_08039_gb300 import workloads as wl
+    if args.actions == "mixed":
+        return wl.all_action_types(seed, n_envs)
+    return np.full(n_envs, ACTION_CHOICES[args.actions], np.uint8)
 
 
 def library_constants(args):
@@ -78,6 +91,8 @@ def library_constants(args):
     c = getattr(mdg.Constants, args.model)()
     c.integrator = mdg.INTEGRATOR_RK4 if args.integrator == "rk4" else mdg.INTEGRATOR_EULER
     c.gnd_heights = mdg.GND_ROTOR if args.gnd_heights == "rotor" else mdg.GND_COM
+    if getattr(args, "controller", "pid") == "dsl":
+        c = c.with_dsl()
     return c
 
 
@@ -87,7 +102,28 @@ def oracle_params(args):
     P = getattr(oracle, args.model)()
     P.integrator = oracle.RK4 if args.integrator == "rk4" else oracle.EULER
     P.gnd_heights = oracle.GND_ROTOR if args.gnd_heights == "rotor" else oracle.GND_COM
+    if getattr(args, "controller", "pid") == "dsl":
+        P = oracle.controller_dsl(P)
     return P
+
+
+def oracle_workload(args, sw, seed: int):
+    """(env action types, actions [1, n, 4] float64, setpoints or None) of the full-aero
+    workload for the oracle legs."""
+    from paper_2606_08039_gb300 import workloads as wl
+    P = oracle_params(args)
+    types = action_types(args, sw.n_envs, seed)
+    if args.actions == "pid":
+        act = wl.waypoints(seed, sw.n)
+    else:
+        act = wl.typed_actions(sw.drones_per_env, types, seed, 0, oracle_hover(P), P.mass * P.g)
+    sp = np.full((sw.n, 4), np.nan) if args.controller == "dsl" else None
+    return types.astype(np.int32), act.astype(np.float64)[None], sp
+
+
+def oracle_hover(P) -> float:
+    import oracle
+    return oracle.hover_rpm(P)
 
 
 def measured_peaks() -> dict:
@@ -181,12 +217,13 @@ def cpu_baseline(args, seconds_target: float = 10.0) -> dict:
     P = oracle_params(args)
     sw = wl.full_aero(1)
     x, integ, a = sw.x13(), np.zeros((sw.n, 6)), np.zeros((sw.n, 4))
-    wp = wl.waypoints(1, sw.n).astype(np.float64)[None]
-    flags, acts = sw.flags.astype(np.int32), np.full(sw.n_envs, 1, np.int32)
+    acts, wp, sp = oracle_workload(args, sw, 1)
+    flags = sw.flags.astype(np.int32)
     steps = 0
     t0 = time.perf_counter()
     while True:
-        x, integ, a, *_ = oracle.control_steps(P, sw.env_off, flags, acts, x, integ, a, wp, N_SUB, obs=True)
+        x, integ, a, *_ = oracle.control_steps(P, sw.env_off, flags, acts, x, integ, a, wp, N_SUB, obs=True,
+                                               setpoint=sp)
         steps += 1
         dt = time.perf_counter() - t0
         if dt >= seconds_target or steps >= 200:
@@ -207,12 +244,13 @@ def run_reference(args) -> None:
     P = oracle_params(args)
     sw = wl.full_aero(1, n_envs=2048)
     x, integ, a = sw.x13(), np.zeros((sw.n, 6)), np.zeros((sw.n, 4))
-    wp = wl.waypoints(1, sw.n).astype(np.float64)[None]
-    flags, acts = sw.flags.astype(np.int32), np.full(sw.n_envs, 1, np.int32)
+    acts, wp, sp = oracle_workload(args, sw, 1)
+    flags = sw.flags.astype(np.int32)
 
     def one():
         nonlocal x, integ, a
-        x, integ, a, *_ = oracle.control_steps(P, sw.env_off, flags, acts, x, integ, a, wp, N_SUB, obs=True)
+        x, integ, a, *_ = oracle.control_steps(P, sw.env_off, flags, acts, x, integ, a, wp, N_SUB, obs=True,
+                                               setpoint=sp)
 
     for _ in range(args.warmup):
         one()
@@ -262,6 +300,21 @@ def algorithmic_flops(sw, K: int, n_sub: int, obs_steps: int, pid_mask=None, rk4
     per_step = n_sub * per_sub + pid
     total = np.sum(N * (K * per_step + obs_steps * (FLOPS_OBS + FLOPS_OBS_PER_NEIGHBOUR * (N - 1))))
     return float(total)
+
+
+def algorithmic_bytes(sw, types, act_type: int, dsl: bool) -> int:
+    """Bytes one fused control step must move for the full-aero workload: per drone the state
+    planes 0-3 read and written (64 + 64 B), plane 4 (attitude integrals) read unless every
+    action is RPM and written where the controller loops run (PID, VEL, ATTITUDE), the action
+    (16 B), plane 5 written (16 B), the observations (192 B), and with the DSL controller the
+    setpoint of each waypoint-driven drone read and written (32 B). 384 B for PID actions."""
+    per_env = np.full(sw.n_envs, 64 + 64 + 16 + 16 + OBS_BYTES, np.int64)
+    if act_type != 0:
+        per_env += 16
+    per_env += 16 * np.isin(types, (1, 5, 6))
+    if dsl:
+        per_env += 32 * (types == 1)
+    return int(np.sum(per_env * sw.drones_per_env))
 
 
 def binding_roofline(bytes_launch: float, flops_launch: float, sec: float, peaks) -> dict:
@@ -614,6 +667,9 @@ def main() -> None:
     ap.add_argument("--model", default="cf2x", choices=["cf2x", "cf2p", "race"])
     ap.add_argument("--integrator", default="euler", choices=["euler", "rk4"])
     ap.add_argument("--gnd-heights", default="com", choices=["com", "rotor"])
+    ap.add_argument("--actions", default="pid", choices=sorted(ACTION_CHOICES),
+                    help="full_aero: the action type of every environment, or mixed (all six types)")
+    ap.add_argument("--controller", default="pid", choices=["pid", "dsl"])
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -621,7 +677,9 @@ def main() -> None:
         run_reference(args)
         return
     if args.workload in ("surrogate", "mlp") and not is_default_model(args):
-        ap.error("--model/--integrator/--gnd-heights apply to the dynamics workloads only")
+        ap.error("--model/--integrator/--gnd-heights/--actions/--controller apply to the dynamics workloads only")
+    if args.workload != "full_aero" and (args.actions, args.controller) != ("pid", "pid"):
+        ap.error("--actions/--controller apply to the full_aero workload")
     if args.workload == "surrogate":
         run_surrogate(args)
         return
@@ -650,8 +708,28 @@ def main() -> None:
     h = mdg.Handle(sw.drones_per_env, sw.flags, library_constants(args))
     init_state = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=dev)
     state = init_state.clone()
-    wp_host = torch.from_numpy(wl.waypoints(replica_seed(rank), sw.n)).pin_memory()
+    # the action of every drone: waypoints for the PID (the headline), else the chosen type
+    c_lib = library_constants(args)
+    types = action_types(args, sw.n_envs, replica_seed(rank))
+    act_type = mdg.ACT_MIXED if args.actions == "mixed" else ACTION_CHOICES[args.actions]
+    if args.actions == "pid":
+        act_np = wl.waypoints(replica_seed(rank), sw.n)
+    else:
+        act_np = wl.typed_actions(sw.drones_per_env, types, replica_seed(rank), 0, c_lib.hover_rpm(),
+                                  c_lib.mass * c_lib.g)
+    if act_type == mdg.ACT_MIXED:
+        h.set_action_types(types)
+    setpoints = None
+    if args.controller == "dsl":
+        setpoints = h.new_setpoints(dev)
+        h.set_setpoints(setpoints)
+    wp_host = torch.from_numpy(act_np).pin_memory()
     wp = wp_host.to(dev)
+
+    def reset():
+        state.copy_(init_state)
+        if setpoints is not None:
+            setpoints.fill_(float("nan"))
     kin, idx, rel = h.new_obs(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     flush_sink = torch.empty((), dtype=torch.float32, device=dev)
@@ -665,8 +743,8 @@ def main() -> None:
     def step():
         nonlocal steps_done
         if steps_done and steps_done % EPISODE == 0:
-            state.copy_(init_state)
-        h.step_obs(state, wp, mdg.ACT_PID, N_SUB, kin, idx, rel, stream=stream)
+            reset()
+        h.step_obs(state, wp, act_type, N_SUB, kin, idx, rel, stream=stream)
         steps_done += 1
 
     for _ in range(args.warmup):
@@ -687,9 +765,9 @@ def main() -> None:
     for i in range(args.steps):
         flush_l2()
         if steps_done % EPISODE == 0 and steps_done:
-            state.copy_(init_state)
+            reset()
         starts[i].record(stream)
-        h.step_obs(state, wp, mdg.ACT_PID, N_SUB, kin, idx, rel, stream=stream)
+        h.step_obs(state, wp, act_type, N_SUB, kin, idx, rel, stream=stream)
         ends[i].record(stream)
         steps_done += 1
     torch.cuda.synchronize()
@@ -708,13 +786,13 @@ def main() -> None:
     rel_h = torch.empty(rel.shape, dtype=rel.dtype).pin_memory()
     e_starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.e2e_steps)]
     e_ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.e2e_steps)]
-    state.copy_(init_state)
+    reset()
     # the step kernel reads the waypoints from, and writes the observations to, the pinned
     # host buffers itself (mdg_step_obs_host): the transfers overlap its arithmetic
     for i in range(args.e2e_steps):
         flush_l2()
         e_starts[i].record(stream)
-        h.step_obs_host(state, wp_host, mdg.ACT_PID, N_SUB, kin_h, idx_h, rel_h, stream=stream)
+        h.step_obs_host(state, wp_host, act_type, N_SUB, kin_h, idx_h, rel_h, stream=stream)
         e_ends[i].record(stream)
         e_ends[i].synchronize()
     e2e_ms = float(sum(s.elapsed_time(e) for s, e in zip(e_starts, e_ends)))
@@ -731,11 +809,11 @@ def main() -> None:
     ep_starts = [torch.cuda.Event(enable_timing=True) for _ in range(EPISODE_REPS)]
     ep_ends = [torch.cuda.Event(enable_timing=True) for _ in range(EPISODE_REPS)]
     for i in range(1 + EPISODE_REPS):
-        state.copy_(init_state)
+        reset()
         flush_l2()
         if i:
             ep_starts[i - 1].record(stream)
-        h.rollout(state, wp, mdg.ACT_PID, N_SUB, EPISODE, mdg.OBS_EVERY_STEP, ep_kin, ep_idx, ep_rel, stream=stream)
+        h.rollout(state, wp, act_type, N_SUB, EPISODE, mdg.OBS_EVERY_STEP, ep_kin, ep_idx, ep_rel, stream=stream)
         if i:
             ep_ends[i - 1].record(stream)
     torch.cuda.synchronize()
@@ -749,9 +827,9 @@ def main() -> None:
     if rank == 0:
         peaks = measured_peaks()
         avg_s = total_ms / args.steps * 1e-3
-        bytes_launch = BYTES_PER_DRONE_STEP * sw.n
-        pid_all = np.ones(sw.n_envs, bool)
-        flops_launch = algorithmic_flops(sw, 1, N_SUB, 1, pid_all, rk4=args.integrator == "rk4")
+        bytes_launch = algorithmic_bytes(sw, types, act_type, args.controller == "dsl")
+        loops_mask = np.isin(types, (1, 5, 6))  # PID, VEL, ATTITUDE run the controller loops
+        flops_launch = algorithmic_flops(sw, 1, N_SUB, 1, loops_mask, rk4=args.integrator == "rk4")
         roofline = binding_roofline(bytes_launch, flops_launch, avg_s, peaks)
         # the ncu capture is of the default configuration's kernel at this source
         roofline["traffic"] = (NCU_TRAFFIC["bytes"] if NCU_TRAFFIC["kernel_sha"] == kernel_sha()
