@@ -32,6 +32,49 @@ FRAME_X, FRAME_P = 0, 1
 EULER, RK4 = 0, 1
 GND_COM, GND_ROTOR = 0, 1
 CTRL_PID, CTRL_DSL = 0, 1
+DR_PARAMS, WIND_STATE = 32, 8
+(DR_MASS, DR_J, DR_ARM, DR_KF, DR_KM, DR_CXY, DR_CZ, DR_CGND, DR_C1, DR_MAXRPM, DR_BIAS, DR_G, DR_TAU, DR_DELAY,
+ DR_WIND, DR_VWIND, DR_KDRAG, DR_GUST_P, DR_GUST_A, DR_GUST_T, DR_DRY_SIGMA, DR_DRY_V, DR_SIN_A, DR_SIN_W,
+ DR_DRY_H) = (0, 1, 4, 5, 6, 7, 8, 9, 10, 11, 12, 16, 17, 18, 19, 20, 23, 24, 25, 26, 27, 28, 29, 30, 31)
+WIND_CONSTANT, WIND_GUST, WIND_DRYDEN, WIND_SINUSOIDAL = 1, 2, 4, 8
+STREAM_WIND = 21
+
+
+class _DR(ctypes.Structure):
+    _fields_ = [("env_dr", ctypes.POINTER(ctypes.c_double)), ("motor", ctypes.POINTER(ctypes.c_double)),
+                ("hist", ctypes.POINTER(ctypes.c_double)), ("depth", ctypes.c_int32),
+                ("wind", ctypes.POINTER(ctypes.c_double)), ("seed", ctypes.c_uint64)]
+
+
+class Randomization:
+    """Domain-randomization and wind inputs and state of orc_control_steps: env_dr
+    [n_envs, DR_PARAMS] (neutral: factors 1, no lag, no delay, no wind), motor [n, 4] and
+    hist [depth, n, 4] (NaN: not set), wind [n_envs, WIND_STATE] (Dryden 0, gust idle,
+    step 0); all float64, updated in place by control_steps."""
+
+    def __init__(self, n_envs: int, n: int, depth: int = 1, seed: int = 0):
+        self.env_dr = neutral_dr(n_envs)
+        self.motor = np.full((n, 4), np.nan)
+        self.hist = np.full((depth, n, 4), np.nan)
+        self.wind = np.zeros((n_envs, WIND_STATE))
+        self.wind[:, 3] = -1.0
+        self.seed = int(seed)
+
+    def struct(self) -> _DR:
+        for a in (self.env_dr, self.motor, self.hist, self.wind):
+            assert a.dtype == np.float64 and a.flags.c_contiguous
+        return _DR(_dptr(self.env_dr), _dptr(self.motor), _dptr(self.hist), self.hist.shape[0], _dptr(self.wind),
+                   ctypes.c_uint64(self.seed))
+
+
+def neutral_dr(n_envs: int) -> np.ndarray:
+    """[n_envs, DR_PARAMS] rows that change nothing: every factor 1, no lag, no delay, no wind."""
+    r = np.zeros((n_envs, DR_PARAMS))
+    r[:, [DR_MASS, DR_J, DR_J + 1, DR_J + 2, DR_ARM, DR_KF, DR_KM, DR_CXY, DR_CZ, DR_CGND, DR_C1, DR_MAXRPM,
+          DR_BIAS, DR_BIAS + 1, DR_BIAS + 2, DR_BIAS + 3, DR_G]] = 1.0
+    r[:, DR_GUST_T] = 1.0
+    r[:, DR_DRY_H] = 1.0
+    return r
 
 _lock = threading.Lock()
 _lib = None
@@ -88,8 +131,8 @@ def lib():
                 "orc_params_cf2x": ([P], None),
                 "orc_params_cf2p": ([P], None),
                 "orc_params_race": ([P], None),
-                "orc_env_deriv": ([P, ctypes.c_int, _D, _D, ctypes.c_int, _D], None),
-                "orc_substep_rk4": ([P, ctypes.c_int, _D, _D, ctypes.c_int, ctypes.c_double, _D], None),
+                "orc_env_deriv": ([P, ctypes.c_int, _D, _D, ctypes.c_int, _D, _D], None),
+                "orc_substep_rk4": ([P, ctypes.c_int, _D, _D, ctypes.c_int, _D, ctypes.c_double, _D], None),
                 "orc_hover_rpm": ([P], ctypes.c_double),
                 "orc_max_rpm": ([P], ctypes.c_double),
                 "orc_quat_mul": ([_D, _D, _D], None),
@@ -97,8 +140,8 @@ def lib():
                 "orc_rpy": ([_D, _D], None),
                 "orc_motor": ([P, _D, _D, _D], None),
                 "orc_rotor_position": ([P, ctypes.c_int, _D], None),
-                "orc_env_forces": ([P, ctypes.c_int, _D, _D, ctypes.c_int, _D, _D], None),
-                "orc_substep": ([P, ctypes.c_int, _D, _D, ctypes.c_int, ctypes.c_double, _D], None),
+                "orc_env_forces": ([P, ctypes.c_int, _D, _D, ctypes.c_int, _D, _D, _D], None),
+                "orc_substep": ([P, ctypes.c_int, _D, _D, ctypes.c_int, _D, ctypes.c_double, _D], None),
                 "orc_allocation_matrix": ([P, _D], None),
                 "orc_pid": ([P, _D, _D, _D, _D, _D, _D], None),
                 "orc_pid_ff": ([P, _D, _D, _D, _D, _D, _D, _D, _D], None),
@@ -109,7 +152,10 @@ def lib():
                 "orc_kin": ([_D, _D, _D], None),
                 "orc_knn": ([ctypes.c_int, _D, ctypes.c_int, ctypes.c_int, _I, _D], None),
                 "orc_control_steps": ([P, ctypes.c_int, _I, _I, _I, _D, _D, _D, _D, ctypes.c_int, ctypes.c_int,
-                                       _D, _I, _D, _D], ctypes.c_int),
+                                       _D, _I, _D, _D, ctypes.POINTER(_DR)], ctypes.c_int),
+                "orc_uniform": ([ctypes.c_uint64] * 5, ctypes.c_double),
+                "orc_params_randomized": ([P, _D, P], None),
+                "orc_wind_step": ([P, _D, _D, ctypes.c_uint64, ctypes.c_int64, _D, _D], None),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -200,39 +246,54 @@ def rotor_position(p: Params, i: int) -> np.ndarray:
     return r
 
 
-def env_forces(p: Params, x, rpm, flags: int):
-    """World force (gravity included) [N,3] and body torque [N,3] for one env."""
+def _ext(f_ext, n):
+    if f_ext is None:
+        return None
+    f = _f64(f_ext)
+    assert f.shape == (n, 3)
+    return f
+
+
+def env_forces(p: Params, x, rpm, flags: int, f_ext=None):
+    """World force (gravity included) [N,3] and body torque [N,3] for one env (plus an
+    external world-frame force f_ext [N,3])."""
     x, rpm = _f64(x), _f64(rpm)
     N = x.shape[0]
     F = np.zeros((N, 3))
     tau = np.zeros((N, 3))
-    lib().orc_env_forces(ctypes.byref(p), N, _dptr(x), _dptr(rpm), int(flags), _dptr(F), _dptr(tau))
+    fe = _ext(f_ext, N)
+    lib().orc_env_forces(ctypes.byref(p), N, _dptr(x), _dptr(rpm), int(flags),
+                         _dptr(fe) if fe is not None else None, _dptr(F), _dptr(tau))
     return F, tau
 
 
-def substep(p: Params, x, rpm, flags: int, dt: float | None = None) -> np.ndarray:
+def substep(p: Params, x, rpm, flags: int, dt: float | None = None, f_ext=None) -> np.ndarray:
     """One substep of one environment: x [N,13], rpm [N,4] -> x' [N,13]."""
     x, rpm = _f64(x), _f64(rpm)
     out = np.zeros_like(x)
+    fe = _ext(f_ext, x.shape[0])
     lib().orc_substep(ctypes.byref(p), x.shape[0], _dptr(x), _dptr(rpm), int(flags),
-                      p.dt_sim if dt is None else float(dt), _dptr(out))
+                      _dptr(fe) if fe is not None else None, p.dt_sim if dt is None else float(dt), _dptr(out))
     return out
 
 
-def env_deriv(p: Params, x, rpm, flags: int) -> np.ndarray:
+def env_deriv(p: Params, x, rpm, flags: int, f_ext=None) -> np.ndarray:
     """Time derivative of one environment's state: x [N,13], rpm [N,4] -> dx/dt [N,13]."""
     x, rpm = _f64(x), _f64(rpm)
     out = np.zeros_like(x)
-    lib().orc_env_deriv(ctypes.byref(p), x.shape[0], _dptr(x), _dptr(rpm), int(flags), _dptr(out))
+    fe = _ext(f_ext, x.shape[0])
+    lib().orc_env_deriv(ctypes.byref(p), x.shape[0], _dptr(x), _dptr(rpm), int(flags),
+                        _dptr(fe) if fe is not None else None, _dptr(out))
     return out
 
 
-def substep_rk4(p: Params, x, rpm, flags: int, dt: float | None = None) -> np.ndarray:
+def substep_rk4(p: Params, x, rpm, flags: int, dt: float | None = None, f_ext=None) -> np.ndarray:
     """One classical RK4 substep of one environment: x [N,13], rpm [N,4] -> x' [N,13]."""
     x, rpm = _f64(x), _f64(rpm)
     out = np.zeros_like(x)
+    fe = _ext(f_ext, x.shape[0])
     lib().orc_substep_rk4(ctypes.byref(p), x.shape[0], _dptr(x), _dptr(rpm), int(flags),
-                          p.dt_sim if dt is None else float(dt), _dptr(out))
+                          _dptr(fe) if fe is not None else None, p.dt_sim if dt is None else float(dt), _dptr(out))
     return out
 
 
@@ -316,8 +377,30 @@ def knn(x_env, j: int, idx_base: int = 0):
     return idx, rel
 
 
+def uniform(seed: int, stream: int, step: int, index: int, comp: int) -> float:
+    """The oracle's counter-based U[0, 1) (SplitMix64 rounds over the five counters)."""
+    return lib().orc_uniform(seed, stream, step, index, comp)
+
+
+def params_randomized(p: Params, row) -> Params:
+    q = Params()
+    r = _f64(row)
+    lib().orc_params_randomized(ctypes.byref(p), _dptr(r), ctypes.byref(q))
+    return q
+
+
+def wind_step(p: Params, row, ws, seed: int, env: int):
+    """One control step of an environment's wind: returns (F_dir [3], v_wind [3]); ws
+    (float64 [WIND_STATE]) is updated in place."""
+    r = _f64(row)
+    assert ws.dtype == np.float64 and ws.flags.c_contiguous
+    F, v = np.zeros(3), np.zeros(3)
+    lib().orc_wind_step(ctypes.byref(p), _dptr(r), _dptr(ws), seed, env, _dptr(F), _dptr(v))
+    return F, v
+
+
 def control_steps(p: Params, env_off, env_flags, env_act, x, integ, a_prev, actions, n_sub: int,
-                  obs: bool = False, setpoint=None):
+                  obs: bool = False, setpoint=None, dr: "Randomization | None" = None):
     """K control steps over a CSR batch. x [n,13], integ [n,6], a_prev [n,4] and actions [K,n,4]
     (float64). Returns (x, integ, a_prev) updated copies, plus (kin, nbr_idx, nbr_rel) when obs.
     setpoint: float64 C-contiguous [n,4] DSL setpoints, updated in place (required with the
@@ -343,7 +426,8 @@ def control_steps(p: Params, env_off, env_flags, env_act, x, integ, a_prev, acti
     rc = lib().orc_control_steps(ctypes.byref(p), n_envs, _iptr(env_off), _iptr(env_flags), _iptr(env_act),
                                  _dptr(x), _dptr(integ), _dptr(a_prev), _dptr(actions), K, int(n_sub),
                                  _dptr(kin_o) if obs else None, _iptr(nbr_i) if obs else None,
-                                 _dptr(nbr_r) if obs else None, _dptr(setpoint) if setpoint is not None else None)
+                                 _dptr(nbr_r) if obs else None, _dptr(setpoint) if setpoint is not None else None,
+                                 ctypes.byref(dr.struct()) if dr is not None else None)
     if rc != 0:
         raise ValueError("orc_control_steps rejected its arguments")
     if obs:

@@ -61,6 +61,43 @@
 #define ORC_CTRL_PID 0
 #define ORC_CTRL_DSL 1
 
+/* Domain randomization (Section 3.5, Table "Recommended domain-randomization ranges")
+ * and wind (Section 3.5, "Wind and turbulence"): one row of ORC_DR_PARAMS values per
+ * environment. Multiplicative factors scale the model the physics integrates; the
+ * controller keeps the nominal model (it does not know the draw). */
+#define ORC_DR_PARAMS 32
+#define ORC_DR_MASS 0      /* x m */
+#define ORC_DR_J 1         /* x Jxx, Jyy, Jzz (1..3) */
+#define ORC_DR_ARM 4       /* x L */
+#define ORC_DR_KF 5        /* x k_f */
+#define ORC_DR_KM 6        /* x k_m */
+#define ORC_DR_CXY 7       /* x c_xy */
+#define ORC_DR_CZ 8        /* x c_z */
+#define ORC_DR_CGND 9      /* x C_gnd */
+#define ORC_DR_C1 10       /* x downwash C1 */
+#define ORC_DR_MAXRPM 11   /* x MAX_RPM (the motors' saturation) */
+#define ORC_DR_BIAS 12     /* per-motor speed bias (12..15) */
+#define ORC_DR_G 16        /* x g */
+#define ORC_DR_TAU 17      /* motor lag time constant [s], 0 = none */
+#define ORC_DR_DELAY 18    /* action latency [control steps], a whole number */
+#define ORC_DR_WIND 19     /* wind model bits: CONSTANT 1, GUST 2, DRYDEN 4, SINUSOIDAL 8 */
+#define ORC_DR_VWIND 20    /* steady wind velocity [m/s], world frame (20..22) */
+#define ORC_DR_KDRAG 23    /* 1/2 rho C_d A [kg/m] of the quadratic wind drag */
+#define ORC_DR_GUST_P 24   /* gust trigger probability per control step */
+#define ORC_DR_GUST_A 25   /* gust amplitude [N] */
+#define ORC_DR_GUST_T 26   /* gust duration [s] */
+#define ORC_DR_DRY_SIGMA 27 /* Dryden turbulence intensity [m/s] */
+#define ORC_DR_DRY_V 28    /* Dryden airspeed V [m/s] */
+#define ORC_DR_SIN_A 29    /* sinusoidal amplitude A [N] */
+#define ORC_DR_SIN_W 30    /* sinusoidal angular frequency [rad/s] */
+#define ORC_DR_DRY_H 31    /* Dryden reference altitude h [m] */
+#define ORC_WIND_CONSTANT 1
+#define ORC_WIND_GUST 2
+#define ORC_WIND_DRYDEN 4
+#define ORC_WIND_SINUSOIDAL 8
+#define ORC_WIND_STATE 8   /* per environment: Dryden x (3), gust phase s (-1 idle), gust direction (3), steps */
+#define ORC_STREAM_WIND 21 /* random stream of the wind draws */
+
 /* Model parameters. Field order is the oracle's own; the Python side of the
  * oracle mirrors it. */
 typedef struct {
@@ -301,7 +338,7 @@ void orc_rotor_position(const orc_params* P, int i, double r[3])
  * one environment of N drones. x is [N][13] = p(3) q(4) v(3) omega(3), omega in
  * the body frame; rpm is [N][4]. All drones read the same state snapshot x. */
 void orc_env_forces(const orc_params* P, int N, const double* x, const double* rpm, int flags,
-                    double* F, double* tau)
+                    const double* f_ext, double* F, double* tau)
 {
     for (int j = 0; j < N; ++j) {
         const double* xj = x + 13 * j;
@@ -369,6 +406,10 @@ void orc_env_forces(const orc_params* P, int N, const double* x, const double* r
                 fw[2] -= alpha * exp(-0.5 * dxy * dxy / b2);
             }
         }
+        if (f_ext) {
+            /* an external world-frame force on the drone (wind; domain randomization) */
+            for (int r = 0; r < 3; ++r) fw[r] += f_ext[3 * j + r];
+        }
         F[3 * j + 0] = fw[0];
         F[3 * j + 1] = fw[1];
         F[3 * j + 2] = fw[2];
@@ -392,11 +433,11 @@ static void orc_angular_accel(const double J[3], const double tau[3], const doub
  * norm-preserving reading of the printed map with Lambda the half quaternion-product
  * matrix; a body-frame rate multiplies on the right), then q+ is renormalised. */
 void orc_substep(const orc_params* P, int N, const double* x_in, const double* rpm, int flags,
-                 double dt, double* x_out)
+                 const double* f_ext, double dt, double* x_out)
 {
     double* F = (double*)malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
     double* tau = (double*)malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
-    orc_env_forces(P, N, x_in, rpm, flags, F, tau);
+    orc_env_forces(P, N, x_in, rpm, flags, f_ext, F, tau);
     const double J[3] = {P->Jxx, P->Jyy, P->Jzz};
     for (int j = 0; j < N; ++j) {
         const double* s = x_in + 13 * j;
@@ -437,7 +478,8 @@ void orc_substep(const orc_params* P, int N, const double* x_in, const double* r
  * omega' = J^-1 (tau - omega x (J omega)), the forces of orc_env_forces evaluated at x
  * with the quaternions taken at unit length (the stage states of a Runge-Kutta step
  * leave the unit sphere by O(dt^2)). dx is [N][13]. */
-void orc_env_deriv(const orc_params* P, int N, const double* x, const double* rpm, int flags, double* dx)
+void orc_env_deriv(const orc_params* P, int N, const double* x, const double* rpm, int flags, const double* f_ext,
+                   double* dx)
 {
     double* xu = (double*)malloc(sizeof(double) * 13 * (size_t)(N > 0 ? N : 1));
     double* F = (double*)malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
@@ -448,7 +490,7 @@ void orc_env_deriv(const orc_params* P, int N, const double* x, const double* rp
         const double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
         for (int r = 0; r < 4; ++r) q[r] /= qn;
     }
-    orc_env_forces(P, N, xu, rpm, flags, F, tau);
+    orc_env_forces(P, N, xu, rpm, flags, f_ext, F, tau);
     const double J[3] = {P->Jxx, P->Jyy, P->Jzz};
     for (int j = 0; j < N; ++j) {
         const double* s = x + 13 * j;
@@ -474,8 +516,8 @@ void orc_env_deriv(const orc_params* P, int N, const double* x, const double* rp
  * evaluates every force at that stage's states), k1 = f(x), k2 = f(x + dt/2 k1),
  * k3 = f(x + dt/2 k2), k4 = f(x + dt k3), x+ = x + dt/6 (k1 + 2 k2 + 2 k3 + k4), the
  * quaternion advanced like the other components and renormalised at the end. */
-void orc_substep_rk4(const orc_params* P, int N, const double* x_in, const double* rpm, int flags, double dt,
-                     double* x_out)
+void orc_substep_rk4(const orc_params* P, int N, const double* x_in, const double* rpm, int flags,
+                     const double* f_ext, double dt, double* x_out)
 {
     const size_t n13 = 13 * (size_t)(N > 0 ? N : 1);
     double* k1 = (double*)malloc(sizeof(double) * n13);
@@ -484,13 +526,13 @@ void orc_substep_rk4(const orc_params* P, int N, const double* x_in, const doubl
     double* k4 = (double*)malloc(sizeof(double) * n13);
     double* xs = (double*)malloc(sizeof(double) * n13);
     const size_t m = 13 * (size_t)N;
-    orc_env_deriv(P, N, x_in, rpm, flags, k1);
+    orc_env_deriv(P, N, x_in, rpm, flags, f_ext, k1);
     for (size_t i = 0; i < m; ++i) xs[i] = x_in[i] + 0.5 * dt * k1[i];
-    orc_env_deriv(P, N, xs, rpm, flags, k2);
+    orc_env_deriv(P, N, xs, rpm, flags, f_ext, k2);
     for (size_t i = 0; i < m; ++i) xs[i] = x_in[i] + 0.5 * dt * k2[i];
-    orc_env_deriv(P, N, xs, rpm, flags, k3);
+    orc_env_deriv(P, N, xs, rpm, flags, f_ext, k3);
     for (size_t i = 0; i < m; ++i) xs[i] = x_in[i] + dt * k3[i];
-    orc_env_deriv(P, N, xs, rpm, flags, k4);
+    orc_env_deriv(P, N, xs, rpm, flags, f_ext, k4);
     for (size_t i = 0; i < m; ++i) x_out[i] = x_in[i] + dt / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
     for (int j = 0; j < N; ++j) {
         double* q = x_out + 13 * j + 3;
@@ -829,6 +871,118 @@ void orc_knn(int N, const double* x, int j, int idx_base, int32_t idx[4], double
 
 /* ---- batched driver: K control steps over a CSR batch of environments ---- */
 
+/* ---- domain randomization and wind ---- */
+
+/* SplitMix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number generators",
+ * OOPSLA 2014): the output function of its counter-based form. */
+static uint64_t orc_splitmix64(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* U[0, 1) with 24 random bits (exact in float and double) for the counters (seed, stream,
+ * step, index, comp): each field is mixed in by one SplitMix64 round. */
+double orc_uniform(uint64_t seed, uint64_t stream, uint64_t step, uint64_t index, uint64_t comp)
+{
+    uint64_t h = orc_splitmix64(seed);
+    h = orc_splitmix64(h ^ stream);
+    h = orc_splitmix64(h ^ step);
+    h = orc_splitmix64(h ^ index);
+    h = orc_splitmix64(h ^ comp);
+    return (double)(h >> 40) * (1.0 / 16777216.0);
+}
+
+/* The physics model of one environment under its domain-randomization row: the factors
+ * scale mass, inertia, arm, k_f, k_m, c_xy, c_z, C_gnd, C1 and g (h_clip, a numerical
+ * guard, stays nominal). */
+void orc_params_randomized(const orc_params* P, const double* dr, orc_params* Pe)
+{
+    *Pe = *P;
+    Pe->mass *= dr[ORC_DR_MASS];
+    Pe->Jxx *= dr[ORC_DR_J + 0];
+    Pe->Jyy *= dr[ORC_DR_J + 1];
+    Pe->Jzz *= dr[ORC_DR_J + 2];
+    Pe->arm *= dr[ORC_DR_ARM];
+    Pe->kf *= dr[ORC_DR_KF];
+    Pe->km *= dr[ORC_DR_KM];
+    Pe->c_xy *= dr[ORC_DR_CXY];
+    Pe->c_z *= dr[ORC_DR_CZ];
+    Pe->c_gnd *= dr[ORC_DR_CGND];
+    Pe->dw_c1 *= dr[ORC_DR_C1];
+    Pe->g *= dr[ORC_DR_G];
+}
+
+/* One control step of an environment's WindField (Section 3.5): advances the wind state
+ * ws[ORC_WIND_STATE] of environment `env` and returns the direct force F_dir [N] (gusts,
+ * sinusoid) and the wind velocity v_w [m/s] the quadratic drag sees (steady wind plus
+ * Dryden turbulence). Readings where the paper gives the models only in outline:
+ *  CONSTANT   v_w += the steady wind; drag on drone j: k |v_rel| v_rel, v_rel = v_w - v_j
+ *             (= 1/2 rho C_d A |v_rel|^2 v_rel_hat), also with DRYDEN alone;
+ *  DRYDEN     per component x <- alpha x + sigma sqrt(1 - alpha^2) xi, xi ~ N(0, 1) (Box-Muller
+ *             on the counter-based uniforms), alpha = exp(-dt_ctrl V / L),
+ *             L = h / (0.177 + 8.23e-4 h)^1.2 with the environment's reference altitude h,
+ *             the same L for all three components; v_w += x;
+ *  GUST       an idle field starts a gust with the given probability per control step, in a
+ *             direction uniform on the sphere; the gust force is A sin(pi s) d for its phase
+ *             s = 0, dt_ctrl/T, ... while s <= 1;
+ *  SINUSOIDAL F += A [sin wt, cos wt, 0.3 sin 2wt], t = steps dt_ctrl;
+ *  COMBINED   every bit set. */
+void orc_wind_step(const orc_params* P, const double* dr, double* ws, uint64_t seed, int64_t env, double F_dir[3],
+                   double v_w[3])
+{
+    const int model = (int)dr[ORC_DR_WIND];
+    const double dt = P->dt_ctrl;
+    const uint64_t step = (uint64_t)ws[7];
+    for (int r = 0; r < 3; ++r) F_dir[r] = v_w[r] = 0.0;
+    if (model & ORC_WIND_CONSTANT)
+        for (int r = 0; r < 3; ++r) v_w[r] += dr[ORC_DR_VWIND + r];
+    if (model & ORC_WIND_DRYDEN) {
+        const double h = dr[ORC_DR_DRY_H];
+        const double L = h / pow(0.177 + 8.23e-4 * h, 1.2);
+        const double alpha = exp(-dt * dr[ORC_DR_DRY_V] / L);
+        const double u1 = 1.0 - orc_uniform(seed, ORC_STREAM_WIND, step, (uint64_t)env, 0);
+        const double u2 = orc_uniform(seed, ORC_STREAM_WIND, step, (uint64_t)env, 1);
+        const double u3 = 1.0 - orc_uniform(seed, ORC_STREAM_WIND, step, (uint64_t)env, 2);
+        const double u4 = orc_uniform(seed, ORC_STREAM_WIND, step, (uint64_t)env, 3);
+        const double r1 = sqrt(-2.0 * log(u1)), r2 = sqrt(-2.0 * log(u3));
+        const double xi[3] = {r1 * cos(2.0 * ORC_PI * u2), r1 * sin(2.0 * ORC_PI * u2), r2 * cos(2.0 * ORC_PI * u4)};
+        for (int r = 0; r < 3; ++r) {
+            ws[r] = alpha * ws[r] + dr[ORC_DR_DRY_SIGMA] * sqrt(1.0 - alpha * alpha) * xi[r];
+            v_w[r] += ws[r];
+        }
+    }
+    if (model & ORC_WIND_GUST) {
+        if (ws[3] < 0.0) {
+            const double u = orc_uniform(seed, ORC_STREAM_WIND, step, (uint64_t)env, 4);
+            if ((float)u < (float)dr[ORC_DR_GUST_P]) {
+                const double z = 2.0 * orc_uniform(seed, ORC_STREAM_WIND, step, (uint64_t)env, 5) - 1.0;
+                const double ph = 2.0 * ORC_PI * orc_uniform(seed, ORC_STREAM_WIND, step, (uint64_t)env, 6);
+                const double rho = sqrt(1.0 - z * z);
+                ws[3] = 0.0;
+                ws[4] = rho * cos(ph);
+                ws[5] = rho * sin(ph);
+                ws[6] = z;
+            }
+        }
+        if (ws[3] >= 0.0) {
+            const double a = dr[ORC_DR_GUST_A] * sin(ORC_PI * ws[3]);
+            for (int r = 0; r < 3; ++r) F_dir[r] += a * ws[4 + r];
+            ws[3] += dt / dr[ORC_DR_GUST_T];
+            if (ws[3] > 1.0) ws[3] = -1.0;
+        }
+    }
+    if (model & ORC_WIND_SINUSOIDAL) {
+        const double t = (double)step * dt, w = dr[ORC_DR_SIN_W], A = dr[ORC_DR_SIN_A];
+        F_dir[0] += A * sin(w * t);
+        F_dir[1] += A * cos(w * t);
+        F_dir[2] += A * 0.3 * sin(2.0 * w * t);
+    }
+    ws[7] = (double)(step + 1);
+}
+
 /* Runs K control steps (Section 3.4.2: sim_freq/ctrl_freq substeps per step) for
  * n_envs environments laid out in CSR order (drones of env e are
  * env_off[e] .. env_off[e+1]-1). Per control step and environment: the action of
@@ -842,13 +996,37 @@ void orc_knn(int N, const double* x, int j, int idx_base, int32_t idx[4], double
  *   kin      [n][20], nbr_idx [n][4], nbr_rel [n][24] (optional)
  *   setpoint [n][4]    DSL setpoints, updated in place (required with the DSL
  *                      controller, else ignored; may be NULL)
+ *   dr                 domain randomization and wind (NULL: none):
+ *     env_dr [n_envs][ORC_DR_PARAMS]; motor [n][4] rotor speeds (the lag's state, NaN =
+ *     not set: starts at the first command); hist [depth][n][4] actions received (the
+ *     latency's shift register, NaN = empty: filled with the first action); wind
+ *     [n_envs][ORC_WIND_STATE]; seed of the wind draws.
+ *   Per control step and drone, with dr: the action received enters the shift register
+ *   and the one received `delay` steps ago is applied; it becomes RPMs through the
+ *   nominal controller (recorded in a_prev); each motor's command is its RPM times its
+ *   bias, saturated at MAX_RPM times the factor; the wind force (orc_wind_step, drag from
+ *   the drone's velocity at the step's start) is held over the substeps; before each
+ *   substep every rotor speed relaxes towards its command, n <- c + (n - c) exp(-dt/tau)
+ *   (exact for a first-order lag under a constant command; tau = 0: n = c), and the
+ *   substep integrates the environment's randomized model with these speeds.
  * Returns 0, or -1 on a bad argument. */
+typedef struct {
+    const double* env_dr;
+    double* motor;
+    double* hist;
+    int32_t depth;
+    double* wind;
+    uint64_t seed;
+} orc_dr;
+
 int orc_control_steps(const orc_params* P, int n_envs, const int32_t* env_off, const int32_t* env_flags,
                       const int32_t* env_act, double* x, double* integ, double* a_prev, const double* actions,
-                      int K, int n_sub, double* kin, int32_t* nbr_idx, double* nbr_rel, double* setpoint)
+                      int K, int n_sub, double* kin, int32_t* nbr_idx, double* nbr_rel, double* setpoint,
+                      const orc_dr* dr)
 {
     if (n_envs < 0 || K < 0 || n_sub < 1) return -1;
     if (P->controller == ORC_CTRL_DSL && !setpoint) return -1;
+    if (dr && (!dr->env_dr || !dr->motor || !dr->hist || dr->depth < 1 || !dr->wind)) return -1;
     int maxN = 0;
     for (int e = 0; e < n_envs; ++e) {
         int N = env_off[e + 1] - env_off[e];
@@ -856,23 +1034,89 @@ int orc_control_steps(const orc_params* P, int n_envs, const int32_t* env_off, c
         if (N > maxN) maxN = N;
     }
     const int64_t n = n_envs > 0 ? env_off[n_envs] : 0;
-    double* rpm = (double*)malloc(sizeof(double) * 4 * (size_t)(maxN > 0 ? maxN : 1));
-    double* tmp = (double*)malloc(sizeof(double) * 13 * (size_t)(maxN > 0 ? maxN : 1));
+    if (dr) {
+        for (int e = 0; e < n_envs; ++e) {
+            const double d = dr->env_dr[(size_t)e * ORC_DR_PARAMS + ORC_DR_DELAY];
+            if (!(d >= 0.0) || d != floor(d) || d >= dr->depth) return -1;
+        }
+    }
+    const size_t nb = (size_t)(maxN > 0 ? maxN : 1);
+    double* rpm = (double*)malloc(sizeof(double) * 4 * nb);
+    double* cmd = (double*)malloc(sizeof(double) * 4 * nb);
+    double* fext = (double*)malloc(sizeof(double) * 3 * nb);
+    double* tmp = (double*)malloc(sizeof(double) * 13 * nb);
+    const double maxrpm = orc_max_rpm(P);
     for (int k = 0; k < K; ++k) {
         const double* act = actions + (size_t)k * (size_t)n * 4;
         for (int e = 0; e < n_envs; ++e) {
             const int b = env_off[e], N = env_off[e + 1] - env_off[e];
-            for (int j = 0; j < N; ++j) {
-                const double* a = act + 4 * (size_t)(b + j);
-                orc_action_to_rpm(P, env_act[e], x + 13 * (size_t)(b + j), integ + 6 * (size_t)(b + j),
-                                  setpoint ? setpoint + 4 * (size_t)(b + j) : NULL, a, rpm + 4 * j);
-                for (int i = 0; i < 4; ++i) a_prev[4 * (size_t)(b + j) + i] = rpm[4 * j + i];
+            const double* row = dr ? dr->env_dr + (size_t)e * ORC_DR_PARAMS : NULL;
+            orc_params Pe = *P;
+            double F_dir[3] = {0.0, 0.0, 0.0}, v_w[3] = {0.0, 0.0, 0.0};
+            if (row) {
+                orc_params_randomized(P, row, &Pe);
+                orc_wind_step(P, row, dr->wind + (size_t)e * ORC_WIND_STATE, dr->seed, e, F_dir, v_w);
             }
+            const int drag_wind = row && ((int)row[ORC_DR_WIND] & (ORC_WIND_CONSTANT | ORC_WIND_DRYDEN));
+            for (int j = 0; j < N; ++j) {
+                const size_t g = (size_t)(b + j);
+                const double* a = act + 4 * g;
+                if (row) {
+                    /* action latency: shift register of the actions received */
+                    double* h0 = dr->hist + 4 * g;
+                    const size_t hs = 4 * (size_t)n;
+                    if (isnan(h0[0])) {
+                        for (int d = 0; d < dr->depth; ++d)
+                            for (int i = 0; i < 4; ++i) h0[d * hs + i] = a[i];
+                    } else {
+                        for (int d = dr->depth - 1; d > 0; --d)
+                            for (int i = 0; i < 4; ++i) h0[d * hs + i] = h0[(d - 1) * hs + i];
+                        for (int i = 0; i < 4; ++i) h0[i] = a[i];
+                    }
+                    a = h0 + (size_t)row[ORC_DR_DELAY] * hs;
+                }
+                orc_action_to_rpm(P, env_act[e], x + 13 * g, integ + 6 * g, setpoint ? setpoint + 4 * g : NULL, a,
+                                  rpm + 4 * j);
+                for (int i = 0; i < 4; ++i) a_prev[4 * g + i] = rpm[4 * j + i];
+                for (int i = 0; i < 4; ++i) {
+                    double c = rpm[4 * j + i];
+                    if (row) {
+                        c *= row[ORC_DR_BIAS + i];
+                        const double sat = maxrpm * row[ORC_DR_MAXRPM];
+                        if (c > sat) c = sat;
+                        if (isnan(dr->motor[4 * g + i])) dr->motor[4 * g + i] = c;
+                    }
+                    cmd[4 * j + i] = c;
+                }
+                for (int r = 0; r < 3; ++r) {
+                    double f = F_dir[r];
+                    if (drag_wind) {
+                        const double* v = x + 13 * g + 7;
+                        const double vr[3] = {v_w[0] - v[0], v_w[1] - v[1], v_w[2] - v[2]};
+                        const double m = sqrt(vr[0] * vr[0] + vr[1] * vr[1] + vr[2] * vr[2]);
+                        f += row[ORC_DR_KDRAG] * m * vr[r];
+                    }
+                    fext[3 * j + r] = f;
+                }
+            }
+            const double lag = row && row[ORC_DR_TAU] > 0.0 ? exp(-P->dt_sim / row[ORC_DR_TAU]) : 0.0;
             for (int s = 0; s < n_sub; ++s) {
+                const double* speeds = cmd;
+                if (row) {
+                    for (int j = 0; j < N; ++j)
+                        for (int i = 0; i < 4; ++i) {
+                            double* m = dr->motor + 4 * (size_t)(b + j) + i;
+                            const double c = cmd[4 * j + i];
+                            *m = c + (*m - c) * lag;
+                            rpm[4 * j + i] = *m;
+                        }
+                    speeds = rpm;
+                }
                 if (P->integrator == ORC_RK4)
-                    orc_substep_rk4(P, N, x + 13 * (size_t)b, rpm, env_flags[e], P->dt_sim, tmp);
+                    orc_substep_rk4(&Pe, N, x + 13 * (size_t)b, speeds, env_flags[e], row ? fext : NULL, P->dt_sim,
+                                    tmp);
                 else
-                    orc_substep(P, N, x + 13 * (size_t)b, rpm, env_flags[e], P->dt_sim, tmp);
+                    orc_substep(&Pe, N, x + 13 * (size_t)b, speeds, env_flags[e], row ? fext : NULL, P->dt_sim, tmp);
                 memcpy(x + 13 * (size_t)b, tmp, sizeof(double) * 13 * (size_t)N);
             }
         }
@@ -889,6 +1133,8 @@ int orc_control_steps(const orc_params* P, int n_envs, const int32_t* env_off, c
         }
     }
     free(rpm);
+    free(cmd);
+    free(fext);
     free(tmp);
     return 0;
 }

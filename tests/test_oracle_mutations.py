@@ -1,6 +1,6 @@
 """The oracle pins have teeth: plant plausible mistakes in a copy of the oracle and
 check that the pin suite (test_oracle_dynamics.py, test_oracle_models.py,
-test_oracle_actions.py) fails on each.
+test_oracle_actions.py, test_oracle_randomization.py) fails on each.
 
 Mistakes are planted only in a temporary copy of the oracle, on the CPU; the real
 oracle is not modified. CPU only.
@@ -74,6 +74,16 @@ MUTATIONS = {
     "dsl_yaw_limit_sign": ("if (dy < -ly) dy = -ly;", "if (dy < -ly) dy = ly;"),
     "feed_forward_dropped": ("a[r] += a_ff[r];", "a[r] += 0.0 * a_ff[r];"),
     "dsl_setpoint_unused": ("        tgt = sp;\n", "        tgt = wp;\n"),
+    "dr_mass_dropped": ("    Pe->mass *= dr[ORC_DR_MASS];\n", "\n"),
+    "wind_drag_sign": ("const double vr[3] = {v_w[0] - v[0], v_w[1] - v[1], v_w[2] - v[2]};",
+                       "const double vr[3] = {v[0] - v_w[0], v[1] - v_w[1], v[2] - v_w[2]};"),
+    "lag_discretization": ("*m = c + (*m - c) * lag;", "*m = c + (*m - c) * (1.0 - lag);"),
+    "latency_newest": ("a = h0 + (size_t)row[ORC_DR_DELAY] * hs;", "a = h0;"),
+    "dryden_noise_scale": ("sqrt(1.0 - alpha * alpha) * xi[r]", "sqrt(1.0 - alpha) * xi[r]"),
+    "gust_envelope": ("sin(ORC_PI * ws[3])", "sin(2.0 * ORC_PI * ws[3])"),
+    "sinusoid_phase": ("F_dir[0] += A * sin(w * t);", "F_dir[0] += A * cos(w * t);"),
+    "motor_bias_dropped": ("c *= row[ORC_DR_BIAS + i];", "c *= 1.0;"),
+    "arm_factor_to_inertia": ("    Pe->arm *= dr[ORC_DR_ARM];\n", "    Pe->Jxx *= dr[ORC_DR_ARM];\n"),
 }
 
 
@@ -100,9 +110,13 @@ def test_planted_mistake_is_caught(name, oracle_source, tmp_path):
     shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle", ignore=shutil.ignore_patterns("_build"))
     shutil.copytree(os.path.join(ROOT, "tests"), tmp_path / "tests",
                     ignore=shutil.ignore_patterns("__pycache__", "test_oracle_mutations.py"))
+    # the pins read their inputs from the package's generators (Python only)
+    shutil.copytree(os.path.join(ROOT, "paper_2606_08039_gb300"), tmp_path / "paper_2606_08039_gb300",
+                    ignore=shutil.ignore_patterns("__pycache__", "csrc", "_build", "*.so"))
     (tmp_path / "oracle" / "mdg_oracle.c").write_text(oracle_source.replace(before, after))
     r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_dynamics.py", "tests/test_oracle_models.py",
-                        "tests/test_oracle_actions.py", "-q", "-x", "-p", "no:cacheprovider"], cwd=tmp_path,
+                        "tests/test_oracle_actions.py", "tests/test_oracle_randomization.py", "-q", "-x", "-p",
+                        "no:cacheprovider"], cwd=tmp_path,
                        capture_output=True, text=True, timeout=300)
     assert r.returncode == 1, f"planted mistake {name} was not caught:\n{r.stdout[-2000:]}"
 

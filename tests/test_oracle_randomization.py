@@ -1,0 +1,237 @@
+"""Pins of the oracle's domain randomization and wind (CPU).
+
+The factors, the actuator effects and the wind models are pinned by what they fix in
+special cases worked out by hand: neutral rows change nothing (bit for bit); at hover a
+mass, gravity or thrust factor gives the exact constant acceleration it implies; inertia
+and arm factors scale a single rotor's roll acceleration by their ratio; motor bias and
+saturation equal pre-scaled RPM actions; the motor lag follows its geometric closed form;
+latency replays the actions shifted by the delay; a steady wind pushes with
+k |v_rel| v_rel and the sinusoid with its closed form; the Dryden process has the stationary
+variance and lag-one correlation of its recursion and Gaussian innovations; gusts follow
+the sin(pi s) envelope and trigger at the set rate in directions uniform on the sphere; the
+counter-based uniforms equal those of the input generator (two implementations of the same
+published SplitMix64 rounds).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_08039_gb300 import workloads as wl
+
+P = oracle.cf2x()
+HOVER = oracle.hover_rpm(P)
+
+
+def _level(z=5.0, v=(0.0, 0.0, 0.0)):
+    return np.array([[0.0, 0.0, z, 1.0, 0.0, 0.0, 0.0, *v, 0.0, 0.0, 0.0]])
+
+
+def _run(x0, actions, dr=None, flags=0, act=oracle.ACT_RPM, P=P):
+    """One drone (or a batch of single-drone envs) over actions [K, n, 4]."""
+    n = x0.shape[0]
+    env_off = np.arange(n + 1, dtype=np.int32)
+    x, integ, a = oracle.control_steps(P, env_off, np.full(n, flags, np.int32), np.full(n, act, np.int32), x0,
+                                       np.zeros((n, 6)), np.zeros((n, 4)), np.asarray(actions, np.float64), 5, dr=dr)
+    return x, a
+
+
+def _dr(n=1, depth=1, seed=0, **set_):
+    r = oracle.Randomization(n, n, depth, seed)
+    for k, v in set_.items():
+        idx = getattr(oracle, "DR_" + k.upper())
+        r.env_dr[:, idx:idx + np.size(v)] = v
+    return r
+
+
+def test_neutral_rows_change_nothing():
+    sw = wl.uneven(3, n_envs=60)
+    x0 = np.concatenate([sw.p, sw.q, sw.v, sw.w], 1).astype(np.float64)
+    acts = np.stack([wl.mixed_actions(sw, 4, k, HOVER) for k in range(3)]).astype(np.float64)
+    env_off = np.concatenate([[0], np.cumsum(sw.drones_per_env)]).astype(np.int32)
+    args = (env_off, sw.flags.astype(np.int32), sw.act_type.astype(np.int32))
+    z6, z4 = np.zeros((sw.n, 6)), np.zeros((sw.n, 4))
+    xa, ia, aa = oracle.control_steps(P, *args, x0, z6, z4, acts, 5)
+    r = oracle.Randomization(sw.n_envs, sw.n, depth=3, seed=9)
+    xb, ib, ab = oracle.control_steps(P, *args, x0, z6, z4, acts, 5, dr=r)
+    np.testing.assert_array_equal(xa, xb)
+    np.testing.assert_array_equal(ia, ib)
+    np.testing.assert_array_equal(aa, ab)
+    np.testing.assert_array_equal(r.wind[:, 7], 3)  # the wind steps advance even when idle
+
+
+@pytest.mark.parametrize("factor, expected", [
+    ("mass", lambda f: P.g * (1.0 / f - 1.0)),   # hover thrust m g on f m
+    ("g", lambda f: -P.g * (f - 1.0)),
+    ("kf", lambda f: P.g * (f - 1.0))])
+def test_body_factors_at_hover(factor, expected):
+    f = 1.2 if factor != "g" else 1.02
+    x, _ = _run(_level(), np.full((1, 1, 4), HOVER), dr=_dr(**{factor: f}))
+    assert x[0, 9] == pytest.approx(expected(f) * P.dt_ctrl, rel=1e-12)
+    np.testing.assert_allclose(x[0, 7:9], 0.0, atol=1e-15)
+
+
+def test_inertia_and_arm_factors_scale_the_roll_acceleration():
+    rpm = np.array([[[12000.0, 0.0, 0.0, 0.0]]])
+    x1, _ = _run(_level(), rpm, dr=_dr())
+    x2, _ = _run(_level(), rpm, dr=_dr(j=[1.5, 1.0, 1.0], arm=1.02))
+    w1, w2 = x1[0, 10], x2[0, 10]
+    assert abs(w1) > 1.0
+    assert w2 / w1 == pytest.approx(1.02 / 1.5, rel=1e-5)  # gyroscopic coupling enters at O(w^2 dt)
+    # at rest (no gyroscopic term) the ratio of the instantaneous accelerations is exact
+    row = oracle.neutral_dr(1)[0]
+    row[oracle.DR_J], row[oracle.DR_ARM] = 1.5, 1.02
+    d1 = oracle.env_deriv(P, _level(), rpm[0], 0)
+    d2 = oracle.env_deriv(oracle.params_randomized(P, row), _level(), rpm[0], 0)
+    assert d2[0, 10] / d1[0, 10] == pytest.approx(1.02 / 1.5, rel=1e-14)
+    assert d2[0, 11] / d1[0, 11] == pytest.approx(1.02, rel=1e-14)  # pitch: arm only, Jyy unscaled
+
+
+def test_drag_factor_scales_the_drag_force():
+    x = _level(v=(1.5, 0.0, 0.0))[0]
+    rpm = np.full((1, 4), HOVER)
+    F0, _ = oracle.env_forces(P, x[None], rpm, oracle.DRAG)
+    Fn, _ = oracle.env_forces(P, x[None], rpm, 0)
+    row = oracle.neutral_dr(1)[0]
+    row[oracle.DR_CXY] = 1.3
+    F1, _ = oracle.env_forces(oracle.params_randomized(P, row), x[None], rpm, oracle.DRAG)
+    assert (F1 - Fn)[0, 0] == pytest.approx(1.3 * (F0 - Fn)[0, 0], rel=1e-12)
+    assert abs((F0 - Fn)[0, 0]) > 0
+
+
+def test_motor_bias_and_saturation():
+    bias = np.array([1.05, 1.0, 0.97, 1.02])
+    a = np.array([[[14000.0, 15000.0, 13500.0, 14500.0]]])
+    xa, _ = _run(_level(), a, dr=_dr(bias=bias), flags=oracle.DRAG)
+    xb, _ = _run(_level(), a * bias, flags=oracle.DRAG)
+    np.testing.assert_array_equal(xa, xb)
+    mx = oracle.max_rpm(P)
+    xa, aa = _run(_level(), np.full((1, 1, 4), mx), dr=_dr(maxrpm=0.95))
+    xb, _ = _run(_level(), np.full((1, 1, 4), 0.95 * mx))
+    np.testing.assert_array_equal(xa, xb)
+    np.testing.assert_allclose(aa, mx)  # a_prev records the action's RPMs
+
+
+def test_motor_lag_closed_form():
+    """Motors at hover speed commanded to 1.1 x hover with tau = 30 ms: before substep s the
+    speed is c + (n0 - c) e^(s+1), e = exp(-dt/tau); level and without effects the climb
+    rate after one control step is the sum of the substeps' accelerations times dt."""
+    tau, c, n0 = 0.03, 1.1 * HOVER, HOVER
+    r = _dr(tau=tau)
+    r.motor[:] = n0
+    x, _ = _run(_level(), np.full((1, 1, 4), c), dr=r)
+    e = np.exp(-P.dt_sim / tau)
+    n = c + (n0 - c) * e ** np.arange(1, 6)
+    vz = np.sum(P.dt_sim * (4 * P.kf * n ** 2 / P.mass - P.g))
+    assert x[0, 9] == pytest.approx(vz, rel=1e-12)
+    np.testing.assert_allclose(r.motor[0], n[-1], rtol=1e-14)
+
+
+def test_action_latency_replays_shifted_actions():
+    K = 5
+    acts = np.stack([np.full((1, 4), HOVER * (0.95 + 0.02 * k)) for k in range(K)])
+    xa, _ = _run(_level(), acts, dr=_dr(depth=3, delay=2), flags=oracle.GND | oracle.DRAG)
+    applied = acts[[0, 0, 0, 1, 2]]
+    xb, _ = _run(_level(), applied, flags=oracle.GND | oracle.DRAG)
+    np.testing.assert_array_equal(xa, xb)
+
+
+def test_steady_wind_drag():
+    k, vw = 0.01, np.array([2.0, -1.0, 0.0])
+    x, _ = _run(_level(), np.full((1, 1, 4), HOVER), dr=_dr(wind=oracle.WIND_CONSTANT, vwind=vw, kdrag=k))
+    F = k * np.linalg.norm(vw) * vw
+    np.testing.assert_allclose(x[0, 7:10], F / P.mass * P.dt_ctrl, rtol=1e-12, atol=1e-15)
+
+
+def test_sinusoidal_wind_closed_form():
+    A, w, K = 0.01, 2.0, 4
+    x, _ = _run(_level(), np.full((K, 1, 4), HOVER), dr=_dr(wind=oracle.WIND_SINUSOIDAL, sin_a=A, sin_w=w))
+    t = np.arange(K) * P.dt_ctrl
+    F = A * np.stack([np.sin(w * t), np.cos(w * t), 0.3 * np.sin(2 * w * t)], axis=1)
+    np.testing.assert_allclose(x[0, 7:10], F.sum(axis=0) / P.mass * P.dt_ctrl, rtol=1e-10, atol=1e-15)
+
+
+def _dryden_series(sigma, V, h, steps, seed=5):
+    row = oracle.neutral_dr(1)[0]
+    row[oracle.DR_WIND] = oracle.WIND_DRYDEN
+    row[oracle.DR_DRY_SIGMA], row[oracle.DR_DRY_V], row[oracle.DR_DRY_H] = sigma, V, h
+    ws = np.zeros(oracle.WIND_STATE)
+    ws[3] = -1.0
+    xs = np.zeros((steps, 3))
+    for i in range(steps):
+        _, v = oracle.wind_step(P, row, ws, seed, 0)
+        xs[i] = v
+    return xs
+
+
+def test_dryden_stationary_statistics():
+    """x_t = alpha x_{t-1} + sigma sqrt(1 - alpha^2) xi: stationary variance sigma^2, lag-one
+    correlation alpha, Gaussian innovations. Started at 0, so the first 5 time constants
+    are dropped."""
+    sigma, V, h = 0.5, 8.0, 2.0
+    L = h / (0.177 + 8.23e-4 * h) ** 1.2
+    alpha = np.exp(-P.dt_ctrl * V / L)
+    xs = _dryden_series(sigma, V, h, 60000)[int(5 / (1 - alpha)):]
+    n_eff = xs.shape[0] * (1 - alpha) / (1 + alpha)
+    assert np.all(np.abs(xs.mean(axis=0)) < 4 * sigma / np.sqrt(n_eff))
+    np.testing.assert_allclose(xs.var(axis=0), sigma ** 2, rtol=6 * np.sqrt(2 / n_eff))
+    for r in range(3):
+        rho = np.corrcoef(xs[:-1, r], xs[1:, r])[0, 1]
+        assert rho == pytest.approx(alpha, abs=4 * np.sqrt((1 - alpha ** 2) / xs.shape[0]))  # AR(1) standard error
+        xi = (xs[1:, r] - alpha * xs[:-1, r]) / (sigma * np.sqrt(1 - alpha ** 2))
+        from scipy import stats
+        assert stats.kstest(xi, "norm").pvalue > 1e-3
+
+
+def _gust_row(p, A, T):
+    row = oracle.neutral_dr(1)[0]
+    row[oracle.DR_WIND] = oracle.WIND_GUST
+    row[oracle.DR_GUST_P], row[oracle.DR_GUST_A], row[oracle.DR_GUST_T] = p, A, T
+    return row
+
+
+def test_gust_envelope():
+    """p = 1, duration 4 control steps: a gust starts at once with phase 0, the force along a
+    fixed unit direction is A sin(pi s) at s = 0, 1/4, ..., 1, then the next gust starts."""
+    A = 0.2
+    row = _gust_row(1.0, A, 4 * P.dt_ctrl)
+    ws = np.zeros(oracle.WIND_STATE)
+    ws[3] = -1.0
+    F = np.array([oracle.wind_step(P, row, ws, 3, 7)[0] for _ in range(10)])
+    mags = np.linalg.norm(F, axis=1)
+    s = np.array([0, 0.25, 0.5, 0.75, 1.0, 0, 0.25, 0.5, 0.75, 1.0])
+    np.testing.assert_allclose(mags, A * np.sin(np.pi * s), atol=1e-12)
+    d1 = F[1:4] / mags[1:4, None]
+    np.testing.assert_allclose(d1, np.repeat(d1[:1], 3, axis=0), atol=1e-12)
+    np.testing.assert_allclose(np.linalg.norm(d1, axis=1), 1.0, atol=1e-12)
+    assert not np.allclose(F[6] / mags[6], d1[0])  # a new direction for the next gust
+    ws[3] = -1.0
+    assert np.all([np.linalg.norm(oracle.wind_step(P, _gust_row(0.0, A, 1.0), ws, 3, 7)[0]) == 0 for _ in range(50)])
+
+
+def test_gust_trigger_rate_and_direction():
+    """Gusts shorter than a control step: every step starts idle, so the starts are
+    Bernoulli(p); their directions are uniform on the sphere (mean 0, E[z^2] = 1/3)."""
+    p, N = 0.25, 20000
+    row = _gust_row(p, 1.0, 0.5 * P.dt_ctrl)
+    ws = np.zeros(oracle.WIND_STATE)
+    ws[3] = -1.0
+    dirs, prev = [], ws[4:7].copy()
+    for _ in range(N):
+        oracle.wind_step(P, row, ws, 11, 2)
+        assert ws[3] == -1.0  # over within its own step
+        if not np.array_equal(ws[4:7], prev):  # a start draws a new direction
+            dirs.append(ws[4:7].copy())
+            prev = ws[4:7].copy()
+    starts = len(dirs)
+    assert abs(starts - p * N) < 4 * np.sqrt(N * p * (1 - p))
+    D = np.array(dirs)
+    np.testing.assert_allclose(np.linalg.norm(D, axis=1), 1.0, atol=1e-12)
+    assert np.all(np.abs(D.mean(axis=0)) < 4 / np.sqrt(3 * len(D)))
+    assert np.mean(D[:, 2] ** 2) == pytest.approx(1 / 3, abs=4 * np.sqrt(4 / 45 / len(D)))
+
+
+def test_uniforms_match_the_input_generator():
+    for seed, stream, step, index, comp in ((0, 21, 0, 0, 0), (7, 21, 3, 12, 4), (2 ** 40 + 3, 5, 99, 7, 6)):
+        u = oracle.uniform(seed, stream, step, index, comp)
+        v = wl.uniform(seed, stream, step, np.uint64(index), np.uint64(comp))
+        assert u == float(v)
