@@ -121,6 +121,44 @@ typedef struct mdg_ctx* mdg_handle;
  * in a caller-owned buffer attached with mdg_set_setpoints). */
 #define MDG_CTRL_PID 0
 #define MDG_CTRL_DSL 1
+
+/* Domain randomization and wind (Section 3.5: the recommended-ranges table, reset per
+ * episode; "Wind and turbulence"): one row of MDG_DR_PARAMS floats per environment.
+ * Factors scale the model the physics integrates (the controller keeps the nominal
+ * constants: it does not know the draw). */
+#define MDG_DR_PARAMS 32
+#define MDG_DR_MASS 0       /* x m */
+#define MDG_DR_J 1          /* x Jxx, Jyy, Jzz (1..3) */
+#define MDG_DR_ARM 4        /* x L */
+#define MDG_DR_KF 5         /* x k_f */
+#define MDG_DR_KM 6         /* x k_m */
+#define MDG_DR_CXY 7        /* x c_xy */
+#define MDG_DR_CZ 8         /* x c_z */
+#define MDG_DR_CGND 9       /* x C_gnd */
+#define MDG_DR_C1 10        /* x downwash C1 */
+#define MDG_DR_MAXRPM 11    /* x MAX_RPM: the motors saturate there */
+#define MDG_DR_BIAS 12      /* per-motor speed bias (12..15): command = RPM x bias */
+#define MDG_DR_G 16         /* x g */
+#define MDG_DR_TAU 17       /* motor lag time constant [s] (0: none) */
+#define MDG_DR_DELAY 18     /* action latency [control steps], a whole number < the history depth */
+#define MDG_DR_WIND 19      /* wind model bits (MDG_WIND_*) */
+#define MDG_DR_VWIND 20     /* steady wind velocity [m/s], world frame (20..22) */
+#define MDG_DR_KDRAG 23     /* 1/2 rho C_d A [kg/m]: drag k |v_rel| v_rel, v_rel = wind - drone */
+#define MDG_DR_GUST_P 24    /* gust trigger probability per control step */
+#define MDG_DR_GUST_A 25    /* gust amplitude [N] */
+#define MDG_DR_GUST_T 26    /* gust duration [s] */
+#define MDG_DR_DRY_SIGMA 27 /* Dryden turbulence intensity [m/s] */
+#define MDG_DR_DRY_V 28     /* Dryden airspeed V [m/s] */
+#define MDG_DR_SIN_A 29     /* sinusoidal force amplitude [N] */
+#define MDG_DR_SIN_W 30     /* sinusoidal angular frequency [rad/s] */
+#define MDG_DR_DRY_H 31     /* Dryden reference altitude h [m] */
+#define MDG_WIND_CONSTANT 1
+#define MDG_WIND_GUST 2
+#define MDG_WIND_DRYDEN 4
+#define MDG_WIND_SINUSOIDAL 8
+#define MDG_WIND_COMBINED 15
+#define MDG_WIND_STATE 8    /* floats per environment: Dryden x (3), gust phase (-1 idle), gust direction (3), steps */
+#define MDG_MAX_HIST_DEPTH 16
 typedef struct mdg_constants {
     double mass, arm, thrust2weight, Jxx, Jyy, Jzz, kf, km, prop_radius;
     double g;
@@ -201,6 +239,30 @@ int mdg_set_action_types(mdg_handle h, const uint8_t* per_env);
  * with NaN to start, or a drone's row to reset it). NULL detaches. Required before any
  * compute call of a handle created with the DSL controller. Errors: MDG_ERR_ARG. */
 int mdg_set_setpoints(mdg_handle h, float* setpoints);
+
+/* Attach domain randomization, motor lag, action latency and wind to every step and
+ * rollout (all caller-owned device buffers, 16-byte aligned; NULL env_params detaches):
+ *   env_params   float32 [n_envs][MDG_DR_PARAMS] (validated here, on a host copy: factors
+ *                positive, tau >= 0, delay whole and < hist_depth, known wind bits,
+ *                gust probability in [0, 1], durations, altitude positive; change it only
+ *                by attaching again)
+ *   motor        float32 [n_drones][4] rotor speeds, the lag's state (NaN: not set, starts
+ *                at the first command)
+ *   action_hist  float32 [hist_depth][n_drones][4] actions received (NaN row: empty, filled
+ *                with the first action), hist_depth in [1, MDG_MAX_HIST_DEPTH]
+ *   wind_state   float32 [n_envs][MDG_WIND_STATE] (start: zeros with the gust phase -1)
+ *   seed         of the counter-based wind draws (SplitMix64 over seed, step, environment)
+ * Per control step and drone: the action received enters the shift register and the one
+ * received `delay` steps ago is applied, through the nominal controller (plane 5 records
+ * its RPMs); each motor's command is its RPM times its bias, saturated at MAX_RPM times
+ * the factor; the environment's wind (evaluated once per control step) adds its direct
+ * force and the quadratic drag on the relative wind at the step's start, held over the
+ * substeps; before each substep every rotor speed relaxes towards its command,
+ * n <- c + (n - c) exp(-dt_sim/tau); the substeps integrate the randomized model.
+ * Euler substeps only (MDG_ERR_UNSUPPORTED with RK4, and in mdg_surrogate_step). Errors:
+ * MDG_ERR_ARG, MDG_ERR_CUDA (the host copy). */
+int mdg_set_randomization(mdg_handle h, const float* env_params, float* motor, float* action_hist,
+                          int32_t hist_depth, float* wind_state, uint64_t seed);
 
 /* Threads per block of the step kernels (a multiple of 32 in [32, 1024] and at least
  * the largest environment, rounded up to 32). Environments are packed whole into

@@ -970,8 +970,10 @@ void orc_wind_step(const orc_params* P, const double* dr, double* ws, uint64_t s
         if (ws[3] >= 0.0) {
             const double a = dr[ORC_DR_GUST_A] * sin(ORC_PI * ws[3]);
             for (int r = 0; r < 3; ++r) F_dir[r] += a * ws[4 + r];
-            ws[3] += dt / dr[ORC_DR_GUST_T];
-            if (ws[3] > 1.0) ws[3] = -1.0;
+            /* the phase decides at which step the gust ends: it advances in single
+             * precision, as in the kernels, so that both end it at the same step */
+            const float s_next = (float)ws[3] + (float)dt / (float)dr[ORC_DR_GUST_T];
+            ws[3] = s_next > 1.0f ? -1.0 : (double)s_next;
         }
     }
     if (model & ORC_WIND_SINUSOIDAL) {

@@ -38,6 +38,11 @@ FRAME_X, FRAME_P = 0, 1
 INTEGRATOR_EULER, INTEGRATOR_RK4 = 0, 1
 GND_COM, GND_ROTOR = 0, 1
 CTRL_PID, CTRL_DSL = 0, 1
+DR_PARAMS, WIND_STATE, MAX_HIST_DEPTH = 32, 8, 16
+(DR_MASS, DR_J, DR_ARM, DR_KF, DR_KM, DR_CXY, DR_CZ, DR_CGND, DR_C1, DR_MAXRPM, DR_BIAS, DR_G, DR_TAU, DR_DELAY,
+ DR_WIND, DR_VWIND, DR_KDRAG, DR_GUST_P, DR_GUST_A, DR_GUST_T, DR_DRY_SIGMA, DR_DRY_V, DR_SIN_A, DR_SIN_W,
+ DR_DRY_H) = (0, 1, 4, 5, 6, 7, 8, 9, 10, 11, 12, 16, 17, 18, 19, 20, 23, 24, 25, 26, 27, 28, 29, 30, 31)
+WIND_CONSTANT, WIND_GUST, WIND_DRYDEN, WIND_SINUSOIDAL, WIND_COMBINED = 1, 2, 4, 8, 15
 OBS_NONE, OBS_LAST, OBS_EVERY_STEP = 0, 1, 2
 MLP_IN, MLP_IN_PAD, MLP_HIDDEN, MLP_OUT, MLP_OUT_PAD = 41, 64, 256, 13, 32
 MLP_DIMS = (MLP_IN_PAD, MLP_HIDDEN, MLP_HIDDEN, MLP_HIDDEN, MLP_OUT_PAD)
@@ -55,6 +60,7 @@ _SIGNATURES = {
     "mdg_constants_race": ([_VP], ctypes.c_int),
     "mdg_controller_dsl": ([_VP], ctypes.c_int),
     "mdg_set_setpoints": ([_VP, _VP], ctypes.c_int),
+    "mdg_set_randomization": ([_VP, _VP, _VP, _VP, ctypes.c_int32, _VP, ctypes.c_uint64], ctypes.c_int),
     "mdg_pid_ff": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "mdg_constants_size": ([], ctypes.c_int),
     "mdg_hover_rpm": ([_VP], ctypes.c_double),
@@ -349,6 +355,34 @@ class Handle:
         """float32 [n, 4] setpoints, all NaN (each starts at its drone's position and yaw)."""
         torch = _torch()
         return torch.full((self.n, 4), float("nan"), dtype=torch.float32, device=device)
+
+    def new_randomization_state(self, depth: int = 1, device="cuda"):
+        """(motor [n, 4], action_hist [depth, n, 4], wind_state [n_envs, WIND_STATE]) float32
+        device tensors in their starting state: rotor speeds and history unset (NaN), wind
+        at rest with no gust (phase -1)."""
+        torch = _torch()
+        motor = torch.full((self.n, 4), float("nan"), dtype=torch.float32, device=device)
+        hist = torch.full((depth, self.n, 4), float("nan"), dtype=torch.float32, device=device)
+        wind = torch.zeros((self.n_envs, WIND_STATE), dtype=torch.float32, device=device)
+        wind[:, 3] = -1.0
+        return motor, hist, wind
+
+    def set_randomization(self, env_params, motor=None, action_hist=None, wind_state=None, seed: int = 0):
+        """Attach domain randomization (mdg_set_randomization): env_params float32
+        [n_envs, DR_PARAMS] and the state tensors of new_randomization_state (kept alive
+        while attached). env_params None detaches."""
+        torch = _torch()
+        if env_params is None:
+            self._dr_keep = None
+            _check(lib().mdg_set_randomization(self._h, None, None, None, 0, None, 0))
+            return
+        depth = int(action_hist.shape[0])
+        self._dr_keep = (env_params, motor, action_hist, wind_state)
+        _check(lib().mdg_set_randomization(
+            self._h, _ptr(env_params, "env_params", torch.float32, (self.n_envs, DR_PARAMS)),
+            _ptr(motor, "motor", torch.float32, (self.n, 4)),
+            _ptr(action_hist, "action_hist", torch.float32, (depth, self.n, 4)), depth,
+            _ptr(wind_state, "wind_state", torch.float32, (self.n_envs, WIND_STATE)), int(seed)))
 
     def set_block_size(self, threads_per_block: int):
         _check(lib().mdg_set_block_size(self._h, int(threads_per_block)))

@@ -409,6 +409,12 @@ mdg::StepArgs base_args(mdg_ctx* h, float* state)
     a.envs_per_tile = h->envs_per_tile;
     a.uniform_bits = h->uniform_bits;
     a.setpoints = h->d_sp;
+    a.dr = h->dr;
+    a.motor = h->dr_motor;
+    a.hist = h->dr_hist;
+    a.wind = h->dr_wind;
+    a.wind_seed = h->dr_seed;
+    a.hist_depth = h->dr_depth;
     a.c = h->dc;
     return a;
 }
@@ -641,6 +647,54 @@ int mdg_set_setpoints(mdg_handle h, float* setpoints)
     if (!h) return fail(MDG_ERR_ARG, "mdg_set_setpoints: NULL handle");
     if (setpoints && !aligned16(setpoints)) return fail(MDG_ERR_ARG, "mdg_set_setpoints: not 16-byte aligned");
     h->d_sp = reinterpret_cast<float4*>(setpoints);
+    return MDG_OK;
+}
+
+int mdg_set_randomization(mdg_handle h, const float* env_params, float* motor, float* action_hist,
+                          int32_t hist_depth, float* wind_state, uint64_t seed)
+{
+    if (!h) return fail(MDG_ERR_ARG, "mdg_set_randomization: NULL handle");
+    if (!env_params) {
+        h->dr = nullptr;
+        h->dr_motor = h->dr_hist = h->dr_wind = nullptr;
+        h->dr_depth = 0;
+        return MDG_OK;
+    }
+    if (h->dc.rk4) return fail(MDG_ERR_UNSUPPORTED, "mdg_set_randomization: randomization integrates with Euler substeps");
+    if (!motor || !action_hist || !wind_state)
+        return fail(MDG_ERR_ARG, "mdg_set_randomization: motor, action_hist and wind_state are required");
+    if (!aligned16(env_params) || !aligned16(motor) || !aligned16(action_hist) || !aligned16(wind_state))
+        return fail(MDG_ERR_ARG, "mdg_set_randomization: buffers must be 16-byte aligned");
+    if (hist_depth < 1 || hist_depth > MDG_MAX_HIST_DEPTH)
+        return fail(MDG_ERR_ARG, "mdg_set_randomization: hist_depth = %d outside [1, %d]", hist_depth,
+                    MDG_MAX_HIST_DEPTH);
+    if (h->n_envs > 0) {
+        DeviceGuard dg(h->device);
+        std::vector<float> tab((size_t)h->n_envs * MDG_DR_PARAMS);
+        cudaError_t e = cudaMemcpy(tab.data(), env_params, tab.size() * sizeof(float), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "mdg_set_randomization: reading env_params");
+        for (int32_t k = 0; k < h->n_envs; ++k) {
+            const float* r = tab.data() + (size_t)k * MDG_DR_PARAMS;
+            for (int i = 0; i <= MDG_DR_G; ++i)
+                if (!(r[i] > 0.f) || !isfinite(r[i]))
+                    return fail(MDG_ERR_ARG, "mdg_set_randomization: env %d: factor %d = %g must be positive", k, i,
+                                (double)r[i]);
+            const float dly = r[MDG_DR_DELAY], bits = r[MDG_DR_WIND];
+            bool ok = r[MDG_DR_TAU] >= 0.f && isfinite(r[MDG_DR_TAU]) && dly >= 0.f && dly == floorf(dly) &&
+                      dly < (float)hist_depth && bits >= 0.f && bits == floorf(bits) && bits <= (float)MDG_WIND_COMBINED &&
+                      r[MDG_DR_KDRAG] >= 0.f && r[MDG_DR_GUST_P] >= 0.f && r[MDG_DR_GUST_P] <= 1.f &&
+                      r[MDG_DR_GUST_T] > 0.f && r[MDG_DR_DRY_SIGMA] >= 0.f && r[MDG_DR_DRY_V] >= 0.f &&
+                      r[MDG_DR_DRY_H] > 0.f;
+            for (int i = MDG_DR_VWIND; i < MDG_DR_PARAMS; ++i) ok = ok && isfinite(r[i]);
+            if (!ok) return fail(MDG_ERR_ARG, "mdg_set_randomization: env %d: invalid lag, delay or wind values", k);
+        }
+    }
+    h->dr = env_params;
+    h->dr_motor = reinterpret_cast<float4*>(motor);
+    h->dr_hist = reinterpret_cast<float4*>(action_hist);
+    h->dr_wind = reinterpret_cast<float4*>(wind_state);
+    h->dr_depth = hist_depth;
+    h->dr_seed = seed;
     return MDG_OK;
 }
 
@@ -899,8 +953,8 @@ static cudaError_t enqueue_rollout(mdg_handle h, const mdg::RolloutArgs& r, cuda
     int n_sm = 152;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device);
     const int flags = launch_flags(h, r.s.act_type);
-    const int grid =
-        n_sm * mdg::rollout_blocks_per_sm(h->block, flags, h->uniform_N, h->dc.rk4 != 0, h->dc.gnd_rotor != 0);
+    const int grid = n_sm * mdg::rollout_blocks_per_sm(h->block, h->dr ? mdg::kVariantRandomized : flags, h->uniform_N, h->dc.rk4 != 0,
+                                                           h->dc.gnd_rotor != 0);
     return mdg::launch_rollout(r, h->block, flags, grid, s);
 }
 

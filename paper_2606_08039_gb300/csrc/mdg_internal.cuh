@@ -75,6 +75,12 @@ struct StepArgs {
     int uniform_bits;         // uniform batches: kTileAnyDW | kTileWarpLocal for every tile
     int obs_host;             // 1: observations go to host memory, written through per-warp staging
     float4* setpoints;        // [n] DSL setpoints (x, y, z, yaw) or null
+    const float* dr;          // [n_envs][MDG_DR_PARAMS] domain randomization and wind, or null
+    float4* motor;            // [n] rotor speeds (the motor lag's state)
+    float4* hist;             // [hist_depth][n] actions received (the latency's shift register)
+    float4* wind;             // [n_envs][2] wind state
+    unsigned long long wind_seed;
+    int hist_depth;
     DevConsts c;
 };
 
@@ -145,6 +151,9 @@ int default_block(int32_t max_env, int64_t n_drones, int n_sm);
 
 cudaError_t launch_step(const StepArgs& a, int n_tiles, int block, bool with_obs, int uniform_flags, cudaStream_t s);
 
+// The step-kernel variant that runs under domain randomization (mdg_set_randomization).
+constexpr int kVariantRandomized = 11;
+
 // Action types the kernels accept, and those only the runtime-flag kernels convert.
 inline bool valid_env_action(int t) { return t == MDG_ACT_RPM || t == MDG_ACT_PID || (t >= MDG_ACT_RPM_NORM && t <= MDG_ACT_ATTITUDE); }
 inline bool valid_action(int t) { return valid_env_action(t) || t == MDG_ACT_MIXED; }
@@ -195,6 +204,13 @@ struct mdg_ctx {
     bool act_set = false;
     bool act_ext = false;  // some environment's type is beyond RPM/PID (runtime-flag kernels)
     float4* d_sp = nullptr;  // caller-owned DSL setpoints (mdg_set_setpoints)
+    // caller-owned domain randomization (mdg_set_randomization); dr == nullptr: none
+    const float* dr = nullptr;
+    float4* dr_motor = nullptr;
+    float4* dr_hist = nullptr;
+    float4* dr_wind = nullptr;
+    unsigned long long dr_seed = 0;
+    int dr_depth = 0;
     mdg::Tile* d_tiles = nullptr;
     int n_tiles = 0;
     int block = 0;

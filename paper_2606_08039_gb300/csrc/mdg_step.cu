@@ -306,11 +306,13 @@ __device__ __forceinline__ float downwash_sum(const float4* env_pos, int N_rt, f
 
 // Kernel variants beyond the compile-time physics subsets 0-7 (all take the physics flags
 // at run time): 8 Euler substeps, kFlagsRK4 Runge-Kutta substeps, kFlagsGndRotor Euler
-// substeps with Eq. ground at each rotor's height. The Runge-Kutta variants handle
+// substeps with Eq. ground at each rotor's height, kFlagsDR Euler substeps under domain
+// randomization (with per-rotor heights too). The Runge-Kutta variants handle
 // per-rotor heights too; variant 8 leaves that code out, so that its register allocation
 // is the one the mixed-physics batches need.
 constexpr int kFlagsRK4 = 9;
 constexpr int kFlagsGndRotor = 10;
+constexpr int kFlagsDR = kVariantRandomized;  // Euler substeps with domain randomization, motor lag, latency, wind
 
 // Eq. ground's increment along world +z, before its gate. With per-rotor heights rotor i
 // is at height p_z + R20 x_i + R21 y_i, and its thrust f_i is recovered from T and the
@@ -319,7 +321,7 @@ template <int kFlags>
 __device__ __forceinline__ float ground_increment(const Motor& m, float pz, float qw, float qx, float qy, float qz,
                                                   float R20, const DevConsts& c)
 {
-    if ((kFlags == kFlagsRK4 || kFlags == kFlagsGndRotor) && c.gnd_rotor) {
+    if ((kFlags == kFlagsRK4 || kFlags == kFlagsGndRotor || kFlags == kFlagsDR) && c.gnd_rotor) {
         const float R21 = 2.f * (qy * qz + qw * qx);
         const float tx = c.alloc_xy * m.tau[0], ty = c.alloc_xy * m.tau[1], tz = c.alloc_z * m.tau[2];
         float acc = 0.f;
@@ -342,7 +344,7 @@ __device__ __forceinline__ float ground_increment(const Motor& m, float pz, floa
 // kFlags = 8 / kN <= 0 take them from the runtime arguments.
 template <int kFlags, int kN>
 __device__ __forceinline__ void substep(Drone& d, const Motor& m, int flags_rt, const float4* env_pos, int N_rt,
-                                        const DevConsts& c)
+                                        const DevConsts& c, const float3 fe = float3{})
 {
     const int flags = kFlags < 8 ? kFlags : flags_rt;
     const float dt = c.dt_sim;
@@ -381,6 +383,11 @@ __device__ __forceinline__ void substep(Drone& d, const Motor& m, int flags_rt, 
         F[2] += kxy * d.v[2] + kr * r2;
     }
     if (flags & MDG_DW) F[2] -= downwash_sum<kN>(env_pos, N_rt, d.p[0], d.p[1], d.p[2], c);
+    if (kFlags == kFlagsDR) {  // the wind's force, world frame
+        F[0] += fe.x;
+        F[1] += fe.y;
+        F[2] += fe.z;
+    }
     // Newton-Euler: omega_dot = J^-1 (tau - omega x (J omega)), omega in the body frame
     const float Jw0 = c.J[0] * d.w[0], Jw1 = c.J[1] * d.w[1], Jw2 = c.J[2] * d.w[2];
     const float wd0 = c.inv_J[0] * (m.tau[0] - (d.w[1] * Jw2 - d.w[2] * Jw1));
@@ -580,6 +587,7 @@ struct TileInfo {
 // This thread's environment: first drone (tile-local), size, flags and action type.
 struct EnvSlot {
     int ls, N, flags, act;
+    int id;  // global environment index
 };
 
 __device__ __forceinline__ TileInfo get_tile(const StepArgs& a)
@@ -625,10 +633,11 @@ __device__ __forceinline__ void check_env(EnvSlot& e, int t, int n_drones, uint3
 __device__ __forceinline__ EnvSlot tile_env(const StepArgs& a, const TileInfo& ti, int* s_off, int* s_info)
 {
     const int t = threadIdx.x;
-    EnvSlot e = {0, 0, 0, 0};
+    EnvSlot e = {0, 0, 0, 0, 0};
     if (a.uniform_N > 0) {
         if (t < ti.n_drones) {
             const int k = t / a.uniform_N;
+            e.id = ti.first_env + k;
             e.ls = k * a.uniform_N;
             e.N = a.uniform_N;
             e.flags = a.env_flags[ti.first_env + k];
@@ -655,9 +664,228 @@ __device__ __forceinline__ EnvSlot tile_env(const StepArgs& a, const TileInfo& t
         e.N = s_off[lo + 1] - e.ls;
         e.flags = s_info[lo] & 0xff;
         e.act = s_info[lo] >> 8;
+        e.id = ti.first_env + lo;
     }
     check_env(e, t, ti.n_drones, a.status);
     return e;
+}
+
+// ---- domain randomization, motor lag, action latency and wind (kFlags == kFlagsDR) ----
+
+constexpr unsigned long long kStreamWind = 21;  // random stream of the wind draws
+
+// SplitMix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number generators",
+// OOPSLA 2014): the output function of its counter-based form.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// U[0, 1) with 24 random bits (exact in float) for the counters (seed, stream, step,
+// index, comp), each mixed in by one SplitMix64 round.
+__device__ __forceinline__ float counter_uniform(unsigned long long seed, unsigned long long stream,
+                                                 unsigned long long step, unsigned long long index,
+                                                 unsigned long long comp)
+{
+    unsigned long long h = splitmix64(seed);
+    h = splitmix64(h ^ stream);
+    h = splitmix64(h ^ step);
+    h = splitmix64(h ^ index);
+    h = splitmix64(h ^ comp);
+    return (float)(h >> 40) * (1.f / 16777216.f);
+}
+
+// The physics constants of an environment under its randomization row: factors on mass,
+// inertia, arm, k_f, k_m, c_xy, c_z, C_gnd, C1 and g (the controller keeps c).
+__device__ __forceinline__ DevConsts randomized_consts(const DevConsts& c, const float* row)
+{
+    DevConsts p = c;
+    const float fm = row[MDG_DR_MASS];
+    p.mass = c.mass * fm;
+    p.inv_mass = c.inv_mass / fm;
+    p.g = c.g * row[MDG_DR_G];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        p.J[r] = c.J[r] * row[MDG_DR_J + r];
+        p.inv_J[r] = c.inv_J[r] / row[MDG_DR_J + r];
+    }
+    const float fl = row[MDG_DR_ARM], fkf = row[MDG_DR_KF], fkm = row[MDG_DR_KM];
+    p.l_sqrt2 = c.l_sqrt2 * fl;
+    p.alloc_xy = c.alloc_xy / fl;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        p.rotor_x[i] = c.rotor_x[i] * fl;
+        p.rotor_y[i] = c.rotor_y[i] * fl;
+    }
+    p.kf = c.kf * fkf;
+    p.km = c.km * fkm;
+    p.alloc_z = c.alloc_z * (fkf / fkm);
+    p.c_xy = c.c_xy * row[MDG_DR_CXY];
+    p.c_z = c.c_z * row[MDG_DR_CZ];
+    p.c_dz = p.c_z - p.c_xy;
+    p.gnd_k = c.gnd_k * row[MDG_DR_CGND];
+    p.dw_k = c.dw_k * row[MDG_DR_C1];
+    return p;
+}
+
+// Action latency: the action received enters the drone's shift register and the one
+// received `delay` control steps ago comes out (an empty register is first filled with
+// the action received).
+__device__ __forceinline__ float4 delayed_action(const StepArgs& a, long long g, const float4 act, int delay)
+{
+    float4* h = a.hist + g;
+    if (isnan(h[0].x)) {
+        for (int k = 0; k < a.hist_depth; ++k) h[k * a.n] = act;
+        return act;
+    }
+    float4 out = act;
+    for (int k = a.hist_depth - 1; k > 0; --k) {
+        const float4 v = h[(k - 1) * a.n];
+        h[k * a.n] = v;
+        if (k == delay) out = v;
+    }
+    h[0] = act;
+    return out;
+}
+
+// One control step of an environment's wind (Section 3.5): advances its state s0 = (Dryden
+// x, gust phase s or -1), s1 = (gust direction, steps taken) and returns the direct force
+// (gusts, sinusoid) and the wind velocity the quadratic drag sees (steady wind, Dryden).
+// CONSTANT: the steady wind; DRYDEN: x <- alpha x + sigma sqrt(1 - alpha^2) xi per component,
+// alpha = exp(-dt V / L), L = h / (0.177 + 8.23e-4 h)^1.2, xi by Box-Muller; GUST: an idle
+// field starts a gust with the set probability, direction uniform on the sphere, force
+// A sin(pi s) while its phase s <= 1; SINUSOIDAL: A [sin wt, cos wt, 0.3 sin 2wt]. The gust
+// phase decides when a gust ends and advances in single precision.
+__device__ __forceinline__ void wind_step(const float* row, float4& s0, float4& s1, unsigned long long seed, int env,
+                                          float dt, float F[3], float vw[3])
+{
+    const int model = (int)row[MDG_DR_WIND];
+    const unsigned long long step = (unsigned long long)s1.w;
+    F[0] = F[1] = F[2] = vw[0] = vw[1] = vw[2] = 0.f;
+    if (model & MDG_WIND_CONSTANT) {
+        vw[0] += row[MDG_DR_VWIND];
+        vw[1] += row[MDG_DR_VWIND + 1];
+        vw[2] += row[MDG_DR_VWIND + 2];
+    }
+    if (model & MDG_WIND_DRYDEN) {
+        const float h = row[MDG_DR_DRY_H];
+        const float L = h / powf(0.177f + 8.23e-4f * h, 1.2f);
+        const float alpha = expf(-dt * row[MDG_DR_DRY_V] / L);
+        const float u1 = 1.f - counter_uniform(seed, kStreamWind, step, env, 0);
+        const float u2 = counter_uniform(seed, kStreamWind, step, env, 1);
+        const float u3 = 1.f - counter_uniform(seed, kStreamWind, step, env, 2);
+        const float u4 = counter_uniform(seed, kStreamWind, step, env, 3);
+        const float r1 = sqrtf(-2.f * logf(u1)), r2 = sqrtf(-2.f * logf(u3));
+        float s2, c2, s4, c4;
+        sincosf(2.f * kPi * u2, &s2, &c2);
+        sincosf(2.f * kPi * u4, &s4, &c4);
+        const float sc = row[MDG_DR_DRY_SIGMA] * sqrtf(fmaxf(0.f, 1.f - alpha * alpha));
+        s0.x = alpha * s0.x + sc * (r1 * c2);
+        s0.y = alpha * s0.y + sc * (r1 * s2);
+        s0.z = alpha * s0.z + sc * (r2 * c4);
+        vw[0] += s0.x;
+        vw[1] += s0.y;
+        vw[2] += s0.z;
+    }
+    if (model & MDG_WIND_GUST) {
+        if (s0.w < 0.f && counter_uniform(seed, kStreamWind, step, env, 4) < row[MDG_DR_GUST_P]) {
+            const float z = 2.f * counter_uniform(seed, kStreamWind, step, env, 5) - 1.f;
+            const float ph = 2.f * kPi * counter_uniform(seed, kStreamWind, step, env, 6);
+            const float rho = sqrtf(fmaxf(0.f, 1.f - z * z));
+            float sn, cs;
+            sincosf(ph, &sn, &cs);
+            s0.w = 0.f;
+            s1.x = rho * cs;
+            s1.y = rho * sn;
+            s1.z = z;
+        }
+        if (s0.w >= 0.f) {
+            const float amp = row[MDG_DR_GUST_A] * sinpif(s0.w);
+            F[0] += amp * s1.x;
+            F[1] += amp * s1.y;
+            F[2] += amp * s1.z;
+            s0.w += dt / row[MDG_DR_GUST_T];
+            if (s0.w > 1.f) s0.w = -1.f;
+        }
+    }
+    if (model & MDG_WIND_SINUSOIDAL) {
+        const float wt = row[MDG_DR_SIN_W] * ((float)step * dt), A = row[MDG_DR_SIN_A];
+        F[0] += A * sinf(wt);
+        F[1] += A * cosf(wt);
+        F[2] += A * 0.3f * sinf(2.f * wt);
+    }
+    s1.w = (float)(step + 1);
+}
+
+// The substeps of one control step under randomization, called by every thread of the
+// block (barriers inside). From the step's start: the environment's wind (each drone
+// evaluates it, the environment's first drone stores the new state once the block has read
+// the old one) and the drone's drag from it, held over the substeps; the randomized
+// constants; each motor's command (its RPM times its bias, saturated at MAX_RPM times the
+// factor). Before each substep every rotor speed relaxes towards its command,
+// n <- c + (n - c) exp(-dt/tau) (exact for a first-order lag under a constant command).
+template <int kN>
+__device__ __forceinline__ void randomized_substeps(const StepArgs& a, Drone& d, const float rpm[4], const EnvSlot& env,
+                                                    float4* s_pos, int B, int t, long long g, bool active,
+                                                    bool tile_dw, bool warp_local, int& ph)
+{
+    const float* row = a.dr + (long long)env.id * MDG_DR_PARAMS;
+    __syncthreads();  // the previous control step's wind state is stored
+    float4 s0 = {}, s1 = {}, ms = {};
+    float cmd[4] = {0.f, 0.f, 0.f, 0.f}, lag = 0.f;
+    float3 fe = {};
+    DevConsts pc = a.c;
+    if (active) {
+        s0 = a.wind[2LL * env.id];
+        s1 = a.wind[2LL * env.id + 1];
+        float Fd[3], vw[3];
+        wind_step(row, s0, s1, a.wind_seed, env.id, a.c.dt_ctrl, Fd, vw);
+        const int model = (int)row[MDG_DR_WIND];
+        if (model & (MDG_WIND_CONSTANT | MDG_WIND_DRYDEN)) {
+            const float vr[3] = {vw[0] - d.v[0], vw[1] - d.v[1], vw[2] - d.v[2]};
+            const float k = row[MDG_DR_KDRAG] * sqrtf(vr[0] * vr[0] + vr[1] * vr[1] + vr[2] * vr[2]);
+            Fd[0] += k * vr[0];
+            Fd[1] += k * vr[1];
+            Fd[2] += k * vr[2];
+        }
+        fe = make_float3(Fd[0], Fd[1], Fd[2]);
+        pc = randomized_consts(a.c, row);
+        const float sat = a.c.max_rpm * row[MDG_DR_MAXRPM];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) cmd[i] = fminf(rpm[i] * row[MDG_DR_BIAS + i], sat);
+        const float tau = row[MDG_DR_TAU];
+        lag = tau > 0.f ? expf(-a.c.dt_sim / tau) : 0.f;
+        ms = a.motor[g];
+        if (isnan(ms.x)) ms.x = cmd[0];
+        if (isnan(ms.y)) ms.y = cmd[1];
+        if (isnan(ms.z)) ms.z = cmd[2];
+        if (isnan(ms.w)) ms.w = cmd[3];
+    }
+    __syncthreads();  // every drone has read the wind state
+    if (active && t == env.ls) {
+        a.wind[2LL * env.id] = s0;
+        a.wind[2LL * env.id + 1] = s1;
+    }
+    for (int s = 0; s < a.n_sub; ++s, ++ph) {
+        float4* buf = s_pos + (ph & 1) * B;
+        if (tile_dw) {
+            buf[t] = make_float4(d.p[0], d.p[1], d.p[2], 0.f);
+            if (warp_local) __syncwarp();
+            else __syncthreads();
+        }
+        if (active) {
+            ms.x = cmd[0] + (ms.x - cmd[0]) * lag;
+            ms.y = cmd[1] + (ms.y - cmd[1]) * lag;
+            ms.z = cmd[2] + (ms.z - cmd[2]) * lag;
+            ms.w = cmd[3] + (ms.w - cmd[3]) * lag;
+            const float n[4] = {ms.x, ms.y, ms.z, ms.w};
+            substep<kFlagsDR, kN>(d, motor(n, pc), env.flags, buf + env.ls, env.N, pc, fe);
+        }
+    }
+    if (active) a.motor[g] = ms;
 }
 
 // ---- fourth-order Runge-Kutta substeps (MDG_INTEGRATOR_RK4) ----
@@ -815,6 +1043,8 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
     unpack_state(s0, s1, s2, s3, s4, d);
     float rpm[4] = {0.f, 0.f, 0.f, 0.f};
     if (active) {
+        if constexpr (kFlags == kFlagsDR)  // action latency
+            act = delayed_action(a, g, act, (int)a.dr[(long long)env.id * MDG_DR_PARAMS + MDG_DR_DELAY]);
         if (kFlags >= 8 && env.act >= MDG_ACT_RPM_NORM) {
             ext_action_rpm(d, act, env.act, a.c, rpm);
         } else if (is_pid) {
@@ -835,8 +1065,10 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
     const bool tile_dw = (tile.bits & kTileAnyDW) != 0;
     const bool warp_local = (tile.bits & kTileWarpLocal) != 0;
     int ph = 0;  // position publications (the double buffer's parity)
-    if (kFlags == kFlagsRK4) {
+    if constexpr (kFlags == kFlagsRK4) {
         rk4_substeps<kFlags, kN>(d, m, env, s_pos, B, t, active, tile_dw, warp_local, a.n_sub, ph, a.c);
+    } else if constexpr (kFlags == kFlagsDR) {
+        randomized_substeps<kN>(a, d, rpm, env, s_pos, B, t, g, active, tile_dw, warp_local, ph);
     } else {
         for (int s = 0; s < a.n_sub; ++s, ++ph) {
             float4* buf = s_pos + (s & 1) * B;
@@ -906,7 +1138,7 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
 
         // ---- this thread's drone and environment
         int n_drones, bits;
-        EnvSlot env = {0, 0, 0, 0};
+        EnvSlot env = {0, 0, 0, 0, 0};
         long long g = 0, env_first = 0;
         if (uniform) {
             const int first_env = item * a.envs_per_tile;
@@ -919,6 +1151,7 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
             bits = a.uniform_bits;
             if (t < n_drones) {
                 const int k = t / a.uniform_N;
+                env.id = first_env + k;
                 env.ls = k * a.uniform_N;
                 env.N = a.uniform_N;
                 env.flags = a.env_flags[first_env + k];
@@ -957,6 +1190,7 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
                 env.N = s_off[lo + 1] - env.ls;
                 env.flags = s_info[lo] & 0xff;
                 env.act = s_info[lo] >> 8;
+                if (kFlags == kFlagsDR) env.id = r.slot_env[it.x + lo];
                 env_first = s_goff[lo];
                 g = env_first + (t - env.ls);
                 // debug builds: the environment's drones lie inside the batch
@@ -994,6 +1228,8 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
             float4 next = {};
             if (active && k + 1 < r.K) next = a.action[(k + 1) * r.action_stride + g];
             if (active) {
+                if constexpr (kFlags == kFlagsDR)  // action latency
+                    act = delayed_action(a, g, act, (int)a.dr[(long long)env.id * MDG_DR_PARAMS + MDG_DR_DELAY]);
                 if (kFlags >= 8 && env.act >= MDG_ACT_RPM_NORM) {
                     ext_action_rpm(d, act, env.act, a.c, rpm);
                 } else if (is_pid) {
@@ -1008,8 +1244,10 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
                 }
             }
             const Motor m = motor(rpm, a.c);
-            if (kFlags == kFlagsRK4) {
+            if constexpr (kFlags == kFlagsRK4) {
                 rk4_substeps<kFlags, kN>(d, m, env, s_pos, B, t, active, tile_dw, warp_local, a.n_sub, sub, a.c);
+            } else if constexpr (kFlags == kFlagsDR) {
+                randomized_substeps<kN>(a, d, rpm, env, s_pos, B, t, g, active, tile_dw, warp_local, sub);
             } else {
                 for (int s = 0; s < a.n_sub; ++s, ++sub) {
                     float4* buf = s_pos + (sub & 1) * B;
@@ -1342,13 +1580,14 @@ __global__ void __launch_bounds__(256) pid_kernel(const PidArgs a)
 // the runtime flags with per-rotor ground heights; kN > 0 a
 // compile-time environment size, -1 a runtime size in blocks of at most kSmallBlock
 // threads, 0 any block size.
-#define MDG_STEP_VARIANTS(X) X(7, 4) X(7, 64) X(3, 1) X(8, -1) X(8, 0) X(9, -1) X(9, 0) X(10, -1) X(10, 0)
+#define MDG_STEP_VARIANTS(X) \
+    X(7, 4) X(7, 64) X(3, 1) X(8, -1) X(8, 0) X(9, -1) X(9, 0) X(10, -1) X(10, 0) X(11, -1) X(11, 0)
 
 template <bool kObs>
 static void* step_kernel_ptr(int flags, int N, int block)
 {
 #define MDG_PICK(F, NN)                                                                       \
-    if ((flags == F || (F == 8 && flags != kFlagsRK4 && flags != kFlagsGndRotor)) &&                                \
+    if ((flags == F || (F == 8 && flags != kFlagsRK4 && flags != kFlagsGndRotor && flags != kFlagsDR)) &&          \
         (NN == 0 || (block <= kSmallBlock && (NN == -1 || N == NN))))                         \
         return (void*)step_kernel<kObs, F, NN>;
     MDG_STEP_VARIANTS(MDG_PICK)
@@ -1387,7 +1626,7 @@ cudaError_t launch_step(const StepArgs& a, int n_tiles, int block, bool with_obs
     // a compile-time variant needs one physics subset and one environment size for the
     // batch; Runge-Kutta substeps have runtime-generic variants of their own
     // Runge-Kutta substeps and per-rotor ground heights run in the runtime-flag variants
-    const int flags = a.c.rk4 ? kFlagsRK4 : (a.c.gnd_rotor ? kFlagsGndRotor : uniform_flags);
+    const int flags = a.dr ? kFlagsDR : a.c.rk4 ? kFlagsRK4 : (a.c.gnd_rotor ? kFlagsGndRotor : uniform_flags);
     const int N = a.c.rk4 ? -1 : a.uniform_N;
     void* fn = with_obs ? step_kernel_ptr<true>(flags, N, block) : step_kernel_ptr<false>(flags, N, block);
     void* args[] = {const_cast<StepArgs*>(&a)};
@@ -1400,7 +1639,7 @@ static size_t rollout_smem_bytes(int B) { return (size_t)B * 48 + (size_t)(3 * B
 static void* rollout_kernel_ptr(int flags, int N, int block)
 {
 #define MDG_PICK(F, NN)                                                                       \
-    if ((flags == F || (F == 8 && flags != kFlagsRK4 && flags != kFlagsGndRotor)) &&                                \
+    if ((flags == F || (F == 8 && flags != kFlagsRK4 && flags != kFlagsGndRotor && flags != kFlagsDR)) &&          \
         (NN == 0 || (block <= kSmallBlock && (NN == -1 || N == NN))))                         \
         return (void*)rollout_kernel<F, NN>;
     MDG_STEP_VARIANTS(MDG_PICK)
@@ -1428,8 +1667,9 @@ static cudaError_t rollout_setup()
 
 int rollout_blocks_per_sm(int block, int uniform_flags, int uniform_N, bool rk4, bool gnd_rotor)
 {
-    if (rk4) uniform_flags = kFlagsRK4, uniform_N = -1;  // Runge-Kutta variants
-    else if (gnd_rotor) uniform_flags = kFlagsGndRotor;    // per-rotor ground heights
+    if (uniform_flags == kFlagsDR) uniform_N = -1;             // randomization variants
+    else if (rk4) uniform_flags = kFlagsRK4, uniform_N = -1;  // Runge-Kutta variants
+    else if (gnd_rotor) uniform_flags = kFlagsGndRotor;       // per-rotor ground heights
     if (rollout_setup() != cudaSuccess) return 1;
     int n = 0;
     void* fn = rollout_kernel_ptr(uniform_flags, uniform_N, block);
@@ -1442,7 +1682,8 @@ cudaError_t launch_rollout(const RolloutArgs& r, int block, int uniform_flags, i
 {
     if (r.n_items == 0 || r.K == 0) return cudaSuccess;
     const int uniform_N = r.s.c.rk4 ? -1 : r.s.uniform_N;
-    if (r.s.c.rk4) uniform_flags = kFlagsRK4;  // Runge-Kutta variants
+    if (r.s.dr) uniform_flags = kFlagsDR;  // randomization variants
+    else if (r.s.c.rk4) uniform_flags = kFlagsRK4;  // Runge-Kutta variants
     else if (r.s.c.gnd_rotor) uniform_flags = kFlagsGndRotor;  // per-rotor ground heights
     cudaError_t e = rollout_setup();
     if (e != cudaSuccess) return e;

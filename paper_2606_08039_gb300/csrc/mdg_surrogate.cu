@@ -358,6 +358,8 @@ int mdg_surrogate_step(mdg_handle h, mdg_mlp m, float* state, const float* actio
     if (action_type == MDG_ACT_MIXED && !h->act_set)
         return fail(MDG_ERR_ARG, "mdg_surrogate_step: MDG_ACT_MIXED needs mdg_set_action_types first");
     if (n_substeps < 1) return fail(MDG_ERR_ARG, "mdg_surrogate_step: n_substeps < 1");
+    if (h->dr)
+        return fail(MDG_ERR_UNSUPPORTED, "mdg_surrogate_step: randomization is not supported (its fallback runs the plain model)");
     if (h->dc.dsl && !h->d_sp)
         return fail(MDG_ERR_ARG, "mdg_surrogate_step: the DSL controller needs mdg_set_setpoints first");
     if (!m->norm_set) return fail(MDG_ERR_ARG, "mdg_surrogate_step: the surrogate has no normalisation");

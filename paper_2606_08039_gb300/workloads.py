@@ -214,7 +214,48 @@ def mixed_actions(swarm: Swarm, seed: int, step: int, hover_rpm: float) -> np.nd
     return a
 
 
-S_ACT_TYPE, S_ACT_EXT = 10, 11
+S_ACT_TYPE, S_ACT_EXT, S_DR = 10, 11, 12
+DR_PARAMS = 32
+
+
+def dr_table(seed: int, n_envs: int, dt_ctrl: float = 1.0 / 48.0, depth: int = 3,
+             wind_bits: int = 15) -> np.ndarray:
+    """float32 [n_envs, 32] domain-randomization rows drawn from the recommended ranges of
+    the paper's table for CF2X (factors U(1 - a, 1 + a)): mass and inertia x[0.8, 1.2], arm
+    x[0.98, 1.02], k_f and k_m x[0.85, 1.15], drag, C_gnd and C1 x[0.7, 1.3], per-motor bias
+    x[0.95, 1.05], MAX_RPM x[0.95, 1.05], g x[0.98, 1.02], motor lag U[5, 50] ms, action
+    latency U[0, 50] ms as whole control steps (below `depth`); wind (the model bits given)
+    with a horizontal steady wind of magnitude U(0, 1) m/s, 1/2 rho C_d A U[5e-4, 2e-3] kg/m,
+    gusts p U[0.02, 0.1] per step, A U[0.02, 0.08] N, duration U[0.1, 0.5] s, Dryden sigma
+    U[0.1, 0.5] m/s, V U[1, 5] m/s, h U[0.5, 2] m, sinusoid A U[0.005, 0.02] N,
+    w U[1, 6] rad/s. The layout is that of MDG_DR_PARAMS in include/mdg.h."""
+    e = np.arange(n_envs, dtype=np.uint64)[:, None]
+    u = uniform(seed, S_DR, 0, e, np.arange(DR_PARAMS, dtype=np.uint64)[None, :]).astype(np.float64)
+    r = np.zeros((n_envs, DR_PARAMS))
+
+    def U(col, lo, hi):
+        return lo + (hi - lo) * u[:, col]
+    r[:, 0] = U(0, 0.8, 1.2)
+    for k in range(3):
+        r[:, 1 + k] = U(1 + k, 0.8, 1.2)
+    r[:, 4] = U(4, 0.98, 1.02)
+    r[:, 5], r[:, 6] = U(5, 0.85, 1.15), U(6, 0.85, 1.15)
+    for k in (7, 8, 9, 10):
+        r[:, k] = U(k, 0.7, 1.3)
+    r[:, 11] = U(11, 0.95, 1.05)
+    for k in range(4):
+        r[:, 12 + k] = U(12 + k, 0.95, 1.05)
+    r[:, 16] = U(16, 0.98, 1.02)
+    r[:, 17] = U(17, 0.005, 0.05)
+    r[:, 18] = np.minimum(np.floor(U(18, 0.0, 0.05) / dt_ctrl + 0.5), depth - 1)
+    r[:, 19] = wind_bits
+    speed, heading = U(19, 0.0, 1.0), U(20, 0.0, 2 * np.pi)
+    r[:, 20], r[:, 21] = speed * np.cos(heading), speed * np.sin(heading)
+    r[:, 23] = U(21, 5e-4, 2e-3)
+    r[:, 24], r[:, 25], r[:, 26] = U(22, 0.02, 0.1), U(23, 0.02, 0.08), U(24, 0.1, 0.5)
+    r[:, 27], r[:, 28], r[:, 31] = U(25, 0.1, 0.5), U(26, 1.0, 5.0), U(27, 0.5, 2.0)
+    r[:, 29], r[:, 30] = U(28, 0.005, 0.02), U(29, 1.0, 6.0)
+    return r.astype(np.float32)
 
 
 def all_action_types(seed: int, n_envs: int) -> np.ndarray:

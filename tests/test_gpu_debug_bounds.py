@@ -9,7 +9,7 @@ in a separate process that loads it, runs every kernel family on the workloads o
 parity suite (uniform and table tiles, compile-time and runtime environment sizes, the
 persistent rollout, observations, PID, surrogate features, preparation, application and
 the fallback pass, the allocation-free entry point, the RK4 and per-rotor ground-height
-variants, every action type); no check may fail.
+variants, every action type, randomization); no check may fail.
 """
 import ctypes
 import os
@@ -114,6 +114,23 @@ def _run():
             h.step_obs(st, act, mdg.ACT_MIXED, 5, kin, idx, rel)
             h.rollout(st, act[None], mdg.ACT_MIXED, 5, 1)
             check(h, f"{name} {tag} block {block}")
+    # the randomization variants (uneven tables and any-size blocks)
+    for name in ("uneven", "dense"):
+        sw = swarms[name]
+        h = mdg.Handle(sw.drones_per_env, sw.flags)
+        h.set_action_types(sw.act_type)
+        motor, hist, wind = h.new_randomization_state(3, dev)
+        h.set_randomization(torch.as_tensor(wl.dr_table(93, sw.n_envs, depth=3), device=dev), motor, hist, wind, 5)
+        st = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=dev)
+        act = torch.as_tensor(wl.mixed_actions(sw, 94, 0, hover), device=dev)
+        kin, idx, rel = h.new_obs(dev)
+        for block in sorted({h.block_size, 256, 1024}):
+            if block < max(sw.drones_per_env):
+                continue
+            h.set_block_size(block)
+            h.step_obs(st, act, mdg.ACT_MIXED, 5, kin, idx, rel)
+            h.rollout(st, act[None], mdg.ACT_MIXED, 5, 1)
+            check(h, f"{name} randomized block {block}")
     # the allocation-free entry point builds its tables in static scratch
     sw = swarms["uneven"]
     st = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=dev)

@@ -1,0 +1,146 @@
+"""GPU parity of domain randomization, motor lag, action latency and wind (Section 3.5).
+
+Rows drawn from the paper's recommended ranges (workloads.dr_table, every wind model on).
+Each control step, the oracle restarts from the GPU's state and randomization state
+(rotor speeds, action history, wind state) and is compared over the step with the horizon
+bound; the RPMs, integrals, rotor speeds and wind state against the oracle's, the action
+history and the gust phases and step counters exactly (the gust phase decides when a gust
+ends and advances in single precision on both sides; the wind draws come from the same
+counter-based SplitMix64 stream). Heights are spread per environment
+(helpers.spread_heights): the randomization is under test, not the downwash's conditioning.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2606_08039_gb300 as mdg
+from paper_2606_08039_gb300 import workloads as wl
+from helpers import assert_horizon_close, excess, oracle_arrays, spread_heights
+
+pytestmark = pytest.mark.gpu
+
+P = oracle.cf2x()
+HOVER = oracle.hover_rpm(P)
+SEED = 77
+DEPTH = 3
+
+
+def _oracle_state(table, motor, hist, wind):
+    r = oracle.Randomization(table.shape[0], motor.shape[0], hist.shape[0], SEED)
+    r.env_dr[:] = table.astype(np.float64)
+    r.motor[:] = motor.cpu().numpy().astype(np.float64)
+    r.hist[:] = hist.cpu().numpy().astype(np.float64)
+    r.wind[:] = wind.cpu().numpy().astype(np.float64)
+    return r
+
+
+def _oracle_steps(sw, types, x, integ, a_prev, actions, r, perturb=False):
+    env_off = np.concatenate([[0], np.cumsum(sw.drones_per_env)]).astype(np.int32)
+    if perturb:  # the horizon bound's response: an initial error of the per-substep tolerance
+        rng = np.random.default_rng(0)
+        sgn = rng.choice([-1.0, 1.0], size=x.shape)
+        x = x.copy()
+        for sl, tol in ((slice(0, 3), 1e-5), (slice(7, 10), 1e-5), (slice(10, 13), 1e-4)):
+            x[:, sl] += sgn[:, sl] * tol * np.maximum(np.abs(x[:, sl]), 1.0)
+        q = x[:, 3:7] + sgn[:, 3:7] * 2e-6
+        x[:, 3:7] = q / np.linalg.norm(q, axis=1, keepdims=True)
+    return oracle.control_steps(P, env_off, sw.flags.astype(np.int32), np.asarray(types, np.int32), x, integ,
+                                a_prev, np.asarray(actions, np.float64), 5, dr=r)
+
+
+def _copy(r):
+    c = oracle.Randomization(r.env_dr.shape[0], r.motor.shape[0], r.hist.shape[0], r.seed)
+    for k in ("env_dr", "motor", "hist", "wind"):
+        getattr(c, k)[:] = getattr(r, k)
+    return c
+
+
+def _setup(cuda, recipe):
+    if recipe == "full_aero":
+        sw = spread_heights(wl.full_aero(91, n_envs=160))
+        types = np.full(sw.n_envs, mdg.ACT_PID, np.uint8)
+    elif recipe == "mixed":
+        sw = spread_heights(wl.uneven(92, n_envs=120))
+        types = wl.all_action_types(93, sw.n_envs)
+    else:
+        sw = wl.single(94, n_envs=128)
+        types = np.full(sw.n_envs, mdg.ACT_RPM, np.uint8)
+    table = wl.dr_table(95, sw.n_envs, depth=DEPTH)
+    h = mdg.Handle(sw.drones_per_env, sw.flags)
+    h.set_action_types(types)
+    motor, hist, wind = h.new_randomization_state(DEPTH, cuda)
+    h.set_randomization(torch.as_tensor(table, device=cuda), motor, hist, wind, seed=SEED)
+    return sw, types, table, h, motor, hist, wind
+
+
+@pytest.mark.parametrize("recipe", ["full_aero", "mixed", "single"])
+def test_randomized_control_steps(cuda, recipe):
+    sw, types, table, h, motor, hist, wind = _setup(cuda, recipe)
+    state = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=cuda)
+    kin, idx, rel = h.new_obs(cuda)
+    for k in range(4):
+        action = wl.typed_actions(sw.drones_per_env, types, 96, k, HOVER, P.mass * P.g)
+        x0, i0, a0 = oracle_arrays(state)
+        r = _oracle_state(table, motor, hist, wind)
+        r2 = _copy(r)
+        h.step_obs(state, torch.as_tensor(action, device=cuda), mdg.ACT_MIXED, 5, kin, idx, rel)
+        torch.cuda.synchronize()
+        xg, ig, ag = oracle_arrays(state)
+        xo, io, ao = _oracle_steps(sw, types, x0, i0, a0, action[None], r)
+        xp, _, _ = _oracle_steps(sw, types, x0, i0, a0, action[None], r2, perturb=True)
+        what = f"{recipe} step {k}"
+        assert_horizon_close(xg, xo, np.abs(xo - xp), 5, what=what)
+        np.testing.assert_allclose(P.kf * ag ** 2, P.kf * ao ** 2, rtol=0, atol=1e-5 * P.kf * oracle.max_rpm(P) ** 2,
+                                   err_msg=f"{what}: rpm")
+        assert excess(ig, io, 1e-5) <= 1.0, f"{what}: integrals"
+        assert excess(motor.cpu().numpy(), r.motor, 1e-5) <= 1.0, f"{what}: rotor speeds"
+        np.testing.assert_array_equal(hist.cpu().numpy().astype(np.float64), r.hist, err_msg=f"{what}: history")
+        wg = wind.cpu().numpy().astype(np.float64)
+        np.testing.assert_array_equal(wg[:, 3], r.wind[:, 3], err_msg=f"{what}: gust phases")
+        np.testing.assert_array_equal(wg[:, 7], r.wind[:, 7], err_msg=f"{what}: wind steps")
+        np.testing.assert_allclose(wg[:, 0:3], r.wind[:, 0:3], rtol=1e-4, atol=1e-5, err_msg=f"{what}: Dryden")
+        np.testing.assert_allclose(wg[:, 4:7], r.wind[:, 4:7], rtol=0, atol=1e-6, err_msg=f"{what}: gust directions")
+    assert (wind[:, 3] >= 0).any(), "no gust was active during the test"
+    assert h.status()[0] == mdg.OK
+
+
+def test_randomized_rollout(cuda):
+    sw, types, table, h, motor, hist, wind = _setup(cuda, "full_aero")
+    K = 4
+    state = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=cuda)
+    actions = np.stack([wl.typed_actions(sw.drones_per_env, types, 97, k, HOVER, P.mass * P.g) for k in range(K)])
+    x0, i0, a0 = oracle_arrays(state)
+    r = _oracle_state(table, motor, hist, wind)
+    r2 = _copy(r)
+    h.rollout(state, torch.as_tensor(actions, device=cuda), mdg.ACT_MIXED, 5, K)
+    torch.cuda.synchronize()
+    xg, _, _ = oracle_arrays(state)
+    xo, _, _ = _oracle_steps(sw, types, x0, i0, a0, actions, r)
+    xp, _, _ = _oracle_steps(sw, types, x0, i0, a0, actions, r2, perturb=True)
+    assert_horizon_close(xg, xo, np.abs(xo - xp), 5 * K, what="randomized rollout")
+    wg = wind.cpu().numpy().astype(np.float64)
+    np.testing.assert_array_equal(wg[:, 7], K)
+    np.testing.assert_array_equal(wg[:, 3], r.wind[:, 3])
+    np.testing.assert_array_equal(hist.cpu().numpy().astype(np.float64), r.hist)
+
+
+def test_randomization_arguments(cuda):
+    sw = wl.full_aero(98, n_envs=8)
+    h = mdg.Handle(sw.drones_per_env, sw.flags)
+    motor, hist, wind = h.new_randomization_state(2, cuda)
+    good = wl.dr_table(99, sw.n_envs, depth=2)
+    for col, val in ((mdg.DR_MASS, 0.0), (mdg.DR_DELAY, 2.0), (mdg.DR_DELAY, 0.5), (mdg.DR_WIND, 16.0),
+                     (mdg.DR_GUST_P, 1.5), (mdg.DR_GUST_T, 0.0), (mdg.DR_TAU, -0.01)):
+        bad = good.copy()
+        bad[3, col] = val
+        with pytest.raises(mdg.MdgError):
+            h.set_randomization(torch.as_tensor(bad, device=cuda), motor, hist, wind)
+    h.set_randomization(torch.as_tensor(good, device=cuda), motor, hist, wind)
+    h.set_randomization(None)
+    c = mdg.Constants.cf2x()
+    c.integrator = mdg.INTEGRATOR_RK4
+    h4 = mdg.Handle(sw.drones_per_env, sw.flags, c)
+    with pytest.raises(mdg.MdgError) as e:
+        h4.set_randomization(torch.as_tensor(good, device=cuda), motor, hist, wind)
+    assert e.value.code == mdg.ERR_UNSUPPORTED

@@ -199,7 +199,7 @@ def test_gust_envelope():
     F = np.array([oracle.wind_step(P, row, ws, 3, 7)[0] for _ in range(10)])
     mags = np.linalg.norm(F, axis=1)
     s = np.array([0, 0.25, 0.5, 0.75, 1.0, 0, 0.25, 0.5, 0.75, 1.0])
-    np.testing.assert_allclose(mags, A * np.sin(np.pi * s), atol=1e-12)
+    np.testing.assert_allclose(mags, A * np.sin(np.pi * s), atol=1e-7)  # the phase advances in float32
     d1 = F[1:4] / mags[1:4, None]
     np.testing.assert_allclose(d1, np.repeat(d1[:1], 3, axis=0), atol=1e-12)
     np.testing.assert_allclose(np.linalg.norm(d1, axis=1), 1.0, atol=1e-12)
