@@ -67,14 +67,23 @@ def kernel_sha() -> str:
 ACTION_CHOICES = {"pid": 1, "rpm": 0, "rpm_norm": 3, "one_d_rpm": 4, "vel": 5, "attitude": 6, "mixed": 2}
 
 
+DR_DEPTH = 3   # action-history depth of the randomized workload (latency up to 2 control steps)
+DR_SEED = 5    # wind draws of the randomized workload
+
+
 def model_config(args) -> dict:
-    return {"model": args.model, "integrator": args.integrator, "gnd_heights": args.gnd_heights,
-            "actions": getattr(args, "actions", "pid"), "controller": getattr(args, "controller", "pid")}
+    out = {"model": args.model, "integrator": args.integrator, "gnd_heights": args.gnd_heights,
+           "actions": getattr(args, "actions", "pid"), "controller": getattr(args, "controller", "pid")}
+    if getattr(args, "randomize", False):
+        out["randomization"] = ("recommended-ranges rows per environment, motor lag, action latency "
+                                f"(history depth {DR_DEPTH}), COMBINED wind")
+    return out
 
 
 def is_default_model(args) -> bool:
     return ((args.model, args.integrator, args.gnd_heights) == ("cf2x", "euler", "com")
-            and getattr(args, "actions", "pid") == "pid" and getattr(args, "controller", "pid") == "pid")
+            and getattr(args, "actions", "pid") == "pid" and getattr(args, "controller", "pid") == "pid"
+            and not getattr(args, "randomize", False))
 
 
 def action_types(args, n_envs: int, seed: int) -> np.ndarray:
@@ -118,7 +127,12 @@ def oracle_workload(args, sw, seed: int):
     else:
         act = wl.typed_actions(sw.drones_per_env, types, seed, 0, oracle_hover(P), P.mass * P.g)
     sp = np.full((sw.n, 4), np.nan) if args.controller == "dsl" else None
-    return types.astype(np.int32), act.astype(np.float64)[None], sp
+    dr = None
+    if getattr(args, "randomize", False):
+        import oracle
+        dr = oracle.Randomization(sw.n_envs, sw.n, DR_DEPTH, DR_SEED)
+        dr.env_dr[:] = wl.dr_table(seed, sw.n_envs, depth=DR_DEPTH).astype(np.float64)
+    return types.astype(np.int32), act.astype(np.float64)[None], sp, dr
 
 
 def oracle_hover(P) -> float:
@@ -217,13 +231,13 @@ def cpu_baseline(args, seconds_target: float = 10.0) -> dict:
     P = oracle_params(args)
     sw = wl.full_aero(1)
     x, integ, a = sw.x13(), np.zeros((sw.n, 6)), np.zeros((sw.n, 4))
-    acts, wp, sp = oracle_workload(args, sw, 1)
+    acts, wp, sp, dr = oracle_workload(args, sw, 1)
     flags = sw.flags.astype(np.int32)
     steps = 0
     t0 = time.perf_counter()
     while True:
         x, integ, a, *_ = oracle.control_steps(P, sw.env_off, flags, acts, x, integ, a, wp, N_SUB, obs=True,
-                                               setpoint=sp)
+                                               setpoint=sp, dr=dr)
         steps += 1
         dt = time.perf_counter() - t0
         if dt >= seconds_target or steps >= 200:
@@ -244,13 +258,13 @@ def run_reference(args) -> None:
     P = oracle_params(args)
     sw = wl.full_aero(1, n_envs=2048)
     x, integ, a = sw.x13(), np.zeros((sw.n, 6)), np.zeros((sw.n, 4))
-    acts, wp, sp = oracle_workload(args, sw, 1)
+    acts, wp, sp, dr = oracle_workload(args, sw, 1)
     flags = sw.flags.astype(np.int32)
 
     def one():
         nonlocal x, integ, a
         x, integ, a, *_ = oracle.control_steps(P, sw.env_off, flags, acts, x, integ, a, wp, N_SUB, obs=True,
-                                               setpoint=sp)
+                                               setpoint=sp, dr=dr)
 
     for _ in range(args.warmup):
         one()
@@ -302,19 +316,25 @@ def algorithmic_flops(sw, K: int, n_sub: int, obs_steps: int, pid_mask=None, rk4
     return float(total)
 
 
-def algorithmic_bytes(sw, types, act_type: int, dsl: bool) -> int:
+def algorithmic_bytes(sw, types, act_type: int, dsl: bool, dr_depth: int = 0) -> int:
     """Bytes one fused control step must move for the full-aero workload: per drone the state
     planes 0-3 read and written (64 + 64 B), plane 4 (attitude integrals) read unless every
     action is RPM and written where the controller loops run (PID, VEL, ATTITUDE), the action
     (16 B), plane 5 written (16 B), the observations (192 B), and with the DSL controller the
-    setpoint of each waypoint-driven drone read and written (32 B). 384 B for PID actions."""
+    setpoint of each waypoint-driven drone read and written (32 B). 384 B for PID actions.
+    Under randomization (history depth D): the rotor speeds read and written (32 B), the
+    action history shifted (D - 1 reads, D writes of 16 B), and per environment its 128 B row
+    and its 32 B wind state read and written."""
     per_env = np.full(sw.n_envs, 64 + 64 + 16 + 16 + OBS_BYTES, np.int64)
     if act_type != 0:
         per_env += 16
     per_env += 16 * np.isin(types, (1, 5, 6))
     if dsl:
         per_env += 32 * (types == 1)
-    return int(np.sum(per_env * sw.drones_per_env))
+    total = int(np.sum(per_env * sw.drones_per_env))
+    if dr_depth:
+        total += sw.n * (32 + 16 * (2 * dr_depth - 1)) + sw.n_envs * (128 + 64)
+    return total
 
 
 def binding_roofline(bytes_launch: float, flops_launch: float, sec: float, peaks) -> dict:
@@ -670,6 +690,8 @@ def main() -> None:
     ap.add_argument("--actions", default="pid", choices=sorted(ACTION_CHOICES),
                     help="full_aero: the action type of every environment, or mixed (all six types)")
     ap.add_argument("--controller", default="pid", choices=["pid", "dsl"])
+    ap.add_argument("--randomize", action="store_true",
+                    help="full_aero: domain randomization from the recommended ranges, motor lag, latency, wind")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -678,8 +700,10 @@ def main() -> None:
         return
     if args.workload in ("surrogate", "mlp") and not is_default_model(args):
         ap.error("--model/--integrator/--gnd-heights/--actions/--controller apply to the dynamics workloads only")
-    if args.workload != "full_aero" and (args.actions, args.controller) != ("pid", "pid"):
-        ap.error("--actions/--controller apply to the full_aero workload")
+    if args.workload != "full_aero" and ((args.actions, args.controller) != ("pid", "pid") or args.randomize):
+        ap.error("--actions/--controller/--randomize apply to the full_aero workload")
+    if args.randomize and args.integrator == "rk4":
+        ap.error("--randomize integrates with Euler substeps")
     if args.workload == "surrogate":
         run_surrogate(args)
         return
@@ -723,6 +747,11 @@ def main() -> None:
     if args.controller == "dsl":
         setpoints = h.new_setpoints(dev)
         h.set_setpoints(setpoints)
+    dr_state = None
+    if args.randomize:
+        dr_state = h.new_randomization_state(DR_DEPTH, dev)
+        table = torch.as_tensor(wl.dr_table(replica_seed(rank), sw.n_envs, depth=DR_DEPTH), device=dev)
+        h.set_randomization(table, *dr_state, seed=DR_SEED)
     wp_host = torch.from_numpy(act_np).pin_memory()
     wp = wp_host.to(dev)
 
@@ -730,6 +759,11 @@ def main() -> None:
         state.copy_(init_state)
         if setpoints is not None:
             setpoints.fill_(float("nan"))
+        if dr_state is not None:
+            dr_state[0].fill_(float("nan"))
+            dr_state[1].fill_(float("nan"))
+            dr_state[2].zero_()
+            dr_state[2][:, 3] = -1.0
     kin, idx, rel = h.new_obs(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     flush_sink = torch.empty((), dtype=torch.float32, device=dev)
@@ -827,7 +861,8 @@ def main() -> None:
     if rank == 0:
         peaks = measured_peaks()
         avg_s = total_ms / args.steps * 1e-3
-        bytes_launch = algorithmic_bytes(sw, types, act_type, args.controller == "dsl")
+        bytes_launch = algorithmic_bytes(sw, types, act_type, args.controller == "dsl",
+                                         DR_DEPTH if args.randomize else 0)
         loops_mask = np.isin(types, (1, 5, 6))  # PID, VEL, ATTITUDE run the controller loops
         flops_launch = algorithmic_flops(sw, 1, N_SUB, 1, loops_mask, rk4=args.integrator == "rk4")
         roofline = binding_roofline(bytes_launch, flops_launch, avg_s, peaks)

@@ -383,6 +383,7 @@ void destroy_ctx(mdg_ctx* h)
     cudaFree(h->d_act);
     cudaFree(h->d_tiles);
     cudaFree(h->d_status);
+    cudaFree(h->d_rand);
     delete h;
 }
 
@@ -409,12 +410,7 @@ mdg::StepArgs base_args(mdg_ctx* h, float* state)
     a.envs_per_tile = h->envs_per_tile;
     a.uniform_bits = h->uniform_bits;
     a.setpoints = h->d_sp;
-    a.dr = h->dr;
-    a.motor = h->dr_motor;
-    a.hist = h->dr_hist;
-    a.wind = h->dr_wind;
-    a.wind_seed = h->dr_seed;
-    a.hist_depth = h->dr_depth;
+    a.rand = h->dr ? h->d_rand : nullptr;
     a.c = h->dc;
     return a;
 }
@@ -656,8 +652,6 @@ int mdg_set_randomization(mdg_handle h, const float* env_params, float* motor, f
     if (!h) return fail(MDG_ERR_ARG, "mdg_set_randomization: NULL handle");
     if (!env_params) {
         h->dr = nullptr;
-        h->dr_motor = h->dr_hist = h->dr_wind = nullptr;
-        h->dr_depth = 0;
         return MDG_OK;
     }
     if (h->dc.rk4) return fail(MDG_ERR_UNSUPPORTED, "mdg_set_randomization: randomization integrates with Euler substeps");
@@ -689,12 +683,19 @@ int mdg_set_randomization(mdg_handle h, const float* env_params, float* motor, f
             if (!ok) return fail(MDG_ERR_ARG, "mdg_set_randomization: env %d: invalid lag, delay or wind values", k);
         }
     }
+    mdg::RandArgs ra;
+    ra.dr = env_params;
+    ra.motor = reinterpret_cast<float4*>(motor);
+    ra.hist = reinterpret_cast<float4*>(action_hist);
+    ra.wind = reinterpret_cast<float4*>(wind_state);
+    ra.seed = seed;
+    ra.depth = hist_depth;
+    DeviceGuard dg(h->device);
+    cudaError_t e = cudaSuccess;
+    if (!h->d_rand) e = cudaMalloc(reinterpret_cast<void**>(&h->d_rand), sizeof(mdg::RandArgs));
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_rand, &ra, sizeof(ra), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "mdg_set_randomization: device copy of the buffers");
     h->dr = env_params;
-    h->dr_motor = reinterpret_cast<float4*>(motor);
-    h->dr_hist = reinterpret_cast<float4*>(action_hist);
-    h->dr_wind = reinterpret_cast<float4*>(wind_state);
-    h->dr_depth = hist_depth;
-    h->dr_seed = seed;
     return MDG_OK;
 }
 

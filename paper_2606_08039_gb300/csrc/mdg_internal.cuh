@@ -55,6 +55,16 @@ constexpr int kTileEnvMask = 0xffff;
 constexpr int kTileAnyDW = 1 << 30;      // some environment of the tile has downwash on
 constexpr int kTileWarpLocal = 1 << 29;  // every environment lies inside one warp
 
+// The buffers of mdg_set_randomization, kept in a small device allocation of the handle.
+struct RandArgs {
+    const float* dr;          // [n_envs][MDG_DR_PARAMS] domain randomization and wind
+    float4* motor;            // [n] rotor speeds (the motor lag's state)
+    float4* hist;             // [depth][n] actions received (the latency's shift register)
+    float4* wind;             // [n_envs][2] wind state
+    unsigned long long seed;  // of the wind draws
+    int depth;
+};
+
 struct StepArgs {
     float4* state;            // [6][n] float4 planes
     const float4* action;     // [n]
@@ -74,14 +84,11 @@ struct StepArgs {
     int envs_per_tile;        // uniform batches: environments per block
     int uniform_bits;         // uniform batches: kTileAnyDW | kTileWarpLocal for every tile
     int obs_host;             // 1: observations go to host memory, written through per-warp staging
-    float4* setpoints;        // [n] DSL setpoints (x, y, z, yaw) or null
-    const float* dr;          // [n_envs][MDG_DR_PARAMS] domain randomization and wind, or null
-    float4* motor;            // [n] rotor speeds (the motor lag's state)
-    float4* hist;             // [hist_depth][n] actions received (the latency's shift register)
-    float4* wind;             // [n_envs][2] wind state
-    unsigned long long wind_seed;
-    int hist_depth;
     DevConsts c;
+    // after the constants, so that their offsets (and the hot kernels' code) stay put; the
+    // randomization buffers sit behind one device pointer to keep the argument block small
+    float4* setpoints;        // [n] DSL setpoints (x, y, z, yaw) or null
+    const RandArgs* rand;     // device copy of the randomization buffers, or null
 };
 
 // A multi-step rollout (persistent kernel): K control steps per launch, tiles pulled
@@ -206,11 +213,7 @@ struct mdg_ctx {
     float4* d_sp = nullptr;  // caller-owned DSL setpoints (mdg_set_setpoints)
     // caller-owned domain randomization (mdg_set_randomization); dr == nullptr: none
     const float* dr = nullptr;
-    float4* dr_motor = nullptr;
-    float4* dr_hist = nullptr;
-    float4* dr_wind = nullptr;
-    unsigned long long dr_seed = 0;
-    int dr_depth = 0;
+    mdg::RandArgs* d_rand = nullptr;  // device copy of the buffers (allocated on first attach)
     mdg::Tile* d_tiles = nullptr;
     int n_tiles = 0;
     int block = 0;

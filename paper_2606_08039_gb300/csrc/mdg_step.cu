@@ -736,13 +736,14 @@ __device__ __forceinline__ DevConsts randomized_consts(const DevConsts& c, const
 // the action received).
 __device__ __forceinline__ float4 delayed_action(const StepArgs& a, long long g, const float4 act, int delay)
 {
-    float4* h = a.hist + g;
+    float4* h = a.rand->hist + g;
+    const int depth = a.rand->depth;
     if (isnan(h[0].x)) {
-        for (int k = 0; k < a.hist_depth; ++k) h[k * a.n] = act;
+        for (int k = 0; k < depth; ++k) h[k * a.n] = act;
         return act;
     }
     float4 out = act;
-    for (int k = a.hist_depth - 1; k > 0; --k) {
+    for (int k = depth - 1; k > 0; --k) {
         const float4 v = h[(k - 1) * a.n];
         h[k * a.n] = v;
         if (k == delay) out = v;
@@ -832,17 +833,18 @@ __device__ __forceinline__ void randomized_substeps(const StepArgs& a, Drone& d,
                                                     float4* s_pos, int B, int t, long long g, bool active,
                                                     bool tile_dw, bool warp_local, int& ph)
 {
-    const float* row = a.dr + (long long)env.id * MDG_DR_PARAMS;
+    const RandArgs& R = *a.rand;
+    const float* row = R.dr + (long long)env.id * MDG_DR_PARAMS;
     __syncthreads();  // the previous control step's wind state is stored
     float4 s0 = {}, s1 = {}, ms = {};
     float cmd[4] = {0.f, 0.f, 0.f, 0.f}, lag = 0.f;
     float3 fe = {};
     DevConsts pc = a.c;
     if (active) {
-        s0 = a.wind[2LL * env.id];
-        s1 = a.wind[2LL * env.id + 1];
+        s0 = R.wind[2LL * env.id];
+        s1 = R.wind[2LL * env.id + 1];
         float Fd[3], vw[3];
-        wind_step(row, s0, s1, a.wind_seed, env.id, a.c.dt_ctrl, Fd, vw);
+        wind_step(row, s0, s1, R.seed, env.id, a.c.dt_ctrl, Fd, vw);
         const int model = (int)row[MDG_DR_WIND];
         if (model & (MDG_WIND_CONSTANT | MDG_WIND_DRYDEN)) {
             const float vr[3] = {vw[0] - d.v[0], vw[1] - d.v[1], vw[2] - d.v[2]};
@@ -858,7 +860,7 @@ __device__ __forceinline__ void randomized_substeps(const StepArgs& a, Drone& d,
         for (int i = 0; i < 4; ++i) cmd[i] = fminf(rpm[i] * row[MDG_DR_BIAS + i], sat);
         const float tau = row[MDG_DR_TAU];
         lag = tau > 0.f ? expf(-a.c.dt_sim / tau) : 0.f;
-        ms = a.motor[g];
+        ms = R.motor[g];
         if (isnan(ms.x)) ms.x = cmd[0];
         if (isnan(ms.y)) ms.y = cmd[1];
         if (isnan(ms.z)) ms.z = cmd[2];
@@ -866,8 +868,8 @@ __device__ __forceinline__ void randomized_substeps(const StepArgs& a, Drone& d,
     }
     __syncthreads();  // every drone has read the wind state
     if (active && t == env.ls) {
-        a.wind[2LL * env.id] = s0;
-        a.wind[2LL * env.id + 1] = s1;
+        R.wind[2LL * env.id] = s0;
+        R.wind[2LL * env.id + 1] = s1;
     }
     for (int s = 0; s < a.n_sub; ++s, ++ph) {
         float4* buf = s_pos + (ph & 1) * B;
@@ -885,7 +887,7 @@ __device__ __forceinline__ void randomized_substeps(const StepArgs& a, Drone& d,
             substep<kFlagsDR, kN>(d, motor(n, pc), env.flags, buf + env.ls, env.N, pc, fe);
         }
     }
-    if (active) a.motor[g] = ms;
+    if (active) R.motor[g] = ms;
 }
 
 // ---- fourth-order Runge-Kutta substeps (MDG_INTEGRATOR_RK4) ----
@@ -1044,7 +1046,7 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
     float rpm[4] = {0.f, 0.f, 0.f, 0.f};
     if (active) {
         if constexpr (kFlags == kFlagsDR)  // action latency
-            act = delayed_action(a, g, act, (int)a.dr[(long long)env.id * MDG_DR_PARAMS + MDG_DR_DELAY]);
+            act = delayed_action(a, g, act, (int)a.rand->dr[(long long)env.id * MDG_DR_PARAMS + MDG_DR_DELAY]);
         if (kFlags >= 8 && env.act >= MDG_ACT_RPM_NORM) {
             ext_action_rpm(d, act, env.act, a.c, rpm);
         } else if (is_pid) {
@@ -1229,7 +1231,7 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
             if (active && k + 1 < r.K) next = a.action[(k + 1) * r.action_stride + g];
             if (active) {
                 if constexpr (kFlags == kFlagsDR)  // action latency
-                    act = delayed_action(a, g, act, (int)a.dr[(long long)env.id * MDG_DR_PARAMS + MDG_DR_DELAY]);
+                    act = delayed_action(a, g, act, (int)a.rand->dr[(long long)env.id * MDG_DR_PARAMS + MDG_DR_DELAY]);
                 if (kFlags >= 8 && env.act >= MDG_ACT_RPM_NORM) {
                     ext_action_rpm(d, act, env.act, a.c, rpm);
                 } else if (is_pid) {
@@ -1626,7 +1628,7 @@ cudaError_t launch_step(const StepArgs& a, int n_tiles, int block, bool with_obs
     // a compile-time variant needs one physics subset and one environment size for the
     // batch; Runge-Kutta substeps have runtime-generic variants of their own
     // Runge-Kutta substeps and per-rotor ground heights run in the runtime-flag variants
-    const int flags = a.dr ? kFlagsDR : a.c.rk4 ? kFlagsRK4 : (a.c.gnd_rotor ? kFlagsGndRotor : uniform_flags);
+    const int flags = a.rand ? kFlagsDR : a.c.rk4 ? kFlagsRK4 : (a.c.gnd_rotor ? kFlagsGndRotor : uniform_flags);
     const int N = a.c.rk4 ? -1 : a.uniform_N;
     void* fn = with_obs ? step_kernel_ptr<true>(flags, N, block) : step_kernel_ptr<false>(flags, N, block);
     void* args[] = {const_cast<StepArgs*>(&a)};
@@ -1682,7 +1684,7 @@ cudaError_t launch_rollout(const RolloutArgs& r, int block, int uniform_flags, i
 {
     if (r.n_items == 0 || r.K == 0) return cudaSuccess;
     const int uniform_N = r.s.c.rk4 ? -1 : r.s.uniform_N;
-    if (r.s.dr) uniform_flags = kFlagsDR;  // randomization variants
+    if (r.s.rand) uniform_flags = kFlagsDR;  // randomization variants
     else if (r.s.c.rk4) uniform_flags = kFlagsRK4;  // Runge-Kutta variants
     else if (r.s.c.gnd_rotor) uniform_flags = kFlagsGndRotor;  // per-rotor ground heights
     cudaError_t e = rollout_setup();
