@@ -121,6 +121,31 @@ def test_planted_mistake_is_caught(name, oracle_source, tmp_path):
     assert r.returncode == 1, f"planted mistake {name} was not caught:\n{r.stdout[-2000:]}"
 
 
+# planted in oracle/camera.py, caught by tests/test_oracle_camera.py
+CAMERA_MUTATIONS = {
+    "camera_fov_horizontal": ("    nx = c * th * W / H\n", "    nx = c * th\n"),
+    "camera_euclidean_depth": ("depth = np.where(np.isfinite(t_best), t_best * (dn @ fwd), np.inf)",
+                               "depth = np.where(np.isfinite(t_best), t_best, np.inf)"),
+    "camera_light_sign": ("np.maximum(0.0, n @ LIGHT)", "np.maximum(0.0, -(n @ LIGHT))"),
+    "camera_own_drone_drawn": ("        if k == j:\n            continue\n", ""),
+    "camera_segment_id": ("seg = np.where(better, 1 + first_index + k, seg)", "seg = np.where(better, first_index + k, seg)"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CAMERA_MUTATIONS))
+def test_planted_camera_mistake_is_caught(name, tmp_path):
+    before, after = CAMERA_MUTATIONS[name]
+    src = open(os.path.join(ROOT, "oracle", "camera.py")).read()
+    assert src.count(before) == 1, f"mutation site of {name} not found exactly once"
+    shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle", ignore=shutil.ignore_patterns("_build"))
+    shutil.copytree(os.path.join(ROOT, "tests"), tmp_path / "tests",
+                    ignore=shutil.ignore_patterns("__pycache__", "test_oracle_mutations.py"))
+    (tmp_path / "oracle" / "camera.py").write_text(src.replace(before, after))
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_camera.py", "-q", "-x", "-p",
+                        "no:cacheprovider"], cwd=tmp_path, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 1, f"planted mistake {name} was not caught:\n{r.stdout[-2000:]}"
+
+
 @pytest.mark.parametrize("name", sorted(MLP_MUTATIONS))
 def test_planted_mlp_mistake_is_caught(name, tmp_path):
     before, after = MLP_MUTATIONS[name]
