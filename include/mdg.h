@@ -328,6 +328,25 @@ int mdg_pid(mdg_handle h, float* state, const float* waypoints, float* rpm_out, 
 int mdg_pid_ff(mdg_handle h, float* state, const float* waypoints, const float* target_acc, float* rpm_out,
                float* pos_err, float* yaw_err, void* stream);
 
+/* Camera frames (Section 3.4.4, the RGB observation: (48, 64, 4) uint8 from each drone's
+ * onboard camera, 60 degree field of view, at [0.02, 0, 0] in the body frame), ray cast from
+ * primitive shapes since no renderer or meshes are used. Readings: pinhole camera along body
+ * +x (image right = body -y, up = body +z), 60 degrees the vertical field of view, pixels
+ * through their cell centres, row 0 on top; the environment's other drones as oblate
+ * ellipsoids in their body frames with semi-axes (L + r_p, L + r_p, 0.3 (L + r_p)); the
+ * ground z = 0 as a 0.5 m checkerboard (greys 0.55 / 0.35) seen from above; the camera's
+ * own drone not drawn; Lambert shading ambient 0.35 + diffuse 0.65 max(0, n . l), l along
+ * (0.3, 0.2, 1); drone k coloured by an 8-entry palette (k mod 8); sky (0.55, 0.70, 0.90);
+ * channels round(255 c), alpha 255. Outputs (each may be NULL; device, 4-byte aligned):
+ *   rgba   uint8 [n_drones][MDG_CAM_H][MDG_CAM_W][4]
+ *   depth  float32 [n_drones][MDG_CAM_H][MDG_CAM_W]: distance along the optical axis to the
+ *          nearest surface beyond 1e-4 m, +inf where only sky is seen
+ *   seg    int32 [n_drones][MDG_CAM_H][MDG_CAM_W]: -1 sky, 0 ground, 1 + global drone index
+ * Errors: MDG_ERR_ARG, MDG_ERR_CUDA. */
+#define MDG_CAM_H 48
+#define MDG_CAM_W 64
+int mdg_render(mdg_handle h, const float* state, uint8_t* rgba, float* depth, int32_t* seg, void* stream);
+
 /* Observations of the current state (Section 3.4.4 KIN, and the neighbourhood
  * adjacency of the abstract):
  *   kin      device float32 [n_drones][20]: p, q, roll/pitch/yaw (ZYX), v, w, a_prev

@@ -38,6 +38,7 @@ FRAME_X, FRAME_P = 0, 1
 INTEGRATOR_EULER, INTEGRATOR_RK4 = 0, 1
 GND_COM, GND_ROTOR = 0, 1
 CTRL_PID, CTRL_DSL = 0, 1
+CAM_H, CAM_W = 48, 64
 DR_PARAMS, WIND_STATE, MAX_HIST_DEPTH = 32, 8, 16
 (DR_MASS, DR_J, DR_ARM, DR_KF, DR_KM, DR_CXY, DR_CZ, DR_CGND, DR_C1, DR_MAXRPM, DR_BIAS, DR_G, DR_TAU, DR_DELAY,
  DR_WIND, DR_VWIND, DR_KDRAG, DR_GUST_P, DR_GUST_A, DR_GUST_T, DR_DRY_SIGMA, DR_DRY_V, DR_SIN_A, DR_SIN_W,
@@ -60,6 +61,7 @@ _SIGNATURES = {
     "mdg_constants_race": ([_VP], ctypes.c_int),
     "mdg_controller_dsl": ([_VP], ctypes.c_int),
     "mdg_set_setpoints": ([_VP, _VP], ctypes.c_int),
+    "mdg_render": ([_VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "mdg_set_randomization": ([_VP, _VP, _VP, _VP, ctypes.c_int32, _VP, ctypes.c_uint64], ctypes.c_int),
     "mdg_pid_ff": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "mdg_constants_size": ([], ctypes.c_int),
@@ -429,6 +431,23 @@ class Handle:
                              _ptr(rpm_out, "rpm_out", torch.float32, (self.n, 4)),
                              _ptr(pos_err, "pos_err", torch.float32, (self.n, 3)),
                              _ptr(yaw_err, "yaw_err", torch.float32, (self.n,)), _stream(stream)))
+
+    def new_frames(self, device="cuda", rgba=True, depth=True, seg=True):
+        """(rgba uint8 [n, CAM_H, CAM_W, 4], depth float32 [n, CAM_H, CAM_W], seg int32
+        [n, CAM_H, CAM_W]) device tensors (None where not asked for)."""
+        torch = _torch()
+        shp = (self.n, CAM_H, CAM_W)
+        return (torch.empty(shp + (4,), dtype=torch.uint8, device=device) if rgba else None,
+                torch.empty(shp, dtype=torch.float32, device=device) if depth else None,
+                torch.empty(shp, dtype=torch.int32, device=device) if seg else None)
+
+    def render(self, state, rgba=None, depth=None, seg=None, stream=None):
+        """Camera frames of every drone (mdg_render); each output may be None."""
+        torch = _torch()
+        shp = (self.n, CAM_H, CAM_W)
+        _check(lib().mdg_render(self._h, _ptr(state, "state", torch.float32, (STATE_PLANES, self.n, 4)),
+                                _ptr(rgba, "rgba", torch.uint8, shp + (4,)), _ptr(depth, "depth", torch.float32, shp),
+                                _ptr(seg, "seg", torch.int32, shp), _stream(stream)))
 
     def obs(self, state, kin, nbr_idx, nbr_rel=None, stream=None):
         torch = _torch()

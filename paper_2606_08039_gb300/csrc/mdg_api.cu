@@ -571,6 +571,7 @@ int mdg_create(int32_t n_envs, const int32_t* drones_per_env, const uint32_t* mo
     h->max_env = max_env;
     h->c = cc;
     h->dc = make_dev_consts(cc);
+    h->cc = cc;
     h->h_off = off;
     h->h_flags = flags;
     h->uniform_flags = n_envs > 0 ? flags[0] : -1;
@@ -863,6 +864,35 @@ int mdg_pid(mdg_handle h, float* state, const float* waypoints, float* rpm_out, 
             void* stream)
 {
     return mdg_pid_ff(h, state, waypoints, nullptr, rpm_out, pos_err, yaw_err, stream);
+}
+
+int mdg_render(mdg_handle h, const float* state, uint8_t* rgba, float* depth, int32_t* seg, void* stream)
+{
+    if (!h) return fail(MDG_ERR_ARG, "mdg_render: NULL handle");
+    int rc;
+    if ((rc = check_state_ptr(h, state, "state")) != MDG_OK) return rc;
+    const void* outs[] = {rgba, depth, seg};
+    for (const void* o : outs)
+        if (o && (reinterpret_cast<uintptr_t>(o) & 3u)) return fail(MDG_ERR_ARG, "mdg_render: outputs must be 4-byte aligned");
+    if (h->n_drones == 0 || (!rgba && !depth && !seg)) return MDG_OK;
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return fail(MDG_ERR_CUDA, "mdg_render: cannot select device %d", h->device);
+    mdg::CamArgs a{};
+    a.state = reinterpret_cast<const float4*>(state);
+    a.n = h->n_drones;
+    a.n_envs = h->n_envs;
+    a.env_off = h->d_off;
+    a.uniform_N = h->uniform_N;
+    a.rgba = reinterpret_cast<uchar4*>(rgba);
+    a.depth = depth;
+    a.seg = seg;
+    a.semi_a = (float)(h->cc.arm + h->cc.prop_radius);
+    a.semi_c = (float)(0.3 * (h->cc.arm + h->cc.prop_radius));
+    a.max_env = h->max_env;
+    a.status = h->d_status;
+    cudaError_t e = mdg::launch_render(a, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mdg_render: launch");
+    return MDG_OK;
 }
 
 int mdg_obs(mdg_handle h, const float* state, float* kin, int32_t* nbr_idx, float* nbr_rel, void* stream)

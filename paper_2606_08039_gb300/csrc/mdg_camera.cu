@@ -1,0 +1,222 @@
+// Camera frames by ray casting (the RGB observation of Section 3.4.4: 48 x 64 frames from
+// each drone's onboard camera, 60 degree field of view, at [0.02, 0, 0] in the body frame).
+// The paper renders them with MuJoCo's OpenGL renderer and the Crazyflie meshes; here every
+// frame is ray cast in a kernel from primitive shapes:
+//   - pinhole camera along body +x, image right = body -y, image up = body +z, 60 degrees
+//     the vertical field of view, each pixel through the centre of its cell, row 0 on top;
+//   - the environment's other drones as oblate ellipsoids in their body frames, semi-axes
+//     (L + r_p, L + r_p, 0.3 (L + r_p)); the ground z = 0 as a 0.5 m checkerboard seen from
+//     above; the camera's own drone is not drawn;
+//   - Lambert shading, ambient 0.35 + diffuse 0.65 max(0, n . l), l along (0.3, 0.2, 1);
+//     ground greys 0.55 / 0.35, drone k coloured by the palette entry k mod 8, sky
+//     (0.55, 0.70, 0.90) unshaded; channels round(255 c), alpha 255;
+//   - depth along the optical axis to the nearest hit beyond 1e-4 m (+inf: sky);
+//     segmentation -1 sky, 0 ground, 1 + the global index of the drone hit.
+// One 256-thread block per camera; the block first builds, in shared memory, each drone's
+// ray transform (world direction -> the drone's scaled body frame), the camera origin in
+// that frame and the normal transform, so that a ray-ellipsoid test is ~25 flops; each
+// thread then renders 12 pixels, consecutive threads consecutive pixels (coalesced stores).
+#include "mdg_internal.cuh"
+
+namespace mdg {
+namespace {
+
+constexpr int kCamH = 48, kCamW = 64, kCamPixels = kCamH * kCamW;
+constexpr int kCamThreads = 256;
+constexpr float kTMin = 1e-4f;
+// unit light direction (0.3, 0.2, 1) / |(0.3, 0.2, 1)|
+constexpr float kLx = 0.28221626f, kLy = 0.18814417f, kLz = 0.94072087f;
+
+__constant__ float c_palette[8][3] = {{0.90f, 0.25f, 0.20f}, {0.20f, 0.70f, 0.30f}, {0.20f, 0.35f, 0.90f},
+                                      {0.95f, 0.75f, 0.15f}, {0.70f, 0.30f, 0.80f}, {0.15f, 0.75f, 0.80f},
+                                      {0.95f, 0.50f, 0.20f}, {0.60f, 0.60f, 0.65f}};
+
+// Per drone of the environment, in shared memory: O = the camera origin in the drone's
+// scaled body frame (3), M = diag(1/s) R^T (9, world ray -> scaled body ray), C = |O|^2 - 1,
+// Nm = R diag(1/s) (9, scaled body point -> world normal direction).
+constexpr int kSceneFloats = 24;
+
+struct Rot {
+    float m[9];  // row-major, body -> world
+};
+
+__device__ __forceinline__ Rot rot_of(float w, float x, float y, float z)
+{
+    Rot R;
+    R.m[0] = 1.f - 2.f * (y * y + z * z);
+    R.m[1] = 2.f * (x * y - w * z);
+    R.m[2] = 2.f * (x * z + w * y);
+    R.m[3] = 2.f * (x * y + w * z);
+    R.m[4] = 1.f - 2.f * (x * x + z * z);
+    R.m[5] = 2.f * (y * z - w * x);
+    R.m[6] = 2.f * (x * z - w * y);
+    R.m[7] = 2.f * (y * z + w * x);
+    R.m[8] = 1.f - 2.f * (x * x + y * y);
+    return R;
+}
+
+__global__ void __launch_bounds__(kCamThreads) render_kernel(const CamArgs a)
+{
+    extern __shared__ float s_scene[];  // [max_env][kSceneFloats]
+    __shared__ int s_env[2];             // first drone of the camera's environment, its size
+    __shared__ float s_cam[3];           // camera origin
+    __shared__ float s_R[9];             // the camera drone's rotation (body -> world)
+    const int t = threadIdx.x;
+    const float inv_a = 1.f / a.semi_a, inv_c = 1.f / a.semi_c;
+    const float th = 0.57735026918962576f;  // tan(30 degrees)
+    const float kInf = __int_as_float(0x7f800000);
+    for (long long cam = blockIdx.x; cam < a.n; cam += gridDim.x) {
+        __syncthreads();  // the previous camera's scene is no longer read
+        if (t == 0) {
+            int first, N;
+            if (a.uniform_N > 0) {
+                const long long e = cam / a.uniform_N;
+                first = (int)(e * a.uniform_N);
+                N = a.uniform_N;
+            } else {
+                int lo = 0, hi = a.n_envs - 1;  // largest env with env_off[env] <= cam
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (a.env_off[mid] <= cam) lo = mid;
+                    else hi = mid - 1;
+                }
+                first = a.env_off[lo];
+                N = a.env_off[lo + 1] - first;
+            }
+            if (!MDG_CHECK(N >= 1 && N <= a.max_env && cam >= first && cam < first + N, a.status)) N = 0;
+            s_env[0] = first;
+            s_env[1] = N;
+            const float4 p0 = a.state[cam], p1 = a.state[a.n + cam];
+            const Rot R = rot_of(p0.w, p1.x, p1.y, p1.z);
+            for (int i = 0; i < 9; ++i) s_R[i] = R.m[i];
+            s_cam[0] = p0.x + 0.02f * R.m[0];
+            s_cam[1] = p0.y + 0.02f * R.m[3];
+            s_cam[2] = p0.z + 0.02f * R.m[6];
+        }
+        __syncthreads();
+        const int first = s_env[0], N = s_env[1];
+        const float ox = s_cam[0], oy = s_cam[1], oz = s_cam[2];
+        for (int k = t; k < N; k += kCamThreads) {
+            const long long g = first + k;
+            const float4 p0 = a.state[g], p1 = a.state[a.n + g];
+            const Rot R = rot_of(p0.w, p1.x, p1.y, p1.z);
+            const float inv_s[3] = {inv_a, inv_a, inv_c};
+            const float dx = ox - p0.x, dy = oy - p0.y, dz = oz - p0.z;
+            float* sc = s_scene + k * kSceneFloats;
+            float C = -1.f;
+            for (int r = 0; r < 3; ++r) {
+                // row r of R^T is column r of R
+                const float O = (R.m[r] * dx + R.m[3 + r] * dy + R.m[6 + r] * dz) * inv_s[r];
+                sc[r] = O;
+                C += O * O;
+                sc[3 + 3 * r + 0] = R.m[r] * inv_s[r];
+                sc[3 + 3 * r + 1] = R.m[3 + r] * inv_s[r];
+                sc[3 + 3 * r + 2] = R.m[6 + r] * inv_s[r];
+            }
+            sc[12] = C;
+            for (int r = 0; r < 3; ++r)
+                for (int q = 0; q < 3; ++q) sc[13 + 3 * r + q] = R.m[3 * r + q] * inv_s[q];
+            sc[22] = __int_as_float((int)(g + 1));  // segment id
+        }
+        __syncthreads();
+        if (N == 0) continue;
+        const int own = (int)(cam - first);
+        const float fx = s_R[0], fy = s_R[3], fz = s_R[6];  // optical axis (body +x in world)
+        for (int p = t; p < kCamPixels; p += kCamThreads) {
+            const int row = p / kCamW, col = p % kCamW;
+            const float nx = ((col + 0.5f) * (2.f / kCamW) - 1.f) * (th * kCamW / kCamH);
+            const float ny = (1.f - (row + 0.5f) * (2.f / kCamH)) * th;
+            // world direction of the body ray (1, -nx, ny), normalised
+            float d0 = s_R[0] - nx * s_R[1] + ny * s_R[2];
+            float d1 = s_R[3] - nx * s_R[4] + ny * s_R[5];
+            float d2 = s_R[6] - nx * s_R[7] + ny * s_R[8];
+            const float inv = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+            d0 *= inv;
+            d1 *= inv;
+            d2 *= inv;
+            float t_best = kInf;
+            int hit = -1;  // -1 sky, -2 ground, else the drone slot
+            if (oz > 0.f && d2 < 0.f) {
+                const float tg = -oz / d2;
+                if (tg > kTMin) {
+                    t_best = tg;
+                    hit = -2;
+                }
+            }
+            for (int k = 0; k < N; ++k) {
+                if (k == own) continue;
+                const float* sc = s_scene + k * kSceneFloats;
+                const float D0 = sc[3] * d0 + sc[4] * d1 + sc[5] * d2;
+                const float D1 = sc[6] * d0 + sc[7] * d1 + sc[8] * d2;
+                const float D2 = sc[9] * d0 + sc[10] * d1 + sc[11] * d2;
+                const float A = D0 * D0 + D1 * D1 + D2 * D2;
+                const float B = 2.f * (D0 * sc[0] + D1 * sc[1] + D2 * sc[2]);
+                const float disc = B * B - 4.f * A * sc[12];
+                if (disc < 0.f) continue;
+                const float sq = sqrtf(disc), i2a = 0.5f / A;
+                const float t1 = (-B - sq) * i2a, t2 = (-B + sq) * i2a;
+                const float tk = t1 > kTMin ? t1 : (t2 > kTMin ? t2 : kInf);
+                if (tk < t_best) {
+                    t_best = tk;
+                    hit = k;
+                }
+            }
+            float r = 0.55f, gcol = 0.70f, b = 0.90f;  // sky
+            int seg = -1;
+            if (hit == -2) {
+                const float px = ox + t_best * d0, py = oy + t_best * d1;
+                const int par = ((int)floorf(px * 2.f) + (int)floorf(py * 2.f)) & 1;
+                const float shade = 0.35f + 0.65f * kLz;  // normal +z
+                const float grey = par ? 0.35f : 0.55f;
+                r = gcol = b = grey * shade;
+                seg = 0;
+            } else if (hit >= 0) {
+                const float* sc = s_scene + hit * kSceneFloats;
+                const float D0 = sc[3] * d0 + sc[4] * d1 + sc[5] * d2;
+                const float D1 = sc[6] * d0 + sc[7] * d1 + sc[8] * d2;
+                const float D2 = sc[9] * d0 + sc[10] * d1 + sc[11] * d2;
+                const float P0 = sc[0] + t_best * D0, P1 = sc[1] + t_best * D1, P2 = sc[2] + t_best * D2;
+                float n0 = sc[13] * P0 + sc[14] * P1 + sc[15] * P2;
+                float n1 = sc[16] * P0 + sc[17] * P1 + sc[18] * P2;
+                float n2 = sc[19] * P0 + sc[20] * P1 + sc[21] * P2;
+                const float in = rsqrtf(fmaxf(n0 * n0 + n1 * n1 + n2 * n2, 1e-30f));
+                const float nl = (n0 * kLx + n1 * kLy + n2 * kLz) * in;
+                const float shade = 0.35f + 0.65f * fmaxf(0.f, nl);
+                const int id = __float_as_int(sc[22]);
+                const int pc = (id - 1) & 7;
+                r = c_palette[pc][0] * shade;
+                gcol = c_palette[pc][1] * shade;
+                b = c_palette[pc][2] * shade;
+                seg = id;
+            }
+            const long long o = cam * kCamPixels + p;
+            if (a.rgba) {
+                const int R8 = __float2int_rn(255.f * fminf(1.f, fmaxf(0.f, r)));
+                const int G8 = __float2int_rn(255.f * fminf(1.f, fmaxf(0.f, gcol)));
+                const int B8 = __float2int_rn(255.f * fminf(1.f, fmaxf(0.f, b)));
+                a.rgba[o] = make_uchar4((unsigned char)R8, (unsigned char)G8, (unsigned char)B8, 255);
+            }
+            if (a.depth) a.depth[o] = hit == -1 ? kInf : t_best * (d0 * fx + d1 * fy + d2 * fz);
+            if (a.seg) a.seg[o] = seg;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_render(const CamArgs& a, cudaStream_t s)
+{
+    if (a.n == 0) return cudaSuccess;
+    const int smem = a.max_env * kSceneFloats * (int)sizeof(float);
+    static int opted = 0;
+    if (smem > 48 * 1024 && smem > opted) {
+        cudaError_t e = cudaFuncSetAttribute(render_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        opted = smem;
+    }
+    const long long grid = a.n < 152LL * 64 ? a.n : 152LL * 64;
+    render_kernel<<<(unsigned)grid, kCamThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace mdg

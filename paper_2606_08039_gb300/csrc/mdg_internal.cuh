@@ -158,6 +158,22 @@ int default_block(int32_t max_env, int64_t n_drones, int n_sm);
 
 cudaError_t launch_step(const StepArgs& a, int n_tiles, int block, bool with_obs, int uniform_flags, cudaStream_t s);
 
+// Camera frames (mdg_render).
+struct CamArgs {
+    const float4* state;     // [6][n] planes (positions and attitudes read)
+    long long n;
+    int n_envs;
+    const int32_t* env_off;  // [n_envs + 1]
+    int uniform_N;           // > 0: every environment has this many drones
+    uchar4* rgba;            // [n][48 * 64] or null
+    float* depth;            // [n][48 * 64] or null
+    int* seg;                // [n][48 * 64] or null
+    float semi_a, semi_c;    // the drones' ellipsoid semi-axes (a, a, c)
+    int max_env;             // drones of the largest environment (shared-memory size)
+    uint32_t* status;        // debug builds: MDG_STATUS_BOUNDS
+};
+cudaError_t launch_render(const CamArgs& a, cudaStream_t s);
+
 // The step-kernel variant that runs under domain randomization (mdg_set_randomization).
 constexpr int kVariantRandomized = 11;
 
@@ -203,6 +219,7 @@ struct mdg_ctx {
     int32_t max_env = 0;
     mdg_constants c{};
     mdg::DevConsts dc{};
+    mdg_constants cc{};  // the constants as given (host)
     std::vector<int32_t> h_off;
     std::vector<uint8_t> h_flags;
     int32_t* d_off = nullptr;

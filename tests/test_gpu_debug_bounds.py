@@ -9,7 +9,7 @@ in a separate process that loads it, runs every kernel family on the workloads o
 parity suite (uniform and table tiles, compile-time and runtime environment sizes, the
 persistent rollout, observations, PID, surrogate features, preparation, application and
 the fallback pass, the allocation-free entry point, the RK4 and per-rotor ground-height
-variants, every action type, randomization); no check may fail.
+variants, every action type, randomization, the camera); no check may fail.
 """
 import ctypes
 import os
@@ -71,6 +71,9 @@ def _run():
             h.rollout(st, acts, mdg.ACT_MIXED, 5, 3, mdg.OBS_EVERY_STEP, kin3, idx3, rel3)
             check(h, f"{name} rollout block {block}")
         h.obs(st, kin, idx, rel)
+        frames = h.new_frames(dev)
+        h.render(st, *frames)
+        check(h, f"{name} render")
         rpm = torch.empty((sw.n, 4), device=dev)
         h.pid(st, torch.as_tensor(wl.waypoints(87, sw.n), device=dev), rpm)
         check(h, f"{name} obs/pid")
