@@ -56,7 +56,7 @@ BYTES_PER_DRONE_STEP = STATE_BYTES_READ + ACTION_BYTES + STATE_BYTES_WRITE + OBS
 # DRAM traffic of one step-kernel launch on the full-aero workload, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel source whose
 # sha256 prefix is recorded with it; profiles/ holds the capture's summary.
-NCU_TRAFFIC = {"kernel_sha": "de4f8370f7563eac", "bytes": 6331648 + 512}
+NCU_TRAFFIC = {"kernel_sha": "e812ebd5d0276a43", "bytes": 6331648 + 256}
 
 
 def kernel_sha() -> str:
@@ -509,6 +509,98 @@ def run_other(args) -> None:
     print(json.dumps(out))
 
 
+# Camera frames (mdg_render): the frames themselves (RGBA, depth and segment, 12 B per pixel)
+# are the algorithmic bytes, and the roofline is HBM. The brute-force arithmetic, counted from
+# the oracle's ray caster (ray generation 25 flops per pixel, ground 15, shading and outputs
+# 30, and 30 per other drone of the environment), is reported beside it as an upper bound:
+# the kernel tests a drone only where its screen rectangle covers the pixels.
+FLOPS_PIXEL_BASE, FLOPS_PIXEL_PAIR = 70, 30
+CAM_PIXELS = 48 * 64
+CAM_BYTES_PER_FRAME = CAM_PIXELS * (4 + 4 + 4) + 32  # RGBA, depth, segment; the camera drone's pose
+
+
+def run_camera(args) -> None:
+    """Camera frames of the full-aero swarm (16384 envs x 4 drones): one step renders every
+    drone's 48 x 64 RGBA, depth and segmentation frame (one mdg_render launch, 2.4 GB of
+    frames), L2 flushed between steps."""
+    import torch
+    import paper_2606_08039_gb300 as mdg
+    from paper_2606_08039_gb300 import workloads as wl
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    sw = wl.full_aero(1, n_envs=args.envs or 16384)
+    h = mdg.Handle(sw.drones_per_env, sw.flags)
+    state = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=dev)
+    rgba, depth, seg = h.new_frames(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    sink = torch.empty((), dtype=torch.float32, device=dev)
+
+    def timed(n):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for a, b in ev:
+            flush.fill_(1.0)
+            torch.sum(flush, dim=0, out=sink)
+            a.record(stream)
+            h.render(state, rgba, depth, seg, stream=stream)
+            b.record(stream)
+        torch.cuda.synchronize()
+        return float(sum(a.elapsed_time(b) for a, b in ev))
+
+    steps = min(args.steps, 500)
+    timed(args.warmup)
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    total_ms = timed(steps)
+    clk = clocks.stop()
+    ms = total_ms / steps
+    N = sw.drones_per_env.astype(np.float64)
+    flops = float(np.sum(N * CAM_PIXELS * (FLOPS_PIXEL_BASE + FLOPS_PIXEL_PAIR * (N - 1))))
+    nbytes = sw.n * CAM_BYTES_PER_FRAME
+    peaks = measured_peaks()
+    roof = binding_roofline(nbytes, 0.0, ms * 1e-3, peaks)
+    roof.pop("other_bound", None)
+    roof["brute_force_flops_per_launch"] = flops
+    roof["kernel"] = "render_kernel"
+    out = {
+        "metric": "camera frames/s on 1 GB300 (48x64 RGBA + depth + segmentation, FP32 ray casting vs oracle)",
+        "value": sw.n / (ms * 1e-3), "unit": "frames/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"camera: every drone of the full-aero swarm ({sw.n_envs} envs x 4), one mdg_render per step",
+                   "n_frames": sw.n, "l2": "flushed between timed steps (512 MiB written, then read back)"},
+        "pixels_per_s": sw.n * CAM_PIXELS / (ms * 1e-3),
+        "gpu_launches": steps, "roofline": roof, "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = camera_cpu_baseline()
+    print(json.dumps(out))
+
+
+def camera_cpu_baseline(seconds_target: float = 10.0) -> dict:
+    """The FP64 oracle's ray caster, as it stands, on the full-aero swarm's cameras, for as
+    many frames as fit in about `seconds_target` seconds on one host core."""
+    import oracle
+    from oracle import camera
+    from paper_2606_08039_gb300 import workloads as wl
+    P = oracle.cf2x()
+    sw = wl.full_aero(1, n_envs=4096)
+    x = sw.x13()
+    frames = 0
+    t0 = time.perf_counter()
+    while True:
+        e, j = divmod(frames, 4)
+        camera.render(P, x[4 * e:4 * e + 4], j, first_index=4 * e)
+        frames += 1
+        dt = time.perf_counter() - t0
+        if dt >= seconds_target or frames >= 4 * 4096:
+            break
+    return {"value": frames / dt, "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": f"{frames} frames of the full-aero swarm's cameras, FP64 numpy, single thread ({dt:.1f} s)"}
+
+
 def run_mlp(args) -> None:
     """The surrogate network's inference kernels alone: 262144 rows (the 65536 x 4 swarm),
     initial weights, bf16 inputs; the fused tcgen05 kernel (the step's path) and, for
@@ -682,7 +774,8 @@ def main() -> None:
     ap.add_argument("--impl", default="mdg", choices=["mdg", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="full_aero", choices=["full_aero", "uneven", "dense", "single", "surrogate", "mlp"],
+    ap.add_argument("--workload", default="full_aero",
+                    choices=["full_aero", "uneven", "dense", "single", "surrogate", "mlp", "camera"],
                     help="full_aero (default, the headline line); the others measure the other swarms")
     ap.add_argument("--model", default="cf2x", choices=["cf2x", "cf2p", "race"])
     ap.add_argument("--integrator", default="euler", choices=["euler", "rk4"])
@@ -690,6 +783,7 @@ def main() -> None:
     ap.add_argument("--actions", default="pid", choices=sorted(ACTION_CHOICES),
                     help="full_aero: the action type of every environment, or mixed (all six types)")
     ap.add_argument("--controller", default="pid", choices=["pid", "dsl"])
+    ap.add_argument("--envs", type=int, default=0, help="camera: environments rendered (default 16384, the swarm's size)")
     ap.add_argument("--randomize", action="store_true",
                     help="full_aero: domain randomization from the recommended ranges, motor lag, latency, wind")
     args = ap.parse_args()
@@ -698,7 +792,7 @@ def main() -> None:
     if args.impl == "reference":
         run_reference(args)
         return
-    if args.workload in ("surrogate", "mlp") and not is_default_model(args):
+    if args.workload in ("surrogate", "mlp", "camera") and not is_default_model(args):
         ap.error("--model/--integrator/--gnd-heights/--actions/--controller apply to the dynamics workloads only")
     if args.workload != "full_aero" and ((args.actions, args.controller) != ("pid", "pid") or args.randomize):
         ap.error("--actions/--controller/--randomize apply to the full_aero workload")
@@ -709,6 +803,9 @@ def main() -> None:
         return
     if args.workload == "mlp":
         run_mlp(args)
+        return
+    if args.workload == "camera":
+        run_camera(args)
         return
     if args.workload != "full_aero":
         run_other(args)

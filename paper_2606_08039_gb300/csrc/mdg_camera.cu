@@ -12,17 +12,21 @@
 //     (0.55, 0.70, 0.90) unshaded; channels round(255 c), alpha 255;
 //   - depth along the optical axis to the nearest hit beyond 1e-4 m (+inf: sky);
 //     segmentation -1 sky, 0 ground, 1 + the global index of the drone hit.
-// One 256-thread block per camera; the block first builds, in shared memory, each drone's
+// One 128-thread block per camera; the block first builds, in shared memory, each drone's
 // ray transform (world direction -> the drone's scaled body frame), the camera origin in
-// that frame and the normal transform, so that a ray-ellipsoid test is ~25 flops; each
-// thread then renders 12 pixels, consecutive threads consecutive pixels (coalesced stores).
+// that frame, the normal transform and the drone's screen rectangle, and then for each
+// 32-pixel segment (half a row: one warp's pixels) the mask of drones whose rectangles it
+// meets; a pixel pays a ~25-flop ray-ellipsoid test only for the drones of its segment's
+// mask (above 64 drones per environment, the rectangles are tested per drone); each thread
+// renders 24 pixels, consecutive threads consecutive pixels (coalesced stores). Small blocks
+// keep eight cameras in flight per SM, so that one camera's setup overlaps others' pixels.
 #include "mdg_internal.cuh"
 
 namespace mdg {
 namespace {
 
 constexpr int kCamH = 48, kCamW = 64, kCamPixels = kCamH * kCamW;
-constexpr int kCamThreads = 256;
+constexpr int kCamThreads = 128;
 constexpr float kTMin = 1e-4f;
 // unit light direction (0.3, 0.2, 1) / |(0.3, 0.2, 1)|
 constexpr float kLx = 0.28221626f, kLy = 0.18814417f, kLz = 0.94072087f;
@@ -33,8 +37,13 @@ __constant__ float c_palette[8][3] = {{0.90f, 0.25f, 0.20f}, {0.20f, 0.70f, 0.30
 
 // Per drone of the environment, in shared memory: O = the camera origin in the drone's
 // scaled body frame (3), M = diag(1/s) R^T (9, world ray -> scaled body ray), C = |O|^2 - 1,
-// Nm = R diag(1/s) (9, scaled body point -> world normal direction).
-constexpr int kSceneFloats = 24;
+// Nm = R diag(1/s) (9, scaled body point -> world normal direction), its segment id, and the
+// pixel rectangle [r0, r1] x [c0, c1] outside which no ray can meet it (the projection of
+// its oriented bounding box, half-extents (a, a, c) along its body axes, padded by a pixel;
+// empty when its bounding cube of half-width a lies behind the camera or beyond a side plane
+// of the view frustum, or for the camera's own drone; the whole image when the cube
+// straddles the image plane inside the frustum).
+constexpr int kSceneFloats = 27;
 
 struct Rot {
     float m[9];  // row-major, body -> world
@@ -59,6 +68,7 @@ __global__ void __launch_bounds__(kCamThreads) render_kernel(const CamArgs a)
 {
     extern __shared__ float s_scene[];  // [max_env][kSceneFloats]
     __shared__ int s_env[2];             // first drone of the camera's environment, its size
+    __shared__ unsigned long long s_mask[kCamPixels / 32];  // per 32-pixel segment: drones it may see (N <= 64)
     __shared__ float s_cam[3];           // camera origin
     __shared__ float s_R[9];             // the camera drone's rotation (body -> world)
     const int t = threadIdx.x;
@@ -96,6 +106,7 @@ __global__ void __launch_bounds__(kCamThreads) render_kernel(const CamArgs a)
         __syncthreads();
         const int first = s_env[0], N = s_env[1];
         const float ox = s_cam[0], oy = s_cam[1], oz = s_cam[2];
+        const int own_k = (int)(cam - first);
         for (int k = t; k < N; k += kCamThreads) {
             const long long g = first + k;
             const float4 p0 = a.state[g], p1 = a.state[a.n + g];
@@ -117,35 +128,109 @@ __global__ void __launch_bounds__(kCamThreads) render_kernel(const CamArgs a)
             for (int r = 0; r < 3; ++r)
                 for (int q = 0; q < 3; ++q) sc[13 + 3 * r + q] = R.m[3 * r + q] * inv_s[q];
             sc[22] = __int_as_float((int)(g + 1));  // segment id
+            // screen rectangle: the drone's centre in the camera drone's body frame
+            const float ex = p0.x - ox, ey = p0.y - oy, ez = p0.z - oz;
+            const float X = s_R[0] * ex + s_R[3] * ey + s_R[6] * ez;
+            const float Y = s_R[1] * ex + s_R[4] * ey + s_R[7] * ez;
+            const float Z = s_R[2] * ex + s_R[5] * ey + s_R[8] * ez;
+            const float rho = a.semi_a;
+            int r0 = 0, r1 = kCamH - 1, c0 = 0, c1 = kCamW - 1;
+            // outside the view frustum: behind the camera, or beyond one of its four side
+            // planes |nx| <= hx, |ny| <= hy (padded by two pixels); for a linear test the cube's
+            // worst corner is the centre's value minus rho times the sum of |coefficients|
+            const float hx = th * kCamW / kCamH * (1.f + 4.f / kCamW), hy = th * (1.f + 4.f / kCamH);
+            const bool unseen = X + rho < 0.f || (-Y - hx * X) - rho * (1.f + hx) > 0.f ||
+                                (Y - hx * X) - rho * (1.f + hx) > 0.f || (Z - hy * X) - rho * (1.f + hy) > 0.f ||
+                                (-Z - hy * X) - rho * (1.f + hy) > 0.f;
+            if (unseen) {
+                r0 = 1, r1 = 0;  // empty
+            } else if (X - rho > 1e-3f) {
+                // the corners of the drone's own bounding box, half-extents (a, a, c) along its
+                // body axes, in the camera drone's body frame: G = R_cam^T R_k (column q = the
+                // drone's axis q) scaled by the half-extent
+                float G[9];
+                for (int r = 0; r < 3; ++r)
+                    for (int q = 0; q < 3; ++q)
+                        G[3 * r + q] = (s_R[r] * R.m[q] + s_R[3 + r] * R.m[3 + q] + s_R[6 + r] * R.m[6 + q]) *
+                                       (q == 2 ? a.semi_c : a.semi_a);
+                float nx_lo = 1e30f, nx_hi = -1e30f, ny_lo = 1e30f, ny_hi = -1e30f;
+                for (int corner = 0; corner < 8; ++corner) {
+                    const float sx = (corner & 1) ? 1.f : -1.f, sy = (corner & 2) ? 1.f : -1.f;
+                    const float sz = (corner & 4) ? 1.f : -1.f;
+                    const float cx = X + sx * G[0] + sy * G[1] + sz * G[2];
+                    const float cy = Y + sx * G[3] + sy * G[4] + sz * G[5];
+                    const float cz = Z + sx * G[6] + sy * G[7] + sz * G[8];
+                    const float ic = __fdividef(1.f, cx);  // the rectangle's padding covers its error
+                    const float nxc = -cy * ic, nyc = cz * ic;
+                    nx_lo = fminf(nx_lo, nxc);
+                    nx_hi = fmaxf(nx_hi, nxc);
+                    ny_lo = fminf(ny_lo, nyc);
+                    ny_hi = fmaxf(ny_hi, nyc);
+                }
+                // col = ((nx / (th W/H)) + 1) W/2 - 0.5, row = (1 - ny / th) H/2 - 0.5
+                const float kx = 0.5f * kCamW / (th * kCamW / kCamH), ky = 0.5f * kCamH / th;
+                c0 = max(0, (int)floorf((nx_lo * kx + 0.5f * kCamW - 0.5f)) - 1);
+                c1 = min(kCamW - 1, (int)ceilf((nx_hi * kx + 0.5f * kCamW - 0.5f)) + 1);
+                r0 = max(0, (int)floorf((0.5f * kCamH - ny_hi * ky - 0.5f)) - 1);
+                r1 = min(kCamH - 1, (int)ceilf((0.5f * kCamH - ny_lo * ky - 0.5f)) + 1);
+            }
+            if (k == own_k) r0 = 1, r1 = 0;  // the camera's own drone: empty
+            sc[23] = __int_as_float(r0);
+            sc[24] = __int_as_float(r1);
+            sc[25] = __int_as_float(c0);
+            sc[26] = __int_as_float(c1);
         }
         __syncthreads();
         if (N == 0) continue;
-        const int own = (int)(cam - first);
-        const float fx = s_R[0], fy = s_R[3], fz = s_R[6];  // optical axis (body +x in world)
+        // per 32-pixel segment (half a row, one warp's pixels), the drones whose screen
+        // rectangles it meets
+        if (N <= 64) {
+            for (int sgm = t; sgm < kCamPixels / 32; sgm += kCamThreads) {
+                const int row = sgm >> 1, sc0 = (sgm & 1) * 32, sc1 = sc0 + 31;
+                unsigned long long m = 0;
+                for (int k = 0; k < N; ++k) {
+                    const float* sc = s_scene + k * kSceneFloats;
+                    const bool meets = row >= __float_as_int(sc[23]) && row <= __float_as_int(sc[24]) &&
+                                       sc1 >= __float_as_int(sc[25]) && sc0 <= __float_as_int(sc[26]);
+                    m |= (unsigned long long)meets << k;
+                }
+                s_mask[sgm] = m;
+            }
+            __syncthreads();
+        }
         for (int p = t; p < kCamPixels; p += kCamThreads) {
             const int row = p / kCamW, col = p % kCamW;
             const float nx = ((col + 0.5f) * (2.f / kCamW) - 1.f) * (th * kCamW / kCamH);
             const float ny = (1.f - (row + 0.5f) * (2.f / kCamH)) * th;
-            // world direction of the body ray (1, -nx, ny), normalised
-            float d0 = s_R[0] - nx * s_R[1] + ny * s_R[2];
-            float d1 = s_R[3] - nx * s_R[4] + ny * s_R[5];
-            float d2 = s_R[6] - nx * s_R[7] + ny * s_R[8];
-            const float inv = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-            d0 *= inv;
-            d1 *= inv;
-            d2 *= inv;
+            // world direction of the body ray (1, -nx, ny), not normalised: its component along
+            // the optical axis is 1, so the ray parameter t of a hit is its depth along the axis
+            // (the minimum distance 1e-4 m is then taken along that axis)
+            const float d0 = s_R[0] - nx * s_R[1] + ny * s_R[2];
+            const float d1 = s_R[3] - nx * s_R[4] + ny * s_R[5];
+            const float d2 = s_R[6] - nx * s_R[7] + ny * s_R[8];
             float t_best = kInf;
             int hit = -1;  // -1 sky, -2 ground, else the drone slot
             if (oz > 0.f && d2 < 0.f) {
-                const float tg = -oz / d2;
+                const float tg = -oz * __frcp_rn(d2);
                 if (tg > kTMin) {
                     t_best = tg;
                     hit = -2;
                 }
             }
+            // a warp covers 32 pixels of one row: its candidates are the segment's mask (the same
+            // for all its lanes); above 64 drones, the rectangles are tested per drone
+            const int wc0 = col & ~31, wc1 = wc0 + 31;
+            unsigned long long cand = N <= 64 ? s_mask[p >> 5] : ~0ull;
             for (int k = 0; k < N; ++k) {
-                if (k == own) continue;
+                if (N <= 64) {
+                    if (!cand) break;
+                    k = __ffsll((long long)cand) - 1;
+                    cand &= cand - 1;
+                }
                 const float* sc = s_scene + k * kSceneFloats;
+                if (N > 64 && (row < __float_as_int(sc[23]) || row > __float_as_int(sc[24]) ||
+                               wc1 < __float_as_int(sc[25]) || wc0 > __float_as_int(sc[26])))
+                    continue;  // outside the drone's screen rectangle (also: the camera's own drone)
                 const float D0 = sc[3] * d0 + sc[4] * d1 + sc[5] * d2;
                 const float D1 = sc[6] * d0 + sc[7] * d1 + sc[8] * d2;
                 const float D2 = sc[9] * d0 + sc[10] * d1 + sc[11] * d2;
@@ -191,12 +276,12 @@ __global__ void __launch_bounds__(kCamThreads) render_kernel(const CamArgs a)
             }
             const long long o = cam * kCamPixels + p;
             if (a.rgba) {
-                const int R8 = __float2int_rn(255.f * fminf(1.f, fmaxf(0.f, r)));
-                const int G8 = __float2int_rn(255.f * fminf(1.f, fmaxf(0.f, gcol)));
-                const int B8 = __float2int_rn(255.f * fminf(1.f, fmaxf(0.f, b)));
+                const int R8 = __float2int_rn(255.f * __saturatef(r));
+                const int G8 = __float2int_rn(255.f * __saturatef(gcol));
+                const int B8 = __float2int_rn(255.f * __saturatef(b));
                 a.rgba[o] = make_uchar4((unsigned char)R8, (unsigned char)G8, (unsigned char)B8, 255);
             }
-            if (a.depth) a.depth[o] = hit == -1 ? kInf : t_best * (d0 * fx + d1 * fy + d2 * fz);
+            if (a.depth) a.depth[o] = t_best;  // +inf for sky
             if (a.seg) a.seg[o] = seg;
         }
     }

@@ -4,8 +4,10 @@ Every pixel the oracle does not mark ambiguous (oracle.camera.ambiguous: a decis
 the relative margin a float32 ray caster may flip) must have the oracle's segment id
 exactly, its depth within 1e-5 relative (+inf for sky on both sides; a ground hit's depth
 -o_z / d_z amplifies a float32 error of the ray direction by 1/|d_z|, so ground pixels take
-1e-5 + 1e-6 / |d_z|) and its RGB within one step per channel (round(255 c) of a float and a
-double shade); an ambiguous pixel must
+1e-5 + 1e-6 / |d_z|; a ray-ellipsoid hit's depth amplifies the error of its discriminant by
+about 1/(2 sqrt(m)), m = |disc| / B^2 its grazing margin, so drone pixels take
+1e-5 + 1e-6 / sqrt(m)) and its RGB within one step per channel (round(255 c) of a float and
+a double shade); an ambiguous pixel must
 carry one of the ids it could show (sky, ground or a drone of its environment).
 """
 import numpy as np
@@ -41,7 +43,8 @@ def _check(h, x, dpe, rgba, depth, seg, cams=None, what=""):
         zg, zr = depth[g][ok].astype(np.float64), zo[ok]
         assert np.array_equal(np.isinf(zg), np.isinf(zr)), tag
         fin = np.isfinite(zr)
-        rtol = 1e-5 + np.where(so[ok] == 0, 1e-6 / np.maximum(m["horizon"][ok], 1e-12), 0.0)
+        rtol = 1e-5 + np.where(so[ok] == 0, 1e-6 / np.maximum(m["horizon"][ok], 1e-12),
+                               np.where(so[ok] > 0, 1e-6 / np.sqrt(np.maximum(m["grazing"][ok], 1e-12)), 0.0))
         rel = np.abs(zg[fin] - zr[fin]) / np.abs(zr[fin])
         assert np.all(rel <= rtol[fin]), f"{tag}: depth off by {np.max(rel / rtol[fin]):.3g} x the tolerance"
         diff = np.abs(rgba[g][ok].astype(int) - ro[ok].astype(int))
