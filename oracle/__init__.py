@@ -32,12 +32,13 @@ FRAME_X, FRAME_P = 0, 1
 EULER, RK4 = 0, 1
 GND_COM, GND_ROTOR = 0, 1
 CTRL_PID, CTRL_DSL = 0, 1
-DR_PARAMS, WIND_STATE = 32, 8
+DR_PARAMS, WIND_STATE = 40, 8
 (DR_MASS, DR_J, DR_ARM, DR_KF, DR_KM, DR_CXY, DR_CZ, DR_CGND, DR_C1, DR_MAXRPM, DR_BIAS, DR_G, DR_TAU, DR_DELAY,
  DR_WIND, DR_VWIND, DR_KDRAG, DR_GUST_P, DR_GUST_A, DR_GUST_T, DR_DRY_SIGMA, DR_DRY_V, DR_SIN_A, DR_SIN_W,
  DR_DRY_H) = (0, 1, 4, 5, 6, 7, 8, 9, 10, 11, 12, 16, 17, 18, 19, 20, 23, 24, 25, 26, 27, 28, 29, 30, 31)
+DR_NOISE_P, DR_NOISE_V, DR_NOISE_RPY, DR_NOISE_W, DR_OBS_DELAY = 32, 33, 34, 35, 36
 WIND_CONSTANT, WIND_GUST, WIND_DRYDEN, WIND_SINUSOIDAL = 1, 2, 4, 8
-STREAM_WIND = 21
+STREAM_WIND, STREAM_OBS = 21, 22
 
 
 class _DR(ctypes.Structure):

@@ -65,7 +65,7 @@
  * and wind (Section 3.5, "Wind and turbulence"): one row of ORC_DR_PARAMS values per
  * environment. Multiplicative factors scale the model the physics integrates; the
  * controller keeps the nominal model (it does not know the draw). */
-#define ORC_DR_PARAMS 32
+#define ORC_DR_PARAMS 40
 #define ORC_DR_MASS 0      /* x m */
 #define ORC_DR_J 1         /* x Jxx, Jyy, Jzz (1..3) */
 #define ORC_DR_ARM 4       /* x L */
@@ -91,12 +91,18 @@
 #define ORC_DR_SIN_A 29    /* sinusoidal amplitude A [N] */
 #define ORC_DR_SIN_W 30    /* sinusoidal angular frequency [rad/s] */
 #define ORC_DR_DRY_H 31    /* Dryden reference altitude h [m] */
+#define ORC_DR_NOISE_P 32  /* observation noise: position sigma [m] */
+#define ORC_DR_NOISE_V 33  /* velocity sigma [m/s] */
+#define ORC_DR_NOISE_RPY 34 /* roll, pitch, yaw sigma [rad] */
+#define ORC_DR_NOISE_W 35  /* gyro (body rate) sigma [rad/s] */
+#define ORC_DR_OBS_DELAY 36 /* sensor latency [control steps]: 0 or 1 */
 #define ORC_WIND_CONSTANT 1
 #define ORC_WIND_GUST 2
 #define ORC_WIND_DRYDEN 4
 #define ORC_WIND_SINUSOIDAL 8
 #define ORC_WIND_STATE 8   /* per environment: Dryden x (3), gust phase s (-1 idle), gust direction (3), steps */
 #define ORC_STREAM_WIND 21 /* random stream of the wind draws */
+#define ORC_STREAM_OBS 22  /* random stream of the observation noise */
 
 /* Model parameters. Field order is the oracle's own; the Python side of the
  * oracle mirrors it. */
@@ -1011,6 +1017,13 @@ void orc_wind_step(const orc_params* P, const double* dr, double* ws, uint64_t s
  *   substep every rotor speed relaxes towards its command, n <- c + (n - c) exp(-dt/tau)
  *   (exact for a first-order lag under a constant command; tau = 0: n = c), and the
  *   substep integrates the environment's randomized model with these speeds.
+ *   Observations under dr (the sensor group of the randomization table): with a sensor
+ *   delay of one control step the KIN observation reports the state and the RPMs of the
+ *   last step's start; KIN positions, roll/pitch/yaw, velocities and body rates get
+ *   Gaussian noise of the row's sigmas, drawn from the counters (seed, ORC_STREAM_OBS, the
+ *   environment's wind step of the last step, drone, component 0..11; Box-Muller on the
+ *   pairs (0, 1), ..., (10, 11): position 0-2, rpy 3-5, velocity 6-8, body rate 9-11); the
+ *   neighbour observation is not delayed and carries no noise.
  * Returns 0, or -1 on a bad argument. */
 typedef struct {
     const double* env_dr;
@@ -1040,8 +1053,13 @@ int orc_control_steps(const orc_params* P, int n_envs, const int32_t* env_off, c
         for (int e = 0; e < n_envs; ++e) {
             const double d = dr->env_dr[(size_t)e * ORC_DR_PARAMS + ORC_DR_DELAY];
             if (!(d >= 0.0) || d != floor(d) || d >= dr->depth) return -1;
+            const double od = dr->env_dr[(size_t)e * ORC_DR_PARAMS + ORC_DR_OBS_DELAY];
+            if (od != 0.0 && od != 1.0) return -1;
         }
     }
+    /* the state and RPMs at the last step's start, for delayed observations */
+    double* x_last = (dr && kin) ? (double*)malloc(sizeof(double) * 13 * (size_t)(n > 0 ? n : 1)) : NULL;
+    double* a_last = (dr && kin) ? (double*)malloc(sizeof(double) * 4 * (size_t)(n > 0 ? n : 1)) : NULL;
     const size_t nb = (size_t)(maxN > 0 ? maxN : 1);
     double* rpm = (double*)malloc(sizeof(double) * 4 * nb);
     double* cmd = (double*)malloc(sizeof(double) * 4 * nb);
@@ -1050,6 +1068,10 @@ int orc_control_steps(const orc_params* P, int n_envs, const int32_t* env_off, c
     const double maxrpm = orc_max_rpm(P);
     for (int k = 0; k < K; ++k) {
         const double* act = actions + (size_t)k * (size_t)n * 4;
+        if (x_last && k == K - 1) {
+            memcpy(x_last, x, sizeof(double) * 13 * (size_t)n);
+            memcpy(a_last, a_prev, sizeof(double) * 4 * (size_t)n);
+        }
         for (int e = 0; e < n_envs; ++e) {
             const int b = env_off[e], N = env_off[e + 1] - env_off[e];
             const double* row = dr ? dr->env_dr + (size_t)e * ORC_DR_PARAMS : NULL;
@@ -1126,8 +1148,31 @@ int orc_control_steps(const orc_params* P, int n_envs, const int32_t* env_off, c
     if (kin) {
         for (int e = 0; e < n_envs; ++e) {
             const int b = env_off[e], N = env_off[e + 1] - env_off[e];
+            const double* row = dr ? dr->env_dr + (size_t)e * ORC_DR_PARAMS : NULL;
+            const int delayed = row && x_last && K > 0 && row[ORC_DR_OBS_DELAY] == 1.0;
             for (int j = 0; j < N; ++j) {
-                orc_kin(x + 13 * (size_t)(b + j), a_prev + 4 * (size_t)(b + j), kin + 20 * (size_t)(b + j));
+                const size_t g = (size_t)(b + j);
+                double* o = kin + 20 * g;
+                if (delayed) orc_kin(x_last + 13 * g, a_last + 4 * g, o);
+                else orc_kin(x + 13 * g, a_prev + 4 * g, o);
+                if (row && K > 0) {
+                    /* Gaussian sensor noise (Box-Muller on counter-based uniforms) */
+                    const uint64_t step = (uint64_t)dr->wind[(size_t)e * ORC_WIND_STATE + 7] - 1;
+                    double xi[12];
+                    for (int m = 0; m < 6; ++m) {
+                        const double u1 = 1.0 - orc_uniform(dr->seed, ORC_STREAM_OBS, step, g, 2 * m);
+                        const double u2 = orc_uniform(dr->seed, ORC_STREAM_OBS, step, g, 2 * m + 1);
+                        const double r = sqrt(-2.0 * log(u1));
+                        xi[2 * m] = r * cos(2.0 * ORC_PI * u2);
+                        xi[2 * m + 1] = r * sin(2.0 * ORC_PI * u2);
+                    }
+                    for (int r = 0; r < 3; ++r) {
+                        o[r] += row[ORC_DR_NOISE_P] * xi[r];           /* KIN 0-2: position */
+                        o[7 + r] += row[ORC_DR_NOISE_RPY] * xi[3 + r]; /* KIN 7-9: roll, pitch, yaw */
+                        o[10 + r] += row[ORC_DR_NOISE_V] * xi[6 + r];  /* KIN 10-12: velocity */
+                        o[13 + r] += row[ORC_DR_NOISE_W] * xi[9 + r];  /* KIN 13-15: body rate */
+                    }
+                }
                 if (nbr_idx && nbr_rel)
                     orc_knn(N, x + 13 * (size_t)b, j, b, nbr_idx + 4 * (size_t)(b + j),
                             nbr_rel + 24 * (size_t)(b + j));
@@ -1138,5 +1183,7 @@ int orc_control_steps(const orc_params* P, int n_envs, const int32_t* env_off, c
     free(cmd);
     free(fext);
     free(tmp);
+    free(x_last);
+    free(a_last);
     return 0;
 }

@@ -215,7 +215,7 @@ def mixed_actions(swarm: Swarm, seed: int, step: int, hover_rpm: float) -> np.nd
 
 
 S_ACT_TYPE, S_ACT_EXT, S_DR = 10, 11, 12
-DR_PARAMS = 32
+DR_PARAMS = 40
 
 
 def dr_table(seed: int, n_envs: int, dt_ctrl: float = 1.0 / 48.0, depth: int = 3,
@@ -228,7 +228,9 @@ def dr_table(seed: int, n_envs: int, dt_ctrl: float = 1.0 / 48.0, depth: int = 3
     with a horizontal steady wind of magnitude U(0, 1) m/s, 1/2 rho C_d A U[5e-4, 2e-3] kg/m,
     gusts p U[0.02, 0.1] per step, A U[0.02, 0.08] N, duration U[0.1, 0.5] s, Dryden sigma
     U[0.1, 0.5] m/s, V U[1, 5] m/s, h U[0.5, 2] m, sinusoid A U[0.005, 0.02] N,
-    w U[1, 6] rad/s. The layout is that of MDG_DR_PARAMS in include/mdg.h."""
+    w U[1, 6] rad/s; sensors: noise sigmas 1 cm, 5 cm/s, 1 degree, 0.05 rad/s, sensor latency
+    U[0, 20] ms as whole control steps (0 or 1). The layout is that of MDG_DR_PARAMS in
+    include/mdg.h."""
     e = np.arange(n_envs, dtype=np.uint64)[:, None]
     u = uniform(seed, S_DR, 0, e, np.arange(DR_PARAMS, dtype=np.uint64)[None, :]).astype(np.float64)
     r = np.zeros((n_envs, DR_PARAMS))
@@ -255,6 +257,8 @@ def dr_table(seed: int, n_envs: int, dt_ctrl: float = 1.0 / 48.0, depth: int = 3
     r[:, 24], r[:, 25], r[:, 26] = U(22, 0.02, 0.1), U(23, 0.02, 0.08), U(24, 0.1, 0.5)
     r[:, 27], r[:, 28], r[:, 31] = U(25, 0.1, 0.5), U(26, 1.0, 5.0), U(27, 0.5, 2.0)
     r[:, 29], r[:, 30] = U(28, 0.005, 0.02), U(29, 1.0, 6.0)
+    r[:, 32], r[:, 33], r[:, 34], r[:, 35] = 0.01, 0.05, np.radians(1.0), 0.05
+    r[:, 36] = np.minimum(np.floor(U(30, 0.0, 0.02) / dt_ctrl + 0.5), 1.0)
     return r.astype(np.float32)
 
 

@@ -84,6 +84,9 @@ MUTATIONS = {
     "sinusoid_phase": ("F_dir[0] += A * sin(w * t);", "F_dir[0] += A * cos(w * t);"),
     "motor_bias_dropped": ("c *= row[ORC_DR_BIAS + i];", "c *= 1.0;"),
     "arm_factor_to_inertia": ("    Pe->arm *= dr[ORC_DR_ARM];\n", "    Pe->Jxx *= dr[ORC_DR_ARM];\n"),
+    "sensor_delay_ignored": ("const int delayed = row && x_last && K > 0 && row[ORC_DR_OBS_DELAY] == 1.0;",
+                             "const int delayed = 0;"),
+    "noise_rpy_channel": ("o[7 + r] += row[ORC_DR_NOISE_RPY] * xi[3 + r];", "o[3 + r] += row[ORC_DR_NOISE_RPY] * xi[3 + r];"),
 }
 
 

@@ -235,3 +235,75 @@ def test_uniforms_match_the_input_generator():
         u = oracle.uniform(seed, stream, step, index, comp)
         v = wl.uniform(seed, stream, step, np.uint64(index), np.uint64(comp))
         assert u == float(v)
+
+
+def _obs_run(P, x0, rpm, r, K=1):
+    n = x0.shape[0]
+    env_off = np.arange(n + 1, dtype=np.int32)
+    return oracle.control_steps(P, env_off, np.zeros(n, np.int32), np.full(n, oracle.ACT_RPM, np.int32), x0,
+                                np.zeros((n, 6)), np.zeros((n, 4)), np.repeat(rpm[None], K, axis=0), 5, obs=True, dr=r)
+
+
+def test_observation_noise_statistics():
+    """2000 identical drones with the table's sensor sigmas: the KIN observation minus the
+    noiseless one, divided by the sigma, is standard normal and uncorrelated per channel;
+    quaternion and RPM channels carry no noise."""
+    n = 2000
+    x0 = np.repeat(_level(z=1.0), n, axis=0)
+    rpm = np.full((n, 4), HOVER)
+    sig = {oracle.DR_NOISE_P: 0.01, oracle.DR_NOISE_V: 0.05, oracle.DR_NOISE_RPY: np.radians(1.0),
+           oracle.DR_NOISE_W: 0.05}
+    r0 = oracle.Randomization(n, n, 1, seed=3)
+    r1 = oracle.Randomization(n, n, 1, seed=3)
+    for col, v in sig.items():
+        r1.env_dr[:, col] = v
+    k0 = _obs_run(P, x0, rpm, r0)[3]
+    k1 = _obs_run(P, x0, rpm, r1)[3]
+    d = k1 - k0
+    np.testing.assert_array_equal(d[:, 3:7], 0.0)
+    np.testing.assert_array_equal(d[:, 16:20], 0.0)
+    z = np.concatenate([d[:, 0:3] / 0.01, d[:, 7:10] / np.radians(1.0), d[:, 10:13] / 0.05, d[:, 13:16] / 0.05], axis=1)
+    assert np.all(np.abs(z.mean(axis=0)) < 4 / np.sqrt(n))
+    np.testing.assert_allclose(z.std(axis=0), 1.0, atol=4 / np.sqrt(2 * n))
+    c = np.corrcoef(z.T)
+    assert np.max(np.abs(c - np.eye(12))) < 4 / np.sqrt(n)
+
+
+def test_sensor_delay_reports_the_step_start():
+    """With a one-step sensor delay (and no noise) the KIN observation after a control step is
+    the one of the state and RPMs at the step's start; the neighbour observation is not
+    delayed. Two steps: the second reports the state after the first."""
+    x0 = np.stack([_level(z=1.0)[0], _level(z=1.3)[0]])
+    x0[1, 0] = 0.2
+    env_off = np.array([0, 2], np.int32)
+    r = oracle.Randomization(1, 2, 1)
+    r.env_dr[0, oracle.DR_OBS_DELAY] = 1.0
+    rpm = np.array([[14000.0, 15000.0, 14500.0, 14800.0], [15500.0, 15000.0, 15200.0, 14900.0]])
+    args = (env_off, np.zeros(1, np.int32), np.array([oracle.ACT_RPM], np.int32))
+    a0 = np.full((2, 4), 123.0)
+    x1, i1, a1, kin, idx, rel = oracle.control_steps(P, *args, x0, np.zeros((2, 6)), a0, rpm[None], 5, obs=True, dr=r)
+    for j in range(2):
+        np.testing.assert_array_equal(kin[j], oracle.kin(x0[j], a0[j]))
+        i_ref, r_ref = oracle.knn(x1, j, 0)
+        np.testing.assert_array_equal(idx[j], i_ref)
+        np.testing.assert_allclose(rel[j], r_ref, rtol=1e-12)
+    r2 = oracle.Randomization(1, 2, 1)
+    r2.env_dr[0, oracle.DR_OBS_DELAY] = 1.0
+    x2, _, a2, kin2, _, _ = oracle.control_steps(P, *args, x0, np.zeros((2, 6)), a0, np.repeat(rpm[None], 2, axis=0),
+                                                 5, obs=True, dr=r2)
+    for j in range(2):
+        np.testing.assert_array_equal(kin2[j], oracle.kin(x1[j], a1[j]))
+
+
+def test_observation_noise_changes_with_the_step():
+    n = 50
+    x0 = np.repeat(_level(z=1.0), n, axis=0)
+    rpm = np.full((n, 4), HOVER)
+    r = oracle.Randomization(n, n, 1, seed=8)
+    r.env_dr[:, oracle.DR_NOISE_P] = 0.01
+    k1 = _obs_run(P, x0, rpm, r)[3]
+    k2 = _obs_run(P, x0, rpm, r)[3]  # same start, wind step counter advanced by one
+    assert np.all(np.abs(k1[:, 0] - k2[:, 0]) > 0)
+    r2 = oracle.Randomization(n, n, 1, seed=8)
+    r2.env_dr[:, oracle.DR_NOISE_P] = 0.01
+    np.testing.assert_array_equal(_obs_run(P, x0, rpm, r2)[3], k1)
