@@ -126,7 +126,7 @@ typedef struct mdg_ctx* mdg_handle;
  * episode; "Wind and turbulence"): one row of MDG_DR_PARAMS floats per environment.
  * Factors scale the model the physics integrates (the controller keeps the nominal
  * constants: it does not know the draw). */
-#define MDG_DR_PARAMS 32
+#define MDG_DR_PARAMS 40
 #define MDG_DR_MASS 0       /* x m */
 #define MDG_DR_J 1          /* x Jxx, Jyy, Jzz (1..3) */
 #define MDG_DR_ARM 4        /* x L */
@@ -152,6 +152,11 @@ typedef struct mdg_ctx* mdg_handle;
 #define MDG_DR_SIN_A 29     /* sinusoidal force amplitude [N] */
 #define MDG_DR_SIN_W 30     /* sinusoidal angular frequency [rad/s] */
 #define MDG_DR_DRY_H 31     /* Dryden reference altitude h [m] */
+#define MDG_DR_NOISE_P 32   /* observation noise sigma of the KIN position [m] */
+#define MDG_DR_NOISE_V 33   /* ... of the KIN velocity [m/s] */
+#define MDG_DR_NOISE_RPY 34 /* ... of the KIN roll, pitch, yaw [rad] */
+#define MDG_DR_NOISE_W 35   /* ... of the KIN body rate [rad/s] */
+#define MDG_DR_OBS_DELAY 36 /* sensor latency [control steps]: 0 or 1 (37..39 unused) */
 #define MDG_WIND_CONSTANT 1
 #define MDG_WIND_GUST 2
 #define MDG_WIND_DRYDEN 4
@@ -244,8 +249,8 @@ int mdg_set_setpoints(mdg_handle h, float* setpoints);
  * rollout (all caller-owned device buffers, 16-byte aligned; NULL env_params detaches):
  *   env_params   float32 [n_envs][MDG_DR_PARAMS] (validated here, on a host copy: factors
  *                positive, tau >= 0, delay whole and < hist_depth, known wind bits,
- *                gust probability in [0, 1], durations, altitude positive; change it only
- *                by attaching again)
+ *                gust probability in [0, 1], durations, altitude positive, noise sigmas
+ *                >= 0, sensor delay 0 or 1; change it only by attaching again)
  *   motor        float32 [n_drones][4] rotor speeds, the lag's state (NaN: not set, starts
  *                at the first command)
  *   action_hist  float32 [hist_depth][n_drones][4] actions received (NaN row: empty, filled
@@ -259,8 +264,12 @@ int mdg_set_setpoints(mdg_handle h, float* setpoints);
  * force and the quadratic drag on the relative wind at the step's start, held over the
  * substeps; before each substep every rotor speed relaxes towards its command,
  * n <- c + (n - c) exp(-dt_sim/tau); the substeps integrate the randomized model.
- * Euler substeps only (MDG_ERR_UNSUPPORTED with RK4, and in mdg_surrogate_step). Errors:
- * MDG_ERR_ARG, MDG_ERR_CUDA (the host copy). */
+ * Observations (the sensor group): with a sensor delay the KIN observation reports the state
+ * and RPMs of the step's start; KIN positions, roll/pitch/yaw, velocities and body rates get
+ * Gaussian noise of the row's sigmas (counter-based draws keyed by the environment's wind
+ * step and the drone); the neighbour observation is neither delayed nor noisy.
+ * Euler substeps only (MDG_ERR_UNSUPPORTED with RK4, in mdg_surrogate_step and for
+ * observations to host buffers). Errors: MDG_ERR_ARG, MDG_ERR_CUDA (the host copy). */
 int mdg_set_randomization(mdg_handle h, const float* env_params, float* motor, float* action_hist,
                           int32_t hist_depth, float* wind_state, uint64_t seed);
 

@@ -39,10 +39,11 @@ INTEGRATOR_EULER, INTEGRATOR_RK4 = 0, 1
 GND_COM, GND_ROTOR = 0, 1
 CTRL_PID, CTRL_DSL = 0, 1
 CAM_H, CAM_W = 48, 64
-DR_PARAMS, WIND_STATE, MAX_HIST_DEPTH = 32, 8, 16
+DR_PARAMS, WIND_STATE, MAX_HIST_DEPTH = 40, 8, 16
 (DR_MASS, DR_J, DR_ARM, DR_KF, DR_KM, DR_CXY, DR_CZ, DR_CGND, DR_C1, DR_MAXRPM, DR_BIAS, DR_G, DR_TAU, DR_DELAY,
  DR_WIND, DR_VWIND, DR_KDRAG, DR_GUST_P, DR_GUST_A, DR_GUST_T, DR_DRY_SIGMA, DR_DRY_V, DR_SIN_A, DR_SIN_W,
  DR_DRY_H) = (0, 1, 4, 5, 6, 7, 8, 9, 10, 11, 12, 16, 17, 18, 19, 20, 23, 24, 25, 26, 27, 28, 29, 30, 31)
+DR_NOISE_P, DR_NOISE_V, DR_NOISE_RPY, DR_NOISE_W, DR_OBS_DELAY = 32, 33, 34, 35, 36
 WIND_CONSTANT, WIND_GUST, WIND_DRYDEN, WIND_SINUSOIDAL, WIND_COMBINED = 1, 2, 4, 8, 15
 OBS_NONE, OBS_LAST, OBS_EVERY_STEP = 0, 1, 2
 MLP_IN, MLP_IN_PAD, MLP_HIDDEN, MLP_OUT, MLP_OUT_PAD = 41, 64, 256, 13, 32

@@ -679,9 +679,12 @@ int mdg_set_randomization(mdg_handle h, const float* env_params, float* motor, f
                       dly < (float)hist_depth && bits >= 0.f && bits == floorf(bits) && bits <= (float)MDG_WIND_COMBINED &&
                       r[MDG_DR_KDRAG] >= 0.f && r[MDG_DR_GUST_P] >= 0.f && r[MDG_DR_GUST_P] <= 1.f &&
                       r[MDG_DR_GUST_T] > 0.f && r[MDG_DR_DRY_SIGMA] >= 0.f && r[MDG_DR_DRY_V] >= 0.f &&
-                      r[MDG_DR_DRY_H] > 0.f;
+                      r[MDG_DR_DRY_H] > 0.f && r[MDG_DR_NOISE_P] >= 0.f && r[MDG_DR_NOISE_V] >= 0.f &&
+                      r[MDG_DR_NOISE_RPY] >= 0.f && r[MDG_DR_NOISE_W] >= 0.f &&
+                      (r[MDG_DR_OBS_DELAY] == 0.f || r[MDG_DR_OBS_DELAY] == 1.f);
             for (int i = MDG_DR_VWIND; i < MDG_DR_PARAMS; ++i) ok = ok && isfinite(r[i]);
-            if (!ok) return fail(MDG_ERR_ARG, "mdg_set_randomization: env %d: invalid lag, delay or wind values", k);
+            if (!ok)
+                return fail(MDG_ERR_ARG, "mdg_set_randomization: env %d: invalid lag, delay, wind or sensor values", k);
         }
     }
     mdg::RandArgs ra;
@@ -745,6 +748,8 @@ static int step_common(mdg_handle h, float* state, const float* action, int32_t 
     if (n_substeps < 1) return fail(MDG_ERR_ARG, "mdg_step: n_substeps = %d < 1", n_substeps);
     int rc;
     if ((rc = check_setpoints(h, "mdg_step")) != MDG_OK) return rc;
+    if (obs_host && h->dr)
+        return fail(MDG_ERR_UNSUPPORTED, "mdg_step_obs_host: not with randomization (use mdg_step_obs)");
     if ((rc = check_state_ptr(h, state, "state")) != MDG_OK) return rc;
     if ((rc = check_state_ptr(h, action, "action")) != MDG_OK) return rc;
     if (with_obs) {

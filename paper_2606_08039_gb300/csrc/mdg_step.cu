@@ -821,6 +821,48 @@ __device__ __forceinline__ void wind_step(const float* row, float4& s0, float4& 
     s1.w = (float)(step + 1);
 }
 
+constexpr unsigned long long kStreamObs = 22;  // random stream of the observation noise
+
+// The KIN observation of d (RPMs a4) with the row's sensor noise: Gaussian (Box-Muller on the
+// counters (seed, kStreamObs, step, drone, 0..11)) of the row's sigmas on the position (0-2),
+// roll/pitch/yaw (3-5), velocity (6-8) and body rate (9-11); stored at kin_row[0..19].
+__device__ __forceinline__ void noisy_kin(float* kin_row, const Drone& d, const float a4[4], const float* row,
+                                          unsigned long long seed, unsigned long long step, long long g)
+{
+    float4 v[5];
+    kin_values(d, a4, v);
+    const float sp = row[MDG_DR_NOISE_P], sv = row[MDG_DR_NOISE_V], sr = row[MDG_DR_NOISE_RPY],
+                sw = row[MDG_DR_NOISE_W];
+    if (sp > 0.f || sv > 0.f || sr > 0.f || sw > 0.f) {
+        float xi[12];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+            const float u1 = 1.f - counter_uniform(seed, kStreamObs, step, g, 2 * m);
+            const float u2 = counter_uniform(seed, kStreamObs, step, g, 2 * m + 1);
+            const float r = sqrtf(-2.f * logf(u1));
+            float sn, cs;
+            sincosf(2.f * kPi * u2, &sn, &cs);
+            xi[2 * m] = r * cs;
+            xi[2 * m + 1] = r * sn;
+        }
+        v[0].x += sp * xi[0];
+        v[0].y += sp * xi[1];
+        v[0].z += sp * xi[2];
+        v[1].w += sr * xi[3];
+        v[2].x += sr * xi[4];
+        v[2].y += sr * xi[5];
+        v[2].z += sv * xi[6];
+        v[2].w += sv * xi[7];
+        v[3].x += sv * xi[8];
+        v[3].y += sw * xi[9];
+        v[3].z += sw * xi[10];
+        v[3].w += sw * xi[11];
+    }
+    float4* o = reinterpret_cast<float4*>(kin_row);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) o[k] = v[k];
+}
+
 // The substeps of one control step under randomization, called by every thread of the
 // block (barriers inside). From the step's start: the environment's wind (each drone
 // evaluates it, the environment's first drone stores the new state once the block has read
@@ -828,10 +870,15 @@ __device__ __forceinline__ void wind_step(const float* row, float4& s0, float4& 
 // constants; each motor's command (its RPM times its bias, saturated at MAX_RPM times the
 // factor). Before each substep every rotor speed relaxes towards its command,
 // n <- c + (n - c) exp(-dt/tau) (exact for a first-order lag under a constant command).
+// Observations (when kin_row is given): with a sensor delay the noisy KIN of the step's
+// start (the state d and the RPMs a_pre of that moment) is written here, and `delayed`
+// tells the caller not to write the end-of-step one; `step` returns the wind step counter
+// of this control step (the noise's key).
 template <int kN>
 __device__ __forceinline__ void randomized_substeps(const StepArgs& a, Drone& d, const float rpm[4], const EnvSlot& env,
                                                     float4* s_pos, int B, int t, long long g, bool active,
-                                                    bool tile_dw, bool warp_local, int& ph)
+                                                    bool tile_dw, bool warp_local, int& ph, float* kin_row,
+                                                    const float a_pre[4], bool& delayed, unsigned long long& step)
 {
     const RandArgs& R = *a.rand;
     const float* row = R.dr + (long long)env.id * MDG_DR_PARAMS;
@@ -840,9 +887,14 @@ __device__ __forceinline__ void randomized_substeps(const StepArgs& a, Drone& d,
     float cmd[4] = {0.f, 0.f, 0.f, 0.f}, lag = 0.f;
     float3 fe = {};
     DevConsts pc = a.c;
+    delayed = false;
+    step = 0;
     if (active) {
         s0 = R.wind[2LL * env.id];
         s1 = R.wind[2LL * env.id + 1];
+        step = (unsigned long long)s1.w;
+        delayed = row[MDG_DR_OBS_DELAY] == 1.f;
+        if (kin_row && delayed) noisy_kin(kin_row, d, a_pre, row, R.seed, step, g);
         float Fd[3], vw[3];
         wind_step(row, s0, s1, R.seed, env.id, a.c.dt_ctrl, Fd, vw);
         const int model = (int)row[MDG_DR_WIND];
@@ -1044,9 +1096,17 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
     Drone d;
     unpack_state(s0, s1, s2, s3, s4, d);
     float rpm[4] = {0.f, 0.f, 0.f, 0.f};
+    float a_pre[4] = {0.f, 0.f, 0.f, 0.f};  // randomization: the RPMs of the step's start (delayed observations)
+    bool delayed = false;
+    unsigned long long obs_step = 0;
     if (active) {
-        if constexpr (kFlags == kFlagsDR)  // action latency
+        if constexpr (kFlags == kFlagsDR) {  // action latency
             act = delayed_action(a, g, act, (int)a.rand->dr[(long long)env.id * MDG_DR_PARAMS + MDG_DR_DELAY]);
+            if (kObs) {
+                const float4 p5 = a.state[5 * a.n + g];
+                a_pre[0] = p5.x, a_pre[1] = p5.y, a_pre[2] = p5.z, a_pre[3] = p5.w;
+            }
+        }
         if (kFlags >= 8 && env.act >= MDG_ACT_RPM_NORM) {
             ext_action_rpm(d, act, env.act, a.c, rpm);
         } else if (is_pid) {
@@ -1070,7 +1130,8 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
     if constexpr (kFlags == kFlagsRK4) {
         rk4_substeps<kFlags, kN>(d, m, env, s_pos, B, t, active, tile_dw, warp_local, a.n_sub, ph, a.c);
     } else if constexpr (kFlags == kFlagsDR) {
-        randomized_substeps<kN>(a, d, rpm, env, s_pos, B, t, g, active, tile_dw, warp_local, ph);
+        randomized_substeps<kN>(a, d, rpm, env, s_pos, B, t, g, active, tile_dw, warp_local, ph,
+                                kObs ? a.kin + 20 * g : nullptr, a_pre, delayed, obs_step);
     } else {
         for (int s = 0; s < a.n_sub; ++s, ++ph) {
             float4* buf = s_pos + (s & 1) * B;
@@ -1104,7 +1165,13 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
             write_obs_staged<kN>(a, stage, active, g, t & 31, tile.first_drone + env.ls, t - env.ls, d, rpm,
                                  pb + env.ls, s_vel + env.ls, env.N);
         } else if (active) {
-            write_kin(a.kin, g, d, rpm);
+            if constexpr (kFlags == kFlagsDR) {  // sensor noise; delayed ones were written at the start
+                if (!delayed)
+                    noisy_kin(a.kin + 20 * g, d, rpm, a.rand->dr + (long long)env.id * MDG_DR_PARAMS, a.rand->seed,
+                              obs_step, g);
+            } else {
+                write_kin(a.kin, g, d, rpm);
+            }
             write_knn<kN>(a.nbr_idx, a.nbr_rel, g, tile.first_drone + env.ls, t - env.ls, d, pb + env.ls,
                           s_vel + env.ls, env.N);
         }
@@ -1225,8 +1292,15 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
         float4 act = {};
         if (active) act = a.action[g];
         float rpm[4] = {0.f, 0.f, 0.f, 0.f};
+        if constexpr (kFlags == kFlagsDR) {  // the RPMs before the rollout (delayed observations)
+            if (active) {
+                const float4 p5 = a.state[5 * a.n + g];
+                rpm[0] = p5.x, rpm[1] = p5.y, rpm[2] = p5.z, rpm[3] = p5.w;
+            }
+        }
         int sub = 0;  // substeps taken in this item: the snapshot buffers alternate across steps
         for (int k = 0; k < r.K; ++k) {
+            const float a_pre[4] = {rpm[0], rpm[1], rpm[2], rpm[3]};  // the RPMs of the step's start
             float4 next = {};
             if (active && k + 1 < r.K) next = a.action[(k + 1) * r.action_stride + g];
             if (active) {
@@ -1246,10 +1320,15 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
                 }
             }
             const Motor m = motor(rpm, a.c);
+            const bool obs_now = r.obs_mode == 2 || (r.obs_mode == 1 && k == r.K - 1);
+            bool delayed = false;
+            unsigned long long obs_step = 0;
             if constexpr (kFlags == kFlagsRK4) {
                 rk4_substeps<kFlags, kN>(d, m, env, s_pos, B, t, active, tile_dw, warp_local, a.n_sub, sub, a.c);
             } else if constexpr (kFlags == kFlagsDR) {
-                randomized_substeps<kN>(a, d, rpm, env, s_pos, B, t, g, active, tile_dw, warp_local, sub);
+                float* kin_row = obs_now ? a.kin + 20 * ((r.obs_mode == 2 ? (long long)k * a.n : 0) + g) : nullptr;
+                randomized_substeps<kN>(a, d, rpm, env, s_pos, B, t, g, active, tile_dw, warp_local, sub, kin_row,
+                                        a_pre, delayed, obs_step);
             } else {
                 for (int s = 0; s < a.n_sub; ++s, ++sub) {
                     float4* buf = s_pos + (sub & 1) * B;
@@ -1268,7 +1347,13 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
                 s_vel[t] = make_float4(d.v[0], d.v[1], d.v[2], 0.f);
                 __syncthreads();
                 if (active) {
-                    write_kin(a.kin, o + g, d, rpm);
+                    if constexpr (kFlags == kFlagsDR) {  // sensor noise; delayed ones were written at the start
+                        if (!delayed)
+                            noisy_kin(a.kin + 20 * (o + g), d, rpm, a.rand->dr + (long long)env.id * MDG_DR_PARAMS,
+                                      a.rand->seed, obs_step, g);
+                    } else {
+                        write_kin(a.kin, o + g, d, rpm);
+                    }
                     write_knn<kN>(a.nbr_idx, a.nbr_rel, o + g, env_first, t - env.ls, d, pb + env.ls,
                                   s_vel + env.ls, env.N);
                 }

@@ -4,7 +4,8 @@ Rows drawn from the paper's recommended ranges (workloads.dr_table, every wind m
 Each control step, the oracle restarts from the GPU's state and randomization state
 (rotor speeds, action history, wind state) and is compared over the step with the horizon
 bound; the RPMs, integrals, rotor speeds and wind state against the oracle's, the action
-history and the gust phases and step counters exactly (the gust phase decides when a gust
+history and the gust phases and step counters exactly, the KIN observation with its sensor
+noise and delay against the oracle's (the gust phase decides when a gust
 ends and advances in single precision on both sides; the wind draws come from the same
 counter-based SplitMix64 stream). Heights are spread per environment
 (helpers.spread_heights): the randomization is under test, not the downwash's conditioning.
@@ -35,7 +36,7 @@ def _oracle_state(table, motor, hist, wind):
     return r
 
 
-def _oracle_steps(sw, types, x, integ, a_prev, actions, r, perturb=False):
+def _oracle_steps(sw, types, x, integ, a_prev, actions, r, perturb=False, obs=False):
     env_off = np.concatenate([[0], np.cumsum(sw.drones_per_env)]).astype(np.int32)
     if perturb:  # the horizon bound's response: an initial error of the per-substep tolerance
         rng = np.random.default_rng(0)
@@ -46,7 +47,7 @@ def _oracle_steps(sw, types, x, integ, a_prev, actions, r, perturb=False):
         q = x[:, 3:7] + sgn[:, 3:7] * 2e-6
         x[:, 3:7] = q / np.linalg.norm(q, axis=1, keepdims=True)
     return oracle.control_steps(P, env_off, sw.flags.astype(np.int32), np.asarray(types, np.int32), x, integ,
-                                a_prev, np.asarray(actions, np.float64), 5, dr=r)
+                                a_prev, np.asarray(actions, np.float64), 5, dr=r, obs=obs)
 
 
 def _copy(r):
@@ -87,7 +88,7 @@ def test_randomized_control_steps(cuda, recipe):
         h.step_obs(state, torch.as_tensor(action, device=cuda), mdg.ACT_MIXED, 5, kin, idx, rel)
         torch.cuda.synchronize()
         xg, ig, ag = oracle_arrays(state)
-        xo, io, ao = _oracle_steps(sw, types, x0, i0, a0, action[None], r)
+        xo, io, ao, ko, _, _ = _oracle_steps(sw, types, x0, i0, a0, action[None], r, obs=True)
         xp, _, _ = _oracle_steps(sw, types, x0, i0, a0, action[None], r2, perturb=True)
         what = f"{recipe} step {k}"
         assert_horizon_close(xg, xo, np.abs(xo - xp), 5, what=what)
@@ -101,6 +102,18 @@ def test_randomized_control_steps(cuda, recipe):
         np.testing.assert_array_equal(wg[:, 7], r.wind[:, 7], err_msg=f"{what}: wind steps")
         np.testing.assert_allclose(wg[:, 0:3], r.wind[:, 0:3], rtol=1e-4, atol=1e-5, err_msg=f"{what}: Dryden")
         np.testing.assert_allclose(wg[:, 4:7], r.wind[:, 4:7], rtol=0, atol=1e-6, err_msg=f"{what}: gust directions")
+        # the KIN observation with sensor noise and delay (the oracle from the same start: a
+        # delayed drone reports the step's start exactly; the others the end of the step,
+        # within the step's tolerance) and the neighbour indices of the end-of-step state
+        kg = kin.cpu().numpy().astype(np.float64)
+        delayed = np.repeat(table[:, oracle.DR_OBS_DELAY] == 1, sw.drones_per_env)
+        assert delayed.any() and (~delayed).any()
+        np.testing.assert_allclose(kg[delayed], ko[delayed], rtol=1e-5, atol=1e-6, err_msg=f"{what}: delayed KIN")
+        ok = ~delayed
+        assert excess(kg[ok][:, 0:3], ko[ok][:, 0:3], 5 * 1e-5) <= 1.0, f"{what}: KIN position"
+        assert np.max(np.abs(kg[:, 16:20] - ko[:, 16:20])) <= 1e-2, f"{what}: KIN RPMs"
+        noise = kg[ok][:, 0:3] - xg[ok][:, 0:3]  # the position noise the GPU added
+        assert np.all(np.abs(noise) < 0.08) and np.std(noise) > 0.005, f"{what}: position noise"
     assert (wind[:, 3] >= 0).any(), "no gust was active during the test"
     assert h.status()[0] == mdg.OK
 
