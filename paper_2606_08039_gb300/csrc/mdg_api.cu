@@ -989,8 +989,7 @@ static cudaError_t enqueue_rollout(mdg_handle h, const mdg::RolloutArgs& r, cuda
     int n_sm = 152;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device);
     const int flags = launch_flags(h, r.s.act_type);
-    const int grid = n_sm * mdg::rollout_blocks_per_sm(h->block, h->dr ? mdg::kVariantRandomized : flags, h->uniform_N, h->dc.rk4 != 0,
-                                                           h->dc.gnd_rotor != 0);
+    const int grid = n_sm * mdg::rollout_blocks_per_sm(r.s, h->block, flags);
     return mdg::launch_rollout(r, h->block, flags, grid, s);
 }
 

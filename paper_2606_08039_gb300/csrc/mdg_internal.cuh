@@ -183,7 +183,7 @@ inline bool valid_action(int t) { return valid_env_action(t) || t == MDG_ACT_MIX
 inline bool extended_action(int t) { return t >= MDG_ACT_RPM_NORM && t <= MDG_ACT_ATTITUDE; }
 // grid: persistent CTAs (0: one per work item)
 cudaError_t launch_rollout(const RolloutArgs& a, int block, int uniform_flags, int grid, cudaStream_t s);
-int rollout_blocks_per_sm(int block, int uniform_flags, int uniform_N, bool rk4, bool gnd_rotor);
+int rollout_blocks_per_sm(const StepArgs& a, int block, int uniform_flags);
 cudaError_t launch_features(const SurrogateArgs& a, int n_tiles, int block, cudaStream_t s);
 cudaError_t launch_surrogate_prepare(const SurrogateArgs& a, int n_tiles, int block, cudaStream_t s);
 cudaError_t launch_surrogate_apply(const SurrogateArgs& a, cudaStream_t s);

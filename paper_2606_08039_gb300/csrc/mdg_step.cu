@@ -312,6 +312,13 @@ __device__ __forceinline__ float downwash_sum(const float4* env_pos, int N_rt, f
 // is the one the mixed-physics batches need.
 constexpr int kFlagsRK4 = 9;
 constexpr int kFlagsGndRotor = 10;
+// Runge-Kutta variants with a compile-time physics subset s: kFlagsRK4Fixed + s.
+constexpr int kFlagsRK4Fixed = 16;
+__host__ __device__ constexpr bool rk4_variant(int f) { return f == kFlagsRK4 || f >= kFlagsRK4Fixed; }
+// variants that take the physics flags (and the extra features) at run time
+__host__ __device__ constexpr bool runtime_variant(int f) { return f >= 8 && f < kFlagsRK4Fixed; }
+// the compile-time physics subset of a variant, or -1
+__host__ __device__ constexpr int fixed_subset(int f) { return f < 8 ? f : (f >= kFlagsRK4Fixed ? f - kFlagsRK4Fixed : -1); }
 constexpr int kFlagsDR = kVariantRandomized;  // Euler substeps with domain randomization, motor lag, latency, wind
 
 // Eq. ground's increment along world +z, before its gate. With per-rotor heights rotor i
@@ -346,7 +353,7 @@ template <int kFlags, int kN>
 __device__ __forceinline__ void substep(Drone& d, const Motor& m, int flags_rt, const float4* env_pos, int N_rt,
                                         const DevConsts& c, const float3 fe = float3{})
 {
-    const int flags = kFlags < 8 ? kFlags : flags_rt;
+    const int flags = fixed_subset(kFlags) >= 0 ? fixed_subset(kFlags) : flags_rt;
     const float dt = c.dt_sim;
     // exponential map with the old body rate: q <- q (x) [cos(theta), sin(theta) w/|w|],
     // theta = |w| dt/2. sin(theta)/|w| = (dt/2) sinc(theta); for theta^2 <= 0.6 both factors
@@ -957,7 +964,7 @@ template <int kFlags, int kN>
 __device__ __forceinline__ void stage_rate(const Drone& s, const Motor& m, int flags_rt, const float4* env_pos,
                                            int N_rt, const DevConsts& c, StateRate& k)
 {
-    const int flags = kFlags < 8 ? kFlags : flags_rt;
+    const int flags = fixed_subset(kFlags) >= 0 ? fixed_subset(kFlags) : flags_rt;
     const float qi = rsqrtf(s.q[0] * s.q[0] + s.q[1] * s.q[1] + s.q[2] * s.q[2] + s.q[3] * s.q[3]);
     const float qw = s.q[0] * qi, qx = s.q[1] * qi, qy = s.q[2] * qi, qz = s.q[3] * qi;
     const float r0 = 2.f * (qx * qz + qw * qy);
@@ -1091,7 +1098,7 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
     }
     const EnvSlot env = tile_env(a, tile, s_off, s_info);
     const bool is_pid = env.act == MDG_ACT_PID;
-    const bool loops = is_pid || (kFlags >= 8 && uses_loops(env.act));
+    const bool loops = is_pid || (runtime_variant(kFlags) && uses_loops(env.act));
 
     Drone d;
     unpack_state(s0, s1, s2, s3, s4, d);
@@ -1107,11 +1114,11 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
                 a_pre[0] = p5.x, a_pre[1] = p5.y, a_pre[2] = p5.z, a_pre[3] = p5.w;
             }
         }
-        if (kFlags >= 8 && env.act >= MDG_ACT_RPM_NORM) {
+        if (runtime_variant(kFlags) && env.act >= MDG_ACT_RPM_NORM) {
             ext_action_rpm(d, act, env.act, a.c, rpm);
         } else if (is_pid) {
             float ep[3], ye;
-            const float4 wp = (kFlags >= 8 && a.c.dsl) ? dsl_setpoint(d, act, a.setpoints + g, a.c) : act;
+            const float4 wp = (runtime_variant(kFlags) && a.c.dsl) ? dsl_setpoint(d, act, a.setpoints + g, a.c) : act;
             pid(d, wp, a.c, rpm, ep, ye);
         } else {
             rpm[0] = fminf(a.c.max_rpm, fmaxf(0.f, act.x));
@@ -1127,7 +1134,7 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
     const bool tile_dw = (tile.bits & kTileAnyDW) != 0;
     const bool warp_local = (tile.bits & kTileWarpLocal) != 0;
     int ph = 0;  // position publications (the double buffer's parity)
-    if constexpr (kFlags == kFlagsRK4) {
+    if constexpr (rk4_variant(kFlags)) {
         rk4_substeps<kFlags, kN>(d, m, env, s_pos, B, t, active, tile_dw, warp_local, a.n_sub, ph, a.c);
     } else if constexpr (kFlags == kFlagsDR) {
         randomized_substeps<kN>(a, d, rpm, env, s_pos, B, t, g, active, tile_dw, warp_local, ph,
@@ -1273,7 +1280,7 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
         }
         const bool active = t < n_drones && env.N > 0;  // env.N == 0 only after a failed debug check
         const bool is_pid = env.act == MDG_ACT_PID;
-        const bool loops = is_pid || (kFlags >= 8 && uses_loops(env.act));
+        const bool loops = is_pid || (runtime_variant(kFlags) && uses_loops(env.act));
         const bool tile_dw = (bits & kTileAnyDW) != 0;
         const bool warp_local = (bits & kTileWarpLocal) != 0;
 
@@ -1306,11 +1313,11 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
             if (active) {
                 if constexpr (kFlags == kFlagsDR)  // action latency
                     act = delayed_action(a, g, act, (int)a.rand->dr[(long long)env.id * MDG_DR_PARAMS + MDG_DR_DELAY]);
-                if (kFlags >= 8 && env.act >= MDG_ACT_RPM_NORM) {
+                if (runtime_variant(kFlags) && env.act >= MDG_ACT_RPM_NORM) {
                     ext_action_rpm(d, act, env.act, a.c, rpm);
                 } else if (is_pid) {
                     float ep[3], ye;
-                    const float4 wp = (kFlags >= 8 && a.c.dsl) ? dsl_setpoint(d, act, a.setpoints + g, a.c) : act;
+                    const float4 wp = (runtime_variant(kFlags) && a.c.dsl) ? dsl_setpoint(d, act, a.setpoints + g, a.c) : act;
                     pid(d, wp, a.c, rpm, ep, ye);
                 } else {
                     rpm[0] = fminf(a.c.max_rpm, fmaxf(0.f, act.x));
@@ -1323,7 +1330,7 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
             const bool obs_now = r.obs_mode == 2 || (r.obs_mode == 1 && k == r.K - 1);
             bool delayed = false;
             unsigned long long obs_step = 0;
-            if constexpr (kFlags == kFlagsRK4) {
+            if constexpr (rk4_variant(kFlags)) {
                 rk4_substeps<kFlags, kN>(d, m, env, s_pos, B, t, active, tile_dw, warp_local, a.n_sub, sub, a.c);
             } else if constexpr (kFlags == kFlagsDR) {
                 float* kin_row = obs_now ? a.kin + 20 * ((r.obs_mode == 2 ? (long long)k * a.n : 0) + g) : nullptr;
@@ -1668,13 +1675,13 @@ __global__ void __launch_bounds__(256) pid_kernel(const PidArgs a)
 // compile-time environment size, -1 a runtime size in blocks of at most kSmallBlock
 // threads, 0 any block size.
 #define MDG_STEP_VARIANTS(X) \
-    X(7, 4) X(7, 64) X(3, 1) X(8, -1) X(8, 0) X(9, -1) X(9, 0) X(10, -1) X(10, 0) X(11, -1) X(11, 0)
+    X(7, 4) X(7, 64) X(3, 1) X(8, -1) X(8, 0) X(9, -1) X(9, 0) X(10, -1) X(10, 0) X(11, -1) X(11, 0) X(23, 4)
 
 template <bool kObs>
 static void* step_kernel_ptr(int flags, int N, int block)
 {
 #define MDG_PICK(F, NN)                                                                       \
-    if ((flags == F || (F == 8 && flags != kFlagsRK4 && flags != kFlagsGndRotor && flags != kFlagsDR)) &&          \
+    if ((flags == F || (F == 8 && flags < 8)) &&                                                                    \
         (NN == 0 || (block <= kSmallBlock && (NN == -1 || N == NN))))                         \
         return (void*)step_kernel<kObs, F, NN>;
     MDG_STEP_VARIANTS(MDG_PICK)
@@ -1705,17 +1712,40 @@ static cudaError_t tile_kernels_setup()
     return cudaSuccess;
 }
 
+// The kernel variant (flags, N) of a launch: randomization, Runge-Kutta substeps (a
+// compile-time all-effects variant for uniform batches without runtime-only features, else
+// the runtime one) and per-rotor ground heights first; uniform_flags is the batch's physics
+// subset, or 8 when a runtime-only feature (action types, the DSL controller) is in use.
+static void variant_of(const StepArgs& a, int uniform_flags, int& flags, int& N)
+{
+    N = a.uniform_N;
+    if (a.rand) {
+        flags = kFlagsDR;
+    } else if (a.c.rk4) {
+        const bool fixed = uniform_flags >= 0 && uniform_flags < 8 && !a.c.gnd_rotor;
+        flags = fixed ? kFlagsRK4Fixed + uniform_flags : kFlagsRK4;
+        if (!fixed) N = -1;
+    } else {
+        flags = a.c.gnd_rotor ? kFlagsGndRotor : uniform_flags;
+    }
+}
+
 cudaError_t launch_step(const StepArgs& a, int n_tiles, int block, bool with_obs, int uniform_flags, cudaStream_t s)
 {
     if (n_tiles == 0) return cudaSuccess;
     cudaError_t e = tile_kernels_setup();
     if (e != cudaSuccess) return e;
     // a compile-time variant needs one physics subset and one environment size for the
-    // batch; Runge-Kutta substeps have runtime-generic variants of their own
-    // Runge-Kutta substeps and per-rotor ground heights run in the runtime-flag variants
-    const int flags = a.rand ? kFlagsDR : a.c.rk4 ? kFlagsRK4 : (a.c.gnd_rotor ? kFlagsGndRotor : uniform_flags);
-    const int N = a.c.rk4 ? -1 : a.uniform_N;
+    // batch; randomization, Runge-Kutta substeps (without a compile-time variant for the
+    // batch) and per-rotor ground heights run in runtime-flag variants of their own
+    int flags, N;
+    variant_of(a, uniform_flags, flags, N);
     void* fn = with_obs ? step_kernel_ptr<true>(flags, N, block) : step_kernel_ptr<false>(flags, N, block);
+    if (!fn && flags >= kFlagsRK4Fixed) {  // no compile-time Runge-Kutta variant for this size or block
+        flags = kFlagsRK4;
+        N = -1;
+        fn = with_obs ? step_kernel_ptr<true>(flags, N, block) : step_kernel_ptr<false>(flags, N, block);
+    }
     void* args[] = {const_cast<StepArgs*>(&a)};
     const size_t smem = with_obs && a.obs_host ? obs_stage_offset(block) + obs_stage_bytes(block) : tile_smem_bytes(block);
     return cudaLaunchKernel(fn, dim3(n_tiles), dim3(block), args, smem, s);
@@ -1726,7 +1756,7 @@ static size_t rollout_smem_bytes(int B) { return (size_t)B * 48 + (size_t)(3 * B
 static void* rollout_kernel_ptr(int flags, int N, int block)
 {
 #define MDG_PICK(F, NN)                                                                       \
-    if ((flags == F || (F == 8 && flags != kFlagsRK4 && flags != kFlagsGndRotor && flags != kFlagsDR)) &&          \
+    if ((flags == F || (F == 8 && flags < 8)) &&                                                                    \
         (NN == 0 || (block <= kSmallBlock && (NN == -1 || N == NN))))                         \
         return (void*)rollout_kernel<F, NN>;
     MDG_STEP_VARIANTS(MDG_PICK)
@@ -1752,29 +1782,33 @@ static cudaError_t rollout_setup()
     return cudaSuccess;
 }
 
-int rollout_blocks_per_sm(int block, int uniform_flags, int uniform_N, bool rk4, bool gnd_rotor)
+// The rollout kernel of a launch (the step kernel's variant choice, with the same fallback).
+static void* rollout_kernel_for(const StepArgs& a, int uniform_flags, int block)
 {
-    if (uniform_flags == kFlagsDR) uniform_N = -1;             // randomization variants
-    else if (rk4) uniform_flags = kFlagsRK4, uniform_N = -1;  // Runge-Kutta variants
-    else if (gnd_rotor) uniform_flags = kFlagsGndRotor;       // per-rotor ground heights
+    int flags, N;
+    variant_of(a, uniform_flags, flags, N);
+    void* fn = rollout_kernel_ptr(flags, N, block);
+    if (!fn && flags >= kFlagsRK4Fixed) fn = rollout_kernel_ptr(kFlagsRK4, -1, block);
+    return fn;
+}
+
+int rollout_blocks_per_sm(const StepArgs& a, int block, int uniform_flags)
+{
     if (rollout_setup() != cudaSuccess) return 1;
     int n = 0;
-    void* fn = rollout_kernel_ptr(uniform_flags, uniform_N, block);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, rollout_smem_bytes(block)) != cudaSuccess || n < 1)
+    void* fn = rollout_kernel_for(a, uniform_flags, block);
+    if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, rollout_smem_bytes(block)) != cudaSuccess ||
+        n < 1)
         return 1;
     return n;
 }
-
 cudaError_t launch_rollout(const RolloutArgs& r, int block, int uniform_flags, int grid, cudaStream_t s)
 {
     if (r.n_items == 0 || r.K == 0) return cudaSuccess;
-    const int uniform_N = r.s.c.rk4 ? -1 : r.s.uniform_N;
-    if (r.s.rand) uniform_flags = kFlagsDR;  // randomization variants
-    else if (r.s.c.rk4) uniform_flags = kFlagsRK4;  // Runge-Kutta variants
-    else if (r.s.c.gnd_rotor) uniform_flags = kFlagsGndRotor;  // per-rotor ground heights
     cudaError_t e = rollout_setup();
     if (e != cudaSuccess) return e;
-    void* fn = rollout_kernel_ptr(uniform_flags, uniform_N, block);
+    void* fn = rollout_kernel_for(r.s, uniform_flags, block);
+    if (!fn) return cudaErrorInvalidConfiguration;
     if (grid <= 0 || grid > r.n_items) grid = r.n_items;
     void* args[] = {const_cast<RolloutArgs*>(&r)};
     return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, rollout_smem_bytes(block), s);
