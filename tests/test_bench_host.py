@@ -1,0 +1,60 @@
+"""Host legs of bench.py on CPU: the oracle split over host threads by environment range
+does the same work, and gives the same states, as one unsharded call."""
+import types
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+
+import bench
+import oracle
+from paper_2606_08039_gb300 import workloads as wl
+
+
+def _args(**kw):
+    a = dict(model="cf2x", integrator="euler", gnd_heights="com", actions="pid", controller="pid",
+             randomize=False)
+    a.update(kw)
+    return types.SimpleNamespace(**a)
+
+
+@pytest.mark.parametrize("kw", [{}, {"controller": "dsl"}, {"actions": "mixed"}])
+def test_sharded_oracle_equals_one_call(kw):
+    args = _args(**kw)
+    sw = wl.full_aero(1, n_envs=24)
+    one = bench.OracleShards(args, sw, 1, 1)
+    many = bench.OracleShards(args, sw, 1, 5)
+    assert len(many.shards) == 5
+    assert sum(sh["x"].shape[0] for sh in many.shards) == sw.n
+    with ThreadPoolExecutor(5) as pool:
+        for _ in range(2):
+            one.step(None)
+            many.step(pool)
+    x_many = np.concatenate([sh["x"] for sh in many.shards])
+    np.testing.assert_array_equal(one.shards[0]["x"], x_many)
+    np.testing.assert_array_equal(one.shards[0]["integ"], np.concatenate([sh["integ"] for sh in many.shards]))
+
+
+def test_sharded_oracle_under_randomization_keeps_each_environments_row():
+    args = _args(randomize=True)
+    sw = wl.full_aero(1, n_envs=10)
+    many = bench.OracleShards(args, sw, 1, 3)
+    _, _, _, dr = bench.oracle_workload(args, sw, 1)
+    rows = np.concatenate([sh["dr"].env_dr for sh in many.shards])
+    np.testing.assert_array_equal(rows, dr.env_dr)
+    many.step(None)
+    for sh in many.shards:
+        assert np.isfinite(sh["x"]).all()
+
+
+def test_more_threads_than_environments():
+    sw = wl.full_aero(1, n_envs=3)
+    sh = bench.OracleShards(_args(), sw, 1, 8)
+    assert len(sh.shards) == 3
+    assert bench.host_cores() >= 1
+
+
+def test_reference_arm_prints_nothing_on_other_ranks(monkeypatch, capsys):
+    monkeypatch.setenv("RANK", "1")
+    bench.run_reference(_args(steps=1, warmup=3, gpus=2))
+    assert capsys.readouterr().out == ""
