@@ -34,6 +34,66 @@ __device__ __forceinline__ float ex2_approx(float x)
     return r;
 }
 
+// Square root of the special function unit (sqrt.approx.ftz.f32, relative error near
+// 2^-23): the RPMs and the collective thrust of the controllers, outputs that no later
+// rounding depends on.
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// atan2 by reduction to a = min(|x|, |y|) / max(|x|, |y|) in [0, 1], then the octant:
+// atan(a) is the odd polynomial a P(a^2), P of degree 7, a near-minimax fit of the absolute
+// error on [0, 1] (Lawson's iteratively reweighted least squares; fit_atan.py beside this
+// file prints the coefficients and checks them): |error| below 1.4e-7 rad in float32, plus
+// the reciprocal's 2^-23. Signs of zeros as in C (the sign bit of x picks the half plane).
+// NaN in, NaN out; both |x| and |y| below 2^-126 give an angle of the right quadrant only.
+__device__ __forceinline__ float atan2_fast(float y, float x)
+{
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    const float a = mn * rcp_approx(fmaxf(mx, 1.17549435e-38f));
+    const float s = a * a;
+    float p = fmaf(s, -0.00405449513f, 0.0218627099f);
+    p = fmaf(p, s, -0.0559119843f);
+    p = fmaf(p, s, 0.0964217335f);
+    p = fmaf(p, s, -0.139086202f);
+    p = fmaf(p, s, 0.199465647f);
+    p = fmaf(p, s, -0.333298594f);
+    p = fmaf(p, s, 0.999999344f);
+    float r = a * p;
+    r = ay > ax ? 1.57079637f - r : r;
+    r = __float_as_int(x) < 0 ? 3.14159274f - r : r;
+    r = copysignf(r, y);
+    const float t = ax + ay;
+    return t != t ? t : r;
+}
+
+// asin(s) for s in [-1, 1] as atan2(s, sqrt((1 - s)(1 + s))).
+__device__ __forceinline__ float asin_fast(float s)
+{
+    return atan2_fast(s, sqrt_approx((1.f - s) * (1.f + s)));
+}
+
+// An angle reduced by a multiple of 2 pi to about [-pi, pi]: Cody and Waite's reduction
+// (2 pi = c_hi + c_lo, c_hi the float nearest 2 pi, c_lo the float nearest the remainder),
+// within a few 1e-7 rad of the exact remainder for |x| up to ~1e5 rad, where a float32
+// difference x - y would already have lost the ulp of x.
+__device__ __forceinline__ float reduce_angle(float x)
+{
+    const float k = rintf(x * 0.159154943f);
+    return fmaf(-k, -1.74845553e-7f, fmaf(-k, 6.28318548f, x));
+}
+
+// sin and cos of an angle reduced to [-pi, pi], where the special function unit's sine and
+// cosine are within 2^-21.4 absolute.
+__device__ __forceinline__ void sincos_reduced(float x, float* s, float* c)
+{
+    __sincosf(reduce_angle(x), s, c);
+}
+
 struct Drone {
     float p[3], q[4], v[3], w[3];
     float ip[3], ia[3];  // PID position / attitude error integrals
@@ -85,9 +145,9 @@ __device__ __forceinline__ void store_state(float4* __restrict__ S, long long n,
 __device__ __forceinline__ void rpy_of(const float q[4], float& roll, float& pitch, float& yaw)
 {
     const float w = q[0], x = q[1], y = q[2], z = q[3];
-    roll = atan2f(2.f * (w * x + y * z), 1.f - 2.f * (x * x + y * y));
-    pitch = asinf(fminf(1.f, fmaxf(-1.f, 2.f * (w * y - z * x))));
-    yaw = atan2f(2.f * (w * z + x * y), 1.f - 2.f * (y * y + z * z));
+    roll = atan2_fast(2.f * (w * x + y * z), 1.f - 2.f * (x * x + y * y));
+    pitch = asin_fast(fminf(1.f, fmaxf(-1.f, 2.f * (w * y - z * x))));
+    yaw = atan2_fast(2.f * (w * z + x * y), 1.f - 2.f * (y * y + z * z));
 }
 
 // Eq. motor, X configuration: F_i = k_f n_i^2, T = sum F_i,
@@ -140,7 +200,7 @@ __device__ __forceinline__ void attitude_and_mix(Drone& d, float T, float phi_t,
                         0.25f * (((T + c.mix_x[2] * tx) + c.mix_y[2] * ty) - tz),
                         0.25f * (((T + c.mix_x[3] * tx) + c.mix_y[3] * ty) + tz)};
 #pragma unroll
-    for (int i = 0; i < 4; ++i) rpm[i] = sqrtf(fminf(c.f_max, fmaxf(0.f, f[i])) * c.inv_kf);
+    for (int i = 0; i < 4; ++i) rpm[i] = sqrt_approx(fminf(c.f_max, fmaxf(0.f, f[i])) * c.inv_kf);
     yaw_err = e[2];
 }
 
@@ -161,14 +221,17 @@ __device__ __forceinline__ void pid(Drone& d, const float4 wp, const DevConsts& 
         if (kFF) acc[r] += aff[r];
     }
     acc[2] += c.g;
-    const float T = c.mass * sqrtf(acc[0] * acc[0] + acc[1] * acc[1] + acc[2] * acc[2]);
+    const float T = c.mass * sqrt_approx(acc[0] * acc[0] + acc[1] * acc[1] + acc[2] * acc[2]);
+    // the target yaw reduced once: its sine and cosine and the yaw error (wrapped again in
+    // attitude_and_mix) both take the reduced angle
+    const float psi_t = reduce_angle(wp.w);
     float sps, cps;
-    sincosf(wp.w, &sps, &cps);
+    __sincosf(psi_t, &sps, &cps);
     const float phi_t = (acc[0] * sps - acc[1] * cps) * c.inv_g;
     const float theta_t = (acc[0] * cps + acc[1] * sps) * c.inv_g;
     float roll, pitch, yaw;
     rpy_of(d.q, roll, pitch, yaw);
-    attitude_and_mix<false>(d, T, phi_t, theta_t, wp.w, 0.f, roll, pitch, yaw, c, rpm, yaw_err);
+    attitude_and_mix<false>(d, T, phi_t, theta_t, psi_t, 0.f, roll, pitch, yaw, c, rpm, yaw_err);
 }
 
 // DSLPIDControl's setpoint limiter (Section 4.2.1): the drone's setpoint moves towards the
@@ -189,7 +252,7 @@ __device__ __forceinline__ float4 dsl_setpoint(const Drone& d, const float4 wp, 
     sp.x += s * dx;
     sp.y += s * dy;
     sp.z += s * dz;
-    float e = wp.w - sp.w;
+    float e = reduce_angle(wp.w) - sp.w;
     e -= 2.f * kPi * floorf((e + kPi) * (0.5f / kPi));
     e = fminf(c.sp_step_yaw, fmaxf(-c.sp_step_yaw, e));
     float y = sp.w + e;
@@ -246,9 +309,9 @@ __device__ __forceinline__ void ext_action_rpm(Drone& d, const float4 act, int t
             acc[r] = c.pos_ki[r] * d.ip[r] + c.pos_kd[r] * (vt[r] - d.v[r]);
         }
         acc[2] += c.g;
-        T = c.mass * sqrtf(acc[0] * acc[0] + acc[1] * acc[1] + acc[2] * acc[2]);
+        T = c.mass * sqrt_approx(acc[0] * acc[0] + acc[1] * acc[1] + acc[2] * acc[2]);
         float sps, cps;
-        sincosf(yaw, &sps, &cps);
+        sincos_reduced(yaw, &sps, &cps);
         phi_t = (acc[0] * sps - acc[1] * cps) * c.inv_g;
         theta_t = (acc[0] * cps + acc[1] * sps) * c.inv_g;
     }

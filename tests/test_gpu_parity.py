@@ -95,13 +95,16 @@ def test_single_substep_all_flag_subsets(cuda, act_type):
     assert h.status()[0] == mdg.OK
 
 
-def test_pid_entry_point(cuda):
+@pytest.mark.parametrize("yaw_range", [3.0, 60.0, 3000.0])
+def test_pid_entry_point(cuda, yaw_range):
+    """The standalone PID against the oracle, target yaws within +-yaw_range rad (beyond
+    +-pi the kernel reduces the angle by 2 pi before its sine and cosine)."""
     n = 3000
     p, q, v, w = wl.random_states(21, n)
     integ = wl.uniform_range(-0.3, 0.3, 21, 10, 0, np.arange(n, dtype=np.uint64)[:, None],
                              np.arange(6, dtype=np.uint64)[None, :])
     wp = wl.waypoints(22, n)
-    wp[:, 3] = wl.uniform_range(-3, 3, 22, 9, 0, np.arange(n, dtype=np.uint64), 0)
+    wp[:, 3] = wl.uniform_range(-yaw_range, yaw_range, 22, 9, 0, np.arange(n, dtype=np.uint64), 0)
     h = mdg.Handle(np.ones(n, np.int32), np.zeros(n, np.uint32))
     state = mdg.pack_state(p, q, v, w, ip=integ[:, :3], ia=integ[:, 3:], device=cuda)
     x0, i0, _ = oracle_arrays(state)
