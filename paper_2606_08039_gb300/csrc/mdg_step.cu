@@ -205,10 +205,11 @@ __device__ __forceinline__ void attitude_and_mix(Drone& d, float T, float phi_t,
 }
 
 // kFF: add the feed-forward acceleration ff (DSLPIDControl's target_acc) to the position
-// loop's output (the standalone controller only; waypoint actions carry none).
+// loop's output (the standalone controller only; waypoint actions carry none). rpy_known:
+// the drone's roll, pitch and yaw when the caller already has them for this state.
 template <bool kFF = false>
 __device__ __forceinline__ void pid(Drone& d, const float4 wp, const DevConsts& c, float rpm[4], float ep[3],
-                                    float& yaw_err, float4 ff = float4{})
+                                    float& yaw_err, float4 ff = float4{}, const float* rpy_known = nullptr)
 {
     const float tgt[3] = {wp.x, wp.y, wp.z};
     const float aff[3] = {ff.x, ff.y, ff.z};
@@ -230,7 +231,11 @@ __device__ __forceinline__ void pid(Drone& d, const float4 wp, const DevConsts& 
     const float phi_t = (acc[0] * sps - acc[1] * cps) * c.inv_g;
     const float theta_t = (acc[0] * cps + acc[1] * sps) * c.inv_g;
     float roll, pitch, yaw;
-    rpy_of(d.q, roll, pitch, yaw);
+    if (rpy_known) {
+        roll = rpy_known[0], pitch = rpy_known[1], yaw = rpy_known[2];
+    } else {
+        rpy_of(d.q, roll, pitch, yaw);
+    }
     attitude_and_mix<false>(d, T, phi_t, theta_t, psi_t, 0.f, roll, pitch, yaw, c, rpm, yaw_err);
 }
 
@@ -348,16 +353,21 @@ __device__ __forceinline__ float downwash_pair(const float4 o, float px, float p
     return (dz > c.dw_dz_min && d2 < c.dw_max_xy2) ? f : 0.f;
 }
 
-// Downwash summed over the N drones of the environment in shared memory. The loop is
-// unrolled and branch-free so that independent pair terms interleave (a per-source warp
-// vote that skips sources below the whole warp measured slower: its branch serialises
-// the pairs).
+// Downwash summed over the N drones of the environment in shared memory; jl is the
+// drone's own index there. The loop is unrolled and branch-free so that independent pair
+// terms interleave (a per-source warp vote that skips sources below the whole warp
+// measured slower: its branch serialises the pairs). For a compile-time environment size
+// that is a power of two up to 8 the loop visits the N - 1 other drones, (jl + i) mod N;
+// otherwise it visits all N and the drone's own entry (dz = 0) drops out of the gate.
 template <int kN>
-__device__ __forceinline__ float downwash_sum(const float4* env_pos, int N_rt, float px, float py, float pz,
+__device__ __forceinline__ float downwash_sum(const float4* env_pos, int N_rt, int jl, float px, float py, float pz,
                                               const DevConsts& c)
 {
     float acc = 0.f;
-    if (kN > 0) {
+    if (kN > 0 && kN <= 8 && (kN & (kN - 1)) == 0) {
+#pragma unroll
+        for (int i = 1; i < (kN > 0 ? kN : 1); ++i) acc += downwash_pair(env_pos[(jl + i) & (kN - 1)], px, py, pz, c);
+    } else if (kN > 0) {
 #pragma unroll((kN > 0 && kN <= 8) ? kN : 8)
         for (int j = 0; j < kN; ++j) acc += downwash_pair(env_pos[j], px, py, pz, c);
     } else {
@@ -413,7 +423,7 @@ __device__ __forceinline__ float ground_increment(const Motor& m, float pz, floa
 // (> 0) fix the physics subset and environment size at compile time for uniform batches;
 // kFlags = 8 / kN <= 0 take them from the runtime arguments.
 template <int kFlags, int kN>
-__device__ __forceinline__ void substep(Drone& d, const Motor& m, int flags_rt, const float4* env_pos, int N_rt,
+__device__ __forceinline__ void substep(Drone& d, const Motor& m, int flags_rt, const float4* env_pos, int N_rt, int jl,
                                         const DevConsts& c, const float3 fe = float3{})
 {
     const int flags = fixed_subset(kFlags) >= 0 ? fixed_subset(kFlags) : flags_rt;
@@ -452,7 +462,7 @@ __device__ __forceinline__ void substep(Drone& d, const Motor& m, int flags_rt, 
         F[1] += kxy * d.v[1] + kr * r1;
         F[2] += kxy * d.v[2] + kr * r2;
     }
-    if (flags & MDG_DW) F[2] -= downwash_sum<kN>(env_pos, N_rt, d.p[0], d.p[1], d.p[2], c);
+    if (flags & MDG_DW) F[2] -= downwash_sum<kN>(env_pos, N_rt, jl, d.p[0], d.p[1], d.p[2], c);
     if (kFlags == kFlagsDR) {  // the wind's force, world frame
         F[0] += fe.x;
         F[1] += fe.y;
@@ -499,22 +509,30 @@ __device__ __forceinline__ bool finite_state(const Drone& d)
     return ok;
 }
 
-// KIN observation [p, q, roll/pitch/yaw, v, w, a_prev] as five float4.
-__device__ __forceinline__ void kin_values(const Drone& d, const float a[4], float4 o[5])
+// KIN observation [p, q, roll/pitch/yaw, v, w, a_prev] as five float4, given the angles.
+__device__ __forceinline__ void kin_values(const Drone& d, const float a[4], const float rpy[3], float4 o[5])
 {
-    float roll, pitch, yaw;
-    rpy_of(d.q, roll, pitch, yaw);
     o[0] = make_float4(d.p[0], d.p[1], d.p[2], d.q[0]);
-    o[1] = make_float4(d.q[1], d.q[2], d.q[3], roll);
-    o[2] = make_float4(pitch, yaw, d.v[0], d.v[1]);
+    o[1] = make_float4(d.q[1], d.q[2], d.q[3], rpy[0]);
+    o[2] = make_float4(rpy[1], rpy[2], d.v[0], d.v[1]);
     o[3] = make_float4(d.v[2], d.w[0], d.w[1], d.w[2]);
     o[4] = make_float4(a[0], a[1], a[2], a[3]);
 }
 
-__device__ __forceinline__ void write_kin(float* __restrict__ kin, long long g, const Drone& d, const float a[4])
+__device__ __forceinline__ void kin_values(const Drone& d, const float a[4], float4 o[5])
+{
+    float rpy[3];
+    rpy_of(d.q, rpy[0], rpy[1], rpy[2]);
+    kin_values(d, a, rpy, o);
+}
+
+// KIN row g; rpy: the angles when the caller has them (else computed here).
+__device__ __forceinline__ void write_kin(float* __restrict__ kin, long long g, const Drone& d, const float a[4],
+                                          const float* rpy = nullptr)
 {
     float4 v[5];
-    kin_values(d, a, v);
+    if (rpy) kin_values(d, a, rpy, v);
+    else kin_values(d, a, v);
     float4* o = reinterpret_cast<float4*>(kin + 20 * g);
 #pragma unroll
     for (int k = 0; k < 5; ++k) o[k] = v[k];
@@ -1007,7 +1025,7 @@ __device__ __forceinline__ void randomized_substeps(const StepArgs& a, Drone& d,
             ms.z = cmd[2] + (ms.z - cmd[2]) * lag;
             ms.w = cmd[3] + (ms.w - cmd[3]) * lag;
             const float n[4] = {ms.x, ms.y, ms.z, ms.w};
-            substep<kFlagsDR, kN>(d, motor(n, pc), env.flags, buf + env.ls, env.N, pc, fe);
+            substep<kFlagsDR, kN>(d, motor(n, pc), env.flags, buf + env.ls, env.N, t - env.ls, pc, fe);
         }
     }
     if (active) R.motor[g] = ms;
@@ -1026,7 +1044,7 @@ struct StateRate {
 
 template <int kFlags, int kN>
 __device__ __forceinline__ void stage_rate(const Drone& s, const Motor& m, int flags_rt, const float4* env_pos,
-                                           int N_rt, const DevConsts& c, StateRate& k)
+                                           int N_rt, int jl, const DevConsts& c, StateRate& k)
 {
     const int flags = fixed_subset(kFlags) >= 0 ? fixed_subset(kFlags) : flags_rt;
     const float qi = rsqrtf(s.q[0] * s.q[0] + s.q[1] * s.q[1] + s.q[2] * s.q[2] + s.q[3] * s.q[3]);
@@ -1047,7 +1065,7 @@ __device__ __forceinline__ void stage_rate(const Drone& s, const Motor& m, int f
         F[1] += kxy * s.v[1] + kr * r1;
         F[2] += kxy * s.v[2] + kr * r2;
     }
-    if (flags & MDG_DW) F[2] -= downwash_sum<kN>(env_pos, N_rt, s.p[0], s.p[1], s.p[2], c);
+    if (flags & MDG_DW) F[2] -= downwash_sum<kN>(env_pos, N_rt, jl, s.p[0], s.p[1], s.p[2], c);
     const float Jw0 = c.J[0] * s.w[0], Jw1 = c.J[1] * s.w[1], Jw2 = c.J[2] * s.w[2];
     k.w[0] = c.inv_J[0] * (m.tau[0] - (s.w[1] * Jw2 - s.w[2] * Jw1));
     k.w[1] = c.inv_J[1] * (m.tau[1] - (s.w[2] * Jw0 - s.w[0] * Jw2));
@@ -1089,7 +1107,7 @@ __device__ __forceinline__ void rk4_substeps(Drone& d, const Motor& m, const Env
             }
             if (active) {
                 StateRate k;
-                stage_rate<kFlags, kN>(st, m, env.flags, buf + env.ls, env.N, c, k);
+                stage_rate<kFlags, kN>(st, m, env.flags, buf + env.ls, env.N, t - env.ls, c, k);
                 const float wgt = (stage == 0 || stage == 3) ? 1.f : 2.f;
                 const float h = stage < 2 ? 0.5f * dt : dt;  // offset of the next stage
 #pragma unroll
@@ -1211,7 +1229,7 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
                 if (warp_local) __syncwarp();
                 else __syncthreads();
             }
-            if (active) substep<kFlags, kN>(d, m, env.flags, buf + env.ls, env.N, a.c);
+            if (active) substep<kFlags, kN>(d, m, env.flags, buf + env.ls, env.N, t - env.ls, a.c);
         }
     }
     bool bad = false;
@@ -1375,6 +1393,10 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
             }
         }
         int sub = 0;  // substeps taken in this item: the snapshot buffers alternate across steps
+        // roll, pitch, yaw of the current state when the previous step's observation computed
+        // them (the PID of the next step reads the same state)
+        float rpy_c[3] = {0.f, 0.f, 0.f};
+        bool have_rpy = false;
         for (int k = 0; k < r.K; ++k) {
             const float a_pre[4] = {rpm[0], rpm[1], rpm[2], rpm[3]};  // the RPMs of the step's start
             float4 next = {};
@@ -1387,7 +1409,7 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
                 } else if (is_pid) {
                     float ep[3], ye;
                     const float4 wp = (runtime_variant(kFlags) && a.c.dsl) ? dsl_setpoint(d, act, a.setpoints + g, a.c) : act;
-                    pid(d, wp, a.c, rpm, ep, ye);
+                    pid(d, wp, a.c, rpm, ep, ye, float4{}, have_rpy ? rpy_c : nullptr);
                 } else {
                     rpm[0] = fminf(a.c.max_rpm, fmaxf(0.f, act.x));
                     rpm[1] = fminf(a.c.max_rpm, fmaxf(0.f, act.y));
@@ -1395,6 +1417,7 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
                     rpm[3] = fminf(a.c.max_rpm, fmaxf(0.f, act.w));
                 }
             }
+            have_rpy = false;
             const Motor m = motor(rpm, a.c);
             const bool obs_now = r.obs_mode == 2 || (r.obs_mode == 1 && k == r.K - 1);
             bool delayed = false;
@@ -1413,7 +1436,7 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
                         if (warp_local) __syncwarp();
                         else __syncthreads();
                     }
-                    if (active) substep<kFlags, kN>(d, m, env.flags, buf + env.ls, env.N, a.c);
+                    if (active) substep<kFlags, kN>(d, m, env.flags, buf + env.ls, env.N, t - env.ls, a.c);
                 }
             }
             if (r.obs_mode == 2 || (r.obs_mode == 1 && k == r.K - 1)) {
@@ -1430,7 +1453,9 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
                             noisy_kin(a.kin + 20 * (o + g), d, rpm, a.rand->dr + (long long)env.id * MDG_DR_PARAMS,
                                       a.rand->seed, obs_step, g);
                     } else {
-                        write_kin(a.kin, o + g, d, rpm);
+                        rpy_of(d.q, rpy_c[0], rpy_c[1], rpy_c[2]);
+                        have_rpy = true;
+                        write_kin(a.kin, o + g, d, rpm, rpy_c);
                     }
                     write_knn<kN>(a.nbr_idx, a.nbr_rel, o + g, env_first, t - env.ls, d, pb + env.ls,
                                   s_vel + env.ls, env.N);
@@ -1700,7 +1725,7 @@ __global__ void __launch_bounds__(128) surrogate_fallback_kernel(const Surrogate
             float4* buf = s_pos[wib][s & 1];
             buf[lane] = make_float4(d.p[0], d.p[1], d.p[2], 0.f);
             __syncwarp();
-            if (active) substep<kFlagsGndRotor, -1>(d, m, flags, buf, N, a.c);
+            if (active) substep<kFlagsGndRotor, -1>(d, m, flags, buf, N, lane, a.c);
         }
         if (active) {
             store_state(a.state, a.n, g, d, false);
