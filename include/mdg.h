@@ -361,7 +361,8 @@ int mdg_render(mdg_handle h, const float* state, uint8_t* rgba, float* depth, in
  *   kin      device float32 [n_drones][20]: p, q, roll/pitch/yaw (ZYX), v, w, a_prev
  *   nbr_idx  device int32 [n_drones][4]: global indices of the 4 nearest other drones
  *            of the same environment (Euclidean distance, ties to the lower index),
- *            -1 where the environment has fewer than 5 drones
+ *            -1 where the environment has fewer than 5 drones; a drone whose squared
+ *            distance is not finite (a NaN or infinite position) is not listed
  *   nbr_rel  device float32 [n_drones][24] or NULL: per neighbour [p_i - p_j, v_i - v_j],
  *            zeros for padded slots */
 int mdg_obs(mdg_handle h, const float* state, float* kin, int32_t* nbr_idx, float* nbr_rel, void* stream);

@@ -429,17 +429,15 @@ __device__ __forceinline__ void substep(Drone& d, const Motor& m, int flags_rt, 
     const int flags = fixed_subset(kFlags) >= 0 ? fixed_subset(kFlags) : flags_rt;
     const float dt = c.dt_sim;
     // exponential map with the old body rate: q <- q (x) [cos(theta), sin(theta) w/|w|],
-    // theta = |w| dt/2. sin(theta)/|w| = (dt/2) sinc(theta); for theta^2 <= 0.6 both factors
-    // are the Taylor series of cos and sinc in theta^2 (truncation below 1.2e-10), with
-    // neither a square root nor a division. Larger rotations per substep take sqrtf/sincosf
-    // (the rarely taken branch below).
+    // theta = |w| dt/2. sin(theta)/|w| = (dt/2) sinc(theta); for theta^2 <= 0.1 both factors
+    // are the Taylor series of cos and sinc in theta^2 to theta^6 (truncation below 2.5e-9),
+    // with neither a square root nor a division. Larger rotations per substep (|w| above
+    // ~152 rad/s at 240 Hz) take sqrtf/sincosf (the rarely taken branch below).
     const float nw2 = d.w[0] * d.w[0] + d.w[1] * d.w[1] + d.w[2] * d.w[2];
     const float hdt = 0.5f * dt;
     const float t2 = nw2 * (hdt * hdt);
-    float co = fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, -2.7557319e-7f, 2.4801587e-5f), -1.3888889e-3f),
-                                      4.1666668e-2f), -0.5f), 1.0f);
-    float k = hdt * fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, -2.5052108e-8f, 2.7557319e-6f), -1.9841270e-4f),
-                                            8.3333333e-3f), -0.16666667f), 1.0f);
+    float co = fmaf(t2, fmaf(t2, fmaf(t2, -1.3888889e-3f, 4.1666668e-2f), -0.5f), 1.0f);
+    float k = hdt * fmaf(t2, fmaf(t2, fmaf(t2, -1.9841270e-4f, 8.3333333e-3f), -0.16666667f), 1.0f);
 
     // Only the body z axis in the world frame, r = R e_z (the third column of R), and R20 are
     // needed: thrust acts along r, the ground-effect gate reads R22 = r.z and R20, and the
@@ -473,7 +471,7 @@ __device__ __forceinline__ void substep(Drone& d, const Motor& m, int flags_rt, 
     const float wd0 = c.inv_J[0] * (m.tau[0] - (d.w[1] * Jw2 - d.w[2] * Jw1));
     const float wd1 = c.inv_J[1] * (m.tau[1] - (d.w[2] * Jw0 - d.w[0] * Jw2));
     const float wd2 = c.inv_J[2] * (m.tau[2] - (d.w[0] * Jw1 - d.w[1] * Jw0));
-    if (t2 > 0.6f) {
+    if (t2 > 0.1f) {
         const float nw = sqrtf(nw2);
         float sn;
         sincosf(hdt * nw, &sn, &co);
@@ -499,14 +497,16 @@ __device__ __forceinline__ void substep(Drone& d, const Motor& m, int flags_rt, 
     d.w[2] += dt * wd2;
 }
 
+// x * 0 is a zero for finite x and NaN for an infinite or NaN x, so the sum of the
+// products is zero exactly when the whole state is finite (one fused multiply-add each).
 __device__ __forceinline__ bool finite_state(const Drone& d)
 {
-    bool ok = true;
+    float z = 0.f;
 #pragma unroll
-    for (int r = 0; r < 3; ++r) ok = ok && isfinite(d.p[r]) && isfinite(d.v[r]) && isfinite(d.w[r]);
+    for (int r = 0; r < 3; ++r) z = fmaf(d.w[r], 0.f, fmaf(d.v[r], 0.f, fmaf(d.p[r], 0.f, z)));
 #pragma unroll
-    for (int r = 0; r < 4; ++r) ok = ok && isfinite(d.q[r]);
-    return ok;
+    for (int r = 0; r < 4; ++r) z = fmaf(d.q[r], 0.f, z);
+    return z == 0.f;
 }
 
 // KIN observation [p, q, roll/pitch/yaw, v, w, a_prev] as five float4, given the angles.
@@ -563,6 +563,39 @@ __device__ __forceinline__ void knn_best4(int j, const float p[3], const float4*
         c = b1 < b0;
         { const float tf = b0; const int ti = i0; b0 = c ? b1 : b0; i0 = c ? i1 : i0; b1 = c ? tf : b1; i1 = c ? ti : i1; }
     };
+    if constexpr (kN == 4) {
+        // The same list for four drones: the three others in index order, k = i + (i >= j),
+        // sorted by the stable three-element network (0,1) (1,2) (0,1) that swaps only on a
+        // strictly smaller distance; a distance that is not finite sorts last as +inf and
+        // leaves its slot empty, as the insertion above would not take it.
+        float dd[3];
+        int kk[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const int k = i + (i >= j ? 1 : 0);
+            const float4 o = env_pos[k];
+            const float dx = __fsub_rn(o.x, p[0]), dy = __fsub_rn(o.y, p[1]), dz = __fsub_rn(o.z, p[2]);
+            const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+            dd[i] = d2 < INFINITY ? d2 : INFINITY;
+            kk[i] = k;
+        }
+        auto cx = [&](int u, int v) {
+            const bool c = dd[v] < dd[u];
+            const float tf = dd[u];
+            const int ti = kk[u];
+            dd[u] = c ? dd[v] : dd[u];
+            kk[u] = c ? kk[v] : kk[u];
+            dd[v] = c ? tf : dd[v];
+            kk[v] = c ? ti : kk[v];
+        };
+        cx(0, 1);
+        cx(1, 2);
+        cx(0, 1);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) bi[i] = dd[i] < INFINITY ? kk[i] : -1;
+        bi[3] = -1;
+        return;
+    }
     if (kN > 0) {
 #pragma unroll((kN > 0 && kN <= 8) ? kN : 4)
         for (int k = 0; k < kN; ++k) consider(k);

@@ -171,8 +171,8 @@ def test_argument_errors(cuda):
 
 def test_exp_map_across_rotation_rates(cuda):
     # The kernel evaluates the exponential map by series in theta^2 = (|w| dt / 2)^2 up to
-    # theta^2 = 0.6 (|w| ~ 372 rad/s at 240 Hz) and by sincosf above: sweep across the switch.
-    rates = np.array([0.0, 1e-6, 1e-3, 1.0, 50.0, 300.0, 371.0, 372.0, 373.0, 380.0, 1000.0, 5000.0])
+    # theta^2 = 0.1 (|w| ~ 151.8 rad/s at 240 Hz) and by sincosf above: sweep across the switch.
+    rates = np.array([0.0, 1e-6, 1e-3, 1.0, 50.0, 150.0, 151.5, 151.8, 152.0, 153.0, 300.0, 1000.0, 5000.0])
     n = len(rates) * 8
     dirs = wl.uniform_range(-1, 1, 81, 2, 0, np.arange(n, dtype=np.uint64)[:, None], np.arange(3, dtype=np.uint64)[None])
     dirs = dirs.astype(np.float64)
@@ -202,3 +202,49 @@ def test_sync_reports_a_busy_stream_then_recovers(cuda):
     assert b"still busy" in mdg.lib().mdg_last_error()
     assert mdg.sync(s, timeout_ms=10000) == mdg.OK
     assert mdg.sync(s, timeout_ms=0) == mdg.OK
+
+
+def test_neighbour_ties_and_nonfinite_in_four_drone_environments(cuda):
+    """The compile-time 4-drone path (a uniform all-effects batch): drones on exact squares
+    tie pairwise (ties to the lower index), a coincident pair ties at distance 0, and a drone
+    with a NaN position is left out of its environment-mates' lists."""
+    n_envs = 64
+    dpe = np.full(n_envs, 4, np.int32)
+    flags = np.full(n_envs, mdg.GND | mdg.DRAG | mdg.DW, np.uint32)
+    sq = np.array([[0, 0], [1, 0], [1, 1], [0, 1]], np.float32)
+    p = np.zeros((4 * n_envs, 3), np.float32)
+    for e in range(n_envs):
+        p[4 * e:4 * e + 4, :2] = sq * (0.25 + 0.01 * e) + np.float32(3.0 * e)
+        p[4 * e:4 * e + 4, 2] = 1.0
+    p[4 * 1 + 3] = p[4 * 1 + 0]          # env 1: drones 0 and 3 coincide
+    p[4 * 2 + 1, 0] = np.nan             # env 2: drone 1 has a NaN position
+    q = np.tile(np.array([1, 0, 0, 0], np.float32), (4 * n_envs, 1))
+    h = mdg.Handle(dpe, flags)
+    state = mdg.pack_state(p, q, np.zeros_like(p), np.zeros_like(p), device=cuda)
+    kin, idx, rel = h.new_obs(cuda)
+    action = np.full((4 * n_envs, 4), HOVER, np.float32)
+    h.step_obs(state, _t(action, cuda), mdg.ACT_RPM, 1, kin, idx, rel)
+    torch.cuda.synchronize()
+    xg, _, _ = oracle_arrays(state)
+    idx = idx.cpu().numpy()
+    # level hover from rest keeps x and y, and every drone of an environment at one height
+    np.testing.assert_array_equal(xg[:, :2][np.isfinite(xg[:, 0])], p[:, :2][np.isfinite(p[:, 0])])
+    square = np.array([[1, 3, 2, -1], [0, 2, 3, -1], [1, 3, 0, -1], [0, 2, 1, -1]])
+    for e in [0] + list(range(3, n_envs)):
+        np.testing.assert_array_equal(idx[4 * e:4 * e + 4], np.where(square >= 0, square + 4 * e, -1),
+                                      err_msg=f"env {e}")
+        for j in range(4):
+            i_ref, _ = oracle.knn(xg[4 * e:4 * e + 4], j, 4 * e)
+            np.testing.assert_array_equal(idx[4 * e + j], i_ref)
+    # env 1: 0 and 3 at distance 0 from each other
+    b = 4
+    np.testing.assert_array_equal(idx[b + 0], [b + 3, b + 1, b + 2, -1])
+    np.testing.assert_array_equal(idx[b + 3], [b + 0, b + 1, b + 2, -1])
+    # env 2: drone 1 is not listed by the others; its own list holds nothing finite
+    b = 8
+    np.testing.assert_array_equal(idx[b + 0], [b + 3, b + 2, -1, -1])
+    np.testing.assert_array_equal(idx[b + 2], [b + 3, b + 0, -1, -1])
+    np.testing.assert_array_equal(idx[b + 3], [b + 0, b + 2, -1, -1])
+    np.testing.assert_array_equal(idx[b + 1], [-1, -1, -1, -1])
+    rc, bits, first = h.status()
+    assert rc == mdg.ERR_NONFINITE and first == b + 1
