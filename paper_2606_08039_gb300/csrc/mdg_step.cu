@@ -752,13 +752,16 @@ __device__ __forceinline__ void check_env(EnvSlot& e, int t, int n_drones, uint3
 }
 
 
+// kN > 0: the batch is uniform with kN drones per environment (the compile-time variants
+// are launched only then), so the division below is by a constant.
+template <int kN = 0>
 __device__ __forceinline__ EnvSlot tile_env(const StepArgs& a, const TileInfo& ti, int* s_off, int* s_info)
 {
     const int t = threadIdx.x;
     EnvSlot e = {0, 0, 0, 0, 0};
     if (a.uniform_N > 0) {
         if (t < ti.n_drones) {
-            const int k = t / a.uniform_N;
+            const int k = t / (kN > 0 ? kN : a.uniform_N);
             e.id = ti.first_env + k;
             e.ls = k * a.uniform_N;
             e.N = a.uniform_N;
@@ -1211,7 +1214,7 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
         if (a.act_type != MDG_ACT_RPM) s4 = a.state[4 * a.n + g];
         act = a.action[g];
     }
-    const EnvSlot env = tile_env(a, tile, s_off, s_info);
+    const EnvSlot env = tile_env<kN>(a, tile, s_off, s_info);
     const bool is_pid = env.act == MDG_ACT_PID;
     const bool loops = is_pid || (runtime_variant(kFlags) && uses_loops(env.act));
 
@@ -1346,7 +1349,7 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
             n_drones = n_envs * a.uniform_N;
             bits = a.uniform_bits;
             if (t < n_drones) {
-                const int k = t / a.uniform_N;
+                const int k = t / (kN > 0 ? kN : a.uniform_N);
                 env.id = first_env + k;
                 env.ls = k * a.uniform_N;
                 env.N = a.uniform_N;
