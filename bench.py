@@ -6,19 +6,23 @@ physics substeps at 240 Hz with motor model, ground effect, drag and pairwise do
 and the KIN + 4-neighbour observations -- one launch of the fused step kernel through
 the C ABI (mdg_step_obs). The metric is drone-substeps per second.
 
-Timing: W untimed warm-up steps, then K timed steps, each bracketed by CUDA events on the
-launching stream with the L2 cache flushed between steps, outside the events: a 512 MiB
-buffer is written and then read back, so that L2 holds only clean lines of that buffer
-and the timed step neither finds its own data in L2 nor pays the write-back of the flush.
-Every 1000 control steps (one episode of the workload) the swarm is reset to its initial
-state, outside the timed region. Under torchrun each rank runs its own replica on
-its own GPU (environments are independent: weak scaling, no data-path collective); the
-time is the max over ranks.
+Timing: W untimed warm-up steps, then K timed steps back to back with inputs larger than
+L2: 16 independent swarms of the full size, each with its own state, waypoints and
+observation buffers, are stepped in rotation (one CUDA graph holds one step of every swarm
+and is replayed), so each step's data was last touched 15 steps and ~300 MB earlier, well
+beyond the 129 MB L2; CUDA events on the launching stream bracket the whole region, with a
+barrier and a synchronisation on both sides. Each swarm is reset to its initial state
+before a region (outside it); a region holds at most one 1000-step episode per swarm.
+Under torchrun each rank runs its own swarms on its own GPU (environments are independent:
+weak scaling, no data-path collective); the time is the max over ranks.
 
-Also reported: an end-to-end number through the public API with host buffers (waypoints
-copied in from pinned memory and the observations copied back every step), the roofline
-of the step kernel against the measured HBM bandwidth, SM clocks sampled during the timed
-region, and the FP64 oracle timed on the host cores on a bounded sample.
+Also reported, on swarm 0: the same step isolated (the L2 flushed before every step -- a
+512 MiB buffer written, then read back -- and every step bracketed by its own events, so
+one launch's latency is counted per step), an end-to-end number through the public API
+with host buffers (waypoints read and observations written in pinned host memory every
+step, synchronised every step), the 1000-step episode as one persistent launch, the
+roofline of the step kernel against the measured HBM bandwidth, SM clocks sampled during
+the timed region, and the FP64 oracle timed on the host cores on a bounded sample.
 
 --model / --integrator / --gnd-heights select the drone model (CF2X, CF2P, RACE), Euler or
 RK4 substeps and the ground-effect heights (centre of mass, or per rotor) for the dynamics
@@ -163,7 +167,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -172,9 +176,12 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
-    def stop(self) -> dict:
+    def stop(self, windows=None) -> dict:
+        """Median SM clock, maximum clock and throttle reasons over the samples read inside
+        `windows` (host perf_counter intervals of the timed region; all samples if none fall
+        inside)."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
         self.proc.terminate()
@@ -183,9 +190,14 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.thread.join(timeout=2)
+        lines = self.lines
+        if windows:
+            inside = [(t, l) for t, l in lines if any(a <= t <= b + 0.06 for a, b in windows)]
+            if inside:
+                lines = inside
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        for _, line in lines:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -198,7 +210,8 @@ class ClockSampler:
                 if f[5 + k].lower().startswith("active"):
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "window": "timed region" if windows and lines is not self.lines else "whole run"}
 
 
 def replica_seed(rank: int) -> int:
@@ -232,10 +245,11 @@ def host_cores() -> int:
 class OracleShards:
     """The full-aero swarm's oracle inputs split into `n_shards` contiguous environment
     ranges, one per host thread. The environments are independent, so each range runs the
-    oracle's own control-step routine, unchanged, on its own slice; ctypes releases the GIL
-    for the duration of the C call, so the threads run on separate cores. Neighbour indices
-    and the randomization's counters are shard-relative (the values differ from one
-    unsharded call, the work does not)."""
+    oracle's own control-step routine, unchanged, on its own slice and its own buffers
+    (oracle.control_steps_into: no copies per call); ctypes releases the GIL for the
+    duration of the C call, so the threads run on separate cores. Neighbour indices and the
+    randomization's counters are shard-relative (the values differ from one unsharded call,
+    the work does not)."""
 
     def __init__(self, args, sw, seed: int, n_shards: int):
         import oracle
@@ -248,9 +262,11 @@ class OracleShards:
         for e0, e1 in zip(bounds[:-1], bounds[1:]):
             d0, d1 = int(sw.env_off[e0]), int(sw.env_off[e1])
             sh = {"off": (sw.env_off[e0:e1 + 1] - d0).astype(np.int32), "flags": flags[e0:e1].copy(),
-                  "acts": acts[e0:e1].copy(), "x": x[d0:d1].copy(), "integ": np.zeros((d1 - d0, 6)),
-                  "a": np.zeros((d1 - d0, 4)), "wp": np.ascontiguousarray(wp[:, d0:d1]),
-                  "sp": None if sp is None else sp[d0:d1].copy(), "dr": None}
+                  "acts": acts[e0:e1].copy(), "x": x[d0:d1].astype(np.float64), "integ": np.zeros((d1 - d0, 6)),
+                  "a": np.zeros((d1 - d0, 4)), "wp": np.ascontiguousarray(wp[:, d0:d1], dtype=np.float64),
+                  "sp": None if sp is None else sp[d0:d1].copy(), "dr": None,
+                  "kin": np.zeros((d1 - d0, 20)), "idx": np.zeros((d1 - d0, 4), np.int32),
+                  "rel": np.zeros((d1 - d0, 24))}
             if dr is not None:
                 r = oracle.Randomization(e1 - e0, d1 - d0, dr.hist.shape[0], dr.seed)
                 r.env_dr[:] = dr.env_dr[e0:e1]
@@ -259,9 +275,9 @@ class OracleShards:
         self.n = sw.n
 
     def _run(self, sh):
-        sh["x"], sh["integ"], sh["a"], *_ = self.oracle.control_steps(
-            self.P, sh["off"], sh["flags"], sh["acts"], sh["x"], sh["integ"], sh["a"], sh["wp"], N_SUB, obs=True,
-            setpoint=sh["sp"], dr=sh["dr"])
+        self.oracle.control_steps_into(self.P, sh["off"], sh["flags"], sh["acts"], sh["x"], sh["integ"], sh["a"],
+                                       sh["wp"], N_SUB, sh["kin"], sh["idx"], sh["rel"], setpoint=sh["sp"],
+                                       dr=sh["dr"])
 
     def step(self, pool) -> None:
         """One control step (PID + substeps + observations) of every shard."""
@@ -315,14 +331,18 @@ def cpu_baseline(args, seconds_target: float = 10.0, all_cores_seconds: float = 
 def run_reference(args) -> None:
     """Reference arm: the FP64 oracle timed as it stands on the host cores (the environments
     split into one range per thread), on a bounded sample of the same workload per step
-    (2048 environments x 4 drones per core, at most the whole swarm; one control step)."""
+    (one control step of a subset of the swarm's environments, sized so that the whole run
+    takes about a minute)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from concurrent.futures import ThreadPoolExecutor
     from paper_2606_08039_gb300 import workloads as wl
     cores = host_cores()
-    n_envs = min(16384, 2048 * cores)
+    # about a minute of host work for the whole run: 2048 environments per core for 5000
+    # steps, fewer per step for more steps (multiples of 64, at most the whole swarm, at
+    # least 4096 so that the threads' per-step overhead stays small)
+    n_envs = int(min(16384, max(4096, round(2048 * cores * 5000 / max(1, args.steps + args.warmup) / 64) * 64)))
     sw = wl.full_aero(1, n_envs=n_envs)
     shards = OracleShards(args, sw, 1, cores)
     pool = ThreadPoolExecutor(cores) if cores > 1 else None
@@ -419,6 +439,10 @@ def binding_roofline(bytes_launch: float, flops_launch: float, sec: float, peaks
 
 
 EPISODE_REPS = 3
+N_SWARMS = 16            # independent full-size swarms stepped in rotation in the timed region
+SWARM_SEED_STRIDE = 97   # seed of swarm k: the rank's replica seed + 97 k
+SWARM_BYTES = 65536 * (96 + 16 + 80 + 16 + 96)  # per swarm and step: state planes, waypoints, KIN, indices, features
+ISOLATED_STEPS = 1000    # steps of the isolated (flushed, per-step events) measurement
 # algorithmic bytes of a K-step rollout with observations every step: the state read and
 # written once (80 B + 96 B), the waypoint once (16 B), KIN + indices + features every step
 BYTES_OBS_PER_DRONE_STEP = 80 + 16 + 96
@@ -833,7 +857,7 @@ def run_surrogate(args) -> None:
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--steps", type=int, default=16000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="mdg", choices=["mdg", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=200)
@@ -888,44 +912,61 @@ def main() -> None:
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
-    # workload: the full-aero swarm, one independent replica per rank
-    sw = wl.full_aero(replica_seed(rank))
-    h = mdg.Handle(sw.drones_per_env, sw.flags, library_constants(args))
-    init_state = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=dev)
-    state = init_state.clone()
-    # the action of every drone: waypoints for the PID (the headline), else the chosen type
+    # workload: N_SWARMS independent full-aero swarms per rank (swarm 0 is the rank's
+    # replica), each with its own handle, state, waypoints and observation buffers
     c_lib = library_constants(args)
-    types = action_types(args, sw.n_envs, replica_seed(rank))
     act_type = mdg.ACT_MIXED if args.actions == "mixed" else ACTION_CHOICES[args.actions]
-    if args.actions == "pid":
-        act_np = wl.waypoints(replica_seed(rank), sw.n)
-    else:
-        act_np = wl.typed_actions(sw.drones_per_env, types, replica_seed(rank), 0, c_lib.hover_rpm(),
-                                  c_lib.mass * c_lib.g)
-    if act_type == mdg.ACT_MIXED:
-        h.set_action_types(types)
-    setpoints = None
-    if args.controller == "dsl":
-        setpoints = h.new_setpoints(dev)
-        h.set_setpoints(setpoints)
-    dr_state = None
-    if args.randomize:
-        dr_state = h.new_randomization_state(DR_DEPTH, dev)
-        table = torch.as_tensor(wl.dr_table(replica_seed(rank), sw.n_envs, depth=DR_DEPTH), device=dev)
-        h.set_randomization(table, *dr_state, seed=DR_SEED)
-    wp_host = torch.from_numpy(act_np).pin_memory()
-    wp = wp_host.to(dev)
 
-    def reset():
-        state.copy_(init_state)
-        if setpoints is not None:
-            setpoints.fill_(float("nan"))
-        if dr_state is not None:
-            dr_state[0].fill_(float("nan"))
-            dr_state[1].fill_(float("nan"))
-            dr_state[2].zero_()
-            dr_state[2][:, 3] = -1.0
-    kin, idx, rel = h.new_obs(dev)
+    class Swarm:
+        def __init__(self, seed: int):
+            sw = wl.full_aero(seed)
+            self.sw = sw
+            self.h = mdg.Handle(sw.drones_per_env, sw.flags, library_constants(args))
+            self.init_state = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=dev)
+            self.state = self.init_state.clone()
+            # the action of every drone: waypoints for the PID (the headline), else the chosen type
+            self.types = action_types(args, sw.n_envs, seed)
+            if args.actions == "pid":
+                act_np = wl.waypoints(seed, sw.n)
+            else:
+                act_np = wl.typed_actions(sw.drones_per_env, self.types, seed, 0, c_lib.hover_rpm(),
+                                          c_lib.mass * c_lib.g)
+            if act_type == mdg.ACT_MIXED:
+                self.h.set_action_types(self.types)
+            self.setpoints = None
+            if args.controller == "dsl":
+                self.setpoints = self.h.new_setpoints(dev)
+                self.h.set_setpoints(self.setpoints)
+            self.dr_state = None
+            if args.randomize:
+                self.dr_state = self.h.new_randomization_state(DR_DEPTH, dev)
+                table = torch.as_tensor(wl.dr_table(seed, sw.n_envs, depth=DR_DEPTH), device=dev)
+                self.h.set_randomization(table, *self.dr_state, seed=DR_SEED)
+            self.wp_host = torch.from_numpy(act_np).pin_memory()
+            self.wp = self.wp_host.to(dev)
+            self.kin, self.idx, self.rel = self.h.new_obs(dev)
+            self.steps_done = 0
+
+        def reset(self):
+            self.state.copy_(self.init_state)
+            if self.setpoints is not None:
+                self.setpoints.fill_(float("nan"))
+            if self.dr_state is not None:
+                self.dr_state[0].fill_(float("nan"))
+                self.dr_state[1].fill_(float("nan"))
+                self.dr_state[2].zero_()
+                self.dr_state[2][:, 3] = -1.0
+            self.steps_done = 0
+
+        def step(self, stream):
+            self.h.step_obs(self.state, self.wp, act_type, N_SUB, self.kin, self.idx, self.rel, stream=stream)
+            self.steps_done += 1
+
+    swarms = [Swarm(replica_seed(rank) + SWARM_SEED_STRIDE * k) for k in range(N_SWARMS)]
+    s0 = swarms[0]
+    sw, h, types = s0.sw, s0.h, s0.types
+    state, wp, wp_host, kin, idx, rel = s0.state, s0.wp, s0.wp_host, s0.kin, s0.idx, s0.rel
+    reset = s0.reset
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     flush_sink = torch.empty((), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -933,47 +974,80 @@ def main() -> None:
     def flush_l2():
         flush.fill_(1.0)
         torch.sum(flush, dim=0, out=flush_sink)
-    steps_done = 0
 
-    def step():
-        nonlocal steps_done
-        if steps_done and steps_done % EPISODE == 0:
-            reset()
-        h.step_obs(state, wp, act_type, N_SUB, kin, idx, rel, stream=stream)
-        steps_done += 1
-
-    for _ in range(args.warmup):
-        flush_l2()
-        step()
+    for i in range(args.warmup):
+        swarms[i % N_SWARMS].step(stream)
     torch.cuda.synchronize()
-    rc, _, _ = h.status()
+    # one step of every swarm, in rotation, as one CUDA graph (16 launches of the step kernel)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        cap = torch.cuda.current_stream(dev)
+        for sm in swarms:
+            sm.h.step_obs(sm.state, sm.wp, act_type, N_SUB, sm.kin, sm.idx, sm.rel, stream=cap)
+    for sm in swarms:
+        sm.reset()
+        sm.h.status()
+    torch.cuda.synchronize()
 
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    # Timed region: K control steps back to back, swarm after swarm (inputs larger than L2:
+    # each swarm's state, waypoints and observations are touched again only after the 15
+    # other swarms' 299 MB), events around the whole region. Every swarm is reset to its
+    # initial state outside the region; a region holds at most one episode per swarm.
+    seg_max = N_SWARMS * EPISODE
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)  # let the sampler start before the timed region
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    wall0 = time.perf_counter()
-    for i in range(args.steps):
+    total_ms = 0.0
+    wall = 0.0
+    windows = []
+    remaining = args.steps
+    while remaining:
+        n_seg = min(remaining, seg_max)
+        for sm in swarms:
+            if sm.steps_done:
+                sm.reset()
         flush_l2()
-        if steps_done % EPISODE == 0 and steps_done:
-            reset()
-        starts[i].record(stream)
-        h.step_obs(state, wp, act_type, N_SUB, kin, idx, rel, stream=stream)
-        ends[i].record(stream)
-        steps_done += 1
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        ev0.record(stream)
+        for _ in range(n_seg // N_SWARMS):
+            graph.replay()
+        for k in range(n_seg % N_SWARMS):
+            swarms[k].step(stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        windows.append((wall0, time.perf_counter()))
+        wall += windows[-1][1] - wall0
+        total_ms += ev0.elapsed_time(ev1)
+        for k, sm in enumerate(swarms):
+            sm.steps_done += n_seg // N_SWARMS + (1 if k < n_seg % N_SWARMS else 0)
+        remaining -= n_seg
+    clk = clocks.stop(windows)
+    nonfinite = False
+    for sm in swarms:
+        rc, bits, first = sm.h.status()
+        nonfinite = nonfinite or bool(bits & mdg.STATUS_NONFINITE)
+
+    # The same step isolated: swarm 0 alone, the L2 flushed before every step and every
+    # step bracketed by its own events (launch and timestamp latency included per step).
+    n_iso = min(args.steps, ISOLATED_STEPS)
+    reset()
+    iso_starts = [torch.cuda.Event(enable_timing=True) for _ in range(n_iso)]
+    iso_ends = [torch.cuda.Event(enable_timing=True) for _ in range(n_iso)]
+    for i in range(n_iso):
+        flush_l2()
+        iso_starts[i].record(stream)
+        s0.step(stream)
+        iso_ends[i].record(stream)
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    wall = time.perf_counter() - wall0
-    clk = clocks.stop()
-    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = float(sum(ms))
-    rc, bits, first = h.status()
-    nonfinite = bool(bits & mdg.STATUS_NONFINITE)
+    iso_ms = float(sum(a.elapsed_time(b) for a, b in zip(iso_starts, iso_ends)))
+    h.status()
 
     # end to end through the public API with host buffers
     kin_h = torch.empty(kin.shape, dtype=kin.dtype).pin_memory()
@@ -983,11 +1057,20 @@ def main() -> None:
     e_ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.e2e_steps)]
     reset()
     # the step kernel reads the waypoints from, and writes the observations to, the pinned
-    # host buffers itself (mdg_step_obs_host): the transfers overlap its arithmetic
+    # host buffers itself (mdg_step_obs_host): the transfers overlap its arithmetic. Under
+    # randomization (whose observation noise and delay the host-buffer path does not take)
+    # the waypoints are copied in and the observations copied out around mdg_step_obs.
     for i in range(args.e2e_steps):
         flush_l2()
         e_starts[i].record(stream)
-        h.step_obs_host(state, wp_host, act_type, N_SUB, kin_h, idx_h, rel_h, stream=stream)
+        if args.randomize:
+            wp.copy_(wp_host, non_blocking=True)
+            h.step_obs(state, wp, act_type, N_SUB, kin, idx, rel, stream=stream)
+            kin_h.copy_(kin, non_blocking=True)
+            idx_h.copy_(idx, non_blocking=True)
+            rel_h.copy_(rel, non_blocking=True)
+        else:
+            h.step_obs_host(state, wp_host, act_type, N_SUB, kin_h, idx_h, rel_h, stream=stream)
         e_ends[i].record(stream)
         e_ends[i].synchronize()
     e2e_ms = float(sum(s.elapsed_time(e) for s, e in zip(e_starts, e_ends)))
@@ -1015,9 +1098,10 @@ def main() -> None:
     ep_ms = float(sum(a.elapsed_time(b) for a, b in zip(ep_starts, ep_ends)))
     del ep_kin, ep_idx, ep_rel
 
-    total_ms, e2e_ms, ep_ms = combine_over_ranks([total_ms, e2e_ms, ep_ms], world, device=dev)
+    total_ms, e2e_ms, ep_ms, iso_ms = combine_over_ranks([total_ms, e2e_ms, ep_ms, iso_ms], world, device=dev)
     value = throughput(sw.n * N_SUB, world, args.steps, total_ms)
     e2e_value = throughput(sw.n * N_SUB, world, args.e2e_steps, e2e_ms)
+    iso_value = throughput(sw.n * N_SUB, world, n_iso, iso_ms)
 
     if rank == 0:
         peaks = measured_peaks()
@@ -1040,18 +1124,30 @@ def main() -> None:
                                    "PID waypoints, 240 Hz physics / 48 Hz control (5 substeps), KIN + 4-NN obs; "
                                    "one step = one control step (one fused kernel launch)",
                        "n_drones_per_gpu": sw.n, "n_substeps": N_SUB, "block_size": h.block_size,
-                       "l2": "flushed between timed steps (512 MiB written, then read back)",
+                       "l2": f"inputs larger than L2: {N_SWARMS} independent swarms of this size stepped in "
+                             f"rotation, each swarm's {SWARM_BYTES / 2**20:.0f} MiB of state, waypoints and "
+                             f"observations touched again after the other swarms' "
+                             f"{(N_SWARMS - 1) * SWARM_BYTES / 2**20:.0f} MiB; no flush inside the timed region",
+                       "timing": f"CUDA graph of {N_SWARMS} step launches (one per swarm) replayed back to back; "
+                                 "events around the whole timed region",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": args.e2e_steps,
-                    "path": "mdg_step_obs_host: waypoints read and observations written in pinned host memory "
-                            "by the step kernel, synchronised on every step"},
+                    "path": ("mdg_step_obs with the waypoints copied in from and the observations copied out to "
+                             "pinned host memory around it, synchronised on every step" if args.randomize else
+                             "mdg_step_obs_host: waypoints read and observations written in pinned host memory "
+                             "by the step kernel, synchronised on every step")},
             "gpu_launches": args.steps,
             "roofline": roofline,
             "clocks": clk,
             "wall_s_timed_region": wall,
             "nonfinite_during_timing": nonfinite,
             "episode": episode_line(sw.n, world, ep_ms, peaks, flops_launch),
+            "isolated_step": {
+                "what": "swarm 0 alone, L2 flushed (512 MiB written, then read back) before every step, every "
+                        "step bracketed by its own events: one launch's latency and timestamps included per step",
+                "value": iso_value, "unit": UNIT, "ms_per_step": iso_ms / n_iso, "steps": n_iso,
+                "roofline": binding_roofline(bytes_launch, flops_launch, iso_ms / n_iso * 1e-3, peaks)},
         }
         out["config"].update(model_config(args))
         if world == 1 and not args.no_cpu_baseline:

@@ -434,3 +434,25 @@ def control_steps(p: Params, env_off, env_flags, env_act, x, integ, a_prev, acti
     if obs:
         return x, integ, a_prev, kin_o, nbr_i, nbr_r
     return x, integ, a_prev
+
+
+def control_steps_into(p: Params, env_off, env_flags, env_act, x, integ, a_prev, actions, n_sub: int,
+                       kin, nbr_idx, nbr_rel, setpoint=None, dr: "Randomization | None" = None) -> None:
+    """control_steps with observations on caller-owned C-contiguous arrays: x [n,13], integ
+    [n,6], a_prev [n,4] (float64) are updated in place, kin [n,20], nbr_rel [n,24] (float64)
+    and nbr_idx [n,4] (int32) written; env_off, env_flags, env_act int32. The same C routine
+    without the wrapper's copies (for timing the oracle on many threads)."""
+    for a, dt in ((x, np.float64), (integ, np.float64), (a_prev, np.float64), (actions, np.float64),
+                  (kin, np.float64), (nbr_rel, np.float64), (nbr_idx, np.int32), (env_off, np.int32),
+                  (env_flags, np.int32), (env_act, np.int32)):
+        assert a.dtype == dt and a.flags.c_contiguous
+    n = x.shape[0]
+    K = actions.shape[0]
+    assert actions.shape == (K, n, 4) and kin.shape == (n, 20) and nbr_idx.shape == (n, 4)
+    rc = lib().orc_control_steps(ctypes.byref(p), env_off.shape[0] - 1, _iptr(env_off), _iptr(env_flags),
+                                 _iptr(env_act), _dptr(x), _dptr(integ), _dptr(a_prev), _dptr(actions), K, int(n_sub),
+                                 _dptr(kin), _iptr(nbr_idx), _dptr(nbr_rel),
+                                 _dptr(setpoint) if setpoint is not None else None,
+                                 ctypes.byref(dr.struct()) if dr is not None else None)
+    if rc != 0:
+        raise ValueError("orc_control_steps rejected its arguments")

@@ -58,3 +58,21 @@ def test_reference_arm_prints_nothing_on_other_ranks(monkeypatch, capsys):
     monkeypatch.setenv("RANK", "1")
     bench.run_reference(_args(steps=1, warmup=3, gpus=2))
     assert capsys.readouterr().out == ""
+
+
+def test_in_place_oracle_call_equals_the_wrapper():
+    """oracle.control_steps_into (no copies, used for timing) gives control_steps' results."""
+    args = _args()
+    sw = wl.full_aero(1, n_envs=12)
+    sh = bench.OracleShards(args, sw, 1, 1)
+    acts, wp, sp, dr = bench.oracle_workload(args, sw, 1)
+    x0 = sw.x13().astype(np.float64)
+    x, integ, a, kin, nbr_i, nbr_r = oracle.control_steps(sh.P, sw.env_off, sw.flags.astype(np.int32), acts, x0,
+                                                          np.zeros((sw.n, 6)), np.zeros((sw.n, 4)), wp, 5, obs=True)
+    sh.step(None)
+    s0 = sh.shards[0]
+    np.testing.assert_array_equal(s0["x"], x)
+    np.testing.assert_array_equal(s0["integ"], integ)
+    np.testing.assert_array_equal(s0["kin"], kin)
+    np.testing.assert_array_equal(s0["idx"], nbr_i)
+    np.testing.assert_array_equal(s0["rel"], nbr_r)
