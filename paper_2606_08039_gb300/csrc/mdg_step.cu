@@ -810,17 +810,21 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long z)
 }
 
 // U[0, 1) with 24 random bits (exact in float) for the counters (seed, stream, step,
-// index, comp), each mixed in by one SplitMix64 round.
-__device__ __forceinline__ float counter_uniform(unsigned long long seed, unsigned long long stream,
-                                                 unsigned long long step, unsigned long long index,
-                                                 unsigned long long comp)
+// index, comp), each mixed in by one SplitMix64 round. The rounds of (seed, stream, step,
+// index) form a prefix that all components of one draw share: counter_prefix mixes it once
+// and prefix_uniform adds the component's round (the same values as mixing all five).
+__device__ __forceinline__ unsigned long long counter_prefix(unsigned long long seed, unsigned long long stream,
+                                                             unsigned long long step, unsigned long long index)
 {
     unsigned long long h = splitmix64(seed);
     h = splitmix64(h ^ stream);
     h = splitmix64(h ^ step);
-    h = splitmix64(h ^ index);
-    h = splitmix64(h ^ comp);
-    return (float)(h >> 40) * (1.f / 16777216.f);
+    return splitmix64(h ^ index);
+}
+
+__device__ __forceinline__ float prefix_uniform(unsigned long long prefix, unsigned long long comp)
+{
+    return (float)(splitmix64(prefix ^ comp) >> 40) * (1.f / 16777216.f);
 }
 
 // The physics constants of an environment under its randomization row: factors on mass,
@@ -890,6 +894,7 @@ __device__ __forceinline__ void wind_step(const float* row, float4& s0, float4& 
 {
     const int model = (int)row[MDG_DR_WIND];
     const unsigned long long step = (unsigned long long)s1.w;
+    const unsigned long long wind_key = counter_prefix(seed, kStreamWind, step, env);
     F[0] = F[1] = F[2] = vw[0] = vw[1] = vw[2] = 0.f;
     if (model & MDG_WIND_CONSTANT) {
         vw[0] += row[MDG_DR_VWIND];
@@ -900,10 +905,10 @@ __device__ __forceinline__ void wind_step(const float* row, float4& s0, float4& 
         const float h = row[MDG_DR_DRY_H];
         const float L = h / powf(0.177f + 8.23e-4f * h, 1.2f);
         const float alpha = expf(-dt * row[MDG_DR_DRY_V] / L);
-        const float u1 = 1.f - counter_uniform(seed, kStreamWind, step, env, 0);
-        const float u2 = counter_uniform(seed, kStreamWind, step, env, 1);
-        const float u3 = 1.f - counter_uniform(seed, kStreamWind, step, env, 2);
-        const float u4 = counter_uniform(seed, kStreamWind, step, env, 3);
+        const float u1 = 1.f - prefix_uniform(wind_key, 0);
+        const float u2 = prefix_uniform(wind_key, 1);
+        const float u3 = 1.f - prefix_uniform(wind_key, 2);
+        const float u4 = prefix_uniform(wind_key, 3);
         const float r1 = sqrtf(-2.f * logf(u1)), r2 = sqrtf(-2.f * logf(u3));
         float s2, c2, s4, c4;
         sincosf(2.f * kPi * u2, &s2, &c2);
@@ -917,9 +922,9 @@ __device__ __forceinline__ void wind_step(const float* row, float4& s0, float4& 
         vw[2] += s0.z;
     }
     if (model & MDG_WIND_GUST) {
-        if (s0.w < 0.f && counter_uniform(seed, kStreamWind, step, env, 4) < row[MDG_DR_GUST_P]) {
-            const float z = 2.f * counter_uniform(seed, kStreamWind, step, env, 5) - 1.f;
-            const float ph = 2.f * kPi * counter_uniform(seed, kStreamWind, step, env, 6);
+        if (s0.w < 0.f && prefix_uniform(wind_key, 4) < row[MDG_DR_GUST_P]) {
+            const float z = 2.f * prefix_uniform(wind_key, 5) - 1.f;
+            const float ph = 2.f * kPi * prefix_uniform(wind_key, 6);
             const float rho = sqrtf(fmaxf(0.f, 1.f - z * z));
             float sn, cs;
             sincosf(ph, &sn, &cs);
@@ -960,10 +965,11 @@ __device__ __forceinline__ void noisy_kin(float* kin_row, const Drone& d, const 
                 sw = row[MDG_DR_NOISE_W];
     if (sp > 0.f || sv > 0.f || sr > 0.f || sw > 0.f) {
         float xi[12];
+        const unsigned long long key = counter_prefix(seed, kStreamObs, step, g);
 #pragma unroll
         for (int m = 0; m < 6; ++m) {
-            const float u1 = 1.f - counter_uniform(seed, kStreamObs, step, g, 2 * m);
-            const float u2 = counter_uniform(seed, kStreamObs, step, g, 2 * m + 1);
+            const float u1 = 1.f - prefix_uniform(key, 2 * m);
+            const float u2 = prefix_uniform(key, 2 * m + 1);
             const float r = sqrtf(-2.f * logf(u1));
             float sn, cs;
             sincosf(2.f * kPi * u2, &sn, &cs);
@@ -1803,11 +1809,12 @@ __global__ void __launch_bounds__(256) pid_kernel(const PidArgs a)
 // uniform batches of the benchmark workloads, and a runtime-generic one for the rest.
 // (physics flags, environment size): kFlags 0-7 a compile-time physics subset, 8 the
 // runtime flags, kFlagsRK4 the runtime flags with Runge-Kutta substeps, kFlagsGndRotor
-// the runtime flags with per-rotor ground heights; kN > 0 a
+// the runtime flags with per-rotor ground heights, kFlagsDR the runtime flags under
+// randomization, kFlagsRK4Fixed + s Runge-Kutta with the compile-time subset s; kN > 0 a
 // compile-time environment size, -1 a runtime size in blocks of at most kSmallBlock
-// threads, 0 any block size.
+// threads, 0 any block size. The first variant that fits a launch is taken.
 #define MDG_STEP_VARIANTS(X) \
-    X(7, 4) X(7, 64) X(3, 1) X(8, -1) X(8, 0) X(9, -1) X(9, 0) X(10, -1) X(10, 0) X(11, -1) X(11, 0) X(23, 4)
+    X(7, 4) X(7, 64) X(3, 1) X(8, -1) X(8, 0) X(9, -1) X(9, 0) X(10, -1) X(10, 0) X(11, 4) X(11, -1) X(11, 0) X(23, 4)
 
 template <bool kObs>
 static void* step_kernel_ptr(int flags, int N, int block)
