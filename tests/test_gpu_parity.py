@@ -250,3 +250,52 @@ def test_every_block_size_matches_oracle(cuda, block):
     resp = tolerance_response(P, layout, x0, i0, a0, action, sw.act_type, 5)
     assert_horizon_close(xg, xo, resp, 5, what=f"block {block}")
     _check_obs(xg, ag, sw.drones_per_env, kin, idx, rel)
+
+
+# ------------------------------------------------------------------ the bench's launch configuration
+def test_graph_replayed_rotation_equals_direct_steps_and_the_oracle(cuda):
+    """The timed region of bench.py: full-size swarms stepped in rotation from one captured
+    CUDA graph (one step launch per swarm). The replayed steps equal direct launches bit for
+    bit, and a sample of the last swarm's environments matches the oracle."""
+    n_sw = 3
+    swarms = []
+    for k in range(n_sw):
+        sw = wl.full_aero(1 + 97 * k)
+        h = mdg.Handle(sw.drones_per_env, sw.flags)
+        st = swarm_state(sw, cuda)
+        wp = _t(wl.waypoints(1 + 97 * k, sw.n), cuda)
+        swarms.append((sw, h, st, st.clone(), wp) + tuple(h.new_obs(cuda)))
+    # direct launches on copies, two steps per swarm
+    ref = []
+    for sw, h, st, st0, wp, kin, idx, rel in swarms:
+        s2 = st0.clone()
+        k2, i2, r2 = h.new_obs(cuda)
+        for _ in range(2):
+            h.step_obs(s2, wp, mdg.ACT_PID, 5, k2, i2, r2)
+        ref.append((s2, k2, i2, r2))
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        cap = torch.cuda.current_stream()
+        for sw, h, st, st0, wp, kin, idx, rel in swarms:
+            h.step_obs(st, wp, mdg.ACT_PID, 5, kin, idx, rel, stream=cap)
+    for sw, h, st, st0, *_ in swarms:
+        st.copy_(st0)
+    g.replay()
+    torch.cuda.synchronize()
+    sw, h, st, st0, wp, kin, idx, rel = swarms[-1]
+    x0, i0, a0 = oracle_arrays(st)   # after one replayed step: the start of the second
+    g.replay()
+    torch.cuda.synchronize()
+    for (sw_, h_, st_, _, _, kin_, idx_, rel_), (s2, k2, i2, r2) in zip(swarms, ref):
+        assert torch.equal(st_, s2) and torch.equal(kin_, k2) and torch.equal(idx_, i2) and torch.equal(rel_, r2)
+        assert h_.status()[0] == mdg.OK
+    xg, _, ag = oracle_arrays(st)
+    envs = np.linspace(0, sw.n_envs - 1, 48).astype(int)
+    sel, dpe = subset_layout(sw.drones_per_env, envs)
+    layout = (dpe, sw.flags[envs])
+    acts = np.full(len(envs), mdg.ACT_PID)
+    action = wl.waypoints(1 + 97 * (n_sw - 1), sw.n)
+    xo, _, _ = oracle_step(P, layout, x0[sel], i0[sel], a0[sel], action[sel], acts, 5)
+    spread = tolerance_response(P, layout, x0[sel], i0[sel], a0[sel], action[sel], acts, 5)
+    assert_horizon_close(xg[sel], xo, spread, 5, what="graph-replayed step")
