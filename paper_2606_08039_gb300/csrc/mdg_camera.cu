@@ -35,15 +35,33 @@ __constant__ float c_palette[8][3] = {{0.90f, 0.25f, 0.20f}, {0.20f, 0.70f, 0.30
                                       {0.95f, 0.75f, 0.15f}, {0.70f, 0.30f, 0.80f}, {0.15f, 0.75f, 0.80f},
                                       {0.95f, 0.50f, 0.20f}, {0.60f, 0.60f, 0.65f}};
 
-// Per drone of the environment, in shared memory: O = the camera origin in the drone's
-// scaled body frame (3), M = diag(1/s) R^T (9, world ray -> scaled body ray), C = |O|^2 - 1,
-// Nm = R diag(1/s) (9, scaled body point -> world normal direction), its segment id, and the
-// pixel rectangle [r0, r1] x [c0, c1] outside which no ray can meet it (the projection of
-// its oriented bounding box, half-extents (a, a, c) along its body axes, padded by a pixel;
-// empty when its bounding cube of half-width a lies behind the camera or beyond a side plane
-// of the view frustum, or for the camera's own drone; the whole image when the cube
-// straddles the image plane inside the frustum).
-constexpr int kSceneFloats = 27;
+// Per drone of the environment, in shared memory, seven float4 (a ray test reads the first
+// four): O = the camera origin in the drone's scaled body frame, M = diag(1/s) R^T (world
+// ray -> scaled body ray, row r in float4 1 + r), C = |O|^2 - 1, Nm = R diag(1/s) (scaled
+// body point -> world normal direction), its segment id, and the pixel rectangle
+// [r0, r1] x [c0, c1] outside which no ray can meet it (the projection of its oriented
+// bounding box, half-extents (a, a, c) along its body axes, padded by a pixel; empty when
+// its bounding cube of half-width a lies behind the camera or beyond a side plane of the
+// view frustum, or for the camera's own drone; the whole image when the cube straddles the
+// image plane inside the frustum):
+//   0: O0 O1 O2 C      1: M00 M01 M02 Nm0   2: M10 M11 M12 Nm1   3: M20 M21 M22 Nm2
+//   4: Nm3 Nm4 Nm5 Nm6   5: Nm7 Nm8 id r0   6: r1 c0 c1 -
+constexpr int kSceneF4 = 7;
+
+// Square root and reciprocal of the special function unit (relative error near 2^-23): the
+// hit distance of a ray-ellipsoid test, well inside the depth tolerance.
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 struct Rot {
     float m[9];  // row-major, body -> world
@@ -66,7 +84,7 @@ __device__ __forceinline__ Rot rot_of(float w, float x, float y, float z)
 
 __global__ void __launch_bounds__(kCamThreads) render_kernel(const CamArgs a)
 {
-    extern __shared__ float s_scene[];  // [max_env][kSceneFloats]
+    extern __shared__ float4 s_scene[];  // [max_env][kSceneF4]
     __shared__ int s_env[2];             // first drone of the camera's environment, its size
     __shared__ unsigned long long s_mask[kCamPixels / 32];  // per 32-pixel segment: drones it may see (N <= 64)
     __shared__ float s_cam[3];           // camera origin
@@ -113,21 +131,25 @@ __global__ void __launch_bounds__(kCamThreads) render_kernel(const CamArgs a)
             const Rot R = rot_of(p0.w, p1.x, p1.y, p1.z);
             const float inv_s[3] = {inv_a, inv_a, inv_c};
             const float dx = ox - p0.x, dy = oy - p0.y, dz = oz - p0.z;
-            float* sc = s_scene + k * kSceneFloats;
+            float4* sc = s_scene + k * kSceneF4;
+            float O[3], M[9], Nm[9];
             float C = -1.f;
             for (int r = 0; r < 3; ++r) {
                 // row r of R^T is column r of R
-                const float O = (R.m[r] * dx + R.m[3 + r] * dy + R.m[6 + r] * dz) * inv_s[r];
-                sc[r] = O;
-                C += O * O;
-                sc[3 + 3 * r + 0] = R.m[r] * inv_s[r];
-                sc[3 + 3 * r + 1] = R.m[3 + r] * inv_s[r];
-                sc[3 + 3 * r + 2] = R.m[6 + r] * inv_s[r];
+                O[r] = (R.m[r] * dx + R.m[3 + r] * dy + R.m[6 + r] * dz) * inv_s[r];
+                C += O[r] * O[r];
+                M[3 * r + 0] = R.m[r] * inv_s[r];
+                M[3 * r + 1] = R.m[3 + r] * inv_s[r];
+                M[3 * r + 2] = R.m[6 + r] * inv_s[r];
             }
-            sc[12] = C;
             for (int r = 0; r < 3; ++r)
-                for (int q = 0; q < 3; ++q) sc[13 + 3 * r + q] = R.m[3 * r + q] * inv_s[q];
-            sc[22] = __int_as_float((int)(g + 1));  // segment id
+                for (int q = 0; q < 3; ++q) Nm[3 * r + q] = R.m[3 * r + q] * inv_s[q];
+            sc[0] = make_float4(O[0], O[1], O[2], C);
+            sc[1] = make_float4(M[0], M[1], M[2], Nm[0]);
+            sc[2] = make_float4(M[3], M[4], M[5], Nm[1]);
+            sc[3] = make_float4(M[6], M[7], M[8], Nm[2]);
+            sc[4] = make_float4(Nm[3], Nm[4], Nm[5], Nm[6]);
+            const float seg_id = __int_as_float((int)(g + 1));
             // screen rectangle: the drone's centre in the camera drone's body frame
             const float ex = p0.x - ox, ey = p0.y - oy, ez = p0.z - oz;
             const float X = s_R[0] * ex + s_R[3] * ey + s_R[6] * ez;
@@ -175,10 +197,8 @@ __global__ void __launch_bounds__(kCamThreads) render_kernel(const CamArgs a)
                 r1 = min(kCamH - 1, (int)ceilf((0.5f * kCamH - ny_lo * ky - 0.5f)) + 1);
             }
             if (k == own_k) r0 = 1, r1 = 0;  // the camera's own drone: empty
-            sc[23] = __int_as_float(r0);
-            sc[24] = __int_as_float(r1);
-            sc[25] = __int_as_float(c0);
-            sc[26] = __int_as_float(c1);
+            sc[5] = make_float4(Nm[7], Nm[8], seg_id, __int_as_float(r0));
+            sc[6] = make_float4(__int_as_float(r1), __int_as_float(c0), __int_as_float(c1), 0.f);
         }
         __syncthreads();
         if (N == 0) continue;
@@ -189,9 +209,9 @@ __global__ void __launch_bounds__(kCamThreads) render_kernel(const CamArgs a)
                 const int row = sgm >> 1, sc0 = (sgm & 1) * 32, sc1 = sc0 + 31;
                 unsigned long long m = 0;
                 for (int k = 0; k < N; ++k) {
-                    const float* sc = s_scene + k * kSceneFloats;
-                    const bool meets = row >= __float_as_int(sc[23]) && row <= __float_as_int(sc[24]) &&
-                                       sc1 >= __float_as_int(sc[25]) && sc0 <= __float_as_int(sc[26]);
+                    const float4 q5 = s_scene[k * kSceneF4 + 5], q6 = s_scene[k * kSceneF4 + 6];
+                    const bool meets = row >= __float_as_int(q5.w) && row <= __float_as_int(q6.x) &&
+                                       sc1 >= __float_as_int(q6.y) && sc0 <= __float_as_int(q6.z);
                     m |= (unsigned long long)meets << k;
                 }
                 s_mask[sgm] = m;
@@ -227,18 +247,22 @@ __global__ void __launch_bounds__(kCamThreads) render_kernel(const CamArgs a)
                     k = __ffsll((long long)cand) - 1;
                     cand &= cand - 1;
                 }
-                const float* sc = s_scene + k * kSceneFloats;
-                if (N > 64 && (row < __float_as_int(sc[23]) || row > __float_as_int(sc[24]) ||
-                               wc1 < __float_as_int(sc[25]) || wc0 > __float_as_int(sc[26])))
-                    continue;  // outside the drone's screen rectangle (also: the camera's own drone)
-                const float D0 = sc[3] * d0 + sc[4] * d1 + sc[5] * d2;
-                const float D1 = sc[6] * d0 + sc[7] * d1 + sc[8] * d2;
-                const float D2 = sc[9] * d0 + sc[10] * d1 + sc[11] * d2;
+                const float4* sc = s_scene + k * kSceneF4;
+                if (N > 64) {
+                    const float4 q5 = sc[5], q6 = sc[6];
+                    if (row < __float_as_int(q5.w) || row > __float_as_int(q6.x) || wc1 < __float_as_int(q6.y) ||
+                        wc0 > __float_as_int(q6.z))
+                        continue;  // outside the drone's screen rectangle (also: the camera's own drone)
+                }
+                const float4 o = sc[0], m0 = sc[1], m1 = sc[2], m2 = sc[3];
+                const float D0 = m0.x * d0 + m0.y * d1 + m0.z * d2;
+                const float D1 = m1.x * d0 + m1.y * d1 + m1.z * d2;
+                const float D2 = m2.x * d0 + m2.y * d1 + m2.z * d2;
                 const float A = D0 * D0 + D1 * D1 + D2 * D2;
-                const float B = 2.f * (D0 * sc[0] + D1 * sc[1] + D2 * sc[2]);
-                const float disc = B * B - 4.f * A * sc[12];
+                const float B = 2.f * (D0 * o.x + D1 * o.y + D2 * o.z);
+                const float disc = B * B - 4.f * A * o.w;
                 if (disc < 0.f) continue;
-                const float sq = sqrtf(disc), i2a = 0.5f / A;
+                const float sq = sqrt_approx(disc), i2a = 0.5f * rcp_approx(A);
                 const float t1 = (-B - sq) * i2a, t2 = (-B + sq) * i2a;
                 const float tk = t1 > kTMin ? t1 : (t2 > kTMin ? t2 : kInf);
                 if (tk < t_best) {
@@ -256,18 +280,19 @@ __global__ void __launch_bounds__(kCamThreads) render_kernel(const CamArgs a)
                 r = gcol = b = grey * shade;
                 seg = 0;
             } else if (hit >= 0) {
-                const float* sc = s_scene + hit * kSceneFloats;
-                const float D0 = sc[3] * d0 + sc[4] * d1 + sc[5] * d2;
-                const float D1 = sc[6] * d0 + sc[7] * d1 + sc[8] * d2;
-                const float D2 = sc[9] * d0 + sc[10] * d1 + sc[11] * d2;
-                const float P0 = sc[0] + t_best * D0, P1 = sc[1] + t_best * D1, P2 = sc[2] + t_best * D2;
-                float n0 = sc[13] * P0 + sc[14] * P1 + sc[15] * P2;
-                float n1 = sc[16] * P0 + sc[17] * P1 + sc[18] * P2;
-                float n2 = sc[19] * P0 + sc[20] * P1 + sc[21] * P2;
+                const float4* sc = s_scene + hit * kSceneF4;
+                const float4 o = sc[0], m0 = sc[1], m1 = sc[2], m2 = sc[3], q4 = sc[4], q5 = sc[5];
+                const float D0 = m0.x * d0 + m0.y * d1 + m0.z * d2;
+                const float D1 = m1.x * d0 + m1.y * d1 + m1.z * d2;
+                const float D2 = m2.x * d0 + m2.y * d1 + m2.z * d2;
+                const float P0 = o.x + t_best * D0, P1 = o.y + t_best * D1, P2 = o.z + t_best * D2;
+                float n0 = m0.w * P0 + m1.w * P1 + m2.w * P2;
+                float n1 = q4.x * P0 + q4.y * P1 + q4.z * P2;
+                float n2 = q4.w * P0 + q5.x * P1 + q5.y * P2;
                 const float in = rsqrtf(fmaxf(n0 * n0 + n1 * n1 + n2 * n2, 1e-30f));
                 const float nl = (n0 * kLx + n1 * kLy + n2 * kLz) * in;
                 const float shade = 0.35f + 0.65f * fmaxf(0.f, nl);
-                const int id = __float_as_int(sc[22]);
+                const int id = __float_as_int(q5.z);
                 const int pc = (id - 1) & 7;
                 r = c_palette[pc][0] * shade;
                 gcol = c_palette[pc][1] * shade;
@@ -292,7 +317,7 @@ __global__ void __launch_bounds__(kCamThreads) render_kernel(const CamArgs a)
 cudaError_t launch_render(const CamArgs& a, cudaStream_t s)
 {
     if (a.n == 0) return cudaSuccess;
-    const int smem = a.max_env * kSceneFloats * (int)sizeof(float);
+    const int smem = a.max_env * kSceneF4 * (int)sizeof(float4);
     static int opted = 0;
     if (smem > 48 * 1024 && smem > opted) {
         cudaError_t e = cudaFuncSetAttribute(render_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
