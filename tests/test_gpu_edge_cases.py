@@ -10,7 +10,8 @@ import torch
 import oracle
 import paper_2606_08039_gb300 as mdg
 from paper_2606_08039_gb300 import workloads as wl
-from helpers import assert_horizon_close, assert_state_close, oracle_arrays, oracle_step, tolerance_response
+from helpers import (assert_horizon_close, assert_state_close, oracle_arrays, oracle_step, spread_heights,
+                     tolerance_response)
 
 pytestmark = pytest.mark.gpu
 
@@ -248,3 +249,34 @@ def test_neighbour_ties_and_nonfinite_in_four_drone_environments(cuda):
     np.testing.assert_array_equal(idx[b + 1], [-1, -1, -1, -1])
     rc, bits, first = h.status()
     assert rc == mdg.ERR_NONFINITE and first == b + 1
+
+
+def test_results_do_not_depend_on_the_tile_size(cuda):
+    """A drone's arithmetic is its own: every block size of one kernel variant gives the
+    same bits (tiles of 8 to 64 environments of the compile-time four-drone variant; 128 and
+    256 environments of the runtime one), and the two variants agree within the stated
+    tolerances."""
+    sw = spread_heights(wl.full_aero(71, n_envs=2048))  # no near-coincident heights: the variants stay close
+    wp = _t(wl.waypoints(71, sw.n), cuda)
+    init = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=cuda)
+    out = {}
+    for block in (32, 64, 128, 256, 512, 1024):
+        h = mdg.Handle(sw.drones_per_env, sw.flags)
+        h.set_block_size(block)
+        st = init.clone()
+        kin, idx, rel = h.new_obs(cuda)
+        for _ in range(3):
+            h.step_obs(st, wp, mdg.ACT_PID, 5, kin, idx, rel)
+        torch.cuda.synchronize()
+        assert h.status()[0] == mdg.OK
+        out[block] = (st, kin, idx, rel)
+    for group in ((32, 64, 128, 256), (512, 1024)):
+        ref = out[group[0]]
+        for b in group[1:]:
+            for x, y in zip(out[b], ref):
+                assert torch.equal(x, y), f"block {b} differs from block {group[0]}"
+    a, b = out[64], out[1024]
+    assert torch.equal(a[2], b[2])                      # neighbour indices: bit-exact decisions
+    # the variants sum the downwash in different orders: within the per-substep tolerances
+    # over the 15 substeps of the three control steps
+    assert_state_close(oracle_arrays(a[0])[0], oracle_arrays(b[0])[0], scale=15, what="variants")
