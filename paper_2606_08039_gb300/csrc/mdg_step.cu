@@ -911,8 +911,10 @@ __device__ __forceinline__ void wind_step(const float* row, float4& s0, float4& 
         const float u4 = prefix_uniform(wind_key, 3);
         const float r1 = sqrtf(-2.f * logf(u1)), r2 = sqrtf(-2.f * logf(u3));
         float s2, c2, s4, c4;
-        sincosf(2.f * kPi * u2, &s2, &c2);
-        sincosf(2.f * kPi * u4, &s4, &c4);
+        // sin and cos of 2 pi u as sincospif(2 u): exact argument reduction, and without the
+        // large-argument path a general sincosf inlines at every call
+        sincospif(2.f * u2, &s2, &c2);
+        sincospif(2.f * u4, &s4, &c4);
         const float sc = row[MDG_DR_DRY_SIGMA] * sqrtf(fmaxf(0.f, 1.f - alpha * alpha));
         s0.x = alpha * s0.x + sc * (r1 * c2);
         s0.y = alpha * s0.y + sc * (r1 * s2);
@@ -924,10 +926,10 @@ __device__ __forceinline__ void wind_step(const float* row, float4& s0, float4& 
     if (model & MDG_WIND_GUST) {
         if (s0.w < 0.f && prefix_uniform(wind_key, 4) < row[MDG_DR_GUST_P]) {
             const float z = 2.f * prefix_uniform(wind_key, 5) - 1.f;
-            const float ph = 2.f * kPi * prefix_uniform(wind_key, 6);
+            const float u6 = prefix_uniform(wind_key, 6);  // direction angle 2 pi u6
             const float rho = sqrtf(fmaxf(0.f, 1.f - z * z));
             float sn, cs;
-            sincosf(ph, &sn, &cs);
+            sincospif(2.f * u6, &sn, &cs);
             s0.w = 0.f;
             s1.x = rho * cs;
             s1.y = rho * sn;
@@ -972,7 +974,7 @@ __device__ __forceinline__ void noisy_kin(float* kin_row, const Drone& d, const 
             const float u2 = prefix_uniform(key, 2 * m + 1);
             const float r = sqrtf(-2.f * logf(u1));
             float sn, cs;
-            sincosf(2.f * kPi * u2, &sn, &cs);
+            sincospif(2.f * u2, &sn, &cs);  // sin and cos of 2 pi u2
             xi[2 * m] = r * cs;
             xi[2 * m + 1] = r * sn;
         }
