@@ -432,7 +432,7 @@ __device__ __forceinline__ void substep(Drone& d, const Motor& m, int flags_rt, 
     // theta = |w| dt/2. sin(theta)/|w| = (dt/2) sinc(theta); for theta^2 <= 0.1 both factors
     // are the Taylor series of cos and sinc in theta^2 to theta^6 (truncation below 2.5e-9),
     // with neither a square root nor a division. Larger rotations per substep (|w| above
-    // ~152 rad/s at 240 Hz) take sqrtf/sincosf (the rarely taken branch below).
+    // ~152 rad/s at 240 Hz) take sqrtf and the reduced sine/cosine (the rarely taken branch below).
     const float nw2 = d.w[0] * d.w[0] + d.w[1] * d.w[1] + d.w[2] * d.w[2];
     const float hdt = 0.5f * dt;
     const float t2 = nw2 * (hdt * hdt);
@@ -472,9 +472,11 @@ __device__ __forceinline__ void substep(Drone& d, const Motor& m, int flags_rt, 
     const float wd1 = c.inv_J[1] * (m.tau[1] - (d.w[2] * Jw0 - d.w[0] * Jw2));
     const float wd2 = c.inv_J[2] * (m.tau[2] - (d.w[0] * Jw1 - d.w[1] * Jw0));
     if (t2 > 0.1f) {
+        // theta reduced by 2 pi, then the special function unit's sine and cosine (within
+        // ~4e-7 absolute): no large-argument reduction code in the kernel
         const float nw = sqrtf(nw2);
         float sn;
-        sincosf(hdt * nw, &sn, &co);
+        __sincosf(reduce_angle(hdt * nw), &sn, &co);
         k = sn / nw;
     }
     {
