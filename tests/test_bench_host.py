@@ -76,3 +76,31 @@ def test_in_place_oracle_call_equals_the_wrapper():
     np.testing.assert_array_equal(s0["kin"], kin)
     np.testing.assert_array_equal(s0["idx"], nbr_i)
     np.testing.assert_array_equal(s0["rel"], nbr_r)
+
+
+def test_clock_summary_uses_the_samples_inside_the_timed_region():
+    """ClockSampler.stop(windows): the median and the throttle reasons come from the samples
+    read inside the timed windows (falling back to every sample when none is inside)."""
+    cs = bench.ClockSampler(0)
+
+    class _Done:  # a finished sampler process
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    class _Joined:
+        def join(self, timeout=None):
+            pass
+
+    idle = "0, 1200, 2070, 150.0, 0x0, Not Active, Not Active, Not Active, Not Active"
+    load = "0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Active"
+    cs.proc, cs.thread = _Done(), _Joined()
+    cs.lines = [(0.0, idle), (1.0, load), (1.1, load), (2.0, idle)]
+    inside = cs.stop(windows=[(0.95, 1.15)])
+    assert inside["sm_mhz"] == 2070 and inside["samples"] == 2 and inside["window"] == "timed region"
+    assert inside["reasons"] == ["sw_power_cap"]
+    cs.proc, cs.thread = _Done(), _Joined()
+    everything = cs.stop(windows=[(5.0, 6.0)])
+    assert everything["samples"] == 4 and everything["window"] == "whole run"
