@@ -1293,7 +1293,9 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
         float4* pb = s_pos + (ph & 1) * B;  // not the buffer the last substep read
         pb[t] = make_float4(d.p[0], d.p[1], d.p[2], 0.f);
         s_vel[t] = make_float4(d.v[0], d.v[1], d.v[2], 0.f);
-        __syncthreads();
+        // every warp reads only its own environments' entries when the tile is warp-local
+        if (warp_local) __syncwarp();
+        else __syncthreads();
         // observations through per-warp staging (coalesced stores: 0.4-0.6 us less per step on
         // the 65536-drone swarm than strided ones); the randomization variant writes its noisy
         // rows directly
@@ -1490,7 +1492,8 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
                 float4* pb = s_pos + (sub & 1) * B;  // not the buffer the last substep read
                 pb[t] = make_float4(d.p[0], d.p[1], d.p[2], 0.f);
                 s_vel[t] = make_float4(d.v[0], d.v[1], d.v[2], 0.f);
-                __syncthreads();
+                if (warp_local) __syncwarp();  // a warp-local tile: each warp reads its own entries
+                else __syncthreads();
                 // direct strided stores: staging them through shared memory as the step kernel
                 // does measured 2% slower per control step here (more registers in the loop)
                 if (active) {
@@ -1506,7 +1509,8 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
                     write_knn<kN>(a.nbr_idx, a.nbr_rel, o + g, env_first, t - env.ls, d, pb + env.ls,
                                   s_vel + env.ls, env.N);
                 }
-                __syncthreads();  // the next step publishes into pb again
+                if (warp_local) __syncwarp();  // the next step publishes into pb again
+                else __syncthreads();
             }
             act = next;
         }
