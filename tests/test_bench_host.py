@@ -104,3 +104,31 @@ def test_clock_summary_uses_the_samples_inside_the_timed_region():
     cs.proc, cs.thread = _Done(), _Joined()
     everything = cs.stop(windows=[(5.0, 6.0)])
     assert everything["samples"] == 4 and everything["window"] == "whole run"
+
+
+def test_algorithmic_bytes_per_drone_and_control_step():
+    """The bytes the roofline divides by: 384 B per drone for PID waypoints (state planes 0-4
+    read, 0-5 written, the waypoint, KIN + indices + features), 352 B for plain RPM actions
+    (no integral plane read or written), +32 B with the DSL setpoint, and 544 B under
+    randomization with an action history of depth 3 (rotor speeds, history shift, the row
+    and wind state of each four-drone environment)."""
+    sw = wl.full_aero(1, n_envs=64)
+    n = sw.n
+    pid = np.full(sw.n_envs, 1, np.uint8)
+    rpm = np.zeros(sw.n_envs, np.uint8)
+    assert bench.algorithmic_bytes(sw, pid, 1, False) == 384 * n
+    assert bench.algorithmic_bytes(sw, rpm, 0, False) == 352 * n
+    assert bench.algorithmic_bytes(sw, pid, 1, True) == 416 * n
+    assert bench.algorithmic_bytes(sw, pid, 1, False, dr_depth=3) == 544 * n
+    assert bench.BYTES_PER_DRONE_STEP == 384
+
+
+def test_binding_roofline_takes_the_longer_ideal_time():
+    peaks = {"hbm_gbs": 1000.0, "src": "test"}
+    # 1 GB at 1000 GB/s is 1 ms; a tiny flop count: HBM binds
+    r = bench.binding_roofline(1e9, 1e6, 2e-3, peaks)
+    assert r["bound"] == "hbm" and r["achieved"] == pytest.approx(500.0) and r["frac"] == pytest.approx(0.5)
+    assert r["other_bound"]["bound"] == "alu"
+    # many flops, few bytes: the ALU binds
+    r = bench.binding_roofline(1e3, bench.FP32_PEAK_TFLOPS * 1e12 * 1e-3, 4e-3, peaks)
+    assert r["bound"] == "alu" and r["frac"] == pytest.approx(0.25)
