@@ -155,6 +155,7 @@ def lib():
                 "orc_control_steps": ([P, ctypes.c_int, _I, _I, _I, _D, _D, _D, _D, ctypes.c_int, ctypes.c_int,
                                        _D, _I, _D, _D, ctypes.POINTER(_DR)], ctypes.c_int),
                 "orc_uniform": ([ctypes.c_uint64] * 5, ctypes.c_double),
+                "orc_splitmix64": ([ctypes.c_uint64], ctypes.c_uint64),
                 "orc_params_randomized": ([P, _D, P], None),
                 "orc_wind_step": ([P, _D, _D, ctypes.c_uint64, ctypes.c_int64, _D, _D], None),
             }
@@ -376,6 +377,12 @@ def knn(x_env, j: int, idx_base: int = 0):
     rel = np.zeros(24)
     lib().orc_knn(x_env.shape[0], _dptr(x_env), int(j), int(idx_base), _iptr(idx), _dptr(rel))
     return idx, rel
+
+
+def splitmix64(z: int) -> int:
+    """The oracle's SplitMix64 round: the generator's output for the state z before its
+    increment by the golden gamma (so z = k * gamma gives the (k+1)-th output from state 0)."""
+    return int(lib().orc_splitmix64(ctypes.c_uint64(z % (1 << 64))))
 
 
 def uniform(seed: int, stream: int, step: int, index: int, comp: int) -> float:

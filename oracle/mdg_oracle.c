@@ -18,7 +18,7 @@
  * test_oracle_*.py.
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared -o liboracle.so mdg_oracle.c -lm
- * (-ffp-contract=off: the kNN selection below must round like the kernel does.)
+ * (-ffp-contract=off: every product and sum rounds as written, the same on x86 and Arm.)
  */
 #include <math.h>
 #include <stdint.h>
@@ -825,28 +825,23 @@ void orc_kin(const double x[13], const double a_prev[4], double out[20])
  * information"; the format is not printed). Reading: the 4 nearest other drones
  * of the same environment by Euclidean distance, ties to the lower index, padded
  * with index -1 and zero features when the environment has fewer than 5 drones;
- * features per neighbour i of drone j: [p_i - p_j, v_i - v_j].
- * The selection is an integer decision taken from floating-point distances; it is
- * made in single precision with the kernel's operation order (squared distance
- * ((dx*dx + dy*dy) + dz*dz), each difference and product rounded to float, no fused
- * multiply-add) so that both sides choose the same indices. The features are
- * computed in double precision. idx_base is added to the local indices written. */
+ * features per neighbour i of drone j: [p_i - p_j, v_i - v_j]. Distances, the
+ * selection and the features are all taken in double precision. A drone whose
+ * squared distance is not finite (a NaN or infinite position) is not listed.
+ * idx_base is added to the local indices written. */
 void orc_knn(int N, const double* x, int j, int idx_base, int32_t idx[4], double rel[24])
 {
-    float bestd[4];
+    double bestd[4];
     int besti[4];
     int nb = 0;
-    const float xj = (float)x[13 * j + 0], yj = (float)x[13 * j + 1], zj = (float)x[13 * j + 2];
     for (int i = 0; i < N; ++i) {
         if (i == j) continue;
-        const float dx = (float)x[13 * i + 0] - xj;
-        const float dy = (float)x[13 * i + 1] - yj;
-        const float dz = (float)x[13 * i + 2] - zj;
-        const float dxx = dx * dx;
-        const float dyy = dy * dy;
-        const float dzz = dz * dz;
-        const float s = dxx + dyy;
-        const float d2 = s + dzz;
+        double d2 = 0.0;
+        for (int r = 0; r < 3; ++r) {
+            const double d = x[13 * i + r] - x[13 * j + r];
+            d2 += d * d;
+        }
+        if (!isfinite(d2)) continue;
         /* insert (d2, i) into the sorted list; strict '<' keeps the lower index first */
         int pos = nb;
         while (pos > 0 && d2 < bestd[pos - 1]) --pos;
@@ -880,8 +875,10 @@ void orc_knn(int N, const double* x, int j, int idx_base, int32_t idx[4], double
 /* ---- domain randomization and wind ---- */
 
 /* SplitMix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number generators",
- * OOPSLA 2014): the output function of its counter-based form. */
-static uint64_t orc_splitmix64(uint64_t z)
+ * OOPSLA 2014): the output function of its counter-based form. Called with the state
+ * before its increment by the golden gamma, so orc_splitmix64(k * gamma) is the (k+1)-th
+ * output of the generator started from state 0 (pinned against the published sequence). */
+uint64_t orc_splitmix64(uint64_t z)
 {
     z += 0x9E3779B97F4A7C15ULL;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
@@ -963,7 +960,7 @@ void orc_wind_step(const orc_params* P, const double* dr, double* ws, uint64_t s
     if (model & ORC_WIND_GUST) {
         if (ws[3] < 0.0) {
             const double u = orc_uniform(seed, ORC_STREAM_WIND, step, (uint64_t)env, 4);
-            if ((float)u < (float)dr[ORC_DR_GUST_P]) {
+            if (u < dr[ORC_DR_GUST_P]) {
                 const double z = 2.0 * orc_uniform(seed, ORC_STREAM_WIND, step, (uint64_t)env, 5) - 1.0;
                 const double ph = 2.0 * ORC_PI * orc_uniform(seed, ORC_STREAM_WIND, step, (uint64_t)env, 6);
                 const double rho = sqrt(1.0 - z * z);
@@ -976,10 +973,8 @@ void orc_wind_step(const orc_params* P, const double* dr, double* ws, uint64_t s
         if (ws[3] >= 0.0) {
             const double a = dr[ORC_DR_GUST_A] * sin(ORC_PI * ws[3]);
             for (int r = 0; r < 3; ++r) F_dir[r] += a * ws[4 + r];
-            /* the phase decides at which step the gust ends: it advances in single
-             * precision, as in the kernels, so that both end it at the same step */
-            const float s_next = (float)ws[3] + (float)dt / (float)dr[ORC_DR_GUST_T];
-            ws[3] = s_next > 1.0f ? -1.0 : (double)s_next;
+            const double s_next = ws[3] + dt / dr[ORC_DR_GUST_T];
+            ws[3] = s_next > 1.0 ? -1.0 : s_next;
         }
     }
     if (model & ORC_WIND_SINUSOIDAL) {

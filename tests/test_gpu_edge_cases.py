@@ -10,7 +10,7 @@ import torch
 import oracle
 import paper_2606_08039_gb300 as mdg
 from paper_2606_08039_gb300 import workloads as wl
-from helpers import (assert_horizon_close, assert_state_close, oracle_arrays, oracle_step, spread_heights,
+from helpers import (assert_horizon_close, assert_knn_valid, assert_state_close, oracle_arrays, oracle_step, spread_heights,
                      tolerance_response)
 
 pytestmark = pytest.mark.gpu
@@ -88,8 +88,7 @@ def test_largest_environment(cuda):
     assert_horizon_close(xg, xo, spread, 5, what="1024-drone env")
     idx = idx.cpu().numpy()
     for j in (0, 17, 500, 1023):
-        i_ref, _ = oracle.knn(xg, j, 0)
-        np.testing.assert_array_equal(idx[j], i_ref)
+        assert_knn_valid(xg, j, 0, idx[j], what=f"neighbours of drone {j}")
     with pytest.raises(mdg.MdgError):
         mdg.Handle(np.array([N + 1], np.int32), np.zeros(1, np.uint32))
 
@@ -235,8 +234,7 @@ def test_neighbour_ties_and_nonfinite_in_four_drone_environments(cuda):
         np.testing.assert_array_equal(idx[4 * e:4 * e + 4], np.where(square >= 0, square + 4 * e, -1),
                                       err_msg=f"env {e}")
         for j in range(4):
-            i_ref, _ = oracle.knn(xg[4 * e:4 * e + 4], j, 4 * e)
-            np.testing.assert_array_equal(idx[4 * e + j], i_ref)
+            assert_knn_valid(xg[4 * e:4 * e + 4], j, 4 * e, idx[4 * e + j], what=f"env {e} drone {j}")
     # env 1: 0 and 3 at distance 0 from each other
     b = 4
     np.testing.assert_array_equal(idx[b + 0], [b + 3, b + 1, b + 2, -1])

@@ -4,11 +4,17 @@ Rows drawn from the paper's recommended ranges (workloads.dr_table, every wind m
 Each control step, the oracle restarts from the GPU's state and randomization state
 (rotor speeds, action history, wind state) and is compared over the step with the horizon
 bound; the RPMs, integrals, rotor speeds and wind state against the oracle's, the action
-history and the gust phases and step counters exactly, the KIN observation with its sensor
-noise and delay against the oracle's (the gust phase decides when a gust
-ends and advances in single precision on both sides; the wind draws come from the same
-counter-based SplitMix64 stream). Heights are spread per environment
+history and the step counters exactly, the gust phases by check_gust_phases, the KIN
+observation with its sensor noise and delay against the oracle's (the wind draws come from the
+same counter-based SplitMix64 stream on both sides). Heights are spread per environment
 (helpers.spread_heights): the randomization is under test, not the downwash's conditioning.
+
+The gust phase advances by dt_ctrl/T per control step, in FP64 in the oracle and in float32
+on the GPU, and a gust ends at the first step whose advanced phase exceeds 1. Where the
+advanced phase lies within float32 rounding of 1 the two may end the gust one step apart;
+both are correct. The force of that step is the same on both sides (it uses the phase before
+the advance); only the next step's trigger may differ, and the tests restart the oracle from
+the GPU's wind state each step.
 """
 import numpy as np
 import pytest
@@ -25,6 +31,28 @@ P = oracle.cf2x()
 HOVER = oracle.hover_rpm(P)
 SEED = 77
 DEPTH = 3
+
+
+# float32 rounding of s + dt/T for s in [0, 1]: the sum's rounding (2^-24), the quotient's
+# relative rounding and that of the float32 inputs (a few units of 2^-24 of dt/T <= 1): far
+# below 1e-6.
+PHASE_ATOL = 1e-6
+
+
+def check_gust_phases(wg, wo, what):
+    """Gust phases of the GPU (wg) and the oracle (wo) after the same step: idle (-1) on both
+    sides or active on both within PHASE_ATOL, except a gust that one side ended and the other
+    did not, which is valid only if the phase still running is within PHASE_ATOL of 1 (the
+    end decision then rests on float32 rounding). Returns the environments where that
+    happened."""
+    ig, io = wg < 0, wo < 0
+    assert np.all(wg[ig] == -1.0) and np.all(wo[io] == -1.0), f"{what}: idle phases"
+    both = ~ig & ~io
+    np.testing.assert_allclose(wg[both], wo[both], rtol=0, atol=PHASE_ATOL, err_msg=f"{what}: gust phases")
+    split = np.flatnonzero(ig != io)
+    running = np.where(ig[split], wo[split], wg[split])
+    assert np.all(running >= 1.0 - PHASE_ATOL), f"{what}: gust ended on one side only at phases {running}"
+    return split
 
 
 def _oracle_state(table, motor, hist, wind):
@@ -98,7 +126,7 @@ def test_randomized_control_steps(cuda, recipe):
         assert excess(motor.cpu().numpy(), r.motor, 1e-5) <= 1.0, f"{what}: rotor speeds"
         np.testing.assert_array_equal(hist.cpu().numpy().astype(np.float64), r.hist, err_msg=f"{what}: history")
         wg = wind.cpu().numpy().astype(np.float64)
-        np.testing.assert_array_equal(wg[:, 3], r.wind[:, 3], err_msg=f"{what}: gust phases")
+        check_gust_phases(wg[:, 3], r.wind[:, 3], what)
         np.testing.assert_array_equal(wg[:, 7], r.wind[:, 7], err_msg=f"{what}: wind steps")
         np.testing.assert_allclose(wg[:, 0:3], r.wind[:, 0:3], rtol=1e-4, atol=1e-5, err_msg=f"{what}: Dryden")
         np.testing.assert_allclose(wg[:, 4:7], r.wind[:, 4:7], rtol=0, atol=1e-6, err_msg=f"{what}: gust directions")
@@ -129,12 +157,24 @@ def test_randomized_rollout(cuda):
     h.rollout(state, torch.as_tensor(actions, device=cuda), mdg.ACT_MIXED, 5, K)
     torch.cuda.synchronize()
     xg, _, _ = oracle_arrays(state)
-    xo, _, _ = _oracle_steps(sw, types, x0, i0, a0, actions, r)
+    # the oracle one step at a time (the same as K steps in one call), recording the gusts
+    # whose end fell within float32 rounding of a phase of 1: from there on the two sides may
+    # follow different, equally valid gust sequences, so those environments leave the state
+    # comparison (the seeds here give none; the assertion below says so)
+    T = table[:, oracle.DR_GUST_T].astype(np.float64)
+    xo, io, ao = x0, i0, a0
+    ambiguous = np.zeros(sw.n_envs, bool)
+    for k in range(K):
+        s_next = r.wind[:, 3] + P.dt_ctrl / T
+        ambiguous |= (r.wind[:, 3] >= 0) & (np.abs(s_next - 1.0) <= PHASE_ATOL)
+        xo, io, ao = _oracle_steps(sw, types, xo, io, ao, actions[k:k + 1], r)
     xp, _, _ = _oracle_steps(sw, types, x0, i0, a0, actions, r2, perturb=True)
-    assert_horizon_close(xg, xo, np.abs(xo - xp), 5 * K, what="randomized rollout")
+    assert ambiguous.sum() <= 1
+    keep = ~np.repeat(ambiguous, sw.drones_per_env)
+    assert_horizon_close(xg[keep], xo[keep], np.abs(xo - xp)[keep], 5 * K, what="randomized rollout")
     wg = wind.cpu().numpy().astype(np.float64)
     np.testing.assert_array_equal(wg[:, 7], K)
-    np.testing.assert_array_equal(wg[:, 3], r.wind[:, 3])
+    check_gust_phases(wg[~ambiguous, 3], r.wind[~ambiguous, 3], "randomized rollout")
     np.testing.assert_array_equal(hist.cpu().numpy().astype(np.float64), r.hist)
 
 

@@ -11,7 +11,7 @@ import paper_2606_08039_gb300 as mdg
 from oracle import mlp as omlp
 from paper_2606_08039_gb300 import surrogate as sg
 from paper_2606_08039_gb300 import workloads as wl
-from helpers import assert_horizon_close, check_obs_against_own_state, excess, oracle_arrays, oracle_step, \
+from helpers import assert_horizon_close, assert_knn_valid, check_obs_against_own_state, excess, oracle_arrays, oracle_step, \
     tolerance_response
 
 pytestmark = pytest.mark.gpu
@@ -171,9 +171,17 @@ def test_features_match_state_and_oracle_neighbours(cuda):
     np.testing.assert_array_equal(raw[:, 13:17], rpm.cpu().numpy())
     env_off = sw.env_off
     for e in range(sw.n_envs):
-        b, N = env_off[e], sw.drones_per_env[e]
+        b, N = int(env_off[e]), int(sw.drones_per_env[e])
+        xe = x[b:b + N]
         for j in range(N):
-            _, r_ref = oracle.knn(x[b:b + N], j, b)
+            # the drone each listed slot describes (the one whose relative position it holds),
+            # then that list checked as a valid 4-nearest list and the features against it
+            listed = np.full(4, -1)
+            for k in range(min(4, N - 1)):
+                dp = np.abs(xe[:, 0:3] - xe[j, 0:3] - raw[b + j, 17 + 6 * k:20 + 6 * k]).sum(axis=1)
+                dp[j] = np.inf
+                listed[k] = b + int(np.argmin(dp))
+            r_ref, _ = assert_knn_valid(xe, j, b, listed, what=f"features of drone {b + j}")
             assert excess(raw[b + j, 17:], r_ref, 1e-6, floor=1e-2) <= 1.0
 
 

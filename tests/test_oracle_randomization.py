@@ -230,6 +230,21 @@ def test_gust_trigger_rate_and_direction():
     assert np.mean(D[:, 2] ** 2) == pytest.approx(1 / 3, abs=4 * np.sqrt(4 / 45 / len(D)))
 
 
+def test_splitmix64_published_sequence():
+    """SplitMix64 (Steele, Lea and Flood 2014) from state 0: the reference implementation's
+    first outputs are 0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F,
+    0xF88BB8A8724C81EC. A wrong constant, shift or increment in the oracle's round fails
+    here (the input generator's copy is a second implementation, not a pin)."""
+    gamma = 0x9E3779B97F4A7C15
+    published = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F, 0xF88BB8A8724C81EC]
+    assert [oracle.splitmix64(k * gamma) for k in range(4)] == published
+    # orc_uniform is five rounds over the counters, the top 24 bits scaled to [0, 1)
+    h = oracle.splitmix64(0)
+    for field in (21, 0, 0, 0):
+        h = oracle.splitmix64(h ^ field)
+    assert oracle.uniform(0, 21, 0, 0, 0) == (h >> 40) / 2.0 ** 24
+
+
 def test_uniforms_match_the_input_generator():
     for seed, stream, step, index, comp in ((0, 21, 0, 0, 0), (7, 21, 3, 12, 4), (2 ** 40 + 3, 5, 99, 7, 6)):
         u = oracle.uniform(seed, stream, step, index, comp)
