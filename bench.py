@@ -51,11 +51,20 @@ METRIC = "drone-substeps/s on 1 GB300 (FP32 vs oracle)"
 UNIT = "drone-substeps/s"
 N_SUB = 5
 EPISODE = 1000
-STATE_BYTES_READ = 80    # planes 0-4 (PID integrals included)
+# Algorithmic bytes per drone and control step (the count the roofline divides by): the
+# 13-value state read and written, the controller's 6 integrals read and written where its
+# loops run, the action, the observations. The kernel moves 24 B more per drone than this
+# count on the PID workload: the padding lane of the integral plane (read and written) and
+# the a_{t-1} plane (written; KIN carries the same four RPMs).
+STATE_BYTES = 13 * 4
+INTEG_BYTES = 6 * 4
 ACTION_BYTES = 16
-STATE_BYTES_WRITE = 96   # planes 0-5
 OBS_BYTES = 80 + 16 + 96  # KIN, neighbour indices, neighbour features
-BYTES_PER_DRONE_STEP = STATE_BYTES_READ + ACTION_BYTES + STATE_BYTES_WRITE + OBS_BYTES  # 384
+BYTES_PER_DRONE_STEP = 2 * STATE_BYTES + 2 * INTEG_BYTES + ACTION_BYTES + OBS_BYTES  # 360
+# A bounded device sleep enqueued before the start event of a back-to-back region, so that
+# the host has submitted the region's launches before the GPU reaches the first one and the
+# events measure device time, not host submission (about 0.2 ms at 2 GHz).
+HEAD_START_CYCLES = 400_000
 
 # DRAM traffic of one step-kernel launch on the full-aero workload, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel source whose
@@ -401,18 +410,16 @@ def algorithmic_flops(sw, K: int, n_sub: int, obs_steps: int, pid_mask=None, rk4
 
 
 def algorithmic_bytes(sw, types, act_type: int, dsl: bool, dr_depth: int = 0) -> int:
-    """Bytes one fused control step must move for the full-aero workload: per drone the state
-    planes 0-3 read and written (64 + 64 B), plane 4 (attitude integrals) read unless every
-    action is RPM and written where the controller loops run (PID, VEL, ATTITUDE), the action
-    (16 B), plane 5 written (16 B), the observations (192 B), and with the DSL controller the
-    setpoint of each waypoint-driven drone read and written (32 B). 384 B for PID actions.
-    Under randomization (history depth D): the rotor speeds read and written (32 B), the
-    action history shifted (D - 1 reads, D writes of 16 B), and per environment its 128 B row
-    and its 32 B wind state read and written."""
-    per_env = np.full(sw.n_envs, 64 + 64 + 16 + 16 + OBS_BYTES, np.int64)
-    if act_type != 0:
-        per_env += 16
-    per_env += 16 * np.isin(types, (1, 5, 6))
+    """Bytes one fused control step must move for the full-aero workload: per drone the
+    13-value state read and written (52 + 52 B), the action (16 B), the observations (192 B),
+    the controller's 6 integrals read and written (24 + 24 B) where its loops run (PID, VEL,
+    ATTITUDE), and with the DSL controller the setpoint of each waypoint-driven drone read and
+    written (32 B). 360 B for PID actions, 312 B for RPM actions. Under randomization (history
+    depth D): the rotor speeds read and written (32 B), the action history shifted (D - 1
+    reads, D writes of 16 B), and per environment its 128 B row and its 32 B wind state read
+    and written."""
+    per_env = np.full(sw.n_envs, 2 * STATE_BYTES + ACTION_BYTES + OBS_BYTES, np.int64)
+    per_env += 2 * INTEG_BYTES * np.isin(types, (1, 5, 6))
     if dsl:
         per_env += 32 * (types == 1)
     total = int(np.sum(per_env * sw.drones_per_env))
@@ -443,15 +450,24 @@ N_SWARMS = 16            # independent full-size swarms stepped in rotation in t
 SWARM_SEED_STRIDE = 97   # seed of swarm k: the rank's replica seed + 97 k
 SWARM_BYTES = 65536 * (96 + 16 + 80 + 16 + 96)  # per swarm and step: state planes, waypoints, KIN, indices, features
 ISOLATED_STEPS = 1000    # steps of the isolated (flushed, per-step events) measurement
-# algorithmic bytes of a K-step rollout with observations every step: the state read and
-# written once (80 B + 96 B), the waypoint once (16 B), KIN + indices + features every step
-BYTES_OBS_PER_DRONE_STEP = 80 + 16 + 96
+# algorithmic bytes of a K-step rollout with observations every step: the state and the
+# integrals read and written once (2 x (52 + 24) B), the waypoint once (16 B), KIN + indices
+# + features every step
+BYTES_OBS_PER_DRONE_STEP = OBS_BYTES
+
+
+def nonfinite_fraction(states) -> float:
+    """Fraction of drones whose position, quaternion, velocity or body rate (state planes
+    0-3) is not finite, over the given [6, n, 4] state tensors."""
+    import torch
+    bad = sum(int((~torch.isfinite(st[0:4]).all(dim=2).all(dim=0)).sum()) for st in states)
+    return bad / sum(int(st.shape[1]) for st in states)
 
 
 def episode_line(n: int, world: int, ep_ms: float, peaks, flops_step: float) -> dict:
     value = throughput(n * N_SUB * EPISODE, world, EPISODE_REPS, ep_ms)
     sec = ep_ms / EPISODE_REPS * 1e-3
-    nbytes = n * (80 + 96 + 16 + EPISODE * BYTES_OBS_PER_DRONE_STEP)
+    nbytes = n * (2 * (STATE_BYTES + INTEG_BYTES) + ACTION_BYTES + EPISODE * BYTES_OBS_PER_DRONE_STEP)
     roof = binding_roofline(nbytes, flops_step * EPISODE, sec, peaks)
     roof["kernel"] = "rollout_kernel<obs every step>"
     return {"what": f"the {EPISODE}-control-step episode as one persistent rollout per launch (mdg_rollout, "
@@ -570,6 +586,7 @@ def run_other(args) -> None:
     total_ms = timed(run, steps)
     clk = clocks.stop()
     rc, bits, _ = h.status()
+    nonfinite_frac = nonfinite_fraction([state])
     if extra_fn is not None:
         timed(extra_fn, 3)
         per_step_ms = timed(extra_fn, min(steps, 200)) / min(steps, 200)
@@ -590,6 +607,7 @@ def run_other(args) -> None:
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
                      "peak_src": ALU_PEAK_SRC, "algorithmic_flops_per_step": flops},
         "clocks": clk, "nonfinite_during_timing": bool(bits & mdg.STATUS_NONFINITE),
+        "nonfinite_fraction_after_timing": nonfinite_frac,
     }
     if args.workload == "single":
         out["us_per_control_step"] = ms * 1e3 / K
@@ -978,12 +996,20 @@ def main() -> None:
     for i in range(args.warmup):
         swarms[i % N_SWARMS].step(stream)
     torch.cuda.synchronize()
-    # one step of every swarm, in rotation, as one CUDA graph (16 launches of the step kernel)
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        cap = torch.cuda.current_stream(dev)
-        for sm in swarms:
-            sm.h.step_obs(sm.state, sm.wp, act_type, N_SUB, sm.kin, sm.idx, sm.rel, stream=cap)
+
+    def capture(first_k):
+        """One step of each of the first first_k swarms, in rotation, as one CUDA graph."""
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            cap = torch.cuda.current_stream(dev)
+            for sm in swarms[:first_k]:
+                sm.h.step_obs(sm.state, sm.wp, act_type, N_SUB, sm.kin, sm.idx, sm.rel, stream=cap)
+        return g
+
+    graph = capture(N_SWARMS)  # 16 launches of the step kernel
+    # regions hold a whole number of rotations except the last one, which ends with one step
+    # of each of the first steps % 16 swarms: that tail is a graph too
+    tail_graph = capture(args.steps % N_SWARMS) if args.steps % N_SWARMS else None
     for sm in swarms:
         sm.reset()
         sm.h.status()
@@ -991,8 +1017,11 @@ def main() -> None:
 
     # Timed region: K control steps back to back, swarm after swarm (inputs larger than L2:
     # each swarm's state, waypoints and observations are touched again only after the 15
-    # other swarms' 299 MB), events around the whole region. Every swarm is reset to its
-    # initial state outside the region; a region holds at most one episode per swarm.
+    # other swarms' 299 MB), events around the whole region. Every launch of the region is in
+    # a CUDA graph (the 16-swarm rotation, then one graph of the first steps % 16 swarms), and
+    # a bounded device sleep before the start event keeps the GPU busy while the host submits
+    # them, so the events see back-to-back device time at any step count. Every swarm is reset
+    # to its initial state outside the region; a region holds at most one episode per swarm.
     seg_max = N_SWARMS * EPISODE
     clocks = ClockSampler(local)
     clocks.start()
@@ -1013,11 +1042,12 @@ def main() -> None:
             dist.barrier()
         torch.cuda.synchronize()
         wall0 = time.perf_counter()
+        torch.cuda._sleep(HEAD_START_CYCLES)
         ev0.record(stream)
         for _ in range(n_seg // N_SWARMS):
             graph.replay()
-        for k in range(n_seg % N_SWARMS):
-            swarms[k].step(stream)
+        if n_seg % N_SWARMS:
+            tail_graph.replay()
         ev1.record(stream)
         torch.cuda.synchronize()
         if world > 1:
@@ -1033,6 +1063,7 @@ def main() -> None:
     for sm in swarms:
         rc, bits, first = sm.h.status()
         nonfinite = nonfinite or bool(bits & mdg.STATUS_NONFINITE)
+    nonfinite_frac = nonfinite_fraction([sm.state for sm in swarms])
 
     # The same step isolated: swarm 0 alone, the L2 flushed before every step and every
     # step bracketed by its own events (launch and timestamp latency included per step).
@@ -1128,8 +1159,10 @@ def main() -> None:
                              f"rotation, each swarm's {SWARM_BYTES / 2**20:.0f} MiB of state, waypoints and "
                              f"observations touched again after the other swarms' "
                              f"{(N_SWARMS - 1) * SWARM_BYTES / 2**20:.0f} MiB; no flush inside the timed region",
-                       "timing": f"CUDA graph of {N_SWARMS} step launches (one per swarm) replayed back to back; "
-                                 "events around the whole timed region",
+                       "timing": f"CUDA graph of {N_SWARMS} step launches (one per swarm) replayed back to back, "
+                                 f"then a graph of the first steps % {N_SWARMS} swarms; a bounded device sleep "
+                                 "before the start event (host submission overlapped); events around the whole "
+                                 "timed region",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": args.e2e_steps,
@@ -1142,6 +1175,7 @@ def main() -> None:
             "clocks": clk,
             "wall_s_timed_region": wall,
             "nonfinite_during_timing": nonfinite,
+            "nonfinite_fraction_after_timing": nonfinite_frac,
             "episode": episode_line(sw.n, world, ep_ms, peaks, flops_launch),
             "isolated_step": {
                 "what": "swarm 0 alone, L2 flushed (512 MiB written, then read back) before every step, every "

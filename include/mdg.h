@@ -453,12 +453,17 @@ int mdg_sync(void* stream, int32_t timeout_ms);
  * Each call uploads the tables and a cleared status word into the array with
  * cudaMemcpyAsync on `stream` from a static host staging buffer, then launches the step
  * kernel there. It calls no cudaMalloc, cudaFree or other allocating routine.
- * The first call on a device performs that device's set-up (it looks up the array's
- * device address with the device current); make that first call before any stream
- * capture. All calls share the array and it keeps the last call's contents, so calls
- * that overlap on the GPU (on different streams or from different host threads) race;
- * serialise them. Errors: MDG_ERR_ARG (as mdg_create / mdg_step_obs, or too many
- * environments), MDG_ERR_CUDA. */
+ * Every call looks up the array's device address with the device current. The first call
+ * on a device also loads the library's device code there (lazy module loading, the CUDA
+ * default), which reserves the array and the code in that device's memory: make it before
+ * another allocator takes the device's free memory (it fails with MDG_ERR_CUDA and a
+ * message naming this cause otherwise). All calls share the array and it keeps the last
+ * call's contents, so calls that overlap on the GPU (on different streams or from
+ * different host threads) race; serialise them. A call made while `stream` is being
+ * captured into a CUDA graph returns MDG_ERR_UNSUPPORTED: the tables come from a host
+ * staging buffer that the next call overwrites, so a replay would read another batch's
+ * tables. Errors: MDG_ERR_ARG (as mdg_create / mdg_step_obs, or too many environments),
+ * MDG_ERR_UNSUPPORTED (DSL controller, stream capture), MDG_ERR_CUDA. */
 #define MDG_NOALLOC_MAX_ENVS 16384
 #define MDG_NOALLOC_SCRATCH_BYTES 360960
 int mdg_step_obs_noalloc(const mdg_constants* c, int32_t n_envs, const int32_t* drones_per_env,
@@ -517,6 +522,18 @@ int mdg_mlp_adam(mdg_mlp m, float lr, void* stream);
 #define MDG_MLP_PATH_MMA_SYNC 0
 #define MDG_MLP_PATH_TCGEN05 1
 int mdg_mlp_set_path(mdg_mlp m, int32_t path);
+/* Bounds of the tcgen05 kernel's waits on its own mbarriers (its MMAs, bulk copies and
+ * epilogue hand-offs): try_waits mbarrier.try_wait calls (each suspends at most ~1 us) for
+ * the producer and MMA waits, polls test_wait polls for the MMA/epilogue hand-offs; a wait
+ * that runs out sets MDG_STATUS_TIMEOUT, and the kernel then abandons its tiles: every role
+ * leaves its loop, the copies and MMAs already issued are waited for with the default bound,
+ * the tensor memory is freed and the launch returns (outputs of abandoned tiles are not
+ * written). For exercising that exit without a stuck device: 0 gives up at the first wait
+ * that is not already complete. A negative value restores the default (the constants below,
+ * a few tenths of a second each). Host only; affects later launches of this surrogate. */
+#define MDG_MLP_DEFAULT_TRY_WAITS 262144
+#define MDG_MLP_DEFAULT_POLLS 4194304
+int mdg_mlp_set_wait_limits(mdg_mlp m, int32_t try_waits, int32_t polls);
 /* Read and clear the surrogate's status word (synchronises `stream`): MDG_STATUS_TIMEOUT
  * if a tensor-core kernel abandoned its work. */
 int mdg_mlp_status(mdg_mlp m, void* stream, uint32_t* bits);

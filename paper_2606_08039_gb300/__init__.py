@@ -99,6 +99,7 @@ _SIGNATURES = {
     "mdg_mlp_grad": ([_VP, _VP, _VP, ctypes.c_int32, _VP, _VP], ctypes.c_int),
     "mdg_mlp_adam": ([_VP, ctypes.c_float, _VP], ctypes.c_int),
     "mdg_mlp_set_path": ([_VP, ctypes.c_int32], ctypes.c_int),
+    "mdg_mlp_set_wait_limits": ([_VP, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "mdg_mlp_status": ([_VP, _VP, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
     "mdg_features": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "mdg_surrogate_step": ([_VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, _VP, _VP],
@@ -614,6 +615,10 @@ class MLP:
     def set_path(self, path: int):
         """Inference path: MLP_PATH_TCGEN05 (fused tensor-memory kernel) or MLP_PATH_MMA_SYNC."""
         _check(lib().mdg_mlp_set_path(self._m, int(path)))
+
+    def set_wait_limits(self, try_waits: int = -1, polls: int = -1):
+        """Bounds of the tcgen05 kernel's mbarrier waits (negative: the defaults)."""
+        _check(lib().mdg_mlp_set_wait_limits(self._m, int(try_waits), int(polls)))
 
     def status(self, stream=None) -> int:
         bits = ctypes.c_uint32()

@@ -204,7 +204,7 @@ cudaError_t mlp_standardize(const float* raw, void* x, long long rows, const flo
 size_t mlp_image_bytes();
 cudaError_t mlp_build_image(const MlpView& w, void* img, cudaStream_t s);
 cudaError_t mlp_forward_umma(const MlpView& w, const void* img, const void* x, int B, float* y, uint32_t* status,
-                             cudaStream_t s);
+                             int wait_limit, int spin_limit, cudaStream_t s);
 
 cudaError_t launch_obs(const StepArgs& a, int n_tiles, int block, cudaStream_t s);
 cudaError_t launch_pid(const PidArgs& a, cudaStream_t s);

@@ -7,9 +7,14 @@
 // point keeps those tables in a file-scope static device array instead, so the only
 // device memory it touches is that array and the caller's own buffers.
 //
-// The array g_scratch is reserved in every GPU that loads the library, for the life of
-// the process. Every call shares it and it keeps the last call's contents, so calls that
-// overlap on the GPU (on different streams, or from different host threads) race.
+// The array g_scratch is reserved in every GPU that loads the library's device code, for
+// the life of the process; with lazy module loading (the CUDA default) that happens at the
+// first call on a device, which therefore needs about 353 KiB of free device memory plus the
+// library's code. Every call shares the array and it keeps the last call's contents, so
+// calls that overlap on the GPU (on different streams, or from different host threads) race.
+// A call made while its stream is being captured into a CUDA graph is refused: the tables
+// are uploaded from a host staging buffer that the next call overwrites, so a replayed
+// graph would pair one batch's sizes with another batch's tables.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -40,7 +45,7 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 // Host staging copy of the tables (static storage, reused by every call under g_lock).
 unsigned char g_stage[kScratchBytes];
 std::mutex g_lock;
-void* g_dev_scratch[64] = {};  // device address of g_scratch, per device
+bool g_loaded[64] = {};  // the device has given g_scratch's address once (its module is loaded)
 
 // Records the message for mdg_last_error() and returns the code.
 int fail(int code, const char* fmt, ...)
@@ -54,19 +59,27 @@ int fail(int code, const char* fmt, ...)
     return code;
 }
 
-// Set-up, once per device with that device current: the device address of g_scratch.
-// (In host code g_scratch names a host-side stand-in, not device memory.)
+// The device address of g_scratch on the current device, looked up on every call with the
+// device current (in host code g_scratch names a host-side stand-in, not device memory). A
+// cached address would outlive the context it belongs to: after cudaDeviceReset the next
+// call runs in a new context, where the array has been reserved again, maybe elsewhere. The
+// first lookup on a device loads the library's device code and reserves the array there.
 int scratch_address(int dev, void** out)
 {
     if (dev < 0 || dev >= 64) return fail(MDG_ERR_UNSUPPORTED, "mdg_step_obs_noalloc: device %d out of range", dev);
-    if (!g_dev_scratch[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(MDG_ERR_CUDA, "mdg_step_obs_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-        g_dev_scratch[dev] = p;
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p) {
+        if (!g_loaded[dev])
+            return fail(MDG_ERR_CUDA,
+                        "mdg_step_obs_noalloc: first call on device %d: loading the library's device code and its "
+                        "%d-byte static array failed (%s); make the first call before another allocator reserves "
+                        "the device's free memory",
+                        dev, (int)kScratchBytes, cudaGetErrorString(e));
+        return fail(MDG_ERR_CUDA, "mdg_step_obs_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
     }
-    *out = g_dev_scratch[dev];
+    g_loaded[dev] = true;
+    *out = p;
     return MDG_OK;
 }
 
@@ -98,6 +111,14 @@ extern "C" int mdg_step_obs_noalloc(const mdg_constants* c, int32_t n_envs, cons
     if (!mdg::constants_valid(cc, why)) return fail(MDG_ERR_ARG, "mdg_step_obs_noalloc: %s", why.c_str());
     if (cc.controller == MDG_CTRL_DSL)
         return fail(MDG_ERR_UNSUPPORTED, "mdg_step_obs_noalloc: the DSL controller needs a handle's setpoints");
+    cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+    const cudaError_t cap = cudaStreamIsCapturing((cudaStream_t)stream, &capturing);
+    if (cap != cudaSuccess)
+        return fail(MDG_ERR_CUDA, "mdg_step_obs_noalloc: cudaStreamIsCapturing: %s", cudaGetErrorString(cap));
+    if (capturing != cudaStreamCaptureStatusNone)
+        return fail(MDG_ERR_UNSUPPORTED,
+                    "mdg_step_obs_noalloc: the stream is being captured; the call uploads its tables from a host "
+                    "buffer that the next call overwrites, so it cannot be replayed from a graph");
 
     std::lock_guard<std::mutex> lock(g_lock);
     int32_t* off = reinterpret_cast<int32_t*>(g_stage + kOffEnvOff);

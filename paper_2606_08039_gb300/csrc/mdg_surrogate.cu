@@ -72,6 +72,8 @@ struct mdg_mlp_s {
     int path = MDG_MLP_PATH_TCGEN05;
     uint8_t* img = nullptr;      // weight image of the tcgen05 kernel
     bool img_stale = true;       // the bf16 weights changed since the image was built
+    int wait_limit = MDG_MLP_DEFAULT_TRY_WAITS;  // bounded waits of the tcgen05 kernel
+    int spin_limit = MDG_MLP_DEFAULT_POLLS;
     mdg::MlpView view() const { return layout(master, w16); }
 };
 
@@ -110,7 +112,7 @@ cudaError_t forward_umma(mdg_mlp m, const void* x, int B, float* y, uint32_t* st
         if (e != cudaSuccess) return e;
         m->img_stale = false;
     }
-    return mdg::mlp_forward_umma(m->view(), m->img, x, B, y, status, s);
+    return mdg::mlp_forward_umma(m->view(), m->img, x, B, y, status, m->wait_limit, m->spin_limit, s);
 }
 
 bool batch_ok(mdg_mlp m, int B) { return B > 0 && B % 128 == 0 && B <= m->max_batch; }
@@ -299,6 +301,14 @@ int mdg_mlp_set_path(mdg_mlp m, int32_t path)
     if (path != MDG_MLP_PATH_MMA_SYNC && path != MDG_MLP_PATH_TCGEN05)
         return fail(MDG_ERR_ARG, "mdg_mlp_set_path: unknown path %d", path);
     m->path = path;
+    return MDG_OK;
+}
+
+int mdg_mlp_set_wait_limits(mdg_mlp m, int32_t try_waits, int32_t polls)
+{
+    if (!m) return fail(MDG_ERR_ARG, "mdg_mlp_set_wait_limits: NULL handle");
+    m->wait_limit = try_waits < 0 ? MDG_MLP_DEFAULT_TRY_WAITS : try_waits;
+    m->spin_limit = polls < 0 ? MDG_MLP_DEFAULT_POLLS : polls;
     return MDG_OK;
 }
 

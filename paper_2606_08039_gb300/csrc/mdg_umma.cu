@@ -53,8 +53,8 @@ constexpr uint32_t kDynBytes = kOffSlot + kSlots * kSlotBytes;
 constexpr uint32_t kTmemCols = 512;        // two accumulators of 256 columns
 constexpr int kLoadsPerTile = 10;          // W1, W2 chunks 0-3, W3 chunks 0-3, W4
 constexpr uint32_t kSuspendNs = 1000;      // longest suspension of one mbarrier try_wait
-constexpr int kWaitLimit = 1 << 18;        // try_waits (at most ~0.26 s) before giving up
-constexpr int kSpinLimit = 1 << 22;        // polls of a spinning wait (a few tenths of a second)
+constexpr int kWaitLimit = MDG_MLP_DEFAULT_TRY_WAITS;  // try_waits (at most ~0.26 s) before giving up
+constexpr int kSpinLimit = MDG_MLP_DEFAULT_POLLS;      // polls of a spinning wait (a few tenths of a second)
 
 // Weight image: the chunks in the order the MMAs consume them, load i at i * 32 KB.
 //   load 0      W1 [256 x 64]
@@ -130,12 +130,15 @@ __device__ __forceinline__ bool mbar_test(uint32_t mbar, uint32_t parity)
 
 // Wait for the phase of `parity` to complete: one non-blocking test, then mbarrier.try_wait,
 // which suspends the thread in hardware until the phase completes or about kSuspendNs pass.
-// Gives up when another role has aborted (abort != null) or after kWaitLimit tries, which
-// records the timeout and aborts the block.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int* abort, uint32_t* status)
+// Gives up when another role has aborted (abort != null) or after `limit` tries, which
+// records the timeout and aborts the block. The work waits take the launch's limit; the
+// drain waits of the exit path always take kWaitLimit, so that a block leaves only once
+// every copy and MMA it issued has completed.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int* abort, uint32_t* status,
+                                          int limit)
 {
     if (mbar_test(mbar, parity)) return true;
-    for (int i = 0; i < kWaitLimit; ++i) {
+    for (int i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
@@ -152,11 +155,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volati
 
 // The same for waits on the critical path between MMAs and epilogue: poll with test_wait
 // (a suspended thread wakes up later than a polling one), backing off by `sleep_ns` between
-// polls (0: none), at most kSpinLimit polls.
+// polls (0: none), at most `limit` polls.
 __device__ __forceinline__ bool mbar_spin(uint32_t mbar, uint32_t parity, volatile int* abort, uint32_t* status,
-                                          int sleep_ns)
+                                          int sleep_ns, int limit)
 {
-    for (int i = 0; i < kSpinLimit; ++i) {
+    for (int i = 0; i < limit; ++i) {
         if (mbar_test(mbar, parity)) return true;
         if ((i & 63) == 63 && *abort) return false;
         if (sleep_ns) __nanosleep(sleep_ns);
@@ -226,7 +229,8 @@ __device__ __forceinline__ __nv_bfloat162 silu_pair(float h0, float h1)
 
 __global__ void __launch_bounds__(kThreads, 1)
     mlp_umma_kernel(const __nv_bfloat16* __restrict__ x, float* __restrict__ y, int n_tiles,
-                    const uint8_t* __restrict__ w_img, const float* __restrict__ master, MlpView w, uint32_t* status)
+                    const uint8_t* __restrict__ w_img, const float* __restrict__ master, MlpView w, uint32_t* status,
+                    int wait_limit, int spin_limit)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -281,7 +285,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++s) {
             for (int i = 0; i < kLoadsPerTile; ++i, ++j) {
                 const int slot = j % kSlots, use = j / kSlots;
-                if (use > 0) ok = __all_sync(0xffffffffu, mbar_wait(bar(kBarWEmpty + slot), (use - 1) & 1, abort, status));
+                if (use > 0) ok = __all_sync(0xffffffffu, mbar_wait(bar(kBarWEmpty + slot), (use - 1) & 1, abort, status, wait_limit));
                 if (!ok) break;
                 const uint32_t bytes = i == kLoadsPerTile - 1 ? 16384u : kSlotBytes;
                 if (lane == 0) {
@@ -297,7 +301,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (lane == 0) mbar_arrive(bar(kBarXFull));
                 } else if (i == 4 && tile + (int)gridDim.x < n_tiles) {
                     // layer 0 of this tile is done with the input buffer: fetch the next tile's
-                    ok = __all_sync(0xffffffffu, mbar_wait(bar(kBarXEmpty), s & 1, abort, status));
+                    ok = __all_sync(0xffffffffu, mbar_wait(bar(kBarXEmpty), s & 1, abort, status, wait_limit));
                     if (!ok) {
                         ++j;
                         break;
@@ -311,7 +315,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0)
             for (int slot = 0; slot < kSlots && slot < j; ++slot) {
                 const int uses = (j - 1 - slot) / kSlots + 1;  // loads issued into this slot
-                mbar_wait(bar(kBarWFull + slot), (uses - 1) & 1, nullptr, status);
+                mbar_wait(bar(kBarWFull + slot), (uses - 1) & 1, nullptr, status, kWaitLimit);
             }
         __syncwarp();
     } else if (warp == kMmaWarp) {
@@ -323,8 +327,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ok = true;
             for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++s) {
                 // layer 0: x [128 x 64] . W1^T -> accumulator 0
-                ok = mbar_wait(bar(kBarXFull), s & 1, abort, status) &&
-                     mbar_wait(bar(kBarWFull + j % kSlots), (j / kSlots) & 1, abort, status);
+                ok = mbar_wait(bar(kBarXFull), s & 1, abort, status, wait_limit) &&
+                     mbar_wait(bar(kBarWFull + j % kSlots), (j / kSlots) & 1, abort, status, wait_limit);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 {
@@ -346,8 +350,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t d = tmem + (uint32_t)(l & 1) * 256;
                     bool act_ok = false, w_ok = false;  // the group's barriers, tested ahead
                     for (int c = 0; c < 4; ++c, ++j) {
-                        ok = (act_ok || mbar_spin(bar(kBarActFull + c), n_act & 1, abort, status, 0)) &&
-                             (w_ok || mbar_wait(bar(kBarWFull + j % kSlots), (j / kSlots) & 1, abort, status));
+                        ok = (act_ok || mbar_spin(bar(kBarActFull + c), n_act & 1, abort, status, 0, spin_limit)) &&
+                             (w_ok || mbar_wait(bar(kBarWFull + j % kSlots), (j / kSlots) & 1, abort, status,
+                                                wait_limit));
                         if (!ok) break;
                         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                         const uint32_t asl = act_a + c * kChunkBytes, wsl = slot_a + (j % kSlots) * kSlotBytes;
@@ -366,11 +371,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 if (!ok) break;
                 // layer 3: W4 [32 x 256] in one slot as four [32 x 64] chunks -> accumulator 1
-                ok = mbar_wait(bar(kBarWFull + j % kSlots), (j / kSlots) & 1, abort, status);
+                ok = mbar_wait(bar(kBarWFull + j % kSlots), (j / kSlots) & 1, abort, status, wait_limit);
                 const uint32_t wsl = slot_a + (j % kSlots) * kSlotBytes;
                 bool act_ok = false;
                 for (int c = 0; c < 4 && ok; ++c) {
-                    ok = act_ok || mbar_spin(bar(kBarActFull + c), n_act & 1, abort, status, 0);
+                    ok = act_ok || mbar_spin(bar(kBarActFull + c), n_act & 1, abort, status, 0, spin_limit);
                     if (!ok) break;
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                     const uint32_t asl = act_a + c * kChunkBytes, bsl = wsl + c * 4096;
@@ -388,7 +393,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             // nothing in flight before the tensor memory is freed
             mma_commit(bar(kBarMmaDone));
-            mbar_wait(bar(kBarMmaDone), 0, nullptr, status);
+            mbar_wait(bar(kBarMmaDone), 0, nullptr, status, kWaitLimit);
         }
         __syncwarp();
     } else {
@@ -402,7 +407,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
             for (int l = 0; l < 3 && ok; ++l) {
                 const int b = l & 1;
-                ok = __all_sync(0xffffffffu, mbar_spin(bar(kBarAccFull + b), (b ? n_acc1 : n_acc0) & 1, abort, status, 32));
+                ok = __all_sync(0xffffffffu, mbar_spin(bar(kBarAccFull + b), (b ? n_acc1 : n_acc0) & 1, abort, status, 32,
+                                                       spin_limit));
                 if (!ok) break;
                 n_acc0 += 1 - b;
                 n_acc1 += b;
@@ -435,7 +441,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (!ok) break;
             // output layer: accumulator 1, 32 columns, eight per column part
-            ok = __all_sync(0xffffffffu, mbar_spin(bar(kBarAccFull + 1), n_acc1 & 1, abort, status, 32));
+            ok = __all_sync(0xffffffffu, mbar_spin(bar(kBarAccFull + 1), n_acc1 & 1, abort, status, 32, spin_limit));
             if (!ok) break;
             ++n_acc1;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -489,7 +495,7 @@ cudaError_t mlp_build_image(const MlpView& w, void* img, cudaStream_t s)
 }
 
 cudaError_t mlp_forward_umma(const MlpView& w, const void* img, const void* x, int B, float* y, uint32_t* status,
-                             cudaStream_t s)
+                             int wait_limit, int spin_limit, cudaStream_t s)
 {
     if (B % kRows) return cudaErrorInvalidValue;
     const int n_tiles = B / kRows;
@@ -508,7 +514,8 @@ cudaError_t mlp_forward_umma(const MlpView& w, const void* img, const void* x, i
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     const int grid = n_tiles < n_sm ? n_tiles : n_sm;
     mlp_umma_kernel<<<grid, kThreads, kUmmaSmem, s>>>(static_cast<const __nv_bfloat16*>(x), y, n_tiles,
-                                                      static_cast<const uint8_t*>(img), w.master, w, status);
+                                                      static_cast<const uint8_t*>(img), w.master, w, status,
+                                                      wait_limit, spin_limit);
     return cudaGetLastError();
 }
 

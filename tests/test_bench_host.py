@@ -107,20 +107,20 @@ def test_clock_summary_uses_the_samples_inside_the_timed_region():
 
 
 def test_algorithmic_bytes_per_drone_and_control_step():
-    """The bytes the roofline divides by: 384 B per drone for PID waypoints (state planes 0-4
-    read, 0-5 written, the waypoint, KIN + indices + features), 352 B for plain RPM actions
-    (no integral plane read or written), +32 B with the DSL setpoint, and 544 B under
-    randomization with an action history of depth 3 (rotor speeds, history shift, the row
-    and wind state of each four-drone environment)."""
+    """The bytes the roofline divides by: 360 B per drone for PID waypoints (the 13-value state
+    and the 6 integrals read and written, the waypoint, KIN + indices + features), 312 B for
+    plain RPM actions (no integrals), +32 B with the DSL setpoint, and 520 B under
+    randomization with an action history of depth 3 (rotor speeds, history shift, the row and
+    wind state of each four-drone environment)."""
     sw = wl.full_aero(1, n_envs=64)
     n = sw.n
     pid = np.full(sw.n_envs, 1, np.uint8)
     rpm = np.zeros(sw.n_envs, np.uint8)
-    assert bench.algorithmic_bytes(sw, pid, 1, False) == 384 * n
-    assert bench.algorithmic_bytes(sw, rpm, 0, False) == 352 * n
-    assert bench.algorithmic_bytes(sw, pid, 1, True) == 416 * n
-    assert bench.algorithmic_bytes(sw, pid, 1, False, dr_depth=3) == 544 * n
-    assert bench.BYTES_PER_DRONE_STEP == 384
+    assert bench.algorithmic_bytes(sw, pid, 1, False) == 360 * n
+    assert bench.algorithmic_bytes(sw, rpm, 0, False) == 312 * n
+    assert bench.algorithmic_bytes(sw, pid, 1, True) == 392 * n
+    assert bench.algorithmic_bytes(sw, pid, 1, False, dr_depth=3) == 520 * n
+    assert bench.BYTES_PER_DRONE_STEP == 360
 
 
 def test_binding_roofline_takes_the_longer_ideal_time():

@@ -82,6 +82,36 @@ def test_forward_matches_oracle(cuda, path, B):
     assert np.all(np.abs(y.cpu().numpy() - yo) <= bound)
 
 
+def test_tcgen05_bounded_wait_exit(cuda):
+    """The tcgen05 kernel's exit on an expired wait, without a stuck device: with wait bounds
+    of zero the first wait that is not already complete (at the latest the epilogue's wait
+    for its first accumulator) gives up on a normal 128-row launch. The launch returns with
+    MDG_STATUS_TIMEOUT set; a launch with the default bounds then matches the oracle, so the
+    abandoned launch drained its copies and MMAs and freed its tensor memory."""
+    layers = _layers(1)
+    m = mdg.MLP(128, layers)
+    m.set_path(mdg.MLP_PATH_TCGEN05)
+    x = torch.as_tensor(_inputs(2, 128), device=cuda).to(torch.bfloat16)
+    y = torch.full((128, mdg.MLP_OUT_PAD), float("nan"), device=cuda)
+    m.set_wait_limits(0, 0)
+    m.forward(x, y)
+    assert mdg.lib().mdg_sync(mdg._stream(None), 5000) == mdg.OK  # the launch returned
+    assert m.status() & mdg.STATUS_TIMEOUT
+    for _ in range(2):  # again, and on the blocks' second use of the SMs' tensor memory
+        m.forward(x, y)
+        torch.cuda.synchronize()
+        assert m.status() & mdg.STATUS_TIMEOUT
+    m.set_wait_limits()
+    y.fill_(float("nan"))
+    m.forward(x, y)
+    torch.cuda.synchronize()
+    assert m.status() == 0
+    xo = x.float().cpu().numpy().astype(np.float64)
+    yo, _ = omlp.forward(_f64(layers), xo, bf16_storage=True)
+    bound = 1e-2 * np.maximum(np.abs(yo), 1.0) + _tanh_error_response(_f64(layers), xo, yo)
+    assert np.all(np.abs(y.cpu().numpy() - yo) <= bound)
+
+
 def test_gradients_and_loss_match_oracle(cuda):
     B = 256
     layers = _layers(3)

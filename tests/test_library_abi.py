@@ -136,3 +136,17 @@ def test_null_handle_calls_fail_cleanly(mdg_lib):
 def test_sync_rejects_a_negative_limit_before_any_cuda_call(mdg_lib):
     assert mdg_lib.mdg_sync(None, -1) == mdg.ERR_ARG
     assert b"timeout_ms" in mdg_lib.mdg_last_error()
+
+
+def test_noalloc_source_names_no_device_allocation():
+    """mdg_step_obs_noalloc's translation unit calls no device allocator (comments and string
+    literals aside): its only device memory is the static array and the caller's buffers."""
+
+    src = open(os.path.join(ROOT, "paper_2606_08039_gb300", "csrc", "mdg_noalloc.cu")).read()
+    code = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    code = re.sub(r"//[^\n]*", "", code)
+    code = re.sub(r'"(\\.|[^"\\])*"', '""', code)
+    banned = re.findall(r"\b(cudaMalloc\w*|cudaFree\w*|cuMemAlloc\w*|cuMemCreate|cudaMemPool\w*|"
+                        r"cudaHostAlloc|cudaMallocHost)\b", code)
+    assert banned == []
+    assert "cudaGetSymbolAddress" in code and "cudaStreamIsCapturing" in code

@@ -70,6 +70,60 @@ def test_noalloc_matches_handle_api_two_steps(cuda, recipe):
         assert h.status()[0] == mdg.OK
 
 
+def _small_batch(cuda):
+    sw = wl.full_aero(93, n_envs=256)
+    state = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=cuda)
+    a = torch.as_tensor(wl.waypoints(93, sw.n), device=cuda)
+    kin = torch.empty((sw.n, 20), device=cuda)
+    idx = torch.empty((sw.n, 4), dtype=torch.int32, device=cuda)
+    rel = torch.empty((sw.n, 24), device=cuda)
+    status = torch.zeros(2, dtype=torch.int32, device=cuda)
+    return sw, state, a, kin, idx, rel, status
+
+
+def test_noalloc_calls_leave_device_memory_unchanged(cuda):
+    """The point of the entry point: after one call (which may load the library's device
+    code on this device), further calls take no device memory. Every tensor is allocated
+    before the first reading, and nothing else runs between the readings."""
+    sw, state, a, kin, idx, rel, status = _small_batch(cuda)
+    _noalloc_step(sw, state, a, mdg.ACT_PID, kin, idx, rel, status)
+    torch.cuda.synchronize()
+    torch.cuda.mem_get_info()  # any first-use set-up of the query itself
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(20):
+        _noalloc_step(sw, state, a, mdg.ACT_PID, kin, idx, rel, status)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
+def test_noalloc_refuses_a_capturing_stream(cuda):
+    """A graph captured around the call would replay uploads from a host buffer that later
+    calls overwrite: the call returns MDG_ERR_UNSUPPORTED while the stream is capturing, and
+    works again on the same stream afterwards."""
+    sw, state, a, kin, idx, rel, status = _small_batch(cuda)
+    L = mdg.lib()
+    dpe = np.ascontiguousarray(sw.drones_per_env, np.int32)
+    flg = np.ascontiguousarray(sw.flags, np.uint32)
+    side = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    marker = torch.zeros(1, device=cuda)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            marker.add_(1.0)  # the graph is not empty
+            rc = L.mdg_step_obs_noalloc(None, sw.n_envs, dpe.ctypes.data_as(VP), flg.ctypes.data_as(VP), None,
+                                        VP(state.data_ptr()), VP(a.data_ptr()), mdg.ACT_PID, 5,
+                                        VP(kin.data_ptr()), VP(idx.data_ptr()), VP(rel.data_ptr()),
+                                        VP(status.data_ptr()), VP(side.cuda_stream))
+            msg = L.mdg_last_error().decode()
+    assert rc == mdg.ERR_UNSUPPORTED and "captured" in msg
+    torch.cuda.synchronize()
+    _noalloc_step(sw, state, a, mdg.ACT_PID, kin, idx, rel, status)
+    torch.cuda.synchronize()
+    assert status.cpu().numpy().view(np.uint32)[0] == 0
+
+
 def test_noalloc_rejects_oversized_batches(cuda):
     L = mdg.lib()
     n_envs = 16385
