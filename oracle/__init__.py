@@ -44,14 +44,16 @@ STREAM_WIND, STREAM_OBS = 21, 22
 class _DR(ctypes.Structure):
     _fields_ = [("env_dr", ctypes.POINTER(ctypes.c_double)), ("motor", ctypes.POINTER(ctypes.c_double)),
                 ("hist", ctypes.POINTER(ctypes.c_double)), ("depth", ctypes.c_int32),
-                ("wind", ctypes.POINTER(ctypes.c_double)), ("seed", ctypes.c_uint64)]
+                ("wind", ctypes.POINTER(ctypes.c_double)), ("seed", ctypes.c_uint64),
+                ("obs_bias", ctypes.POINTER(ctypes.c_double))]
 
 
 class Randomization:
     """Domain-randomization and wind inputs and state of orc_control_steps: env_dr
     [n_envs, DR_PARAMS] (neutral: factors 1, no lag, no delay, no wind), motor [n, 4] and
     hist [depth, n, 4] (NaN: not set), wind [n_envs, WIND_STATE] (Dryden 0, gust idle,
-    step 0); all float64, updated in place by control_steps."""
+    step 0); all float64, updated in place by control_steps. obs_bias: None or [n, 12], the
+    sticky per-episode observation bias added to the KIN channels (orc_obs_bias)."""
 
     def __init__(self, n_envs: int, n: int, depth: int = 1, seed: int = 0):
         self.env_dr = neutral_dr(n_envs)
@@ -60,12 +62,16 @@ class Randomization:
         self.wind = np.zeros((n_envs, WIND_STATE))
         self.wind[:, 3] = -1.0
         self.seed = int(seed)
+        self.obs_bias = None
 
     def struct(self) -> _DR:
         for a in (self.env_dr, self.motor, self.hist, self.wind):
             assert a.dtype == np.float64 and a.flags.c_contiguous
+        if self.obs_bias is not None:
+            assert self.obs_bias.dtype == np.float64 and self.obs_bias.flags.c_contiguous
+            assert self.obs_bias.shape == (self.motor.shape[0], 12)
         return _DR(_dptr(self.env_dr), _dptr(self.motor), _dptr(self.hist), self.hist.shape[0], _dptr(self.wind),
-                   ctypes.c_uint64(self.seed))
+                   ctypes.c_uint64(self.seed), _dptr(self.obs_bias) if self.obs_bias is not None else None)
 
 
 def neutral_dr(n_envs: int) -> np.ndarray:
@@ -156,6 +162,8 @@ def lib():
                                        _D, _I, _D, _D, ctypes.POINTER(_DR)], ctypes.c_int),
                 "orc_uniform": ([ctypes.c_uint64] * 5, ctypes.c_double),
                 "orc_splitmix64": ([ctypes.c_uint64], ctypes.c_uint64),
+                "orc_reset_state": ([_D, _D, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _D], None),
+                "orc_obs_bias": ([_D, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _D], None),
                 "orc_params_randomized": ([P, _D, P], None),
                 "orc_wind_step": ([P, _D, _D, ctypes.c_uint64, ctypes.c_int64, _D, _D], None),
             }
@@ -383,6 +391,24 @@ def splitmix64(z: int) -> int:
     """The oracle's SplitMix64 round: the generator's output for the state z before its
     increment by the golden gamma (so z = k * gamma gives the (k+1)-th output from state 0)."""
     return int(lib().orc_splitmix64(ctypes.c_uint64(z % (1 << 64))))
+
+
+def reset_state(nominal, ranges, seed: int, episode: int, drone: int) -> np.ndarray:
+    """Initial state [13] of one drone for one episode (orc_reset_state): nominal [x, y, z,
+    yaw], ranges [p0 (m), rpy0 (rad), v0 (m/s)] half-widths of the uniform perturbations."""
+    nom, rng = _f64(nominal), _f64(ranges)
+    x = np.zeros(13)
+    lib().orc_reset_state(_dptr(nom), _dptr(rng), seed, episode, drone, _dptr(x))
+    return x
+
+
+def obs_bias(sigmas, seed: int, episode: int, drone: int) -> np.ndarray:
+    """Sticky per-episode observation bias [12] of one drone (orc_obs_bias): sigmas [position,
+    roll/pitch/yaw, velocity, body rate]."""
+    sg = _f64(sigmas)
+    b = np.zeros(12)
+    lib().orc_obs_bias(_dptr(sg), seed, episode, drone, _dptr(b))
+    return b
 
 
 def uniform(seed: int, stream: int, step: int, index: int, comp: int) -> float:

@@ -103,6 +103,8 @@
 #define ORC_WIND_STATE 8   /* per environment: Dryden x (3), gust phase s (-1 idle), gust direction (3), steps */
 #define ORC_STREAM_WIND 21 /* random stream of the wind draws */
 #define ORC_STREAM_OBS 22  /* random stream of the observation noise */
+#define ORC_STREAM_INIT 23 /* random stream of the per-episode initial states */
+#define ORC_STREAM_BIAS 24 /* random stream of the per-episode observation bias */
 
 /* Model parameters. Field order is the oracle's own; the Python side of the
  * oracle mirrors it. */
@@ -986,6 +988,53 @@ void orc_wind_step(const orc_params* P, const double* dr, double* ws, uint64_t s
     ws[7] = (double)(step + 1);
 }
 
+/* ---- episode reset under domain randomization (Section 3.5) ---- */
+
+/* The initial state of one drone for one episode, the "init" row of Table "Recommended
+ * domain-randomization ranges" (p0 +-0.2 m, RPY0 +-0.1 rad, v0 +-0.5 m/s, drawn at every
+ * reset like the rest of the table): each component is its nominal value plus a uniform
+ * draw in [-r, r],
+ *   p0   = nominal[0..2] + r[0] (2 u_k - 1), k = 0, 1, 2
+ *   RPY0 = (0, 0, nominal[3]) + r[1] (2 u_k - 1), k = 3, 4, 5 (roll, pitch, yaw)
+ *   v0   = r[2] (2 u_k - 1), k = 6, 7, 8
+ * with u_k = orc_uniform(seed, ORC_STREAM_INIT, episode, drone, k); the attitude is the
+ * quaternion of R = Rz(yaw) Ry(pitch) Rx(roll) (the ZYX convention orc_rpy inverts), the body
+ * rate zero. x = [p, q, v, omega]. */
+void orc_reset_state(const double nominal[4], const double r[3], uint64_t seed, uint64_t episode, uint64_t drone,
+                     double x[13])
+{
+    double u[9];
+    for (int k = 0; k < 9; ++k) u[k] = 2.0 * orc_uniform(seed, ORC_STREAM_INIT, episode, drone, (uint64_t)k) - 1.0;
+    const double roll = r[1] * u[3], pitch = r[1] * u[4], yaw = nominal[3] + r[1] * u[5];
+    const double qx[4] = {cos(0.5 * roll), sin(0.5 * roll), 0.0, 0.0};
+    const double qy[4] = {cos(0.5 * pitch), 0.0, sin(0.5 * pitch), 0.0};
+    const double qz[4] = {cos(0.5 * yaw), 0.0, 0.0, sin(0.5 * yaw)};
+    double qzy[4];
+    orc_quat_mul(qz, qy, qzy);
+    for (int k = 0; k < 3; ++k) x[k] = nominal[k] + r[0] * u[k];
+    orc_quat_mul(qzy, qx, x + 3);
+    for (int k = 0; k < 3; ++k) x[7 + k] = r[2] * u[6 + k];
+    for (int k = 0; k < 3; ++k) x[10 + k] = 0.0;
+}
+
+/* The sticky per-episode observation bias of recommendation (iii) of Section 3.5 ("coupling
+ * DR with a sticky per-episode bias on the observation"; its size is not printed): one
+ * Gaussian offset per KIN channel that the sensor noise also perturbs, drawn at the reset
+ * and held for the episode, b_k = sigma[k / 3] xi_k for the channels k = 0..11 (position
+ * 0-2, roll/pitch/yaw 3-5, velocity 6-8, body rate 9-11), xi by Box-Muller on the pairs of
+ * uniforms (seed, ORC_STREAM_BIAS, episode, drone, 2m) and (.., 2m + 1): xi_2m = rho cos(2 pi
+ * u_2m+1), xi_2m+1 = rho sin(2 pi u_2m+1), rho = sqrt(-2 ln(1 - u_2m)). */
+void orc_obs_bias(const double sigma[4], uint64_t seed, uint64_t episode, uint64_t drone, double b[12])
+{
+    for (int m = 0; m < 6; ++m) {
+        const double u1 = 1.0 - orc_uniform(seed, ORC_STREAM_BIAS, episode, drone, (uint64_t)(2 * m));
+        const double u2 = orc_uniform(seed, ORC_STREAM_BIAS, episode, drone, (uint64_t)(2 * m + 1));
+        const double rho = sqrt(-2.0 * log(u1));
+        b[2 * m] = sigma[(2 * m) / 3] * rho * cos(2.0 * ORC_PI * u2);
+        b[2 * m + 1] = sigma[(2 * m + 1) / 3] * rho * sin(2.0 * ORC_PI * u2);
+    }
+}
+
 /* Runs K control steps (Section 3.4.2: sim_freq/ctrl_freq substeps per step) for
  * n_envs environments laid out in CSR order (drones of env e are
  * env_off[e] .. env_off[e+1]-1). Per control step and environment: the action of
@@ -1018,7 +1067,9 @@ void orc_wind_step(const orc_params* P, const double* dr, double* ws, uint64_t s
  *   Gaussian noise of the row's sigmas, drawn from the counters (seed, ORC_STREAM_OBS, the
  *   environment's wind step of the last step, drone, component 0..11; Box-Muller on the
  *   pairs (0, 1), ..., (10, 11): position 0-2, rpy 3-5, velocity 6-8, body rate 9-11); the
- *   neighbour observation is not delayed and carries no noise.
+ *   neighbour observation is not delayed and carries no noise. obs_bias [n][12] (or NULL),
+ *   the sticky per-episode bias of orc_obs_bias, is added to the same KIN channels as the
+ *   noise (position, roll/pitch/yaw, velocity, body rate), delayed or not.
  * Returns 0, or -1 on a bad argument. */
 typedef struct {
     const double* env_dr;
@@ -1027,6 +1078,7 @@ typedef struct {
     int32_t depth;
     double* wind;
     uint64_t seed;
+    const double* obs_bias;
 } orc_dr;
 
 int orc_control_steps(const orc_params* P, int n_envs, const int32_t* env_off, const int32_t* env_flags,
@@ -1166,6 +1218,15 @@ int orc_control_steps(const orc_params* P, int n_envs, const int32_t* env_off, c
                         o[7 + r] += row[ORC_DR_NOISE_RPY] * xi[3 + r]; /* KIN 7-9: roll, pitch, yaw */
                         o[10 + r] += row[ORC_DR_NOISE_V] * xi[6 + r];  /* KIN 10-12: velocity */
                         o[13 + r] += row[ORC_DR_NOISE_W] * xi[9 + r];  /* KIN 13-15: body rate */
+                    }
+                    if (dr->obs_bias) {
+                        const double* bb = dr->obs_bias + 12 * g;
+                        for (int r = 0; r < 3; ++r) {
+                            o[r] += bb[r];
+                            o[7 + r] += bb[3 + r];
+                            o[10 + r] += bb[6 + r];
+                            o[13 + r] += bb[9 + r];
+                        }
                     }
                 }
                 if (nbr_idx && nbr_rel)

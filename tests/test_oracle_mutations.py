@@ -87,6 +87,13 @@ MUTATIONS = {
     "sensor_delay_ignored": ("const int delayed = row && x_last && K > 0 && row[ORC_DR_OBS_DELAY] == 1.0;",
                              "const int delayed = 0;"),
     "noise_rpy_channel": ("o[7 + r] += row[ORC_DR_NOISE_RPY] * xi[3 + r];", "o[3 + r] += row[ORC_DR_NOISE_RPY] * xi[3 + r];"),
+    "reset_xyz_euler_order": ("orc_quat_mul(qz, qy, qzy);", "orc_quat_mul(qy, qz, qzy);"),
+    "reset_full_angle": ("const double qx[4] = {cos(0.5 * roll), sin(0.5 * roll), 0.0, 0.0};",
+                         "const double qx[4] = {cos(roll), sin(roll), 0.0, 0.0};"),
+    "reset_velocity_range": ("x[7 + k] = r[2] * u[6 + k];", "x[7 + k] = r[2] * (0.5 + 0.5 * u[6 + k]);"),
+    "bias_sigma_group": ("b[2 * m] = sigma[(2 * m) / 3] * rho * cos(2.0 * ORC_PI * u2);",
+                         "b[2 * m] = sigma[m / 3] * rho * cos(2.0 * ORC_PI * u2);"),
+    "bias_rate_channel": ("o[13 + r] += bb[9 + r];", "o[13 + r] += bb[6 + r];"),
 }
 
 

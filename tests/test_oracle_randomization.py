@@ -322,3 +322,110 @@ def test_observation_noise_changes_with_the_step():
     r2 = oracle.Randomization(n, n, 1, seed=8)
     r2.env_dr[:, oracle.DR_NOISE_P] = 0.01
     np.testing.assert_array_equal(_obs_run(P, x0, rpm, r2)[3], k1)
+
+
+# ---- episode reset: the "init" row and the sticky observation bias (Section 3.5) ----
+
+INIT = (0.2, 0.1, 0.5)  # the table's init row: p0 m, RPY0 rad, v0 m/s
+NOMINAL = (1.0, -2.0, 1.5, 0.7)
+
+
+def _rot_zyx(roll, pitch, yaw):
+    cr, sr, cp, sp, cy, sy = np.cos(roll), np.sin(roll), np.cos(pitch), np.sin(pitch), np.cos(yaw), np.sin(yaw)
+    Rx = np.array([[1, 0, 0], [0, cr, -sr], [0, sr, cr]])
+    Ry = np.array([[cp, 0, sp], [0, 1, 0], [-sp, 0, cp]])
+    Rz = np.array([[cy, -sy, 0], [sy, cy, 0], [0, 0, 1]])
+    return Rz @ Ry @ Rx
+
+
+def test_reset_state_is_the_nominal_pose_plus_the_drawn_perturbation():
+    """Each component is nominal + r (2u - 1) of its own counter-based uniform (stream 23):
+    position and velocity directly, the attitude as the rotation Rz(yaw) Ry(pitch) Rx(roll)
+    of the perturbed angles (built here as matrices; the oracle composes quaternions), at
+    rest in rotation; the reset is a function of (seed, episode, drone) alone."""
+    for drone in (0, 5, 12345):
+        x = oracle.reset_state(NOMINAL, INIT, 9, 3, drone)
+        u = np.array([2 * oracle.uniform(9, 23, 3, drone, k) - 1 for k in range(9)])
+        np.testing.assert_allclose(x[0:3], np.array(NOMINAL[:3]) + INIT[0] * u[0:3], rtol=0, atol=1e-15)
+        np.testing.assert_allclose(x[7:10], INIT[2] * u[6:9], rtol=0, atol=1e-15)
+        assert np.all(x[10:13] == 0)
+        assert abs(np.linalg.norm(x[3:7]) - 1) < 1e-15
+        R = oracle.rotation(x[3:7])
+        np.testing.assert_allclose(R, _rot_zyx(INIT[1] * u[3], INIT[1] * u[4], NOMINAL[3] + INIT[1] * u[5]),
+                                   rtol=0, atol=1e-15)
+        np.testing.assert_allclose(oracle.rpy(x[3:7]), [INIT[1] * u[3], INIT[1] * u[4], NOMINAL[3] + INIT[1] * u[5]],
+                                   rtol=0, atol=1e-14)
+        assert np.array_equal(x, oracle.reset_state(NOMINAL, INIT, 9, 3, drone))
+        assert not np.array_equal(x, oracle.reset_state(NOMINAL, INIT, 9, 4, drone))
+        assert not np.array_equal(x, oracle.reset_state(NOMINAL, INIT, 10, 3, drone))
+
+
+def test_reset_state_uniform_moments():
+    """Over 20000 drones each perturbation is uniform on [-r, r]: inside the range, mean 0 and
+    variance r^2/3 within 4 standard errors, and the roll/pitch/yaw read back from the
+    quaternion follow the same law (yaw about its nominal value)."""
+    n = 20000
+    X = np.array([oracle.reset_state(NOMINAL, INIT, 1, 0, d) for d in range(n)])
+    rpy = np.array([oracle.rpy(q) for q in X[:, 3:7]]) - np.array([0.0, 0.0, NOMINAL[3]])
+    for vals, r in ((X[:, 0:3] - np.array(NOMINAL[:3]), INIT[0]), (rpy, INIT[1]), (X[:, 7:10], INIT[2])):
+        z = vals / r
+        assert np.all(np.abs(z) <= 1.0 + 1e-12)
+        assert np.all(np.abs(z.mean(axis=0)) < 4 * np.sqrt(1 / 3 / n))
+        # var of U[-1, 1] is 1/3; the variance of z^2 is 1/5 - 1/9
+        assert np.all(np.abs((z ** 2).mean(axis=0) - 1 / 3) < 4 * np.sqrt((1 / 5 - 1 / 9) / n))
+    # the nine components are drawn independently
+    C = np.corrcoef(np.concatenate([X[:, 0:3], rpy, X[:, 7:10]], 1).T)
+    assert np.max(np.abs(C - np.eye(9))) < 4 / np.sqrt(n)
+
+
+def test_obs_bias_gaussian_per_channel():
+    """b_k = sigma[k // 3] xi_k with xi standard normal (Box-Muller, stream 24): per channel
+    mean 0 and variance sigma^2 within 4 standard errors, a Kolmogorov-Smirnov test against
+    the normal law, uncorrelated channels; a zero sigma gives zero channels."""
+    from scipy import stats
+    n = 20000
+    sig = np.array([0.01, np.deg2rad(1.0), 0.05, 0.05])
+    B = np.array([oracle.obs_bias(sig, 4, 2, d) for d in range(n)])
+    Z = B / np.repeat(sig, 3)[None, :]
+    assert np.all(np.abs(Z.mean(axis=0)) < 4 / np.sqrt(n))
+    assert np.all(np.abs(Z.var(axis=0) - 1) < 4 * np.sqrt(2 / n))
+    for k in range(12):
+        assert stats.kstest(Z[:, k], "norm").pvalue > 1e-4
+    C = np.corrcoef(Z.T)
+    assert np.max(np.abs(C - np.eye(12))) < 4 / np.sqrt(n)
+    b = oracle.obs_bias([0.0, 1.0, 0.0, 0.0], 4, 2, 7)
+    assert np.all(b[0:3] == 0) and np.all(b[6:12] == 0) and np.all(b[3:6] != 0)
+    assert np.array_equal(oracle.obs_bias(sig, 4, 2, 7), oracle.obs_bias(sig, 4, 2, 7))
+    assert not np.array_equal(oracle.obs_bias(sig, 4, 2, 7), oracle.obs_bias(sig, 4, 3, 7))
+
+
+def test_obs_bias_is_sticky_on_the_noisy_kin_channels():
+    """With the sensor noise off, the KIN observation under a bias differs from the one
+    without by exactly the bias, on position, roll/pitch/yaw, velocity and body rate, at
+    every step of the episode (the same bias); quaternion and RPMs carry none; the state is
+    untouched."""
+    P = oracle.cf2x()
+    n = 6
+    x0 = np.array([oracle.reset_state(NOMINAL, INIT, 2, 0, d) for d in range(n)])
+    rpm = np.full((n, 4), oracle.hover_rpm(P))
+    bias = np.array([oracle.obs_bias([0.01, 0.02, 0.05, 0.05], 2, 0, d) for d in range(n)])
+    env_off = np.arange(n + 1, dtype=np.int32)
+    args = (P, env_off, np.zeros(n, np.int32), np.full(n, oracle.ACT_RPM, np.int32))
+    outs = []
+    for b in (None, bias):
+        r = oracle.Randomization(n, n, 1, 3)
+        r.obs_bias = b
+        x, integ, a = x0, np.zeros((n, 6)), np.zeros((n, 4))
+        ks = []
+        for _ in range(2):
+            x, integ, a, kin, _, _ = oracle.control_steps(*args, x, integ, a, rpm[None], 5, obs=True, dr=r)
+            ks.append((x.copy(), kin))
+        outs.append(ks)
+    for (xa, ka), (xb, kb) in zip(*outs):
+        assert np.array_equal(xa, xb)
+        d = kb - ka
+        np.testing.assert_allclose(d[:, 0:3], bias[:, 0:3], rtol=0, atol=1e-15)
+        np.testing.assert_allclose(d[:, 7:10], bias[:, 3:6], rtol=0, atol=1e-15)
+        np.testing.assert_allclose(d[:, 10:13], bias[:, 6:9], rtol=0, atol=1e-15)
+        np.testing.assert_allclose(d[:, 13:16], bias[:, 9:12], rtol=0, atol=1e-15)
+        assert np.all(d[:, 3:7] == 0) and np.all(d[:, 16:20] == 0)
