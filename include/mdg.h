@@ -273,6 +273,41 @@ int mdg_set_setpoints(mdg_handle h, float* setpoints);
 int mdg_set_randomization(mdg_handle h, const float* env_params, float* motor, float* action_hist,
                           int32_t hist_depth, float* wind_state, uint64_t seed);
 
+/* Episode reset under domain randomization (Section 3.5: the "init" row of Table
+ * "Recommended domain-randomization ranges", p0 +-0.2 m, RPY0 +-0.1 rad, v0 +-0.5 m/s, drawn
+ * at every reset like the rest of the table, and the "sticky per-episode bias on the
+ * observation" of its recommendation (iii), whose size is not printed). For every drone g,
+ * from the counter-based generator (SplitMix64 over seed, stream, episode, g, component):
+ *   p0   = nominal[g].xyz + init_range[0] (2u - 1) per axis
+ *   RPY0 = (0, 0, nominal[g].w) + init_range[1] (2u - 1) per angle, q0 the quaternion of
+ *          Rz(yaw) Ry(pitch) Rx(roll)
+ *   v0   = init_range[2] (2u - 1) per axis; body rate, PID integrals and last RPMs zero
+ * and, when obs_bias is given, obs_bias[g] = 12 Gaussian offsets N(0, bias_sigma[k / 3]^2)
+ * for the KIN channels position (k = 0-2), roll/pitch/yaw (3-5), velocity (6-8) and body rate
+ * (9-11), which mdg_set_obs_bias makes the observations carry for the episode.
+ *   state       device float32 [MDG_STATE_PLANES][n_drones][4], overwritten
+ *   nominal     device float32 [n_drones][4] = nominal x, y, z [m] and yaw [rad] (the
+ *               constructor's initial_xyzs / initial_rpys, Section 3.4.2)
+ *   init_range  host float [3] half-widths (position m, angles rad, velocity m/s), NULL = 0
+ *   bias_sigma  host float [4] (position m, angles rad, velocity m/s, body rate rad/s);
+ *               required when obs_bias is given
+ *   obs_bias    device float32 [n_drones][12] or NULL
+ *   seed, episode  the draws' keys: the same pair gives the same episode
+ * The randomization's own state (rotor speeds, action history, wind state) and the DSL
+ * setpoints are the caller's buffers, reset by the caller (their documented start values).
+ * Asynchronous on `stream`. Errors: MDG_ERR_ARG, MDG_ERR_CUDA. */
+int mdg_reset(mdg_handle h, float* state, const float* nominal, const float* init_range, const float* bias_sigma,
+              float* obs_bias, uint64_t seed, uint64_t episode, void* stream);
+
+/* Attach (or, with NULL, detach) a sticky per-episode observation bias, device float32
+ * [n_drones][12] as mdg_reset writes it, 16-byte aligned, caller-owned: every step and
+ * rollout under randomization adds it to the KIN observation's position, roll/pitch/yaw,
+ * velocity and body rate (on top of the sensor noise, delayed observations included).
+ * Requires the randomization to be attached (mdg_set_randomization; attaching it again
+ * keeps the bias, detaching it detaches the bias too). Synchronous with the legacy default
+ * stream, like mdg_set_randomization. Errors: MDG_ERR_ARG, MDG_ERR_CUDA. */
+int mdg_set_obs_bias(mdg_handle h, const float* obs_bias);
+
 /* Threads per block of the step kernels (a multiple of 32 in [32, 1024] and at least
  * the largest environment, rounded up to 32). Environments are packed whole into
  * blocks of at most this many drones. The default (chosen at creation) spreads the

@@ -100,6 +100,8 @@ _SIGNATURES = {
     "mdg_mlp_adam": ([_VP, ctypes.c_float, _VP], ctypes.c_int),
     "mdg_mlp_set_path": ([_VP, ctypes.c_int32], ctypes.c_int),
     "mdg_mlp_set_wait_limits": ([_VP, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "mdg_reset": ([_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_uint64, ctypes.c_uint64, _VP], ctypes.c_int),
+    "mdg_set_obs_bias": ([_VP, _VP], ctypes.c_int),
     "mdg_mlp_status": ([_VP, _VP, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
     "mdg_features": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "mdg_surrogate_step": ([_VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, _VP, _VP],
@@ -387,6 +389,29 @@ class Handle:
             _ptr(motor, "motor", torch.float32, (self.n, 4)),
             _ptr(action_hist, "action_hist", torch.float32, (depth, self.n, 4)), depth,
             _ptr(wind_state, "wind_state", torch.float32, (self.n_envs, WIND_STATE)), int(seed)))
+
+    def reset(self, state, nominal, init_range=None, bias_sigma=None, obs_bias=None, seed: int = 0,
+              episode: int = 0, stream=None):
+        """Episode reset with the init row of the randomization table (mdg_reset): state
+        [6, n, 4] overwritten from nominal [n, 4] (x, y, z, yaw) perturbed uniformly by
+        init_range (p m, angles rad, v m/s); obs_bias [n, 12] (optional) drawn with
+        bias_sigma (p, angles, v, body rate)."""
+        torch = _torch()
+        rng = None if init_range is None else (ctypes.c_float * 3)(*[float(v) for v in init_range])
+        sig = None if bias_sigma is None else (ctypes.c_float * 4)(*[float(v) for v in bias_sigma])
+        _check(lib().mdg_reset(self._h, _ptr(state, "state", torch.float32, (STATE_PLANES, self.n, 4)),
+                               _ptr(nominal, "nominal", torch.float32, (self.n, 4)),
+                               ctypes.cast(rng, _VP) if rng is not None else None,
+                               ctypes.cast(sig, _VP) if sig is not None else None,
+                               None if obs_bias is None else _ptr(obs_bias, "obs_bias", torch.float32, (self.n, 12)),
+                               int(seed), int(episode), _stream(stream)))
+
+    def set_obs_bias(self, obs_bias):
+        """Attach (None: detach) the sticky observation bias [n, 12] (mdg_set_obs_bias)."""
+        torch = _torch()
+        self._bias_keep = obs_bias
+        _check(lib().mdg_set_obs_bias(self._h, None if obs_bias is None else
+                                      _ptr(obs_bias, "obs_bias", torch.float32, (self.n, 12))))
 
     def set_block_size(self, threads_per_block: int):
         _check(lib().mdg_set_block_size(self._h, int(threads_per_block)))

@@ -653,6 +653,7 @@ int mdg_set_randomization(mdg_handle h, const float* env_params, float* motor, f
     if (!h) return fail(MDG_ERR_ARG, "mdg_set_randomization: NULL handle");
     if (!env_params) {
         h->dr = nullptr;
+        h->rand_host.obs_bias = nullptr;
         return MDG_OK;
     }
     if (h->dc.rk4) return fail(MDG_ERR_UNSUPPORTED, "mdg_set_randomization: randomization integrates with Euler substeps");
@@ -694,12 +695,69 @@ int mdg_set_randomization(mdg_handle h, const float* env_params, float* motor, f
     ra.wind = reinterpret_cast<float4*>(wind_state);
     ra.seed = seed;
     ra.depth = hist_depth;
+    ra.obs_bias = h->dr ? h->rand_host.obs_bias : nullptr;  // an attached bias stays attached
     DeviceGuard dg(h->device);
     cudaError_t e = cudaSuccess;
     if (!h->d_rand) e = cudaMalloc(reinterpret_cast<void**>(&h->d_rand), sizeof(mdg::RandArgs));
     if (e == cudaSuccess) e = cudaMemcpy(h->d_rand, &ra, sizeof(ra), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "mdg_set_randomization: device copy of the buffers");
     h->dr = env_params;
+    h->rand_host = ra;
+    return MDG_OK;
+}
+
+int mdg_set_obs_bias(mdg_handle h, const float* obs_bias)
+{
+    if (!h) return fail(MDG_ERR_ARG, "mdg_set_obs_bias: NULL handle");
+    if (!h->dr) return fail(MDG_ERR_ARG, "mdg_set_obs_bias: attach the randomization first (mdg_set_randomization)");
+    if (obs_bias && !aligned16(obs_bias)) return fail(MDG_ERR_ARG, "mdg_set_obs_bias: obs_bias is not 16-byte aligned");
+    mdg::RandArgs ra = h->rand_host;
+    ra.obs_bias = reinterpret_cast<const float4*>(obs_bias);
+    DeviceGuard dg(h->device);
+    // the device copy is read by kernels already queued: replace it in stream order on the
+    // legacy default stream, as mdg_set_randomization does
+    const cudaError_t e = cudaMemcpy(h->d_rand, &ra, sizeof(ra), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "mdg_set_obs_bias: device copy of the buffers");
+    h->rand_host = ra;
+    return MDG_OK;
+}
+
+int mdg_reset(mdg_handle h, float* state, const float* nominal, const float* init_range, const float* bias_sigma,
+              float* obs_bias, uint64_t seed, uint64_t episode, void* stream)
+{
+    if (!h) return fail(MDG_ERR_ARG, "mdg_reset: NULL handle");
+    int rc;
+    if ((rc = check_state_ptr(h, state, "state")) != MDG_OK) return rc;
+    if ((rc = check_state_ptr(h, nominal, "nominal")) != MDG_OK) return rc;
+    if (obs_bias && !aligned16(obs_bias)) return fail(MDG_ERR_ARG, "mdg_reset: obs_bias is not 16-byte aligned");
+    if (obs_bias && !bias_sigma) return fail(MDG_ERR_ARG, "mdg_reset: obs_bias needs bias_sigma");
+    mdg::ResetArgs r{};
+    r.state = reinterpret_cast<float4*>(state);
+    r.nominal = reinterpret_cast<const float4*>(nominal);
+    r.obs_bias = reinterpret_cast<float4*>(obs_bias);
+    r.n = h->n_drones;
+    if (init_range) {
+        for (int k = 0; k < 3; ++k)
+            if (!(init_range[k] >= 0.f) || !isfinite(init_range[k]))
+                return fail(MDG_ERR_ARG, "mdg_reset: init_range[%d] = %g must be finite and >= 0", k,
+                            (double)init_range[k]);
+        r.range_pos = init_range[0];
+        r.range_att = init_range[1];
+        r.range_vel = init_range[2];
+    }
+    if (obs_bias)
+        for (int k = 0; k < 4; ++k) {
+            if (!(bias_sigma[k] >= 0.f) || !isfinite(bias_sigma[k]))
+                return fail(MDG_ERR_ARG, "mdg_reset: bias_sigma[%d] = %g must be finite and >= 0", k,
+                            (double)bias_sigma[k]);
+            r.sigma[k] = bias_sigma[k];
+        }
+    r.seed = seed;
+    r.episode = episode;
+    if (r.n == 0) return MDG_OK;
+    DeviceGuard dg(h->device);
+    const cudaError_t e = mdg::launch_reset(r, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mdg_reset: launch");
     return MDG_OK;
 }
 

@@ -63,6 +63,18 @@ struct RandArgs {
     float4* wind;             // [n_envs][2] wind state
     unsigned long long seed;  // of the wind draws
     int depth;
+    const float4* obs_bias;   // [n][3] sticky per-episode observation bias (12 floats per drone), or null
+};
+
+// Episode reset (mdg_reset): the init row of the randomization table and the observation bias.
+struct ResetArgs {
+    float4* state;            // [6][n]
+    const float4* nominal;    // [n] x, y, z, yaw
+    float4* obs_bias;         // [n][3] or null
+    long long n;
+    float range_pos, range_att, range_vel;
+    float sigma[4];           // bias sigmas: position, roll/pitch/yaw, velocity, body rate
+    unsigned long long seed, episode;
 };
 
 struct StepArgs {
@@ -207,6 +219,7 @@ cudaError_t mlp_forward_umma(const MlpView& w, const void* img, const void* x, i
                              int wait_limit, int spin_limit, cudaStream_t s);
 
 cudaError_t launch_obs(const StepArgs& a, int n_tiles, int block, cudaStream_t s);
+cudaError_t launch_reset(const ResetArgs& r, cudaStream_t s);
 cudaError_t launch_pid(const PidArgs& a, cudaStream_t s);
 
 }  // namespace mdg
@@ -231,6 +244,7 @@ struct mdg_ctx {
     // caller-owned domain randomization (mdg_set_randomization); dr == nullptr: none
     const float* dr = nullptr;
     mdg::RandArgs* d_rand = nullptr;  // device copy of the buffers (allocated on first attach)
+    mdg::RandArgs rand_host = {};     // what d_rand holds (valid while dr != nullptr)
     mdg::Tile* d_tiles = nullptr;
     int n_tiles = 0;
     int block = 0;

@@ -959,9 +959,12 @@ constexpr unsigned long long kStreamObs = 22;  // random stream of the observati
 
 // The KIN observation of d (RPMs a4) with the row's sensor noise: Gaussian (Box-Muller on the
 // counters (seed, kStreamObs, step, drone, 0..11)) of the row's sigmas on the position (0-2),
-// roll/pitch/yaw (3-5), velocity (6-8) and body rate (9-11); stored at kin_row[0..19].
+// roll/pitch/yaw (3-5), velocity (6-8) and body rate (9-11), plus the drone's sticky
+// per-episode bias on the same channels when obs_bias ([n][12] as three float4) is given;
+// stored at kin_row[0..19].
 __device__ __forceinline__ void noisy_kin(float* kin_row, const Drone& d, const float a4[4], const float* row,
-                                          unsigned long long seed, unsigned long long step, long long g)
+                                          unsigned long long seed, unsigned long long step, long long g,
+                                          const float4* obs_bias)
 {
     float4 v[5];
     kin_values(d, a4, v);
@@ -993,9 +996,81 @@ __device__ __forceinline__ void noisy_kin(float* kin_row, const Drone& d, const 
         v[3].z += sw * xi[10];
         v[3].w += sw * xi[11];
     }
+    if (obs_bias) {  // [p (3), rpy (3), v (3), w (3)] as (p.xyz, roll) (pitch, yaw, v.xy) (v.z, w.xyz)
+        const float4 b0 = obs_bias[3 * g], b1 = obs_bias[3 * g + 1], b2 = obs_bias[3 * g + 2];
+        v[0].x += b0.x;
+        v[0].y += b0.y;
+        v[0].z += b0.z;
+        v[1].w += b0.w;
+        v[2].x += b1.x;
+        v[2].y += b1.y;
+        v[2].z += b1.z;
+        v[2].w += b1.w;
+        v[3].x += b2.x;
+        v[3].y += b2.y;
+        v[3].z += b2.z;
+        v[3].w += b2.w;
+    }
     float4* o = reinterpret_cast<float4*>(kin_row);
 #pragma unroll
     for (int k = 0; k < 5; ++k) o[k] = v[k];
+}
+
+constexpr unsigned long long kStreamInit = 23;  // random stream of the per-episode initial states
+constexpr unsigned long long kStreamBias = 24;  // random stream of the per-episode observation bias
+
+// Episode reset (Section 3.5: the "init" row of Table "Recommended domain-randomization
+// ranges" and the sticky per-episode observation bias of its recommendation (iii)), one thread
+// per drone g: uniforms u_k = U(seed, kStreamInit, episode, g, k),
+//   p0 = nominal.xyz + r_p (2 u_0..2 - 1), (roll, pitch, yaw)0 = (0, 0, nominal.w) + r_a (2 u_3..5 - 1),
+//   q0 = the quaternion of Rz(yaw) Ry(pitch) Rx(roll), v0 = r_v (2 u_6..8 - 1), w0 = 0,
+// integrals and the last RPMs zero; with a bias buffer, b_k = sigma[k / 3] xi_k by Box-Muller on
+// U(seed, kStreamBias, episode, g, 2m) and (.., 2m + 1), k = 0..11.
+__global__ void __launch_bounds__(256) reset_kernel(const ResetArgs r)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= r.n) return;
+    const unsigned long long key = counter_prefix(r.seed, kStreamInit, r.episode, (unsigned long long)g);
+    float u[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) u[k] = 2.f * prefix_uniform(key, k) - 1.f;
+    const float4 nom = r.nominal[g];
+    const float roll = r.range_att * u[3], pitch = r.range_att * u[4], yaw = nom.w + r.range_att * u[5];
+    float sr, cr, sp, cp, sy, cy;  // of the half angles (once per episode: the accurate sincosf)
+    sincosf(0.5f * roll, &sr, &cr);
+    sincosf(0.5f * pitch, &sp, &cp);
+    sincosf(0.5f * yaw, &sy, &cy);
+    const float qw = cr * cp * cy + sr * sp * sy;
+    const float qx = sr * cp * cy - cr * sp * sy;
+    const float qy = cr * sp * cy + sr * cp * sy;
+    const float qz = cr * cp * sy - sr * sp * cy;
+    const float px = nom.x + r.range_pos * u[0], py = nom.y + r.range_pos * u[1], pz = nom.z + r.range_pos * u[2];
+    const float vx = r.range_vel * u[6], vy = r.range_vel * u[7], vz = r.range_vel * u[8];
+    float4* S = r.state;
+    S[g] = make_float4(px, py, pz, qw);
+    S[r.n + g] = make_float4(qx, qy, qz, vx);
+    S[2 * r.n + g] = make_float4(vy, vz, 0.f, 0.f);
+    S[3 * r.n + g] = make_float4(0.f, 0.f, 0.f, 0.f);
+    S[4 * r.n + g] = make_float4(0.f, 0.f, 0.f, 0.f);
+    S[5 * r.n + g] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r.obs_bias) {
+        const unsigned long long bkey = counter_prefix(r.seed, kStreamBias, r.episode, (unsigned long long)g);
+        float b[12];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+            const float u1 = 1.f - prefix_uniform(bkey, 2 * m);
+            const float u2 = prefix_uniform(bkey, 2 * m + 1);
+            const float rho = sqrtf(-2.f * logf(u1));
+            float sn, cs;
+            sincospif(2.f * u2, &sn, &cs);  // sin and cos of 2 pi u2
+            b[2 * m] = r.sigma[(2 * m) / 3] * rho * cs;
+            b[2 * m + 1] = r.sigma[(2 * m + 1) / 3] * rho * sn;
+        }
+        float4* o = r.obs_bias + 3 * g;
+        o[0] = make_float4(b[0], b[1], b[2], b[3]);
+        o[1] = make_float4(b[4], b[5], b[6], b[7]);
+        o[2] = make_float4(b[8], b[9], b[10], b[11]);
+    }
 }
 
 // The substeps of one control step under randomization, called by every thread of the
@@ -1029,7 +1104,7 @@ __device__ __forceinline__ void randomized_substeps(const StepArgs& a, Drone& d,
         s1 = R.wind[2LL * env.id + 1];
         step = (unsigned long long)s1.w;
         delayed = row[MDG_DR_OBS_DELAY] == 1.f;
-        if (kin_row && delayed) noisy_kin(kin_row, d, a_pre, row, R.seed, step, g);
+        if (kin_row && delayed) noisy_kin(kin_row, d, a_pre, row, R.seed, step, g, R.obs_bias);
         float Fd[3], vw[3];
         wind_step(row, s0, s1, R.seed, env.id, a.c.dt_ctrl, Fd, vw);
         const int model = (int)row[MDG_DR_WIND];
@@ -1308,7 +1383,7 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
             if constexpr (kFlags == kFlagsDR) {  // sensor noise; delayed ones were written at the start
                 if (!delayed)
                     noisy_kin(a.kin + 20 * g, d, rpm, a.rand->dr + (long long)env.id * MDG_DR_PARAMS, a.rand->seed,
-                              obs_step, g);
+                              obs_step, g, a.rand->obs_bias);
             }
             write_knn<kN>(a.nbr_idx, a.nbr_rel, g, tile.first_drone + env.ls, t - env.ls, d, pb + env.ls,
                           s_vel + env.ls, env.N);
@@ -1500,7 +1575,7 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
                     if constexpr (kFlags == kFlagsDR) {  // sensor noise; delayed ones were written at the start
                         if (!delayed)
                             noisy_kin(a.kin + 20 * (o + g), d, rpm, a.rand->dr + (long long)env.id * MDG_DR_PARAMS,
-                                      a.rand->seed, obs_step, g);
+                                      a.rand->seed, obs_step, g, a.rand->obs_bias);
                     } else {
                         rpy_of(d.q, rpy_c[0], rpy_c[1], rpy_c[2]);
                         have_rpy = true;
@@ -1979,6 +2054,13 @@ cudaError_t launch_surrogate_prepare(const SurrogateArgs& a, int n_tiles, int bl
         cudaFuncSetAttribute(surrogate_prepare_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     surrogate_prepare_kernel<<<n_tiles, block, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset(const ResetArgs& r, cudaStream_t s)
+{
+    if (r.n == 0) return cudaSuccess;
+    reset_kernel<<<(unsigned)((r.n + 255) / 256), 256, 0, s>>>(r);
     return cudaGetLastError();
 }
 

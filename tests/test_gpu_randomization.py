@@ -55,12 +55,14 @@ def check_gust_phases(wg, wo, what):
     return split
 
 
-def _oracle_state(table, motor, hist, wind):
+def _oracle_state(table, motor, hist, wind, bias=None):
     r = oracle.Randomization(table.shape[0], motor.shape[0], hist.shape[0], SEED)
     r.env_dr[:] = table.astype(np.float64)
     r.motor[:] = motor.cpu().numpy().astype(np.float64)
     r.hist[:] = hist.cpu().numpy().astype(np.float64)
     r.wind[:] = wind.cpu().numpy().astype(np.float64)
+    if bias is not None:
+        r.obs_bias = np.ascontiguousarray(bias.cpu().numpy().astype(np.float64))
     return r
 
 
@@ -82,7 +84,21 @@ def _copy(r):
     c = oracle.Randomization(r.env_dr.shape[0], r.motor.shape[0], r.hist.shape[0], r.seed)
     for k in ("env_dr", "motor", "hist", "wind"):
         getattr(c, k)[:] = getattr(r, k)
+    c.obs_bias = r.obs_bias
     return c
+
+
+INIT = (0.2, 0.1, 0.5)  # the init row of the randomization table
+BIAS_SIGMA = (0.01, float(np.deg2rad(1.0)), 0.05, 0.05)
+
+
+def _bias(h, sw, cuda, episode=0):
+    """A sticky observation bias drawn by mdg_reset (into a scratch state)."""
+    scratch = torch.zeros((mdg.STATE_PLANES, sw.n, 4), device=cuda)
+    nominal = torch.zeros((sw.n, 4), device=cuda)
+    bias = torch.empty((sw.n, 12), device=cuda)
+    h.reset(scratch, nominal, None, BIAS_SIGMA, bias, seed=SEED, episode=episode)
+    return bias
 
 
 def _setup(cuda, recipe):
@@ -100,18 +116,20 @@ def _setup(cuda, recipe):
     h.set_action_types(types)
     motor, hist, wind = h.new_randomization_state(DEPTH, cuda)
     h.set_randomization(torch.as_tensor(table, device=cuda), motor, hist, wind, seed=SEED)
-    return sw, types, table, h, motor, hist, wind
+    bias = _bias(h, sw, cuda)
+    h.set_obs_bias(bias)
+    return sw, types, table, h, motor, hist, wind, bias
 
 
 @pytest.mark.parametrize("recipe", ["full_aero", "mixed", "single"])
 def test_randomized_control_steps(cuda, recipe):
-    sw, types, table, h, motor, hist, wind = _setup(cuda, recipe)
+    sw, types, table, h, motor, hist, wind, bias = _setup(cuda, recipe)
     state = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=cuda)
     kin, idx, rel = h.new_obs(cuda)
     for k in range(4):
         action = wl.typed_actions(sw.drones_per_env, types, 96, k, HOVER, P.mass * P.g)
         x0, i0, a0 = oracle_arrays(state)
-        r = _oracle_state(table, motor, hist, wind)
+        r = _oracle_state(table, motor, hist, wind, bias)
         r2 = _copy(r)
         h.step_obs(state, torch.as_tensor(action, device=cuda), mdg.ACT_MIXED, 5, kin, idx, rel)
         torch.cuda.synchronize()
@@ -140,19 +158,19 @@ def test_randomized_control_steps(cuda, recipe):
         ok = ~delayed
         assert excess(kg[ok][:, 0:3], ko[ok][:, 0:3], 5 * 1e-5) <= 1.0, f"{what}: KIN position"
         assert np.max(np.abs(kg[:, 16:20] - ko[:, 16:20])) <= 1e-2, f"{what}: KIN RPMs"
-        noise = kg[ok][:, 0:3] - xg[ok][:, 0:3]  # the position noise the GPU added
+        noise = kg[ok][:, 0:3] - xg[ok][:, 0:3] - bias.cpu().numpy()[ok][:, 0:3]  # the position noise the GPU added
         assert np.all(np.abs(noise) < 0.08) and np.std(noise) > 0.005, f"{what}: position noise"
     assert (wind[:, 3] >= 0).any(), "no gust was active during the test"
     assert h.status()[0] == mdg.OK
 
 
 def test_randomized_rollout(cuda):
-    sw, types, table, h, motor, hist, wind = _setup(cuda, "full_aero")
+    sw, types, table, h, motor, hist, wind, bias = _setup(cuda, "full_aero")
     K = 4
     state = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=cuda)
     actions = np.stack([wl.typed_actions(sw.drones_per_env, types, 97, k, HOVER, P.mass * P.g) for k in range(K)])
     x0, i0, a0 = oracle_arrays(state)
-    r = _oracle_state(table, motor, hist, wind)
+    r = _oracle_state(table, motor, hist, wind, bias)
     r2 = _copy(r)
     h.rollout(state, torch.as_tensor(actions, device=cuda), mdg.ACT_MIXED, 5, K)
     torch.cuda.synchronize()
@@ -197,3 +215,44 @@ def test_randomization_arguments(cuda):
     with pytest.raises(mdg.MdgError) as e:
         h4.set_randomization(torch.as_tensor(good, device=cuda), motor, hist, wind)
     assert e.value.code == mdg.ERR_UNSUPPORTED
+
+
+def test_reset_matches_oracle(cuda):
+    """mdg_reset against orc_reset_state / orc_obs_bias drone by drone: the drawn initial
+    position, attitude and velocity (the init row of the randomization table) and the sticky
+    bias, float32 against FP64 rounding; body rates, integrals and last RPMs zero; another
+    episode draws another state, the same one the same state."""
+    sw = wl.full_aero(98, n_envs=512)
+    h = mdg.Handle(sw.drones_per_env, sw.flags)
+    yaw = wl.uniform_range(-3.0, 3.0, 98, 40, 0, np.arange(sw.n, dtype=np.uint64), 0)
+    nominal = np.concatenate([sw.p, yaw[:, None]], 1).astype(np.float32)
+    state = torch.full((mdg.STATE_PLANES, sw.n, 4), float("nan"), device=cuda)
+    bias = torch.empty((sw.n, 12), device=cuda)
+    h.reset(state, torch.as_tensor(nominal, device=cuda), INIT, BIAS_SIGMA, bias, seed=SEED, episode=7)
+    torch.cuda.synchronize()
+    x, integ, a_prev = oracle_arrays(state)
+    b = bias.cpu().numpy().astype(np.float64)
+    xo = np.array([oracle.reset_state(nominal[g].astype(np.float64), INIT, SEED, 7, g) for g in range(sw.n)])
+    bo = np.array([oracle.obs_bias(BIAS_SIGMA, SEED, 7, g) for g in range(sw.n)])
+    np.testing.assert_allclose(x[:, 0:3], xo[:, 0:3], rtol=0, atol=1e-6)
+    np.testing.assert_allclose(x[:, 3:7], xo[:, 3:7], rtol=0, atol=2e-6)
+    np.testing.assert_allclose(x[:, 7:10], xo[:, 7:10], rtol=0, atol=1e-6)
+    assert np.all(x[:, 10:13] == 0) and np.all(integ == 0) and np.all(a_prev == 0)
+    np.testing.assert_allclose(b, bo, rtol=1e-5, atol=1e-7)
+    again = torch.empty_like(state)
+    h.reset(again, torch.as_tensor(nominal, device=cuda), INIT, None, None, seed=SEED, episode=7)
+    other = torch.empty_like(state)
+    h.reset(other, torch.as_tensor(nominal, device=cuda), INIT, None, None, seed=SEED, episode=8)
+    torch.cuda.synchronize()
+    assert torch.equal(again, state) and not torch.equal(other, state)
+    with pytest.raises(mdg.MdgError):
+        h.reset(state, torch.as_tensor(nominal, device=cuda), (0.2, -0.1, 0.5))
+    with pytest.raises(mdg.MdgError):
+        h.reset(state, torch.as_tensor(nominal, device=cuda), INIT, None, bias)
+
+
+def test_obs_bias_needs_randomization(cuda):
+    sw = wl.full_aero(99, n_envs=8)
+    h = mdg.Handle(sw.drones_per_env, sw.flags)
+    with pytest.raises(mdg.MdgError):
+        h.set_obs_bias(torch.zeros((sw.n, 12), device=cuda))
