@@ -158,8 +158,9 @@ def measured_peaks() -> dict:
     if os.path.exists(p):
         with open(p) as f:
             d = json.load(f)
-        return {"hbm_gbs": d["hbm_gbs"], "src": "measured"}
-    return {"hbm_gbs": 6800.0, "src": "fallback"}
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d.get("bf16_tflops", 1900.0),
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained", 1700.0), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "src": "fallback"}
 
 
 class ClockSampler:
@@ -872,6 +873,125 @@ def run_surrogate(args) -> None:
     print(json.dumps(out))
 
 
+def run_surrogate_dense(args) -> None:
+    """The learned surrogate on the dense swarm (1024 envs x 64 drones, all effects, the dense
+    workload's RPM actions): trained on ~10.5M transitions of the plain integrator on fresh
+    draws of the same workload (episodes of 40 control steps), with the integrator chosen by
+    --integrator (Euler, or RK4 as the MuJoCo modes integrate), then one control step of the
+    benchmark swarm with the surrogate against the plain step of the same integrator (both
+    without observations, L2 flushed between steps). Metric: drone-control-steps/s of the
+    surrogate step, with the plain step's figure, the one-step state error of the surrogate
+    against the plain integrator on the regular regime, and the out-of-distribution fraction."""
+    import torch
+    import paper_2606_08039_gb300 as mdg
+    from paper_2606_08039_gb300 import surrogate as sg
+    from paper_2606_08039_gb300 import workloads as wl
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    c = library_constants(args)
+    hover = c.hover_rpm()
+    t0 = time.perf_counter()
+    steps_gen, episode = 160, 40
+    raw, delta = sg.generate_transitions(1024, steps_gen, seed=31, device=dev, workload="dense", constants=c,
+                                         episode=episode)
+    data = sg.Dataset(raw, delta)
+    del raw, delta
+    sw = wl.dense(5)
+    m = mdg.MLP(sw.n, wl.mlp_init(3))
+    data.attach(m)
+    hist = sg.fit(m, data, epochs=4, batch=8192, lr=2e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    n_train, kept, out_std, out_mean = len(data), data.kept_fraction, data.out_std, data.out_mean
+    del data
+
+    h = mdg.Handle(sw.drones_per_env, sw.flags, c)
+    init = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=dev)
+    act = torch.as_tensor(wl.rpm_actions(5, sw.n, 0, hover), device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    sink = torch.empty((), dtype=torch.float32, device=dev)
+
+    def timed(fn, n, state):
+        st = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+        en = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+        for i in range(n):
+            state.copy_(init)
+            flush.fill_(1.0)
+            torch.sum(flush, dim=0, out=sink)
+            st[i].record(stream)
+            fn()
+            en[i].record(stream)
+        torch.cuda.synchronize()
+        return float(sum(a.elapsed_time(b) for a, b in zip(st, en))) / n
+
+    steps = min(args.steps, 500)
+    s_sur, s_pln = init.clone(), init.clone()
+    nfb = torch.zeros(1, dtype=torch.int32, device=dev)
+    sur = lambda: m.step(h, s_sur, act, mdg.ACT_RPM, N_SUB, 4.0, nfb, stream=stream)
+    pln = lambda: h.step(s_pln, act, mdg.ACT_RPM, N_SUB, stream=stream)
+    timed(sur, args.warmup, s_sur)
+    timed(pln, args.warmup, s_pln)
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    ms_sur = timed(sur, steps, s_sur)
+    ms_pln = timed(pln, steps, s_pln)
+    clk = clocks.stop()
+    x = torch.empty((sw.n, mdg.MLP_IN_PAD), dtype=torch.bfloat16, device=dev)
+    x.copy_(torch.randn_like(x, dtype=torch.float32).to(torch.bfloat16))
+    y = torch.empty((sw.n, mdg.MLP_OUT_PAD), device=dev)
+    ms_net = timed(lambda: m.forward(x, y, stream=stream), steps, s_sur)
+    flops = 2.0 * sw.n * (64 * 256 + 2 * 256 * 256 + 256 * 32)
+    # one-step accuracy from the benchmark swarm's initial state
+    s_sur.copy_(init)
+    s_pln.copy_(init)
+    before = sg.state13(init).clone()
+    sur()
+    pln()
+    torch.cuda.synchronize()
+    xs, xp = sg.state13(s_sur), sg.state13(s_pln)
+    true_d = xp - before
+    zt = (true_d - out_mean) / out_std
+    N = int(sw.drones_per_env[0])
+    fb_env = ((xs - xp).abs().max(1).values.view(-1, N) == 0).all(1).repeat_interleave(N)
+    regular = (zt.abs() <= 8).all(1) & ~fb_env
+    err = {}
+    for name, sl in (("position", slice(0, 3)), ("quaternion", slice(3, 7)), ("velocity", slice(7, 10)),
+                     ("body_rate", slice(10, 13))):
+        e = float((xs[regular, sl] - xp[regular, sl]).pow(2).mean().sqrt())
+        b = float(true_d[regular, sl].pow(2).mean().sqrt())
+        err[name] = {"rms_error": e, "rms_change": b, "ratio_vs_no_network": e / b if b > 0 else None}
+    peaks = measured_peaks()
+    ach = flops / (ms_net * 1e-3) / 1e12
+    out = {
+        "metric": "surrogate speedup at stated error: drone-control-steps/s of the surrogate step",
+        "value": sw.n / (ms_sur * 1e-3), "unit": "drone-control-steps/s", "n_gpus": 1, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms_sur, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": f"surrogate on the dense swarm: 1024 envs x 64 drones, all effects, RPM actions, one "
+                               f"control step ({args.integrator} substeps in the plain step and the fallback); network "
+                               "41-256-256-256-13 SiLU, bf16/FP32 accumulation, fused tcgen05 kernel",
+                   "l2": "flushed between timed steps (512 MiB written, then read back)",
+                   "training": {"transitions_generated": 1024 * 64 * steps_gen, "transitions_kept": n_train,
+                                "kept_fraction": kept, "episode_steps": episode, "epochs": 4, "batch": 8192,
+                                "seconds": train_s, "loss_per_epoch": hist},
+                   **model_config(args)},
+        "plain_integrator": {"value": sw.n / (ms_pln * 1e-3), "ms_per_step": ms_pln,
+                             "integrator": args.integrator},
+        "speedup_vs_plain": ms_pln / ms_sur,
+        "one_step_error_vs_plain": err, "regular_fraction": float(regular.float().mean()),
+        "ood_env_fraction": int(nfb) / sw.n_envs,
+        "gpu_launches": 5 * steps,
+        "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                     "frac": ach / peaks["bf16_tflops"], "traffic": None, "peak_src": peaks["src"],
+                     "kernel": "mlp_umma_kernel", "ms": ms_net, "algorithmic_flops_per_launch": flops},
+        "clocks": clk,
+    }
+    print(json.dumps(out))
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -881,7 +1001,8 @@ def main() -> None:
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="full_aero",
-                    choices=["full_aero", "uneven", "dense", "single", "surrogate", "mlp", "camera"],
+                    choices=["full_aero", "uneven", "dense", "single", "surrogate", "surrogate_dense", "mlp",
+                             "camera"],
                     help="full_aero (default, the headline line); the others measure the other swarms")
     ap.add_argument("--model", default="cf2x", choices=["cf2x", "cf2p", "race"])
     ap.add_argument("--integrator", default="euler", choices=["euler", "rk4"])
@@ -906,6 +1027,9 @@ def main() -> None:
         ap.error("--randomize integrates with Euler substeps")
     if args.workload == "surrogate":
         run_surrogate(args)
+        return
+    if args.workload == "surrogate_dense":
+        run_surrogate_dense(args)
         return
     if args.workload == "mlp":
         run_mlp(args)

@@ -578,12 +578,13 @@ int mdg_mlp_status(mdg_mlp m, void* stream, uint32_t* bits);
  * [n_drones][4] are the RPMs to be applied. */
 int mdg_features(mdg_handle h, const float* state, const float* rpm, float* raw, void* stream);
 
-/* One control step with the surrogate in place of the substep loop (uniform batches of
- * at most 32 drones per environment, n_drones <= the surrogate's max_batch): the action
+/* One control step with the surrogate in place of the substep loop (uniform batches: every
+ * environment of one size; n_drones <= the surrogate's max_batch): the action
  * becomes RPMs as in mdg_step (PID integrals and plane 5 updated), the inputs are
  * standardised, the network predicts the state change, q is renormalised. An environment
  * any of whose drones has a standardised input beyond +-ood_z or a raw input outside the
- * normalisation box takes the plain integrator instead (n_substeps substeps).
+ * normalisation box takes the plain integrator instead (n_substeps substeps of the handle's
+ * integrator, Euler or RK4, with the handle's physics).
  * n_fallback: device int32 or NULL, receives the number of such environments. */
 int mdg_surrogate_step(mdg_handle h, mdg_mlp m, float* state, const float* action, int32_t action_type,
                        int32_t n_substeps, float ood_z, int32_t* n_fallback, void* stream);

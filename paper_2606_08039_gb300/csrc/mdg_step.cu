@@ -1863,6 +1863,57 @@ __global__ void __launch_bounds__(128) surrogate_fallback_kernel(const Surrogate
     }
 }
 
+// The plain integrator for the flagged environments of larger size or with Runge-Kutta
+// substeps: one block per listed environment (blockDim = N rounded up to 32), the RPMs the
+// prepare step stored in plane 5, n_sub substeps with the block's position snapshot.
+template <bool kRK4>
+__global__ void __launch_bounds__(1024) surrogate_fallback_block_kernel(const SurrogateArgs sa)
+{
+    extern __shared__ float4 smem[];
+    float4* s_pos = smem;  // [2][B]
+    const StepArgs& a = sa.s;
+    const int t = threadIdx.x, B = blockDim.x;
+    const int count = *sa.fallback_count;
+    for (int item = blockIdx.x; item < count; item += gridDim.x) {
+        const int e = sa.fallback_list[item];
+        if (!MDG_CHECK(e >= 0 && e < a.n_envs && a.uniform_N <= B, a.status)) continue;
+        const int N = a.uniform_N;
+        const bool active = t < N;
+        const long long g = (long long)e * N + t;
+        Drone d = {};
+        float rpm[4] = {0.f, 0.f, 0.f, 0.f};
+        if (active) {
+            load_state(a.state, a.n, g, d, false);
+            const float4 r = a.state[5 * a.n + g];
+            rpm[0] = r.x; rpm[1] = r.y; rpm[2] = r.z; rpm[3] = r.w;
+        }
+        EnvSlot env = {0, N, (int)a.env_flags[e], 0, e};
+        const Motor m = motor(rpm, a.c);
+        const bool dw = (env.flags & MDG_DW) != 0;
+        int ph = 0;
+        if constexpr (kRK4) {
+            rk4_substeps<kFlagsRK4, -1>(d, m, env, s_pos, B, t, active, dw, false, a.n_sub, ph, a.c);
+        } else {
+            for (int s = 0; s < a.n_sub; ++s, ++ph) {
+                float4* buf = s_pos + (ph & 1) * B;
+                if (dw) {
+                    buf[t] = make_float4(d.p[0], d.p[1], d.p[2], 0.f);
+                    __syncthreads();
+                }
+                if (active) substep<kFlagsGndRotor, -1>(d, m, env.flags, buf, N, t, a.c);
+            }
+        }
+        if (active) {
+            store_state(a.state, a.n, g, d, false);
+            if (!finite_state(d)) {
+                atomicOr(a.status, MDG_STATUS_NONFINITE);
+                atomicMin(a.status + 1, (unsigned)g);
+            }
+        }
+        __syncthreads();  // the snapshot is rewritten for the next environment
+    }
+}
+
 __global__ void __launch_bounds__(256) pid_kernel(const PidArgs a)
 {
     for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < a.n;
@@ -2076,9 +2127,19 @@ cudaError_t launch_surrogate_apply(const SurrogateArgs& a, cudaStream_t s)
 cudaError_t launch_surrogate_fallback(const SurrogateArgs& a, cudaStream_t s)
 {
     if (a.s.n == 0) return cudaSuccess;
-    int blocks = (a.s.n_envs + 3) / 4;
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    surrogate_fallback_kernel<<<blocks, 128, 0, s>>>(a);
+    const int N = a.s.uniform_N;
+    if (N <= 32 && !a.s.c.rk4) {  // one warp per environment
+        int blocks = (a.s.n_envs + 3) / 4;
+        if (blocks > 152 * 8) blocks = 152 * 8;
+        surrogate_fallback_kernel<<<blocks, 128, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+    // one block per environment, grid-stride over the listed environments
+    const int B = (N + 31) / 32 * 32;
+    int blocks = a.s.n_envs < 152 * 4 ? a.s.n_envs : 152 * 4;
+    const size_t smem = (size_t)2 * B * sizeof(float4);
+    if (a.s.c.rk4) surrogate_fallback_block_kernel<true><<<blocks, B, smem, s>>>(a);
+    else surrogate_fallback_block_kernel<false><<<blocks, B, smem, s>>>(a);
     return cudaGetLastError();
 }
 

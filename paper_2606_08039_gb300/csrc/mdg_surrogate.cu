@@ -359,10 +359,8 @@ int mdg_surrogate_step(mdg_handle h, mdg_mlp m, float* state, const float* actio
 {
     if (!h || !m) return fail(MDG_ERR_ARG, "mdg_surrogate_step: NULL handle");
     if (h->n_drones == 0) return MDG_OK;
-    if (h->uniform_N <= 0 || h->uniform_N > 32)
-        return fail(MDG_ERR_UNSUPPORTED, "mdg_surrogate_step: needs environments of one size, at most 32 drones");
-    if (h->dc.rk4)
-        return fail(MDG_ERR_UNSUPPORTED, "mdg_surrogate_step: the fallback integrates with Euler substeps only");
+    if (h->uniform_N <= 0)
+        return fail(MDG_ERR_UNSUPPORTED, "mdg_surrogate_step: needs environments of one size");
     if (!mdg::valid_action(action_type))
         return fail(MDG_ERR_ARG, "mdg_surrogate_step: unknown action_type %d", action_type);
     if (action_type == MDG_ACT_MIXED && !h->act_set)

@@ -37,12 +37,19 @@ def state13(state):
                       s[3, :, 0:1]], dim=1)
 
 
-def generate_transitions(n_envs: int, steps: int, seed: int, device, perturb: float = 0.1, n_substeps: int = 5):
-    """Transitions of the full-aero swarm: (raw inputs [steps * n, 41], state change [steps * n, 13])."""
+def generate_transitions(n_envs: int, steps: int, seed: int, device, perturb: float = 0.1, n_substeps: int = 5,
+                         workload: str = "full_aero", constants=None, episode: int = 0):
+    """Transitions of a swarm under the library's plain integrator (the handle's constants:
+    Euler or RK4 substeps): (raw inputs [steps * n, 41], state change [steps * n, 13]).
+    full_aero: PID RPMs towards the workload's waypoints, each motor times U[1 - perturb,
+    1 + perturb]; dense: the dense workload's RPM actions (hover times U[0.9, 1.1] per motor).
+    episode > 0: the swarm restarts from a fresh draw of its workload every `episode` steps."""
     torch = _torch()
     import paper_2606_08039_gb300 as mdg
-    sw = wl.full_aero(seed, n_envs)
-    h = mdg.Handle(sw.drones_per_env, sw.flags)
+    make = {"full_aero": wl.full_aero, "dense": wl.dense}[workload]
+    sw = make(seed, n_envs)
+    h = mdg.Handle(sw.drones_per_env, sw.flags, constants)
+    hover = (constants or mdg.Constants.cf2x()).hover_rpm()
     state = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=device)
     wp = torch.as_tensor(wl.waypoints(seed, sw.n), device=device)
     raw = torch.empty((steps, sw.n, mdg.MLP_IN), dtype=torch.float32, device=device)
@@ -51,9 +58,15 @@ def generate_transitions(n_envs: int, steps: int, seed: int, device, perturb: fl
     idx = np.arange(sw.n, dtype=np.uint64)[:, None]
     comp = np.arange(4, dtype=np.uint64)[None, :]
     for k in range(steps):
-        h.pid(state, wp, rpm)
-        noise = wl.uniform_range(1.0 - perturb, 1.0 + perturb, seed, wl.S_ACT, 1000 + k, idx, comp)
-        rpm.mul_(torch.as_tensor(noise, device=device))
+        if episode and k and k % episode == 0:
+            fresh = make(seed + 7919 * (k // episode), n_envs)
+            state.copy_(mdg.pack_state(fresh.p, fresh.q, fresh.v, fresh.w, device=device))
+        if workload == "full_aero":
+            h.pid(state, wp, rpm)
+            noise = wl.uniform_range(1.0 - perturb, 1.0 + perturb, seed, wl.S_ACT, 1000 + k, idx, comp)
+            rpm.mul_(torch.as_tensor(noise, device=device))
+        else:
+            rpm.copy_(torch.as_tensor(wl.rpm_actions(seed, sw.n, k, hover), device=device))
         h.features(state, rpm, raw[k])
         before = state13(state).clone()
         h.step(state, rpm, mdg.ACT_RPM, n_substeps)

@@ -12,7 +12,7 @@ from oracle import mlp as omlp
 from paper_2606_08039_gb300 import surrogate as sg
 from paper_2606_08039_gb300 import workloads as wl
 from helpers import assert_horizon_close, assert_knn_valid, check_obs_against_own_state, excess, oracle_arrays, oracle_step, \
-    tolerance_response
+    spread_heights, tolerance_response
 
 pytestmark = pytest.mark.gpu
 
@@ -283,6 +283,37 @@ def test_out_of_distribution_environments_take_the_integrator(cuda, trained):
     resp = tolerance_response(P, layout, x0, i0, a0, wp, acts, 5)
     assert_horizon_close(xg, xo, resp, 5, what="fallback")
     assert excess(ig, io, 1e-5) <= 1.0
+    assert h.status()[0] == mdg.OK
+
+
+@pytest.mark.parametrize("integrator", ["euler", "rk4"])
+def test_fallback_of_large_environments(cuda, trained, integrator):
+    """Environments of 64 drones (the dense swarm's size, one block per environment in the
+    fallback) and Runge-Kutta substeps: with every environment out of distribution the
+    surrogate step is the plain integrator, against the oracle over the control step (heights
+    spread per environment, so that the downwash is well conditioned)."""
+    m, data, _ = trained
+    sw = spread_heights(wl.dense(80, n_envs=24), dz=0.3, z0=0.5)
+    c = mdg.Constants.cf2x()
+    Po = oracle.cf2x()
+    if integrator == "rk4":
+        c.integrator = mdg.INTEGRATOR_RK4
+        Po.integrator = oracle.RK4
+    h = mdg.Handle(sw.drones_per_env, sw.flags, c)
+    state = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=cuda)
+    x0, i0, a0 = oracle_arrays(state)
+    act = wl.rpm_actions(80, sw.n, 0, HOVER)
+    nfb = torch.zeros(1, dtype=torch.int32, device=cuda)
+    m.step(h, state, torch.as_tensor(act, device=cuda), mdg.ACT_RPM, 5, 0.0, nfb)
+    torch.cuda.synchronize()
+    assert int(nfb) == sw.n_envs
+    xg, _, ag = oracle_arrays(state)
+    layout = (sw.drones_per_env, sw.flags)
+    acts = np.full(sw.n_envs, mdg.ACT_RPM)
+    xo, _, ao = oracle_step(Po, layout, x0, i0, a0, act, acts, 5)
+    resp = tolerance_response(Po, layout, x0, i0, a0, act, acts, 5)
+    assert_horizon_close(xg, xo, resp, 5, what=f"fallback of 64-drone environments ({integrator})")
+    np.testing.assert_allclose(ag, ao, rtol=1e-6)
     assert h.status()[0] == mdg.OK
 
 
