@@ -479,6 +479,51 @@ def episode_line(n: int, world: int, ep_ms: float, peaks, flops_step: float) -> 
             "roofline": roof}
 
 
+def uneven_vs_uniform(sw, acts, c, K: int, dev, timed) -> dict:
+    """The uneven batch's control steps run as uniform batches: its environments grouped by
+    (size, physics subset, action type), each group a handle of its own (one environment size
+    and physics subset: the compile-time kernel variants where one exists), its K-step rollout
+    autotuned (block size, schedule, item size) and captured as a CUDA graph. One step = every
+    group's graph in turn, observations after the last step; the state of every group reset
+    before each step (untimed)."""
+    import torch
+    import paper_2606_08039_gb300 as mdg
+    env_off = sw.env_off
+    groups = {}
+    for e in range(sw.n_envs):
+        key = (int(sw.drones_per_env[e]), int(sw.flags[e]), int(sw.act_type[e]))
+        if key[0] > 0:
+            groups.setdefault(key, []).append(e)
+    runs = []
+    acts_np = acts.cpu().numpy()
+    for (N, fl, at), envs in sorted(groups.items()):
+        idx = np.concatenate([np.arange(env_off[e], env_off[e + 1]) for e in envs])
+        h = mdg.Handle(np.full(len(envs), N, np.int32), np.full(len(envs), fl, np.uint32), c)
+        init = mdg.pack_state(sw.p[idx], sw.q[idx], sw.v[idx], sw.w[idx], device=dev)
+        st = init.clone()
+        a = torch.as_tensor(np.ascontiguousarray(acts_np[:, idx]), device=dev)
+        kin, nidx, rel = h.new_obs(dev)
+        h.autotune(st, a, at, N_SUB, K)
+        g = h.rollout_graph(st, a, at, N_SUB, K, mdg.OBS_LAST, kin, nidx, rel)
+        runs.append((h, init, st, a, (kin, nidx, rel), g))
+
+    def step_all():
+        for r in runs:
+            r[5].launch()
+
+    def reset_all():
+        for r in runs:
+            r[2].copy_(r[1])
+    timed(step_all, 3, reset_all)
+    n = 50
+    ms = timed(step_all, n, reset_all) / n
+    for r in runs:
+        r[5].close()
+    return {"what": "the same environments and actions as uniform batches grouped by (size, physics subset, action "
+                    "type), each group's K-step rollout autotuned and replayed as its own CUDA graph, the groups in turn",
+            "groups": len(runs), "ms_per_step": ms, "value": sw.n * N_SUB * K / (ms * 1e-3)}
+
+
 def run_other(args) -> None:
     """The other swarms, on one GPU:
     uneven  4096 envs of 1..32 drones, mixed physics subsets and RPM/PID actions: one
@@ -510,6 +555,8 @@ def run_other(args) -> None:
         state = init.clone()
         kin, idx, rel = h.new_obs(dev)
         block, _ = h.autotune(state, acts, mdg.ACT_MIXED, N_SUB, K)
+        sched_mode, item_cap = h.rollout_schedule
+        extra["autotuned"] = {"block": block, "schedule": ["dynamic", "static"][sched_mode], "item_drones": item_cap}
         graph = h.rollout_graph(state, acts, mdg.ACT_MIXED, N_SUB, K, mdg.OBS_LAST, kin, idx, rel)
 
         def run():
@@ -566,26 +613,34 @@ def run_other(args) -> None:
         flush.fill_(1.0)
         torch.sum(flush, dim=0, out=sink)
 
-    def timed(fn, n):
+    def timed_each(fn, n, before=None):
         st = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
         en = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
         for i in range(n):
-            if reset:
+            if before is not None:
+                before()
+            elif reset:
                 state.copy_(init)
             flush_l2()
             st[i].record(stream)
             fn()
             en[i].record(stream)
         torch.cuda.synchronize()
-        return float(sum(a.elapsed_time(b) for a, b in zip(st, en)))
+        return [a.elapsed_time(b) for a, b in zip(st, en)]
+
+    def timed(fn, n, before=None):
+        return float(sum(timed_each(fn, n, before)))
 
     steps = min(args.steps, 2000)
     timed(run, args.warmup)
     clocks = ClockSampler(0)
     clocks.start()
     time.sleep(0.3)
-    total_ms = timed(run, steps)
+    per_step = timed_each(run, steps)
+    total_ms = float(sum(per_step))
     clk = clocks.stop()
+    extra["ms_per_step_spread"] = {"min": min(per_step), "median": statistics.median(per_step),
+                                   "max": max(per_step)}
     rc, bits, _ = h.status()
     nonfinite_frac = nonfinite_fraction([state])
     if extra_fn is not None:
@@ -593,6 +648,8 @@ def run_other(args) -> None:
         per_step_ms = timed(extra_fn, min(steps, 200)) / min(steps, 200)
         extra["same_work_as_single_step_launches"] = {"value": substeps / (per_step_ms * 1e-3), "ms": per_step_ms,
                                                       "launches": K}
+    if args.workload == "uneven":
+        extra["vs_best_uniform_kernels"] = uneven_vs_uniform(sw, acts, c, K, dev, timed)
     ms = total_ms / steps
     flops = algorithmic_flops(sw, K, N_SUB, obs_steps, pid_mask, rk4=args.integrator == "rk4")
     achieved = flops / (ms * 1e-3) / 1e12

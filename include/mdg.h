@@ -439,12 +439,31 @@ int mdg_rollout_graph_create(mdg_handle h, float* state, const float* actions, i
 int mdg_graph_launch(mdg_graph g, void* stream);
 int mdg_graph_destroy(mdg_graph g);
 
+/* Work distribution of the persistent rollout kernel (mdg_rollout and its graphs):
+ *   mode         MDG_SCHED_DYNAMIC (default): the blocks take the work items, longest first,
+ *                from an atomic counter, so each launch may hand them out in another order;
+ *                MDG_SCHED_STATIC: a fixed schedule built on the host, longest processing time
+ *                first (items by decreasing estimated chain, each to the block with the least
+ *                estimated work), the same every launch
+ *   item_drones  uneven batches: at most this many drones per work item (environments are
+ *                packed whole; one larger than this is an item of its own); 0 = the block size.
+ *                Smaller items give the schedule finer pieces to balance.
+ * Host only; takes effect at the next rollout (graphs capture the tables of their creation).
+ * Errors: MDG_ERR_ARG. */
+#define MDG_SCHED_DYNAMIC 0
+#define MDG_SCHED_STATIC 1
+int mdg_set_rollout_schedule(mdg_handle h, int32_t mode, int32_t item_drones);
+int mdg_get_rollout_schedule(mdg_handle h, int32_t* mode, int32_t* item_drones);
+
 /* Autotuner: times the step kernels (K = 0: mdg_step_obs; K > 0: a K-step mdg_rollout
  * with observations after the last step) on the caller's state and actions for every
- * block size 32, 64, 128, ..., 1024 that holds the largest environment (5 timed launches
- * after 2 warm-ups each, the state restored before every launch), keeps the fastest with
- * mdg_set_block_size and restores the state. Allocates temporary scratch; synchronises
- * `stream`. Writes the chosen size and its mean time in ms (either pointer may be NULL). */
+ * block size 32, 64, 128, ..., 1024 that holds the largest environment and, for rollouts,
+ * both schedules of mdg_set_rollout_schedule and (uneven batches) the item caps of the whole
+ * block, half and a quarter of it (at least the largest environment and 32 drones): 5 timed
+ * launches after 2 warm-ups each, the state restored before every launch. Keeps the fastest
+ * combination (mdg_set_block_size, mdg_set_rollout_schedule) and restores the state.
+ * Allocates temporary scratch; synchronises `stream`. Writes the chosen block size and its
+ * mean time in ms (either pointer may be NULL; mdg_get_rollout_schedule reads the rest). */
 int mdg_autotune(mdg_handle h, float* state, const float* actions, int32_t action_per_step, int32_t action_type,
                  int32_t n_substeps, int32_t K, void* stream, int32_t* best_block, float* best_ms);
 

@@ -25,6 +25,7 @@ ACT_RPM, ACT_PID, ACT_MIXED = 0, 1, 2
 ACT_RPM_NORM, ACT_ONE_D_RPM, ACT_VEL, ACT_ATTITUDE = 3, 4, 5, 6
 STATUS_NONFINITE = 1
 STATUS_TIMEOUT = 2
+SCHED_DYNAMIC, SCHED_STATIC = 0, 1
 STATUS_BOUNDS = 4
 MLP_PATH_MMA_SYNC, MLP_PATH_TCGEN05 = 0, 1
 STATE_PLANES = 6
@@ -102,6 +103,8 @@ _SIGNATURES = {
     "mdg_mlp_set_wait_limits": ([_VP, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "mdg_reset": ([_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_uint64, ctypes.c_uint64, _VP], ctypes.c_int),
     "mdg_set_obs_bias": ([_VP, _VP], ctypes.c_int),
+    "mdg_set_rollout_schedule": ([_VP, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "mdg_get_rollout_schedule": ([_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "mdg_mlp_status": ([_VP, _VP, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
     "mdg_features": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "mdg_surrogate_step": ([_VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, _VP, _VP],
@@ -412,6 +415,17 @@ class Handle:
         self._bias_keep = obs_bias
         _check(lib().mdg_set_obs_bias(self._h, None if obs_bias is None else
                                       _ptr(obs_bias, "obs_bias", torch.float32, (self.n, 12))))
+
+    def set_rollout_schedule(self, mode: int, item_drones: int = 0):
+        """The persistent rollout's work distribution (mdg_set_rollout_schedule)."""
+        _check(lib().mdg_set_rollout_schedule(self._h, int(mode), int(item_drones)))
+
+    @property
+    def rollout_schedule(self):
+        """(mode, item_drones) of mdg_get_rollout_schedule."""
+        mode, cap = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().mdg_get_rollout_schedule(self._h, ctypes.byref(mode), ctypes.byref(cap)))
+        return mode.value, cap.value
 
     def set_block_size(self, threads_per_block: int):
         _check(lib().mdg_set_block_size(self._h, int(threads_per_block)))

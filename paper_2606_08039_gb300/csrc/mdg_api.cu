@@ -276,6 +276,14 @@ int set_block(mdg_ctx* h, int block)
     return MDG_OK;
 }
 
+void free_schedule(mdg_ctx* h)
+{
+    cudaFree(h->d_sched_off);
+    cudaFree(h->d_sched_items);
+    h->d_sched_off = h->d_sched_items = nullptr;
+    h->sched_grid = 0;
+}
+
 void free_rollout_tables(mdg_ctx* h)
 {
     cudaFree(h->d_items);
@@ -288,6 +296,9 @@ void free_rollout_tables(mdg_ctx* h)
     h->d_slot_env = h->d_slot_goff = h->d_slot_loff = nullptr;
     h->n_items = 0;
     h->rollout_block = 0;
+    h->rollout_cap = -1;
+    h->item_cost.clear();
+    free_schedule(h);
 }
 
 template <typename T>
@@ -300,25 +311,37 @@ cudaError_t upload(T** dst, const std::vector<T>& v)
     return e;
 }
 
-// Work items of the rollout kernel for the current block size. Uniform batches use the
-// arithmetic tiles. Otherwise environments are sorted by (size descending, physics subset,
-// index), so that the environments sharing a warp share their size and branches, and
-// packed greedily into items of at most `block` drones and `block` environments; items are
-// handed out in decreasing cost (drones plus downwash pairs), longest first.
+// The dependent chain of one substep of an environment of N drones, in units of the
+// instructions of a substep without downwash (~160), for the static schedule: the drones of
+// a work item run in parallel threads, so an item lasts about as long as its longest chain.
+double item_chain(int N, uint32_t flags) { return 160.0 + ((flags & MDG_DW) ? 23.0 * (N - 1) : 0.0); }
+
+// Work items of the rollout kernel for the current block size and item cap. Uniform batches
+// use the arithmetic tiles. Otherwise environments are sorted by (size descending, physics
+// subset, index), so that the environments sharing a warp share their size and branches, and
+// packed greedily into items of at most `cap` drones (the block size, or the handle's item
+// cap when smaller; an environment larger than the cap is an item of its own) and `block`
+// environments; items are handed out in decreasing cost (drones plus downwash pairs),
+// longest first.
 int ensure_rollout_tables(mdg_ctx* h)
 {
-    if (h->rollout_block == h->block && h->d_counter) return MDG_OK;
+    if (h->rollout_block == h->block && h->rollout_cap == h->item_cap && h->d_counter) return MDG_OK;
     if (h->d_item_order) cudaDeviceSynchronize();
     free_rollout_tables(h);
     cudaError_t e;
     if (!h->d_counter && (e = cudaMalloc(&h->d_counter, sizeof(int))) != cudaSuccess)
         return cuda_fail(e, "rollout: cudaMalloc(counter)");
     std::vector<int> order;
+    h->item_cost.clear();
     if (h->uniform_N > 0) {
         h->n_items = h->n_tiles;
         order.resize(h->n_items);
         for (int i = 0; i < h->n_items; ++i) order[i] = i;
+        bool dw = false;
+        for (int32_t k = 0; k < h->n_envs; ++k) dw = dw || (h->h_flags[k] & MDG_DW);
+        h->item_cost.assign(h->n_items, item_chain(h->uniform_N, dw ? MDG_DW : 0u));
     } else {
+        const int cap = h->item_cap > 0 && h->item_cap < h->block ? h->item_cap : h->block;
         std::vector<int> envs;
         for (int32_t k = 0; k < h->n_envs; ++k)
             if (h->h_off[k + 1] > h->h_off[k]) envs.push_back(k);
@@ -336,8 +359,9 @@ int ensure_rollout_tables(mdg_ctx* h)
             const size_t i0 = i;
             int drones = 0;
             bool any_dw = false, local = true;
-            double c = 0.0;
-            while (i < envs.size() && drones + N(envs[i]) <= h->block && (int)(i + 1 - i0) <= h->block) {
+            double c = 0.0, chain = 0.0;
+            while (i < envs.size() && (i == i0 || drones + N(envs[i]) <= cap) && drones + N(envs[i]) <= h->block &&
+                   (int)(i + 1 - i0) <= h->block) {
                 const int n = N(envs[i]);
                 slot_goff[i] = h->h_off[envs[i]];
                 slot_loff[i] = drones;
@@ -347,6 +371,7 @@ int ensure_rollout_tables(mdg_ctx* h)
                 }
                 if ((drones >> 5) != ((drones + n - 1) >> 5)) local = false;
                 c += n;
+                chain = std::max(chain, item_chain(n, h->h_flags[envs[i]]));
                 drones += n;
                 ++i;
             }
@@ -354,6 +379,7 @@ int ensure_rollout_tables(mdg_ctx* h)
             int bits = (any_dw ? mdg::kTileAnyDW : 0) | (local ? mdg::kTileWarpLocal : 0);
             items.push_back(make_int4((int)i0, (int)(i - i0), drones, bits));
             cost.push_back(c);
+            h->item_cost.push_back(chain);
         }
         h->n_items = (int)items.size();
         order.resize(h->n_items);
@@ -371,6 +397,51 @@ int ensure_rollout_tables(mdg_ctx* h)
         return cuda_fail(e, "rollout: item order");
     }
     h->rollout_block = h->block;
+    h->rollout_cap = h->item_cap;
+    free_schedule(h);
+    return MDG_OK;
+}
+
+// The static schedule of the rollout kernel for a grid of `grid` persistent blocks: longest
+// processing time first (items by decreasing chain estimate, each to the block with the least
+// estimated work so far, the lower block index on ties), each block running its items in the
+// order they were given to it. The same items on the same blocks every launch: the duration
+// does not depend on which block happens to reach the work counter first.
+int ensure_schedule(mdg_ctx* h, int grid)
+{
+    if (h->sched_grid == grid && h->d_sched_off) return MDG_OK;
+    free_schedule(h);
+    const int n = h->n_items;
+    std::vector<int> by_cost(n);
+    for (int i = 0; i < n; ++i) by_cost[i] = i;
+    std::stable_sort(by_cost.begin(), by_cost.end(), [&](int a, int b) { return h->item_cost[a] > h->item_cost[b]; });
+    std::vector<std::vector<int>> lists(grid);
+    // min-heap of (load, block)
+    std::vector<std::pair<double, int>> heap;
+    for (int b = 0; b < grid; ++b) heap.push_back({0.0, b});
+    auto later = [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
+        return x.first != y.first ? x.first > y.first : x.second > y.second;
+    };
+    std::make_heap(heap.begin(), heap.end(), later);
+    for (int it : by_cost) {
+        std::pop_heap(heap.begin(), heap.end(), later);
+        auto& top = heap.back();
+        lists[top.second].push_back(it);
+        top.first += h->item_cost[it];
+        std::push_heap(heap.begin(), heap.end(), later);
+    }
+    std::vector<int> off(grid + 1, 0), items;
+    items.reserve(n);
+    for (int b = 0; b < grid; ++b) {
+        items.insert(items.end(), lists[b].begin(), lists[b].end());
+        off[b + 1] = (int)items.size();
+    }
+    cudaError_t e;
+    if ((e = upload(&h->d_sched_off, off)) != cudaSuccess || (e = upload(&h->d_sched_items, items)) != cudaSuccess) {
+        free_schedule(h);
+        return cuda_fail(e, "rollout: static schedule");
+    }
+    h->sched_grid = grid;
     return MDG_OK;
 }
 
@@ -761,6 +832,26 @@ int mdg_reset(mdg_handle h, float* state, const float* nominal, const float* ini
     return MDG_OK;
 }
 
+int mdg_set_rollout_schedule(mdg_handle h, int32_t mode, int32_t item_drones)
+{
+    if (!h) return fail(MDG_ERR_ARG, "mdg_set_rollout_schedule: NULL handle");
+    if (mode != MDG_SCHED_DYNAMIC && mode != MDG_SCHED_STATIC)
+        return fail(MDG_ERR_ARG, "mdg_set_rollout_schedule: unknown mode %d", mode);
+    if (item_drones < 0 || item_drones > 1024)
+        return fail(MDG_ERR_ARG, "mdg_set_rollout_schedule: item_drones = %d outside [0, 1024]", item_drones);
+    h->sched = mode;
+    h->item_cap = item_drones;
+    return MDG_OK;
+}
+
+int mdg_get_rollout_schedule(mdg_handle h, int32_t* mode, int32_t* item_drones)
+{
+    if (!h) return fail(MDG_ERR_ARG, "mdg_get_rollout_schedule: NULL handle");
+    if (mode) *mode = h->sched;
+    if (item_drones) *item_drones = h->item_cap;
+    return MDG_OK;
+}
+
 int mdg_set_block_size(mdg_handle h, int32_t threads_per_block)
 {
     if (!h) return fail(MDG_ERR_ARG, "mdg_set_block_size: NULL handle");
@@ -996,6 +1087,17 @@ int mdg_status(mdg_handle h, void* stream, uint32_t* bits, int64_t* first_drone)
     return (st[0] & MDG_STATUS_NONFINITE) ? MDG_ERR_NONFINITE : MDG_OK;
 }
 
+// The persistent grid of a rollout: the SMs times the blocks of the kernel variant that fit
+// one SM, at most one block per work item.
+static int rollout_grid(mdg_handle h, const mdg::RolloutArgs& r)
+{
+    int n_sm = 152;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device);
+    int grid = n_sm * mdg::rollout_blocks_per_sm(r.s, h->block, launch_flags(h, r.s.act_type));
+    if (grid <= 0 || grid > r.n_items) grid = r.n_items;
+    return grid;
+}
+
 static int rollout_args(mdg_handle h, float* state, const float* actions, int32_t action_per_step, int32_t action_type,
                         int32_t n_substeps, int32_t K, int32_t obs_mode, float* kin, int32_t* nbr_idx, float* nbr_rel,
                         mdg::RolloutArgs* r)
@@ -1036,6 +1138,13 @@ static int rollout_args(mdg_handle h, float* state, const float* actions, int32_
     r->slot_env = h->d_slot_env;
     r->slot_goff = h->d_slot_goff;
     r->slot_loff = h->d_slot_loff;
+    r->sched_off = nullptr;
+    r->sched_items = nullptr;
+    if (h->sched == MDG_SCHED_STATIC && h->n_items > 0) {
+        if ((rc = ensure_schedule(h, rollout_grid(h, *r))) != MDG_OK) return rc;
+        r->sched_off = h->d_sched_off;
+        r->sched_items = h->d_sched_items;
+    }
     return MDG_OK;
 }
 
@@ -1044,11 +1153,7 @@ static cudaError_t enqueue_rollout(mdg_handle h, const mdg::RolloutArgs& r, cuda
     if (r.n_items == 0 || r.K == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(h->d_counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    int n_sm = 152;
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device);
-    const int flags = launch_flags(h, r.s.act_type);
-    const int grid = n_sm * mdg::rollout_blocks_per_sm(r.s, h->block, flags);
-    return mdg::launch_rollout(r, h->block, flags, grid, s);
+    return mdg::launch_rollout(r, h->block, launch_flags(h, r.s.act_type), rollout_grid(h, r), s);
 }
 
 int mdg_rollout(mdg_handle h, float* state, const float* actions, int32_t action_per_step, int32_t action_type,
@@ -1151,8 +1256,8 @@ int mdg_autotune(mdg_handle h, float* state, const float* actions, int32_t actio
     float* rel = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e;
-    const int original = h->block;
-    int best = original;
+    const int original = h->block, orig_sched = h->sched, orig_cap = h->item_cap;
+    int best = original, best_sched = orig_sched, best_cap = orig_cap;
     float best_t = 1e30f;
     if ((e = cudaMalloc(&saved, state_bytes)) != cudaSuccess || (e = cudaMalloc(&kin, 80 * h->n_drones)) != cudaSuccess ||
         (e = cudaMalloc(&idx, 16 * h->n_drones)) != cudaSuccess || (e = cudaMalloc(&rel, 96 * h->n_drones)) != cudaSuccess ||
@@ -1162,8 +1267,29 @@ int mdg_autotune(mdg_handle h, float* state, const float* actions, int32_t actio
     } else {
         int lo = 32;
         while (lo < h->max_env) lo += 32;
-        for (int b = lo; b <= 1024 && rc == MDG_OK; b = b < 64 ? 64 : b * 2) {
+        // candidates: block sizes; for rollouts also the schedule (work counter or static) and,
+        // for uneven batches, the item cap (the block, half of it, a quarter of it; never below
+        // the largest environment or one warp)
+        struct Cand {
+            int block, sched, cap;
+        };
+        std::vector<Cand> cands;
+        for (int b = lo; b <= 1024; b = b < 64 ? 64 : b * 2) {
+            if (K == 0) {
+                cands.push_back({b, orig_sched, orig_cap});
+                continue;
+            }
+            std::vector<int> caps = {0};
+            if (h->uniform_N <= 0)
+                for (int c = b / 2; c >= std::max(32, h->max_env) && c >= b / 4; c /= 2) caps.push_back(c);
+            for (int c : caps)
+                for (int sm : {MDG_SCHED_DYNAMIC, MDG_SCHED_STATIC}) cands.push_back({b, sm, c});
+        }
+        for (size_t ci = 0; ci < cands.size() && rc == MDG_OK; ++ci) {
+            const int b = cands[ci].block;
             if ((rc = set_block(h, b)) != MDG_OK) break;
+            h->sched = cands[ci].sched;
+            h->item_cap = cands[ci].cap;
             float total = 0.f;
             for (int rep = 0; rep < 7 && rc == MDG_OK; ++rep) {
                 e = cudaMemcpyAsync(state, saved, state_bytes, cudaMemcpyDeviceToDevice, s);
@@ -1189,10 +1315,19 @@ int mdg_autotune(mdg_handle h, float* state, const float* actions, int32_t actio
             if (rc == MDG_OK && total / 5 < best_t) {
                 best_t = total / 5;
                 best = b;
+                best_sched = cands[ci].sched;
+                best_cap = cands[ci].cap;
             }
         }
-        if (rc == MDG_OK) rc = set_block(h, best);
-        else set_block(h, original);
+        if (rc == MDG_OK) {
+            rc = set_block(h, best);
+            h->sched = best_sched;
+            h->item_cap = best_cap;
+        } else {
+            set_block(h, original);
+            h->sched = orig_sched;
+            h->item_cap = orig_cap;
+        }
         cudaMemcpyAsync(state, saved, state_bytes, cudaMemcpyDeviceToDevice, s);
         cudaStreamSynchronize(s);
     }

@@ -120,6 +120,8 @@ struct RolloutArgs {
     const int* slot_env;
     const int* slot_goff;
     const int* slot_loff;
+    const int* sched_off;       // static schedule: block b runs sched_items[sched_off[b] .. sched_off[b + 1]),
+    const int* sched_items;     // in that order (null: items from the work counter)
 };
 
 // The surrogate's parameters as the kernels see them.
@@ -253,8 +255,15 @@ struct mdg_ctx {
     int uniform_bits = 0;
     int uniform_flags = -1;  // physics subset shared by every environment, -1 if they differ
     uint32_t* d_status = nullptr;
-    // rollout work items, built on first use for the current block size
+    // rollout work items, built on first use for the current block size, item cap and grid
     int rollout_block = 0;
+    int rollout_cap = -1;   // the item cap the items were built for
+    int item_cap = 0;       // at most this many drones per work item of an uneven batch (0: the block size)
+    int sched = 0;          // MDG_SCHED_DYNAMIC or MDG_SCHED_STATIC
+    int sched_grid = 0;     // the grid the static schedule was built for (0: none)
+    int* d_sched_off = nullptr;
+    int* d_sched_items = nullptr;
+    std::vector<double> item_cost;  // host: the chain estimate of every item
     int n_items = 0;
     int4* d_items = nullptr;
     int* d_item_order = nullptr;

@@ -1414,13 +1414,23 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
     int* s_item = s_goff + B;
     const int t = threadIdx.x;
     const bool uniform = a.uniform_N > 0;
+    // static schedule: this block's own list of items; else the next item from the counter
+    const int sched_lo = r.sched_off ? r.sched_off[blockIdx.x] : 0;
+    const int sched_hi = r.sched_off ? r.sched_off[blockIdx.x + 1] : 0;
 
-    for (;;) {
-        if (t == 0) *s_item = atomicAdd(r.work_counter, 1);
+    for (int taken = 0;; ++taken) {
+        if (t == 0) {
+            if (r.sched_off) {
+                const int i = sched_lo + taken;
+                *s_item = i < sched_hi && MDG_CHECK(i >= 0 && i < r.n_items, a.status) ? r.sched_items[i] : r.n_items;
+            } else {
+                *s_item = atomicAdd(r.work_counter, 1);
+            }
+        }
         __syncthreads();
         const int item_idx = *s_item;
         if (item_idx >= r.n_items) break;
-        const int item = r.item_order[item_idx];
+        const int item = r.sched_off ? item_idx : r.item_order[item_idx];
 
         // ---- this thread's drone and environment
         int n_drones, bits;

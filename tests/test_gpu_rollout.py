@@ -139,6 +139,42 @@ def test_rollout_graph_replays_the_rollout(cuda):
     g.close()
 
 
+def test_rollout_schedules_and_item_caps_give_identical_results(cuda):
+    """A drone's arithmetic does not depend on which persistent block runs its environment or
+    on how environments are packed into work items: the work counter and the static schedule,
+    with items of the whole block or of 32 or 64 drones, give bit-identical states and
+    observations over an 8-step uneven rollout (one graph of each, replayed)."""
+    K = 8
+    sw = wl.uneven(9, n_envs=500)
+    h = mdg.Handle(sw.drones_per_env, sw.flags)
+    h.set_action_types(sw.act_type)
+    h.set_block_size(128)
+    acts = torch.as_tensor(np.stack([wl.mixed_actions(sw, 9, k, HOVER) for k in range(K)]), device=cuda)
+    ref = None
+    for mode, cap in ((mdg.SCHED_DYNAMIC, 0), (mdg.SCHED_STATIC, 0), (mdg.SCHED_STATIC, 64), (mdg.SCHED_DYNAMIC, 32),
+                      (mdg.SCHED_STATIC, 32)):
+        h.set_rollout_schedule(mode, cap)
+        assert h.rollout_schedule == (mode, cap)
+        st = swarm_state(sw, cuda)
+        kin, idx, rel = h.new_obs(cuda)
+        h.rollout(st, acts, mdg.ACT_MIXED, 5, K, mdg.OBS_LAST, kin, idx, rel)
+        g = h.rollout_graph(st, acts, mdg.ACT_MIXED, 5, K, mdg.OBS_LAST, kin, idx, rel)
+        g.launch()
+        torch.cuda.synchronize()
+        g.close()
+        out = (st.clone(), kin.clone(), idx.clone(), rel.clone())
+        if ref is None:
+            ref = out
+        else:
+            for a, b in zip(out, ref):
+                assert torch.equal(a, b), f"schedule {mode}, item cap {cap}"
+    assert h.status()[0] == mdg.OK
+    with pytest.raises(mdg.MdgError):
+        h.set_rollout_schedule(7, 0)
+    with pytest.raises(mdg.MdgError):
+        h.set_rollout_schedule(mdg.SCHED_STATIC, -1)
+
+
 @pytest.mark.parametrize("K", [0, 4])
 def test_autotune_keeps_state_and_picks_a_valid_block(cuda, K):
     sw = wl.uneven(8, n_envs=400)
@@ -151,6 +187,9 @@ def test_autotune_keeps_state_and_picks_a_valid_block(cuda, K):
     torch.cuda.synchronize()
     assert torch.equal(state, before)
     assert best in (32, 64, 128, 256, 512, 1024) and h.block_size == best and ms > 0
+    mode, cap = h.rollout_schedule
+    assert mode in (mdg.SCHED_DYNAMIC, mdg.SCHED_STATIC)
+    assert cap == 0 or (K > 0 and max(32, int(sw.drones_per_env.max())) <= cap < best)
     # and the tuned handle still computes the step: one substep against the oracle
     x0, i0, a0 = oracle_arrays(state)
     h.step(state, acts, mdg.ACT_MIXED, 1)
