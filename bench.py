@@ -813,6 +813,38 @@ def run_mlp(args) -> None:
         "status": m.status()}))
 
 
+def training_step_ms(data, steps: int = 200, batch: int = 8192) -> dict:
+    """Milliseconds per training step (mdg_mlp_grad of one batch + mdg_mlp_adam) of each
+    training path, on a fresh network and the same batches of the standardised data set."""
+    import torch
+    import paper_2606_08039_gb300 as mdg
+    from paper_2606_08039_gb300 import workloads as wl
+    out = {}
+    gen = torch.Generator(device=data.x.device)
+    for name, path in (("tcgen05", mdg.MLP_PATH_TCGEN05), ("mma_sync", mdg.MLP_PATH_MMA_SYNC)):
+        m = mdg.MLP(batch, wl.mlp_init(5))
+        m.set_train_path(path)
+        gen.manual_seed(0)
+        idx = torch.randint(0, len(data), (steps + 5, batch), generator=gen, device=data.x.device)
+        xs = [data.x.index_select(0, i) for i in idx]
+        ts = [data.t.index_select(0, i) for i in idx]
+        loss = torch.zeros(1, device=data.x.device)
+        for k in range(5):
+            m.grad(xs[k], ts[k], loss)
+            m.adam(1e-3)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for k in range(5, steps + 5):
+            m.grad(xs[k], ts[k], loss)
+            m.adam(1e-3)
+        b.record()
+        torch.cuda.synchronize()
+        out[name] = a.elapsed_time(b) / steps
+        del xs, ts
+    return {"ms_per_step": out, "batch": batch, "steps": steps,
+            "what": "one training step (forward, backward, Adam) of a batch of 8192 transitions per path"}
+
+
 def run_surrogate(args) -> None:
     """The learned surrogate on one GPU: trained on ~10M transitions generated by the
     full-aero kernels (16384 envs x 4 drones, 153 control steps of PID with +-10% RPM
@@ -843,6 +875,7 @@ def run_surrogate(args) -> None:
     kept = data.kept_fraction
     out_std = data.out_std
     out_mean = data.out_mean
+    train_paths = training_step_ms(data)
     del data
 
     h = mdg.Handle(sw.drones_per_env, sw.flags)
@@ -916,7 +949,7 @@ def run_surrogate(args) -> None:
                    "l2": "flushed between timed steps (512 MiB written, then read back)",
                    "training": {"transitions_generated": 16384 * 4 * 153, "transitions_kept": n_train,
                                 "kept_fraction": kept, "epochs": 4, "batch": 8192, "seconds": train_s,
-                                "loss_per_epoch": hist}},
+                                "loss_per_epoch": hist, "path": "tcgen05", "per_path": train_paths}},
         "plain_integrator": {"value": sw.n / (ms_pln * 1e-3), "ms_per_step": ms_pln},
         "speedup_vs_plain": ms_pln / ms_sur,
         "one_step_error_vs_plain": err, "regular_fraction": float(regular.float().mean()),
@@ -962,6 +995,7 @@ def run_surrogate_dense(args) -> None:
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     n_train, kept, out_std, out_mean = len(data), data.kept_fraction, data.out_std, data.out_mean
+    train_paths = training_step_ms(data)
     del data
 
     h = mdg.Handle(sw.drones_per_env, sw.flags, c)
@@ -1033,7 +1067,8 @@ def run_surrogate_dense(args) -> None:
                    "l2": "flushed between timed steps (512 MiB written, then read back)",
                    "training": {"transitions_generated": 1024 * 64 * steps_gen, "transitions_kept": n_train,
                                 "kept_fraction": kept, "episode_steps": episode, "epochs": 4, "batch": 8192,
-                                "seconds": train_s, "loss_per_epoch": hist},
+                                "seconds": train_s, "loss_per_epoch": hist, "path": "tcgen05",
+                                "per_path": train_paths},
                    **model_config(args)},
         "plain_integrator": {"value": sw.n / (ms_pln * 1e-3), "ms_per_step": ms_pln,
                              "integrator": args.integrator},

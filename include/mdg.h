@@ -572,10 +572,17 @@ int mdg_mlp_adam(mdg_mlp m, float lr, void* stream);
 /* Inference path of mdg_mlp_forward and mdg_surrogate_step: MDG_MLP_PATH_TCGEN05 (default:
  * one fused kernel on tcgen05.mma with the accumulator in tensor memory and the
  * activations in shared memory) or MDG_MLP_PATH_MMA_SYNC (one mma.sync GEMM per layer, the
- * training kernels). Training always uses the mma.sync kernels. */
+ * training kernels). Training has its own setting, mdg_mlp_set_train_path. */
 #define MDG_MLP_PATH_MMA_SYNC 0
 #define MDG_MLP_PATH_TCGEN05 1
 int mdg_mlp_set_path(mdg_mlp m, int32_t path);
+/* Training path of mdg_mlp_grad: MDG_MLP_PATH_TCGEN05 (default: every GEMM of the forward and
+ * backward pass on tcgen05.mma with the accumulator in tensor memory, both operands K-major in
+ * shared memory; the epilogues write the pre-activations, the SiLU activations and the
+ * hidden gradients together with their transposes, which are the K-major operands of the
+ * weight gradients dW = dZ^T X; those are split over the batch and added up with atomics) or
+ * MDG_MLP_PATH_MMA_SYNC (the mma.sync GEMMs). Errors: MDG_ERR_ARG. */
+int mdg_mlp_set_train_path(mdg_mlp m, int32_t path);
 /* Bounds of the tcgen05 kernel's waits on its own mbarriers (its MMAs, bulk copies and
  * epilogue hand-offs): try_waits mbarrier.try_wait calls (each suspends at most ~1 us) for
  * the producer and MMA waits, polls test_wait polls for the MMA/epilogue hand-offs; a wait

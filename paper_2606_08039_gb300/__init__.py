@@ -101,6 +101,7 @@ _SIGNATURES = {
     "mdg_mlp_adam": ([_VP, ctypes.c_float, _VP], ctypes.c_int),
     "mdg_mlp_set_path": ([_VP, ctypes.c_int32], ctypes.c_int),
     "mdg_mlp_set_wait_limits": ([_VP, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "mdg_mlp_set_train_path": ([_VP, ctypes.c_int32], ctypes.c_int),
     "mdg_reset": ([_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_uint64, ctypes.c_uint64, _VP], ctypes.c_int),
     "mdg_set_obs_bias": ([_VP, _VP], ctypes.c_int),
     "mdg_set_rollout_schedule": ([_VP, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
@@ -654,6 +655,10 @@ class MLP:
     def set_path(self, path: int):
         """Inference path: MLP_PATH_TCGEN05 (fused tensor-memory kernel) or MLP_PATH_MMA_SYNC."""
         _check(lib().mdg_mlp_set_path(self._m, int(path)))
+
+    def set_train_path(self, path: int):
+        """GEMMs of mdg_mlp_grad: MLP_PATH_TCGEN05 (default) or MLP_PATH_MMA_SYNC."""
+        _check(lib().mdg_mlp_set_train_path(self._m, int(path)))
 
     def set_wait_limits(self, try_waits: int = -1, polls: int = -1):
         """Bounds of the tcgen05 kernel's mbarrier waits (negative: the defaults)."""

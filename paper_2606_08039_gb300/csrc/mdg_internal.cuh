@@ -212,6 +212,26 @@ cudaError_t mlp_adam(const MlpView& w, const float* grad, float* m, float* v, fl
 cudaError_t mlp_refresh_bf16(const MlpView& w, cudaStream_t s);
 cudaError_t mlp_standardize(const float* raw, void* x, long long rows, const float* mean, const float* inv_std,
                             cudaStream_t s);
+// db[n] = sum over the M rows of dz[m][n] (bf16 [M][N])
+cudaError_t mlp_bias_grad(const void* dz, int M, int N, float* db, cudaStream_t s);
+
+// Scratch of the tcgen05 training pass (batch B <= max_batch rows): the forward pass's
+// pre-activations z (FP32 [B][256]) and activations h (bf16 [B][256]) with their transposes hT
+// ([256][B]), the output y (FP32 [B][32]) and its gradient dy (bf16 [B][32], transposed dyT
+// [32][B]), the hidden gradients dz ([B][256], transposed dzT), the transposed input xT
+// ([64][B]) and the transposed weights wT (W2^T, W3^T [256][256], W4^T [256][32], bf16).
+struct TrainBuffers {
+    float* z[3];
+    void* h[3];
+    void* hT[3];
+    void* dz[3];
+    void* dzT[3];
+    float* y;
+    void* dy;
+    void* dyT;
+    void* xT;
+    const void* wT;
+};
 // mdg_umma.cu: fused tcgen05 forward, B a multiple of 128, y [B][32]. `img` is the weight
 // image of mlp_build_image (mlp_image_bytes() bytes, 16-byte aligned), rebuilt whenever the
 // bf16 weights change.
@@ -219,6 +239,13 @@ size_t mlp_image_bytes();
 cudaError_t mlp_build_image(const MlpView& w, void* img, cudaStream_t s);
 cudaError_t mlp_forward_umma(const MlpView& w, const void* img, const void* x, int B, float* y, uint32_t* status,
                              int wait_limit, int spin_limit, cudaStream_t s);
+// Training on tcgen05: the loss of the standardised targets t ([B][32], columns 13..31
+// ignored) added to *loss_acc and every parameter's gradient written to grad (flat FP32
+// layout); B a multiple of 128. wT must hold the current weights' transposes.
+cudaError_t mlp_grad_umma(const MlpView& w, const TrainBuffers& t, const void* x, int B, const float* target,
+                          float* loss_acc, float* grad, uint32_t* status, cudaStream_t s);
+cudaError_t mlp_weights_transposed(const MlpView& w, void* wT, cudaStream_t s);
+size_t mlp_weights_transposed_elems();
 
 cudaError_t launch_obs(const StepArgs& a, int n_tiles, int block, cudaStream_t s);
 cudaError_t launch_reset(const ResetArgs& r, cudaStream_t s);

@@ -372,6 +372,12 @@ cudaError_t mlp_refresh_bf16(const MlpView& w, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t mlp_bias_grad(const void* dz, int M, int N, float* db, cudaStream_t s)
+{
+    bias_grad_kernel<<<(N + 31) / 32, 256, 0, s>>>(static_cast<const bf16*>(dz), M, N, db);
+    return cudaGetLastError();
+}
+
 cudaError_t mlp_standardize(const float* raw, void* x, long long rows, const float* mean, const float* inv_std,
                             cudaStream_t s)
 {

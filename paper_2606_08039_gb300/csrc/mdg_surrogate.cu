@@ -74,6 +74,13 @@ struct mdg_mlp_s {
     bool img_stale = true;       // the bf16 weights changed since the image was built
     int wait_limit = MDG_MLP_DEFAULT_TRY_WAITS;  // bounded waits of the tcgen05 kernel
     int spin_limit = MDG_MLP_DEFAULT_POLLS;
+    int train_path = MDG_MLP_PATH_TCGEN05;
+    __nv_bfloat16* hT[3] = {};  // tcgen05 training: transposed activations and gradients
+    __nv_bfloat16* dzT[3] = {};
+    __nv_bfloat16* dyT = nullptr;
+    __nv_bfloat16* xT = nullptr;
+    __nv_bfloat16* wT = nullptr;  // W2^T, W3^T, W4^T
+    bool wT_stale = true;
     mdg::MlpView view() const { return layout(master, w16); }
 };
 
@@ -101,6 +108,13 @@ void destroy_mlp(mdg_mlp m)
     cudaFree(m->fb_count);
     cudaFree(m->status);
     cudaFree(m->img);
+    for (int l = 0; l < 3; ++l) {
+        cudaFree(m->hT[l]);
+        cudaFree(m->dzT[l]);
+    }
+    cudaFree(m->dyT);
+    cudaFree(m->xT);
+    cudaFree(m->wT);
     delete m;
 }
 
@@ -168,6 +182,13 @@ int mdg_mlp_create(int32_t max_batch, const float* init, mdg_mlp* out)
     alloc((void**)&m->fb_count, 4);
     alloc((void**)&m->status, 8);
     alloc((void**)&m->img, mdg::mlp_image_bytes());
+    for (int l = 0; l < 3; ++l) {
+        alloc((void**)&m->hT[l], B * H * 2);
+        alloc((void**)&m->dzT[l], B * H * 2);
+    }
+    alloc((void**)&m->dyT, B * MDG_MLP_OUT_PAD * 2);
+    alloc((void**)&m->xT, B * MDG_MLP_IN_PAD * 2);
+    alloc((void**)&m->wT, mdg::mlp_weights_transposed_elems() * 2);
     if (e == cudaSuccess && init) e = cudaMemcpy(m->master, init, P * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = mdg::mlp_refresh_bf16(m->view(), 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -203,6 +224,7 @@ int mdg_mlp_set_params(mdg_mlp m, const float* host_in)
     cudaError_t e = cudaMemcpy(m->master, host_in, (size_t)MDG_MLP_PARAMS * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = mdg::mlp_refresh_bf16(m->view(), 0);
     m->img_stale = true;
+    m->wT_stale = true;
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     return e == cudaSuccess ? MDG_OK : cuda_fail(e, "mdg_mlp_set_params");
 }
@@ -278,8 +300,29 @@ int mdg_mlp_grad(mdg_mlp m, const uint16_t* x, const float* t, int32_t B, float*
     float* zs[3] = {m->z[0], m->z[1], m->z[2]};
     void* hs[3] = {m->h[0], m->h[1], m->h[2]};
     void* dzs[3] = {m->dz[0], m->dz[1], m->dz[2]};
-    if (e == cudaSuccess) e = mdg::mlp_forward(m->view(), x, B, zs, hs, m->y, t, m->dy, m->loss, s);
-    if (e == cudaSuccess) e = mdg::mlp_backward(m->view(), x, B, zs, hs, m->dy, dzs, m->grad, s);
+    if (m->train_path == MDG_MLP_PATH_TCGEN05) {
+        if (e == cudaSuccess && m->wT_stale) {
+            e = mdg::mlp_weights_transposed(m->view(), m->wT, s);
+            if (e == cudaSuccess) m->wT_stale = false;
+        }
+        mdg::TrainBuffers tb;
+        for (int l = 0; l < 3; ++l) {
+            tb.z[l] = m->z[l];
+            tb.h[l] = m->h[l];
+            tb.hT[l] = m->hT[l];
+            tb.dz[l] = m->dz[l];
+            tb.dzT[l] = m->dzT[l];
+        }
+        tb.y = m->y;
+        tb.dy = m->dy;
+        tb.dyT = m->dyT;
+        tb.xT = m->xT;
+        tb.wT = m->wT;
+        if (e == cudaSuccess) e = mdg::mlp_grad_umma(m->view(), tb, x, B, t, m->loss, m->grad, m->status, s);
+    } else {
+        if (e == cudaSuccess) e = mdg::mlp_forward(m->view(), x, B, zs, hs, m->y, t, m->dy, m->loss, s);
+        if (e == cudaSuccess) e = mdg::mlp_backward(m->view(), x, B, zs, hs, m->dy, dzs, m->grad, s);
+    }
     if (e == cudaSuccess && loss_out) e = cudaMemcpyAsync(loss_out, m->loss, 4, cudaMemcpyDeviceToDevice, s);
     return e == cudaSuccess ? MDG_OK : cuda_fail(e, "mdg_mlp_grad");
 }
@@ -291,6 +334,7 @@ int mdg_mlp_adam(mdg_mlp m, float lr, void* stream)
     Guard g(m->device);
     m->step += 1;
     m->img_stale = true;
+    m->wT_stale = true;
     cudaError_t e = mdg::mlp_adam(m->view(), m->grad, m->m, m->v, lr, m->step, (cudaStream_t)stream);
     return e == cudaSuccess ? MDG_OK : cuda_fail(e, "mdg_mlp_adam");
 }
@@ -301,6 +345,15 @@ int mdg_mlp_set_path(mdg_mlp m, int32_t path)
     if (path != MDG_MLP_PATH_MMA_SYNC && path != MDG_MLP_PATH_TCGEN05)
         return fail(MDG_ERR_ARG, "mdg_mlp_set_path: unknown path %d", path);
     m->path = path;
+    return MDG_OK;
+}
+
+int mdg_mlp_set_train_path(mdg_mlp m, int32_t path)
+{
+    if (!m) return fail(MDG_ERR_ARG, "mdg_mlp_set_train_path: NULL handle");
+    if (path != MDG_MLP_PATH_MMA_SYNC && path != MDG_MLP_PATH_TCGEN05)
+        return fail(MDG_ERR_ARG, "mdg_mlp_set_train_path: unknown path %d", path);
+    m->train_path = path;
     return MDG_OK;
 }
 

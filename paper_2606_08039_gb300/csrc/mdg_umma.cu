@@ -54,7 +54,6 @@ constexpr uint32_t kTmemCols = 512;        // two accumulators of 256 columns
 constexpr int kLoadsPerTile = 10;          // W1, W2 chunks 0-3, W3 chunks 0-3, W4
 constexpr uint32_t kSuspendNs = 1000;      // longest suspension of one mbarrier try_wait
 constexpr int kWaitLimit = MDG_MLP_DEFAULT_TRY_WAITS;  // try_waits (at most ~0.26 s) before giving up
-constexpr int kSpinLimit = MDG_MLP_DEFAULT_POLLS;      // polls of a spinning wait (a few tenths of a second)
 
 // Weight image: the chunks in the order the MMAs consume them, load i at i * 32 KB.
 //   load 0      W1 [256 x 64]
@@ -461,6 +460,223 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
 }
 
+// ---- training GEMMs on tcgen05: C[M x N] = A[M x K] B[N x K]^T, both operands K-major ----
+//
+// One 128-thread block computes a 128 x BN tile of C over a range of K (split-K when
+// gridDim.z > 1: the partial tiles are added to the output with atomics). Per 64-wide K chunk
+// every thread copies its share of the A and B chunks into shared memory (cp.async, 16 bytes
+// each, written straight into the 128-byte-swizzled K-major layout of the inference kernel's
+// operands; a 32-wide last chunk is padded with zeros), one thread issues the chunk's four
+// tcgen05.mma (K = 16 each) into the TMEM accumulator and commits them to the chunk's stage
+// mbarrier; two stages alternate, so the next chunk's copies overlap this chunk's MMAs. The
+// epilogue reads the accumulator row by row (thread = row, tcgen05.ld.32x32b) and hands every
+// element (m, n, acc) to the layer's epilogue functor. Waits are bounded: on expiry the block
+// records MDG_STATUS_TIMEOUT, drains its MMAs, skips its epilogue and frees its TMEM.
+constexpr int kGemmThreads = 128;
+
+template <int BN>
+struct GemmShape {
+    static constexpr uint32_t a_bytes = 128 * 128;                    // [128 x 64] bf16
+    static constexpr uint32_t b_bytes = BN * 128;                     // [BN x 64] bf16
+    static constexpr uint32_t stage_bytes = a_bytes + b_bytes;
+    static constexpr uint32_t smem = 1024 + 2 * stage_bytes;          // alignment slack + two stages
+    static constexpr uint32_t tmem_cols = BN < 32 ? 32 : BN;
+};
+
+// Copies rows [row0, row0 + rows) x columns [k0, k0 + kw) (kw = 64 or 32) of a K-major bf16
+// matrix (leading dimension ld elements) into a swizzled [rows x 64] chunk at `dst`; columns
+// beyond kw are zero.
+__device__ __forceinline__ void load_chunk(uint32_t dst, const __nv_bfloat16* src, int ld, int row0, int rows, int k0,
+                                           int kw, uint8_t* dst_generic)
+{
+    const int pieces = kw / 8;
+    for (int i = threadIdx.x; i < rows * 8; i += kGemmThreads) {
+        const int r = i >> 3, k8 = i & 7;
+        const uint32_t off = (uint32_t)r * 128 + ((k8 ^ (r & 7)) << 4);
+        if (k8 < pieces) cp_async16(dst + off, src + (size_t)(row0 + r) * ld + k0 + k8 * 8);
+        else *reinterpret_cast<uint4*>(dst_generic + off) = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+template <int BN, class Epi>
+__global__ void __launch_bounds__(kGemmThreads) umma_gemm_kernel(const __nv_bfloat16* __restrict__ A, int lda,
+                                                                 const __nv_bfloat16* __restrict__ B, int ldb, int K,
+                                                                 int k_per_split, Epi epi, uint32_t* status)
+{
+    using S = GemmShape<BN>;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t bars[3];  // stage 0, stage 1: MMAs done with the stage; 2: accumulator done
+    __shared__ uint32_t s_tmem;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * 128, n0 = blockIdx.x * BN;
+    const int k_begin = blockIdx.z * k_per_split;
+    const int k_end = min(K, k_begin + k_per_split);
+    const uint32_t bar0 = smem_u32(&bars[0]);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 3; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar0 + 8u * i));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
+                     "r"(S::tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    const uint32_t idesc = idesc_bf16(128, BN);
+
+    bool ok = true;
+    int c = 0;  // chunks issued
+    for (int k0 = k_begin; k0 < k_end; k0 += 64, ++c) {
+        const int st = c & 1;
+        if (c >= 2) {  // the MMAs of chunk c - 2 have read this stage
+            const bool done = mbar_wait(bar0 + 8u * st, ((c - 2) >> 1) & 1, nullptr, status, kWaitLimit);
+            ok = __syncthreads_and(done);
+            if (!ok) break;
+        }
+        const int kw = min(64, k_end - k0);
+        uint8_t* sa = base + st * S::stage_bytes;
+        uint8_t* sb = sa + S::a_bytes;
+        load_chunk(smem_u32(sa), A, lda, m0, 128, k0, kw, sa);
+        load_chunk(smem_u32(sb), B, ldb, n0, BN, k0, kw, sb);
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                mma_bf16_ss(tmem, sw128_desc(smem_u32(sa) + kk * 32), sw128_desc(smem_u32(sb) + kk * 32), idesc,
+                            (c > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(bar0 + 8u * st);
+        }
+    }
+    // every MMA issued has completed before the accumulator is read or the TMEM freed
+    if (threadIdx.x == 0) mma_commit(bar0 + 16u);
+    const bool drained = mbar_wait(bar0 + 16u, 0, nullptr, status, kWaitLimit);
+    ok = __syncthreads_and(ok && drained && c > 0);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (ok) {
+        const int row = warp * 32 + lane;
+        const uint32_t t_row = tmem + ((uint32_t)(warp * 32) << 16);
+        float loss = 0.f;
+#pragma unroll 1
+        for (int cc = 0; cc < BN; cc += 16) {
+            float v[16];
+            tmem_ld16(t_row + cc, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) loss += epi(m0 + row, n0 + cc + i, v[i]);
+        }
+        epi.finish(loss);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(S::tmem_cols));
+}
+
+__device__ __forceinline__ float silu_train(float z) { return z / (1.f + __expf(-z)); }
+__device__ __forceinline__ float silu_grad_train(float z)
+{
+    const float sg = 1.f / (1.f + __expf(-z));
+    return sg * (1.f + z * (1.f - sg));
+}
+
+// Hidden layer forward: z = acc + b[n] (FP32, kept for the backward pass), h = bf16(silu(z))
+// row-major and transposed (the transposed copy is the K-major operand of the weight gradient).
+struct TrainEpiHidden {
+    const float* bias;
+    float* z;
+    __nv_bfloat16* h;
+    __nv_bfloat16* hT;
+    int ld, ldT;
+    __device__ __forceinline__ float operator()(int m, int n, float acc) const
+    {
+        const float zz = acc + bias[n];
+        z[(size_t)m * ld + n] = zz;
+        const __nv_bfloat16 hv = __float2bfloat16_rn(silu_train(zz));
+        h[(size_t)m * ld + n] = hv;
+        hT[(size_t)n * ldT + m] = hv;
+        return 0.f;
+    }
+    __device__ __forceinline__ void finish(float) const {}
+};
+
+// Output layer forward with the MSE: y = acc + b[n]; on the n_valid used columns
+// dy = scale (y - t) (bf16, row-major and transposed) and loss += (y - t)^2 / (rows n_valid).
+struct TrainEpiOut {
+    const float* bias;
+    float* y;
+    const float* target;
+    __nv_bfloat16* dy;
+    __nv_bfloat16* dyT;
+    float* loss_acc;
+    int ld, ldT, n_valid;
+    float grad_scale, loss_scale;
+    __device__ __forceinline__ float operator()(int m, int n, float acc) const
+    {
+        const float yy = acc + bias[n];
+        y[(size_t)m * ld + n] = yy;
+        const float d = n < n_valid ? yy - target[(size_t)m * ld + n] : 0.f;
+        const __nv_bfloat16 g = __float2bfloat16_rn(grad_scale * d);
+        dy[(size_t)m * ld + n] = g;
+        dyT[(size_t)n * ldT + m] = g;
+        return d * d * loss_scale;
+    }
+    __device__ __forceinline__ void finish(float loss) const
+    {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(loss_acc, loss);
+    }
+};
+
+// Input gradient of a hidden layer: dz_prev = bf16(acc silu'(z_prev)), row-major and transposed.
+struct TrainEpiDx {
+    const float* zprev;
+    __nv_bfloat16* dz;
+    __nv_bfloat16* dzT;
+    int ld, ldT;
+    __device__ __forceinline__ float operator()(int m, int n, float acc) const
+    {
+        const __nv_bfloat16 g = __float2bfloat16_rn(acc * silu_grad_train(zprev[(size_t)m * ld + n]));
+        dz[(size_t)m * ld + n] = g;
+        dzT[(size_t)n * ldT + m] = g;
+        return 0.f;
+    }
+    __device__ __forceinline__ void finish(float) const {}
+};
+
+// Weight gradient (split over K = the batch): g[m][n] (or g[n][m] when transposed) += acc.
+struct TrainEpiGrad {
+    float* g;
+    int ld;
+    bool transpose;
+    __device__ __forceinline__ float operator()(int m, int n, float acc) const
+    {
+        atomicAdd(transpose ? g + (size_t)n * ld + m : g + (size_t)m * ld + n, acc);
+        return 0.f;
+    }
+    __device__ __forceinline__ void finish(float) const {}
+};
+
+// out[c][r] = in[r][c] for a [rows x cols] bf16 matrix (32 x 32 tiles through shared memory).
+__global__ void __launch_bounds__(256) transpose_bf16_kernel(const __nv_bfloat16* __restrict__ in,
+                                                             __nv_bfloat16* __restrict__ out, int rows, int cols)
+{
+    __shared__ __nv_bfloat16 tile[32][34];
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int i = ty; i < 32; i += 8)
+        if (r0 + i < rows && c0 + tx < cols) tile[i][tx] = in[(size_t)(r0 + i) * cols + c0 + tx];
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8)
+        if (c0 + i < cols && r0 + tx < rows) out[(size_t)(c0 + i) * rows + r0 + tx] = tile[tx][i];
+}
+
 // One thread per 16-byte piece (8 consecutive k of one row n) of every weight matrix.
 __global__ void build_image_kernel(const __nv_bfloat16* __restrict__ w16, MlpView w, uint8_t* __restrict__ img)
 {
@@ -517,6 +733,108 @@ cudaError_t mlp_forward_umma(const MlpView& w, const void* img, const void* x, i
                                                       static_cast<const uint8_t*>(img), w.master, w, status,
                                                       wait_limit, spin_limit);
     return cudaGetLastError();
+}
+
+template <int BN, class Epi>
+static cudaError_t umma_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
+                             int splits, Epi epi, uint32_t* status, cudaStream_t s)
+{
+    if (M % 128 || N % BN || K % 32 || K <= 0 || splits < 1) return cudaErrorInvalidValue;
+    using S = GemmShape<BN>;
+    static bool attr_done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr_done[dev]) {
+        e = cudaFuncSetAttribute(umma_gemm_kernel<BN, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem);
+        if (e != cudaSuccess) return e;
+        attr_done[dev] = true;
+    }
+    // K per split: whole 64-wide chunks
+    const int chunks = (K + 63) / 64;
+    const int per = (chunks + splits - 1) / splits;
+    splits = (chunks + per - 1) / per;
+    dim3 grid(N / BN, M / 128, splits);
+    umma_gemm_kernel<BN, Epi><<<grid, kGemmThreads, S::smem, s>>>(reinterpret_cast<const __nv_bfloat16*>(A), lda,
+                                                                  reinterpret_cast<const __nv_bfloat16*>(B), ldb, K,
+                                                                  per * 64, epi, status);
+    return cudaGetLastError();
+}
+
+static cudaError_t transpose_bf16(const void* in, void* out, int rows, int cols, cudaStream_t s)
+{
+    dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+    transpose_bf16_kernel<<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(in), static_cast<__nv_bfloat16*>(out),
+                                               rows, cols);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_weights_transposed(const MlpView& w, void* wT, cudaStream_t s)
+{
+    // W2^T, W3^T [256 x 256] and W4^T [256 x 32] (the B operands of the input gradients)
+    const __nv_bfloat16* w16 = static_cast<const __nv_bfloat16*>(w.w16);
+    __nv_bfloat16* o = static_cast<__nv_bfloat16*>(wT);
+    cudaError_t e = transpose_bf16(w16 + w.w_off[1], o, MDG_MLP_HIDDEN, MDG_MLP_HIDDEN, s);
+    if (e == cudaSuccess) e = transpose_bf16(w16 + w.w_off[2], o + MDG_MLP_HIDDEN * MDG_MLP_HIDDEN, MDG_MLP_HIDDEN,
+                                             MDG_MLP_HIDDEN, s);
+    if (e == cudaSuccess) e = transpose_bf16(w16 + w.w_off[3], o + 2 * MDG_MLP_HIDDEN * MDG_MLP_HIDDEN,
+                                             MDG_MLP_OUT_PAD, MDG_MLP_HIDDEN, s);
+    return e;
+}
+
+size_t mlp_weights_transposed_elems() { return 2 * MDG_MLP_HIDDEN * MDG_MLP_HIDDEN + MDG_MLP_HIDDEN * MDG_MLP_OUT_PAD; }
+
+cudaError_t mlp_grad_umma(const MlpView& w, const TrainBuffers& t, const void* x, int B, const float* target,
+                          float* loss_acc, float* grad, uint32_t* status, cudaStream_t s)
+{
+    const int H = MDG_MLP_HIDDEN, I = MDG_MLP_IN_PAD, O = MDG_MLP_OUT_PAD;
+    const __nv_bfloat16* w16 = static_cast<const __nv_bfloat16*>(w.w16);
+    const __nv_bfloat16* xin = static_cast<const __nv_bfloat16*>(x);
+    const __nv_bfloat16* wT = static_cast<const __nv_bfloat16*>(t.wT);
+    auto bf = [](void* p) { return static_cast<__nv_bfloat16*>(p); };
+    // the weight gradients are split over the batch and added up with atomics
+    const int splits = B / 512 > 0 ? B / 512 : 1;
+    cudaError_t e = cudaMemsetAsync(grad, 0, (size_t)MDG_MLP_PARAMS * 4, s);
+    if (e == cudaSuccess) e = transpose_bf16(x, t.xT, B, I, s);
+    // forward
+    const __nv_bfloat16* in = xin;
+    int fan_in = I;
+    for (int l = 0; l < 3 && e == cudaSuccess; ++l) {
+        TrainEpiHidden ep{w.master + w.b_off[l], t.z[l], bf(t.h[l]), bf(t.hT[l]), H, B};
+        e = umma_gemm<256>(in, fan_in, w16 + w.w_off[l], fan_in, B, H, fan_in, 1, ep, status, s);
+        in = bf(t.h[l]);
+        fan_in = H;
+    }
+    if (e == cudaSuccess) {
+        TrainEpiOut eo{w.master + w.b_off[3], t.y, target, bf(t.dy), bf(t.dyT), loss_acc, O, B, MDG_MLP_OUT,
+                       2.f / ((float)B * MDG_MLP_OUT), 1.f / ((float)B * MDG_MLP_OUT)};
+        e = umma_gemm<32>(in, H, w16 + w.w_off[3], H, B, O, H, 1, eo, status, s);
+    }
+    // backward: output layer (dW4 as its transpose [256 x 32] = H3^T dY)
+    if (e == cudaSuccess) {
+        TrainEpiGrad eg{grad + w.w_off[3], H, true};
+        e = umma_gemm<32>(bf(t.hT[2]), B, bf(t.dyT), B, H, O, B, splits, eg, status, s);
+    }
+    if (e == cudaSuccess) e = mlp_bias_grad(t.dy, B, O, grad + w.b_off[3], s);
+    if (e == cudaSuccess) {  // dH3 = dY W4 (K = 32) -> dZ3
+        TrainEpiDx ex{t.z[2], bf(t.dz[2]), bf(t.dzT[2]), H, B};
+        e = umma_gemm<256>(bf(t.dy), O, wT + 2 * H * H, O, B, H, O, 1, ex, status, s);
+    }
+    // hidden layers l = 2, 1, 0 (weights W3, W2, W1)
+    for (int l = 2; l >= 0 && e == cudaSuccess; --l) {
+        const int fi = l == 0 ? I : H;
+        const __nv_bfloat16* inT = l == 0 ? bf(t.xT) : bf(t.hT[l - 1]);
+        TrainEpiGrad eg{grad + w.w_off[l], fi, false};
+        if (fi == H) e = umma_gemm<256>(bf(t.dzT[l]), B, inT, B, H, fi, B, splits, eg, status, s);
+        else e = umma_gemm<64>(bf(t.dzT[l]), B, inT, B, H, fi, B, splits, eg, status, s);
+        if (e == cudaSuccess) e = mlp_bias_grad(t.dz[l], B, H, grad + w.b_off[l], s);
+        if (e == cudaSuccess && l > 0) {  // dH_{l-1} = dZ_l W_l -> dZ_{l-1}
+            TrainEpiDx ex{t.z[l - 1], bf(t.dz[l - 1]), bf(t.dzT[l - 1]), H, B};
+            e = umma_gemm<256>(bf(t.dz[l]), H, wT + (size_t)(l - 1) * H * H, H, B, H, H, 1, ex, status, s);
+        }
+    }
+    return e;
 }
 
 }  // namespace mdg

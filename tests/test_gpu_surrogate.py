@@ -82,6 +82,40 @@ def test_forward_matches_oracle(cuda, path, B):
     assert np.all(np.abs(y.cpu().numpy() - yo) <= bound)
 
 
+def test_training_paths_agree_over_steps(cuda):
+    """Eight Adam steps on the tcgen05 path and on the mma.sync path from the same weights and
+    batches: losses within 1% and the weights within 10% of their change (accumulation order
+    and bf16 rounding of the stored activations differ, and Adam's first steps move a weight
+    by about lr whatever the size of its gradient, so the sign of a near-zero gradient
+    matters)."""
+    B = 512
+    layers = _layers(7)
+    x = torch.as_tensor(_inputs(8, B), device=cuda).to(torch.bfloat16)
+    t = torch.zeros((B, mdg.MLP_OUT_PAD), device=cuda)
+    t[:, :mdg.MLP_OUT] = torch.as_tensor(
+        wl.uniform_range(-1, 1, 9, 12, 0, np.arange(B, dtype=np.uint64)[:, None],
+                         np.arange(mdg.MLP_OUT, dtype=np.uint64)[None, :]), device=cuda)
+    w0 = mdg.mlp_flatten(layers).astype(np.float64)
+    out = []
+    for path in (mdg.MLP_PATH_TCGEN05, mdg.MLP_PATH_MMA_SYNC):
+        m = mdg.MLP(B, layers)
+        m.set_train_path(path)
+        loss = torch.zeros(1, device=cuda)
+        losses = []
+        for _ in range(8):
+            m.grad(x, t, loss)
+            losses.append(float(loss))
+            m.adam(1e-3)
+        torch.cuda.synchronize()
+        assert m.status() == 0
+        out.append((np.array(losses), m.params().astype(np.float64)))
+    (la, wa), (lb, wb) = out
+    np.testing.assert_allclose(la, lb, rtol=1e-2)
+    assert la[-1] < la[0]
+    dw = np.abs(wb - w0)
+    assert np.linalg.norm(wa - wb) <= 0.1 * np.linalg.norm(dw)
+
+
 def test_tcgen05_bounded_wait_exit(cuda):
     """The tcgen05 kernel's exit on an expired wait, without a stuck device: with wait bounds
     of zero the first wait that is not already complete (at the latest the epilogue's wait
@@ -112,10 +146,15 @@ def test_tcgen05_bounded_wait_exit(cuda):
     assert np.all(np.abs(y.cpu().numpy() - yo) <= bound)
 
 
-def test_gradients_and_loss_match_oracle(cuda):
-    B = 256
+@pytest.mark.parametrize("path,B", [(mdg.MLP_PATH_TCGEN05, 256), (mdg.MLP_PATH_TCGEN05, 1024),
+                                    (mdg.MLP_PATH_MMA_SYNC, 256)])
+def test_gradients_and_loss_match_oracle(cuda, path, B):
+    """Loss and every gradient of both training paths (tcgen05 with TMEM accumulators, the
+    default; mma.sync) against the FP64 oracle's backward on the same bf16 tensors; B = 1024
+    splits the weight gradients over the batch (two slices added with atomics)."""
     layers = _layers(3)
     m = mdg.MLP(B, layers)
+    m.set_train_path(path)
     x = torch.as_tensor(_inputs(4, B), device=cuda).to(torch.bfloat16)
     t = np.zeros((B, mdg.MLP_OUT_PAD), np.float32)
     t[:, :mdg.MLP_OUT] = wl.uniform_range(-1, 1, 5, 12, 0, np.arange(B, dtype=np.uint64)[:, None],
