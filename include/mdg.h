@@ -599,6 +599,40 @@ int mdg_mlp_set_wait_limits(mdg_mlp m, int32_t try_waits, int32_t polls);
  * if a tensor-core kernel abandoned its work. */
 int mdg_mlp_status(mdg_mlp m, void* stream, uint32_t* bits);
 
+/* One transition of the plain integrator, the surrogate's training data: the RPMs applied
+ * (applied = rpm times rpm_scale elementwise, or rpm when rpm_scale is NULL; device
+ * [n_drones][4], written), the raw inputs of the current state with them (as mdg_features),
+ * one control step of n_substeps with them as RPM actions (the state advances in place), and
+ * the 13-d state change delta = [p, q, v, w] after minus before (device [n_drones][13]).
+ * rpm, rpm_scale, applied and state 16-byte aligned. Errors: as mdg_step, mdg_features. */
+int mdg_transition(mdg_handle h, float* state, const float* rpm, const float* rpm_scale, float* applied, float* raw,
+                   float* delta, int32_t n_substeps, void* stream);
+
+/* Standardisation of a set of N transitions (raw device [N][41], delta device [N][13]) for
+ * training, and the surrogate's normalisation from it (as mdg_mlp_set_normalization):
+ *  1. rows with a non-finite value are dropped;
+ *  2. trim box: per column the quantiles trim_frac and 1 - trim_frac (linear interpolation
+ *     between order statistics) over an evenly strided sample of at most 262144 finite rows,
+ *     widened on each side by margin times their distance; rows outside the box in any column
+ *     are dropped (the chaotic tail of near-coincident downwash heights lives there);
+ *  3. mean and standard deviation (FP64, unbiased) of every column over the kept rows; a
+ *     column whose deviation is below 1e-6 max(|mean|, 1) is scaled by 1;
+ *  4. rows with a standardised input beyond +-ood_z or a standardised target beyond
+ *     +-target_clip are dropped;
+ *  5. out-of-distribution box: the kept inputs' range, widened by 10% of it plus 1e-6;
+ *  6. the kept rows, in their order, truncated to a multiple of 128: x_out device [N][64]
+ *     bf16 (uint16) standardised inputs (zero padded), t_out device [N][32] standardised
+ *     targets (zero padded); *n_kept receives their number, *n_finite the rows of step 1.
+ * Allocates temporary device scratch and synchronises `stream`.
+ * Errors: MDG_ERR_ARG (bad arguments, too few usable rows), MDG_ERR_CUDA. */
+int mdg_mlp_fit_normalization(mdg_mlp m, const float* raw, const float* delta, int64_t N, float trim_frac, float margin,
+                              float ood_z, float target_clip, uint16_t* x_out, float* t_out, int64_t* n_finite,
+                              int64_t* n_kept, void* stream);
+/* The normalisation in use (host arrays: 41 input means, standard deviations, box lower and
+ * upper bounds; 13 output means and standard deviations; any pointer may be NULL). */
+int mdg_mlp_get_normalization(mdg_mlp m, float* in_mean, float* in_std, float* out_mean, float* out_std, float* in_lo,
+                              float* in_hi);
+
 /* Raw surrogate inputs of the current state: raw device [n_drones][41] =
  * [p, q, v, w, rpm (4), 4 nearest neighbours' (p_i - p_j, v_i - v_j)]; rpm device
  * [n_drones][4] are the RPMs to be applied. */

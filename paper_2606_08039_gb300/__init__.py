@@ -102,6 +102,11 @@ _SIGNATURES = {
     "mdg_mlp_set_path": ([_VP, ctypes.c_int32], ctypes.c_int),
     "mdg_mlp_set_wait_limits": ([_VP, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "mdg_mlp_set_train_path": ([_VP, ctypes.c_int32], ctypes.c_int),
+    "mdg_transition": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int32, _VP], ctypes.c_int),
+    "mdg_mlp_fit_normalization": ([_VP, _VP, _VP, ctypes.c_int64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                   ctypes.c_float, _VP, _VP, ctypes.POINTER(ctypes.c_int64),
+                                   ctypes.POINTER(ctypes.c_int64), _VP], ctypes.c_int),
+    "mdg_mlp_get_normalization": ([_VP] * 7, ctypes.c_int),
     "mdg_reset": ([_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_uint64, ctypes.c_uint64, _VP], ctypes.c_int),
     "mdg_set_obs_bias": ([_VP, _VP], ctypes.c_int),
     "mdg_set_rollout_schedule": ([_VP, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
@@ -558,6 +563,19 @@ class Handle:
                                   _ptr(rpm, "rpm", torch.float32, (self.n, 4)),
                                   _ptr(raw, "raw", torch.float32, (self.n, MLP_IN)), _stream(stream)))
 
+    def transition(self, state, rpm, applied, raw, delta, rpm_scale=None, n_substeps: int = 5, stream=None):
+        """One transition of the plain integrator (mdg_transition): applied [n, 4] = rpm
+        (times rpm_scale), raw [n, 41] the inputs of the state with them, one control step,
+        delta [n, 13] the state change."""
+        torch = _torch()
+        _check(lib().mdg_transition(self._h, _ptr(state, "state", torch.float32, (STATE_PLANES, self.n, 4)),
+                                    _ptr(rpm, "rpm", torch.float32, (self.n, 4)),
+                                    _ptr(rpm_scale, "rpm_scale", torch.float32, (self.n, 4)),
+                                    _ptr(applied, "applied", torch.float32, (self.n, 4)),
+                                    _ptr(raw, "raw", torch.float32, (self.n, MLP_IN)),
+                                    _ptr(delta, "delta", torch.float32, (self.n, MLP_OUT)), int(n_substeps),
+                                    _stream(stream)))
+
     # -- output buffers
     def new_obs(self, device="cuda"):
         torch = _torch()
@@ -631,6 +649,27 @@ class MLP:
     def set_normalization(self, in_mean, in_std, out_mean, out_std, in_lo, in_hi):
         arrs = [np.ascontiguousarray(a, np.float32) for a in (in_mean, in_std, out_mean, out_std, in_lo, in_hi)]
         _check(lib().mdg_mlp_set_normalization(self._m, *[a.ctypes.data_as(_VP) for a in arrs]))
+
+    def fit_normalization(self, raw, delta, x_out, t_out, trim_frac: float = 0.005, margin: float = 0.1,
+                          ood_z: float = 4.0, target_clip: float = 8.0, stream=None):
+        """Standardise a set of transitions for training and set the normalisation from it
+        (mdg_mlp_fit_normalization). Returns (finite rows, rows written to x_out / t_out)."""
+        torch = _torch()
+        N = raw.shape[0]
+        n_fin, n_kept = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().mdg_mlp_fit_normalization(
+            self._m, _ptr(raw, "raw", torch.float32, (N, MLP_IN)), _ptr(delta, "delta", torch.float32, (N, MLP_OUT)),
+            int(N), ctypes.c_float(trim_frac), ctypes.c_float(margin), ctypes.c_float(ood_z),
+            ctypes.c_float(target_clip), _ptr(x_out, "x_out", torch.bfloat16, (N, MLP_IN_PAD)),
+            _ptr(t_out, "t_out", torch.float32, (N, MLP_OUT_PAD)), ctypes.byref(n_fin), ctypes.byref(n_kept),
+            _stream(stream)))
+        return n_fin.value, n_kept.value
+
+    def normalization(self):
+        """(in_mean, in_std, out_mean, out_std, in_lo, in_hi) in use (mdg_mlp_get_normalization)."""
+        arrs = [np.zeros(n, np.float32) for n in (MLP_IN, MLP_IN, MLP_OUT, MLP_OUT, MLP_IN, MLP_IN)]
+        _check(lib().mdg_mlp_get_normalization(self._m, *[a.ctypes.data_as(_VP) for a in arrs]))
+        return tuple(arrs)
 
     def standardize(self, raw, x, stream=None):
         torch = _torch()

@@ -290,6 +290,28 @@ int mdg_mlp_forward(mdg_mlp m, const uint16_t* x, float* y, int32_t B, void* str
     return e == cudaSuccess ? MDG_OK : cuda_fail(e, "mdg_mlp_forward");
 }
 
+int mdg_mlp_get_normalization(mdg_mlp m, float* in_mean, float* in_std, float* out_mean, float* out_std, float* in_lo,
+                              float* in_hi)
+{
+    if (!m) return fail(MDG_ERR_ARG, "mdg_mlp_get_normalization: NULL handle");
+    if (!m->norm_set) return fail(MDG_ERR_ARG, "mdg_mlp_get_normalization: the surrogate has no normalisation");
+    std::vector<float> h(4 * MDG_MLP_IN + 2 * MDG_MLP_OUT);
+    Guard g(m->device);
+    cudaError_t e = cudaMemcpy(h.data(), m->norm, h.size() * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "mdg_mlp_get_normalization");
+    for (int k = 0; k < MDG_MLP_IN; ++k) {
+        if (in_mean) in_mean[k] = h[k];
+        if (in_std) in_std[k] = 1.f / h[MDG_MLP_IN + k];
+        if (in_lo) in_lo[k] = h[2 * MDG_MLP_IN + k];
+        if (in_hi) in_hi[k] = h[3 * MDG_MLP_IN + k];
+    }
+    for (int k = 0; k < MDG_MLP_OUT; ++k) {
+        if (out_mean) out_mean[k] = h[4 * MDG_MLP_IN + k];
+        if (out_std) out_std[k] = h[4 * MDG_MLP_IN + MDG_MLP_OUT + k];
+    }
+    return MDG_OK;
+}
+
 int mdg_mlp_grad(mdg_mlp m, const uint16_t* x, const float* t, int32_t B, float* loss_out, void* stream)
 {
     if (!m || !x || !t) return fail(MDG_ERR_ARG, "mdg_mlp_grad: NULL argument");

@@ -567,8 +567,7 @@ __global__ void __launch_bounds__(kGemmThreads) umma_gemm_kernel(const __nv_bflo
         for (int cc = 0; cc < BN; cc += 16) {
             float v[16];
             tmem_ld16(t_row + cc, v);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) loss += epi(m0 + row, n0 + cc + i, v[i]);
+            loss += epi.chunk(m0 + row, n0 + cc, v);
         }
         epi.finish(loss);
     }
@@ -585,6 +584,35 @@ __device__ __forceinline__ float silu_grad_train(float z)
     return sg * (1.f + z * (1.f - sg));
 }
 
+// The epilogues take the 16 consecutive accumulator columns n0 .. n0 + 15 of row m (one
+// thread per row): row-major outputs are written 16 bytes at a time, transposed outputs one
+// element per thread, consecutive rows of a warp side by side.
+__device__ __forceinline__ void store_bf16x16(__nv_bfloat16* dst, const float v[16])
+{
+    uint32_t w[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const __nv_bfloat162 p = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        w[i] = *reinterpret_cast<const uint32_t*>(&p);
+    }
+    reinterpret_cast<uint4*>(dst)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    reinterpret_cast<uint4*>(dst)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+__device__ __forceinline__ void store_f32x16(float* dst, const float v[16])
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        reinterpret_cast<float4*>(dst)[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+}
+__device__ __forceinline__ void load_f32x16(const float* src, float v[16])
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float4 t = reinterpret_cast<const float4*>(src)[i];
+        v[4 * i] = t.x, v[4 * i + 1] = t.y, v[4 * i + 2] = t.z, v[4 * i + 3] = t.w;
+    }
+}
+
 // Hidden layer forward: z = acc + b[n] (FP32, kept for the backward pass), h = bf16(silu(z))
 // row-major and transposed (the transposed copy is the K-major operand of the weight gradient).
 struct TrainEpiHidden {
@@ -593,13 +621,18 @@ struct TrainEpiHidden {
     __nv_bfloat16* h;
     __nv_bfloat16* hT;
     int ld, ldT;
-    __device__ __forceinline__ float operator()(int m, int n, float acc) const
+    __device__ __forceinline__ float chunk(int m, int n0, const float acc[16]) const
     {
-        const float zz = acc + bias[n];
-        z[(size_t)m * ld + n] = zz;
-        const __nv_bfloat16 hv = __float2bfloat16_rn(silu_train(zz));
-        h[(size_t)m * ld + n] = hv;
-        hT[(size_t)n * ldT + m] = hv;
+        float zz[16], hv[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            zz[i] = acc[i] + bias[n0 + i];
+            hv[i] = silu_train(zz[i]);
+        }
+        store_f32x16(z + (size_t)m * ld + n0, zz);
+        store_bf16x16(h + (size_t)m * ld + n0, hv);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) hT[(size_t)(n0 + i) * ldT + m] = __float2bfloat16_rn(hv[i]);
         return 0.f;
     }
     __device__ __forceinline__ void finish(float) const {}
@@ -616,15 +649,23 @@ struct TrainEpiOut {
     float* loss_acc;
     int ld, ldT, n_valid;
     float grad_scale, loss_scale;
-    __device__ __forceinline__ float operator()(int m, int n, float acc) const
+    __device__ __forceinline__ float chunk(int m, int n0, const float acc[16]) const
     {
-        const float yy = acc + bias[n];
-        y[(size_t)m * ld + n] = yy;
-        const float d = n < n_valid ? yy - target[(size_t)m * ld + n] : 0.f;
-        const __nv_bfloat16 g = __float2bfloat16_rn(grad_scale * d);
-        dy[(size_t)m * ld + n] = g;
-        dyT[(size_t)n * ldT + m] = g;
-        return d * d * loss_scale;
+        float yy[16], tt[16], g[16];
+        load_f32x16(target + (size_t)m * ld + n0, tt);
+        float loss = 0.f;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            yy[i] = acc[i] + bias[n0 + i];
+            const float d = n0 + i < n_valid ? yy[i] - tt[i] : 0.f;
+            g[i] = grad_scale * d;
+            loss += d * d * loss_scale;
+        }
+        store_f32x16(y + (size_t)m * ld + n0, yy);
+        store_bf16x16(dy + (size_t)m * ld + n0, g);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) dyT[(size_t)(n0 + i) * ldT + m] = __float2bfloat16_rn(g[i]);
+        return loss;
     }
     __device__ __forceinline__ void finish(float loss) const
     {
@@ -640,24 +681,37 @@ struct TrainEpiDx {
     __nv_bfloat16* dz;
     __nv_bfloat16* dzT;
     int ld, ldT;
-    __device__ __forceinline__ float operator()(int m, int n, float acc) const
+    __device__ __forceinline__ float chunk(int m, int n0, const float acc[16]) const
     {
-        const __nv_bfloat16 g = __float2bfloat16_rn(acc * silu_grad_train(zprev[(size_t)m * ld + n]));
-        dz[(size_t)m * ld + n] = g;
-        dzT[(size_t)n * ldT + m] = g;
+        float zp[16], g[16];
+        load_f32x16(zprev + (size_t)m * ld + n0, zp);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) g[i] = acc[i] * silu_grad_train(zp[i]);
+        store_bf16x16(dz + (size_t)m * ld + n0, g);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) dzT[(size_t)(n0 + i) * ldT + m] = __float2bfloat16_rn(g[i]);
         return 0.f;
     }
     __device__ __forceinline__ void finish(float) const {}
 };
 
-// Weight gradient (split over K = the batch): g[m][n] (or g[n][m] when transposed) += acc.
+// Weight gradient (split over K = the batch): g[m][n] (or g[n][m] when transposed) += acc,
+// four columns per vector reduction in the row-major case.
 struct TrainEpiGrad {
     float* g;
     int ld;
     bool transpose;
-    __device__ __forceinline__ float operator()(int m, int n, float acc) const
+    __device__ __forceinline__ float chunk(int m, int n0, const float acc[16]) const
     {
-        atomicAdd(transpose ? g + (size_t)n * ld + m : g + (size_t)m * ld + n, acc);
+        if (transpose) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) atomicAdd(g + (size_t)(n0 + i) * ld + m, acc[i]);
+        } else {
+            float4* row = reinterpret_cast<float4*>(g + (size_t)m * ld + n0);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                atomicAdd(row + i, make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]));
+        }
         return 0.f;
     }
     __device__ __forceinline__ void finish(float) const {}
@@ -794,7 +848,7 @@ cudaError_t mlp_grad_umma(const MlpView& w, const TrainBuffers& t, const void* x
     const __nv_bfloat16* wT = static_cast<const __nv_bfloat16*>(t.wT);
     auto bf = [](void* p) { return static_cast<__nv_bfloat16*>(p); };
     // the weight gradients are split over the batch and added up with atomics
-    const int splits = B / 512 > 0 ? B / 512 : 1;
+    const int splits = B / 256 > 0 ? B / 256 : 1;
     cudaError_t e = cudaMemsetAsync(grad, 0, (size_t)MDG_MLP_PARAMS * 4, s);
     if (e == cudaSuccess) e = transpose_bf16(x, t.xT, B, I, s);
     // forward
@@ -802,7 +856,7 @@ cudaError_t mlp_grad_umma(const MlpView& w, const TrainBuffers& t, const void* x
     int fan_in = I;
     for (int l = 0; l < 3 && e == cudaSuccess; ++l) {
         TrainEpiHidden ep{w.master + w.b_off[l], t.z[l], bf(t.h[l]), bf(t.hT[l]), H, B};
-        e = umma_gemm<256>(in, fan_in, w16 + w.w_off[l], fan_in, B, H, fan_in, 1, ep, status, s);
+        e = umma_gemm<128>(in, fan_in, w16 + w.w_off[l], fan_in, B, H, fan_in, 1, ep, status, s);
         in = bf(t.h[l]);
         fan_in = H;
     }
@@ -819,19 +873,19 @@ cudaError_t mlp_grad_umma(const MlpView& w, const TrainBuffers& t, const void* x
     if (e == cudaSuccess) e = mlp_bias_grad(t.dy, B, O, grad + w.b_off[3], s);
     if (e == cudaSuccess) {  // dH3 = dY W4 (K = 32) -> dZ3
         TrainEpiDx ex{t.z[2], bf(t.dz[2]), bf(t.dzT[2]), H, B};
-        e = umma_gemm<256>(bf(t.dy), O, wT + 2 * H * H, O, B, H, O, 1, ex, status, s);
+        e = umma_gemm<128>(bf(t.dy), O, wT + 2 * H * H, O, B, H, O, 1, ex, status, s);
     }
     // hidden layers l = 2, 1, 0 (weights W3, W2, W1)
     for (int l = 2; l >= 0 && e == cudaSuccess; --l) {
         const int fi = l == 0 ? I : H;
         const __nv_bfloat16* inT = l == 0 ? bf(t.xT) : bf(t.hT[l - 1]);
         TrainEpiGrad eg{grad + w.w_off[l], fi, false};
-        if (fi == H) e = umma_gemm<256>(bf(t.dzT[l]), B, inT, B, H, fi, B, splits, eg, status, s);
+        if (fi == H) e = umma_gemm<128>(bf(t.dzT[l]), B, inT, B, H, fi, B, splits, eg, status, s);
         else e = umma_gemm<64>(bf(t.dzT[l]), B, inT, B, H, fi, B, splits, eg, status, s);
         if (e == cudaSuccess) e = mlp_bias_grad(t.dz[l], B, H, grad + w.b_off[l], s);
         if (e == cudaSuccess && l > 0) {  // dH_{l-1} = dZ_l W_l -> dZ_{l-1}
             TrainEpiDx ex{t.z[l - 1], bf(t.dz[l - 1]), bf(t.dzT[l - 1]), H, B};
-            e = umma_gemm<256>(bf(t.dz[l]), H, wT + (size_t)(l - 1) * H * H, H, B, H, H, 1, ex, status, s);
+            e = umma_gemm<128>(bf(t.dz[l]), H, wT + (size_t)(l - 1) * H * H, H, B, H, H, 1, ex, status, s);
         }
     }
     return e;

@@ -1,19 +1,14 @@
 """Training and evaluation of the learned surrogate on transitions of the simulator itself.
 
 The network (MLP, C ABI mdg_mlp_*) learns the 13-d state change of one control step from
-the 41 inputs mdg_features builds (state, RPMs, 4 nearest neighbours' relative state).
-Transitions come from the GPU simulator on the full-aero swarm: PID RPMs towards random
-waypoints, each motor perturbed by U[1 - perturb, 1 + perturb] for diversity, then one
-plain control step. Every computation of the network (forward, backward, Adam, input
-standardisation) runs in the library's kernels; this module only moves tensors:
-shuffling, batching and the normalisation statistics.
-
-Normalisation: transitions are trimmed per dimension to the central 99% of inputs and
-targets (plus a 10% margin of that range) — the excluded tail is dominated by the chaotic
-near-coincident heights of the downwash law — and the mean and standard deviation of the
-kept set standardise inputs and targets (scale 1 where a feature is constant). The
-surrogate step sends an environment to the plain integrator when a drone's standardised
-input leaves +-ood_z or its raw input leaves the kept set's box (plus 10%).
+the 41 inputs the library builds (state, RPMs, 4 nearest neighbours' relative state).
+Transitions come from the GPU simulator (mdg_transition: the inputs, one plain control step,
+the state change), on the full-aero swarm with PID RPMs towards random waypoints, each motor
+perturbed by a factor U[1 - perturb, 1 + perturb] drawn by the input generator, or on the
+dense swarm with its RPM actions. The standardisation of the training set (trim, mean and
+standard deviation, out-of-distribution box: mdg_mlp_fit_normalization) and every
+computation of the network (forward, backward, Adam) run in the library's kernels; this
+module only moves tensors: batching, shuffling and the learning-rate schedule.
 """
 from __future__ import annotations
 
@@ -55,6 +50,7 @@ def generate_transitions(n_envs: int, steps: int, seed: int, device, perturb: fl
     raw = torch.empty((steps, sw.n, mdg.MLP_IN), dtype=torch.float32, device=device)
     delta = torch.empty((steps, sw.n, mdg.MLP_OUT), dtype=torch.float32, device=device)
     rpm = torch.empty((sw.n, 4), dtype=torch.float32, device=device)
+    applied = torch.empty((sw.n, 4), dtype=torch.float32, device=device)
     idx = np.arange(sw.n, dtype=np.uint64)[:, None]
     comp = np.arange(4, dtype=np.uint64)[None, :]
     for k in range(steps):
@@ -63,72 +59,43 @@ def generate_transitions(n_envs: int, steps: int, seed: int, device, perturb: fl
             state.copy_(mdg.pack_state(fresh.p, fresh.q, fresh.v, fresh.w, device=device))
         if workload == "full_aero":
             h.pid(state, wp, rpm)
-            noise = wl.uniform_range(1.0 - perturb, 1.0 + perturb, seed, wl.S_ACT, 1000 + k, idx, comp)
-            rpm.mul_(torch.as_tensor(noise, device=device))
+            scale = torch.as_tensor(wl.uniform_range(1.0 - perturb, 1.0 + perturb, seed, wl.S_ACT, 1000 + k, idx, comp),
+                                    device=device)
         else:
             rpm.copy_(torch.as_tensor(wl.rpm_actions(seed, sw.n, k, hover), device=device))
-        h.features(state, rpm, raw[k])
-        before = state13(state).clone()
-        h.step(state, rpm, mdg.ACT_RPM, n_substeps)
-        delta[k] = state13(state) - before
+            scale = None
+        h.transition(state, rpm, applied, raw[k], delta[k], rpm_scale=scale, n_substeps=n_substeps)
     return raw.reshape(-1, mdg.MLP_IN), delta.reshape(-1, mdg.MLP_OUT)
 
 
-def _trim_box(a, frac: float = 0.005, margin: float = 0.1):
-    """Per-column [q(frac) - margin r, q(1 - frac) + margin r], r the quantile range, on an
-    evenly strided sample of at most 262144 rows."""
-    torch = _torch()
-    stride = max(1, a.shape[0] // 262144)
-    q = torch.quantile(a[::stride].float(), torch.tensor([frac, 1.0 - frac], device=a.device), dim=0)
-    r = q[1] - q[0]
-    return q[0] - margin * r, q[1] + margin * r
-
-
-def _mean_std(a):
-    torch = _torch()
-    mean = a.double().mean(0)
-    std = a.double().std(0)
-    std = torch.where(std > 1e-6 * torch.clamp(mean.abs(), min=1.0), std, torch.ones_like(std))
-    return mean.float(), std.float()
-
-
 class Dataset:
-    """Standardised training set (bf16 inputs [N, 64], FP32 targets [N, 32]) and its statistics."""
+    """Standardised training set (bf16 inputs [N, 64], FP32 targets [N, 32]) of a set of
+    transitions and its statistics (mdg_mlp_fit_normalization, held by a small network that
+    carries the normalisation: attach() gives it to the network that trains)."""
 
     def __init__(self, raw, delta, ood_z: float = 4.0, target_clip: float = 8.0):
         torch = _torch()
         import paper_2606_08039_gb300 as mdg
-        finite = torch.isfinite(raw).all(1) & torch.isfinite(delta).all(1)
-        raw, delta = raw[finite], delta[finite]
-        ilo, ihi = _trim_box(raw)
-        olo, ohi = _trim_box(delta)
-        keep = ((raw >= ilo) & (raw <= ihi)).all(1) & ((delta >= olo) & (delta <= ohi)).all(1)
-        raw, delta = raw[keep], delta[keep]
-        self.in_mean, self.in_std = _mean_std(raw)
-        self.out_mean, self.out_std = _mean_std(delta)
-        zin = (raw - self.in_mean) / self.in_std
-        keep2 = (zin.abs() <= ood_z).all(1) & (((delta - self.out_mean) / self.out_std).abs() <= target_clip).all(1)
-        self.kept_fraction = float(keep.float().mean()) * float(keep2.float().mean())
-        raw = raw[keep2]
-        zout = ((delta - self.out_mean) / self.out_std)[keep2]
-        lo, hi = raw.min(0).values, raw.max(0).values
-        pad = 0.1 * (hi - lo) + 1e-6
-        self.in_lo, self.in_hi = lo - pad, hi + pad
+        N = raw.shape[0]
+        self._holder = mdg.MLP(128)
+        x = torch.empty((N, mdg.MLP_IN_PAD), dtype=torch.bfloat16, device=raw.device)
+        t = torch.empty((N, mdg.MLP_OUT_PAD), dtype=torch.float32, device=raw.device)
+        n_fin, n = self._holder.fit_normalization(raw, delta, x, t, ood_z=ood_z, target_clip=target_clip)
+        self.x, self.t = x[:n], t[:n]
+        self.kept_fraction = n / max(1, n_fin)
         self.ood_z = ood_z
-        n = raw.shape[0] // 128 * 128
-        self.raw = raw[:n]
-        self.t = torch.zeros((n, mdg.MLP_OUT_PAD), dtype=torch.float32, device=raw.device)
-        self.t[:, :mdg.MLP_OUT] = zout[:n]
-        self.x = torch.empty((n, mdg.MLP_IN_PAD), dtype=torch.bfloat16, device=raw.device)
+        (in_mean, in_std, out_mean, out_std, in_lo, in_hi) = self._holder.normalization()
+        dev = raw.device
+        self.in_mean, self.in_std = torch.as_tensor(in_mean, device=dev), torch.as_tensor(in_std, device=dev)
+        self.out_mean, self.out_std = torch.as_tensor(out_mean, device=dev), torch.as_tensor(out_std, device=dev)
+        self.in_lo, self.in_hi = torch.as_tensor(in_lo, device=dev), torch.as_tensor(in_hi, device=dev)
 
     def stats(self):
-        return [t.detach().cpu().numpy().astype(np.float32) for t in
-                (self.in_mean, self.in_std, self.out_mean, self.out_std, self.in_lo, self.in_hi)]
+        return self._holder.normalization()
 
     def attach(self, mlp):
-        """Give the network these statistics and standardise the inputs with its kernel."""
+        """Give the network this set's normalisation."""
         mlp.set_normalization(*self.stats())
-        mlp.standardize(self.raw, self.x)
 
     def __len__(self):
         return self.x.shape[0]

@@ -164,17 +164,31 @@ def test_model_control_step_matches_oracle(cuda, model, recipe):
     _check_obs(xg, ag, sw.drones_per_env, kin, idx, rel)
 
 
-def test_surrogate_step_refuses_rk4(cuda):
-    sw = wl.full_aero(12, n_envs=32)
+def test_surrogate_step_with_rk4_falls_back_to_rk4(cuda):
+    """With RK4 constants, a surrogate step whose environments are all out of distribution
+    (a box that excludes everything) is the plain RK4 control step: the PID's RPMs and the
+    fallback's RK4 substeps against the oracle's RK4 control step within the horizon bound."""
+    sw = spread_heights(wl.full_aero(12, n_envs=32))
     c, _ = _pair("cf2x", rk4=True)
     h = mdg.Handle(sw.drones_per_env, sw.flags, c)
     m = mdg.MLP(128, wl.mlp_init(1))
     z = np.zeros(mdg.MLP_IN, np.float32)
-    m.set_normalization(z, z + 1, np.zeros(mdg.MLP_OUT, np.float32), np.ones(mdg.MLP_OUT, np.float32), z - 1, z + 1)
-    state = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=cuda)
-    with pytest.raises(mdg.MdgError) as e:
-        m.step(h, state, torch.as_tensor(wl.waypoints(1, sw.n), device=cuda), mdg.ACT_PID)
-    assert e.value.code == mdg.ERR_UNSUPPORTED
+    m.set_normalization(z, z + 1, np.zeros(mdg.MLP_OUT, np.float32), np.ones(mdg.MLP_OUT, np.float32), z - 1, z - 1)
+    s_sur = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=cuda)
+    x0, i0, a0 = oracle_arrays(s_sur)
+    wp = wl.waypoints(1, sw.n)
+    nfb = torch.zeros(1, dtype=torch.int32, device=cuda)
+    m.step(h, s_sur, torch.as_tensor(wp, device=cuda), mdg.ACT_PID, 5, 4.0, nfb)
+    torch.cuda.synchronize()
+    assert int(nfb) == sw.n_envs
+    xg, ig, _ = oracle_arrays(s_sur)
+    _, P = _pair("cf2x", rk4=True)
+    layout = (sw.drones_per_env, sw.flags)
+    acts = np.full(sw.n_envs, mdg.ACT_PID)
+    xo, io, _ = oracle_step(P, layout, x0, i0, a0, wp, acts, 5)
+    resp = tolerance_response(P, layout, x0, i0, a0, wp, acts, 5)
+    assert_horizon_close(xg, xo, resp, 5, what="RK4 fallback")
+    assert h.status()[0] == mdg.OK
 
 
 def _with_gnd_rotor(model, rk4):

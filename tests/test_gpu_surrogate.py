@@ -375,3 +375,86 @@ def test_surrogate_step_paths_agree(cuda, trained):
     tol = 0.05 * data.out_std.cpu().numpy().astype(np.float64)
     assert np.all(np.abs(out[1] - out[0]) <= tol[None, :])
     assert h.status()[0] == mdg.OK
+
+
+def test_transition_is_features_then_step(cuda):
+    """mdg_transition: the applied RPMs are rpm times rpm_scale, the inputs are mdg_features of
+    the state with them, the state advances by mdg_step, and delta is after minus before."""
+    sw = wl.full_aero(14, n_envs=200)
+    h = mdg.Handle(sw.drones_per_env, sw.flags)
+    s_a = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=cuda)
+    s_b = s_a.clone()
+    rpm = torch.as_tensor(wl.rpm_actions(14, sw.n, 0, HOVER), device=cuda)
+    scale = torch.as_tensor(wl.uniform_range(0.9, 1.1, 14, 13, 0, np.arange(sw.n, dtype=np.uint64)[:, None],
+                                             np.arange(4, dtype=np.uint64)[None, :]), device=cuda)
+    applied = torch.empty_like(rpm)
+    raw = torch.empty((sw.n, mdg.MLP_IN), device=cuda)
+    delta = torch.empty((sw.n, mdg.MLP_OUT), device=cuda)
+    h.transition(s_a, rpm, applied, raw, delta, rpm_scale=scale)
+    ref_rpm = rpm * scale
+    raw_b = torch.empty_like(raw)
+    before = sg.state13(s_b).clone()
+    h.features(s_b, ref_rpm, raw_b)
+    h.step(s_b, ref_rpm, mdg.ACT_RPM, 5)
+    torch.cuda.synchronize()
+    assert torch.equal(applied, ref_rpm)
+    assert torch.equal(raw, raw_b) and torch.equal(s_a, s_b)
+    assert torch.equal(delta, sg.state13(s_b) - before)
+
+
+def test_fit_normalization_matches_its_definition(cuda):
+    """mdg_mlp_fit_normalization against the same steps in numpy (float64): non-finite rows
+    dropped; per column the 0.5% / 99.5% quantiles (linear interpolation) of an evenly strided
+    sample, widened by 10% of their distance, as the trim box; FP64 mean and unbiased standard
+    deviation of the kept rows (scale 1 for a constant column); rows with a standardised input
+    beyond +-4 or target beyond +-8 dropped; the kept inputs' range widened by 10% plus 1e-6 as
+    the out-of-distribution box; the standardised rows in order, truncated to a multiple of 128."""
+    rng = np.random.default_rng(5)
+    N = 300_000  # above the 262144-row sample: stride 1 (the stride is 2 only from 524288 rows)
+    raw = rng.standard_normal((N, mdg.MLP_IN)).astype(np.float32) * np.linspace(0.1, 3, mdg.MLP_IN)[None, :].astype(np.float32)
+    delta = rng.standard_normal((N, mdg.MLP_OUT)).astype(np.float32)
+    raw[:, 5] = 2.5  # a constant column
+    heavy = rng.random(N) < 0.01  # a heavy tail the trim removes
+    delta[heavy, 3] *= 1e3
+    raw[rng.integers(0, N, 50), 7] = np.nan
+    delta[rng.integers(0, N, 50), 2] = np.inf
+    m = mdg.MLP(128)
+    x = torch.empty((N, mdg.MLP_IN_PAD), dtype=torch.bfloat16, device=cuda)
+    t = torch.empty((N, mdg.MLP_OUT_PAD), device=cuda)
+    n_fin, n_kept = m.fit_normalization(torch.as_tensor(raw, device=cuda), torch.as_tensor(delta, device=cuda), x, t)
+    in_mean, in_std, out_mean, out_std, in_lo, in_hi = m.normalization()
+    # the definition, in numpy
+    A = np.concatenate([raw, delta], 1).astype(np.float64)
+    fin = np.isfinite(A).all(1)
+    F = A[fin]
+    assert n_fin == F.shape[0]
+    stride = max(1, F.shape[0] // 262144)
+    S = F[::stride]
+    qlo, qhi = np.quantile(S, 0.005, axis=0), np.quantile(S, 0.995, axis=0)
+    r = qhi - qlo
+    keep1 = ((F >= qlo - 0.1 * r) & (F <= qhi + 0.1 * r)).all(1)
+    K1 = F[keep1]
+    mean = K1.mean(0)
+    sd = K1.std(0, ddof=1)
+    sd = np.where(sd > 1e-6 * np.maximum(np.abs(mean), 1.0), sd, 1.0)
+    np.testing.assert_allclose(in_mean, mean[:mdg.MLP_IN], rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(out_mean, mean[mdg.MLP_IN:], rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(in_std, sd[:mdg.MLP_IN], rtol=1e-5)
+    np.testing.assert_allclose(out_std, sd[mdg.MLP_IN:], rtol=1e-5)
+    assert in_std[5] == 1.0
+    Z = (K1 - mean) / sd
+    keep2 = (np.abs(Z[:, :mdg.MLP_IN]) <= 4.0).all(1) & (np.abs(Z[:, mdg.MLP_IN:]) <= 8.0).all(1)
+    K2 = K1[keep2]
+    assert abs(K2.shape[0] // 128 * 128 - n_kept) <= 128  # boundary rows may round either way in float32
+    lo, hi = K2[:, :mdg.MLP_IN].min(0), K2[:, :mdg.MLP_IN].max(0)
+    pad = 0.1 * (hi - lo) + 1e-6
+    np.testing.assert_allclose(in_lo, lo - pad, rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(in_hi, hi + pad, rtol=1e-5, atol=1e-5)
+    # the emitted rows: the kept rows in order, standardised
+    xs = x[:n_kept].float().cpu().numpy()
+    ts = t[:n_kept].cpu().numpy()
+    n_cmp = min(n_kept, K2.shape[0]) // 2  # rows before any boundary difference
+    zin = (K2[:n_cmp, :mdg.MLP_IN] - mean[:mdg.MLP_IN]) / sd[:mdg.MLP_IN]
+    np.testing.assert_allclose(xs[:n_cmp, :mdg.MLP_IN], zin, rtol=1e-2, atol=1e-2)
+    assert np.all(xs[:, mdg.MLP_IN:] == 0) and np.all(ts[:, mdg.MLP_OUT:] == 0)
+    np.testing.assert_allclose(ts[:n_cmp, :mdg.MLP_OUT], Z[keep2][:n_cmp, mdg.MLP_IN:], rtol=1e-4, atol=1e-4)
