@@ -465,17 +465,17 @@ def nonfinite_fraction(states) -> float:
     return bad / sum(int(st.shape[1]) for st in states)
 
 
-def episode_line(n: int, world: int, ep_ms: float, peaks, flops_step: float) -> dict:
-    value = throughput(n * N_SUB * EPISODE, world, EPISODE_REPS, ep_ms)
+def episode_line(n: int, world: int, ep_ms: float, peaks, flops_step: float, episode: int = EPISODE) -> dict:
+    value = throughput(n * N_SUB * episode, world, EPISODE_REPS, ep_ms)
     sec = ep_ms / EPISODE_REPS * 1e-3
-    nbytes = n * (2 * (STATE_BYTES + INTEG_BYTES) + ACTION_BYTES + EPISODE * BYTES_OBS_PER_DRONE_STEP)
-    roof = binding_roofline(nbytes, flops_step * EPISODE, sec, peaks)
+    nbytes = n * (2 * (STATE_BYTES + INTEG_BYTES) + ACTION_BYTES + episode * BYTES_OBS_PER_DRONE_STEP)
+    roof = binding_roofline(nbytes, flops_step * episode, sec, peaks)
     roof["kernel"] = "rollout_kernel<obs every step>"
-    return {"what": f"the {EPISODE}-control-step episode as one persistent rollout per launch (mdg_rollout, "
+    return {"what": f"the {episode}-control-step episode as one persistent rollout per launch (mdg_rollout, "
                     "observations of every step written), L2 flushed between episodes; the headline value "
                     "above is one control step per launch",
             "value": value, "unit": UNIT, "ms_per_episode": ep_ms / EPISODE_REPS, "episodes": EPISODE_REPS,
-            "us_per_control_step": ep_ms / EPISODE_REPS / EPISODE * 1e3,
+            "us_per_control_step": ep_ms / EPISODE_REPS / episode * 1e3,
             "roofline": roof}
 
 
@@ -1091,6 +1091,8 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="mdg", choices=["mdg", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--episode-steps", type=int, default=EPISODE,
+                    help="full_aero: control steps of the persistent-episode leg (the workload's episode: 1000)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="full_aero",
                     choices=["full_aero", "uneven", "dense", "single", "surrogate", "surrogate_dense", "mlp",
@@ -1328,9 +1330,10 @@ def main() -> None:
     # state stays in registers across steps, the PID waypoints are fixed for the episode and
     # the observations of every step are written ([K][n] buffers, 12.6 GB). L2 flushed
     # between episodes.
-    ep_kin = torch.empty((EPISODE,) + tuple(kin.shape), dtype=kin.dtype, device=dev)
-    ep_idx = torch.empty((EPISODE,) + tuple(idx.shape), dtype=idx.dtype, device=dev)
-    ep_rel = torch.empty((EPISODE,) + tuple(rel.shape), dtype=rel.dtype, device=dev)
+    episode = args.episode_steps
+    ep_kin = torch.empty((episode,) + tuple(kin.shape), dtype=kin.dtype, device=dev)
+    ep_idx = torch.empty((episode,) + tuple(idx.shape), dtype=idx.dtype, device=dev)
+    ep_rel = torch.empty((episode,) + tuple(rel.shape), dtype=rel.dtype, device=dev)
     ep_starts = [torch.cuda.Event(enable_timing=True) for _ in range(EPISODE_REPS)]
     ep_ends = [torch.cuda.Event(enable_timing=True) for _ in range(EPISODE_REPS)]
     for i in range(1 + EPISODE_REPS):
@@ -1338,7 +1341,7 @@ def main() -> None:
         flush_l2()
         if i:
             ep_starts[i - 1].record(stream)
-        h.rollout(state, wp, act_type, N_SUB, EPISODE, mdg.OBS_EVERY_STEP, ep_kin, ep_idx, ep_rel, stream=stream)
+        h.rollout(state, wp, act_type, N_SUB, episode, mdg.OBS_EVERY_STEP, ep_kin, ep_idx, ep_rel, stream=stream)
         if i:
             ep_ends[i - 1].record(stream)
     torch.cuda.synchronize()
@@ -1392,7 +1395,7 @@ def main() -> None:
             "wall_s_timed_region": wall,
             "nonfinite_during_timing": nonfinite,
             "nonfinite_fraction_after_timing": nonfinite_frac,
-            "episode": episode_line(sw.n, world, ep_ms, peaks, flops_launch),
+            "episode": episode_line(sw.n, world, ep_ms, peaks, flops_launch, episode),
             "isolated_step": {
                 "what": "swarm 0 alone, L2 flushed (512 MiB written, then read back) before every step, every "
                         "step bracketed by its own events: one launch's latency and timestamps included per step",
