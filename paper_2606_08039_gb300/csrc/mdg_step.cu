@@ -361,26 +361,9 @@ __device__ __forceinline__ float downwash_pair(const float4 o, float px, float p
 // otherwise it visits all N and the drone's own entry (dz = 0) drops out of the gate.
 template <int kN>
 __device__ __forceinline__ float downwash_sum(const float4* env_pos, int N_rt, int jl, float px, float py, float pz,
-                                              const DevConsts& c, const int* cand = nullptr, int n_cand = 0)
+                                              const DevConsts& c)
 {
     float acc = 0.f;
-    if (cand) {
-        // only the sources of the warp's list (warp_sources_above): the others add exact zeros
-        // here, so the sum over the list, in the same index order, is the same value
-        int k = 0;
-        for (; k + 4 <= n_cand; k += 4) {
-            const float f0 = downwash_pair(env_pos[cand[k]], px, py, pz, c);
-            const float f1 = downwash_pair(env_pos[cand[k + 1]], px, py, pz, c);
-            const float f2 = downwash_pair(env_pos[cand[k + 2]], px, py, pz, c);
-            const float f3 = downwash_pair(env_pos[cand[k + 3]], px, py, pz, c);
-            acc += f0;
-            acc += f1;
-            acc += f2;
-            acc += f3;
-        }
-        for (; k < n_cand; ++k) acc += downwash_pair(env_pos[cand[k]], px, py, pz, c);
-        return acc;
-    }
     if (kN > 0 && kN <= 8 && (kN & (kN - 1)) == 0) {
 #pragma unroll
         for (int i = 1; i < (kN > 0 ? kN : 1); ++i) acc += downwash_pair(env_pos[(jl + i) & (kN - 1)], px, py, pz, c);
@@ -392,27 +375,6 @@ __device__ __forceinline__ float downwash_sum(const float4* env_pos, int N_rt, i
         for (int j = 0; j < N_rt; ++j) acc += downwash_pair(env_pos[j], px, py, pz, c);
     }
     return acc;
-}
-
-// The sources of a 64-drone environment that can press on some drone of this warp: source i
-// adds to drone j only if fl(z_i - z_j) > dz_min, and fl(z_i - z) falls as z rises, so a source
-// with fl(z_i - zmin) <= dz_min (zmin the warp's lowest active drone) adds an exact zero to every
-// drone of the warp. The kept sources' indices go to cand in increasing order (two ballots over
-// the environment's 64 positions); returns their number. Every lane of the warp calls this.
-__device__ __forceinline__ int warp_sources_above(const float4* env_pos, float pz, bool active, float dz_min, int* cand)
-{
-    float zmin = active ? pz : INFINITY;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) zmin = fminf(zmin, __shfl_xor_sync(0xffffffffu, zmin, o));
-    const int lane = threadIdx.x & 31;
-    const bool k0 = env_pos[lane].z - zmin > dz_min;
-    const bool k1 = env_pos[lane + 32].z - zmin > dz_min;
-    const unsigned m0 = __ballot_sync(0xffffffffu, k0), m1 = __ballot_sync(0xffffffffu, k1);
-    const unsigned below = (1u << lane) - 1u;
-    if (k0) cand[__popc(m0 & below)] = lane;
-    if (k1) cand[__popc(m0) + __popc(m1 & below)] = lane + 32;
-    __syncwarp();
-    return __popc(m0) + __popc(m1);
 }
 
 // Kernel variants beyond the compile-time physics subsets 0-7 (all take the physics flags
@@ -462,8 +424,7 @@ __device__ __forceinline__ float ground_increment(const Motor& m, float pz, floa
 // kFlags = 8 / kN <= 0 take them from the runtime arguments.
 template <int kFlags, int kN>
 __device__ __forceinline__ void substep(Drone& d, const Motor& m, int flags_rt, const float4* env_pos, int N_rt, int jl,
-                                        const DevConsts& c, const float3 fe = float3{}, const int* cand = nullptr,
-                                        int n_cand = 0)
+                                        const DevConsts& c, const float3 fe = float3{})
 {
     const int flags = fixed_subset(kFlags) >= 0 ? fixed_subset(kFlags) : flags_rt;
     const float dt = c.dt_sim;
@@ -499,7 +460,7 @@ __device__ __forceinline__ void substep(Drone& d, const Motor& m, int flags_rt, 
         F[1] += kxy * d.v[1] + kr * r1;
         F[2] += kxy * d.v[2] + kr * r2;
     }
-    if (flags & MDG_DW) F[2] -= downwash_sum<kN>(env_pos, N_rt, jl, d.p[0], d.p[1], d.p[2], c, cand, n_cand);
+    if (flags & MDG_DW) F[2] -= downwash_sum<kN>(env_pos, N_rt, jl, d.p[0], d.p[1], d.p[2], c);
     if (kFlags == kFlagsDR) {  // the wind's force, world frame
         F[0] += fe.x;
         F[1] += fe.y;
@@ -1307,10 +1268,6 @@ __device__ __forceinline__ void rk4_substeps(Drone& d, const Motor& m, const Env
 // kN = -1, run blocks of at most kSmallBlock threads and may use up to 128 registers;
 // the kN = 0 variant takes any block size (64 registers).
 constexpr int kSmallBlock = 256;
-// The compile-time 64-drone variants with downwash cull the sources below each warp
-// (warp_sources_above): every environment is two whole warps there.
-template <int kFlags, int kN>
-constexpr bool kCullSources = kN == 64 && fixed_subset(kFlags) >= 0 && (fixed_subset(kFlags) & MDG_DW) != 0;
 template <int kN>
 struct StepBounds {
     static constexpr int threads = kN != 0 ? kSmallBlock : 1024;
@@ -1393,14 +1350,7 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
                 if (warp_local) __syncwarp();
                 else __syncthreads();
             }
-            if constexpr (kCullSources<kFlags, kN>) {  // every warp lies inside one 64-drone environment
-                __shared__ int s_cand[kSmallBlock / 32][64];
-                int* cand = s_cand[t >> 5];
-                const int nc = warp_sources_above(buf + env.ls, d.p[2], active, a.c.dw_dz_min, cand);
-                if (active) substep<kFlags, kN>(d, m, env.flags, buf + env.ls, env.N, t - env.ls, a.c, float3{}, cand, nc);
-            } else {
-                if (active) substep<kFlags, kN>(d, m, env.flags, buf + env.ls, env.N, t - env.ls, a.c);
-            }
+            if (active) substep<kFlags, kN>(d, m, env.flags, buf + env.ls, env.N, t - env.ls, a.c);
         }
     }
     bool bad = false;
@@ -1619,16 +1569,7 @@ __global__ void __launch_bounds__(StepBounds<kN>::threads, StepBounds<kN>::min_b
                         if (warp_local) __syncwarp();
                         else __syncthreads();
                     }
-                    if constexpr (kCullSources<kFlags, kN>) {  // every warp lies inside one 64-drone environment
-                        __shared__ int s_cand[kSmallBlock / 32][64];
-                        int* cand = s_cand[t >> 5];
-                        const int nc = warp_sources_above(buf + env.ls, d.p[2], active, a.c.dw_dz_min, cand);
-                        if (active)
-                            substep<kFlags, kN>(d, m, env.flags, buf + env.ls, env.N, t - env.ls, a.c, float3{}, cand,
-                                                nc);
-                    } else {
-                        if (active) substep<kFlags, kN>(d, m, env.flags, buf + env.ls, env.N, t - env.ls, a.c);
-                    }
+                    if (active) substep<kFlags, kN>(d, m, env.flags, buf + env.ls, env.N, t - env.ls, a.c);
                 }
             }
             if (r.obs_mode == 2 || (r.obs_mode == 1 && k == r.K - 1)) {
