@@ -575,6 +575,11 @@ int mdg_mlp_adam(mdg_mlp m, float lr, void* stream);
  * training kernels). Training has its own setting, mdg_mlp_set_train_path. */
 #define MDG_MLP_PATH_MMA_SYNC 0
 #define MDG_MLP_PATH_TCGEN05 1
+/* MDG_MLP_PATH_TCGEN05_PAIRS: the fused tcgen05 kernel with two 128-row tiles in flight per
+ * block (each layer's accumulator is moved to registers before its SiLU, so one tile needs one
+ * 256-column accumulator and the tensor cores run one tile while the epilogue works on the
+ * other). Inference only; training uses mdg_mlp_set_train_path. */
+#define MDG_MLP_PATH_TCGEN05_PAIRS 2
 int mdg_mlp_set_path(mdg_mlp m, int32_t path);
 /* Training path of mdg_mlp_grad: MDG_MLP_PATH_TCGEN05 (default: every GEMM of the forward and
  * backward pass on tcgen05.mma with the accumulator in tensor memory, both operands K-major in

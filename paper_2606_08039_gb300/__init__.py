@@ -27,7 +27,7 @@ STATUS_NONFINITE = 1
 STATUS_TIMEOUT = 2
 SCHED_DYNAMIC, SCHED_STATIC = 0, 1
 STATUS_BOUNDS = 4
-MLP_PATH_MMA_SYNC, MLP_PATH_TCGEN05 = 0, 1
+MLP_PATH_MMA_SYNC, MLP_PATH_TCGEN05, MLP_PATH_TCGEN05_PAIRS = 0, 1, 2
 STATE_PLANES = 6
 KIN_DIM = 20
 NBR_K = 4

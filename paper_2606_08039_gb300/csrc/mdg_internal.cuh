@@ -239,6 +239,9 @@ size_t mlp_image_bytes();
 cudaError_t mlp_build_image(const MlpView& w, void* img, cudaStream_t s);
 cudaError_t mlp_forward_umma(const MlpView& w, const void* img, const void* x, int B, float* y, uint32_t* status,
                              int wait_limit, int spin_limit, cudaStream_t s);
+// The same with two 128-row tiles in flight per block (one 256-column accumulator each).
+cudaError_t mlp_forward_umma_pairs(const MlpView& w, const void* img, const void* x, int B, float* y,
+                                   uint32_t* status, int wait_limit, int spin_limit, cudaStream_t s);
 // Training on tcgen05: the loss of the standardised targets t ([B][32], columns 13..31
 // ignored) added to *loss_acc and every parameter's gradient written to grad (flat FP32
 // layout); B a multiple of 128. wT must hold the current weights' transposes.

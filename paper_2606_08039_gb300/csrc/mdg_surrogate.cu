@@ -126,6 +126,8 @@ cudaError_t forward_umma(mdg_mlp m, const void* x, int B, float* y, uint32_t* st
         if (e != cudaSuccess) return e;
         m->img_stale = false;
     }
+    if (m->path == MDG_MLP_PATH_TCGEN05_PAIRS)
+        return mdg::mlp_forward_umma_pairs(m->view(), m->img, x, B, y, status, m->wait_limit, m->spin_limit, s);
     return mdg::mlp_forward_umma(m->view(), m->img, x, B, y, status, m->wait_limit, m->spin_limit, s);
 }
 
@@ -280,7 +282,7 @@ int mdg_mlp_forward(mdg_mlp m, const uint16_t* x, float* y, int32_t B, void* str
         return fail(MDG_ERR_ARG, "mdg_mlp_forward: x and y must be 16-byte aligned");
     Guard g(m->device);
     cudaError_t e;
-    if (m->path == MDG_MLP_PATH_TCGEN05) {
+    if (m->path != MDG_MLP_PATH_MMA_SYNC) {
         e = forward_umma(m, x, B, y, m->status, (cudaStream_t)stream);
     } else {
         float* zs[3] = {nullptr, nullptr, nullptr};
@@ -364,7 +366,7 @@ int mdg_mlp_adam(mdg_mlp m, float lr, void* stream)
 int mdg_mlp_set_path(mdg_mlp m, int32_t path)
 {
     if (!m) return fail(MDG_ERR_ARG, "mdg_mlp_set_path: NULL handle");
-    if (path != MDG_MLP_PATH_MMA_SYNC && path != MDG_MLP_PATH_TCGEN05)
+    if (path != MDG_MLP_PATH_MMA_SYNC && path != MDG_MLP_PATH_TCGEN05 && path != MDG_MLP_PATH_TCGEN05_PAIRS)
         return fail(MDG_ERR_ARG, "mdg_mlp_set_path: unknown path %d", path);
     m->path = path;
     return MDG_OK;
@@ -491,7 +493,7 @@ int mdg_surrogate_step(mdg_handle h, mdg_mlp m, float* state, const float* actio
                             (size_t)(n_pad - h->n_drones) * MDG_MLP_IN_PAD * 2, s);
     if (e == cudaSuccess) e = mdg::launch_surrogate_prepare(a, h->n_tiles, h->block, s);
     if (e == cudaSuccess) {
-        if (m->path == MDG_MLP_PATH_TCGEN05) {
+        if (m->path != MDG_MLP_PATH_MMA_SYNC) {
             e = forward_umma(m, m->x, n_pad, m->y, h->d_status, s);
         } else {
             float* zs[3] = {nullptr, nullptr, nullptr};

@@ -460,6 +460,323 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
 }
 
+// ---- paired inference: two 128-row tiles in flight ----
+//
+// The kernel above holds both 256-column TMEM accumulators for its one tile (layer l is read
+// out while layer l + 1 accumulates), so its tensor cores idle while the epilogue of each
+// layer's first chunk runs. Here the epilogue first moves a layer's whole accumulator into
+// registers (each of the 16 epilogue threads of a row quadrant and column part holds its 64
+// values) and only then computes SiLU, so the layer's 256 columns are free again at once: one
+// tile needs one accumulator, and two tiles, A in columns 0-255 and B in 256-511, alternate:
+// while the epilogue works on one tile's layer, the tensor cores run the other tile's. The
+// MMA thread issues, per pair of tiles, A.L1, B.L1 (one W1 chunk for both), A.L2, B.L2, A.L3,
+// B.L3 (each tile's four W2/W3 chunks streamed through a two-slot ring, so each is loaded
+// twice per pair, as often as by one tile per block), A.L4, B.L4 (one W4 load). A layer's
+// first MMA into a tile's accumulator waits for the epilogue to have drained the previous
+// layer (AccDrained); its MMA on K chunk c waits for chunk c of the previous layer's
+// activations (ActFull). Waits are bounded as above, with the same exit.
+constexpr uint32_t kPActA = 0;                          // tile A activations: 4 chunks
+constexpr uint32_t kPActB = 4 * kChunkBytes;            // tile B activations
+constexpr uint32_t kPX = 8 * kChunkBytes;               // inputs of A, then of B
+constexpr uint32_t kPSlot = 10 * kChunkBytes;           // two weight slots
+constexpr int kPSlots = 2;
+constexpr uint32_t kPDynBytes = kPSlot + kPSlots * kSlotBytes;
+static_assert(kPDynBytes + 1024 + 512 <= 232448, "shared memory of one paired block");
+constexpr int kPLoadsPerPair = 18;  // W1, W2 c0-3 (A), W2 c0-3 (B), W3 (A), W3 (B), W4
+
+enum {
+    kPBarWFull = 0,                       // [2]
+    kPBarWEmpty = kPBarWFull + kPSlots,   // [2]
+    kPBarXFull = kPBarWEmpty + kPSlots,   // [2] tiles A, B
+    kPBarXEmpty = kPBarXFull + 2,         // [2]
+    kPBarAccFull = kPBarXEmpty + 2,       // [2] MMA commit: the tile's layer is accumulated
+    kPBarAccDrained = kPBarAccFull + 2,   // [2] 16 epilogue warps: the accumulator is in registers
+    kPBarActFull = kPBarAccDrained + 2,   // [2][4] 16 epilogue warps: activation chunk c written
+    kPBarMmaDone = kPBarActFull + 8,
+    kPNumBars
+};
+
+// Weight chunk of load k of a pair (image index, bytes): 0 W1; 1-4 W2 c0-3 for A, 5-8 for B;
+// 9-12 W3 for A, 13-16 for B; 17 W4.
+__device__ __forceinline__ int pair_load_image(int k) { return k == 0 ? 0 : k <= 8 ? 1 + (k - 1) % 4 : k <= 16 ? 5 + (k - 9) % 4 : 9; }
+
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t r[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    mlp_umma_pair_kernel(const __nv_bfloat16* __restrict__ x, float* __restrict__ y, int n_tiles,
+                         const uint8_t* __restrict__ w_img, const float* __restrict__ master, MlpView w,
+                         uint32_t* status, int wait_limit, int spin_limit)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t bars[kPNumBars];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t act0 = smem_u32(base + kPActA), x0 = smem_u32(base + kPX), slot_a = smem_u32(base + kPSlot);
+    const uint32_t bar0 = smem_u32(&bars[0]);
+    auto bar = [bar0](int i) { return bar0 + 8u * (uint32_t)i; };
+    volatile int* abort = &s_abort;
+    const int n_pairs = (n_tiles + 1) / 2;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kPNumBars; ++i) {
+            const bool epi = (i >= kPBarAccDrained && i < kPBarMmaDone);
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar(i)), "r"(epi ? kEpiWarps : 1));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        s_abort = 0;
+    }
+    if (warp == kMmaWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = s_tmem;
+
+    if (warp == kProdWarp) {
+        // ---------------- producer ----------------
+        int j = 0;  // weight loads issued
+        int s = 0;  // pairs of this block
+        bool ok = true;
+        auto load_x = [&](int tile, int t) {
+            const __nv_bfloat16* src = x + (size_t)tile * kRows * MDG_MLP_IN_PAD;
+            const uint32_t dst = x0 + (uint32_t)t * kChunkBytes;
+#pragma unroll 4
+            for (int i = lane; i < kRows * 8; i += 32) {
+                const int r = i >> 3, k8 = i & 7;
+                cp_async16(dst + r * 128 + ((k8 ^ (r & 7)) << 4), src + r * MDG_MLP_IN_PAD + k8 * 8);
+            }
+        };
+        if (blockIdx.x < n_pairs) {  // the grid never exceeds the pair count
+            load_x(2 * blockIdx.x, 0);
+            if (2 * blockIdx.x + 1 < n_tiles) load_x(2 * blockIdx.x + 1, 1);
+        }
+        for (int pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x, ++s) {
+            const bool hasB = 2 * pr + 1 < n_tiles;
+            const int next = pr + (int)gridDim.x;
+            for (int k = 0; k < kPLoadsPerPair; ++k, ++j) {
+                const int slot = j % kPSlots, use = j / kPSlots;
+                if (use > 0)
+                    ok = __all_sync(0xffffffffu, mbar_wait(bar(kPBarWEmpty + slot), (use - 1) & 1, abort, status, wait_limit));
+                if (!ok) break;
+                const int img = pair_load_image(k);
+                const uint32_t bytes = img == 9 ? 16384u : kSlotBytes;
+                if (lane == 0) {
+                    mbar_expect_tx(bar(kPBarWFull + slot), bytes);
+                    bulk_g2s(slot_a + slot * kSlotBytes, w_img + (size_t)img * kSlotBytes, bytes, bar(kPBarWFull + slot));
+                }
+                __syncwarp();
+                if (k == 0) {  // this pair's inputs (issued one pair ahead) have landed
+                    asm volatile("cp.async.wait_all;\n" ::: "memory");
+                    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) {
+                        mbar_arrive(bar(kPBarXFull + 0));
+                        if (hasB) mbar_arrive(bar(kPBarXFull + 1));
+                    }
+                } else if (k == 1 && next < n_pairs) {
+                    // layer 1 of this pair is done with the input buffers: fetch the next pair's
+                    ok = __all_sync(0xffffffffu, mbar_wait(bar(kPBarXEmpty + 0), s & 1, abort, status, wait_limit));
+                    if (ok) ok = __all_sync(0xffffffffu, mbar_wait(bar(kPBarXEmpty + 1), s & 1, abort, status, wait_limit));
+                    if (!ok) {
+                        ++j;
+                        break;
+                    }
+                    load_x(2 * next, 0);
+                    if (2 * next + 1 < n_tiles) load_x(2 * next + 1, 1);
+                }
+            }
+        }
+        // drain: every copy issued has landed before the block may exit
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        if (lane == 0)
+            for (int slot = 0; slot < kPSlots && slot < j; ++slot) {
+                const int uses = (j - 1 - slot) / kPSlots + 1;
+                mbar_wait(bar(kPBarWFull + slot), (uses - 1) & 1, nullptr, status, kWaitLimit);
+            }
+        __syncwarp();
+    } else if (warp == kMmaWarp) {
+        // ---------------- MMA issue (one thread) ----------------
+        if (lane == 0) {
+            const uint32_t id_h = idesc_bf16(kRows, MDG_MLP_HIDDEN), id_o = idesc_bf16(kRows, MDG_MLP_OUT_PAD);
+            int j = 0, s = 0;
+            uint32_t n_drain[2] = {0u, 0u};  // AccDrained phases completed per tile
+            uint32_t n_act[2] = {0u, 0u};    // ActFull phases completed per tile
+            bool ok = true;
+            auto wfull = [&](int jj) {
+                return mbar_wait(bar(kPBarWFull + jj % kPSlots), (jj / kPSlots) & 1, abort, status, wait_limit);
+            };
+            // the first MMA of a layer into tile t's accumulator: the previous layer drained
+            auto drained = [&](int t) {
+                const bool r = mbar_spin(bar(kPBarAccDrained + t), n_drain[t] & 1, abort, status, 0, spin_limit);
+                ++n_drain[t];
+                return r;
+            };
+            for (int pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x, ++s) {
+                const bool hasB = 2 * pr + 1 < n_tiles;
+                const int nt = hasB ? 2 : 1;
+                // layer 1: x [128 x 64] . W1^T for A then B, one W1 chunk
+                ok = wfull(j);
+                for (int t = 0; t < nt && ok; ++t) {
+                    ok = mbar_wait(bar(kPBarXFull + t), s & 1, abort, status, wait_limit) && (s == 0 || drained(t));
+                    if (!ok) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    const uint32_t xs = x0 + (uint32_t)t * kChunkBytes, ws = slot_a + (j % kPSlots) * kSlotBytes;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        mma_bf16_ss(tmem + 256u * t, sw128_desc(xs + k * 32), sw128_desc(ws + k * 32), id_h, k != 0);
+                    mma_commit(bar(kPBarAccFull + t));
+                    mma_commit(bar(kPBarXEmpty + t));
+                }
+                if (!ok) break;
+                if (!hasB) mma_commit(bar(kPBarXEmpty + 1));  // keeps the producer's phase count of B
+                mma_commit(bar(kPBarWEmpty + j % kPSlots));
+                ++j;
+                // layers 2 and 3: per tile four K chunks, each as soon as the epilogue has written it
+                for (int l = 1; l < 3 && ok; ++l) {
+                    for (int t = 0; t < 2 && ok; ++t) {
+                        for (int c = 0; c < 4; ++c, ++j) {
+                            if (t < nt) {
+                                ok = wfull(j) && (c != 0 || drained(t)) &&
+                                     mbar_spin(bar(kPBarActFull + 4 * t + c), n_act[t] & 1, abort, status, 0, spin_limit);
+                                if (!ok) break;
+                                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                                const uint32_t asl = act0 + (uint32_t)t * 4 * kChunkBytes + c * kChunkBytes;
+                                const uint32_t wsl = slot_a + (j % kPSlots) * kSlotBytes;
+#pragma unroll
+                                for (int k = 0; k < 4; ++k)
+                                    mma_bf16_ss(tmem + 256u * t, sw128_desc(asl + k * 32), sw128_desc(wsl + k * 32), id_h,
+                                                (c | k) != 0);
+                                if (c == 3) mma_commit(bar(kPBarAccFull + t));
+                            } else {
+                                ok = wfull(j);  // tile B missing: its chunks are still loaded, and released
+                                if (!ok) break;
+                            }
+                            mma_commit(bar(kPBarWEmpty + j % kPSlots));
+                        }
+                        if (ok && t < nt) ++n_act[t];
+                    }
+                }
+                if (!ok) break;
+                // layer 4: W4 [32 x 256] as four [32 x 64] chunks in one slot, A then B
+                ok = wfull(j);
+                for (int t = 0; t < nt && ok; ++t) {
+                    ok = drained(t);
+                    const uint32_t wsl = slot_a + (j % kPSlots) * kSlotBytes;
+                    for (int c = 0; c < 4 && ok; ++c) {
+                        ok = mbar_spin(bar(kPBarActFull + 4 * t + c), n_act[t] & 1, abort, status, 0, spin_limit);
+                        if (!ok) break;
+                        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                        const uint32_t asl = act0 + (uint32_t)t * 4 * kChunkBytes + c * kChunkBytes, bsl = wsl + c * 4096;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            mma_bf16_ss(tmem + 256u * t, sw128_desc(asl + k * 32), sw128_desc(bsl + k * 32), id_o,
+                                        (c | k) != 0);
+                    }
+                    if (!ok) break;
+                    ++n_act[t];
+                    mma_commit(bar(kPBarAccFull + t));
+                }
+                if (!ok) break;
+                mma_commit(bar(kPBarWEmpty + j % kPSlots));
+                ++j;
+            }
+            // nothing in flight before the tensor memory is freed
+            mma_commit(bar(kPBarMmaDone));
+            mbar_wait(bar(kPBarMmaDone), 0, nullptr, status, kWaitLimit);
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue (warps 0-15) ----------------
+        const int q = warp & 3, p = warp >> 2;  // TMEM lane quadrant, column part
+        const int row = q * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        const int sw = row & 7;
+        uint32_t n_acc[2] = {0u, 0u};
+        bool ok = true;
+        for (int pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
+            const bool hasB = 2 * pr + 1 < n_tiles;
+            const int nt = hasB ? 2 : 1;
+            for (int l = 0; l < 3 && ok; ++l) {
+                const float* bias = master + w.b_off[l];
+                for (int t = 0; t < nt && ok; ++t) {
+                    ok = __all_sync(0xffffffffu, mbar_spin(bar(kPBarAccFull + t), n_acc[t] & 1, abort, status, 32,
+                                                           spin_limit));
+                    if (!ok) break;
+                    ++n_acc[t];
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    // the whole accumulator part of this thread (4 chunks x 16 columns) into registers
+                    uint32_t r[4][16];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        tmem_ld16_nowait(tmem + 256u * t + lane_off + (uint32_t)(c * 64 + p * 16), r[c]);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar(kPBarAccDrained + t));
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int col = c * 64 + p * 16;
+                        float hb[16];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float4 b4 = __ldg(reinterpret_cast<const float4*>(bias + col) + i);
+                            hb[4 * i] = 0.5f * b4.x, hb[4 * i + 1] = 0.5f * b4.y, hb[4 * i + 2] = 0.5f * b4.z,
+                                      hb[4 * i + 3] = 0.5f * b4.w;
+                        }
+                        __nv_bfloat162 o[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            o[i] = silu_pair(fmaf(__uint_as_float(r[c][2 * i]), 0.5f, hb[2 * i]),
+                                             fmaf(__uint_as_float(r[c][2 * i + 1]), 0.5f, hb[2 * i + 1]));
+                        uint8_t* dst = base + (t ? kPActB : kPActA) + c * kChunkBytes + row * 128;
+                        *reinterpret_cast<uint4*>(dst + (((2 * p) ^ sw) << 4)) = *reinterpret_cast<const uint4*>(&o[0]);
+                        *reinterpret_cast<uint4*>(dst + (((2 * p + 1) ^ sw) << 4)) = *reinterpret_cast<const uint4*>(&o[4]);
+                        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(bar(kPBarActFull + 4 * t + c));
+                    }
+                }
+            }
+            // output layer: 32 columns, eight per column part
+            for (int t = 0; t < nt && ok; ++t) {
+                ok = __all_sync(0xffffffffu, mbar_spin(bar(kPBarAccFull + t), n_acc[t] & 1, abort, status, 32,
+                                                       spin_limit));
+                if (!ok) break;
+                ++n_acc[t];
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                float v[8];
+                tmem_ld8(tmem + 256u * t + lane_off + p * 8, v);
+                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar(kPBarAccDrained + t));
+                const float* b4 = master + w.b_off[3] + p * 8;
+                const int tile = 2 * pr + t;
+                float4* out = reinterpret_cast<float4*>(y + ((size_t)tile * kRows + row) * MDG_MLP_OUT_PAD + p * 8);
+                out[0] = make_float4(v[0] + b4[0], v[1] + b4[1], v[2] + b4[2], v[3] + b4[3]);
+                out[1] = make_float4(v[4] + b4[4], v[5] + b4[5], v[6] + b4[6], v[7] + b4[7]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (warp == kMmaWarp)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
+}
+
 // ---- training GEMMs on tcgen05: C[M x N] = A[M x K] B[N x K]^T, both operands K-major ----
 //
 // One 128-thread block computes a 128 x BN tile of C over a range of K (split-K when
@@ -754,6 +1071,8 @@ __global__ void build_image_kernel(const __nv_bfloat16* __restrict__ w16, MlpVie
 
 constexpr size_t kUmmaSmem = 1024 + kDynBytes;
 
+constexpr size_t kUmmaPairSmem = 1024 + kPDynBytes;
+
 size_t mlp_image_bytes() { return kImgBytes; }
 
 cudaError_t mlp_build_image(const MlpView& w, void* img, cudaStream_t s)
@@ -761,6 +1080,32 @@ cudaError_t mlp_build_image(const MlpView& w, void* img, cudaStream_t s)
     const int pieces = (int)(kImgBytes / 16);
     build_image_kernel<<<(pieces + 255) / 256, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(w.w16), w,
                                                              static_cast<uint8_t*>(img));
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_forward_umma_pairs(const MlpView& w, const void* img, const void* x, int B, float* y,
+                                   uint32_t* status, int wait_limit, int spin_limit, cudaStream_t s)
+{
+    if (B % kRows) return cudaErrorInvalidValue;
+    const int n_tiles = B / kRows;
+    if (n_tiles == 0) return cudaSuccess;
+    static bool attr_done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr_done[dev]) {
+        e = cudaFuncSetAttribute(mlp_umma_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmmaPairSmem);
+        if (e != cudaSuccess) return e;
+        attr_done[dev] = true;
+    }
+    int n_sm = 152;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    const int n_pairs = (n_tiles + 1) / 2;
+    const int grid = n_pairs < n_sm ? n_pairs : n_sm;
+    mlp_umma_pair_kernel<<<grid, kThreads, kUmmaPairSmem, s>>>(static_cast<const __nv_bfloat16*>(x), y, n_tiles,
+                                                               static_cast<const uint8_t*>(img), w.master, w, status,
+                                                               wait_limit, spin_limit);
     return cudaGetLastError();
 }
 

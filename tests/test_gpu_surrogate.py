@@ -57,11 +57,13 @@ def _f64(layers):
 
 
 @pytest.mark.parametrize("path,B", [(mdg.MLP_PATH_TCGEN05, 128), (mdg.MLP_PATH_TCGEN05, 384 * 8),
-                                    (mdg.MLP_PATH_MMA_SYNC, 384)])
+                                    (mdg.MLP_PATH_MMA_SYNC, 384), (mdg.MLP_PATH_TCGEN05_PAIRS, 128),
+                                    (mdg.MLP_PATH_TCGEN05_PAIRS, 384 * 8), (mdg.MLP_PATH_TCGEN05_PAIRS, 128 * 611)])
 def test_forward_matches_oracle(cuda, path, B):
-    """Both inference paths (fused tcgen05 kernel, per-layer mma.sync GEMMs) against the
-    oracle on identical bf16 inputs and weights; several tiles per block for the persistent
-    tcgen05 kernel."""
+    """The inference paths (fused tcgen05 kernel, its two-tiles-in-flight form, per-layer
+    mma.sync GEMMs) against the oracle on identical bf16 inputs and weights; several tiles per
+    block for the persistent tcgen05 kernels, and for the paired one a lone tile, and 611
+    tiles (two to three pairs per block, the last pair a lone tile)."""
     layers = _layers(1)
     m = mdg.MLP(B, layers)
     m.set_path(path)
@@ -77,7 +79,7 @@ def test_forward_matches_oracle(cuda, path, B):
     # tcgen05 path evaluates SiLU as z/2 (1 + tanh(z/2)) with tanh.approx.f32 (relative error
     # 2^-11): its bound adds the oracle's own response to that error.
     bound = 1e-2 * np.maximum(np.abs(yo), 1.0)
-    if path == mdg.MLP_PATH_TCGEN05:
+    if path != mdg.MLP_PATH_MMA_SYNC:
         bound = bound + _tanh_error_response(_f64(layers), xo, yo)
     assert np.all(np.abs(y.cpu().numpy() - yo) <= bound)
 
@@ -116,17 +118,19 @@ def test_training_paths_agree_over_steps(cuda):
     assert np.linalg.norm(wa - wb) <= 0.1 * np.linalg.norm(dw)
 
 
-def test_tcgen05_bounded_wait_exit(cuda):
+@pytest.mark.parametrize("path", [mdg.MLP_PATH_TCGEN05, mdg.MLP_PATH_TCGEN05_PAIRS])
+def test_tcgen05_bounded_wait_exit(cuda, path):
     """The tcgen05 kernel's exit on an expired wait, without a stuck device: with wait bounds
     of zero the first wait that is not already complete (at the latest the epilogue's wait
-    for its first accumulator) gives up on a normal 128-row launch. The launch returns with
+    for its first accumulator) gives up on a normal 256-row launch, in both tcgen05 kernels. The launch returns with
     MDG_STATUS_TIMEOUT set; a launch with the default bounds then matches the oracle, so the
     abandoned launch drained its copies and MMAs and freed its tensor memory."""
     layers = _layers(1)
-    m = mdg.MLP(128, layers)
-    m.set_path(mdg.MLP_PATH_TCGEN05)
-    x = torch.as_tensor(_inputs(2, 128), device=cuda).to(torch.bfloat16)
-    y = torch.full((128, mdg.MLP_OUT_PAD), float("nan"), device=cuda)
+    B = 256  # one pair of tiles for the paired kernel
+    m = mdg.MLP(B, layers)
+    m.set_path(path)
+    x = torch.as_tensor(_inputs(2, B), device=cuda).to(torch.bfloat16)
+    y = torch.full((B, mdg.MLP_OUT_PAD), float("nan"), device=cuda)
     m.set_wait_limits(0, 0)
     m.forward(x, y)
     assert mdg.lib().mdg_sync(mdg._stream(None), 5000) == mdg.OK  # the launch returned
