@@ -767,8 +767,9 @@ def camera_cpu_baseline(seconds_target: float = 10.0) -> dict:
 
 def run_mlp(args) -> None:
     """The surrogate network's inference kernels alone: 262144 rows (the 65536 x 4 swarm),
-    initial weights, bf16 inputs; the fused tcgen05 kernel (the step's path) and, for
-    comparison, the per-layer mma.sync GEMMs. Tensor roofline against the measured bf16 peak."""
+    initial weights, bf16 inputs; the fused tcgen05 kernel with two tiles in flight per block
+    (the step's default path) and, for comparison, its single-tile form and the per-layer
+    mma.sync GEMMs. Tensor roofline against the measured bf16 peak."""
     import torch
     import paper_2606_08039_gb300 as mdg
     from paper_2606_08039_gb300 import workloads as wl
@@ -800,18 +801,19 @@ def run_mlp(args) -> None:
         res[name] = a.elapsed_time(b) / steps
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0}
-    ach = flops / (res["tcgen05"] * 1e-3) / 1e12
+    ach = flops / (res["tcgen05_pairs"] * 1e-3) / 1e12
     print(json.dumps({
         "per_path_ms": res,
-        "metric": "surrogate network rows/s", "value": rows / (res["tcgen05"] * 1e-3), "unit": "rows/s",
-        "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": res["tcgen05"], "higher_is_better": True,
+        "metric": "surrogate network rows/s", "value": rows / (res["tcgen05_pairs"] * 1e-3), "unit": "rows/s",
+        "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": res["tcgen05_pairs"],
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": "surrogate network forward, 262144 rows, 64-256-256-256-32, bf16/FP32 accumulation",
                    "l2": "inputs (33.5 MB) and weights stay in L2 between launches"},
         "mma_sync_ms": res["mma_sync"], "gpu_launches": steps,
         "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                      "frac": ach / peaks["bf16_tflops"], "traffic": None, "peak_src": "measured (bf16 burst)",
-                     "kernel": "mlp_umma_kernel", "algorithmic_flops_per_launch": flops},
+                     "kernel": "mlp_umma_pair_kernel", "algorithmic_flops_per_launch": flops},
         "status": m.status()}))
 
 
@@ -947,7 +949,7 @@ def run_surrogate(args) -> None:
         "data": "synthetic",
         "config": {"workload": "surrogate: 65536 envs x 4 drones, PID waypoints, one control step; network "
                                "41-256-256-256-13 SiLU, bf16 weights/activations, FP32 accumulation, fused tcgen05 "
-                               "kernel; out-of-distribution environments on the plain integrator",
+                               "kernel (two tiles in flight per block); out-of-distribution environments on the plain integrator",
                    "l2": "flushed between timed steps (512 MiB written, then read back)",
                    "training": {"transitions_generated": 16384 * 4 * 153, "transitions_kept": n_train,
                                 "kept_fraction": kept, "epochs": 4, "batch": 8192, "seconds": train_s,
@@ -959,7 +961,7 @@ def run_surrogate(args) -> None:
         "gpu_launches": 5 * steps,
         "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                      "frac": ach / peaks["bf16_tflops"], "traffic": None, "peak_src": "measured (bf16 burst)",
-                     "kernel": "mlp_umma_kernel", "ms": ms_net, "algorithmic_flops_per_launch": flops},
+                     "kernel": "mlp_umma_pair_kernel", "ms": ms_net, "algorithmic_flops_per_launch": flops},
         "clocks": clk,
     }
     print(json.dumps(out))
@@ -1080,7 +1082,7 @@ def run_surrogate_dense(args) -> None:
         "gpu_launches": 5 * steps,
         "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                      "frac": ach / peaks["bf16_tflops"], "traffic": None, "peak_src": peaks["src"],
-                     "kernel": "mlp_umma_kernel", "ms": ms_net, "algorithmic_flops_per_launch": flops},
+                     "kernel": "mlp_umma_pair_kernel", "ms": ms_net, "algorithmic_flops_per_launch": flops},
         "clocks": clk,
     }
     print(json.dumps(out))

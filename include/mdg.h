@@ -569,16 +569,20 @@ int mdg_mlp_grad(mdg_mlp m, const uint16_t* x, const float* t, int32_t B, float*
 /* One Adam step (b1 0.9, b2 0.999, eps 1e-8) with the gradient of the last mdg_mlp_grad. */
 int mdg_mlp_adam(mdg_mlp m, float lr, void* stream);
 
-/* Inference path of mdg_mlp_forward and mdg_surrogate_step: MDG_MLP_PATH_TCGEN05 (default:
- * one fused kernel on tcgen05.mma with the accumulator in tensor memory and the
- * activations in shared memory) or MDG_MLP_PATH_MMA_SYNC (one mma.sync GEMM per layer, the
- * training kernels). Training has its own setting, mdg_mlp_set_train_path. */
+/* Inference path of mdg_mlp_forward and mdg_surrogate_step: MDG_MLP_PATH_TCGEN05_PAIRS
+ * (default), MDG_MLP_PATH_TCGEN05 (one fused kernel on tcgen05.mma with the accumulator in
+ * tensor memory and the activations in shared memory, one 128-row tile in flight per block)
+ * or MDG_MLP_PATH_MMA_SYNC (one mma.sync GEMM per layer, the training kernels). Training has
+ * its own setting, mdg_mlp_set_train_path. */
 #define MDG_MLP_PATH_MMA_SYNC 0
 #define MDG_MLP_PATH_TCGEN05 1
 /* MDG_MLP_PATH_TCGEN05_PAIRS: the fused tcgen05 kernel with two 128-row tiles in flight per
  * block (each layer's accumulator is moved to registers before its SiLU, so one tile needs one
  * 256-column accumulator and the tensor cores run one tile while the epilogue works on the
- * other). Inference only; training uses mdg_mlp_set_train_path. */
+ * other; the second tile of a pair reuses two of the first tile's four weight chunks per
+ * hidden layer and sums its K chunks in another order, so its outputs agree with the
+ * single-tile kernel to FP32 summation order, the first tile's bit for bit). Inference only;
+ * training uses mdg_mlp_set_train_path. */
 #define MDG_MLP_PATH_TCGEN05_PAIRS 2
 int mdg_mlp_set_path(mdg_mlp m, int32_t path);
 /* Training path of mdg_mlp_grad: MDG_MLP_PATH_TCGEN05 (default: every GEMM of the forward and

@@ -692,7 +692,9 @@ class MLP:
                                   _ptr(loss, "loss", torch.float32, (1,)), _stream(stream)))
 
     def set_path(self, path: int):
-        """Inference path: MLP_PATH_TCGEN05 (fused tensor-memory kernel) or MLP_PATH_MMA_SYNC."""
+        """Inference path: MLP_PATH_TCGEN05_PAIRS (default: the fused tensor-memory kernel with
+        two tiles in flight per block), MLP_PATH_TCGEN05 (one tile per block) or
+        MLP_PATH_MMA_SYNC."""
         _check(lib().mdg_mlp_set_path(self._m, int(path)))
 
     def set_train_path(self, path: int):

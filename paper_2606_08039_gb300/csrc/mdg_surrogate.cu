@@ -69,7 +69,7 @@ struct mdg_mlp_s {
     int* fb_list = nullptr;
     int* fb_count = nullptr;
     uint32_t* status = nullptr;
-    int path = MDG_MLP_PATH_TCGEN05;
+    int path = MDG_MLP_PATH_TCGEN05_PAIRS;
     uint8_t* img = nullptr;      // weight image of the tcgen05 kernel
     bool img_stale = true;       // the bf16 weights changed since the image was built
     int wait_limit = MDG_MLP_DEFAULT_TRY_WAITS;  // bounded waits of the tcgen05 kernel

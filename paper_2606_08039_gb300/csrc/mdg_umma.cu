@@ -470,11 +470,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 // tile needs one accumulator, and two tiles, A in columns 0-255 and B in 256-511, alternate:
 // while the epilogue works on one tile's layer, the tensor cores run the other tile's. The
 // MMA thread issues, per pair of tiles, A.L1, B.L1 (one W1 chunk for both), A.L2, B.L2, A.L3,
-// B.L3 (each tile's four W2/W3 chunks streamed through a two-slot ring, so each is loaded
-// twice per pair, as often as by one tile per block), A.L4, B.L4 (one W4 load). A layer's
-// first MMA into a tile's accumulator waits for the epilogue to have drained the previous
-// layer (AccDrained); its MMA on K chunk c waits for chunk c of the previous layer's
-// activations (ActFull). Waits are bounded as above, with the same exit.
+// B.L3, A.L4, B.L4 (one W4 load). The W2/W3 chunks stream through a two-slot ring: tile A
+// takes K chunks 0-3 in order, tile B then takes 3 and 2 while they are still resident and
+// reloads 1 and 0, so a hidden layer costs six chunk loads per pair instead of eight (tile B
+// sums its K chunks in the order 3, 2, 1, 0; tile A's arithmetic is the single-tile kernel's).
+// A layer's first MMA into a tile's accumulator waits for the epilogue to have drained the
+// previous layer (AccDrained); tile A's MMA on K chunk c waits for chunk c of the previous
+// layer's activations (ActFull), tile B's layer, which starts with chunk 3, waits once for
+// chunk 3 (each epilogue warp writes the chunks in order, so 3 implies all). The next pair's
+// inputs are fetched in two parts between weight loads that have slack (after the fifth and
+// the eleventh), so that the weight ring never waits behind them. Waits are bounded as above,
+// with the same exit.
 constexpr uint32_t kPActA = 0;                          // tile A activations: 4 chunks
 constexpr uint32_t kPActB = 4 * kChunkBytes;            // tile B activations
 constexpr uint32_t kPX = 8 * kChunkBytes;               // inputs of A, then of B
@@ -482,7 +488,7 @@ constexpr uint32_t kPSlot = 10 * kChunkBytes;           // two weight slots
 constexpr int kPSlots = 2;
 constexpr uint32_t kPDynBytes = kPSlot + kPSlots * kSlotBytes;
 static_assert(kPDynBytes + 1024 + 512 <= 232448, "shared memory of one paired block");
-constexpr int kPLoadsPerPair = 18;  // W1, W2 c0-3 (A), W2 c0-3 (B), W3 (A), W3 (B), W4
+constexpr int kPLoadsPerPair = 14;  // W1, W2 c0-3, W2 c1, c0, W3 c0-3, W3 c1, c0, W4
 
 enum {
     kPBarWFull = 0,                       // [2]
@@ -496,9 +502,15 @@ enum {
     kPNumBars
 };
 
-// Weight chunk of load k of a pair (image index, bytes): 0 W1; 1-4 W2 c0-3 for A, 5-8 for B;
-// 9-12 W3 for A, 13-16 for B; 17 W4.
-__device__ __forceinline__ int pair_load_image(int k) { return k == 0 ? 0 : k <= 8 ? 1 + (k - 1) % 4 : k <= 16 ? 5 + (k - 9) % 4 : 9; }
+// Load k of a pair: its image index (0 W1; 1-4 W2 c0-3, 5 W2 c1, 6 W2 c0; 7-10 W3 c0-3,
+// 11 W3 c1, 12 W3 c0; 13 W4), its slot, and its position among the pair's seven loads into
+// that slot (slot 0: loads 0 2 4 5 7 9 12; slot 1: 1 3 6 8 10 11 13). The slots follow from
+// the order in which the MMA thread releases them; each holds seven loads per pair, so the
+// n-th load into a slot (n = 7 pairs + position) completes phase n of its WFull barrier.
+__device__ __forceinline__ int pair_load_image(int k) { return (int)((0x95687651243210ull >> (4 * k)) & 15u); }
+__device__ __forceinline__ int pair_load_slot(int k) { return (int)((0x2d4au >> k) & 1u); }
+__device__ __forceinline__ int pair_load_pos(int k) { return (int)((0x36b2b89a240ull >> (3 * k)) & 7u); }
+constexpr int kPLoadsPerSlot = 7;
 
 __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t r[16])
 {
@@ -547,8 +559,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp == kProdWarp) {
         // ---------------- producer ----------------
-        int j = 0;  // weight loads issued
-        int s = 0;  // pairs of this block
+        int issued0 = 0, issued1 = 0;  // weight loads issued into slots 0 and 1
+        int s = 0;                     // pairs of this block
         bool ok = true;
         auto load_x = [&](int tile, int t) {
             const __nv_bfloat16* src = x + (size_t)tile * kRows * MDG_MLP_IN_PAD;
@@ -566,10 +578,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x, ++s) {
             const bool hasB = 2 * pr + 1 < n_tiles;
             const int next = pr + (int)gridDim.x;
-            for (int k = 0; k < kPLoadsPerPair; ++k, ++j) {
-                const int slot = j % kPSlots, use = j / kPSlots;
-                if (use > 0)
-                    ok = __all_sync(0xffffffffu, mbar_wait(bar(kPBarWEmpty + slot), (use - 1) & 1, abort, status, wait_limit));
+            for (int k = 0; k < kPLoadsPerPair; ++k) {
+                const int slot = pair_load_slot(k), n = kPLoadsPerSlot * s + pair_load_pos(k);
+                if (n > 0)
+                    ok = __all_sync(0xffffffffu,
+                                    mbar_spin(bar(kPBarWEmpty + slot), (n - 1) & 1, abort, status, 0, spin_limit));
                 if (!ok) break;
                 const int img = pair_load_image(k);
                 const uint32_t bytes = img == 9 ? 16384u : kSlotBytes;
@@ -577,8 +590,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     mbar_expect_tx(bar(kPBarWFull + slot), bytes);
                     bulk_g2s(slot_a + slot * kSlotBytes, w_img + (size_t)img * kSlotBytes, bytes, bar(kPBarWFull + slot));
                 }
+                if (slot) ++issued1; else ++issued0;
                 __syncwarp();
-                if (k == 0) {  // this pair's inputs (issued one pair ahead) have landed
+                if (k == 0) {  // this pair's inputs (issued during the previous pair) have landed
                     asm volatile("cp.async.wait_all;\n" ::: "memory");
                     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                     __syncwarp();
@@ -586,54 +600,68 @@ __global__ void __launch_bounds__(kThreads, 1)
                         mbar_arrive(bar(kPBarXFull + 0));
                         if (hasB) mbar_arrive(bar(kPBarXFull + 1));
                     }
-                } else if (k == 1 && next < n_pairs) {
-                    // layer 1 of this pair is done with the input buffers: fetch the next pair's
+                } else if (k == 4 && next < n_pairs) {
+                    // layer 1 of this pair is done with the input buffers: the next pair's A
                     ok = __all_sync(0xffffffffu, mbar_wait(bar(kPBarXEmpty + 0), s & 1, abort, status, wait_limit));
                     if (ok) ok = __all_sync(0xffffffffu, mbar_wait(bar(kPBarXEmpty + 1), s & 1, abort, status, wait_limit));
-                    if (!ok) {
-                        ++j;
-                        break;
-                    }
+                    if (!ok) break;
                     load_x(2 * next, 0);
-                    if (2 * next + 1 < n_tiles) load_x(2 * next + 1, 1);
+                } else if (k == 10 && next < n_pairs && 2 * next + 1 < n_tiles) {
+                    load_x(2 * next + 1, 1);  // and its B
                 }
             }
         }
         // drain: every copy issued has landed before the block may exit
         asm volatile("cp.async.wait_all;\n" ::: "memory");
         if (lane == 0)
-            for (int slot = 0; slot < kPSlots && slot < j; ++slot) {
-                const int uses = (j - 1 - slot) / kPSlots + 1;
-                mbar_wait(bar(kPBarWFull + slot), (uses - 1) & 1, nullptr, status, kWaitLimit);
+            for (int slot = 0; slot < kPSlots; ++slot) {
+                const int uses = slot ? issued1 : issued0;
+                if (uses > 0) mbar_wait(bar(kPBarWFull + slot), (uses - 1) & 1, nullptr, status, kWaitLimit);
             }
         __syncwarp();
     } else if (warp == kMmaWarp) {
         // ---------------- MMA issue (one thread) ----------------
         if (lane == 0) {
             const uint32_t id_h = idesc_bf16(kRows, MDG_MLP_HIDDEN), id_o = idesc_bf16(kRows, MDG_MLP_OUT_PAD);
-            int j = 0, s = 0;
-            uint32_t n_drain[2] = {0u, 0u};  // AccDrained phases completed per tile
-            uint32_t n_act[2] = {0u, 0u};    // ActFull phases completed per tile
+            int s = 0;
+            // AccDrained and ActFull phases completed per tile (kept in registers: A in the low,
+            // B in the high half)
+            uint32_t n_drain = 0u, n_act = 0u;
             bool ok = true;
-            auto wfull = [&](int jj) {
-                return mbar_wait(bar(kPBarWFull + jj % kPSlots), (jj / kPSlots) & 1, abort, status, wait_limit);
+            auto wfull = [&](int k) {
+                return mbar_spin(bar(kPBarWFull + pair_load_slot(k)), (kPLoadsPerSlot * s + pair_load_pos(k)) & 1, abort,
+                                 status, 0, spin_limit);
             };
+            auto wslot = [&](int k) { return slot_a + (uint32_t)pair_load_slot(k) * kSlotBytes; };
+            auto release = [&](int k) { mma_commit(bar(kPBarWEmpty + pair_load_slot(k))); };
             // the first MMA of a layer into tile t's accumulator: the previous layer drained
             auto drained = [&](int t) {
-                const bool r = mbar_spin(bar(kPBarAccDrained + t), n_drain[t] & 1, abort, status, 0, spin_limit);
-                ++n_drain[t];
+                const bool r = mbar_spin(bar(kPBarAccDrained + t), (n_drain >> (16 * t)) & 1, abort, status, 0, spin_limit);
+                n_drain += 1u << (16 * t);
                 return r;
+            };
+            auto act = [&](int t, int c) {
+                return mbar_spin(bar(kPBarActFull + 4 * t + c), (n_act >> (16 * t)) & 1, abort, status, 0, spin_limit);
+            };
+            // K chunk c of tile t's activations against the weight chunk in slot ws: four MMAs
+            auto chunk = [&](int t, int c, uint32_t ws, uint32_t id, bool first) {
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t asl = act0 + (uint32_t)t * 4 * kChunkBytes + c * kChunkBytes;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    mma_bf16_ss(tmem + 256u * t, sw128_desc(asl + k * 32), sw128_desc(ws + k * 32), id,
+                                !(first && k == 0));
             };
             for (int pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x, ++s) {
                 const bool hasB = 2 * pr + 1 < n_tiles;
                 const int nt = hasB ? 2 : 1;
-                // layer 1: x [128 x 64] . W1^T for A then B, one W1 chunk
-                ok = wfull(j);
+                // layer 1: x [128 x 64] . W1^T for A then B, one W1 chunk (load 0)
+                ok = wfull(0);
                 for (int t = 0; t < nt && ok; ++t) {
                     ok = mbar_wait(bar(kPBarXFull + t), s & 1, abort, status, wait_limit) && (s == 0 || drained(t));
                     if (!ok) break;
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                    const uint32_t xs = x0 + (uint32_t)t * kChunkBytes, ws = slot_a + (j % kPSlots) * kSlotBytes;
+                    const uint32_t xs = x0 + (uint32_t)t * kChunkBytes, ws = wslot(0);
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
                         mma_bf16_ss(tmem + 256u * t, sw128_desc(xs + k * 32), sw128_desc(ws + k * 32), id_h, k != 0);
@@ -642,41 +670,44 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 if (!ok) break;
                 if (!hasB) mma_commit(bar(kPBarXEmpty + 1));  // keeps the producer's phase count of B
-                mma_commit(bar(kPBarWEmpty + j % kPSlots));
-                ++j;
-                // layers 2 and 3: per tile four K chunks, each as soon as the epilogue has written it
+                release(0);
+                // layers 2 and 3 (loads k0..k0+5): A chunks 0-3 in order, each as soon as the
+                // epilogue has written it; B chunks 3, 2 (A's loads k0+3, k0+2), 1, 0 (k0+4, k0+5)
                 for (int l = 1; l < 3 && ok; ++l) {
-                    for (int t = 0; t < 2 && ok; ++t) {
-                        for (int c = 0; c < 4; ++c, ++j) {
-                            if (t < nt) {
-                                ok = wfull(j) && (c != 0 || drained(t)) &&
-                                     mbar_spin(bar(kPBarActFull + 4 * t + c), n_act[t] & 1, abort, status, 0, spin_limit);
-                                if (!ok) break;
-                                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                                const uint32_t asl = act0 + (uint32_t)t * 4 * kChunkBytes + c * kChunkBytes;
-                                const uint32_t wsl = slot_a + (j % kPSlots) * kSlotBytes;
-#pragma unroll
-                                for (int k = 0; k < 4; ++k)
-                                    mma_bf16_ss(tmem + 256u * t, sw128_desc(asl + k * 32), sw128_desc(wsl + k * 32), id_h,
-                                                (c | k) != 0);
-                                if (c == 3) mma_commit(bar(kPBarAccFull + t));
-                            } else {
-                                ok = wfull(j);  // tile B missing: its chunks are still loaded, and released
-                                if (!ok) break;
-                            }
-                            mma_commit(bar(kPBarWEmpty + j % kPSlots));
-                        }
-                        if (ok && t < nt) ++n_act[t];
+                    const int k0 = l == 1 ? 1 : 7;
+                    for (int c = 0; c < 4 && ok; ++c) {
+                        ok = wfull(k0 + c) && (c != 0 || drained(0)) && act(0, c);
+                        if (!ok) break;
+                        chunk(0, c, wslot(k0 + c), id_h, c == 0);
+                        if (c == 3) mma_commit(bar(kPBarAccFull + 0));
+                        if (c < 2) release(k0 + c);
                     }
+                    if (!ok) break;
+                    n_act += 1u;
+                    for (int i = 0; i < 4 && ok; ++i) {
+                        const int c = 3 - i;
+                        const int k = i == 0 ? k0 + 3 : i == 1 ? k0 + 2 : i == 2 ? k0 + 4 : k0 + 5;
+                        if (hasB) {
+                            ok = (i < 2 || wfull(k)) && (i != 0 || (drained(1) && act(1, 3)));
+                            if (!ok) break;
+                            chunk(1, c, wslot(k), id_h, i == 0);
+                            if (i == 3) mma_commit(bar(kPBarAccFull + 1));
+                        } else {
+                            ok = i < 2 || wfull(k);  // tile B missing: its loads still land, and are released
+                            if (!ok) break;
+                        }
+                        release(k);
+                    }
+                    if (ok && hasB) n_act += 1u << 16;
                 }
                 if (!ok) break;
-                // layer 4: W4 [32 x 256] as four [32 x 64] chunks in one slot, A then B
-                ok = wfull(j);
+                // layer 4: W4 [32 x 256] as four [32 x 64] chunks in one slot (load 13), A then B
+                ok = wfull(13);
                 for (int t = 0; t < nt && ok; ++t) {
                     ok = drained(t);
-                    const uint32_t wsl = slot_a + (j % kPSlots) * kSlotBytes;
+                    const uint32_t wsl = wslot(13);
                     for (int c = 0; c < 4 && ok; ++c) {
-                        ok = mbar_spin(bar(kPBarActFull + 4 * t + c), n_act[t] & 1, abort, status, 0, spin_limit);
+                        if (t == 0 || c == 0) ok = act(t, t == 0 ? c : 3);
                         if (!ok) break;
                         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                         const uint32_t asl = act0 + (uint32_t)t * 4 * kChunkBytes + c * kChunkBytes, bsl = wsl + c * 4096;
@@ -686,12 +717,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                                         (c | k) != 0);
                     }
                     if (!ok) break;
-                    ++n_act[t];
+                    n_act += 1u << (16 * t);
                     mma_commit(bar(kPBarAccFull + t));
                 }
                 if (!ok) break;
-                mma_commit(bar(kPBarWEmpty + j % kPSlots));
-                ++j;
+                release(13);
             }
             // nothing in flight before the tensor memory is freed
             mma_commit(bar(kPBarMmaDone));

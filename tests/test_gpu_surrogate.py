@@ -151,10 +151,12 @@ def test_tcgen05_bounded_wait_exit(cuda, path):
 
 @pytest.mark.parametrize("n_tiles", [305, 611])
 def test_paired_kernel_equals_single_tile_kernel(cuda, n_tiles):
-    """The two-tiles-in-flight kernel does each tile's arithmetic exactly as the single-tile
-    kernel (the same MMAs, the same epilogue per element), so their outputs are bit-identical,
-    here with two to three pairs per block and a lone last tile (305 tiles: 153 pairs on 152
-    SMs; 611 tiles); and sampled tiles of it against the oracle."""
+    """The two-tiles-in-flight kernel does the first tile of each pair (A, even tiles) exactly
+    as the single-tile kernel (the same MMAs in the same order, the same epilogue per element),
+    so those outputs are bit-identical; the second tile (B) sums the K chunks of its hidden
+    layers in the order 3, 2, 1, 0, so it agrees to FP32 summation order (and the bf16
+    rounding that follows). Here with two to three pairs per block and a lone last tile (305
+    tiles: 153 pairs on 152 SMs; 611 tiles); and sampled tiles of it against the oracle."""
     B = 128 * n_tiles
     layers = _layers(4)
     m = mdg.MLP(B, layers)
@@ -167,7 +169,9 @@ def test_paired_kernel_equals_single_tile_kernel(cuda, n_tiles):
         torch.cuda.synchronize()
         assert m.status() == 0
         ys.append(y)
-    assert torch.equal(ys[0], ys[1])
+    single, paired = (y.view(n_tiles, 128, mdg.MLP_OUT_PAD) for y in ys)
+    assert torch.equal(single[0::2], paired[0::2])
+    assert torch.all((single[1::2] - paired[1::2]).abs() <= 1e-2 * torch.clamp(single[1::2].abs(), min=1.0))
     tiles = [0, 1, 151, 152, 153, 303, 304, n_tiles - 2, n_tiles - 1]
     rows = np.concatenate([np.arange(128 * t, 128 * t + 128) for t in sorted(set(tiles))])
     xo = x[torch.as_tensor(rows, device=cuda)].float().cpu().numpy().astype(np.float64)
@@ -392,18 +396,19 @@ def test_surrogate_step_paths_agree(cuda, trained):
     h = mdg.Handle(sw.drones_per_env, sw.flags)
     wp = torch.as_tensor(wl.waypoints(79, sw.n), device=cuda)
     out = []
-    for path in (mdg.MLP_PATH_MMA_SYNC, mdg.MLP_PATH_TCGEN05):
+    for path in (mdg.MLP_PATH_MMA_SYNC, mdg.MLP_PATH_TCGEN05, mdg.MLP_PATH_TCGEN05_PAIRS):
         m.set_path(path)
         st = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=cuda)
         m.step(h, st, wp, mdg.ACT_PID, 5, 4.0)
         torch.cuda.synchronize()
         out.append(sg.state13(st).cpu().numpy().astype(np.float64))
-    m.set_path(mdg.MLP_PATH_TCGEN05)
+    m.set_path(mdg.MLP_PATH_TCGEN05_PAIRS)  # the default
     # same network, same inputs and the same out-of-distribution decisions: the states differ
     # only by out_std times the difference of the standardised outputs, which the forward
     # test bounds by 1e-2 max(|y|, 1); |y| stays below ~4 in distribution, hence 0.05 out_std
     tol = 0.05 * data.out_std.cpu().numpy().astype(np.float64)
-    assert np.all(np.abs(out[1] - out[0]) <= tol[None, :])
+    for o in out[1:]:
+        assert np.all(np.abs(o - out[0]) <= tol[None, :])
     assert h.status()[0] == mdg.OK
 
 
