@@ -103,17 +103,43 @@ def tolerance_response(P, layout, x, integ, a_prev, action, act_types, n_sub, se
     return np.abs(a - b)
 
 
-def assert_horizon_close(xg, xo, response, n_sub, what=""):
-    """Short-horizon comparison over n_sub substeps: per component,
-    |gpu - ref| <= n_sub * (tol * max(|ref|, 1) + response), where `response` is
-    tolerance_response(): each of the n_sub substeps may add an error up to the per-substep
-    tolerance, and the dynamics propagate it at most like an error of that size at the start
-    (linear propagation of the per-substep bound)."""
+# Share of drones whose horizon bound is set by the dynamics' amplification rather than by the
+# tolerance in a component other than height and vertical velocity: the downwash's 1/dz^2 law
+# at near-equal heights amplifies an error mostly along z (measured with the oracle alone:
+# full aero 0.25% of drones, dense 7.3%; the single drone none).
+LOOSE_FACTOR = 10.0
+VERTICAL = (2, 9)
+
+
+def loose_share(xo, response):
+    """Share of drones with any component other than z and v_z whose response exceeds
+    LOOSE_FACTOR times its per-substep tolerance (there the horizon bound is wide)."""
     tol = np.zeros(13)
     tol[0:3] = tol[7:10] = RTOL_PV
     tol[10:13] = RTOL_W
     base = tol[None, :] * np.maximum(np.abs(xo), 1.0)
     base[:, 3:7] = ATOL_Q
+    r = np.delete(response / base, VERTICAL, axis=1)
+    return float((r > LOOSE_FACTOR).any(axis=1).mean()) if len(r) else 0.0
+
+
+def assert_horizon_close(xg, xo, response, n_sub, what="", max_loose=None):
+    """Short-horizon comparison over n_sub substeps: per component,
+    |gpu - ref| <= n_sub * (tol * max(|ref|, 1) + response), where `response` is
+    tolerance_response(): each of the n_sub substeps may add an error up to the per-substep
+    tolerance, and the dynamics propagate it at most like an error of that size at the start
+    (linear propagation of the per-substep bound). With max_loose, also that on all but that
+    share of the drones every component other than z and v_z is held to
+    n_sub * (1 + LOOSE_FACTOR) * tolerance (loose_share), so that the bound is not wide
+    everywhere."""
+    tol = np.zeros(13)
+    tol[0:3] = tol[7:10] = RTOL_PV
+    tol[10:13] = RTOL_W
+    base = tol[None, :] * np.maximum(np.abs(xo), 1.0)
+    base[:, 3:7] = ATOL_Q
+    if max_loose is not None:
+        share = loose_share(xo, response)
+        assert share <= max_loose, f"{what}: horizon bound wide on {share:.1%} of the drones"
     bound = n_sub * (base + response)
     err = np.abs(xg - xo)
     ratio = err / bound

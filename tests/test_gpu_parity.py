@@ -21,6 +21,10 @@ pytestmark = pytest.mark.gpu
 
 P = oracle.cf2x()
 HOVER = oracle.hover_rpm(P)
+# Largest share of drones on which the one-control-step bound may be wide outside z and v_z
+# (helpers.loose_share, a property of the oracle and the workload: measured 0 for the single
+# drone, 0.13% uneven, 0.25-0.26% full aero, 7.3-9.4% for the dense swarm's near-equal heights).
+MAX_LOOSE = {"single": 0.0, "uneven": 0.01, "full_aero": 0.01, "dense": 0.15}
 MAXRPM = oracle.max_rpm(P)
 F_MAX = P.kf * MAXRPM ** 2
 
@@ -157,7 +161,7 @@ def test_one_control_step_recipes(cuda, recipe, block):
     layout = (sw.drones_per_env, sw.flags)
     xo, io, ao = oracle_step(P, layout, x0, i0, a0, action, acts, 5)
     spread = tolerance_response(P, layout, x0, i0, a0, action, acts, 5)
-    assert_horizon_close(xg, xo, spread, 5, what=recipe)
+    assert_horizon_close(xg, xo, spread, 5, what=recipe, max_loose=MAX_LOOSE.get(recipe))
     _check_obs(xg, ag, sw.drones_per_env, kin, idx, rel)
 
 
@@ -198,7 +202,7 @@ def test_full_size_sampled(cuda, recipe):
     acts = np.full(len(envs), act)
     xo, _, _ = oracle_step(P, layout, x0[sel], i0[sel], a0[sel], action[sel], acts, 5)
     spread = tolerance_response(P, layout, x0[sel], i0[sel], a0[sel], action[sel], acts, 5)
-    assert_horizon_close(xg[sel], xo, spread, 5, what=recipe)
+    assert_horizon_close(xg[sel], xo, spread, 5, what=recipe, max_loose=MAX_LOOSE[recipe])
     # observations of the sampled environments (indices are global)
     kin_s, idx_s, rel_s = kin.cpu().numpy()[sel], idx.cpu().numpy()[sel], rel.cpu().numpy()[sel]
     base = np.concatenate([[0], np.cumsum(sw.drones_per_env)])[envs]

@@ -325,11 +325,14 @@ def test_surrogate_step_gains_over_no_network(cuda, trained):
     assert float(regular.float().mean()) > 0.5
     # One-step error of the surrogate vs the plain integrator against the error of a
     # predictor without the network (state unchanged). The rotational change depends on
-    # the motor torques alone and is learned closely; the translational change is
-    # dominated by the downwash law's 1/dz^2 at small height differences, which the
-    # inputs do not pin down, so there the network is only required not to be worse.
+    # the motor torques alone and is learned closely (this small training: 0.22 quaternion,
+    # 0.085 body rate). The translational change is dominated by the downwash law's 1/dz^2:
+    # the formation's drones fly at nearly equal heights (median 1.1 cm to the nearest other
+    # height), which the network does not represent; velocity is required to gain (0.955
+    # measured), position only not to lose more than 10% (1.06 measured: the network's
+    # spurious vertical motion costs about what it gains).
     for name, sl, bound in (("quaternion", slice(3, 7), 0.3), ("body rate", slice(10, 13), 0.3),
-                            ("position", slice(0, 3), 1.1), ("velocity", slice(7, 10), 1.1)):
+                            ("position", slice(0, 3), 1.1), ("velocity", slice(7, 10), 1.0)):
         err = (xs[regular, sl] - xp[regular, sl]).pow(2).mean().sqrt()
         base = true_d[regular, sl].pow(2).mean().sqrt()
         assert err < bound * base, f"{name}: surrogate rms error {float(err):.3g} vs no-network {float(base):.3g}"
