@@ -560,7 +560,8 @@ int mdg_mlp_set_normalization(mdg_mlp m, const float* in_mean, const float* in_s
 /* x = bf16((raw - mean) / std), raw device [rows][41] FP32, x device [rows][64] bf16 (uint16). */
 int mdg_mlp_standardize(mdg_mlp m, const float* raw, uint16_t* x, int64_t rows, void* stream);
 /* Forward pass: x device [B][64] bf16, y device [B][32] FP32 (standardised outputs);
- * B a multiple of 128, at most max_batch. */
+ * B a multiple of 128, at most max_batch. On MDG_MLP_PATH_TCGEN05_PAIRS x is read by TMA
+ * (a tensor map over [B][64]) and must be 16-byte aligned (else MDG_ERR_CUDA). */
 int mdg_mlp_forward(mdg_mlp m, const uint16_t* x, float* y, int32_t B, void* stream);
 /* Gradient of the MSE between the forward output and the standardised targets
  * t device [B][32] (columns 13..31 ignored) into the surrogate's gradient buffer;

@@ -29,6 +29,7 @@
 // MDG_STATUS_TIMEOUT in the status word, every role leaves its loop, the copies and MMAs
 // already issued are waited for (again with a bound), the tensor memory is freed and the
 // block returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -470,47 +471,55 @@ __global__ void __launch_bounds__(kThreads, 1)
 // tile needs one accumulator, and two tiles, A in columns 0-255 and B in 256-511, alternate:
 // while the epilogue works on one tile's layer, the tensor cores run the other tile's. The
 // MMA thread issues, per pair of tiles, A.L1, B.L1 (one W1 chunk for both), A.L2, B.L2, A.L3,
-// B.L3, A.L4, B.L4 (one W4 load). The W2/W3 chunks stream through a two-slot ring: tile A
-// takes K chunks 0-3 in order, tile B then takes 3 and 2 while they are still resident and
-// reloads 1 and 0, so a hidden layer costs six chunk loads per pair instead of eight (tile B
-// sums its K chunks in the order 3, 2, 1, 0; tile A's arithmetic is the single-tile kernel's).
+// B.L3, A.L4, B.L4 (one W4 load). The W2/W3 chunks stream through a three-slot ring: tile A
+// takes K chunks 0-3 in order, tile B then takes 1, 2 and 3 while they are still resident and
+// reloads 0, so a hidden layer costs five chunk loads per pair instead of eight (tile B sums
+// its K chunks in the order 1, 2, 3, 0; tile A's arithmetic is the single-tile kernel's). The
+// slots are released in the order they were filled, so load n of the block goes to slot n % 3.
+// The inputs have no buffer of their own: each tile's [128 x 64] input is written by TMA (a
+// tensor map with the 128-byte swizzle) into chunk 0 of its activation buffer once the
+// previous pair's layer 4 has read that buffer (ActFree), prefetched into L2 a pair ahead.
 // A layer's first MMA into a tile's accumulator waits for the epilogue to have drained the
 // previous layer (AccDrained); tile A's MMA on K chunk c waits for chunk c of the previous
-// layer's activations (ActFull), tile B's layer, which starts with chunk 3, waits once for
-// chunk 3 (each epilogue warp writes the chunks in order, so 3 implies all). The next pair's
-// inputs are fetched in two parts between weight loads that have slack (after the fifth and
-// the eleventh), so that the weight ring never waits behind them. Waits are bounded as above,
-// with the same exit.
+// layer's activations (ActFull); tile B's layer waits once for chunk 3 (each epilogue warp
+// writes the chunks in order, so 3 implies all). Waits are bounded as above, with the same exit.
 constexpr uint32_t kPActA = 0;                          // tile A activations: 4 chunks
 constexpr uint32_t kPActB = 4 * kChunkBytes;            // tile B activations
-constexpr uint32_t kPX = 8 * kChunkBytes;               // inputs of A, then of B
-constexpr uint32_t kPSlot = 10 * kChunkBytes;           // two weight slots
-constexpr int kPSlots = 2;
+constexpr uint32_t kPSlot = 8 * kChunkBytes;            // three weight slots
+constexpr int kPSlots = 3;
 constexpr uint32_t kPDynBytes = kPSlot + kPSlots * kSlotBytes;
 static_assert(kPDynBytes + 1024 + 512 <= 232448, "shared memory of one paired block");
-constexpr int kPLoadsPerPair = 14;  // W1, W2 c0-3, W2 c1, c0, W3 c0-3, W3 c1, c0, W4
+constexpr int kPLoadsPerPair = 12;  // W1, W2 c0-3, W2 c0 (B), W3 c0-3, W3 c0 (B), W4
+static_assert(kPLoadsPerPair % kPSlots == 0, "every pair starts at slot 0");
 
 enum {
-    kPBarWFull = 0,                       // [2]
-    kPBarWEmpty = kPBarWFull + kPSlots,   // [2]
-    kPBarXFull = kPBarWEmpty + kPSlots,   // [2] tiles A, B
-    kPBarXEmpty = kPBarXFull + 2,         // [2]
-    kPBarAccFull = kPBarXEmpty + 2,       // [2] MMA commit: the tile's layer is accumulated
+    kPBarWFull = 0,                       // [3]
+    kPBarWEmpty = kPBarWFull + kPSlots,   // [3]
+    kPBarXFull = kPBarWEmpty + kPSlots,   // [2] TMA: tile A's, B's inputs landed
+    kPBarActFree = kPBarXFull + 2,        // [2] MMA commit: layer 4 has read the tile's activations
+    kPBarAccFull = kPBarActFree + 2,      // [2] MMA commit: the tile's layer is accumulated
     kPBarAccDrained = kPBarAccFull + 2,   // [2] 16 epilogue warps: the accumulator is in registers
     kPBarActFull = kPBarAccDrained + 2,   // [2][4] 16 epilogue warps: activation chunk c written
     kPBarMmaDone = kPBarActFull + 8,
     kPNumBars
 };
 
-// Load k of a pair: its image index (0 W1; 1-4 W2 c0-3, 5 W2 c1, 6 W2 c0; 7-10 W3 c0-3,
-// 11 W3 c1, 12 W3 c0; 13 W4), its slot, and its position among the pair's seven loads into
-// that slot (slot 0: loads 0 2 4 5 7 9 12; slot 1: 1 3 6 8 10 11 13). The slots follow from
-// the order in which the MMA thread releases them; each holds seven loads per pair, so the
-// n-th load into a slot (n = 7 pairs + position) completes phase n of its WFull barrier.
-__device__ __forceinline__ int pair_load_image(int k) { return (int)((0x95687651243210ull >> (4 * k)) & 15u); }
-__device__ __forceinline__ int pair_load_slot(int k) { return (int)((0x2d4au >> k) & 1u); }
-__device__ __forceinline__ int pair_load_pos(int k) { return (int)((0x36b2b89a240ull >> (3 * k)) & 7u); }
-constexpr int kPLoadsPerSlot = 7;
+// Image index of load k of a pair: 0 W1; 1-4 W2 c0-3, 5 W2 c0; 6-9 W3 c0-3, 10 W3 c0; 11 W4.
+__device__ __forceinline__ int pair_load_image(int k) { return (int)((0x958765143210ull >> (4 * k)) & 15u); }
+
+// TMA of one [128 x 64] bf16 input tile (rows row..row+127) into 128-byte-swizzled shared
+// memory, completing on mbar; and its prefetch into L2.
+__device__ __forceinline__ void tma_rows(uint32_t dst, const CUtensorMap* map, int row, uint32_t mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(row), "r"(mbar) : "memory");
+}
+__device__ __forceinline__ void tma_rows_prefetch(const CUtensorMap* map, int row)
+{
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];\n"
+                 ::"l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(row) : "memory");
+}
 
 __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t r[16])
 {
@@ -522,7 +531,7 @@ __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t r[16])
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-    mlp_umma_pair_kernel(const __nv_bfloat16* __restrict__ x, float* __restrict__ y, int n_tiles,
+    mlp_umma_pair_kernel(const __grid_constant__ CUtensorMap xmap, float* __restrict__ y, int n_tiles,
                          const uint8_t* __restrict__ w_img, const float* __restrict__ master, MlpView w,
                          uint32_t* status, int wait_limit, int spin_limit)
 {
@@ -533,7 +542,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ int s_abort;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t act0 = smem_u32(base + kPActA), x0 = smem_u32(base + kPX), slot_a = smem_u32(base + kPSlot);
+    const uint32_t act0 = smem_u32(base + kPActA), slot_a = smem_u32(base + kPSlot);
     const uint32_t bar0 = smem_u32(&bars[0]);
     auto bar = [bar0](int i) { return bar0 + 8u * (uint32_t)i; };
     volatile int* abort = &s_abort;
@@ -558,66 +567,57 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = s_tmem;
 
     if (warp == kProdWarp) {
-        // ---------------- producer ----------------
-        int issued0 = 0, issued1 = 0;  // weight loads issued into slots 0 and 1
-        int s = 0;                     // pairs of this block
-        bool ok = true;
-        auto load_x = [&](int tile, int t) {
-            const __nv_bfloat16* src = x + (size_t)tile * kRows * MDG_MLP_IN_PAD;
-            const uint32_t dst = x0 + (uint32_t)t * kChunkBytes;
-#pragma unroll 4
-            for (int i = lane; i < kRows * 8; i += 32) {
-                const int r = i >> 3, k8 = i & 7;
-                cp_async16(dst + r * 128 + ((k8 ^ (r & 7)) << 4), src + r * MDG_MLP_IN_PAD + k8 * 8);
+        // ---------------- producer (one thread) ----------------
+        if (lane == 0) {
+            int issued = 0, x_issued0 = 0, x_issued1 = 0;
+            bool ok = true;
+            auto load_x = [&](int pr, int t) {
+                mbar_expect_tx(bar(kPBarXFull + t), kChunkBytes);
+                tma_rows(act0 + (uint32_t)t * 4 * kChunkBytes, &xmap, (2 * pr + t) * kRows, bar(kPBarXFull + t));
+                if (t) ++x_issued1; else ++x_issued0;
+            };
+            if (blockIdx.x < n_pairs) {  // the grid never exceeds the pair count
+                load_x(blockIdx.x, 0);
+                if (2 * blockIdx.x + 1 < n_tiles) load_x(blockIdx.x, 1);
             }
-        };
-        if (blockIdx.x < n_pairs) {  // the grid never exceeds the pair count
-            load_x(2 * blockIdx.x, 0);
-            if (2 * blockIdx.x + 1 < n_tiles) load_x(2 * blockIdx.x + 1, 1);
-        }
-        for (int pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x, ++s) {
-            const bool hasB = 2 * pr + 1 < n_tiles;
-            const int next = pr + (int)gridDim.x;
-            for (int k = 0; k < kPLoadsPerPair; ++k) {
-                const int slot = pair_load_slot(k), n = kPLoadsPerSlot * s + pair_load_pos(k);
-                if (n > 0)
-                    ok = __all_sync(0xffffffffu,
-                                    mbar_spin(bar(kPBarWEmpty + slot), (n - 1) & 1, abort, status, 0, spin_limit));
-                if (!ok) break;
-                const int img = pair_load_image(k);
-                const uint32_t bytes = img == 9 ? 16384u : kSlotBytes;
-                if (lane == 0) {
+            int s = 0;  // pairs of this block
+            for (int pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x, ++s) {
+                const int next = pr + (int)gridDim.x;
+                const bool hasB = 2 * pr + 1 < n_tiles;
+                for (int k = 0; k < kPLoadsPerPair; ++k) {
+                    const int n = kPLoadsPerPair * s + k, slot = k % kPSlots;
+                    if (n >= kPSlots)
+                        ok = mbar_spin(bar(kPBarWEmpty + slot), (n / kPSlots - 1) & 1, abort, status, 0, spin_limit);
+                    if (!ok) break;
+                    const int img = pair_load_image(k);
+                    const uint32_t bytes = img == 9 ? 16384u : kSlotBytes;
                     mbar_expect_tx(bar(kPBarWFull + slot), bytes);
                     bulk_g2s(slot_a + slot * kSlotBytes, w_img + (size_t)img * kSlotBytes, bytes, bar(kPBarWFull + slot));
-                }
-                if (slot) ++issued1; else ++issued0;
-                __syncwarp();
-                if (k == 0) {  // this pair's inputs (issued during the previous pair) have landed
-                    asm volatile("cp.async.wait_all;\n" ::: "memory");
-                    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                    __syncwarp();
-                    if (lane == 0) {
-                        mbar_arrive(bar(kPBarXFull + 0));
-                        if (hasB) mbar_arrive(bar(kPBarXFull + 1));
+                    ++issued;
+                    if (k == 1 && s > 0) {
+                        // the previous pair's layer 4 has read tile A's (then B's) activations:
+                        // this pair's inputs go into their chunk 0
+                        ok = mbar_spin(bar(kPBarActFree + 0), (s - 1) & 1, abort, status, 0, spin_limit);
+                        if (!ok) break;
+                        load_x(pr, 0);
+                        ok = mbar_spin(bar(kPBarActFree + 1), (s - 1) & 1, abort, status, 0, spin_limit);
+                        if (!ok) break;
+                        if (hasB) load_x(pr, 1);
+                    } else if (k == 2 && next < n_pairs) {
+                        tma_rows_prefetch(&xmap, 2 * next * kRows);
+                        if (2 * next + 1 < n_tiles) tma_rows_prefetch(&xmap, (2 * next + 1) * kRows);
                     }
-                } else if (k == 4 && next < n_pairs) {
-                    // layer 1 of this pair is done with the input buffers: the next pair's A
-                    ok = __all_sync(0xffffffffu, mbar_wait(bar(kPBarXEmpty + 0), s & 1, abort, status, wait_limit));
-                    if (ok) ok = __all_sync(0xffffffffu, mbar_wait(bar(kPBarXEmpty + 1), s & 1, abort, status, wait_limit));
-                    if (!ok) break;
-                    load_x(2 * next, 0);
-                } else if (k == 10 && next < n_pairs && 2 * next + 1 < n_tiles) {
-                    load_x(2 * next + 1, 1);  // and its B
                 }
             }
-        }
-        // drain: every copy issued has landed before the block may exit
-        asm volatile("cp.async.wait_all;\n" ::: "memory");
-        if (lane == 0)
+            // drain: every copy issued has landed before the block may exit
             for (int slot = 0; slot < kPSlots; ++slot) {
-                const int uses = slot ? issued1 : issued0;
-                if (uses > 0) mbar_wait(bar(kPBarWFull + slot), (uses - 1) & 1, nullptr, status, kWaitLimit);
+                int last = issued - 1;
+                while (last >= 0 && last % kPSlots != slot) --last;
+                if (last >= 0) mbar_wait(bar(kPBarWFull + slot), (last / kPSlots) & 1, nullptr, status, kWaitLimit);
             }
+            if (x_issued0 > 0) mbar_wait(bar(kPBarXFull + 0), (x_issued0 - 1) & 1, nullptr, status, kWaitLimit);
+            if (x_issued1 > 0) mbar_wait(bar(kPBarXFull + 1), (x_issued1 - 1) & 1, nullptr, status, kWaitLimit);
+        }
         __syncwarp();
     } else if (warp == kMmaWarp) {
         // ---------------- MMA issue (one thread) ----------------
@@ -629,11 +629,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t n_drain = 0u, n_act = 0u;
             bool ok = true;
             auto wfull = [&](int k) {
-                return mbar_spin(bar(kPBarWFull + pair_load_slot(k)), (kPLoadsPerSlot * s + pair_load_pos(k)) & 1, abort,
-                                 status, 0, spin_limit);
+                const int n = kPLoadsPerPair * s + k;
+                return mbar_spin(bar(kPBarWFull + k % kPSlots), (n / kPSlots) & 1, abort, status, 0, spin_limit);
             };
-            auto wslot = [&](int k) { return slot_a + (uint32_t)pair_load_slot(k) * kSlotBytes; };
-            auto release = [&](int k) { mma_commit(bar(kPBarWEmpty + pair_load_slot(k))); };
+            auto wslot = [&](int k) { return slot_a + (uint32_t)(k % kPSlots) * kSlotBytes; };
+            auto release = [&](int k) { mma_commit(bar(kPBarWEmpty + k % kPSlots)); };
             // the first MMA of a layer into tile t's accumulator: the previous layer drained
             auto drained = [&](int t) {
                 const bool r = mbar_spin(bar(kPBarAccDrained + t), (n_drain >> (16 * t)) & 1, abort, status, 0, spin_limit);
@@ -655,45 +655,39 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x, ++s) {
                 const bool hasB = 2 * pr + 1 < n_tiles;
                 const int nt = hasB ? 2 : 1;
-                // layer 1: x [128 x 64] . W1^T for A then B, one W1 chunk (load 0)
+                // layer 1: the inputs in chunk 0 of each tile's activation buffer, one W1 chunk (load 0)
                 ok = wfull(0);
                 for (int t = 0; t < nt && ok; ++t) {
                     ok = mbar_wait(bar(kPBarXFull + t), s & 1, abort, status, wait_limit) && (s == 0 || drained(t));
                     if (!ok) break;
-                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                    const uint32_t xs = x0 + (uint32_t)t * kChunkBytes, ws = wslot(0);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        mma_bf16_ss(tmem + 256u * t, sw128_desc(xs + k * 32), sw128_desc(ws + k * 32), id_h, k != 0);
+                    chunk(t, 0, wslot(0), id_h, true);
                     mma_commit(bar(kPBarAccFull + t));
-                    mma_commit(bar(kPBarXEmpty + t));
                 }
                 if (!ok) break;
-                if (!hasB) mma_commit(bar(kPBarXEmpty + 1));  // keeps the producer's phase count of B
                 release(0);
-                // layers 2 and 3 (loads k0..k0+5): A chunks 0-3 in order, each as soon as the
-                // epilogue has written it; B chunks 3, 2 (A's loads k0+3, k0+2), 1, 0 (k0+4, k0+5)
+                // layers 2 and 3 (loads k0..k0+4): A chunks 0-3 in order, each as soon as the
+                // epilogue has written it; B chunks 1, 2, 3 (A's loads, still resident) and 0 (reloaded)
                 for (int l = 1; l < 3 && ok; ++l) {
-                    const int k0 = l == 1 ? 1 : 7;
+                    const int k0 = l == 1 ? 1 : 6;
                     for (int c = 0; c < 4 && ok; ++c) {
                         ok = wfull(k0 + c) && (c != 0 || drained(0)) && act(0, c);
                         if (!ok) break;
                         chunk(0, c, wslot(k0 + c), id_h, c == 0);
                         if (c == 3) mma_commit(bar(kPBarAccFull + 0));
-                        if (c < 2) release(k0 + c);
+                        if (c == 0) release(k0);
                     }
                     if (!ok) break;
                     n_act += 1u;
                     for (int i = 0; i < 4 && ok; ++i) {
-                        const int c = 3 - i;
-                        const int k = i == 0 ? k0 + 3 : i == 1 ? k0 + 2 : i == 2 ? k0 + 4 : k0 + 5;
+                        const int c = (i + 1) & 3;
+                        const int k = i < 3 ? k0 + 1 + i : k0 + 4;
                         if (hasB) {
-                            ok = (i < 2 || wfull(k)) && (i != 0 || (drained(1) && act(1, 3)));
+                            ok = (i < 3 || wfull(k)) && (i != 0 || (drained(1) && act(1, 3)));
                             if (!ok) break;
                             chunk(1, c, wslot(k), id_h, i == 0);
                             if (i == 3) mma_commit(bar(kPBarAccFull + 1));
                         } else {
-                            ok = i < 2 || wfull(k);  // tile B missing: its loads still land, and are released
+                            ok = i < 3 || wfull(k);  // tile B missing: its load still lands, and is released
                             if (!ok) break;
                         }
                         release(k);
@@ -701,11 +695,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (ok && hasB) n_act += 1u << 16;
                 }
                 if (!ok) break;
-                // layer 4: W4 [32 x 256] as four [32 x 64] chunks in one slot (load 13), A then B
-                ok = wfull(13);
+                // layer 4: W4 [32 x 256] as four [32 x 64] chunks in one slot (load 11), A then B;
+                // after each, the tile's activation buffer is free for the next pair's inputs
+                ok = wfull(11);
                 for (int t = 0; t < nt && ok; ++t) {
                     ok = drained(t);
-                    const uint32_t wsl = wslot(13);
+                    const uint32_t wsl = wslot(11);
                     for (int c = 0; c < 4 && ok; ++c) {
                         if (t == 0 || c == 0) ok = act(t, t == 0 ? c : 3);
                         if (!ok) break;
@@ -719,9 +714,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (!ok) break;
                     n_act += 1u << (16 * t);
                     mma_commit(bar(kPBarAccFull + t));
+                    mma_commit(bar(kPBarActFree + t));
                 }
                 if (!ok) break;
-                release(13);
+                if (!hasB) mma_commit(bar(kPBarActFree + 1));
+                release(11);
             }
             // nothing in flight before the tensor memory is freed
             mma_commit(bar(kPBarMmaDone));
@@ -1113,12 +1110,32 @@ cudaError_t mlp_build_image(const MlpView& w, void* img, cudaStream_t s)
     return cudaGetLastError();
 }
 
+namespace {
+// cuTensorMapEncodeTiled, looked up through the runtime (no link against the driver library).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+}  // namespace
+
 cudaError_t mlp_forward_umma_pairs(const MlpView& w, const void* img, const void* x, int B, float* y,
                                    uint32_t* status, int wait_limit, int spin_limit, cudaStream_t s)
 {
     if (B % kRows) return cudaErrorInvalidValue;
     const int n_tiles = B / kRows;
     if (n_tiles == 0) return cudaSuccess;
+    if (reinterpret_cast<uintptr_t>(x) % 16) return cudaErrorMisalignedAddress;  // TMA source
     static bool attr_done[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1129,13 +1146,24 @@ cudaError_t mlp_forward_umma_pairs(const MlpView& w, const void* img, const void
         if (e != cudaSuccess) return e;
         attr_done[dev] = true;
     }
+    const EncodeTiledFn encode = encode_tiled();
+    if (!encode) return cudaErrorNotSupported;
+    // the inputs [B x 64] bf16, row-major: boxes of one tile (128 rows x 128 bytes), 128-byte swizzle
+    CUtensorMap xmap;
+    const cuuint64_t dims[2] = {MDG_MLP_IN_PAD, (cuuint64_t)B};
+    const cuuint64_t strides[1] = {MDG_MLP_IN_PAD * sizeof(__nv_bfloat16)};
+    const cuuint32_t box[2] = {MDG_MLP_IN_PAD, kRows};
+    const cuuint32_t elem_strides[2] = {1, 1};
+    if (encode(&xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(x), dims, strides, box, elem_strides,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
     int n_sm = 152;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     const int n_pairs = (n_tiles + 1) / 2;
     const int grid = n_pairs < n_sm ? n_pairs : n_sm;
-    mlp_umma_pair_kernel<<<grid, kThreads, kUmmaPairSmem, s>>>(static_cast<const __nv_bfloat16*>(x), y, n_tiles,
-                                                               static_cast<const uint8_t*>(img), w.master, w, status,
-                                                               wait_limit, spin_limit);
+    mlp_umma_pair_kernel<<<grid, kThreads, kUmmaPairSmem, s>>>(xmap, y, n_tiles, static_cast<const uint8_t*>(img),
+                                                               w.master, w, status, wait_limit, spin_limit);
     return cudaGetLastError();
 }
 
