@@ -69,7 +69,7 @@ HEAD_START_CYCLES = 400_000
 # DRAM traffic of one step-kernel launch on the full-aero workload, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel source whose
 # sha256 prefix is recorded with it; profiles/ holds the capture's summary.
-NCU_TRAFFIC = {"kernel_sha": "940b554927d2988f", "bytes": 6319104 + 0}
+NCU_TRAFFIC = {"kernel_sha": "cf5d9e7547c2a1c2", "bytes": 6319104 + 0}
 
 
 def kernel_sha() -> str:
