@@ -248,22 +248,32 @@ cudaError_t gemm(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, i
     return cudaGetLastError();
 }
 
-// db[n] = sum over rows of dz[m][n] (bf16 input, FP32 sum); 32 columns x 8 row-strands per block.
+// db[n] = sum over rows of dz[m][n] (bf16 input, FP32 sums): one block per 64 columns and 256
+// rows (each lane two adjacent columns, eight warps over the rows), its partial sums added to
+// db (zeroed by the launcher) with atomics, so that a batch of 8192 rows spreads over 32 x N/64
+// blocks instead of N/32.
+constexpr int kBiasRows = 256;
 __global__ void __launch_bounds__(256) bias_grad_kernel(const bf16* __restrict__ dz, int M, int N, float* db)
 {
-    __shared__ float part[8][33];
+    __shared__ float2 part[8][32];
     const int x = threadIdx.x & 31, y = threadIdx.x >> 5;
-    const int n = blockIdx.x * 32 + x;
-    float s = 0.f;
+    const int n = blockIdx.x * 64 + 2 * x;
+    const int m0 = blockIdx.y * kBiasRows, m1 = min(M, m0 + kBiasRows);
+    float2 acc = make_float2(0.f, 0.f);
     if (n < N)
-        for (int m = y; m < M; m += 8) s += __bfloat162float(dz[(size_t)m * N + n]);
-    part[y][x] = s;
+        for (int m = m0 + y; m < m1; m += 8) {
+            const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(dz + (size_t)m * N + n));
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+    part[y][x] = acc;
     __syncthreads();
     if (y == 0 && n < N) {
-        float t = 0.f;
+        float2 t = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) t += part[k][x];
-        db[n] = t;
+        for (int k = 0; k < 8; ++k) t.x += part[k][x].x, t.y += part[k][x].y;
+        atomicAdd(db + n, t.x);
+        atomicAdd(db + n + 1, t.y);
     }
 }
 
@@ -345,8 +355,7 @@ cudaError_t mlp_backward(const MlpView& w, const void* x, int B, float* const z_
             e = gemm<64, true, true>(dcur, fan_out, hin, fan_in, fan_out, fan_in, B, eg, s);
         }
         if (e != cudaSuccess) return e;
-        bias_grad_kernel<<<(fan_out + 31) / 32, 256, 0, s>>>(dcur, B, fan_out, grad + w.b_off[l]);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = mlp_bias_grad(dcur, B, fan_out, grad + w.b_off[l], s)) != cudaSuccess) return e;
         if (l > 0) {  // dH_{l-1} = dZ_l W_l (W_l stored [fan_out][fan_in] = [K][N]) -> dZ_{l-1}
             EpiDx ex{z_hidden[l - 1], static_cast<bf16*>(dz_hidden[l - 1]), fan_in};
             e = gemm<64, false, true>(dcur, fan_out, w16 + w.w_off[l], fan_in, B, fan_in, fan_out, ex, s);
@@ -374,7 +383,11 @@ cudaError_t mlp_refresh_bf16(const MlpView& w, cudaStream_t s)
 
 cudaError_t mlp_bias_grad(const void* dz, int M, int N, float* db, cudaStream_t s)
 {
-    bias_grad_kernel<<<(N + 31) / 32, 256, 0, s>>>(static_cast<const bf16*>(dz), M, N, db);
+    if (N % 2) return cudaErrorInvalidValue;  // the layer widths (256, 32) are even
+    cudaError_t e = cudaMemsetAsync(db, 0, (size_t)N * sizeof(float), s);
+    if (e != cudaSuccess || M == 0) return e;
+    const dim3 grid((N + 63) / 64, (M + kBiasRows - 1) / kBiasRows);
+    bias_grad_kernel<<<grid, 256, 0, s>>>(static_cast<const bf16*>(dz), M, N, db);
     return cudaGetLastError();
 }
 
