@@ -496,3 +496,61 @@ def test_fit_normalization_matches_its_definition(cuda):
     np.testing.assert_allclose(xs[:n_cmp, :mdg.MLP_IN], zin, rtol=1e-2, atol=1e-2)
     assert np.all(xs[:, mdg.MLP_IN:] == 0) and np.all(ts[:, mdg.MLP_OUT:] == 0)
     np.testing.assert_allclose(ts[:n_cmp, :mdg.MLP_OUT], Z[keep2][:n_cmp, mdg.MLP_IN:], rtol=1e-4, atol=1e-4)
+
+
+@pytest.mark.parametrize("recipe", ["full_aero", "dense", "dense_pid"])
+def test_surrogate_step_composes_its_parts(cuda, trained, recipe):
+    """mdg_surrogate_step equals its parts called one by one: the plain integrator's inputs of
+    the state and its RPMs (mdg_transition), their standardisation (mdg_mlp_standardize), the
+    network (mdg_mlp_forward) and the de-standardised change added on the host (quaternion
+    renormalised), on 4-drone (PID) and 64-drone (RPM and PID) environments. With the trained box every
+    environment with an input outside it is counted for the fallback; with an unbounded box
+    none is, and every drone is compared."""
+    _, data, _ = trained
+    sw = wl.full_aero(81, n_envs=256) if recipe == "full_aero" else wl.dense(82, n_envs=16)
+    h = mdg.Handle(sw.drones_per_env, sw.flags)
+    if recipe == "dense":
+        action, act = torch.as_tensor(wl.rpm_actions(82, sw.n, 0, HOVER), device=cuda), mdg.ACT_RPM
+    else:
+        action, act = torch.as_tensor(wl.waypoints(81, sw.n), device=cuda), mdg.ACT_PID
+    in_mean, in_std, out_mean, out_std, in_lo, in_hi = data.stats()
+    for bounded in (True, False):
+        m = mdg.MLP(sw.n + 128, wl.mlp_init(23))
+        lo, hi = (in_lo, in_hi) if bounded else (np.full_like(in_lo, -1e30), np.full_like(in_hi, 1e30))
+        m.set_normalization(in_mean, in_std, out_mean, out_std, lo, hi)
+        ood_z = 4.0 if bounded else 1e30
+        state = mdg.pack_state(sw.p, sw.q, sw.v, sw.w, device=cuda)
+        before = state.clone()
+        nfb = torch.zeros(1, dtype=torch.int32, device=cuda)
+        m.step(h, state, action, act, 5, ood_z, nfb)
+        # the parts: RPMs (the PID on a copy of the state), inputs, standardisation, network
+        s2 = before.clone()
+        rpm = torch.empty((sw.n, 4), device=cuda)
+        if act == mdg.ACT_PID:
+            h.pid(s2, action, rpm)
+        else:
+            rpm.copy_(action.clamp(0.0, mdg.Constants.cf2x().max_rpm()))
+        raw = torch.empty((sw.n, mdg.MLP_IN), device=cuda)
+        delta = torch.empty((sw.n, mdg.MLP_OUT), device=cuda)
+        applied = torch.empty((sw.n, 4), device=cuda)
+        h.transition(s2.clone(), rpm, applied, raw, delta)
+        rows = (sw.n + 127) // 128 * 128
+        x = torch.zeros((rows, mdg.MLP_IN_PAD), dtype=torch.bfloat16, device=cuda)
+        m.standardize(raw, x[:sw.n])
+        y = torch.empty((rows, mdg.MLP_OUT_PAD), device=cuda)
+        m.forward(x, y)
+        torch.cuda.synchronize()
+        rawn = raw.cpu().numpy().astype(np.float64)
+        z = (rawn - in_mean) / in_std
+        bad = ~((np.abs(z) <= ood_z) & (rawn >= lo) & (rawn <= hi))
+        env_bad = bad.reshape(sw.n_envs, -1).any(axis=1)
+        assert int(nfb) == int(env_bad.sum()), (int(nfb), int(env_bad.sum()))
+        if bounded:
+            continue
+        assert int(nfb) == 0
+        d = y[:sw.n, :mdg.MLP_OUT].double().cpu().numpy() * out_std + out_mean
+        x0 = sg.state13(before).double().cpu().numpy()
+        want = x0 + d
+        want[:, 3:7] /= np.linalg.norm(want[:, 3:7], axis=1, keepdims=True)
+        got = sg.state13(state).double().cpu().numpy()
+        assert np.all(np.abs(got - want) <= 1e-5 * np.maximum(np.abs(want), 1.0)), np.abs(got - want).max()
