@@ -239,9 +239,23 @@ size_t mlp_image_bytes();
 cudaError_t mlp_build_image(const MlpView& w, void* img, cudaStream_t s);
 cudaError_t mlp_forward_umma(const MlpView& w, const void* img, const void* x, int B, float* y, uint32_t* status,
                              int wait_limit, int spin_limit, cudaStream_t s);
-// The same with two 128-row tiles in flight per block (one 256-column accumulator each).
+// The surrogate's update of the state by the network's prediction, done in the output stage
+// of the paired kernel instead of writing y: for every row g < n whose environment
+// (g / uniform_N) is not flagged, p, v, omega += out_mean + out_std * y and the quaternion the
+// same, renormalised (the arithmetic of surrogate_apply_kernel). state: the [6][n] planes.
+struct MlpApply {
+    float4* state;
+    long long n;
+    int uniform_N;
+    const unsigned* env_flag;  // [n_envs]
+    const float* out_mean;     // [13]
+    const float* out_std;      // [13]
+};
+// The same with two 128-row tiles in flight per block (one 256-column accumulator each); with
+// apply, the state is updated and y is not written.
 cudaError_t mlp_forward_umma_pairs(const MlpView& w, const void* img, const void* x, int B, float* y,
-                                   uint32_t* status, int wait_limit, int spin_limit, cudaStream_t s);
+                                   uint32_t* status, int wait_limit, int spin_limit, cudaStream_t s,
+                                   const MlpApply* apply = nullptr);
 // Training on tcgen05: the loss of the standardised targets t ([B][32], columns 13..31
 // ignored) added to *loss_acc and every parameter's gradient written to grad (flat FP32
 // layout); B a multiple of 128. wT must hold the current weights' transposes.

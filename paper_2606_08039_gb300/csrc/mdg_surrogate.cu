@@ -119,7 +119,8 @@ void destroy_mlp(mdg_mlp m)
 }
 
 // The tcgen05 kernel reads the weights from their image; rebuild it after they change.
-cudaError_t forward_umma(mdg_mlp m, const void* x, int B, float* y, uint32_t* status, cudaStream_t s)
+cudaError_t forward_umma(mdg_mlp m, const void* x, int B, float* y, uint32_t* status, cudaStream_t s,
+                         const mdg::MlpApply* apply = nullptr)
 {
     if (m->img_stale) {
         cudaError_t e = mdg::mlp_build_image(m->view(), m->img, s);
@@ -127,7 +128,7 @@ cudaError_t forward_umma(mdg_mlp m, const void* x, int B, float* y, uint32_t* st
         m->img_stale = false;
     }
     if (m->path == MDG_MLP_PATH_TCGEN05_PAIRS)
-        return mdg::mlp_forward_umma_pairs(m->view(), m->img, x, B, y, status, m->wait_limit, m->spin_limit, s);
+        return mdg::mlp_forward_umma_pairs(m->view(), m->img, x, B, y, status, m->wait_limit, m->spin_limit, s, apply);
     return mdg::mlp_forward_umma(m->view(), m->img, x, B, y, status, m->wait_limit, m->spin_limit, s);
 }
 
@@ -491,9 +492,15 @@ int mdg_surrogate_step(mdg_handle h, mdg_mlp m, float* state, const float* actio
     if (e == cudaSuccess && n_pad > h->n_drones)  // padding rows of the network input
         e = cudaMemsetAsync(m->x + (size_t)h->n_drones * MDG_MLP_IN_PAD, 0,
                             (size_t)(n_pad - h->n_drones) * MDG_MLP_IN_PAD * 2, s);
+    bool fused = false;
     if (e == cudaSuccess) e = mdg::launch_surrogate_prepare(a, h->n_tiles, h->block, s);
     if (e == cudaSuccess) {
-        if (m->path != MDG_MLP_PATH_MMA_SYNC) {
+        if (m->path == MDG_MLP_PATH_TCGEN05_PAIRS) {
+            // the paired kernel updates the state itself (no y, no separate update launch)
+            mdg::MlpApply ap{a.s.state, h->n_drones, h->uniform_N, m->env_flag, a.out_mean, a.out_std};
+            e = forward_umma(m, m->x, n_pad, m->y, h->d_status, s, &ap);
+            fused = true;
+        } else if (m->path != MDG_MLP_PATH_MMA_SYNC) {
             e = forward_umma(m, m->x, n_pad, m->y, h->d_status, s);
         } else {
             float* zs[3] = {nullptr, nullptr, nullptr};
@@ -501,7 +508,7 @@ int mdg_surrogate_step(mdg_handle h, mdg_mlp m, float* state, const float* actio
             e = mdg::mlp_forward(m->view(), m->x, n_pad, zs, hs, m->y, nullptr, nullptr, nullptr, s);
         }
     }
-    if (e == cudaSuccess) e = mdg::launch_surrogate_apply(a, s);
+    if (e == cudaSuccess && !fused) e = mdg::launch_surrogate_apply(a, s);
     if (e == cudaSuccess) e = mdg::launch_surrogate_fallback(a, s);
     if (e == cudaSuccess && n_fallback) e = cudaMemcpyAsync(n_fallback, m->fb_count, 4, cudaMemcpyDeviceToDevice, s);
     return e == cudaSuccess ? MDG_OK : cuda_fail(e, "mdg_surrogate_step");

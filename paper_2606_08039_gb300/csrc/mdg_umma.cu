@@ -530,10 +530,11 @@ __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t r[16])
         : "r"(taddr));
 }
 
+template <bool kApply>
 __global__ void __launch_bounds__(kThreads, 1)
     mlp_umma_pair_kernel(const __grid_constant__ CUtensorMap xmap, float* __restrict__ y, int n_tiles,
                          const uint8_t* __restrict__ w_img, const float* __restrict__ master, MlpView w,
-                         uint32_t* status, int wait_limit, int spin_limit)
+                         uint32_t* status, int wait_limit, int spin_limit, const MlpApply ap)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -784,16 +785,50 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!ok) break;
                 ++n_acc[t];
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                float v[8];
-                tmem_ld8(tmem + 256u * t + lane_off + p * 8, v);
+                const int tile = 2 * pr + t;
+                if constexpr (!kApply) {
+                    float v[8];
+                    tmem_ld8(tmem + 256u * t + lane_off + p * 8, v);
+                    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar(kPBarAccDrained + t));
+                    const float* b4 = master + w.b_off[3] + p * 8;
+                    float4* out = reinterpret_cast<float4*>(y + ((size_t)tile * kRows + row) * MDG_MLP_OUT_PAD + p * 8);
+                    out[0] = make_float4(v[0] + b4[0], v[1] + b4[1], v[2] + b4[2], v[3] + b4[3]);
+                    out[1] = make_float4(v[4] + b4[4], v[5] + b4[5], v[6] + b4[6], v[7] + b4[7]);
+                    continue;
+                } else {
+                // the state update instead of y: the warps of column part 0 read the row's first
+                // 16 columns (the 13 outputs) and update their drone; the others only release
+                float v[16];
+                if (p == 0) {
+                    tmem_ld8(tmem + 256u * t + lane_off, v);
+                    tmem_ld8(tmem + 256u * t + lane_off + 8, v + 8);
+                }
                 asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(bar(kPBarAccDrained + t));
-                const float* b4 = master + w.b_off[3] + p * 8;
-                const int tile = 2 * pr + t;
-                float4* out = reinterpret_cast<float4*>(y + ((size_t)tile * kRows + row) * MDG_MLP_OUT_PAD + p * 8);
-                out[0] = make_float4(v[0] + b4[0], v[1] + b4[1], v[2] + b4[2], v[3] + b4[3]);
-                out[1] = make_float4(v[4] + b4[4], v[5] + b4[5], v[6] + b4[6], v[7] + b4[7]);
+                const long long g = (long long)tile * kRows + row;
+                if (p == 0 && g < ap.n && !ap.env_flag[g / ap.uniform_N]) {
+                    const float* b = master + w.b_off[3];
+                    float dl[13];
+#pragma unroll
+                    for (int k = 0; k < 13; ++k) dl[k] = ap.out_mean[k] + ap.out_std[k] * (v[k] + b[k]);
+                    float4* S = ap.state;
+                    const long long n = ap.n;
+                    float4 s0 = S[g], s1 = S[n + g], s2 = S[2 * n + g], s3 = S[3 * n + g];
+                    s0.x += dl[0], s0.y += dl[1], s0.z += dl[2];
+                    float qv[4] = {s0.w + dl[3], s1.x + dl[4], s1.y + dl[5], s1.z + dl[6]};
+                    s1.w += dl[7], s2.x += dl[8], s2.y += dl[9];
+                    s2.z += dl[10], s2.w += dl[11], s3.x += dl[12];
+                    float qn = 0.f;
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) qn += qv[r] * qv[r];
+                    const float inv = rsqrtf(qn);
+                    s0.w = qv[0] * inv, s1.x = qv[1] * inv, s1.y = qv[2] * inv, s1.z = qv[3] * inv;
+                    S[g] = s0, S[n + g] = s1, S[2 * n + g] = s2, S[3 * n + g] = s3;
+                }
+                }
             }
         }
     }
@@ -1130,7 +1165,8 @@ EncodeTiledFn encode_tiled()
 }  // namespace
 
 cudaError_t mlp_forward_umma_pairs(const MlpView& w, const void* img, const void* x, int B, float* y,
-                                   uint32_t* status, int wait_limit, int spin_limit, cudaStream_t s)
+                                   uint32_t* status, int wait_limit, int spin_limit, cudaStream_t s,
+                                   const MlpApply* apply)
 {
     if (B % kRows) return cudaErrorInvalidValue;
     const int n_tiles = B / kRows;
@@ -1142,7 +1178,11 @@ cudaError_t mlp_forward_umma_pairs(const MlpView& w, const void* img, const void
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr_done[dev]) {
-        e = cudaFuncSetAttribute(mlp_umma_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmmaPairSmem);
+        e = cudaFuncSetAttribute(mlp_umma_pair_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kUmmaPairSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(mlp_umma_pair_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kUmmaPairSmem);
         if (e != cudaSuccess) return e;
         attr_done[dev] = true;
     }
@@ -1162,8 +1202,13 @@ cudaError_t mlp_forward_umma_pairs(const MlpView& w, const void* img, const void
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     const int n_pairs = (n_tiles + 1) / 2;
     const int grid = n_pairs < n_sm ? n_pairs : n_sm;
-    mlp_umma_pair_kernel<<<grid, kThreads, kUmmaPairSmem, s>>>(xmap, y, n_tiles, static_cast<const uint8_t*>(img),
-                                                               w.master, w, status, wait_limit, spin_limit);
+    const MlpApply ap = apply ? *apply : MlpApply{};
+    if (apply)
+        mlp_umma_pair_kernel<true><<<grid, kThreads, kUmmaPairSmem, s>>>(
+            xmap, y, n_tiles, static_cast<const uint8_t*>(img), w.master, w, status, wait_limit, spin_limit, ap);
+    else
+        mlp_umma_pair_kernel<false><<<grid, kThreads, kUmmaPairSmem, s>>>(
+            xmap, y, n_tiles, static_cast<const uint8_t*>(img), w.master, w, status, wait_limit, spin_limit, ap);
     return cudaGetLastError();
 }
 
