@@ -654,7 +654,9 @@ int mdg_features(mdg_handle h, const float* state, const float* rpm, float* raw,
  * standardised, the network predicts the state change, q is renormalised. An environment
  * any of whose drones has a standardised input beyond +-ood_z or a raw input outside the
  * normalisation box takes the plain integrator instead (n_substeps substeps of the handle's
- * integrator, Euler or RK4, with the handle's physics).
+ * integrator, Euler or RK4, with the handle's physics). On MDG_MLP_PATH_TCGEN05_PAIRS (the
+ * default) the network kernel adds the de-standardised change to the state itself; the other
+ * paths write the network's outputs and a separate kernel adds them (same arithmetic).
  * n_fallback: device int32 or NULL, receives the number of such environments. */
 int mdg_surrogate_step(mdg_handle h, mdg_mlp m, float* state, const float* action, int32_t action_type,
                        int32_t n_substeps, float ood_z, int32_t* n_fallback, void* stream);
