@@ -633,7 +633,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int n = kPLoadsPerPair * s + k;
                 return mbar_spin(bar(kPBarWFull + k % kPSlots), (n / kPSlots) & 1, abort, status, 0, spin_limit);
             };
-            auto wslot = [&](int k) { return slot_a + (uint32_t)(k % kPSlots) * kSlotBytes; };
+            // Shared-memory descriptors, computed once: a chunk's or slot's descriptor is the base
+            // descriptor plus its byte offset / 16 in the start-address field (every address of
+            // the block's shared memory is below 256 KB, so the field never carries), and the
+            // K step of 16 bf16 within a 128-byte row adds 32 bytes, i.e. 2.
+            const uint64_t act_desc = sw128_desc(act0), slot_desc = sw128_desc(slot_a);
+            auto wslot = [&](int k) { return slot_desc + (uint64_t)((k % kPSlots) * (kSlotBytes >> 4)); };
             auto release = [&](int k) { mma_commit(bar(kPBarWEmpty + k % kPSlots)); };
             // the first MMA of a layer into tile t's accumulator: the previous layer drained
             auto drained = [&](int t) {
@@ -645,13 +650,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 return mbar_spin(bar(kPBarActFull + 4 * t + c), (n_act >> (16 * t)) & 1, abort, status, 0, spin_limit);
             };
             // K chunk c of tile t's activations against the weight chunk in slot ws: four MMAs
-            auto chunk = [&](int t, int c, uint32_t ws, uint32_t id, bool first) {
+            auto chunk = [&](int t, int c, uint64_t wd, uint32_t id, bool first) {
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                const uint32_t asl = act0 + (uint32_t)t * 4 * kChunkBytes + c * kChunkBytes;
+                const uint64_t ad = act_desc + (uint64_t)((t * 4 + c) * (kChunkBytes >> 4));
+                const uint32_t d = tmem + 256u * t;
+                mma_bf16_ss(d, ad, wd, id, !first);
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    mma_bf16_ss(tmem + 256u * t, sw128_desc(asl + k * 32), sw128_desc(ws + k * 32), id,
-                                !(first && k == 0));
+                for (int k = 1; k < 4; ++k) mma_bf16_ss(d, ad + 2 * k, wd + 2 * k, id, 1);
             };
             for (int pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x, ++s) {
                 const bool hasB = 2 * pr + 1 < n_tiles;
@@ -701,16 +706,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                 ok = wfull(11);
                 for (int t = 0; t < nt && ok; ++t) {
                     ok = drained(t);
-                    const uint32_t wsl = wslot(11);
+                    const uint64_t wsl = wslot(11);
                     for (int c = 0; c < 4 && ok; ++c) {
                         if (t == 0 || c == 0) ok = act(t, t == 0 ? c : 3);
                         if (!ok) break;
                         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                        const uint32_t asl = act0 + (uint32_t)t * 4 * kChunkBytes + c * kChunkBytes, bsl = wsl + c * 4096;
+                        const uint64_t ad = act_desc + (uint64_t)((t * 4 + c) * (kChunkBytes >> 4));
+                        const uint64_t bd = wsl + (uint64_t)(c * (4096 >> 4));
 #pragma unroll
                         for (int k = 0; k < 4; ++k)
-                            mma_bf16_ss(tmem + 256u * t, sw128_desc(asl + k * 32), sw128_desc(bsl + k * 32), id_o,
-                                        (c | k) != 0);
+                            mma_bf16_ss(tmem + 256u * t, ad + 2 * k, bd + 2 * k, id_o, (c | k) != 0);
                     }
                     if (!ok) break;
                     n_act += 1u << (16 * t);
