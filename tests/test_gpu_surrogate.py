@@ -498,16 +498,21 @@ def test_fit_normalization_matches_its_definition(cuda):
     np.testing.assert_allclose(ts[:n_cmp, :mdg.MLP_OUT], Z[keep2][:n_cmp, mdg.MLP_IN:], rtol=1e-4, atol=1e-4)
 
 
-@pytest.mark.parametrize("recipe", ["full_aero", "dense", "dense_pid"])
+@pytest.mark.parametrize("recipe", ["full_aero", "full_aero_ragged", "dense", "dense_pid"])
 def test_surrogate_step_composes_its_parts(cuda, trained, recipe):
     """mdg_surrogate_step equals its parts called one by one: the plain integrator's inputs of
     the state and its RPMs (mdg_transition), their standardisation (mdg_mlp_standardize), the
     network (mdg_mlp_forward) and the de-standardised change added on the host (quaternion
-    renormalised), on 4-drone (PID) and 64-drone (RPM and PID) environments. With the trained box every
+    renormalised), on 4-drone (PID; also a drone count that is not a multiple of 128) and
+    64-drone (RPM and PID) environments. With the trained box every
     environment with an input outside it is counted for the fallback; with an unbounded box
     none is, and every drone is compared."""
     _, data, _ = trained
-    sw = wl.full_aero(81, n_envs=256) if recipe == "full_aero" else wl.dense(82, n_envs=16)
+    # full_aero_ragged: 1204 drones, not a multiple of the network's 128-row tiles: the last
+    # tile holds padding rows, which the fused update must not write (a row past the end of a
+    # state plane is the next plane's first drone, compared below)
+    sw = (wl.full_aero(81, n_envs=256) if recipe == "full_aero" else
+          wl.full_aero(83, n_envs=301) if recipe == "full_aero_ragged" else wl.dense(82, n_envs=16))
     h = mdg.Handle(sw.drones_per_env, sw.flags)
     if recipe == "dense":
         action, act = torch.as_tensor(wl.rpm_actions(82, sw.n, 0, HOVER), device=cuda), mdg.ACT_RPM
@@ -515,7 +520,7 @@ def test_surrogate_step_composes_its_parts(cuda, trained, recipe):
         action, act = torch.as_tensor(wl.waypoints(81, sw.n), device=cuda), mdg.ACT_PID
     in_mean, in_std, out_mean, out_std, in_lo, in_hi = data.stats()
     for bounded in (True, False):
-        m = mdg.MLP(sw.n + 128, wl.mlp_init(23))
+        m = mdg.MLP((sw.n + 127) // 128 * 128, wl.mlp_init(23))
         lo, hi = (in_lo, in_hi) if bounded else (np.full_like(in_lo, -1e30), np.full_like(in_hi, 1e30))
         m.set_normalization(in_mean, in_std, out_mean, out_std, lo, hi)
         ood_z = 4.0 if bounded else 1e30
